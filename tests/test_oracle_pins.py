@@ -1,0 +1,473 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks an oracle function against something other than itself: a
+closed form, an invariant, an independent brute-force computation, hand-derived
+values (tests/golden) or an analytic decay rate.  All run on the CPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from workloads import make_case
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------ Eq. 2 ---------
+def test_equilibrium_moments_closed_form(orc):
+    """Eq. 2: sum f^eq = rho, sum c f^eq = rho u, sum c c f^eq = rho/3 I + rho u u."""
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        rho = 1 + 0.1 * rng.standard_normal()
+        ux, uy = 0.1 * rng.standard_normal(2)
+        f = orc.feq(rho, ux, uy)
+        assert abs(f.sum() - rho) < 1e-15
+        assert abs((CX * f).sum() - rho * ux) < 1e-15
+        assert abs((CY * f).sum() - rho * uy) < 1e-15
+        assert abs((CX * CX * f).sum() - (rho / 3 + rho * ux * ux)) < 1e-15
+        assert abs((CX * CY * f).sum() - rho * ux * uy) < 1e-15
+        assert abs((CY * CY * f).sum() - (rho / 3 + rho * uy * uy)) < 1e-15
+
+
+def test_equilibrium_at_rest_is_weights(orc):
+    assert np.allclose(orc.feq(1.0, 0.0, 0.0), W, rtol=0, atol=1e-17)
+
+
+def test_collision_conserves_mass_and_momentum(orc):
+    """Eq. 1: the BGK collision leaves rho and rho u unchanged and relaxes f^neq by (1 - 1/tau)."""
+    rng = np.random.default_rng(2)
+    for tau in (0.51, 0.8, 1.7):
+        f = W * (1 + 0.05 * rng.standard_normal(9))
+        g = orc.bgk_collide(f, tau)
+        assert abs(g.sum() - f.sum()) < 1e-15
+        assert abs((CX * g).sum() - (CX * f).sum()) < 1e-15
+        assert abs((CY * g).sum() - (CY * f).sum()) < 1e-15
+        r, ux, uy = orc.moments(f)
+        eq = orc.feq(r, ux, uy)
+        assert np.allclose(g - eq, (1 - 1 / tau) * (f - eq), rtol=0, atol=1e-16)
+
+
+def test_moments(orc):
+    rng = np.random.default_rng(3)
+    f = W * (1 + 0.1 * rng.standard_normal(9))
+    r, ux, uy = orc.moments(f)
+    assert r == pytest.approx(f.sum(), abs=1e-16)
+    assert ux * r == pytest.approx((CX * f).sum(), abs=1e-16)
+    assert uy * r == pytest.approx((CY * f).sum(), abs=1e-16)
+
+
+# ------------------------------------------------------------ Eq. 1 ---------
+def _shear_wave_decay(orc, ny, tau, steps):
+    nx = 4
+    k = 2 * math.pi / ny
+    U = 1e-3
+    y = np.arange(ny)
+    f = np.zeros((ny, nx, 9))
+    for j in range(ny):
+        f[j, :, :] = orc.feq(1.0, U * math.sin(k * j), 0.0)
+    amp = []
+    for _ in range(2):
+        f = orc.lattice_periodic(f, tau, steps)
+        ux = (f * CX).sum(-1) / f.sum(-1)
+        amp.append(2 / ny * (ux.mean(axis=1) * np.sin(k * y)).sum())
+    rate = math.log(amp[0] / amp[1]) / steps
+    return rate / k**2  # measured viscosity
+
+
+def test_lattice_viscosity_and_order(orc):
+    """Eq. 1 with nu = c_s^2 (tau - 1/2): a shear wave decays at nu k^2, error O(k^2)."""
+    tau = 0.8
+    nu = (tau - 0.5) / 3
+    e16 = abs(_shear_wave_decay(orc, 16, tau, 60) / nu - 1)
+    e32 = abs(_shear_wave_decay(orc, 32, tau, 240) / nu - 1)
+    assert e32 < 3e-3
+    assert 3.5 < e16 / e32 < 4.5  # second order in space
+
+
+def test_periodic_lattice_streams_downstream(orc):
+    """Eq. 1 streaming: with tau = 1 a single population moves by c_i per step."""
+    ny, nx = 5, 6
+    f = np.zeros((ny, nx, 9))
+    f[2, 3, :] = orc.feq(1.0, 0.0, 0.0)
+    g = orc.lattice_periodic(f, 1.0, 1)
+    for i in range(9):
+        assert g[(2 + CY[i]) % ny, (3 + CX[i]) % nx, i] == pytest.approx(W[i], rel=1e-15)
+
+
+# ------------------------------------------------------------ Eq. 3 ---------
+def _random_patch(n=6, seed=4):
+    rng = np.random.default_rng(seed)
+    xs, ys = np.meshgrid(np.arange(n, dtype=float), np.arange(n, dtype=float))
+    xy = np.stack([xs.ravel(), ys.ravel()], 1)
+    inner = (xy[:, 0] > 0) & (xy[:, 0] < n - 1) & (xy[:, 1] > 0) & (xy[:, 1] < n - 1)
+    xy[inner] += 0.25 * (rng.random((inner.sum(), 2)) - 0.5)
+    tri = []
+    for j in range(n - 1):
+        for i in range(n - 1):
+            a, b, c, d = j * n + i, j * n + i + 1, (j + 1) * n + i, (j + 1) * n + i + 1
+            if (i + j) % 2:
+                tri += [(a, b, d), (a, d, c)]
+            else:
+                tri += [(a, b, c), (b, d, c)]
+    return xy, np.array(tri, dtype=np.int32)
+
+
+def test_fv_operator_invariants(orc):
+    """Eq. 3 operators: sum_k s_k = 0, sum_k C_Pk = 1, C_PP = 11/18, and linear exactness
+    sum_k s_k phi(P_k) = -grad phi on every node (the control volume is closed)."""
+    xy, tri = _random_patch()
+    rp, col, sx, sy, cc, area = orc.fv_operators(xy, tri)
+    for p in range(xy.shape[0]):
+        sl = slice(rp[p], rp[p + 1])
+        assert abs(sx[sl].sum()) < 1e-12 and abs(sy[sl].sum()) < 1e-12
+        assert cc[sl].sum() == pytest.approx(1.0, abs=1e-14)
+        assert cc[sl][col[sl] == p][0] == pytest.approx(11 / 18, abs=1e-14)
+        for gx, gy in ((1.0, 0.0), (0.0, 1.0), (0.3, -0.7)):
+            phi = gx * xy[col[sl], 0] + gy * xy[col[sl], 1]
+            assert (sx[sl] * phi).sum() == pytest.approx(-gx, abs=1e-12)
+            assert (sy[sl] * phi).sum() == pytest.approx(-gy, abs=1e-12)
+    p = xy[tri]
+    at = 0.5 * ((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) - (p[:, 1, 1] - p[:, 0, 1]) * (p[:, 2, 0] - p[:, 0, 0]))
+    assert area.sum() == pytest.approx(at.sum(), rel=1e-14)
+
+
+def _bary(pt, tri_pts):
+    a, b, c = tri_pts
+    d = (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0])
+    la = ((b[0] - pt[0]) * (c[1] - pt[1]) - (b[1] - pt[1]) * (c[0] - pt[0])) / d
+    lb = ((c[0] - pt[0]) * (a[1] - pt[1]) - (c[1] - pt[1]) * (a[0] - pt[0])) / d
+    return np.array([la, lb, 1 - la - lb])
+
+
+def test_fv_operators_match_brute_force_quadrature(orc):
+    """Eq. 3 operators against a direct numerical evaluation of the cell-vertex
+    control-volume integrals: Gauss quadrature of the hat functions over every
+    sub-quad and Gauss-Legendre flux integrals along every sub-quad edge (the
+    contributions of edges interior to the control volume cancel)."""
+    xy, tri = _random_patch(5, seed=9)
+    rp, col, sx, sy, cc, area = orc.fv_operators(xy, tri)
+    gl = [(0.5 - 0.5 / math.sqrt(3), 0.5), (0.5 + 0.5 / math.sqrt(3), 0.5)]
+    tq = [((1 / 6, 1 / 6), 1 / 3), ((2 / 3, 1 / 6), 1 / 3), ((1 / 6, 2 / 3), 1 / 3)]
+    n = xy.shape[0]
+    for p in range(n):
+        A = 0.0
+        integ = {}
+        flux = {}
+        for t in tri:
+            if p not in t:
+                continue
+            r = list(t).index(p)
+            order = [t[r], t[(r + 1) % 3], t[(r + 2) % 3]]
+            P, Aa, B = xy[order[0]], xy[order[1]], xy[order[2]]
+            tp = (P, Aa, B)
+            quad = [P, (P + Aa) / 2, (P + Aa + B) / 3, (P + B) / 2]
+            for s0, s1, s2 in ((quad[0], quad[1], quad[2]), (quad[0], quad[2], quad[3])):
+                ar = 0.5 * ((s1[0] - s0[0]) * (s2[1] - s0[1]) - (s1[1] - s0[1]) * (s2[0] - s0[0]))
+                A += ar
+                for (u, v), wq in tq:
+                    pt = s0 + u * (s1 - s0) + v * (s2 - s0)
+                    lam = _bary(pt, tp)
+                    for kk in range(3):
+                        integ[order[kk]] = integ.get(order[kk], 0.0) + ar * wq * lam[kk]
+            for e in range(4):
+                u0, u1 = quad[e], quad[(e + 1) % 4]
+                nl = np.array([u1[1] - u0[1], -(u1[0] - u0[0])])
+                for s, wq in gl:
+                    lam = _bary(u0 + s * (u1 - u0), tp)
+                    for kk in range(3):
+                        flux[order[kk]] = flux.get(order[kk], np.zeros(2)) + wq * lam[kk] * nl
+        assert area[p] == pytest.approx(A, rel=1e-13)
+        for e in range(rp[p], rp[p + 1]):
+            k = col[e]
+            assert cc[e] == pytest.approx(integ[k] / A, abs=1e-13)
+            assert sx[e] == pytest.approx(-flux[k][0] / A, abs=1e-12)
+            assert sy[e] == pytest.approx(-flux[k][1] / A, abs=1e-12)
+
+
+def test_fv_operators_unit_square_golden(orc):
+    """Eq. 3 operators of a corner node of the two-triangle unit square, against
+    the hand derivation in tests/golden/fv_unit_square.txt."""
+    rows = []
+    area = None
+    with open(os.path.join(GOLDEN, "fv_unit_square.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            if tok[0] == "area":
+                area = float(tok[1])
+            else:
+                rows.append([float(t) for t in tok])
+    xy = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], dtype=float)
+    tri = np.array([[0, 1, 2], [0, 2, 3]], dtype=np.int32)
+    rp, col, sx, sy, cc, ar = orc.fv_operators(xy, tri)
+    assert ar[0] == pytest.approx(area, abs=1e-15)
+    assert list(col[rp[0]:rp[1]]) == [0, 1, 2, 3]
+    for e, (k, gx, gy, gc) in zip(range(rp[0], rp[1]), rows):
+        assert col[e] == int(k)
+        assert sx[e] == pytest.approx(gx, abs=1e-15)
+        assert sy[e] == pytest.approx(gy, abs=1e-15)
+        assert cc[e] == pytest.approx(gc, abs=1e-15)
+
+
+def _periodic_mesh(n):
+    xy = np.array([[i, j] for j in range(n) for i in range(n)], dtype=float)
+    tri, txy = [], []
+    for j in range(n):
+        for i in range(n):
+            a = j * n + i
+            b = j * n + (i + 1) % n
+            c = ((j + 1) % n) * n + i
+            d = ((j + 1) % n) * n + (i + 1) % n
+            pa, pb, pc, pd = (i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1)
+            tri += [(a, b, d), (a, d, c)]
+            txy += [(pa, pb, pd), (pa, pd, pc)]
+    return xy, np.array(tri, dtype=np.int32), np.array(txy, dtype=float)
+
+
+def _fv_shear_nu(orc, n, tau_u, dt, t_end):
+    xy, tri, txy = _periodic_mesh(n)
+    ops = orc.fv_operators(xy, tri, txy)
+    k = 2 * math.pi / n
+    U = 1e-3
+    g = np.array([orc.feq(1.0, U * math.sin(k * y), 0.0) for _, y in xy])
+    steps = int(round(t_end / dt))
+    amp = []
+    for _ in range(2):
+        for _ in range(steps):
+            g = orc.fv_substep(ops, dt, tau_u, g)
+        ux = (g * CX).sum(1) / g.sum(1)
+        amp.append(2 / n**2 * (ux * np.sin(k * xy[:, 1])).sum())
+    return math.log(amp[0] / amp[1]) / t_end / k**2
+
+
+def test_fv_viscosity_on_periodic_triangles(orc):
+    """Eq. 3 with nu = c_s^2 tau_u: a shear wave on a periodic triangulated square
+    decays at nu k^2; the spatial error falls by about 4x per halving of h."""
+    tau_u = 0.1
+    nu = tau_u / 3
+    e8 = abs(_fv_shear_nu(orc, 8, tau_u, 0.002, 10.0) / nu - 1)
+    e16 = abs(_fv_shear_nu(orc, 16, tau_u, 0.002, 40.0) / nu - 1)
+    assert e16 < 0.035
+    assert 3.5 < e8 / e16 < 4.5
+
+
+def test_fv_uniform_state_is_steady(orc):
+    """Eq. 3: a uniform equilibrium is a fixed point (sum_k s_k = 0, and f = f^eq)."""
+    xy, tri = _random_patch()
+    ops = orc.fv_operators(xy, tri)
+    g = np.tile(orc.feq(1.01, 0.03, -0.02), (xy.shape[0], 1))
+    g2 = orc.fv_substep(ops, 0.01, 0.05, g)
+    assert np.abs(g2 - g).max() < 1e-16
+
+
+# ------------------------------------------------------------ wall ----------
+def test_wall_rule_closed_form(orc):
+    """Wall rule: density and non-equilibrium part kept, velocity set to zero."""
+    rng = np.random.default_rng(5)
+    g = W * (1 + 0.05 * rng.standard_normal(9))
+    h = orc.wall_rule(g)
+    r0, ux0, uy0 = orc.moments(g)
+    r1, ux1, uy1 = orc.moments(h)
+    assert r1 == pytest.approx(r0, abs=1e-15)
+    assert abs(ux1) < 1e-16 and abs(uy1) < 1e-16
+    assert np.allclose(h - orc.feq(r1, 0, 0), g - orc.feq(r0, ux0, uy0), rtol=0, atol=1e-16)
+
+
+# ------------------------------------------------------------ Eq. 8, 9 ------
+def test_quad6_weights_reproduce_quadratics(orc):
+    """Eq. 8: the six shape functions reproduce every quadratic exactly and sum to 1."""
+    rng = np.random.default_rng(6)
+    # a triangle plus the far vertices of its three edge neighbours (Fig. 1 layout)
+    base = np.array([[0, 0], [1, 0], [0, 1], [1, 1], [1, -1], [-1, 1]], dtype=float)
+    for _ in range(10):
+        A = np.eye(2) + 0.2 * rng.standard_normal((2, 2))
+        pts = base @ A.T * 1.7 + rng.standard_normal(2) * 5
+        pts += 0.05 * rng.standard_normal(pts.shape)
+        lam = rng.random(3)
+        lam /= lam.sum()
+        x, y = lam @ pts[:3]
+        w = orc.quad6_weights(pts, x, y)
+        assert w.sum() == pytest.approx(1.0, abs=1e-13)
+        c = rng.standard_normal(6)
+        q = lambda X, Y: c[0] + c[1] * X + c[2] * Y + c[3] * X * X + c[4] * X * Y + c[5] * Y * Y
+        assert (w * q(pts[:, 0], pts[:, 1])).sum() == pytest.approx(q(x, y), abs=1e-11)
+
+
+def test_quad6_weights_at_a_donor_are_a_delta(orc):
+    pts = np.array([[0, 0], [1, 0], [0, 1], [1, 1], [1, -1], [-1, 1]], dtype=float)
+    w = orc.quad6_weights(pts, 1.0, 0.0)
+    assert np.allclose(w, [0, 1, 0, 0, 0, 0], atol=1e-14)
+
+
+def test_biquad9_weights_reproduce_biquadratics(orc):
+    """Eq. 9: tensor Lagrange weights reproduce x^a y^b (a, b <= 2) exactly."""
+    rng = np.random.default_rng(7)
+    off = np.array([(a, b) for b in (-1, 0, 1) for a in (-1, 0, 1)], dtype=float)
+    for _ in range(20):
+        fx, fy = rng.random(2) - 0.5
+        w = orc.biquad9_weights(fx, fy)
+        for a in range(3):
+            for b in range(3):
+                assert (w * off[:, 0] ** a * off[:, 1] ** b).sum() == pytest.approx(fx**a * fy**b, abs=1e-15)
+    assert np.allclose(orc.biquad9_weights(0.0, 0.0), np.eye(9)[4], atol=0)
+
+
+# ------------------------------------------------------------ Eq. 10-11 -----
+def _polygon_walls(nv=24, rx=3.0, ry=1.3):
+    t = np.linspace(0, 2 * math.pi, nv, endpoint=False)
+    xy = np.stack([5 + rx * np.cos(t), 2 + ry * np.sin(t)], 1)
+    # fluid outside: walk the body clockwise so the fluid is on the left
+    ea = np.arange(nv)[::-1]
+    eb = np.roll(ea, -1)
+    area = 0.5 * abs(np.sum(xy[:, 0] * np.roll(xy[:, 1], -1) - np.roll(xy[:, 0], -1) * xy[:, 1]))
+    return xy, ea, eb, area
+
+
+def test_force_of_linear_pressure_is_buoyancy(orc):
+    """Eq. 10-11 pressure part: p = rho/3 linear in space gives
+    F = -(closed integral of p n) = -grad p * body area (divergence theorem;
+    the edge-mean rule is exact for a linear field on straight edges)."""
+    xy, ea, eb, area = _polygon_walls()
+    a, b = 0.013, -0.021
+    g = np.array([orc.feq(1 + a * x + b * y, 0.0, 0.0) for x, y in xy])
+    F = orc.wall_force(ea, eb, xy, g)
+    assert F[0] == pytest.approx(-a / 3 * area, rel=1e-12)
+    assert F[1] == pytest.approx(-b / 3 * area, rel=1e-12)
+
+
+def test_force_of_linear_stress_is_its_divergence(orc):
+    """Eq. 10-11 viscous part: with Pi^neq_xx = kappa x (other components 0) the
+    traction -Pi.n integrates to -kappa * body area in x (and 0 in y)."""
+    xy, ea, eb, area = _polygon_walls()
+    kappa = 0.004
+    g = []
+    for x, _ in xy:
+        M = np.array([[kappa * x, 0.0], [0.0, 0.0]])
+        neq = 4.5 * W * (CX * CX * M[0, 0] + 2 * CX * CY * M[0, 1] + CY * CY * M[1, 1]
+                         - (M[0, 0] + M[1, 1]) / 3)
+        g.append(orc.feq(1.0, 0.0, 0.0) + neq)
+    F = orc.wall_force(ea, eb, xy, np.array(g))
+    assert F[0] == pytest.approx(-kappa * area, rel=1e-12)
+    assert abs(F[1]) < 1e-15
+
+
+def test_airfoil_wall_edges_enclose_the_section(orc):
+    """The oracle's wall-edge list walks the whole NACA 0012 surface with the
+    fluid on its left: buoyancy of a linear pressure equals -grad p times the
+    section area (shoelace of the wall ring)."""
+    case = make_case("hlbm_small")
+    o = orc.Oracle(case, n_sub=10)
+    we = o.table("wall_edges").astype(int).reshape(-1, 2)
+    xy = o.table("xy").reshape(-1, 2)
+    wall = xy[: case.n_theta]
+    area = 0.5 * abs(np.sum(wall[:, 0] * np.roll(wall[:, 1], -1) - np.roll(wall[:, 0], -1) * wall[:, 1]))
+    assert we.shape[0] == case.n_theta
+    b = 0.01
+    g = np.array([orc.feq(1 + b * y, 0.0, 0.0) for _, y in xy])
+    F = orc.wall_force(we[:, 0], we[:, 1], xy, g)
+    assert F[1] == pytest.approx(-b / 3 * area, rel=1e-10)
+    # thickness 12 % of the chord: area of NACA 0012 is about 0.0822 C^2
+    assert area == pytest.approx(0.0822 * case.chord**2, rel=0.02)
+
+
+# ------------------------------------------------------------ whole method --
+def _max_dev(o, case, rho0, u0):
+    dev = 0.0
+    for grid in list(range(case.n_levels)) + ([-1] if case.n_nodes else []):
+        r, ux, uy = o.fields(grid)
+        m = np.isfinite(r)
+        dev = max(dev, np.abs(r[m] - rho0).max(), np.abs(ux[m] - u0).max(), np.abs(uy[m]).max())
+    return dev
+
+
+def test_uniform_stream_through_the_channel_is_steady(orc):
+    """Eq. 1 with the outer rules: a uniform stream (rho 1, u = (u0, 0)) is kept exactly."""
+    case = make_case("channel", perturb=0.0)
+    o = orc.Oracle(case)
+    o.step(40)
+    assert _max_dev(o, case, 1.0, case.Ma / math.sqrt(3)) < 1e-14
+
+
+@pytest.mark.parametrize("name", ["hlbm_small", "hlbm_mini2"])
+def test_rest_state_is_steady_through_the_coupling(orc, name):
+    """Fluid at rest stays exactly at rest through every part of the coupled method:
+    wall rule, Eq. 3, Eq. 4 with Eq. 8 and Eq. 5-7 with Eq. 9 (weights summing to
+    one), refinement and the outer rules.  (The stream speed u0 = Ma c_s is made
+    negligible; Re is scaled with it to keep nu = u0 C / Re = 0.005.)"""
+    case = make_case(name, perturb=0.0)
+    case.Ma = 1e-30
+    case.Re = case.Ma / math.sqrt(3) * case.chord / 0.005
+    o = orc.Oracle(case)
+    o.step(2)
+    assert _max_dev(o, case, 1.0, 0.0) < 1e-14
+
+
+def test_fv_conserves_mass_and_momentum_on_a_periodic_mesh(orc):
+    """Eq. 3 is conservative: on a closed (periodic) mesh sum_P A_P sum_i g_i and
+    sum_P A_P sum_i c_i g_i do not change (fluxes between neighbouring control
+    volumes cancel; the collision term has zero mass and momentum per node)."""
+    xy, tri, txy = _periodic_mesh(6)
+    rng = np.random.default_rng(8)
+    xy = xy.astype(float)
+    ops = orc.fv_operators(xy, tri, txy)
+    area = ops[5]
+    g = np.array([orc.feq(1 + 0.01 * rng.standard_normal(), *(0.05 * rng.standard_normal(2)))
+                  for _ in range(xy.shape[0])])
+    g += 1e-3 * rng.standard_normal(g.shape) * W
+    m0 = (area[:, None] * g).sum()
+    jx0 = (area[:, None] * g * CX).sum()
+    jy0 = (area[:, None] * g * CY).sum()
+    for _ in range(20):
+        g = orc.fv_substep(ops, 0.02, 0.05, g)
+    assert (area[:, None] * g).sum() == pytest.approx(m0, rel=1e-14)
+    assert (area[:, None] * g * CX).sum() == pytest.approx(jx0, abs=1e-14)
+    assert (area[:, None] * g * CY).sum() == pytest.approx(jy0, abs=1e-14)
+
+
+def test_refinement_interface_keeps_the_viscous_decay(orc):
+    """Refinement (factor 2, neq rescaled by tau_f / (2 tau_c) and back): a shear
+    wave on a periodic coarse level with a nested fine box decays at the
+    single-grid rate nu k^2 (same physical viscosity on both levels)."""
+    from workloads.naca import Case
+    n0 = 64
+    lv = np.array([[n0, n0, 0, 0], [65, 65, 16, 16]], dtype=np.int32)
+    # nu_finest = u0 C / Re with tau_f = 0.8  ->  nu_f = 0.1, nu_0 = 0.05
+    u0 = 0.1 / math.sqrt(3)
+    case = Case("shear2", lv, np.zeros((0, 2)), np.zeros((0, 3), np.int32), np.zeros(0, np.uint8),
+                chord=1.0, pivot=(0, 0), hole=(0, 0, 0, 0), Re=u0 / 0.1, Ma=0.1, aoa_deg=0.0,
+                perturb=0.0)
+    o = orc.Oracle(case, periodic0=True)
+    k = 2 * math.pi / n0
+    U = 1e-3
+    tau0, tau1 = o.tau(0), o.tau(1)
+    nu0 = (tau0 - 0.5) / 3
+
+    def ce_state(yc, dudy, tau):
+        # equilibrium plus the first-order Chapman-Enskog part of a shear flow
+        f = orc.feq(1.0, U * math.sin(k * yc), 0.0)
+        return f - tau * 3 * W * CX * CY * dudy
+
+    f0 = np.array([ce_state(j, U * k * math.cos(k * j), tau0) for j in range(n0) for _ in range(n0)])
+    o.set_populations(0, f0)
+    f1 = np.array([ce_state(16 + j / 2, U * k * math.cos(k * (16 + j / 2)) / 2, tau1)
+                   for j in range(65) for _ in range(65)])
+    o.set_populations(1, f1)
+    y = np.arange(n0)
+
+    def amp():
+        r, ux, _ = o.fields(0)
+        return 2 / n0 * (ux.reshape(n0, n0).mean(1) * np.sin(k * y)).sum()
+
+    o.step(50)
+    a0 = amp()
+    o.step(300)
+    a1 = amp()
+    nu_meas = math.log(a0 / a1) / 300 / k**2
+    assert nu_meas == pytest.approx(nu0, rel=0.01)

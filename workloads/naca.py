@@ -1,0 +1,220 @@
+"""NACA 0012 O-mesh and nested Cartesian levels (geometry inputs only).
+
+Geometry follows the problem statement of Di Ilio et al. (Section 4,
+"Problem setup"): a NACA 0012 airfoil placed symmetrically between the top
+and bottom boundaries, a body-fitted triangular mesh whose outer boundary is
+an ellipse, an inner interface curve that is also an ellipse, and nested
+Cartesian boxes refined by a factor of two whose innermost box has unit
+spacing and overlaps the triangular mesh.
+
+All coordinates are in finest-level lattice units in the frame of the finest
+level (its node (i, j) sits at (i, j)), in the zero-incidence pose; the solver
+rotates mesh and hole by the angle of attack itself.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Node kinds of the triangular mesh (the C ABI uses the same codes).
+KIND_FLUID = 0
+KIND_WALL = 1
+KIND_RING = 2
+
+
+def naca0012_half_thickness(x):
+    """Half thickness of the closed-trailing-edge NACA 0012 section, chord 1.
+
+    t(x) = 0.6 (0.2969 sqrt(x) - 0.1260 x - 0.3516 x^2 + 0.2843 x^3 - 0.1036 x^4);
+    the last coefficient closes the trailing edge (t(1) = 0).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    return 0.6 * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x**2
+                  + 0.2843 * x**3 - 0.1036 * x**4)
+
+
+def o_mesh(chord, leading_edge, n_theta, n_layers, stretch, ell_a, ell_b):
+    """Body-fitted O-type triangular mesh around a NACA 0012 section.
+
+    Surface node k (k = 0 .. n_theta-1) has parameter theta_k = 2 pi k / n_theta
+    and, with u = theta/pi on the upper surface (theta <= pi) and
+    u = 2 - theta/pi on the lower one, chord position
+    x = a (1 + cos(pi u)) / 2 + (1 - a) (1 - u)^2, where a is chosen so that
+    the wall spacing at the trailing edge equals the first-layer spacing
+    there (k = 0 is the trailing edge, k = n_theta/2 the leading edge).
+    Index k runs counter-clockwise.  The
+    matching outer-ellipse point (centred at mid-chord) has the same
+    parameter theta.  Mesh line k is the cubic Hermite curve from the surface
+    point (leaving along the outward surface normal) to the ellipse point;
+    ring j (0 .. n_layers) sits at curve parameter
+    s_j = (r^j - 1)/(r^n_layers - 1), r = stretch (uniform if r == 1).
+
+    Returns (xy[N,2] float64, tri[T,3] int32 counter-clockwise,
+    kind[N] uint8) with node index j * n_theta + k; ring 0 is the wall and
+    ring n_layers is the outer (overlap) ring.
+    """
+    if n_theta % 2:
+        raise ValueError("n_theta must be even")
+    le = np.asarray(leading_edge, dtype=np.float64)
+    j = np.arange(n_layers + 1, dtype=np.float64)
+    if stretch == 1.0:
+        s = j / n_layers
+    else:
+        s = (stretch**j - 1.0) / (stretch**n_layers - 1.0)
+    # trailing-edge wall spacing = first-layer spacing there (square cells at
+    # the sharp trailing edge instead of slivers)
+    h1 = s[1] * (ell_a - 0.5 * chord)
+    alpha = min(1.0, max(0.0, 1.0 - h1 * n_theta / (4.0 * chord)))
+    theta = 2.0 * math.pi * np.arange(n_theta) / n_theta
+    u = np.where(theta <= math.pi, theta, 2.0 * math.pi - theta) / math.pi
+    xc = alpha * 0.5 * (1.0 + np.cos(math.pi * u)) + (1.0 - alpha) * (1.0 - u) ** 2
+    sign = np.where(theta <= math.pi, 1.0, -1.0)
+    surf = np.stack([le[0] + chord * xc,
+                     le[1] + sign * chord * naca0012_half_thickness(xc)], axis=1)
+    mid = np.array([le[0] + 0.5 * chord, le[1]])
+    outer = np.stack([mid[0] + ell_a * np.cos(theta),
+                      mid[1] + ell_b * np.sin(theta)], axis=1)
+    # Mesh line k: cubic Hermite curve from surface point S_k, leaving along the
+    # outward surface normal, to ellipse point E_k, arriving along E_k - S_k.
+    tang = np.roll(surf, -1, axis=0) - np.roll(surf, 1, axis=0)
+    normal = np.stack([tang[:, 1], -tang[:, 0]], axis=1)
+    normal /= np.linalg.norm(normal, axis=1, keepdims=True)
+    span = outer - surf
+    length = np.linalg.norm(span, axis=1, keepdims=True)
+    t0 = length * normal
+    t1 = span
+    ss = s[:, None, None]
+    h00 = 2 * ss**3 - 3 * ss**2 + 1
+    h10 = ss**3 - 2 * ss**2 + ss
+    h01 = -2 * ss**3 + 3 * ss**2
+    h11 = ss**3 - ss**2
+    xy = h00 * surf[None] + h10 * t0[None] + h01 * outer[None] + h11 * t1[None]
+    xy = xy.reshape(-1, 2)
+
+    def nid(jj, kk):
+        return jj * n_theta + (kk % n_theta)
+
+    def min_altitude(t3):
+        p = xy[list(t3)]
+        a2 = ((p[1, 0] - p[0, 0]) * (p[2, 1] - p[0, 1])
+              - (p[1, 1] - p[0, 1]) * (p[2, 0] - p[0, 0]))
+        edge = max(np.hypot(*(p[1] - p[0])), np.hypot(*(p[2] - p[1])), np.hypot(*(p[0] - p[2])))
+        return a2 / edge
+
+    tris = []
+    for jj in range(n_layers):
+        for kk in range(n_theta):
+            a, b = nid(jj, kk), nid(jj, kk + 1)
+            c, d = nid(jj + 1, kk), nid(jj + 1, kk + 1)
+            # index k runs counter-clockwise and j outward, so (k,j),(k,j+1),(k+1,j)
+            # is counter-clockwise.  Each quad is split along the diagonal that
+            # gives the larger smallest altitude (this avoids slivers at the
+            # sharp trailing edge).
+            split1 = [(a, c, b), (b, c, d)]
+            split2 = [(a, c, d), (a, d, b)]
+            q1 = min(min_altitude(t) for t in split1)
+            q2 = min(min_altitude(t) for t in split2)
+            tris.extend(split1 if q1 >= q2 else split2)
+    tri = np.asarray(tris, dtype=np.int32)
+    kind = np.zeros(xy.shape[0], dtype=np.uint8)
+    kind[:n_theta] = KIND_WALL
+    kind[n_layers * n_theta:] = KIND_RING
+    p = xy[tri]
+    area2 = ((p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1])
+             - (p[:, 1, 1] - p[:, 0, 1]) * (p[:, 2, 0] - p[:, 0, 0]))
+    if not np.all(area2 > 0):
+        raise ValueError("O-mesh has inverted triangles; adjust its parameters")
+    return xy, tri, kind
+
+
+@dataclasses.dataclass
+class Case:
+    """One HLBM problem: Cartesian levels, triangular mesh and flow parameters."""
+
+    name: str
+    levels: np.ndarray          # [L,4] int32: nx, ny, ox, oy (origin in parent-level nodes)
+    xy: np.ndarray              # [N,2] float64, finest-level units, zero-incidence pose
+    tri: np.ndarray             # [T,3] int32, counter-clockwise
+    kind: np.ndarray            # [N] uint8: 0 fluid, 1 wall, 2 outer (overlap) ring
+    chord: float
+    pivot: tuple                # rotation centre (quarter chord)
+    hole: tuple                 # inner interface ellipse (cx, cy, a, b)
+    Re: float
+    Ma: float
+    aoa_deg: float
+    n_sub: int = 0              # 0: chosen by the solver from its stability bound
+    seed: int = 0
+    perturb: float = 1e-4
+    steps: int = 100            # coarse steps of the nominal run
+    n_theta: int = 0
+    n_layers: int = 0
+
+    @property
+    def n_levels(self):
+        return int(self.levels.shape[0])
+
+    @property
+    def n_nodes(self):
+        return int(self.xy.shape[0])
+
+
+def _mesh_case(name, levels, chord, mid, n_theta, n_layers, stretch, ell_b_ratio,
+               overlap, Re, Ma, aoa_deg, steps, **kw):
+    le = (mid[0] - 0.5 * chord, mid[1])
+    ell_a, ell_b = chord, ell_b_ratio * chord
+    xy, tri, kind = o_mesh(chord, le, n_theta, n_layers, stretch, ell_a, ell_b)
+    return Case(name=name, levels=np.asarray(levels, dtype=np.int32), xy=xy, tri=tri,
+                kind=kind, chord=float(chord), pivot=(le[0] + 0.25 * chord, le[1]),
+                hole=(mid[0], mid[1], ell_a - overlap, ell_b - overlap), Re=float(Re),
+                Ma=float(Ma), aoa_deg=float(aoa_deg), steps=steps, n_theta=n_theta,
+                n_layers=n_layers, **kw)
+
+
+def _channel(name, nx, ny, Re, Ma, steps):
+    return Case(name=name, levels=np.asarray([[nx, ny, 0, 0]], dtype=np.int32),
+                xy=np.zeros((0, 2)), tri=np.zeros((0, 3), dtype=np.int32),
+                kind=np.zeros(0, dtype=np.uint8), chord=float(ny), pivot=(0.0, 0.0),
+                hole=(0.0, 0.0, 0.0, 0.0), Re=float(Re), Ma=float(Ma), aoa_deg=0.0,
+                steps=steps)
+
+
+def make_case(name, aoa_deg=None, **overrides):
+    """Build a named configuration (see CONFIGS); keyword overrides patch the Case."""
+    if name not in CONFIGS:
+        raise KeyError(f"unknown configuration {name!r}; known: {sorted(CONFIGS)}")
+    case = CONFIGS[name]()
+    if aoa_deg is not None:
+        case.aoa_deg = float(aoa_deg)
+    for k, v in overrides.items():
+        if not hasattr(case, k):
+            raise AttributeError(k)
+        setattr(case, k, v)
+    return case
+
+
+CONFIGS = {
+    # Plain HLBM, small: one 200x100 level, chord 40, 80 x 65-ring O-mesh
+    # (64 layers stretched 1.05), outer ring overlapping the lattice by 4 cells,
+    # Re 500, Ma 0.1, 2000 steps.
+    "hlbm_small": lambda: _mesh_case(
+        "hlbm_small", [[200, 100, 0, 0]], chord=40.0, mid=(70.0, 50.0),
+        n_theta=80, n_layers=64, stretch=1.05, ell_b_ratio=0.6, overlap=4.0,
+        Re=500.0, Ma=0.1, aoa_deg=0.0, steps=2000),
+    # Two-level mini case for refinement parity: 96x48 coarse level and one
+    # 97x65 fine box, chord 24 finest units.
+    "hlbm_mini2": lambda: _mesh_case(
+        "hlbm_mini2", [[96, 48, 0, 0], [97, 65, 24, 8]], chord=24.0, mid=(40.0, 32.0),
+        n_theta=48, n_layers=20, stretch=1.08, ell_b_ratio=0.6, overlap=4.0,
+        Re=200.0, Ma=0.1, aoa_deg=0.0, steps=100),
+    # Single case: 2048x1024 coarse level with two nested factor-2 boxes of
+    # 1025x513 nodes, chord 200 finest units, 1024 x 196-ring O-mesh
+    # (200 704 nodes), Re 1000, Ma 0.1.
+    "hlbm_single": lambda: _mesh_case(
+        "hlbm_single", [[2048, 1024, 0, 0], [1025, 513, 512, 384], [1025, 513, 256, 128]],
+        chord=200.0, mid=(412.0, 256.0), n_theta=1024, n_layers=195, stretch=1.01,
+        ell_b_ratio=0.6, overlap=4.0, Re=1000.0, Ma=0.1, aoa_deg=0.0, steps=100000),
+    # Mesh-less channel (lattice and outer boundaries only).
+    "channel": lambda: _channel("channel", 64, 32, Re=100.0, Ma=0.1, steps=100),
+}

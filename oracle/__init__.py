@@ -74,6 +74,8 @@ def lib(openmp=False):
             L.orc_fv_operators.argtypes = [C.c_int, _dp, C.c_int, _ip, _dp, _ip, _ip, _dp, _dp, _dp, _dp]
             L.orc_fv_substep.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
             L.orc_wall_rule.argtypes = [_dp]
+            L.orc_eq4_post.argtypes = [_dp, C.c_double, _dp]
+            L.orc_eq5_base.argtypes = [_dp, C.c_double, _dp]
             L.orc_quad6_weights.argtypes = [_dp, C.c_double, C.c_double, _dp]
             L.orc_biquad9_weights.argtypes = [C.c_double, C.c_double, _dp]
             L.orc_wall_force.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp]
@@ -159,6 +161,20 @@ def wall_rule(g):
     g = _d(g).copy()
     lib().orc_wall_rule(_pd(g))
     return g
+
+
+def eq4_post(q, tau_s):
+    """Eq. 4 post-collision structured state from q = (rho, ux, uy, f^neq[9])."""
+    q, out = _d(q), np.empty(9)
+    lib().orc_eq4_post(_pd(q), tau_s, _pd(out))
+    return out
+
+
+def eq5_base(q, tau_s):
+    """Eq. 5-6 structured part of an unstructured interface state."""
+    q, out = _d(q), np.empty(9)
+    lib().orc_eq5_base(_pd(q), tau_s, _pd(out))
+    return out
 
 
 def quad6_weights(pts, x, y):

@@ -82,6 +82,22 @@ static void from_q(const double *q, double scale, double *f)
     for (int i = 0; i < 9; i++) f[i] = eq[i] + scale * q[3 + i];
 }
 
+/* Eq. 4: post-collision state of a structured interpolation node from
+ * interpolated unstructured data q = (rho, u, f^neq,u):
+ * f~s = f^eq + 2 (tau_s - 1) / (2 tau_s - 1) f^neq,u  (unit structured step). */
+void orc_eq4_post(const double *q, double tau_s, double *f)
+{
+    from_q(q, 2.0 * (tau_s - 1.0) / (2.0 * tau_s - 1.0), f);
+}
+
+/* Eq. 5-6: the structured part of the state of an unstructured interpolation
+ * node from interpolated lattice data q = (rho, u, f^neq,s):
+ * f^eq,s + (1 - 1/(2 tau_s)) f^neq,s. */
+void orc_eq5_base(const double *q, double tau_s, double *g)
+{
+    from_q(q, 1.0 - 1.0 / (2.0 * tau_s), g);
+}
+
 /* Eq. 1 collision (right-hand side), unit time step on the grid's own clock:
  * f* = f - (f - f^eq) / tau. */
 void orc_bgk_collide(double *f, double tau)
@@ -599,7 +615,7 @@ static void ring_set(orc *o, double theta)
         double q[12];
         for (int m = 0; m < 12; m++)
             q[m] = (1.0 - theta) * o->Q0[12 * (size_t)r + m] + theta * o->Q1[12 * (size_t)r + m];
-        from_q(q, 1.0 - 1.0 / (2.0 * tau_s), o->g + 9 * (size_t)o->ring[r]);
+        orc_eq5_base(q, tau_s, o->g + 9 * (size_t)o->ring[r]);
     }
 }
 
@@ -608,7 +624,6 @@ static void ring_set(orc *o, double theta)
 static void hole_interp(orc *o)
 {
     olevel *l = &o->lv[o->L - 1];
-    double tau_s = l->tau, scale = 2.0 * (tau_s - 1.0) / (2.0 * tau_s - 1.0);
     for (int s = 0; s < o->n_is; s++) {
         double q[12] = {0};
         for (int k = 0; k < 6; k++) {
@@ -616,7 +631,7 @@ static void hole_interp(orc *o)
             state_q(o->g + 9 * (size_t)o->is_don[6 * s + k], qk);
             for (int m = 0; m < 12; m++) q[m] += o->is_w[6 * s + k] * qk[m];
         }
-        from_q(q, scale, l->post + 9 * (size_t)o->is_node[s]);
+        orc_eq4_post(q, l->tau, l->post + 9 * (size_t)o->is_node[s]);
     }
 }
 

@@ -1,0 +1,176 @@
+/*
+ * hlbm.h - C ABI of the GB300 hybrid lattice Boltzmann (HLBM) library.
+ *
+ * The library advances the coupled grid system of Di Ilio, Chiappini,
+ * Ubertini, Bella and Succi ("Fluid flow around NACA 0012 airfoil at
+ * low-Reynolds numbers with hybrid lattice Boltzmann method") on one GPU:
+ *   - D2Q9 BGK lattice on nested Cartesian levels refined by a factor of two
+ *     (Eq. 1, Eq. 2; Section 4 for the refinement boxes and outer conditions),
+ *   - cell-vertex finite-volume LBE on a body-fitted triangular mesh with the
+ *     airfoil wall condition (Eq. 3; Section 4),
+ *   - the overlap interpolation between the two grids (Eq. 4-9),
+ *   - the drag and lift coefficients (Eq. 10-11).
+ *
+ * Conventions used by every entry point:
+ *   - All functions return an int status (HLBM_OK = 0, negative on error);
+ *     hlbm_last_error(ctx) gives a message for the last failing call on ctx.
+ *   - Pointers are plain host pointers unless stated otherwise; the library
+ *     copies every input it needs, so the caller may free them on return.
+ *   - Lengths are finest-level lattice units: the finest level has unit
+ *     spacing and unit time step.  Flow enters along +x.
+ *   - A context is not thread-safe; separate contexts are independent.
+ */
+#ifndef HLBM_H
+#define HLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HLBM_OK 0
+#define HLBM_EINVAL (-1)    /* invalid argument or geometry                    */
+#define HLBM_ENOMEM (-2)    /* device or host allocation failed                */
+#define HLBM_ECUDA (-3)     /* CUDA runtime error                              */
+#define HLBM_EUNSTABLE (-4) /* NaN in the force reduction (simulation unstable) */
+#define HLBM_ETIMEOUT (-5)  /* a device-side wait gave up                      */
+#define HLBM_ESTATE (-6)    /* call not valid in the context's current state   */
+#define HLBM_ENOTIMPL (-7)  /* feature not available in this build             */
+
+#define HLBM_FP64 0 /* populations and arithmetic in double precision          */
+#define HLBM_FP32 1 /* populations stored as f - w_i in float, float arithmetic */
+
+/* Node kinds of the triangular mesh. */
+#define HLBM_NODE_FLUID 0
+#define HLBM_NODE_WALL 1 /* airfoil surface: no-slip wall rule, force nodes      */
+#define HLBM_NODE_RING 2 /* outer ring: unstructured interpolation node (Eq. 5)  */
+
+/* One Cartesian level (Section 4: nested rectangular boxes, spacing halved
+ * per level).  Level 0 is the coarsest and has ox = oy = 0.  Level l > 0 has
+ * odd nx, ny; its node (i, j) sits at (ox + i/2, oy + j/2) in level l-1 node
+ * units and the box lies at least two parent nodes inside its parent. */
+typedef struct {
+    int32_t nx, ny;
+    int32_t ox, oy;
+} hlbm_level;
+
+/* The body-fitted triangular mesh (Section 4), in finest-level units and in
+ * the zero-incidence pose.  xy: [n_nodes][2]; tri: [n_tri][3] counter-
+ * clockwise node indices; kind: [n_nodes] HLBM_NODE_*.  pivot: rotation
+ * centre (quarter chord).  hole: inner interface ellipse (cx, cy, a, b), axis
+ * aligned in the zero-incidence pose; finest-level nodes inside it are not
+ * computed.  n_nodes == 0 gives a plain channel (lattice only). */
+typedef struct {
+    int32_t n_nodes;
+    const double *xy;
+    int32_t n_tri;
+    const int32_t *tri;
+    const uint8_t *kind;
+    double chord;
+    double pivot[2];
+    double hole[4];
+} hlbm_mesh;
+
+/* Options.  precision: HLBM_FP64 or HLBM_FP32.  n_sub: finite-volume
+ * sub-steps per finest lattice step (Section 6.3 uses 10); 0 selects the
+ * library's stability bound.  seed, perturb: initial density 1 + perturb*xi
+ * with xi uniform in [-1, 1) from splitmix64(seed ^ (grid << 40) ^ node)
+ * (grid = level index, 63 for the mesh).  force_cap: length of the device
+ * ring buffer of force samples (one sample per coarse step; 0 -> 4096).
+ * check_every: hlbm_step synchronises and reads the health flag every
+ * check_every coarse steps (0 -> only at the end of each call).
+ * stream: cudaStream_t to run on (NULL: the legacy default stream).
+ * alloc/free/alloc_ctx: optional device allocator (e.g. PyTorch's caching
+ * allocator); NULL alloc means cudaMalloc/cudaFree.  use_graphs: capture one
+ * coarse step as a CUDA graph (1, default when the struct is zeroed is 0). */
+typedef struct {
+    int32_t precision;
+    int32_t n_sub;
+    uint64_t seed;
+    double perturb;
+    int32_t force_cap;
+    int32_t check_every;
+    void *stream;
+    void *(*alloc)(size_t bytes, void *alloc_ctx);
+    void (*free)(void *ptr, void *alloc_ctx);
+    void *alloc_ctx;
+    int32_t use_graphs;
+} hlbm_options;
+
+typedef struct hlbm_ctx hlbm_ctx;
+
+/* Create a simulation.  lv: [n_levels] levels (1 <= n_levels <= 8); m: the
+ * mesh (may have n_nodes == 0); Re = u0 C / nu with u0 = Ma c_s, c_s^2 = 1/3;
+ * aoa_deg: angle of attack, applied as a rotation of mesh and hole by -aoa
+ * about the pivot (positive = nose up).  Copies every input, computes all
+ * set-up tables on the host (Eq. 3 operators, Eq. 8 and Eq. 9 stencils,
+ * refinement maps), uploads them and initialises the state.  On error *out is
+ * NULL and the message is available via hlbm_last_error(NULL). */
+int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re, double Ma,
+                double aoa_deg, const hlbm_options *opt, hlbm_ctx **out);
+
+/* Advance n_coarse coarse (level-0) steps, asynchronously on the context's
+ * stream.  One coarse step runs 2^l steps of level l and, per finest step,
+ * n_sub finite-volume sub-steps; one force sample is recorded per coarse
+ * step.  Returns HLBM_EUNSTABLE if the health flag (NaN in the forces) is set. */
+int hlbm_step(hlbm_ctx *ctx, int n_coarse);
+
+/* Copy the force samples recorded since the previous call (oldest first, at
+ * most cap of them, FP64) into host arrays cd[], cl[] (Eq. 10-11: force over
+ * 1/2 rho0 u0^2 C).  *n_written receives the count.  Samples older than
+ * force_cap coarse steps are lost.  Synchronises the stream. */
+int hlbm_forces(hlbm_ctx *ctx, double *cd, double *cl, int cap, int *n_written);
+
+/* Density and velocity of one grid into host FP64 arrays of cap entries:
+ * grid = -1 for the mesh (n_nodes entries, input node order) or a level
+ * index (nx*ny entries, x fastest).  Nodes that are not computed (inside the
+ * hole) get NaN.  Synchronises the stream. */
+int hlbm_fields(hlbm_ctx *ctx, int grid, double *rho, double *ux, double *uy, size_t cap);
+
+/* Populations f_i (not deviations) of one grid into a host FP64 array of
+ * cap entries, node-major: out[9 * node + i], D2Q9 order
+ * (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1). */
+int hlbm_populations(hlbm_ctx *ctx, int grid, double *out, size_t cap);
+
+/* Scalar information: "n_sub", "n_levels", "tau_u", "tau0".."tau7", "steps",
+ * "n_interp" (structured interpolation nodes), "n_ring", "n_wall_edges",
+ * "lattice_updates" (computed lattice node updates per coarse step),
+ * "fv_updates" (finite-volume node updates per coarse step),
+ * "launches_per_step" (kernels in one coarse step), "fv_bytes" (algorithmic
+ * bytes of one finite-volume sub-step), "collide_bytes<l>" (algorithmic bytes
+ * of one lattice step of level l). */
+int hlbm_info(const hlbm_ctx *ctx, const char *key, double *value);
+
+/* Measurement hook: runs one kernel of the step `reps` times back to back on
+ * the context's stream (kernel = "fv" for the Eq. 3 sub-step, "collide<l>" for
+ * the Eq. 1 step of level l) and returns the mean duration from CUDA events.
+ * The kernels really update the state, so afterwards the context only serves
+ * readback and hlbm_destroy (hlbm_step returns HLBM_ESTATE). */
+int hlbm_time_kernel(hlbm_ctx *ctx, const char *kernel, int reps, double *avg_ms);
+
+/* Host-only set-up (no GPU needed): runs the same set-up as hlbm_create and
+ * copies the named table into out (cap doubles); *n receives its length.
+ * Tables: "rowptr", "col", "sx", "sy", "cc" (Eq. 3 operators, CSR over the
+ * input node order, columns ascending), "area", "xy" (rotated),
+ * "is_node", "is_don", "is_w" (Eq. 8 stencils), "ring", "ring_don",
+ * "ring_w" (Eq. 9 stencils), "wall_edges", "n_sub".  out == NULL queries n. */
+int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re, double Ma,
+                 double aoa_deg, const hlbm_options *opt, const char *table, double *out,
+                 size_t cap, size_t *n);
+
+/* Wait for all work of the context. */
+int hlbm_sync(hlbm_ctx *ctx);
+
+/* Release the context and its device memory. */
+int hlbm_destroy(hlbm_ctx *ctx);
+
+/* Message of the last error on ctx (ctx == NULL: the last failing create or
+ * inspect on this thread). */
+const char *hlbm_last_error(const hlbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HLBM_H */

@@ -1,0 +1,261 @@
+"""GB300 hybrid lattice Boltzmann (HLBM) library: Python binding of libhlbm.so.
+
+The binding only marshals arguments; every step of the method runs in the
+library's CUDA kernels.  PyTorch supplies the CUDA stream and (optionally) the
+device allocator.  The functions mirror the C ABI in include/hlbm.h:
+hlbm_create, hlbm_step, hlbm_forces, hlbm_fields, hlbm_populations,
+hlbm_info, hlbm_inspect, hlbm_sync, hlbm_destroy, hlbm_last_error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhlbm.so")
+
+HLBM_OK, HLBM_EINVAL, HLBM_ENOMEM, HLBM_ECUDA = 0, -1, -2, -3
+HLBM_EUNSTABLE, HLBM_ETIMEOUT, HLBM_ESTATE, HLBM_ENOTIMPL = -4, -5, -6, -7
+HLBM_FP64, HLBM_FP32 = 0, 1
+PRECISIONS = {"fp64": HLBM_FP64, "fp32": HLBM_FP32}
+
+
+class HlbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hlbm error {code}: {msg}")
+        self.code = code
+
+
+class hlbm_level(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("ox", C.c_int32), ("oy", C.c_int32)]
+
+
+class hlbm_mesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("xy", C.POINTER(C.c_double)), ("n_tri", C.c_int32),
+                ("tri", C.POINTER(C.c_int32)), ("kind", C.POINTER(C.c_uint8)), ("chord", C.c_double),
+                ("pivot", C.c_double * 2), ("hole", C.c_double * 4)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class hlbm_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("n_sub", C.c_int32), ("seed", C.c_uint64), ("perturb", C.c_double),
+                ("force_cap", C.c_int32), ("check_every", C.c_int32), ("stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("use_graphs", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libhlbm.so; raises if the CUDA library has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_2006_10487_gb300.build` (there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
+        L.hlbm_create.argtypes = [C.POINTER(hlbm_level), C.c_int, C.POINTER(hlbm_mesh), C.c_double, C.c_double,
+                                  C.c_double, C.POINTER(hlbm_options), C.POINTER(C.c_void_p)]
+        L.hlbm_step.argtypes = [C.c_void_p, C.c_int]
+        L.hlbm_forces.argtypes = [C.c_void_p, dp, dp, C.c_int, ip]
+        L.hlbm_fields.argtypes = [C.c_void_p, C.c_int, dp, dp, dp, C.c_size_t]
+        L.hlbm_populations.argtypes = [C.c_void_p, C.c_int, dp, C.c_size_t]
+        L.hlbm_info.argtypes = [C.c_void_p, C.c_char_p, dp]
+        L.hlbm_inspect.argtypes = [C.POINTER(hlbm_level), C.c_int, C.POINTER(hlbm_mesh), C.c_double, C.c_double,
+                                   C.c_double, C.POINTER(hlbm_options), C.c_char_p, dp, C.c_size_t,
+                                   C.POINTER(C.c_size_t)]
+        L.hlbm_time_kernel.argtypes = [C.c_void_p, C.c_char_p, C.c_int, dp]
+        L.hlbm_sync.argtypes = [C.c_void_p]
+        L.hlbm_destroy.argtypes = [C.c_void_p]
+        L.hlbm_last_error.argtypes = [C.c_void_p]
+        L.hlbm_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def hlbm_last_error(ctx=None):
+    return lib().hlbm_last_error(ctx).decode()
+
+
+def _check(rc, ctx=None):
+    if rc != HLBM_OK:
+        raise HlbmError(rc, hlbm_last_error(ctx))
+
+
+def _marshal(case, precision="fp64", n_sub=None, seed=None, perturb=None, force_cap=0, check_every=0,
+             stream=None, use_graphs=True, allocator=None):
+    """C structures for a workloads.Case (kept alive by the returned tuple)."""
+    lv = (hlbm_level * case.n_levels)(*[hlbm_level(*map(int, r)) for r in case.levels])
+    xy = np.ascontiguousarray(case.xy, dtype=np.float64).reshape(-1)
+    tri = np.ascontiguousarray(case.tri, dtype=np.int32).reshape(-1)
+    kind = np.ascontiguousarray(case.kind, dtype=np.uint8)
+    m = hlbm_mesh()
+    m.n_nodes = case.n_nodes
+    m.xy = xy.ctypes.data_as(C.POINTER(C.c_double))
+    m.n_tri = int(case.tri.shape[0]) if case.n_nodes else 0
+    m.tri = tri.ctypes.data_as(C.POINTER(C.c_int32))
+    m.kind = kind.ctypes.data_as(C.POINTER(C.c_uint8))
+    m.chord = case.chord
+    m.pivot[:] = list(map(float, case.pivot))
+    m.hole[:] = list(map(float, case.hole))
+    o = hlbm_options()
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.n_sub = int(case.n_sub if n_sub is None else n_sub)
+    o.seed = int(case.seed if seed is None else seed)
+    o.perturb = float(case.perturb if perturb is None else perturb)
+    o.force_cap = int(force_cap)
+    o.check_every = int(check_every)
+    o.stream = stream
+    o.use_graphs = 1 if use_graphs else 0
+    if allocator is not None:
+        o.alloc, o.free = allocator
+    return lv, m, o, (xy, tri, kind)
+
+
+def hlbm_inspect(case, table, **kw):
+    """Host-only set-up table (no GPU needed), as float64 numpy array."""
+    lv, m, o, keep = _marshal(case, **kw)
+    n = C.c_size_t()
+    L = lib()
+    _check(L.hlbm_inspect(lv, case.n_levels, C.byref(m), case.Re, case.Ma, case.aoa_deg, C.byref(o),
+                          table.encode(), None, 0, C.byref(n)))
+    out = np.empty(n.value)
+    _check(L.hlbm_inspect(lv, case.n_levels, C.byref(m), case.Re, case.Ma, case.aoa_deg, C.byref(o),
+                          table.encode(), out.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n)))
+    return out
+
+
+def _torch_allocator():
+    import torch
+    dev = torch.cuda.current_device()
+
+    def _alloc(size, _ctx):
+        return torch.cuda.caching_allocator_alloc(int(size), dev, torch.cuda.current_stream(dev))
+
+    def _free(ptr, _ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return ALLOC_FN(_alloc), FREE_FN(_free)
+
+
+class Solver:
+    """One HLBM simulation on the current CUDA device (wraps an hlbm_ctx)."""
+
+    def __init__(self, case, precision="fp64", n_sub=None, seed=None, perturb=None, force_cap=0, check_every=0,
+                 use_graphs=True, stream=None, torch_memory=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the HLBM library needs a CUDA device (there is no CPU fallback)")
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self._alloc = _torch_allocator() if torch_memory else None
+        self._args = _marshal(case, precision, n_sub, seed, perturb, force_cap, check_every, stream, use_graphs,
+                              self._alloc)
+        lv, m, o, _ = self._args
+        ctx = C.c_void_p()
+        self._lib = lib()
+        _check(self._lib.hlbm_create(lv, case.n_levels, C.byref(m), case.Re, case.Ma, case.aoa_deg, C.byref(o),
+                                     C.byref(ctx)))
+        self.ctx = ctx
+        self.case = case
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self._lib.hlbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n_coarse=1):
+        _check(self._lib.hlbm_step(self.ctx, int(n_coarse)), self.ctx)
+
+    def sync(self):
+        _check(self._lib.hlbm_sync(self.ctx), self.ctx)
+
+    def info(self, key):
+        v = C.c_double()
+        _check(self._lib.hlbm_info(self.ctx, key.encode(), C.byref(v)), self.ctx)
+        return v.value
+
+    def forces(self, cap=1 << 20):
+        cd, cl = np.empty(cap), np.empty(cap)
+        n = C.c_int()
+        dp = C.POINTER(C.c_double)
+        _check(self._lib.hlbm_forces(self.ctx, cd.ctypes.data_as(dp), cl.ctypes.data_as(dp), cap, C.byref(n)),
+               self.ctx)
+        return cd[:n.value].copy(), cl[:n.value].copy()
+
+    def time_kernel(self, kernel, reps=50):
+        """Mean duration (ms) of one kernel of the step ("fv", "collide<l>"),
+        from CUDA events; consumes the state (only readback afterwards)."""
+        v = C.c_double()
+        _check(self._lib.hlbm_time_kernel(self.ctx, kernel.encode(), int(reps), C.byref(v)), self.ctx)
+        return v.value
+
+    def _size(self, grid):
+        if grid == -1:
+            return self.case.n_nodes
+        nx, ny = self.case.levels[grid][:2]
+        return int(nx) * int(ny)
+
+    def fields(self, grid):
+        n = self._size(grid)
+        r, x, y = np.empty(n), np.empty(n), np.empty(n)
+        dp = C.POINTER(C.c_double)
+        _check(self._lib.hlbm_fields(self.ctx, grid, r.ctypes.data_as(dp), x.ctypes.data_as(dp),
+                                     y.ctypes.data_as(dp), n), self.ctx)
+        return r, x, y
+
+    def populations(self, grid):
+        n = self._size(grid)
+        out = np.empty(9 * n)
+        _check(self._lib.hlbm_populations(self.ctx, grid, out.ctypes.data_as(C.POINTER(C.c_double)), 9 * n),
+               self.ctx)
+        return out.reshape(n, 9)
+
+
+# names of the C ABI, for callers that prefer the flat interface
+def hlbm_create(case, **kw):
+    return Solver(case, **kw)
+
+
+def hlbm_step(solver, n_coarse=1):
+    return solver.step(n_coarse)
+
+
+def hlbm_forces(solver, cap=1 << 20):
+    return solver.forces(cap)
+
+
+def hlbm_fields(solver, grid):
+    return solver.fields(grid)
+
+
+def hlbm_populations(solver, grid):
+    return solver.populations(grid)
+
+
+def hlbm_info(solver, key):
+    return solver.info(key)
+
+
+def hlbm_time_kernel(solver, kernel, reps=50):
+    return solver.time_kernel(kernel, reps)
+
+
+def hlbm_sync(solver):
+    return solver.sync()
+
+
+def hlbm_destroy(solver):
+    return solver.close()

@@ -1,0 +1,658 @@
+// C ABI of the HLBM library: context, device upload, the per-coarse-step
+// launch schedule (level recursion, sub-cycling, CUDA graphs) and readback.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hlbm_device.h"
+#include "hlbm_internal.h"
+
+using namespace hlbm;
+
+struct hlbm_ctx {
+    Plan plan;
+    DevCtx dev;
+    cudaStream_t stream = nullptr;    // caller's stream
+    cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+    void *(*alloc_fn)(size_t, void *) = nullptr;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    std::vector<void *> blocks;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool use_graphs = false;
+    long steps = 0;
+    long forces_read = 0;
+    long launches = 0;            // kernels enqueued by the scheduler (counter)
+    long launches_per_step = 0;   // kernels of one coarse step
+    bool timing_dirty = false;    // hlbm_time_kernel ran kernels outside the schedule
+    int check_every = 0;
+    double *d_out = nullptr;  // fields / populations scratch, 12 doubles per node of the largest grid
+    size_t d_out_n = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+struct CudaError {
+    std::string msg;
+};
+
+void ck(cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess) throw CudaError{std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+void *dalloc(hlbm_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (c->alloc_fn) {
+        p = c->alloc_fn(bytes, c->alloc_ctx);
+        if (!p) throw CudaError{"device allocation failed (callback)"};
+    } else {
+        ck(cudaMalloc(&p, bytes), "cudaMalloc");
+    }
+    c->blocks.push_back(p);
+    return p;
+}
+
+template <typename V> V *upload(hlbm_ctx *c, const std::vector<V> &h)
+{
+    V *d = (V *)dalloc(c, h.size() * sizeof(V));
+    if (!h.empty()) ck(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice, c->stream), "upload");
+    return d;
+}
+
+template <typename T> std::vector<T> convert(const std::vector<double> &v) { return std::vector<T>(v.begin(), v.end()); }
+
+// Runtime parities for the start of coarse step k: level 0 alternates, finer
+// levels take an even number of steps per coarse step, and the mesh buffer
+// flips once per finite-volume sub-step.
+void set_phase(hlbm_ctx *c, long k)
+{
+    DevCtx &D = c->dev;
+    D.lv[0].parity = int(k & 1);
+    for (int l = 1; l < D.L; l++) D.lv[l].parity = 0;
+    long per = long(D.n_sub) << (D.L - 1);
+    D.m.gcur = int((k * per) & 1);
+}
+
+template <typename T> void advance(hlbm_ctx *c, int lvl, double theta, cudaStream_t s);
+
+// One step of level lvl on its own clock; theta: parent-time fraction at the
+// end of the step (refills the boundary ring by prolongation).
+template <typename T> void level_step(hlbm_ctx *c, int lvl, double theta, cudaStream_t s)
+{
+    DevCtx &D = c->dev;
+    bool hybrid = (lvl == D.L - 1) && D.m.n > 0;
+    if (hybrid) {
+        launch_ring_interp<T>(D, false, s);  // Eq. 9 data at t
+        launch_hole_interp<T>(D, s);         // Eq. 4: post-collision of the hole boundary
+        c->launches += 1 + (D.m.n_is > 0);
+    }
+    launch_collide<T>(D, lvl, s);  // Eq. 1
+    D.lv[lvl].parity ^= 1;
+    if (lvl == 0) launch_outer_bc<T>(D, s);
+    else launch_prolong<T>(D, lvl, theta, s);
+    c->launches += 2;
+    if (hybrid) {
+        launch_ring_interp<T>(D, true, s);  // Eq. 9 data at t + 1, ring state of sub-step 0
+        for (int m = 0; m < D.n_sub; m++) {  // Eq. 3, Eq. 5-7, wall rule
+            launch_fv<T>(D, m, s);
+            D.m.gcur ^= 1;
+        }
+        c->launches += 1 + D.n_sub;
+    }
+}
+
+template <typename T> void advance(hlbm_ctx *c, int lvl, double theta, cudaStream_t s)
+{
+    DevCtx &D = c->dev;
+    bool child = lvl < D.L - 1;
+    if (child) launch_snapshot<T>(D, lvl, false, s);
+    level_step<T>(c, lvl, theta, s);
+    if (child) {
+        launch_snapshot<T>(D, lvl, true, s);
+        advance<T>(c, lvl + 1, 0.5, s);
+        advance<T>(c, lvl + 1, 1.0, s);
+        launch_restrict<T>(D, lvl, s);
+        c->launches += 3;
+    }
+}
+
+template <typename T> void coarse_step(hlbm_ctx *c, cudaStream_t s)
+{
+    long before = c->launches;
+    advance<T>(c, 0, 0.0, s);
+    if (c->dev.m.n > 0) {
+        launch_forces<T>(c->dev, s);
+        c->launches++;
+    }
+    c->launches_per_step = c->launches - before;
+}
+
+void enqueue_coarse_step(hlbm_ctx *c, cudaStream_t s)
+{
+    if (c->plan.precision == HLBM_FP32) coarse_step<float>(c, s);
+    else coarse_step<double>(c, s);
+}
+
+template <typename T> void init_state(hlbm_ctx *c)
+{
+    DevCtx &D = c->dev;
+    const Plan &P = c->plan;
+    cudaStream_t s = c->stream;
+    for (int l = 0; l < D.L; l++) {
+        D.lv[l].parity = 0;
+        launch_init_level<T>(D, l, P.seed, P.perturb, s);
+    }
+    // make the initial state consistent across the interfaces
+    launch_outer_bc<T>(D, s);
+    for (int l = 1; l < D.L; l++) {
+        launch_snapshot<T>(D, l - 1, false, s);
+        launch_snapshot<T>(D, l - 1, true, s);
+        launch_prolong<T>(D, l, 0.0, s);
+    }
+    for (int l = D.L - 2; l >= 0; l--) launch_restrict<T>(D, l, s);
+    if (D.m.n > 0) {
+        // mesh: f^eq(1 + perturb xi, u) with u = 0 on wall nodes, device order
+        std::vector<T> g(size_t(9) * D.m.Np, T(0));
+        for (int p = 0; p < P.n; p++) {
+            double rho = 1.0 + P.perturb * init_deviate(P.seed, kMeshGrid, uint64_t(p));
+            double ux = P.kind[p] == HLBM_NODE_WALL ? 0.0 : P.u0;
+            int q = P.inv[p];
+            for (int i = 0; i < 9; i++) {
+                static const int CXh[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+                static const double Wh[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+                double cu = CXh[i] * ux;
+                g[size_t(i) * D.m.Np + q] = T(Wh[i] * ((rho - 1.0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * ux * ux)));
+            }
+        }
+        ck(cudaMemcpyAsync(D.m.g[0], g.data(), g.size() * sizeof(T), cudaMemcpyHostToDevice, s), "upload mesh state");
+        ck(cudaStreamSynchronize(s), "sync");  // g (host) goes out of scope
+        D.m.gcur = 0;
+        launch_ring_interp<T>(D, false, s);  // Q0
+        launch_ring_interp<T>(D, true, s);   // Q1 and the ring state at theta = 0
+    }
+    ck(cudaGetLastError(), "init kernels");
+}
+
+template <typename T> void upload_mesh(hlbm_ctx *c)
+{
+    Plan &P = c->plan;
+    DevMesh &M = c->dev.m;
+    const LevelPlan &F = P.lv[P.L - 1];
+    const DevLevel &FL = c->dev.lv[P.L - 1];
+    M.n = P.n;
+    M.Np = (P.n + 31) / 32 * 32;
+    M.n_wall = P.n_wall;
+    M.ring_start = P.ring_start;
+    M.n_ring = P.n_ring;
+    for (int b = 0; b < 2; b++) M.g[b] = dalloc(c, size_t(9) * M.Np * sizeof(T));
+    // sliced-ELL operator rows in device order
+    using E = typename std::conditional<std::is_same<T, float>::value, float4, double4_32a>::type;
+    M.n_slices = M.Np / 32;
+    std::vector<int> sptr(M.n_slices), slen(M.n_slices);
+    std::vector<E> ent;
+    for (int sl = 0; sl < M.n_slices; sl++) {
+        int len = 0;
+        for (int l = 0; l < 32; l++) {
+            int r = sl * 32 + l;
+            if (r < P.n) len = std::max(len, P.rowptr[P.perm[r] + 1] - P.rowptr[P.perm[r]]);
+        }
+        sptr[sl] = int(ent.size());
+        slen[sl] = len;
+        size_t base = ent.size();
+        ent.resize(base + size_t(32) * len);
+        for (int l = 0; l < 32; l++) {
+            int r = sl * 32 + l;
+            for (int e = 0; e < len; e++) {
+                E v{};
+                int old = r < P.n ? P.perm[r] : -1;
+                int k = old >= 0 ? P.rowptr[old] + e : -1;
+                if (old >= 0 && k < P.rowptr[old + 1]) {
+                    v.x = T(P.sx[k]); v.y = T(P.sy[k]); v.z = T(P.cc[k]);
+                    int col = P.inv[P.col[k]];
+                    if (std::is_same<T, float>::value) { float fcol; std::memcpy(&fcol, &col, 4); std::memcpy(&v.w, &fcol, 4); }
+                    else v.w = T(col);
+                } else {
+                    int col = r < P.n ? r : 0;  // padding: zero coefficients on a valid column
+                    v.x = v.y = v.z = T(0);
+                    if (std::is_same<T, float>::value) { float fcol; std::memcpy(&fcol, &col, 4); std::memcpy(&v.w, &fcol, 4); }
+                    else v.w = T(col);
+                }
+                ent[base + size_t(32) * e + l] = v;
+            }
+        }
+    }
+    M.ent = upload(c, ent);
+    M.slice_ptr = upload(c, sptr);
+    M.slice_len = upload(c, slen);
+    M.Q0 = dalloc(c, size_t(12) * std::max(1, P.n_ring) * sizeof(T));
+    M.Q1 = dalloc(c, size_t(12) * std::max(1, P.n_ring) * sizeof(T));
+    // Eq. 8 stencils
+    M.n_is = int(P.is_node.size());
+    std::vector<int> isn(M.n_is), isd(6 * size_t(M.n_is));
+    for (int s = 0; s < M.n_is; s++) {
+        int x = P.is_node[s] % F.nx, y = P.is_node[s] / F.nx;
+        isn[s] = (y + 1) * FL.pitch + x + 1;
+        for (int k = 0; k < 6; k++) isd[6 * s + k] = P.inv[P.is_don[6 * s + k]];
+    }
+    M.is_n = upload(c, isn);
+    M.is_don = upload(c, isd);
+    M.is_w = upload(c, convert<T>(P.is_w));
+    // Eq. 9 stencils
+    std::vector<int> rd(9 * size_t(P.n_ring));
+    for (size_t k = 0; k < rd.size(); k++) {
+        int x = P.ring_don[k] % F.nx, y = P.ring_don[k] / F.nx;
+        rd[k] = (y + 1) * FL.pitch + x + 1;
+    }
+    M.ring_don = upload(c, rd);
+    M.ring_w = upload(c, convert<T>(P.ring_w));
+    // wall edges: device-order nodes and the normal times length into the fluid
+    M.n_edges = int(P.wea.size());
+    std::vector<int> ea(M.n_edges), eb(M.n_edges);
+    std::vector<double> wn(2 * size_t(M.n_edges));
+    for (int e = 0; e < M.n_edges; e++) {
+        ea[e] = P.inv[P.wea[e]];
+        eb[e] = P.inv[P.web[e]];
+        double dx = P.xy[2 * P.web[e]] - P.xy[2 * P.wea[e]], dy = P.xy[2 * P.web[e] + 1] - P.xy[2 * P.wea[e] + 1];
+        wn[2 * e] = -dy;  // left normal: from the body into the fluid
+        wn[2 * e + 1] = dx;
+    }
+    M.wea = upload(c, ea);
+    M.web = upload(c, eb);
+    M.wn = upload(c, wn);
+    M.inv = upload(c, P.inv);
+}
+
+template <typename T> void build_device(hlbm_ctx *c)
+{
+    Plan &P = c->plan;
+    DevCtx &D = c->dev;
+    D.L = P.L;
+    D.u0 = P.u0;
+    D.tau_u = P.tau_u;
+    D.n_sub = P.n_sub;
+    D.dt_u = P.n_sub > 0 ? 1.0 / P.n_sub : 0.0;
+    D.qdyn = P.qdyn;
+    size_t maxnodes = size_t(std::max(P.n, 1));
+    for (int l = 0; l < P.L; l++) {
+        const LevelPlan &lp = P.lv[l];
+        DevLevel &dl = D.lv[l];
+        dl.nx = lp.nx;
+        dl.ny = lp.ny;
+        dl.pitch = (lp.nx + 2 + 31) / 32 * 32;
+        dl.stride = size_t(lp.ny + 2) * dl.pitch;
+        dl.f = dalloc(c, 9 * dl.stride * sizeof(T));
+        dl.tau = lp.tau;
+        if (l == P.L - 1 && P.n > 0) {
+            dl.hx0 = upload(c, lp.hx0);
+            dl.hx1 = upload(c, lp.hx1);
+        }
+        dl.has_child = lp.has_child;
+        if (lp.has_child) {
+            dl.cox = lp.cox; dl.coy = lp.coy; dl.cmx = lp.cmx; dl.cmy = lp.cmy;
+            dl.band_n = 2 * (lp.cmx + 2) + 2 * (lp.cmy + 2);
+            dl.snapA = dalloc(c, size_t(12) * dl.band_n * sizeof(T));
+            dl.snapB = dalloc(c, size_t(12) * dl.band_n * sizeof(T));
+        }
+        maxnodes = std::max(maxnodes, size_t(lp.nx) * lp.ny);
+    }
+    if (P.n > 0) upload_mesh<T>(c);
+    D.force_cap = std::max(1, D.force_cap);
+    D.force_buf = (double *)dalloc(c, size_t(2) * D.force_cap * sizeof(double));
+    D.force_counter = (int *)dalloc(c, 2 * sizeof(int));
+    D.flag = D.force_counter + 1;
+    ck(cudaMemsetAsync(D.force_counter, 0, 2 * sizeof(int), c->stream), "memset");
+    c->d_out_n = maxnodes;
+    c->d_out = (double *)dalloc(c, maxnodes * 12 * sizeof(double));
+    init_state<T>(c);
+}
+
+void capture_graphs(hlbm_ctx *c)
+{
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    for (int k = 0; k < 2; k++) {
+        set_phase(c, k);
+        cudaGraph_t g = nullptr;
+        ck(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        try {
+            enqueue_coarse_step(c, c->cap_stream);
+        } catch (...) {
+            cudaStreamEndCapture(c->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        ck(cudaStreamEndCapture(c->cap_stream, &g), "end capture");
+        ck(cudaGraphInstantiate(&c->graph[k], g, 0), "graph instantiate");
+        cudaGraphDestroy(g);
+    }
+    set_phase(c, c->steps);
+}
+
+void release(hlbm_ctx *c)
+{
+    for (int k = 0; k < 2; k++)
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (void *p : c->blocks) {
+        if (c->free_fn) c->free_fn(p, c->alloc_ctx);
+        else cudaFree(p);
+    }
+    c->blocks.clear();
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+}
+
+int fail(hlbm_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re, double Ma, double aoa_deg,
+                const hlbm_options *opt, hlbm_ctx **out)
+{
+    if (!out) return fail(nullptr, HLBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    hlbm_ctx *c = new (std::nothrow) hlbm_ctx();
+    if (!c) return fail(nullptr, HLBM_ENOMEM, "host allocation failed");
+    std::string err;
+    int rc = build_plan(lv, n_levels, m, Re, Ma, aoa_deg, opt, c->plan, err);
+    if (rc != HLBM_OK) { delete c; return fail(nullptr, rc, err); }
+    hlbm_options o{};
+    if (opt) o = *opt;
+    c->stream = (cudaStream_t)o.stream;
+    c->alloc_fn = o.alloc;
+    c->free_fn = o.alloc ? o.free : nullptr;
+    c->alloc_ctx = o.alloc_ctx;
+    c->use_graphs = o.use_graphs != 0;
+    c->check_every = std::max(0, o.check_every);
+    c->dev.force_cap = o.force_cap > 0 ? o.force_cap : 4096;
+    try {
+        ck(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "stream create");
+        if (c->plan.precision == HLBM_FP32) build_device<float>(c);
+        else build_device<double>(c);
+        if (c->use_graphs) capture_graphs(c);
+        ck(cudaStreamSynchronize(c->stream), "sync after create");
+    } catch (const CudaError &e) {
+        std::string msg = e.msg;
+        release(c);
+        delete c;
+        return fail(nullptr, msg.find("alloc") != std::string::npos ? HLBM_ENOMEM : HLBM_ECUDA, msg);
+    } catch (const std::bad_alloc &) {
+        release(c);
+        delete c;
+        return fail(nullptr, HLBM_ENOMEM, "host allocation failed");
+    }
+    set_phase(c, 0);
+    *out = c;
+    return HLBM_OK;
+}
+
+int hlbm_step(hlbm_ctx *c, int n_coarse)
+{
+    if (!c) return HLBM_EINVAL;
+    if (c->timing_dirty) return fail(c, HLBM_ESTATE, "the state was consumed by hlbm_time_kernel");
+    if (n_coarse < 0) return fail(c, HLBM_EINVAL, "n_coarse must be >= 0");
+    try {
+        for (int k = 0; k < n_coarse; k++) {
+            if (c->use_graphs) {
+                ck(cudaGraphLaunch(c->graph[c->steps & 1], c->stream), "graph launch");
+            } else {
+                set_phase(c, c->steps);
+                enqueue_coarse_step(c, c->stream);
+                ck(cudaGetLastError(), "kernel launch");
+            }
+            c->steps++;
+            set_phase(c, c->steps);
+            if (c->check_every > 0 && (c->steps % c->check_every) == 0) {
+                int flag = 0;
+                ck(cudaMemcpyAsync(&flag, c->dev.flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
+                ck(cudaStreamSynchronize(c->stream), "sync");
+                if (flag) return fail(c, HLBM_EUNSTABLE, "NaN in the force reduction: the simulation is unstable");
+            }
+        }
+    } catch (const CudaError &e) {
+        return fail(c, HLBM_ECUDA, e.msg);
+    }
+    return HLBM_OK;
+}
+
+int hlbm_forces(hlbm_ctx *c, double *cd, double *cl, int cap, int *n_written)
+{
+    if (!c || !n_written || (cap > 0 && (!cd || !cl))) return c ? fail(c, HLBM_EINVAL, "bad arguments") : HLBM_EINVAL;
+    *n_written = 0;
+    if (c->dev.m.n == 0) return HLBM_OK;
+    try {
+        int counter = 0;
+        ck(cudaMemcpyAsync(&counter, c->dev.force_counter, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "counter");
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        long first = std::max<long>(c->forces_read, long(counter) - c->dev.force_cap);
+        long n = std::min<long>(long(counter) - first, cap);
+        if (n <= 0) return HLBM_OK;
+        std::vector<double> buf(size_t(2) * c->dev.force_cap);
+        ck(cudaMemcpy(buf.data(), c->dev.force_buf, buf.size() * sizeof(double), cudaMemcpyDeviceToHost), "forces");
+        for (long k = 0; k < n; k++) {
+            long slot = (first + k) % c->dev.force_cap;
+            cd[k] = buf[2 * slot];
+            cl[k] = buf[2 * slot + 1];
+        }
+        c->forces_read = first + n;
+        *n_written = int(n);
+    } catch (const CudaError &e) {
+        return fail(c, HLBM_ECUDA, e.msg);
+    }
+    return HLBM_OK;
+}
+
+static int readback(hlbm_ctx *c, int grid, double *rho, double *ux, double *uy, double *pop, size_t cap)
+{
+    if (!c) return HLBM_EINVAL;
+    size_t n;
+    if (grid == -1) n = size_t(c->plan.n);
+    else if (grid >= 0 && grid < c->plan.L) n = size_t(c->plan.lv[grid].nx) * c->plan.lv[grid].ny;
+    else return fail(c, HLBM_EINVAL, "grid out of range");
+    size_t need = pop ? 9 * n : n;
+    if (cap < need) return fail(c, HLBM_EINVAL, "output capacity too small");
+    if (n == 0) return HLBM_OK;
+    try {
+        double *d = c->d_out;
+        if (pop) {
+            if (c->plan.precision == HLBM_FP32) launch_fields<float>(c->dev, grid, nullptr, nullptr, nullptr, d, c->stream);
+            else launch_fields<double>(c->dev, grid, nullptr, nullptr, nullptr, d, c->stream);
+            ck(cudaGetLastError(), "fields kernel");
+            ck(cudaMemcpyAsync(pop, d, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
+        } else {
+            if (c->plan.precision == HLBM_FP32) launch_fields<float>(c->dev, grid, d, d + n, d + 2 * n, nullptr, c->stream);
+            else launch_fields<double>(c->dev, grid, d, d + n, d + 2 * n, nullptr, c->stream);
+            ck(cudaGetLastError(), "fields kernel");
+            if (rho) ck(cudaMemcpyAsync(rho, d, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
+            if (ux) ck(cudaMemcpyAsync(ux, d + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
+            if (uy) ck(cudaMemcpyAsync(uy, d + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
+        }
+        ck(cudaStreamSynchronize(c->stream), "sync");
+    } catch (const CudaError &e) {
+        return fail(c, HLBM_ECUDA, e.msg);
+    }
+    return HLBM_OK;
+}
+
+int hlbm_fields(hlbm_ctx *c, int grid, double *rho, double *ux, double *uy, size_t cap)
+{
+    return readback(c, grid, rho, ux, uy, nullptr, cap);
+}
+
+int hlbm_populations(hlbm_ctx *c, int grid, double *out, size_t cap)
+{
+    if (!out) return c ? fail(c, HLBM_EINVAL, "out is NULL") : HLBM_EINVAL;
+    return readback(c, grid, nullptr, nullptr, nullptr, out, cap);
+}
+
+int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
+{
+    if (!c || !key || !value) return HLBM_EINVAL;
+    const Plan &P = c->plan;
+    std::string k(key);
+    if (k == "n_sub") *value = P.n_sub;
+    else if (k == "n_levels") *value = P.L;
+    else if (k == "tau_u") *value = P.tau_u;
+    else if (k.size() == 4 && k.compare(0, 3, "tau") == 0 && k[3] >= '0' && k[3] < '0' + P.L) *value = P.lv[k[3] - '0'].tau;
+    else if (k == "steps") *value = double(c->steps);
+    else if (k == "n_interp") *value = double(P.is_node.size());
+    else if (k == "n_ring") *value = P.n_ring;
+    else if (k == "n_wall_edges") *value = double(P.wea.size());
+    else if (k == "lattice_updates") {
+        double u = 0;
+        for (int l = 0; l < P.L; l++) {
+            double nn = double(P.lv[l].nx) * P.lv[l].ny;
+            if (l == P.L - 1 && P.n > 0)
+                for (int y = 0; y < P.lv[l].ny; y++) nn -= P.lv[l].hx1[y] - P.lv[l].hx0[y];
+            u += nn * double(1L << l);
+        }
+        *value = u;
+    } else if (k == "fv_updates") *value = double(P.n) * P.n_sub * double(1L << (P.L - 1));
+    else if (k == "launches_per_step") *value = double(c->launches_per_step);
+    else if (k == "fv_bytes") {
+        // algorithmic bytes of one finite-volume sub-step: 9 reads + 9 writes of
+        // every node's populations, one (s_x, s_y, C, column) entry per operator
+        // coefficient
+        double vb = P.precision == HLBM_FP32 ? 4.0 : 8.0;
+        *value = double(P.n) * 18.0 * vb + double(P.col.size()) * 4.0 * vb;
+    } else if (k.size() == 14 && k.compare(0, 13, "collide_bytes") == 0) {
+        int l = k[13] - '0';
+        if (l < 0 || l >= P.L) return HLBM_EINVAL;
+        double nn = double(P.lv[l].nx) * P.lv[l].ny;
+        if (l == P.L - 1 && P.n > 0)
+            for (int y = 0; y < P.lv[l].ny; y++) nn -= P.lv[l].hx1[y] - P.lv[l].hx0[y];
+        *value = nn * 18.0 * (P.precision == HLBM_FP32 ? 4.0 : 8.0);
+    }
+    else return HLBM_EINVAL;
+    return HLBM_OK;
+}
+
+int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re, double Ma, double aoa_deg,
+                 const hlbm_options *opt, const char *table, double *out, size_t cap, size_t *n)
+{
+    if (!table || !n) return fail(nullptr, HLBM_EINVAL, "table and n are required");
+    Plan P;
+    std::string err;
+    int rc;
+    try {
+        rc = build_plan(lv, n_levels, m, Re, Ma, aoa_deg, opt, P, err);
+    } catch (const std::bad_alloc &) {
+        return fail(nullptr, HLBM_ENOMEM, "host allocation failed");
+    }
+    if (rc != HLBM_OK) return fail(nullptr, rc, err);
+    std::vector<double> v;
+    std::string t(table);
+    auto put_i = [&](const std::vector<int> &a) { v.assign(a.begin(), a.end()); };
+    if (t == "rowptr") put_i(P.rowptr);
+    else if (t == "col") put_i(P.col);
+    else if (t == "sx") v = P.sx;
+    else if (t == "sy") v = P.sy;
+    else if (t == "cc") v = P.cc;
+    else if (t == "area") v = P.area;
+    else if (t == "xy") v = P.xy;
+    else if (t == "is_node") put_i(P.is_node);
+    else if (t == "is_don") put_i(P.is_don);
+    else if (t == "is_w") v = P.is_w;
+    else if (t == "ring") put_i(P.ring);
+    else if (t == "ring_don") put_i(P.ring_don);
+    else if (t == "ring_w") v = P.ring_w;
+    else if (t == "wall_edges") {
+        for (size_t e = 0; e < P.wea.size(); e++) { v.push_back(P.wea[e]); v.push_back(P.web[e]); }
+    } else if (t == "n_sub") v.assign(1, double(P.n_sub));
+    else return fail(nullptr, HLBM_EINVAL, "unknown table");
+    *n = v.size();
+    if (out) {
+        if (cap < v.size()) return fail(nullptr, HLBM_EINVAL, "output capacity too small");
+        std::copy(v.begin(), v.end(), out);
+    }
+    return HLBM_OK;
+}
+
+int hlbm_time_kernel(hlbm_ctx *c, const char *kernel, int reps, double *avg_ms)
+{
+    if (!c || !kernel || !avg_ms || reps < 1) return c ? fail(c, HLBM_EINVAL, "bad arguments") : HLBM_EINVAL;
+    std::string k(kernel);
+    int lvl = -1;
+    if (k == "fv") {
+        if (c->dev.m.n == 0) return fail(c, HLBM_EINVAL, "no mesh");
+    } else if (k.size() == 8 && k.compare(0, 7, "collide") == 0 && k[7] >= '0' && k[7] < '0' + c->plan.L) {
+        lvl = k[7] - '0';
+    } else {
+        return fail(c, HLBM_EINVAL, "unknown kernel");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    try {
+        ck(cudaEventCreate(&e0), "event");
+        ck(cudaEventCreate(&e1), "event");
+        bool f32 = c->plan.precision == HLBM_FP32;
+        auto one = [&](int r) {
+            if (lvl < 0) {
+                int m = r % std::max(1, c->dev.n_sub);
+                if (f32) launch_fv<float>(c->dev, m, c->stream);
+                else launch_fv<double>(c->dev, m, c->stream);
+                c->dev.m.gcur ^= 1;
+            } else {
+                if (f32) launch_collide<float>(c->dev, lvl, c->stream);
+                else launch_collide<double>(c->dev, lvl, c->stream);
+                c->dev.lv[lvl].parity ^= 1;
+            }
+        };
+        one(0);  // warm-up
+        ck(cudaEventRecord(e0, c->stream), "record");
+        for (int r = 0; r < reps; r++) one(r + 1);
+        ck(cudaEventRecord(e1, c->stream), "record");
+        ck(cudaEventSynchronize(e1), "sync");
+        float ms = 0;
+        ck(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+        *avg_ms = double(ms) / reps;
+        ck(cudaGetLastError(), "kernel launch");
+    } catch (const CudaError &e) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return fail(c, HLBM_ECUDA, e.msg);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->timing_dirty = true;
+    return HLBM_OK;
+}
+
+int hlbm_sync(hlbm_ctx *c)
+{
+    if (!c) return HLBM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, HLBM_ECUDA, cudaGetErrorString(e));
+    return HLBM_OK;
+}
+
+int hlbm_destroy(hlbm_ctx *c)
+{
+    if (!c) return HLBM_OK;
+    release(c);
+    delete c;
+    return HLBM_OK;
+}
+
+const char *hlbm_last_error(const hlbm_ctx *c)
+{
+    if (!c) return g_create_err.c_str();
+    return c->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Device-side state of one HLBM context and the kernel launchers
+// (implemented in kernels.cu for float and double storage).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace hlbm {
+
+// One Cartesian level in the in-place (AA) layout: nine planes of
+// (ny + 2) x pitch values (one halo node on each side), plane stride `stride`;
+// node (x, y) sits at index (y + 1) * pitch + x + 1.  Values are deviations
+// f_i - w_i.  With parity 0 the state of node n is plane i at n; with parity 1
+// it is plane opp(i) at n - c_i.
+struct DevLevel {
+    int nx = 0, ny = 0, pitch = 0;
+    size_t stride = 0;
+    void *f = nullptr;
+    int parity = 0;
+    double tau = 0;
+    int *hx0 = nullptr, *hx1 = nullptr;  // finest level: hole interval per row
+    bool has_child = false;
+    int cox = 0, coy = 0, cmx = 0, cmy = 0, band_n = 0;
+    void *snapA = nullptr, *snapB = nullptr;  // [12][band_n] (rho, ux, uy, f^neq)
+};
+
+// The triangular mesh in device order (wall nodes, fluid nodes, ring nodes).
+struct DevMesh {
+    int n = 0, Np = 0, n_wall = 0, ring_start = 0, n_ring = 0;
+    void *g[2] = {nullptr, nullptr};  // [9][Np] deviations, double-buffered
+    int gcur = 0;
+    // Eq. 3 operators, sliced ELL with 32-row slices: entry e of row r sits at
+    // slice_ptr[r / 32] + 32 e + r % 32, as (s_x, s_y, C, column)
+    int n_slices = 0;
+    void *ent = nullptr;
+    int *slice_ptr = nullptr, *slice_len = nullptr;
+    void *Q0 = nullptr, *Q1 = nullptr;  // [12][n_ring] Eq. 9 data at t and t + 1
+    int n_is = 0;
+    int *is_n = nullptr;    // padded finest-level index of each structured interpolation node
+    int *is_don = nullptr;  // [n_is][6] device-order mesh nodes
+    void *is_w = nullptr;   // [n_is][6]
+    int *ring_don = nullptr;  // [n_ring][9] padded finest-level indices
+    void *ring_w = nullptr;   // [n_ring][9]
+    int n_edges = 0;
+    int *wea = nullptr, *web = nullptr;  // wall edges, device-order nodes
+    double *wn = nullptr;                // [n_edges][2] normal times length, into the fluid
+    int *inv = nullptr;                  // input node -> device node
+};
+
+struct DevCtx {
+    int L = 0;
+    DevLevel lv[8];
+    DevMesh m;
+    double u0 = 0, tau_u = 0, dt_u = 0, qdyn = 0;
+    int n_sub = 0;
+    double *force_buf = nullptr;  // [force_cap][2]
+    int *force_counter = nullptr;
+    int *flag = nullptr;
+    int force_cap = 0;
+};
+
+template <typename T> void launch_init_level(const DevCtx &, int c, unsigned long long seed, double perturb, cudaStream_t);
+template <typename T> void launch_collide(const DevCtx &, int c, cudaStream_t);
+template <typename T> void launch_outer_bc(const DevCtx &, cudaStream_t);
+template <typename T> void launch_snapshot(const DevCtx &, int c, bool into_b, cudaStream_t);
+template <typename T> void launch_prolong(const DevCtx &, int c_fine, double theta, cudaStream_t);
+template <typename T> void launch_restrict(const DevCtx &, int c_coarse, cudaStream_t);
+template <typename T> void launch_ring_interp(const DevCtx &, bool q1_and_star, cudaStream_t);
+template <typename T> void launch_hole_interp(const DevCtx &, cudaStream_t);
+template <typename T> void launch_fv(const DevCtx &, int m, cudaStream_t);
+template <typename T> void launch_forces(const DevCtx &, cudaStream_t);
+template <typename T> void launch_fields(const DevCtx &, int grid, double *rho, double *ux, double *uy, double *pop, cudaStream_t);
+
+}  // namespace hlbm

@@ -1,0 +1,69 @@
+// Internal declarations of the HLBM library (host set-up plan, device state,
+// kernel launchers).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hlbm.h"
+
+namespace hlbm {
+
+constexpr int kMaxLevels = 8;
+constexpr int kMeshGrid = 63;  // grid id of the mesh in the initial-state generator
+
+// Host-side description of one Cartesian level.
+struct LevelPlan {
+    int nx = 0, ny = 0, ox = 0, oy = 0;
+    double tau = 0.0;
+    // finest level with a mesh: per row y, nodes x in [hx0[y], hx1[y]) are not computed
+    std::vector<int> hx0, hx1;
+    // refinement towards the child level (if any)
+    bool has_child = false;
+    int cmx = 0, cmy = 0;  // child box size in this level's cells
+    int cox = 0, coy = 0;  // child origin in this level's nodes
+};
+
+// Everything hlbm_create derives on the host, in FP64.
+struct Plan {
+    int L = 0;
+    LevelPlan lv[kMaxLevels];
+    double u0 = 0, nu = 0, tau_u = 0, chord = 0, qdyn = 0;
+    int n_sub = 0;
+    int precision = HLBM_FP64;
+    uint64_t seed = 0;
+    double perturb = 0;
+
+    // mesh, input node order
+    int n = 0, ntri = 0;
+    std::vector<double> xy;       // rotated coordinates [n][2]
+    std::vector<int> tri;         // [ntri][3]
+    std::vector<uint8_t> kind;    // [n]
+    std::vector<int> rowptr, col; // Eq. 3 operators, CSR, columns ascending
+    std::vector<double> sx, sy, cc, area;
+    // device order: wall nodes, then fluid nodes, then ring nodes (stable)
+    std::vector<int> perm;  // perm[new] = old
+    std::vector<int> inv;   // inv[old] = new
+    int n_wall = 0, ring_start = 0, n_ring = 0;
+    // structured interpolation nodes (Eq. 4, Eq. 8)
+    std::vector<int> is_node;    // finest-level node index y*nx + x, row-major
+    std::vector<int> is_don;     // [n_is][6] mesh nodes (input order)
+    std::vector<double> is_w;    // [n_is][6]
+    // unstructured interpolation nodes (Eq. 5, Eq. 9), ring nodes in input order
+    std::vector<int> ring;       // mesh node (input order)
+    std::vector<int> ring_don;   // [n_ring][9] finest-level node index y*nx + x
+    std::vector<double> ring_w;  // [n_ring][9]
+    // wall edges (a -> b, fluid on the left), input order
+    std::vector<int> wea, web;
+};
+
+// Builds the plan; returns HLBM_OK or an error code with a message in err.
+int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re, double Ma,
+               double aoa_deg, const hlbm_options *opt, Plan &plan, std::string &err);
+
+// splitmix64-based initial density deviate in [-1, 1) (host side).
+double init_deviate(uint64_t seed, uint64_t grid, uint64_t node);
+
+}  // namespace hlbm

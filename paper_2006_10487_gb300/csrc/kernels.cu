@@ -1,0 +1,660 @@
+// CUDA kernels of the HLBM step for sm_103a.
+//
+// Storage is deviations d_i = f_i - w_i (float or double); arithmetic is in
+// the storage type.  Every kernel is a pure gather (each thread writes only
+// its own outputs), so results are deterministic; no atomics are used.
+//
+// Paper passages: Eq. 1-2 (lattice), Eq. 3 (finite volume), Eq. 4-9 (overlap
+// coupling), Section 4 (refinement boxes, wall, outer conditions),
+// Eq. 10-11 (forces).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hlbm_device.h"
+
+namespace hlbm {
+namespace {
+
+// ---------------------------------------------------------------- D2Q9 -----
+// order: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+__host__ __device__ __forceinline__ constexpr int cx(int i)
+{
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int cy(int i)
+{
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int opp(int i)
+{
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+template <typename T> __device__ __forceinline__ T wq(int i)
+{
+    return i == 0 ? T(4.0 / 9.0) : (i <= 4 ? T(1.0 / 9.0) : T(1.0 / 36.0));
+}
+
+// Eq. 2 in deviation form: f^eq_i - w_i = w_i [(rho - 1) + rho (3 cu + 9/2 cu^2 - 3/2 u.u)].
+template <typename T> __device__ __forceinline__ T deq(int i, T rho, T ux, T uy)
+{
+    T cu = T(cx(i)) * ux + T(cy(i)) * uy;
+    T uu = ux * ux + uy * uy;
+    return wq<T>(i) * ((rho - T(1)) + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+}
+
+template <typename T> __device__ __forceinline__ void moments(const T d[9], T &rho, T &ux, T &uy)
+{
+    T s = 0, mx = 0, my = 0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        s += d[i];
+        mx += T(cx(i)) * d[i];
+        my += T(cy(i)) * d[i];
+    }
+    rho = T(1) + s;
+    ux = mx / rho;
+    uy = my / rho;
+}
+
+// q = (rho, ux, uy, f^neq_0..8)
+template <typename T> __device__ __forceinline__ void to_q(const T d[9], T q[12])
+{
+    moments(d, q[0], q[1], q[2]);
+#pragma unroll
+    for (int i = 0; i < 9; i++) q[3 + i] = d[i] - deq<T>(i, q[0], q[1], q[2]);
+}
+
+// d = f^eq(rho, u) - w + scale * f^neq
+template <typename T> __device__ __forceinline__ void from_q(const T q[12], T scale, T d[9])
+{
+#pragma unroll
+    for (int i = 0; i < 9; i++) d[i] = deq<T>(i, q[0], q[1], q[2]) + scale * q[3 + i];
+}
+
+// AA-pattern addressing.  State of node n at parity p:
+//   p = 0: plane i at n;  p = 1: plane opp(i) at n - c_i.
+// A collision at parity p writes its post-collision value c_i-bound to
+//   p = 0: plane opp(i) at n;  p = 1: plane i at n + c_i.
+template <int P> __device__ __forceinline__ size_t st_idx(int i, size_t n, int pitch, size_t stride)
+{
+    if (P == 0) return size_t(i) * stride + n;
+    return size_t(opp(i)) * stride + n - cx(i) - ptrdiff_t(cy(i)) * pitch;
+}
+template <int P> __device__ __forceinline__ size_t wr_idx(int i, size_t n, int pitch, size_t stride)
+{
+    if (P == 0) return size_t(opp(i)) * stride + n;
+    return size_t(i) * stride + n + cx(i) + ptrdiff_t(cy(i)) * pitch;
+}
+
+__device__ __forceinline__ size_t node(int x, int y, int pitch) { return size_t(y + 1) * pitch + x + 1; }
+
+template <typename T, int P>
+__device__ __forceinline__ void load_state(const T *f, size_t n, int pitch, size_t stride, T d[9])
+{
+#pragma unroll
+    for (int i = 0; i < 9; i++) d[i] = f[st_idx<P>(i, n, pitch, stride)];
+}
+template <typename T, int P>
+__device__ __forceinline__ void store_state(T *f, size_t n, int pitch, size_t stride, const T d[9])
+{
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[st_idx<P>(i, n, pitch, stride)] = d[i];
+}
+
+// splitmix64 (Steele, Lea and Flood): uniform deviate in [-1, 1)
+__device__ __forceinline__ double deviate(uint64_t seed, uint64_t grid, uint64_t idx)
+{
+    uint64_t z = (seed ^ (grid << 40) ^ idx) + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    return double(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+// -------------------------------------------------------------- kernels ----
+// Initial lattice state: f = f^eq(1 + perturb xi, (u0, 0)); hole nodes and the
+// halo hold NaN so that any read of them shows up in the results.
+template <typename T>
+__global__ void k_init_level(T *f, int nx, int ny, int pitch, size_t stride, const int *hx0, const int *hx1,
+                             uint64_t seed, int grid, double perturb, double u0)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x - 1, y = int(blockIdx.y) - 1;
+    if (x > nx) return;
+    size_t n = size_t(y + 1) * pitch + x + 1;
+    bool inside = x >= 0 && y >= 0 && x < nx && y < ny;
+    bool hole = inside && hx0 && x >= hx0[y] && x < hx1[y];
+    if (!inside || hole) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) f[size_t(i) * stride + n] = T(NAN);
+        return;
+    }
+    double rho = 1.0 + perturb * deviate(seed, uint64_t(grid), uint64_t(y) * nx + x);
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[size_t(i) * stride + n] = T(deq<double>(i, rho, u0, 0.0));
+}
+
+// Eq. 1: BGK collision and (implicit, AA-pattern) streaming on one level.
+template <typename T, int P>
+__global__ void __launch_bounds__(128) k_collide(T *__restrict__ f, int nx, int ny, int pitch, size_t stride,
+                                                 T omega, const int *__restrict__ hx0, const int *__restrict__ hx1)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    if (hx0 && x >= hx0[y] && x < hx1[y]) return;
+    size_t n = node(x, y, pitch);
+    T d[9];
+    load_state<T, P>(f, n, pitch, stride, d);
+    T rho, ux, uy;
+    moments(d, rho, ux, uy);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        T post = d[i] - omega * (d[i] - deq<T>(i, rho, ux, uy));
+        f[wr_idx<P>(i, n, pitch, stride)] = post;
+    }
+}
+
+// Outer conditions on the level-0 perimeter (Section 4), written as the
+// state at parity P: every perimeter node copies the state of its nearest
+// interior node n (coordinates clamped to the interior) with
+//   inlet (x = 0):        f^eq(rho_n, (u0, 0)) + f^neq_n
+//   outlet (x = nx - 1):  f^eq(1, u_n) + f^neq_n
+//   top / bottom:         f_n
+template <typename T, int P>
+__global__ void k_outer_bc(T *f, int nx, int ny, int pitch, size_t stride, T u0)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int nper = 2 * nx + 2 * (ny - 2);
+    if (k >= nper) return;
+    int x, y;
+    if (k < nx) { x = k; y = 0; }
+    else if (k < 2 * nx) { x = k - nx; y = ny - 1; }
+    else if (k < 2 * nx + ny - 2) { x = 0; y = k - 2 * nx + 1; }
+    else { x = nx - 1; y = k - 2 * nx - (ny - 2) + 1; }
+    int xn = min(max(x, 1), nx - 2), yn = min(max(y, 1), ny - 2);
+    T d[9];
+    load_state<T, P>(f, node(xn, yn, pitch), pitch, stride, d);
+    if (x == 0 || x == nx - 1) {
+        T q[12];
+        to_q(d, q);
+        if (x == 0) { q[1] = u0; q[2] = T(0); }
+        else q[0] = T(1);
+        from_q(q, T(1), d);
+    }
+    store_state<T, P>(f, node(x, y, pitch), pitch, stride, d);
+}
+
+// Coarse node of band entry b: the lines y = coy and y = coy + cmy for
+// x in [cox - 1, cox + cmx], then x = cox and x = cox + cmx for
+// y in [coy - 1, coy + cmy].
+__device__ __forceinline__ void band_node(int b, int cox, int coy, int cmx, int cmy, int &X, int &Y)
+{
+    int w = cmx + 2, h = cmy + 2;
+    if (b < w) { X = cox - 1 + b; Y = coy; }
+    else if (b < 2 * w) { X = cox - 1 + b - w; Y = coy + cmy; }
+    else if (b < 2 * w + h) { X = cox; Y = coy - 1 + b - 2 * w; }
+    else { X = cox + cmx; Y = coy - 1 + b - 2 * w - h; }
+}
+
+// (rho, u, f^neq) of the parent level along its child's boundary band.
+template <typename T, int P>
+__global__ void k_snapshot(const T *f, int pitch, size_t stride, int cox, int coy, int cmx, int cmy, T *snap,
+                           int band_n)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= band_n) return;
+    int X, Y;
+    band_node(b, cox, coy, cmx, cmy, X, Y);
+    T d[9], q[12];
+    load_state<T, P>(f, node(X, Y, pitch), pitch, stride, d);
+    to_q(d, q);
+#pragma unroll
+    for (int m = 0; m < 12; m++) snap[size_t(m) * band_n + b] = q[m];
+}
+
+// Refinement coarse -> fine (Section 4): the fine boundary ring at parity P
+// takes f^eq(rho, u) + tau_f / (2 tau_c) f^neq from the parent band, linear
+// in time (theta) and, midway between coarse nodes, quadratic along the
+// ring through coarse nodes X-1, X, X+1 (weights -1/8, 3/4, 3/8).
+template <typename T, int P>
+__global__ void k_prolong(T *f, int nx, int ny, int pitch, size_t stride, const T *snapA, const T *snapB,
+                          int band_n, int cox, int coy, int cmx, int cmy, T theta, T scale)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int nper = 2 * nx + 2 * (ny - 2);
+    if (k >= nper) return;
+    int i, j;
+    if (k < nx) { i = k; j = 0; }
+    else if (k < 2 * nx) { i = k - nx; j = ny - 1; }
+    else if (k < 2 * nx + ny - 2) { i = 0; j = k - 2 * nx + 1; }
+    else { i = nx - 1; j = k - 2 * nx - (ny - 2) + 1; }
+    int w = cmx + 2, h = cmy + 2;
+    int base, pos, odd;
+    if (j == 0 || j == ny - 1) {  // bottom / top line, along x
+        base = (j == 0) ? 0 : w;
+        pos = (i >> 1) + 1;  // band position of coarse x = cox + floor(i/2)
+        odd = i & 1;
+    } else {  // left / right line, along y
+        base = 2 * w + ((i == 0) ? 0 : h);
+        pos = (j >> 1) + 1;
+        odd = j & 1;
+    }
+    T q[12];
+#pragma unroll
+    for (int m = 0; m < 12; m++) q[m] = T(0);
+    const int nd = odd ? 3 : 1;
+    for (int t = 0; t < nd; t++) {
+        int b = base + pos + (odd ? t - 1 : 0);
+        T wk = odd ? (t == 0 ? T(-0.125) : (t == 1 ? T(0.75) : T(0.375))) : T(1);
+#pragma unroll
+        for (int m = 0; m < 12; m++)
+            q[m] += wk * ((T(1) - theta) * snapA[size_t(m) * band_n + b] + theta * snapB[size_t(m) * band_n + b]);
+    }
+    T d[9];
+    from_q(q, scale, d);
+    store_state<T, P>(f, node(i, j, pitch), pitch, stride, d);
+}
+
+// Refinement fine -> coarse: coarse nodes at least one cell inside the child
+// box take the coincident fine state with f^neq scaled by 2 tau_c / tau_f.
+template <typename T, int PC, int PF>
+__global__ void k_restrict(T *fc, int pitch_c, size_t stride_c, const T *ff, int pitch_f, size_t stride_f, int cox,
+                           int coy, int cmx, int cmy, T scale)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (a >= cmx - 1) return;
+    int X = cox + 1 + a, Y = coy + 1 + b;
+    T d[9], q[12];
+    load_state<T, PF>(ff, node(2 * (X - cox), 2 * (Y - coy), pitch_f), pitch_f, stride_f, d);
+    to_q(d, q);
+    from_q(q, scale, d);
+    store_state<T, PC>(fc, node(X, Y, pitch_c), pitch_c, stride_c, d);
+}
+
+// Eq. 9: (rho, u, f^neq) at the unstructured interpolation nodes from their
+// 3x3 lattice donors.  With star != 0 (after the lattice step) the kernel also
+// sets the ring nodes of the read buffer to the Eq. 5-6 state at theta = 0:
+// f^eq + (1 - 1/(2 tau_s)) f^neq of the data at t (Q0).
+template <typename T, int P>
+__global__ void k_ring_interp(const T *f, int pitch, size_t stride, const int *don, const T *w, int n_ring,
+                              T *Q, const T *Q0, T *g, int Np, int ring_start, T scale5, int star)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_ring) return;
+    T acc[12];
+#pragma unroll
+    for (int m = 0; m < 12; m++) acc[m] = T(0);
+    for (int k = 0; k < 9; k++) {
+        T d[9], q[12];
+        load_state<T, P>(f, size_t(don[9 * r + k]), pitch, stride, d);
+        to_q(d, q);
+        T wk = w[9 * r + k];
+#pragma unroll
+        for (int m = 0; m < 12; m++) acc[m] += wk * q[m];
+    }
+#pragma unroll
+    for (int m = 0; m < 12; m++) Q[size_t(m) * n_ring + r] = acc[m];
+    if (star) {
+        T q[12], d[9];
+#pragma unroll
+        for (int m = 0; m < 12; m++) q[m] = Q0[size_t(m) * n_ring + r];
+        from_q(q, scale5, d);
+#pragma unroll
+        for (int i = 0; i < 9; i++) g[size_t(i) * Np + ring_start + r] = d[i];
+    }
+}
+
+// Eq. 4 with Eq. 8: post-collision state of the structured interpolation
+// nodes from six unstructured donors, written where the collision at parity
+// P would write it.
+template <typename T, int P>
+__global__ void k_hole_interp(T *f, int pitch, size_t stride, const int *is_n, const int *don, const T *w, int n_is,
+                              const T *g, int Np, T scale4)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_is) return;
+    T acc[12];
+#pragma unroll
+    for (int m = 0; m < 12; m++) acc[m] = T(0);
+    for (int k = 0; k < 6; k++) {
+        int p = don[6 * s + k];
+        T d[9], q[12];
+#pragma unroll
+        for (int i = 0; i < 9; i++) d[i] = g[size_t(i) * Np + p];
+        to_q(d, q);
+        T wk = w[6 * s + k];
+#pragma unroll
+        for (int m = 0; m < 12; m++) acc[m] += wk * q[m];
+    }
+    T d[9];
+    from_q(acc, scale4, d);
+    size_t n = size_t(is_n[s]);
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[wr_idx<P>(i, n, pitch, stride)] = d[i];
+}
+
+template <typename T> struct Ent;
+template <> struct Ent<float> { using type = float4; };
+template <> struct Ent<double> { using type = double4_32a; };
+
+__device__ __forceinline__ void unpack(const float4 &e, float &sx, float &sy, float &c, int &col)
+{
+    sx = e.x; sy = e.y; c = e.z; col = __float_as_int(e.w);
+}
+__device__ __forceinline__ void unpack(const double4_32a &e, double &sx, double &sy, double &c, int &col)
+{
+    sx = e.x; sy = e.y; c = e.z; col = int(e.w);
+}
+
+// Eq. 3, one explicit sub-step on every mesh node (node-major gather over the
+// sliced-ELL operator rows, no atomics):
+//   g'_i(P) = g_i(P) + dt sum_k (c_i . s_Pk) g_i(P_k) - dt/tau_u sum_k C_Pk g^neq_i(P_k)
+// then, on wall rows, the no-slip rule (rho and f^neq kept, u = 0); on ring
+// rows, unless this is the last sub-step, the Eq. 5-6 state of the next
+// sub-step (theta_next) replaces the result.
+template <typename T>
+__global__ void __launch_bounds__(128) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
+                                            const int *__restrict__ slice_ptr, const int *__restrict__ slice_len,
+                                            const typename Ent<T>::type *__restrict__ ent, T dt, T dt_tau, int n_wall,
+                                            int ring_start, int n_ring, const T *__restrict__ Q0,
+                                            const T *__restrict__ Q1, T theta_next, T scale5, int star)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int sl = r >> 5, lane = r & 31;
+    int base = slice_ptr[sl] + lane, len = slice_len[sl];
+    T acc[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) acc[i] = T(0);
+    for (int e = 0; e < len; e++) {
+        T sx, sy, c;
+        int k;
+        unpack(ent[base + 32 * e], sx, sy, c, k);
+        T d[9];
+#pragma unroll
+        for (int i = 0; i < 9; i++) d[i] = g[size_t(i) * Np + k];
+        T rho, ux, uy;
+        moments(d, rho, ux, uy);
+        T cs = dt_tau * c;
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            T s = dt * (T(cx(i)) * sx + T(cy(i)) * sy);
+            acc[i] += s * d[i] - cs * (d[i] - deq<T>(i, rho, ux, uy));
+        }
+    }
+    T d[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) d[i] = g[size_t(i) * Np + r] + acc[i];
+    if (r < n_wall) {
+        T rho, ux, uy;
+        moments(d, rho, ux, uy);
+#pragma unroll
+        for (int i = 0; i < 9; i++) d[i] = d[i] - deq<T>(i, rho, ux, uy) + deq<T>(i, rho, T(0), T(0));
+    } else if (star && r >= ring_start) {
+        int q_ = r - ring_start;
+        T q[12];
+#pragma unroll
+        for (int m = 0; m < 12; m++)
+            q[m] = (T(1) - theta_next) * Q0[size_t(m) * n_ring + q_] + theta_next * Q1[size_t(m) * n_ring + q_];
+        from_q(q, scale5, d);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; i++) gn[size_t(i) * Np + r] = d[i];
+}
+
+// Eq. 10-11: force on the body from nodal pressure and stress at the wall,
+// traction -(p - p0) n - Pi^neq . n with p = rho / 3, edge values the mean of
+// the two end nodes; one block, FP64 tree reduction (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(512) k_forces(const T *g, int Np, const int *wea, const int *web, const double *wn,
+                                                int n_edges, double qdyn, double *buf, int *counter, int cap,
+                                                int *flag)
+{
+    double fx = 0.0, fy = 0.0;
+    for (int e = threadIdx.x; e < n_edges; e += blockDim.x) {
+        double p = 0, pxx = 0, pxy = 0, pyy = 0;
+        for (int s = 0; s < 2; s++) {
+            int k = s ? web[e] : wea[e];
+            T d[9], q[12];
+#pragma unroll
+            for (int i = 0; i < 9; i++) d[i] = g[size_t(i) * Np + k];
+            to_q(d, q);
+            p += 0.5 * double(q[0]) / 3.0;
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                double nq = double(q[3 + i]);
+                pxx += 0.5 * cx(i) * cx(i) * nq;
+                pxy += 0.5 * cx(i) * cy(i) * nq;
+                pyy += 0.5 * cy(i) * cy(i) * nq;
+            }
+        }
+        double nx = wn[2 * e], ny = wn[2 * e + 1];
+        double pm = p - 1.0 / 3.0;
+        fx += -pm * nx - (pxx * nx + pxy * ny);
+        fy += -pm * ny - (pxy * nx + pyy * ny);
+    }
+    __shared__ double sx[32], sy[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_down_sync(0xffffffffu, fx, o);
+        fy += __shfl_down_sync(0xffffffffu, fy, o);
+    }
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sx[warp] = fx; sy[warp] = fy; }
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        fx = lane < nw ? sx[lane] : 0.0;
+        fy = lane < nw ? sy[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fx += __shfl_down_sync(0xffffffffu, fx, o);
+            fy += __shfl_down_sync(0xffffffffu, fy, o);
+        }
+        if (lane == 0) {
+            int c = *counter;
+            buf[2 * (c % cap)] = fx / qdyn;
+            buf[2 * (c % cap) + 1] = fy / qdyn;
+            *counter = c + 1;
+            if (!(fx == fx) || !(fy == fy)) *flag = 1;
+        }
+    }
+}
+
+// Density, velocity (and optionally populations) of a level in FP64, x fastest;
+// NaN inside the hole.
+template <typename T, int P>
+__global__ void k_fields_level(const T *f, int nx, int ny, int pitch, size_t stride, const int *hx0, const int *hx1,
+                               double *rho, double *ux, double *uy, double *pop)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    size_t o = size_t(y) * nx + x;
+    if (hx0 && x >= hx0[y] && x < hx1[y]) {
+        if (rho) { rho[o] = NAN; ux[o] = NAN; uy[o] = NAN; }
+        if (pop)
+            for (int i = 0; i < 9; i++) pop[9 * o + i] = NAN;
+        return;
+    }
+    T d[9];
+    load_state<T, P>(f, node(x, y, pitch), pitch, stride, d);
+    if (rho) {
+        double dd[9];
+        for (int i = 0; i < 9; i++) dd[i] = double(d[i]);
+        double r, u, v;
+        moments(dd, r, u, v);
+        rho[o] = r; ux[o] = u; uy[o] = v;
+    }
+    if (pop)
+        for (int i = 0; i < 9; i++) pop[9 * o + i] = double(d[i]) + wq<double>(i);
+}
+
+template <typename T>
+__global__ void k_fields_mesh(const T *g, int Np, const int *inv, int n, double *rho, double *ux, double *uy,
+                              double *pop)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int k = inv[p];
+    double dd[9];
+    for (int i = 0; i < 9; i++) dd[i] = double(g[size_t(i) * Np + k]);
+    if (rho) {
+        double r, u, v;
+        moments(dd, r, u, v);
+        rho[p] = r; ux[p] = u; uy[p] = v;
+    }
+    if (pop)
+        for (int i = 0; i < 9; i++) pop[9 * size_t(p) + i] = dd[i] + wq<double>(i);
+}
+
+inline unsigned cdiv(long a, long b) { return unsigned((a + b - 1) / b); }
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers ----
+template <typename T> void launch_init_level(const DevCtx &C, int c, unsigned long long seed, double perturb, cudaStream_t s)
+{
+    const DevLevel &l = C.lv[c];
+    dim3 grid(cdiv(l.nx + 2, 128), l.ny + 2);
+    k_init_level<T><<<grid, 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, seed, c, perturb, C.u0);
+}
+
+template <typename T> void launch_collide(const DevCtx &C, int c, cudaStream_t s)
+{
+    const DevLevel &l = C.lv[c];
+    dim3 grid(cdiv(l.nx, 128), l.ny);
+    T omega = T(1.0 / l.tau);
+    if (l.parity == 0) k_collide<T, 0><<<grid, 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0, l.hx1);
+    else k_collide<T, 1><<<grid, 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0, l.hx1);
+}
+
+template <typename T> void launch_outer_bc(const DevCtx &C, cudaStream_t s)
+{
+    const DevLevel &l = C.lv[0];
+    int nper = 2 * l.nx + 2 * (l.ny - 2);
+    if (l.parity == 0) k_outer_bc<T, 0><<<cdiv(nper, 128), 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, T(C.u0));
+    else k_outer_bc<T, 1><<<cdiv(nper, 128), 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, T(C.u0));
+}
+
+template <typename T> void launch_snapshot(const DevCtx &C, int c, bool into_b, cudaStream_t s)
+{
+    const DevLevel &l = C.lv[c];
+    T *dst = (T *)(into_b ? l.snapB : l.snapA);
+    if (l.parity == 0)
+        k_snapshot<T, 0><<<cdiv(l.band_n, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, l.cox, l.coy, l.cmx, l.cmy, dst, l.band_n);
+    else
+        k_snapshot<T, 1><<<cdiv(l.band_n, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, l.cox, l.coy, l.cmx, l.cmy, dst, l.band_n);
+}
+
+template <typename T> void launch_prolong(const DevCtx &C, int cf, double theta, cudaStream_t s)
+{
+    const DevLevel &p = C.lv[cf - 1], &l = C.lv[cf];
+    int nper = 2 * l.nx + 2 * (l.ny - 2);
+    T scale = T(l.tau / (2.0 * p.tau));
+    if (l.parity == 0)
+        k_prolong<T, 0><<<cdiv(nper, 128), 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, (const T *)p.snapA,
+                                                         (const T *)p.snapB, p.band_n, p.cox, p.coy, p.cmx, p.cmy, T(theta), scale);
+    else
+        k_prolong<T, 1><<<cdiv(nper, 128), 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, (const T *)p.snapA,
+                                                         (const T *)p.snapB, p.band_n, p.cox, p.coy, p.cmx, p.cmy, T(theta), scale);
+}
+
+template <typename T> void launch_restrict(const DevCtx &C, int cc, cudaStream_t s)
+{
+    const DevLevel &p = C.lv[cc], &l = C.lv[cc + 1];
+    if (p.cmx < 2 || p.cmy < 2) return;
+    dim3 grid(cdiv(p.cmx - 1, 128), p.cmy - 1);
+    T scale = T(2.0 * p.tau / l.tau);
+#define HLBM_RESTRICT(PC, PF)                                                                                     \
+    k_restrict<T, PC, PF><<<grid, 128, 0, s>>>((T *)p.f, p.pitch, p.stride, (const T *)l.f, l.pitch, l.stride, p.cox, \
+                                               p.coy, p.cmx, p.cmy, scale)
+    if (p.parity == 0 && l.parity == 0) HLBM_RESTRICT(0, 0);
+    else if (p.parity == 0) HLBM_RESTRICT(0, 1);
+    else if (l.parity == 0) HLBM_RESTRICT(1, 0);
+    else HLBM_RESTRICT(1, 1);
+#undef HLBM_RESTRICT
+}
+
+template <typename T> void launch_ring_interp(const DevCtx &C, bool q1_and_star, cudaStream_t s)
+{
+    const DevLevel &l = C.lv[C.L - 1];
+    const DevMesh &m = C.m;
+    if (m.n_ring == 0) return;
+    T scale5 = T(1.0 - 1.0 / (2.0 * l.tau));
+    T *Q = (T *)(q1_and_star ? m.Q1 : m.Q0);
+    T *g = (T *)m.g[m.gcur];
+    int star = q1_and_star ? 1 : 0;
+    if (l.parity == 0)
+        k_ring_interp<T, 0><<<cdiv(m.n_ring, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, m.ring_don, (const T *)m.ring_w,
+                                                                 m.n_ring, Q, (const T *)m.Q0, g, m.Np, m.ring_start, scale5, star);
+    else
+        k_ring_interp<T, 1><<<cdiv(m.n_ring, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, m.ring_don, (const T *)m.ring_w,
+                                                                 m.n_ring, Q, (const T *)m.Q0, g, m.Np, m.ring_start, scale5, star);
+}
+
+template <typename T> void launch_hole_interp(const DevCtx &C, cudaStream_t s)
+{
+    const DevLevel &l = C.lv[C.L - 1];
+    const DevMesh &m = C.m;
+    if (m.n_is == 0) return;
+    T scale4 = T(2.0 * (l.tau - 1.0) / (2.0 * l.tau - 1.0));
+    if (l.parity == 0)
+        k_hole_interp<T, 0><<<cdiv(m.n_is, 128), 128, 0, s>>>((T *)l.f, l.pitch, l.stride, m.is_n, m.is_don, (const T *)m.is_w,
+                                                               m.n_is, (const T *)m.g[m.gcur], m.Np, scale4);
+    else
+        k_hole_interp<T, 1><<<cdiv(m.n_is, 128), 128, 0, s>>>((T *)l.f, l.pitch, l.stride, m.is_n, m.is_don, (const T *)m.is_w,
+                                                               m.n_is, (const T *)m.g[m.gcur], m.Np, scale4);
+}
+
+template <typename T> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
+{
+    const DevMesh &m = C.m;
+    const DevLevel &l = C.lv[C.L - 1];
+    T dt = T(C.dt_u), dt_tau = T(C.dt_u / C.tau_u);
+    T scale5 = T(1.0 - 1.0 / (2.0 * l.tau));
+    int star = msub < C.n_sub - 1 ? 1 : 0;
+    T theta_next = T(double(msub + 1) / double(C.n_sub));
+    k_fv<T><<<cdiv(m.n, 128), 128, 0, s>>>((const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n, m.slice_ptr, m.slice_len,
+                                            (const typename Ent<T>::type *)m.ent, dt, dt_tau, m.n_wall, m.ring_start,
+                                            m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5, star);
+}
+
+template <typename T> void launch_forces(const DevCtx &C, cudaStream_t s)
+{
+    const DevMesh &m = C.m;
+    k_forces<T><<<1, 512, 0, s>>>((const T *)m.g[m.gcur], m.Np, m.wea, m.web, m.wn, m.n_edges, C.qdyn, C.force_buf,
+                                   C.force_counter, C.force_cap, C.flag);
+}
+
+template <typename T>
+void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *uy, double *pop, cudaStream_t s)
+{
+    if (grid < 0) {
+        const DevMesh &m = C.m;
+        k_fields_mesh<T><<<cdiv(m.n, 128), 128, 0, s>>>((const T *)m.g[m.gcur], m.Np, m.inv, m.n, rho, ux, uy, pop);
+        return;
+    }
+    const DevLevel &l = C.lv[grid];
+    dim3 g(cdiv(l.nx, 128), l.ny);
+    if (l.parity == 0)
+        k_fields_level<T, 0><<<g, 128, 0, s>>>((const T *)l.f, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, rho, ux, uy, pop);
+    else
+        k_fields_level<T, 1><<<g, 128, 0, s>>>((const T *)l.f, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, rho, ux, uy, pop);
+}
+
+#define HLBM_INSTANTIATE(T)                                                                                   \
+    template void launch_init_level<T>(const DevCtx &, int, unsigned long long, double, cudaStream_t);        \
+    template void launch_collide<T>(const DevCtx &, int, cudaStream_t);                                       \
+    template void launch_outer_bc<T>(const DevCtx &, cudaStream_t);                                           \
+    template void launch_snapshot<T>(const DevCtx &, int, bool, cudaStream_t);                                \
+    template void launch_prolong<T>(const DevCtx &, int, double, cudaStream_t);                               \
+    template void launch_restrict<T>(const DevCtx &, int, cudaStream_t);                                      \
+    template void launch_ring_interp<T>(const DevCtx &, bool, cudaStream_t);                                  \
+    template void launch_hole_interp<T>(const DevCtx &, cudaStream_t);                                        \
+    template void launch_fv<T>(const DevCtx &, int, cudaStream_t);                                            \
+    template void launch_forces<T>(const DevCtx &, cudaStream_t);                                             \
+    template void launch_fields<T>(const DevCtx &, int, double *, double *, double *, double *, cudaStream_t);
+HLBM_INSTANTIATE(float)
+HLBM_INSTANTIATE(double)
+
+}  // namespace hlbm

@@ -1,0 +1,398 @@
+// Host set-up of the HLBM step: geometry, Eq. 3 finite-volume operators,
+// Eq. 8 / Eq. 9 interpolation stencils, refinement maps and the sub-step
+// count.  All in FP64; the device tables are converted from this plan.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
+#include "hlbm_internal.h"
+
+namespace hlbm {
+namespace {
+
+struct V2 {
+    double x, y;
+};
+inline V2 sub(V2 a, V2 b) { return {a.x - b.x, a.y - b.y}; }
+// outward normal times length of a directed segment along d (domain on the left)
+inline V2 perp(V2 d) { return {d.y, -d.x}; }
+
+inline uint64_t edge_key(int a, int b) { return (uint64_t(uint32_t(a)) << 32) | uint32_t(b); }
+
+// Solves A x = b for a small dense system by Gauss-Jordan elimination with
+// full pivoting; A is row-major n x n.  Returns false if singular.
+bool gauss_jordan(int n, double *A, double *b)
+{
+    int colmap[16];
+    for (int i = 0; i < n; i++) colmap[i] = i;
+    for (int k = 0; k < n; k++) {
+        int pr = k, pc = k;
+        double best = 0.0;
+        for (int r = k; r < n; r++)
+            for (int c = k; c < n; c++)
+                if (std::fabs(A[r * n + c]) > best) { best = std::fabs(A[r * n + c]); pr = r; pc = c; }
+        if (best == 0.0) return false;
+        if (pr != k) {
+            for (int c = 0; c < n; c++) std::swap(A[k * n + c], A[pr * n + c]);
+            std::swap(b[k], b[pr]);
+        }
+        if (pc != k) {
+            for (int r = 0; r < n; r++) std::swap(A[r * n + k], A[r * n + pc]);
+            std::swap(colmap[k], colmap[pc]);
+        }
+        double inv = 1.0 / A[k * n + k];
+        for (int c = 0; c < n; c++) A[k * n + c] *= inv;
+        b[k] *= inv;
+        for (int r = 0; r < n; r++) {
+            if (r == k) continue;
+            double m = A[r * n + k];
+            if (m == 0.0) continue;
+            for (int c = 0; c < n; c++) A[r * n + c] -= m * A[k * n + c];
+            b[r] -= m * b[k];
+        }
+    }
+    double x[16];
+    for (int k = 0; k < n; k++) x[colmap[k]] = b[k];
+    for (int k = 0; k < n; k++) b[k] = x[k];
+    return true;
+}
+
+}  // namespace
+
+double init_deviate(uint64_t seed, uint64_t grid, uint64_t node)
+{
+    // splitmix64 (Steele, Lea and Flood), one output from the given state
+    uint64_t z = (seed ^ (grid << 40) ^ node) + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    z ^= z >> 31;
+    return double(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re, double Ma,
+               double aoa_deg, const hlbm_options *opt, Plan &P, std::string &err)
+{
+    if (!lv || n_levels < 1 || n_levels > kMaxLevels) { err = "n_levels must be in 1..8"; return HLBM_EINVAL; }
+    if (!m) { err = "mesh pointer is NULL"; return HLBM_EINVAL; }
+    if (!(Re > 0.0) || !(Ma > 0.0)) { err = "Re and Ma must be positive"; return HLBM_EINVAL; }
+    hlbm_options o{};
+    if (opt) o = *opt;
+    if (o.precision != HLBM_FP64 && o.precision != HLBM_FP32) { err = "unknown precision"; return HLBM_EINVAL; }
+    if (o.n_sub < 0) { err = "n_sub must be >= 0"; return HLBM_EINVAL; }
+    P = Plan();
+    P.L = n_levels;
+    P.precision = o.precision;
+    P.seed = o.seed;
+    P.perturb = o.perturb;
+    P.chord = m->n_nodes > 0 ? m->chord : 1.0;
+    if (m->n_nodes > 0 && !(m->chord > 0.0)) { err = "chord must be positive"; return HLBM_EINVAL; }
+    // u0 = Ma c_s with c_s^2 = 1/3; nu = u0 C / Re (finest-level units)
+    P.u0 = Ma / std::sqrt(3.0);
+    P.nu = P.u0 * P.chord / Re;
+    P.qdyn = 0.5 * P.u0 * P.u0 * P.chord;
+    // structured viscosity nu = c_s^2 (tau - 1/2) per level in its own units,
+    // unstructured nu = c_s^2 tau_u (finest units)
+    for (int c = 0; c < P.L; c++) {
+        LevelPlan &l = P.lv[c];
+        l.nx = lv[c].nx; l.ny = lv[c].ny; l.ox = lv[c].ox; l.oy = lv[c].oy;
+        if (l.nx < 4 || l.ny < 4) { err = "every level needs at least 4x4 nodes"; return HLBM_EINVAL; }
+        if (c == 0 && (l.ox != 0 || l.oy != 0)) { err = "level 0 must have origin (0,0)"; return HLBM_EINVAL; }
+        if (c > 0 && (l.nx % 2 == 0 || l.ny % 2 == 0)) { err = "refined levels need odd node counts"; return HLBM_EINVAL; }
+        double scale = std::ldexp(1.0, P.L - 1 - c);
+        l.tau = 0.5 + 3.0 * P.nu / scale;
+    }
+    for (int c = 1; c < P.L; c++) {
+        LevelPlan &pa = P.lv[c - 1], &ch = P.lv[c];
+        pa.has_child = true;
+        pa.cmx = (ch.nx - 1) / 2;
+        pa.cmy = (ch.ny - 1) / 2;
+        pa.cox = ch.ox;
+        pa.coy = ch.oy;
+        if (ch.ox < 2 || ch.oy < 2 || ch.ox + pa.cmx > pa.nx - 3 || ch.oy + pa.cmy > pa.ny - 3) {
+            err = "a refined box must lie at least two nodes inside its parent";
+            return HLBM_EINVAL;
+        }
+    }
+    P.tau_u = 3.0 * P.nu;
+
+    P.n = m->n_nodes;
+    P.ntri = m->n_tri;
+    if (P.n == 0) { P.n_sub = 0; return HLBM_OK; }
+    if (!m->xy || !m->tri || !m->kind || P.ntri < 1) { err = "mesh arrays missing"; return HLBM_EINVAL; }
+
+    // ---- rigid rotation by -alpha about the pivot (alpha > 0: nose up)
+    const double al = aoa_deg * M_PI / 180.0, ca = std::cos(al), sa = std::sin(al);
+    const double px = m->pivot[0], py = m->pivot[1];
+    P.xy.resize(2 * size_t(P.n));
+    for (int p = 0; p < P.n; p++) {
+        double dx = m->xy[2 * p] - px, dy = m->xy[2 * p + 1] - py;
+        P.xy[2 * p] = px + (ca * dx + sa * dy);
+        P.xy[2 * p + 1] = py + (ca * dy - sa * dx);
+    }
+    P.tri.assign(m->tri, m->tri + 3 * size_t(P.ntri));
+    P.kind.assign(m->kind, m->kind + P.n);
+    for (int t = 0; t < 3 * P.ntri; t++)
+        if (P.tri[t] < 0 || P.tri[t] >= P.n) { err = "triangle index out of range"; return HLBM_EINVAL; }
+    for (int p = 0; p < P.n; p++)
+        if (P.kind[p] > 2) { err = "unknown node kind"; return HLBM_EINVAL; }
+    auto X = [&](int p) { return V2{P.xy[2 * size_t(p)], P.xy[2 * size_t(p) + 1]}; };
+
+    // ---- directed-edge map: edge (a,b) -> triangle index and far vertex
+    std::unordered_map<uint64_t, std::pair<int, int>> emap;
+    emap.reserve(size_t(3) * P.ntri * 2);
+    for (int t = 0; t < P.ntri; t++)
+        for (int a = 0; a < 3; a++) {
+            int i0 = P.tri[3 * t + a], i1 = P.tri[3 * t + (a + 1) % 3], i2 = P.tri[3 * t + (a + 2) % 3];
+            if (!emap.emplace(edge_key(i0, i1), std::make_pair(t, i2)).second) {
+                err = "mesh is not a consistently oriented manifold";
+                return HLBM_EINVAL;
+            }
+        }
+
+    // ---- Eq. 3 operators (cell-vertex / median-dual control volumes,
+    // piecewise-linear populations).  For triangle (P, A, B), counter-clockwise,
+    // the two dual faces of P's control volume contribute, in closed form,
+    //   s_P += -(5/24) perp(B - A)
+    //   s_A += -(1/24) perp(4B - P - 3A)
+    //   s_B += -(1/24) perp(3B + P - 4A)
+    // (exact integration of -(c.n) f along M_PA -> G -> M_PB); a boundary
+    // edge a -> b closes the control volumes of a and b with half-edge fluxes
+    //   row a: s_a += -(3/8) perp(b - a), s_b += -(1/8) perp(b - a)
+    //   row b: s_b += -(3/8) perp(b - a), s_a += -(1/8) perp(b - a).
+    // Collision weights are the control-volume means of the hat functions:
+    //   C_PP += 11/54 |T|, C_PA, C_PB += 7/108 |T|; all rows divided by
+    //   A_P = sum |T| / 3.
+    std::vector<std::vector<int>> nb(P.n);
+    for (int t = 0; t < P.ntri; t++)
+        for (int a = 0; a < 3; a++) {
+            int p = P.tri[3 * t + a];
+            nb[p].push_back(P.tri[3 * t + (a + 1) % 3]);
+            nb[p].push_back(P.tri[3 * t + (a + 2) % 3]);
+        }
+    P.rowptr.assign(P.n + 1, 0);
+    for (int p = 0; p < P.n; p++) {
+        nb[p].push_back(p);
+        std::sort(nb[p].begin(), nb[p].end());
+        nb[p].erase(std::unique(nb[p].begin(), nb[p].end()), nb[p].end());
+        P.rowptr[p + 1] = P.rowptr[p] + int(nb[p].size());
+    }
+    P.col.resize(P.rowptr[P.n]);
+    for (int p = 0; p < P.n; p++) std::copy(nb[p].begin(), nb[p].end(), P.col.begin() + P.rowptr[p]);
+    nb.clear();
+    nb.shrink_to_fit();
+    P.sx.assign(P.col.size(), 0.0);
+    P.sy.assign(P.col.size(), 0.0);
+    P.cc.assign(P.col.size(), 0.0);
+    P.area.assign(P.n, 0.0);
+    auto slot = [&](int row, int c) {
+        int lo = P.rowptr[row], hi = P.rowptr[row + 1];
+        return int(std::lower_bound(P.col.begin() + lo, P.col.begin() + hi, c) - P.col.begin());
+    };
+    for (int t = 0; t < P.ntri; t++) {
+        int v[3] = {P.tri[3 * t], P.tri[3 * t + 1], P.tri[3 * t + 2]};
+        V2 p0 = X(v[0]), p1 = X(v[1]), p2 = X(v[2]);
+        double at = 0.5 * ((p1.x - p0.x) * (p2.y - p0.y) - (p1.y - p0.y) * (p2.x - p0.x));
+        if (!(at > 0.0)) { err = "inverted or degenerate triangle"; return HLBM_EINVAL; }
+        for (int a = 0; a < 3; a++) {
+            int ip = v[a], ia = v[(a + 1) % 3], ib = v[(a + 2) % 3];
+            V2 Pp = X(ip), A = X(ia), B = X(ib);
+            V2 dP = perp(sub(B, A));
+            V2 dA = perp({4 * B.x - Pp.x - 3 * A.x, 4 * B.y - Pp.y - 3 * A.y});
+            V2 dB = perp({3 * B.x + Pp.x - 4 * A.x, 3 * B.y + Pp.y - 4 * A.y});
+            int eP = slot(ip, ip), eA = slot(ip, ia), eB = slot(ip, ib);
+            P.sx[eP] -= (5.0 / 24.0) * dP.x; P.sy[eP] -= (5.0 / 24.0) * dP.y;
+            P.sx[eA] -= dA.x / 24.0;         P.sy[eA] -= dA.y / 24.0;
+            P.sx[eB] -= dB.x / 24.0;         P.sy[eB] -= dB.y / 24.0;
+            P.cc[eP] += (11.0 / 54.0) * at;
+            P.cc[eA] += (7.0 / 108.0) * at;
+            P.cc[eB] += (7.0 / 108.0) * at;
+            P.area[ip] += at / 3.0;
+        }
+    }
+    for (int t = 0; t < P.ntri; t++)
+        for (int a = 0; a < 3; a++) {
+            int ia = P.tri[3 * t + a], ib = P.tri[3 * t + (a + 1) % 3];
+            if (emap.count(edge_key(ib, ia))) continue;  // interior edge
+            V2 n = perp(sub(X(ib), X(ia)));
+            int e;
+            e = slot(ia, ia); P.sx[e] -= 0.375 * n.x; P.sy[e] -= 0.375 * n.y;
+            e = slot(ia, ib); P.sx[e] -= 0.125 * n.x; P.sy[e] -= 0.125 * n.y;
+            e = slot(ib, ib); P.sx[e] -= 0.375 * n.x; P.sy[e] -= 0.375 * n.y;
+            e = slot(ib, ia); P.sx[e] -= 0.125 * n.x; P.sy[e] -= 0.125 * n.y;
+        }
+    for (int p = 0; p < P.n; p++)
+        for (int e = P.rowptr[p]; e < P.rowptr[p + 1]; e++) {
+            P.sx[e] /= P.area[p];
+            P.sy[e] /= P.area[p];
+            P.cc[e] /= P.area[p];
+        }
+
+    // ---- sub-steps: forward Euler stability of a mode damped at a = 1/tau_u
+    // and oscillating at b = sqrt(2) max_P sum_k |s_Pk|: dt_u <= 2a/(a^2+b^2),
+    // safety factor 1.1, at least the paper's n = 10
+    if (o.n_sub > 0) {
+        P.n_sub = o.n_sub;
+    } else {
+        double smax = 0.0;
+        for (int p = 0; p < P.n; p++) {
+            double s = 0.0;
+            for (int e = P.rowptr[p]; e < P.rowptr[p + 1]; e++) s += std::hypot(P.sx[e], P.sy[e]);
+            smax = std::max(smax, s);
+        }
+        double a = 1.0 / P.tau_u, b = std::sqrt(2.0) * smax;
+        double n = std::ceil(1.1 * (a * a + b * b) / (2.0 * a));
+        P.n_sub = n < 10.0 ? 10 : int(n);
+    }
+
+    // ---- node order on the device: wall, fluid, ring
+    P.perm.clear();
+    for (int want : {HLBM_NODE_WALL, HLBM_NODE_FLUID, HLBM_NODE_RING})
+        for (int p = 0; p < P.n; p++)
+            if (P.kind[p] == want) P.perm.push_back(p);
+    P.inv.assign(P.n, 0);
+    for (int q = 0; q < P.n; q++) P.inv[P.perm[q]] = q;
+    P.n_wall = 0;
+    P.n_ring = 0;
+    for (int p = 0; p < P.n; p++) {
+        P.n_wall += P.kind[p] == HLBM_NODE_WALL;
+        P.n_ring += P.kind[p] == HLBM_NODE_RING;
+    }
+    P.ring_start = P.n - P.n_ring;
+    for (int p = 0; p < P.n; p++)
+        if (P.kind[p] == HLBM_NODE_RING) P.ring.push_back(p);
+
+    // ---- wall edges: boundary edges between two wall nodes, in triangle order
+    for (int t = 0; t < P.ntri; t++)
+        for (int a = 0; a < 3; a++) {
+            int ia = P.tri[3 * t + a], ib = P.tri[3 * t + (a + 1) % 3];
+            if (P.kind[ia] != HLBM_NODE_WALL || P.kind[ib] != HLBM_NODE_WALL) continue;
+            if (emap.count(edge_key(ib, ia))) continue;
+            P.wea.push_back(ia);
+            P.web.push_back(ib);
+        }
+
+    // ---- finest level: nodes inside the rotated hole ellipse are not computed.
+    // Membership: rotate the node back by +alpha about the pivot and test
+    // ((X - cx)/a)^2 + ((Y - cy)/b)^2 < 1 (this arithmetic is fixed so that
+    // every implementation classifies the same nodes).
+    LevelPlan &F = P.lv[P.L - 1];
+    const double *H = m->hole;
+    if (!(H[2] > 0.0) || !(H[3] > 0.0)) { err = "hole semi-axes must be positive"; return HLBM_EINVAL; }
+    std::vector<uint8_t> inhole(size_t(F.nx) * F.ny, 0);
+    F.hx0.assign(F.ny, 0);
+    F.hx1.assign(F.ny, 0);
+    for (int y = 0; y < F.ny; y++) {
+        int first = -1, last = -2;
+        for (int x = 0; x < F.nx; x++) {
+            double dx = double(x) - px, dy = double(y) - py;
+            double Xr = (ca * dx - sa * dy) + px - H[0];
+            double Yr = (sa * dx + ca * dy) + py - H[1];
+            double qx = Xr / H[2], qy = Yr / H[3];
+            if (qx * qx + qy * qy < 1.0) {
+                if (x == 0 || y == 0 || x == F.nx - 1 || y == F.ny - 1) { err = "hole reaches a level boundary"; return HLBM_EINVAL; }
+                if (first < 0) first = x;
+                else if (x != last + 1) { err = "hole row is not contiguous"; return HLBM_EINVAL; }
+                last = x;
+                inhole[size_t(y) * F.nx + x] = 1;
+            }
+        }
+        if (first >= 0) { F.hx0[y] = first; F.hx1[y] = last + 1; }
+    }
+    // structured interpolation nodes: hole nodes with a computed D2Q9 neighbour
+    static const int ex[8] = {1, 0, -1, 0, 1, -1, -1, 1}, ey[8] = {0, 1, 0, -1, 1, 1, -1, -1};
+    for (int y = 1; y < F.ny - 1; y++)
+        for (int x = 1; x < F.nx - 1; x++) {
+            if (!inhole[size_t(y) * F.nx + x]) continue;
+            bool near = false;
+            for (int d = 0; d < 8; d++) near |= !inhole[size_t(y + ey[d]) * F.nx + x + ex[d]];
+            if (near) P.is_node.push_back(y * F.nx + x);
+        }
+
+    // ---- Eq. 8 stencils: containing triangle (lowest index when on an edge)
+    // plus the far vertex across each of its three edges (Section 3, Fig. 1)
+    double bx0 = 1e300, by0 = 1e300, bx1 = -1e300, by1 = -1e300;
+    for (int p = 0; p < P.n; p++) {
+        bx0 = std::min(bx0, P.xy[2 * p]); bx1 = std::max(bx1, P.xy[2 * p]);
+        by0 = std::min(by0, P.xy[2 * p + 1]); by1 = std::max(by1, P.xy[2 * p + 1]);
+    }
+    const double cell = 2.0;
+    int gw = int((bx1 - bx0) / cell) + 1, gh = int((by1 - by0) / cell) + 1;
+    std::vector<std::vector<int>> bucket(size_t(gw) * gh);
+    for (int t = 0; t < P.ntri; t++) {
+        double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
+        for (int a = 0; a < 3; a++) {
+            V2 q = X(P.tri[3 * t + a]);
+            x0 = std::min(x0, q.x); x1 = std::max(x1, q.x); y0 = std::min(y0, q.y); y1 = std::max(y1, q.y);
+        }
+        int i0 = int((x0 - bx0) / cell), i1 = int((x1 - bx0) / cell);
+        int j0 = int((y0 - by0) / cell), j1 = int((y1 - by0) / cell);
+        for (int j = j0; j <= j1; j++)
+            for (int i = i0; i <= i1; i++) bucket[size_t(j) * gw + i].push_back(t);
+    }
+    const size_t nis = P.is_node.size();
+    P.is_don.resize(6 * nis);
+    P.is_w.resize(6 * nis);
+    for (size_t s = 0; s < nis; s++) {
+        double x = double(P.is_node[s] % F.nx), y = double(P.is_node[s] / F.nx);
+        int found = -1;
+        if (x >= bx0 && x <= bx1 && y >= by0 && y <= by1) {
+            const std::vector<int> &cand = bucket[size_t(int((y - by0) / cell)) * gw + int((x - bx0) / cell)];
+            for (int t : cand) {  // ascending triangle index
+                V2 a = X(P.tri[3 * t]), b = X(P.tri[3 * t + 1]), c = X(P.tri[3 * t + 2]);
+                double s0 = (b.x - x) * (c.y - y) - (b.y - y) * (c.x - x);
+                double s1 = (c.x - x) * (a.y - y) - (c.y - y) * (a.x - x);
+                double s2 = (a.x - x) * (b.y - y) - (a.y - y) * (b.x - x);
+                if (s0 >= 0.0 && s1 >= 0.0 && s2 >= 0.0) { found = t; break; }
+            }
+        }
+        if (found < 0) { err = "a structured interpolation node lies outside the mesh"; return HLBM_EINVAL; }
+        int *d = &P.is_don[6 * s];
+        for (int a = 0; a < 3; a++) d[a] = P.tri[3 * found + a];
+        for (int a = 0; a < 3; a++) {
+            int e0 = P.tri[3 * found + (a + 1) % 3], e1 = P.tri[3 * found + (a + 2) % 3];
+            auto it = emap.find(edge_key(e1, e0));
+            if (it == emap.end()) { err = "an interpolation triangle touches the mesh boundary"; return HLBM_EINVAL; }
+            d[3 + a] = it->second.second;
+        }
+        // psi_k reproduce {1, X, Y, X^2, XY, Y^2} exactly at (x, y):
+        // sum_k psi_k m_j(x_k - x) = m_j(0)
+        double h = 0.0;
+        for (int k = 0; k < 6; k++) {
+            V2 q = X(d[k]);
+            h = std::max(h, std::max(std::fabs(q.x - x), std::fabs(q.y - y)));
+        }
+        double A[36], rhs[6] = {1, 0, 0, 0, 0, 0};
+        for (int k = 0; k < 6; k++) {
+            V2 q = X(d[k]);
+            double u = (q.x - x) / h, v = (q.y - y) / h;
+            double mono[6] = {1.0, u, v, u * u, u * v, v * v};
+            for (int j = 0; j < 6; j++) A[j * 6 + k] = mono[j];
+        }
+        if (!gauss_jordan(6, A, rhs)) { err = "singular 6-node interpolation stencil"; return HLBM_EINVAL; }
+        for (int k = 0; k < 6; k++) P.is_w[6 * s + k] = rhs[k];
+    }
+
+    // ---- Eq. 9 stencils: 3x3 block of finest-level nodes centred on the node
+    // nearest to the ring node, biquadratic Lagrange weights
+    P.ring_don.resize(9 * size_t(P.n_ring));
+    P.ring_w.resize(9 * size_t(P.n_ring));
+    for (int r = 0; r < P.n_ring; r++) {
+        V2 q = X(P.ring[r]);
+        int X0 = int(std::floor(q.x + 0.5)), Y0 = int(std::floor(q.y + 0.5));
+        double fx = q.x - X0, fy = q.y - Y0;
+        double lx[3] = {0.5 * fx * (fx - 1.0), 1.0 - fx * fx, 0.5 * fx * (fx + 1.0)};
+        double ly[3] = {0.5 * fy * (fy - 1.0), 1.0 - fy * fy, 0.5 * fy * (fy + 1.0)};
+        for (int b = 0; b < 3; b++)
+            for (int a = 0; a < 3; a++) {
+                int xx = X0 + a - 1, yy = Y0 + b - 1;
+                if (xx < 0 || yy < 0 || xx >= F.nx || yy >= F.ny) { err = "a ring donor lies outside the finest level"; return HLBM_EINVAL; }
+                if (inhole[size_t(yy) * F.nx + xx]) { err = "a ring donor lies inside the hole"; return HLBM_EINVAL; }
+                P.ring_don[9 * size_t(r) + 3 * b + a] = yy * F.nx + xx;
+                P.ring_w[9 * size_t(r) + 3 * b + a] = lx[a] * ly[b];
+            }
+    }
+    return HLBM_OK;
+}
+
+}  // namespace hlbm

@@ -1,0 +1,81 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared
+entry point, validates its inputs, and its host set-up (Eq. 3 operators,
+Eq. 8 / Eq. 9 stencils, hole classification, wall edges, sub-step count)
+matches the oracle's independent set-up."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2006_10487_gb300 as H
+from workloads import make_case
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2006_10487_gb300 import build
+    build.build()
+    return H.lib()
+
+
+def test_every_declared_symbol_is_exported(built):
+    hdr = open(os.path.join(ROOT, "include", "hlbm.h")).read()
+    names = sorted(set(re.findall(r"\b(hlbm_[a-z_]+)\s*\(", hdr)))
+    assert "hlbm_create" in names and "hlbm_step" in names
+    for name in names:
+        assert hasattr(built, name), name
+
+
+INTEGER_TABLES = ["rowptr", "col", "is_node", "is_don", "ring", "ring_don", "wall_edges", "n_sub"]
+REAL_TABLES = {"sx": 1e-12, "sy": 1e-12, "cc": 1e-14, "area": 1e-14, "xy": 0.0, "is_w": 1e-14, "ring_w": 1e-15}
+
+
+@pytest.mark.parametrize("name,aoa", [("hlbm_small", 0.0), ("hlbm_small", 8.0), ("hlbm_mini2", 3.0),
+                                      ("hlbm_single", 0.0)])
+def test_host_setup_matches_the_oracle(built, orc, name, aoa):
+    case = make_case(name, aoa_deg=aoa)
+    o = orc.Oracle(case)
+    for t in INTEGER_TABLES:
+        a = np.array([o.n_sub]) if t == "n_sub" else o.table(t)
+        b = H.hlbm_inspect(case, t)
+        assert a.shape == b.shape and np.array_equal(a, b), t
+    for t, tol in REAL_TABLES.items():
+        a, b = o.table(t), H.hlbm_inspect(case, t)
+        assert a.shape == b.shape
+        assert np.abs(a - b).max() <= tol * max(1.0, np.abs(a).max()), t
+
+
+def test_rejects_bad_inputs(built):
+    case = make_case("hlbm_small")
+    with pytest.raises(H.HlbmError, match="n_levels"):
+        case2 = make_case("hlbm_small")
+        case2.levels = np.zeros((0, 4), np.int32)
+        H.hlbm_inspect(case2, "n_sub")
+    bad = make_case("hlbm_small")
+    bad.tri = bad.tri[:, ::-1].copy()  # clockwise triangles
+    with pytest.raises(H.HlbmError, match="inverted"):
+        H.hlbm_inspect(bad, "n_sub")
+    big_hole = make_case("hlbm_small")
+    big_hole.hole = (70.0, 50.0, 90.0, 20.0)  # reaches the level boundary
+    with pytest.raises(H.HlbmError, match="hole"):
+        H.hlbm_inspect(big_hole, "n_sub")
+    small_hole = make_case("hlbm_small")
+    small_hole.hole = (70.0, 50.0, 3.0, 1.0)  # inside the airfoil, not covered by triangles
+    with pytest.raises(H.HlbmError, match="outside the mesh"):
+        H.hlbm_inspect(small_hole, "n_sub")
+    lv = make_case("hlbm_mini2")
+    lv.levels = np.array([[96, 48, 0, 0], [98, 65, 24, 8]], np.int32)  # even fine size
+    with pytest.raises(H.HlbmError, match="odd"):
+        H.hlbm_inspect(lv, "n_sub")
+    with pytest.raises(H.HlbmError, match="positive"):
+        H.hlbm_inspect(make_case("hlbm_small", Re=-1.0), "n_sub")
+    with pytest.raises(H.HlbmError, match="unknown table"):
+        H.hlbm_inspect(case, "nope")
+
+
+def test_explicit_sub_steps_are_kept(built):
+    case = make_case("hlbm_mini2")
+    assert H.hlbm_inspect(case, "n_sub", n_sub=37)[0] == 37

@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars: FP64 max relative field difference (max|a - b| / max|b| per field and
+grid) <= 1e-12; FP32 velocity relative L2 <= 1e-5 against FP64 and mean
+C_D / C_L relative error <= 1e-3.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from workloads import make_case
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_10487_gb300 import build
+    build.build()
+    import paper_2006_10487_gb300 as H
+    return H
+
+
+def grids(case):
+    return list(range(case.n_levels)) + ([-1] if case.n_nodes else [])
+
+
+def rel_field_diff(a, b):
+    fa, fb = np.isfinite(a), np.isfinite(b)
+    assert np.array_equal(fa, fb), "NaN pattern (hole nodes) differs"
+    if not fb.any():
+        return 0.0
+    scale = np.abs(b[fb]).max()
+    return np.abs(a[fa] - b[fb]).max() / (scale if scale > 0 else 1.0)
+
+
+def compare_fields(sol, orc_sim, case, tol):
+    worst = 0.0
+    for g in grids(case):
+        for name, a, b in zip(("rho", "ux", "uy"), sol.fields(g), orc_sim.fields(g)):
+            d = rel_field_diff(a, b)
+            assert d <= tol, f"grid {g} field {name}: relative difference {d:.3e} > {tol:.1e}"
+            worst = max(worst, d)
+    return worst
+
+
+@pytest.mark.parametrize("name,steps,aoa", [("channel", 200, 0.0), ("hlbm_small", 100, 0.0),
+                                            ("hlbm_small", 20, 8.0), ("hlbm_mini2", 100, 0.0),
+                                            ("hlbm_mini2", 30, 5.0)])
+def test_fp64_matches_oracle(H, orc, name, steps, aoa):
+    case = make_case(name, aoa_deg=aoa)
+    sol = H.Solver(case, precision="fp64")
+    sim = orc.Oracle(case)
+    assert sol.info("n_sub") == sim.n_sub
+    sol.step(steps)
+    sim.step(steps)
+    compare_fields(sol, sim, case, FP64_TOL)
+    if case.n_nodes:
+        cd, cl = sol.forces()
+        ocd, ocl = sim.forces()
+        assert len(cd) == steps
+        assert np.abs(cd - ocd).max() <= FP64_TOL * np.abs(ocd).max()
+        assert np.abs(cl - ocl).max() <= FP64_TOL * max(np.abs(ocl).max(), np.abs(ocd).max())
+
+
+def test_populations_match_oracle(H, orc):
+    case = make_case("hlbm_mini2")
+    sol = H.Solver(case, precision="fp64")
+    sim = orc.Oracle(case)
+    sol.step(7)
+    sim.step(7)
+    for g in grids(case):
+        a, b = sol.populations(g), sim.populations(g)
+        fin = np.isfinite(b).all(axis=1)
+        assert np.array_equal(np.isfinite(a).all(axis=1), fin)
+        assert np.abs(a[fin] - b[fin]).max() <= FP64_TOL
+
+
+def test_single_config_one_coarse_step_fp64(H, orc):
+    """Full-size single case (2048x1024 + two nested boxes, 200 704-node mesh),
+    the configuration the benchmark times, after one coarse step
+    (4 finest steps x n_sub finite-volume sub-steps)."""
+    case = make_case("hlbm_single")
+    sol = H.Solver(case, precision="fp64")
+    sim = orc.Oracle(case)
+    sol.step(1)
+    sim.step(1)
+    compare_fields(sol, sim, case, FP64_TOL)
+
+
+def test_single_config_one_coarse_step_fp32(H, orc):
+    case = make_case("hlbm_single")
+    sol = H.Solver(case, precision="fp32")
+    sim = orc.Oracle(case)
+    sol.step(1)
+    sim.step(1)
+    u0 = case.Ma / math.sqrt(3)
+    for g in grids(case):
+        r, ux, uy = sol.fields(g)
+        orr, oux, ouy = sim.fields(g)
+        m = np.isfinite(orr)
+        err = math.sqrt(((ux[m] - oux[m]) ** 2 + (uy[m] - ouy[m]) ** 2).sum() / (oux[m] ** 2 + ouy[m] ** 2).sum())
+        assert err <= 1e-5, f"grid {g}: velocity relative L2 {err:.2e}"
+        assert np.abs(r[m] - orr[m]).max() <= 1e-5
+        assert np.abs(ux[m] - oux[m]).max() <= 1e-4 * u0 * 10
+
+
+@pytest.mark.parametrize("aoa", [0.0, 8.0])
+def test_fp32_accuracy_against_fp64(H, aoa):
+    case = make_case("hlbm_small", aoa_deg=aoa)
+    a = H.Solver(case, precision="fp32")
+    b = H.Solver(case, precision="fp64")
+    a.step(400)
+    b.step(400)
+    for g in grids(case):
+        _, ux, uy = a.fields(g)
+        _, vx, vy = b.fields(g)
+        m = np.isfinite(vx)
+        err = math.sqrt(((ux[m] - vx[m]) ** 2 + (uy[m] - vy[m]) ** 2).sum() / (vx[m] ** 2 + vy[m] ** 2).sum())
+        assert err <= 1e-5, f"grid {g}: velocity relative L2 {err:.2e}"
+    cd32, cl32 = a.forces()
+    cd64, cl64 = b.forces()
+    mcd, mcl = cd64[100:].mean(), cl64[100:].mean()
+    assert abs(cd32[100:].mean() - mcd) <= 1e-3 * abs(mcd)
+    assert abs(cl32[100:].mean() - mcl) <= 1e-3 * max(abs(mcl), abs(mcd) if aoa == 0 else 0.0)
+
+
+def test_graphs_and_plain_launches_agree_bitwise(H):
+    case = make_case("hlbm_mini2")
+    a = H.Solver(case, precision="fp64", use_graphs=True)
+    b = H.Solver(case, precision="fp64", use_graphs=False)
+    a.step(9)
+    b.step(9)
+    for g in grids(case):
+        for x, y in zip(a.fields(g), b.fields(g)):
+            assert np.array_equal(x, y, equal_nan=True)
+    assert np.array_equal(a.forces()[0], b.forces()[0])
+
+
+def test_runs_are_deterministic(H):
+    case = make_case("hlbm_small")
+    res = []
+    for _ in range(2):
+        s = H.Solver(case, precision="fp32")
+        s.step(25)
+        res.append((s.fields(-1), s.fields(0), s.forces()))
+    for x, y in zip(res[0][0] + res[0][1], res[1][0] + res[1][1]):
+        assert np.array_equal(x, y, equal_nan=True)
+    assert np.array_equal(res[0][2][0], res[1][2][0])
+
+
+def test_hole_nodes_are_nan_and_the_rest_finite(H):
+    case = make_case("hlbm_small")
+    s = H.Solver(case, precision="fp64")
+    s.step(3)
+    r, _, _ = s.fields(0)
+    nan = ~np.isfinite(r)
+    n_interp = s.info("n_interp")
+    assert nan.sum() > n_interp > 0
+    y, x = np.divmod(np.arange(r.size), case.levels[0][0])
+    cx, cy, a, b = case.hole
+    inside = ((x - cx) / a) ** 2 + ((y - cy) / b) ** 2 < 1
+    assert np.array_equal(nan, inside)
+
+
+def test_force_ring_buffer_keeps_the_latest_samples(H):
+    case = make_case("hlbm_mini2")
+    s = H.Solver(case, precision="fp64", force_cap=8)
+    s.step(5)
+    cd1, _ = s.forces()
+    assert len(cd1) == 5
+    s.step(20)
+    cd2, _ = s.forces()
+    assert len(cd2) == 8  # older samples were overwritten
+    ref = H.Solver(case, precision="fp64")
+    ref.step(25)
+    cd_all, _ = ref.forces()
+    assert np.array_equal(cd1, cd_all[:5])
+    assert np.array_equal(cd2, cd_all[-8:])
+
+
+def test_health_flag_reports_instability(H):
+    """An explicit finite-volume sub-step count far below the stability bound
+    blows up; hlbm_step reports it through the NaN health flag."""
+    case = make_case("hlbm_small")
+    s = H.Solver(case, precision="fp64", n_sub=10, check_every=10)
+    with pytest.raises(H.HlbmError) as e:
+        s.step(400)
+    assert e.value.code == H.HLBM_EUNSTABLE

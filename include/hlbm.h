@@ -61,7 +61,8 @@ typedef struct {
  * clockwise node indices; kind: [n_nodes] HLBM_NODE_*.  pivot: rotation
  * centre (quarter chord).  hole: inner interface ellipse (cx, cy, a, b), axis
  * aligned in the zero-incidence pose; finest-level nodes inside it are not
- * computed.  n_nodes == 0 gives a plain channel (lattice only). */
+ * computed.  n_nodes == 0 gives a plain channel (lattice only); chord is
+ * always the length scale of Re and must be positive. */
 typedef struct {
     int32_t n_nodes;
     const double *xy;
@@ -155,7 +156,8 @@ int hlbm_time_kernel(hlbm_ctx *ctx, const char *kernel, int reps, double *avg_ms
  * Tables: "rowptr", "col", "sx", "sy", "cc" (Eq. 3 operators, CSR over the
  * input node order, columns ascending), "area", "xy" (rotated),
  * "is_node", "is_don", "is_w" (Eq. 8 stencils), "ring", "ring_don",
- * "ring_w" (Eq. 9 stencils), "wall_edges", "n_sub".  out == NULL queries n. */
+ * "ring_w" (Eq. 9 stencils), "wall_edges", "n_sub", "inactive<l>" (1 for
+ * nodes of level l that are not computed).  out == NULL queries n. */
 int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re, double Ma,
                  double aoa_deg, const hlbm_options *opt, const char *table, double *out,
                  size_t cap, size_t *n);

@@ -265,12 +265,16 @@ int orc_fv_operators(int n, const double *xy, int ntri, const int *tri, const do
         double at = 0.5 * ((v[1][0] - v[0][0]) * (v[2][1] - v[0][1])
                            - (v[1][1] - v[0][1]) * (v[2][0] - v[0][0]));
         if (!(at > 0.0)) { nnz = -1; goto done; }
-        double g[2] = {(v[0][0] + v[1][0] + v[2][0]) / 3.0, (v[0][1] + v[1][1] + v[2][1]) / 3.0};
         for (int a = 0; a < 3; a++) {
             int ip = tri[3 * t + a], ia = tri[3 * t + (a + 1) % 3], ib = tri[3 * t + (a + 2) % 3];
-            const double *P = v[a], *A = v[(a + 1) % 3], *B = v[(a + 2) % 3];
-            double mpa[2] = {0.5 * (P[0] + A[0]), 0.5 * (P[1] + A[1])};
-            double mpb[2] = {0.5 * (P[0] + B[0]), 0.5 * (P[1] + B[1])};
+            /* coordinates relative to P (P at the origin), so that the short
+             * dual segments are not formed by cancelling large absolute
+             * coordinates */
+            double A[2] = {v[(a + 1) % 3][0] - v[a][0], v[(a + 1) % 3][1] - v[a][1]};
+            double B[2] = {v[(a + 2) % 3][0] - v[a][0], v[(a + 2) % 3][1] - v[a][1]};
+            double g[2] = {(A[0] + B[0]) / 3.0, (A[1] + B[1]) / 3.0};
+            double mpa[2] = {0.5 * A[0], 0.5 * A[1]};
+            double mpb[2] = {0.5 * B[0], 0.5 * B[1]};
             /* the sub-quad P, M_PA, G, M_PB is counter-clockwise, so the outward
              * normal times length of a directed edge (u -> v) is (dy, -dx) */
             double n1[2] = {g[1] - mpa[1], -(g[0] - mpa[0])};
@@ -881,6 +885,18 @@ orc *orc_create(int L, const int *levels, int n, const double *xy, int ntri, con
                 if (near) o->is_node[o->n_is++] = (int)p;
             }
         for (int s = 0; s < o->n_is; s++) lf->type[o->is_node[s]] = T_INTERP;
+        /* a covered coarse node whose coincident finer node is not computed
+         * (hole or interpolation node) is not computed either */
+        for (int c = L - 2; c >= 0; c--) {
+            olevel *pc = &o->lv[c], *pf = &o->lv[c + 1];
+            for (int y = 0; y < pc->ny; y++)
+                for (int x = 0; x < pc->nx; x++) {
+                    size_t p = (size_t)y * pc->nx + x;
+                    if (pc->type[p] != T_COVERED) continue;
+                    unsigned char t = pf->type[(size_t)(2 * (y - pf->oy)) * pf->nx + 2 * (x - pf->ox)];
+                    if (t == T_HOLE || t == T_INTERP) pc->type[p] = T_HOLE;
+                }
+        }
         /* Eq. 8 stencils: the triangle holding the node (lowest index if on an
          * edge) plus the far vertex of each of its three edge neighbours */
         o->is_don = malloc((size_t)o->n_is * 6 * sizeof(int));

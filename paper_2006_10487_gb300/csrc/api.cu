@@ -293,7 +293,7 @@ template <typename T> void build_device(hlbm_ctx *c)
         dl.stride = size_t(lp.ny + 2) * dl.pitch;
         dl.f = dalloc(c, 9 * dl.stride * sizeof(T));
         dl.tau = lp.tau;
-        if (l == P.L - 1 && P.n > 0) {
+        if (!lp.hx0.empty()) {
             dl.hx0 = upload(c, lp.hx0);
             dl.hx1 = upload(c, lp.hx1);
         }
@@ -518,8 +518,7 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
         double u = 0;
         for (int l = 0; l < P.L; l++) {
             double nn = double(P.lv[l].nx) * P.lv[l].ny;
-            if (l == P.L - 1 && P.n > 0)
-                for (int y = 0; y < P.lv[l].ny; y++) nn -= P.lv[l].hx1[y] - P.lv[l].hx0[y];
+            for (size_t y = 0; y < P.lv[l].hx0.size(); y++) nn -= P.lv[l].hx1[y] - P.lv[l].hx0[y];
             u += nn * double(1L << l);
         }
         *value = u;
@@ -535,8 +534,7 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
         int l = k[13] - '0';
         if (l < 0 || l >= P.L) return HLBM_EINVAL;
         double nn = double(P.lv[l].nx) * P.lv[l].ny;
-        if (l == P.L - 1 && P.n > 0)
-            for (int y = 0; y < P.lv[l].ny; y++) nn -= P.lv[l].hx1[y] - P.lv[l].hx0[y];
+        for (size_t y = 0; y < P.lv[l].hx0.size(); y++) nn -= P.lv[l].hx1[y] - P.lv[l].hx0[y];
         *value = nn * 18.0 * (P.precision == HLBM_FP32 ? 4.0 : 8.0);
     }
     else return HLBM_EINVAL;
@@ -575,6 +573,12 @@ int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double 
     else if (t == "wall_edges") {
         for (size_t e = 0; e < P.wea.size(); e++) { v.push_back(P.wea[e]); v.push_back(P.web[e]); }
     } else if (t == "n_sub") v.assign(1, double(P.n_sub));
+    else if (t.size() == 9 && t.compare(0, 8, "inactive") == 0 && t[8] >= '0' && t[8] < '0' + P.L) {
+        const LevelPlan &l = P.lv[t[8] - '0'];
+        v.assign(size_t(l.nx) * l.ny, 0.0);
+        for (size_t y = 0; y < l.hx0.size(); y++)
+            for (int x = l.hx0[y]; x < l.hx1[y]; x++) v[y * l.nx + x] = 1.0;
+    }
     else return fail(nullptr, HLBM_EINVAL, "unknown table");
     *n = v.size();
     if (out) {

@@ -259,11 +259,12 @@ __global__ void k_prolong(T *f, int nx, int ny, int pitch, size_t stride, const 
 // box take the coincident fine state with f^neq scaled by 2 tau_c / tau_f.
 template <typename T, int PC, int PF>
 __global__ void k_restrict(T *fc, int pitch_c, size_t stride_c, const T *ff, int pitch_f, size_t stride_f, int cox,
-                           int coy, int cmx, int cmy, T scale)
+                           int coy, int cmx, int cmy, T scale, const int *hx0, const int *hx1)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
     if (a >= cmx - 1) return;
     int X = cox + 1 + a, Y = coy + 1 + b;
+    if (hx0 && X >= hx0[Y] && X < hx1[Y]) return;  // over the hole: not computed
     T d[9], q[12];
     load_state<T, PF>(ff, node(2 * (X - cox), 2 * (Y - coy), pitch_f), pitch_f, stride_f, d);
     to_q(d, q);
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(512) k_forces(const T *g, int Np, const int *w
 }
 
 // Density, velocity (and optionally populations) of a level in FP64, x fastest;
-// NaN inside the hole.
+// NaN on nodes that are not computed (the hole and the coarse nodes over it).
 template <typename T, int P>
 __global__ void k_fields_level(const T *f, int nx, int ny, int pitch, size_t stride, const int *hx0, const int *hx1,
                                double *rho, double *ux, double *uy, double *pop)
@@ -567,7 +568,7 @@ template <typename T> void launch_restrict(const DevCtx &C, int cc, cudaStream_t
     T scale = T(2.0 * p.tau / l.tau);
 #define HLBM_RESTRICT(PC, PF)                                                                                     \
     k_restrict<T, PC, PF><<<grid, 128, 0, s>>>((T *)p.f, p.pitch, p.stride, (const T *)l.f, l.pitch, l.stride, p.cox, \
-                                               p.coy, p.cmx, p.cmy, scale)
+                                               p.coy, p.cmx, p.cmy, scale, p.hx0, p.hx1)
     if (p.parity == 0 && l.parity == 0) HLBM_RESTRICT(0, 0);
     else if (p.parity == 0) HLBM_RESTRICT(0, 1);
     else if (l.parity == 0) HLBM_RESTRICT(1, 0);

@@ -85,8 +85,9 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     P.precision = o.precision;
     P.seed = o.seed;
     P.perturb = o.perturb;
-    P.chord = m->n_nodes > 0 ? m->chord : 1.0;
-    if (m->n_nodes > 0 && !(m->chord > 0.0)) { err = "chord must be positive"; return HLBM_EINVAL; }
+    // the chord is the length scale of Re, also for a mesh-less channel
+    P.chord = m->chord;
+    if (!(m->chord > 0.0)) { err = "chord must be positive"; return HLBM_EINVAL; }
     // u0 = Ma c_s with c_s^2 = 1/3; nu = u0 C / Re (finest-level units)
     P.u0 = Ma / std::sqrt(3.0);
     P.nu = P.u0 * P.chord / Re;
@@ -156,6 +157,7 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     //   s_P += -(5/24) perp(B - A)
     //   s_A += -(1/24) perp(4B - P - 3A)
     //   s_B += -(1/24) perp(3B + P - 4A)
+    // (evaluated with P at the origin)
     // (exact integration of -(c.n) f along M_PA -> G -> M_PB); a boundary
     // edge a -> b closes the control volumes of a and b with half-edge fluxes
     //   row a: s_a += -(3/8) perp(b - a), s_b += -(1/8) perp(b - a)
@@ -196,10 +198,12 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
         if (!(at > 0.0)) { err = "inverted or degenerate triangle"; return HLBM_EINVAL; }
         for (int a = 0; a < 3; a++) {
             int ip = v[a], ia = v[(a + 1) % 3], ib = v[(a + 2) % 3];
-            V2 Pp = X(ip), A = X(ia), B = X(ib);
+            // edge vectors from P (keeps the short dual segments free of
+            // cancellation between large absolute coordinates)
+            V2 A = sub(X(ia), X(ip)), B = sub(X(ib), X(ip));
             V2 dP = perp(sub(B, A));
-            V2 dA = perp({4 * B.x - Pp.x - 3 * A.x, 4 * B.y - Pp.y - 3 * A.y});
-            V2 dB = perp({3 * B.x + Pp.x - 4 * A.x, 3 * B.y + Pp.y - 4 * A.y});
+            V2 dA = perp({4 * B.x - 3 * A.x, 4 * B.y - 3 * A.y});
+            V2 dB = perp({3 * B.x - 4 * A.x, 3 * B.y - 4 * A.y});
             int eP = slot(ip, ip), eA = slot(ip, ia), eB = slot(ip, ib);
             P.sx[eP] -= (5.0 / 24.0) * dP.x; P.sy[eP] -= (5.0 / 24.0) * dP.y;
             P.sx[eA] -= dA.x / 24.0;         P.sy[eA] -= dA.y / 24.0;
@@ -298,6 +302,22 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
             }
         }
         if (first >= 0) { F.hx0[y] = first; F.hx1[y] = last + 1; }
+    }
+    // coarser levels: a covered node whose coincident finer node is not computed
+    // is not computed either (per row again one interval)
+    for (int c = P.L - 2; c >= 0; c--) {
+        LevelPlan &pa = P.lv[c];
+        const LevelPlan &ch = P.lv[c + 1];
+        pa.hx0.assign(pa.ny, 0);
+        pa.hx1.assign(pa.ny, 0);
+        for (int Y = pa.coy + 1; Y <= pa.coy + pa.cmy - 1; Y++) {
+            int j = 2 * (Y - pa.coy);
+            int a = ch.hx0[j], b = ch.hx1[j];
+            if (a >= b) continue;
+            int X0 = std::max(pa.cox + (a + 1) / 2, pa.cox + 1);
+            int X1 = std::min(pa.cox + (b - 1) / 2, pa.cox + pa.cmx - 1);
+            if (X0 <= X1) { pa.hx0[Y] = X0; pa.hx1[Y] = X1 + 1; }
+        }
     }
     // structured interpolation nodes: hole nodes with a computed D2Q9 neighbour
     static const int ex[8] = {1, 0, -1, 0, 1, -1, -1, 1}, ey[8] = {0, 1, 0, -1, 1, 1, -1, -1};

@@ -42,6 +42,10 @@ def test_host_setup_matches_the_oracle(built, orc, name, aoa):
         a = np.array([o.n_sub]) if t == "n_sub" else o.table(t)
         b = H.hlbm_inspect(case, t)
         assert a.shape == b.shape and np.array_equal(a, b), t
+    for lv in range(case.n_levels):
+        typ = o.table(f"type{lv}")
+        want = ((typ == 4) | (typ == 5)).astype(float)  # hole or interpolation node
+        assert np.array_equal(H.hlbm_inspect(case, f"inactive{lv}"), want), f"inactive{lv}"
     for t, tol in REAL_TABLES.items():
         a, b = o.table(t), H.hlbm_inspect(case, t)
         assert a.shape == b.shape

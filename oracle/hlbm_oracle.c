@@ -336,12 +336,16 @@ done:
 }
 
 /* Eq. 3, one explicit sub-step on every node (no wall or interface rule):
- * g'_i(P) = g_i(P) + dt sum_k S_ik g_i(P_k) - (dt/tau_u) sum_k C_Pk [g_i - g_i^eq](P_k). */
+ * g'_i(P) = g_i(P) + dt sum_k S_ik g_i(P_k) - (dt/tau_u) sum_k C_Pk [g_i - g_i^eq](P_k).
+ * The control volume is closed, so sum_k S_ik = 0 and the streaming sum equals
+ * sum_k S_ik [g_i(P_k) - g_i(P)]; it is evaluated in that form, which avoids
+ * cancelling terms of size |S| g against a result of size |S| h |grad g|. */
 void orc_fv_substep(int n, const int *rowptr, const int *col, const double *sx, const double *sy,
                     const double *cc, double dt, double tau_u, const double *g, double *gnew)
 {
     for (int p = 0; p < n; p++) {
         double acc[9] = {0};
+        const double *gp = g + 9 * (size_t)p;
         for (int e = rowptr[p]; e < rowptr[p + 1]; e++) {
             const double *gk = g + 9 * (size_t)col[e];
             double rho, ux, uy, eq[9];
@@ -349,7 +353,7 @@ void orc_fv_substep(int n, const int *rowptr, const int *col, const double *sx, 
             orc_feq(rho, ux, uy, eq);
             for (int i = 0; i < 9; i++) {
                 double s = CX[i] * sx[e] + CY[i] * sy[e];
-                acc[i] += dt * s * gk[i] - (dt / tau_u) * cc[e] * (gk[i] - eq[i]);
+                acc[i] += dt * s * (gk[i] - gp[i]) - (dt / tau_u) * cc[e] * (gk[i] - eq[i]);
             }
         }
         for (int i = 0; i < 9; i++) gnew[9 * (size_t)p + i] = g[9 * (size_t)p + i] + acc[i];

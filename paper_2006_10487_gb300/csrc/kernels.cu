@@ -364,9 +364,12 @@ __global__ void __launch_bounds__(128) k_fv(const T *__restrict__ g, T *__restri
     if (r >= n) return;
     int sl = r >> 5, lane = r & 31;
     int base = slice_ptr[sl] + lane, len = slice_len[sl];
-    T acc[9];
+    T own[9], acc[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) acc[i] = T(0);
+    for (int i = 0; i < 9; i++) {
+        own[i] = g[size_t(i) * Np + r];
+        acc[i] = T(0);
+    }
     for (int e = 0; e < len; e++) {
         T sx, sy, c;
         int k;
@@ -379,13 +382,15 @@ __global__ void __launch_bounds__(128) k_fv(const T *__restrict__ g, T *__restri
         T cs = dt_tau * c;
 #pragma unroll
         for (int i = 0; i < 9; i++) {
+            // streaming against the node's own value: sum_k s_Pk = 0, so
+            // sum_k s_Pk g_k = sum_k s_Pk (g_k - g_P) without cancellation
             T s = dt * (T(cx(i)) * sx + T(cy(i)) * sy);
-            acc[i] += s * d[i] - cs * (d[i] - deq<T>(i, rho, ux, uy));
+            acc[i] += s * (d[i] - own[i]) - cs * (d[i] - deq<T>(i, rho, ux, uy));
         }
     }
     T d[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) d[i] = g[size_t(i) * Np + r] + acc[i];
+    for (int i = 0; i < 9; i++) d[i] = own[i] + acc[i];
     if (r < n_wall) {
         T rho, ux, uy;
         moments(d, rho, ux, uy);

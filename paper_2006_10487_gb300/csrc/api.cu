@@ -133,7 +133,7 @@ template <typename T> void coarse_step(hlbm_ctx *c, cudaStream_t s)
     advance<T>(c, 0, 0.0, s);
     if (c->dev.m.n > 0) {
         launch_forces<T>(c->dev, s);
-        c->launches++;
+        c->launches += 2;
     }
     c->launches_per_step = c->launches - before;
 }
@@ -309,6 +309,7 @@ template <typename T> void build_device(hlbm_ctx *c)
     if (P.n > 0) upload_mesh<T>(c);
     D.force_cap = std::max(1, D.force_cap);
     D.force_buf = (double *)dalloc(c, size_t(2) * D.force_cap * sizeof(double));
+    D.force_partial = (double *)dalloc(c, size_t(2) * std::max(1, (D.m.n_edges + 127) / 128) * sizeof(double));
     D.force_counter = (int *)dalloc(c, 2 * sizeof(int));
     D.flag = D.force_counter + 1;
     ck(cudaMemsetAsync(D.force_counter, 0, 2 * sizeof(int), c->stream), "memset");

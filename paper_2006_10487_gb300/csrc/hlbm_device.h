@@ -55,6 +55,7 @@ struct DevCtx {
     double u0 = 0, tau_u = 0, dt_u = 0, qdyn = 0;
     int n_sub = 0;
     double *force_buf = nullptr;  // [force_cap][2]
+    double *force_partial = nullptr;  // [ceil(n_edges / 128)][2] per-block partial sums
     int *force_counter = nullptr;
     int *flag = nullptr;
     int force_cap = 0;

@@ -9,6 +9,7 @@
 // Eq. 10-11 (forces).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "hlbm_device.h"
@@ -276,62 +277,75 @@ __global__ void k_restrict(T *fc, int pitch_c, size_t stride_c, const T *ff, int
 // 3x3 lattice donors.  With star != 0 (after the lattice step) the kernel also
 // sets the ring nodes of the read buffer to the Eq. 5-6 state at theta = 0:
 // f^eq + (1 - 1/(2 tau_s)) f^neq of the data at t (Q0).
+// 16 lanes per ring node: lane k < 9 takes donor k; xor-shuffle sum.
 template <typename T, int P>
 __global__ void k_ring_interp(const T *f, int pitch, size_t stride, const int *don, const T *w, int n_ring,
                               T *Q, const T *Q0, T *g, int Np, int ring_start, T scale5, int star)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_ring) return;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int r = t >> 4, k = t & 15;
+    bool live = r < n_ring;
+    int rr = live ? r : n_ring - 1;
     T acc[12];
 #pragma unroll
     for (int m = 0; m < 12; m++) acc[m] = T(0);
-    for (int k = 0; k < 9; k++) {
+    if (k < 9) {
         T d[9], q[12];
-        load_state<T, P>(f, size_t(don[9 * r + k]), pitch, stride, d);
+        load_state<T, P>(f, size_t(don[9 * rr + k]), pitch, stride, d);
         to_q(d, q);
-        T wk = w[9 * r + k];
+        T wk = w[9 * rr + k];
 #pragma unroll
-        for (int m = 0; m < 12; m++) acc[m] += wk * q[m];
+        for (int m = 0; m < 12; m++) acc[m] = wk * q[m];
     }
 #pragma unroll
-    for (int m = 0; m < 12; m++) Q[size_t(m) * n_ring + r] = acc[m];
-    if (star) {
-        T q[12], d[9];
+    for (int m = 0; m < 12; m++)
 #pragma unroll
-        for (int m = 0; m < 12; m++) q[m] = Q0[size_t(m) * n_ring + r];
-        from_q(q, scale5, d);
+        for (int o = 1; o < 16; o <<= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+    if (!live) return;
 #pragma unroll
-        for (int i = 0; i < 9; i++) g[size_t(i) * Np + ring_start + r] = d[i];
+    for (int m = 0; m < 12; m++)
+        if (m == k) Q[size_t(m) * n_ring + r] = acc[m];
+    if (star && k < 9) {
+        T rho = Q0[r], ux = Q0[size_t(n_ring) + r], uy = Q0[size_t(2) * n_ring + r];
+        T nk = Q0[size_t(3 + k) * n_ring + r];
+        g[size_t(k) * Np + ring_start + r] = deq<T>(k, rho, ux, uy) + scale5 * nk;
     }
 }
 
 // Eq. 4 with Eq. 8: post-collision state of the structured interpolation
 // nodes from six unstructured donors, written where the collision at parity
-// P would write it.
+// P would write it.  8 lanes per node: lane k < 6 takes donor k.
 template <typename T, int P>
 __global__ void k_hole_interp(T *f, int pitch, size_t stride, const int *is_n, const int *don, const T *w, int n_is,
                               const T *g, int Np, T scale4)
 {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_is) return;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int s = t >> 3, k = t & 7;
+    bool live = s < n_is;
+    int ss = live ? s : n_is - 1;
     T acc[12];
 #pragma unroll
     for (int m = 0; m < 12; m++) acc[m] = T(0);
-    for (int k = 0; k < 6; k++) {
-        int p = don[6 * s + k];
+    if (k < 6) {
+        int p = don[6 * ss + k];
         T d[9], q[12];
 #pragma unroll
         for (int i = 0; i < 9; i++) d[i] = g[size_t(i) * Np + p];
         to_q(d, q);
-        T wk = w[6 * s + k];
+        T wk = w[6 * ss + k];
 #pragma unroll
-        for (int m = 0; m < 12; m++) acc[m] += wk * q[m];
+        for (int m = 0; m < 12; m++) acc[m] = wk * q[m];
     }
-    T d[9];
-    from_q(acc, scale4, d);
-    size_t n = size_t(is_n[s]);
 #pragma unroll
-    for (int i = 0; i < 9; i++) f[wr_idx<P>(i, n, pitch, stride)] = d[i];
+    for (int m = 0; m < 12; m++)
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+    if (!live) return;
+    size_t n = size_t(is_n[s]);
+    // lane k writes population k (lane 0 also population 8)
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+        if ((i & 7) == k) f[wr_idx<P>(i, n, pitch, stride)] = deq<T>(i, acc[0], acc[1], acc[2]) + scale4 * acc[3 + i];
 }
 
 template <typename T> struct Ent;
@@ -349,28 +363,40 @@ __device__ __forceinline__ void unpack(const double4_32a &e, double &sx, double 
 
 // Eq. 3, one explicit sub-step on every mesh node (node-major gather over the
 // sliced-ELL operator rows, no atomics):
-//   g'_i(P) = g_i(P) + dt sum_k (c_i . s_Pk) g_i(P_k) - dt/tau_u sum_k C_Pk g^neq_i(P_k)
+//   g'_i(P) = g_i(P) + dt sum_k (c_i . s_Pk) (g_i(P_k) - g_i(P)) - dt/tau_u sum_k C_Pk g^neq_i(P_k)
+// (sum_k s_Pk = 0, so the streaming sum is taken against the node's own value)
 // then, on wall rows, the no-slip rule (rho and f^neq kept, u = 0); on ring
 // rows, unless this is the last sub-step, the Eq. 5-6 state of the next
 // sub-step (theta_next) replaces the result.
+//
+// Work split: a block of 128 threads is one 32-row slice; each row is served
+// by 4 adjacent lanes, lane q taking entries q, q + 4, ... so the gathers of
+// all neighbours are in flight together; the four partial sums are combined
+// with two xor shuffles and lane q stores populations q, q + 4 (and 8 for q = 0).
+constexpr int kFvThreads = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
-                                            const int *__restrict__ slice_ptr, const int *__restrict__ slice_len,
-                                            const typename Ent<T>::type *__restrict__ ent, T dt, T dt_tau, int n_wall,
-                                            int ring_start, int n_ring, const T *__restrict__ Q0,
-                                            const T *__restrict__ Q1, T theta_next, T scale5, int star)
+__global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
+                                                   const int *__restrict__ slice_ptr,
+                                                   const int *__restrict__ slice_len,
+                                                   const typename Ent<T>::type *__restrict__ ent, T dt, T dt_tau,
+                                                   int n_wall, int ring_start, int n_ring,
+                                                   const T *__restrict__ Q0, const T *__restrict__ Q1, T theta_next,
+                                                   T scale5, int star)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    int sl = r >> 5, lane = r & 31;
-    int base = slice_ptr[sl] + lane, len = slice_len[sl];
+    const int sl = blockIdx.x;
+    const int row_local = threadIdx.x >> 2, q = threadIdx.x & 3;
+    const int r = sl * 32 + row_local;
+    const bool live = r < n;
+    const int rr = live ? r : n - 1;  // padding lanes shadow a valid row (results discarded)
+    const int base = slice_ptr[sl] + row_local, len = slice_len[sl];
     T own[9], acc[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        own[i] = g[size_t(i) * Np + r];
+        own[i] = g[size_t(i) * Np + rr];
         acc[i] = T(0);
     }
-    for (int e = 0; e < len; e++) {
+    for (int e = q; e < len; e += 4) {
         T sx, sy, c;
         int k;
         unpack(ent[base + 32 * e], sx, sy, c, k);
@@ -382,12 +408,16 @@ __global__ void __launch_bounds__(128) k_fv(const T *__restrict__ g, T *__restri
         T cs = dt_tau * c;
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            // streaming against the node's own value: sum_k s_Pk = 0, so
-            // sum_k s_Pk g_k = sum_k s_Pk (g_k - g_P) without cancellation
-            T s = dt * (T(cx(i)) * sx + T(cy(i)) * sy);
-            acc[i] += s * (d[i] - own[i]) - cs * (d[i] - deq<T>(i, rho, ux, uy));
+            T sd = dt * (T(cx(i)) * sx + T(cy(i)) * sy);
+            acc[i] += sd * (d[i] - own[i]) - cs * (d[i] - deq<T>(i, rho, ux, uy));
         }
     }
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 1);
+        acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 2);
+    }
+    if (!live) return;
     T d[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) d[i] = own[i] + acc[i];
@@ -398,47 +428,52 @@ __global__ void __launch_bounds__(128) k_fv(const T *__restrict__ g, T *__restri
         for (int i = 0; i < 9; i++) d[i] = d[i] - deq<T>(i, rho, ux, uy) + deq<T>(i, rho, T(0), T(0));
     } else if (star && r >= ring_start) {
         int q_ = r - ring_start;
-        T q[12];
+        T qq[12];
 #pragma unroll
         for (int m = 0; m < 12; m++)
-            q[m] = (T(1) - theta_next) * Q0[size_t(m) * n_ring + q_] + theta_next * Q1[size_t(m) * n_ring + q_];
-        from_q(q, scale5, d);
+            qq[m] = (T(1) - theta_next) * Q0[size_t(m) * n_ring + q_] + theta_next * Q1[size_t(m) * n_ring + q_];
+        from_q(qq, scale5, d);
     }
 #pragma unroll
-    for (int i = 0; i < 9; i++) gn[size_t(i) * Np + r] = d[i];
+    for (int i = 0; i < 9; i++)
+        if ((i & 3) == q) gn[size_t(i) * Np + r] = d[i];
 }
 
 // Eq. 10-11: force on the body from nodal pressure and stress at the wall,
 // traction -(p - p0) n - Pi^neq . n with p = rho / 3, edge values the mean of
-// the two end nodes; one block, FP64 tree reduction (deterministic).
+// the two end nodes.  Two passes with a fixed summation order (deterministic):
+// k_forces_partial writes one FP64 (F_x, F_y) partial per block of wall
+// edges, k_forces_final adds the partials in block order and records
+// (C_D, C_L) in the ring buffer.
+constexpr int kForceThreads = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(512) k_forces(const T *g, int Np, const int *wea, const int *web, const double *wn,
-                                                int n_edges, double qdyn, double *buf, int *counter, int cap,
-                                                int *flag)
+__device__ __forceinline__ void edge_force(const T *g, int Np, int a, int b, double nx, double ny, double &fx,
+                                           double &fy)
 {
-    double fx = 0.0, fy = 0.0;
-    for (int e = threadIdx.x; e < n_edges; e += blockDim.x) {
-        double p = 0, pxx = 0, pxy = 0, pyy = 0;
-        for (int s = 0; s < 2; s++) {
-            int k = s ? web[e] : wea[e];
-            T d[9], q[12];
+    double p = 0, pxx = 0, pxy = 0, pyy = 0;
+    for (int s = 0; s < 2; s++) {
+        int k = s ? b : a;
+        T d[9], q[12];
 #pragma unroll
-            for (int i = 0; i < 9; i++) d[i] = g[size_t(i) * Np + k];
-            to_q(d, q);
-            p += 0.5 * double(q[0]) / 3.0;
+        for (int i = 0; i < 9; i++) d[i] = g[size_t(i) * Np + k];
+        to_q(d, q);
+        p += 0.5 * double(q[0]) / 3.0;
 #pragma unroll
-            for (int i = 0; i < 9; i++) {
-                double nq = double(q[3 + i]);
-                pxx += 0.5 * cx(i) * cx(i) * nq;
-                pxy += 0.5 * cx(i) * cy(i) * nq;
-                pyy += 0.5 * cy(i) * cy(i) * nq;
-            }
+        for (int i = 0; i < 9; i++) {
+            double nq = double(q[3 + i]);
+            pxx += 0.5 * cx(i) * cx(i) * nq;
+            pxy += 0.5 * cx(i) * cy(i) * nq;
+            pyy += 0.5 * cy(i) * cy(i) * nq;
         }
-        double nx = wn[2 * e], ny = wn[2 * e + 1];
-        double pm = p - 1.0 / 3.0;
-        fx += -pm * nx - (pxx * nx + pxy * ny);
-        fy += -pm * ny - (pxy * nx + pyy * ny);
     }
+    double pm = p - 1.0 / 3.0;
+    fx = -pm * nx - (pxx * nx + pxy * ny);
+    fy = -pm * ny - (pxy * nx + pyy * ny);
+}
+
+__device__ __forceinline__ void block_sum2(double &fx, double &fy)
+{
     __shared__ double sx[32], sy[32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -449,7 +484,7 @@ __global__ void __launch_bounds__(512) k_forces(const T *g, int Np, const int *w
     if (lane == 0) { sx[warp] = fx; sy[warp] = fy; }
     __syncthreads();
     if (warp == 0) {
-        int nw = blockDim.x >> 5;
+        int nw = (blockDim.x + 31) >> 5;
         fx = lane < nw ? sx[lane] : 0.0;
         fy = lane < nw ? sy[lane] : 0.0;
 #pragma unroll
@@ -457,13 +492,38 @@ __global__ void __launch_bounds__(512) k_forces(const T *g, int Np, const int *w
             fx += __shfl_down_sync(0xffffffffu, fx, o);
             fy += __shfl_down_sync(0xffffffffu, fy, o);
         }
-        if (lane == 0) {
-            int c = *counter;
-            buf[2 * (c % cap)] = fx / qdyn;
-            buf[2 * (c % cap) + 1] = fy / qdyn;
-            *counter = c + 1;
-            if (!(fx == fx) || !(fy == fy)) *flag = 1;
-        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kForceThreads) k_forces_partial(const T *g, int Np, const int *wea, const int *web,
+                                                                  const double *wn, int n_edges, double *partial)
+{
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    double fx = 0.0, fy = 0.0;
+    if (e < n_edges) edge_force(g, Np, wea[e], web[e], wn[2 * e], wn[2 * e + 1], fx, fy);
+    block_sum2(fx, fy);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = fx;
+        partial[2 * blockIdx.x + 1] = fy;
+    }
+}
+
+__global__ void __launch_bounds__(kForceThreads) k_forces_final(const double *partial, int n_part, double qdyn,
+                                                                double *buf, int *counter, int cap, int *flag)
+{
+    double fx = 0.0, fy = 0.0;
+    for (int b = threadIdx.x; b < n_part; b += blockDim.x) {
+        fx += partial[2 * b];
+        fy += partial[2 * b + 1];
+    }
+    block_sum2(fx, fy);
+    if (threadIdx.x == 0) {
+        int c = *counter;
+        buf[2 * (c % cap)] = fx / qdyn;
+        buf[2 * (c % cap) + 1] = fy / qdyn;
+        *counter = c + 1;
+        if (!(fx == fx) || !(fy == fy)) *flag = 1;
     }
 }
 
@@ -591,10 +651,10 @@ template <typename T> void launch_ring_interp(const DevCtx &C, bool q1_and_star,
     T *g = (T *)m.g[m.gcur];
     int star = q1_and_star ? 1 : 0;
     if (l.parity == 0)
-        k_ring_interp<T, 0><<<cdiv(m.n_ring, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, m.ring_don, (const T *)m.ring_w,
+        k_ring_interp<T, 0><<<cdiv(16L * m.n_ring, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, m.ring_don, (const T *)m.ring_w,
                                                                  m.n_ring, Q, (const T *)m.Q0, g, m.Np, m.ring_start, scale5, star);
     else
-        k_ring_interp<T, 1><<<cdiv(m.n_ring, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, m.ring_don, (const T *)m.ring_w,
+        k_ring_interp<T, 1><<<cdiv(16L * m.n_ring, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, m.ring_don, (const T *)m.ring_w,
                                                                  m.n_ring, Q, (const T *)m.Q0, g, m.Np, m.ring_start, scale5, star);
 }
 
@@ -605,10 +665,10 @@ template <typename T> void launch_hole_interp(const DevCtx &C, cudaStream_t s)
     if (m.n_is == 0) return;
     T scale4 = T(2.0 * (l.tau - 1.0) / (2.0 * l.tau - 1.0));
     if (l.parity == 0)
-        k_hole_interp<T, 0><<<cdiv(m.n_is, 128), 128, 0, s>>>((T *)l.f, l.pitch, l.stride, m.is_n, m.is_don, (const T *)m.is_w,
+        k_hole_interp<T, 0><<<cdiv(8L * m.n_is, 128), 128, 0, s>>>((T *)l.f, l.pitch, l.stride, m.is_n, m.is_don, (const T *)m.is_w,
                                                                m.n_is, (const T *)m.g[m.gcur], m.Np, scale4);
     else
-        k_hole_interp<T, 1><<<cdiv(m.n_is, 128), 128, 0, s>>>((T *)l.f, l.pitch, l.stride, m.is_n, m.is_don, (const T *)m.is_w,
+        k_hole_interp<T, 1><<<cdiv(8L * m.n_is, 128), 128, 0, s>>>((T *)l.f, l.pitch, l.stride, m.is_n, m.is_don, (const T *)m.is_w,
                                                                m.n_is, (const T *)m.g[m.gcur], m.Np, scale4);
 }
 
@@ -620,7 +680,7 @@ template <typename T> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
     T scale5 = T(1.0 - 1.0 / (2.0 * l.tau));
     int star = msub < C.n_sub - 1 ? 1 : 0;
     T theta_next = T(double(msub + 1) / double(C.n_sub));
-    k_fv<T><<<cdiv(m.n, 128), 128, 0, s>>>((const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n, m.slice_ptr, m.slice_len,
+    k_fv<T><<<m.n_slices, kFvThreads, 0, s>>>((const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n, m.slice_ptr, m.slice_len,
                                             (const typename Ent<T>::type *)m.ent, dt, dt_tau, m.n_wall, m.ring_start,
                                             m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5, star);
 }
@@ -628,8 +688,11 @@ template <typename T> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
 template <typename T> void launch_forces(const DevCtx &C, cudaStream_t s)
 {
     const DevMesh &m = C.m;
-    k_forces<T><<<1, 512, 0, s>>>((const T *)m.g[m.gcur], m.Np, m.wea, m.web, m.wn, m.n_edges, C.qdyn, C.force_buf,
-                                   C.force_counter, C.force_cap, C.flag);
+    int nb = std::max(1, int(cdiv(m.n_edges, kForceThreads)));
+    k_forces_partial<T><<<nb, kForceThreads, 0, s>>>((const T *)m.g[m.gcur], m.Np, m.wea, m.web, m.wn, m.n_edges,
+                                                     C.force_partial);
+    k_forces_final<<<1, kForceThreads, 0, s>>>(C.force_partial, nb, C.qdyn, C.force_buf, C.force_counter,
+                                               C.force_cap, C.flag);
 }
 
 template <typename T>

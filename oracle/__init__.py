@@ -75,6 +75,7 @@ def lib(openmp=False):
             L.orc_fv_substep.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
             L.orc_wall_rule.argtypes = [_dp]
             L.orc_eq4_post.argtypes = [_dp, C.c_double, _dp]
+            L.orc_feq_diff.argtypes = [C.c_double] * 6 + [_dp]
             L.orc_eq5_base.argtypes = [_dp, C.c_double, _dp]
             L.orc_quad6_weights.argtypes = [_dp, C.c_double, C.c_double, _dp]
             L.orc_biquad9_weights.argtypes = [C.c_double, C.c_double, _dp]
@@ -161,6 +162,13 @@ def wall_rule(g):
     g = _d(g).copy()
     lib().orc_wall_rule(_pd(g))
     return g
+
+
+def feq_diff(ra, uax, uay, rb, ubx, uby):
+    """f^eq(rho_a, u_a) - f^eq(rho_b, u_b) through moment differences."""
+    out = np.empty(9)
+    lib().orc_feq_diff(ra, uax, uay, rb, ubx, uby, _pd(out))
+    return out
 
 
 def eq4_post(q, tau_s):

@@ -82,6 +82,24 @@ static void from_q(const double *q, double scale, double *f)
     for (int i = 0; i < 9; i++) f[i] = eq[i] + scale * q[3 + i];
 }
 
+/* f^eq_i(rho_a, u_a) - f^eq_i(rho_b, u_b) written through the differences of
+ * the moments (Eq. 2):  w_i [ (rho_a - rho_b) E_i(u_b) + rho_a (E_i(u_a) - E_i(u_b)) ]
+ * with E_i(u) = 1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u and
+ * E_i(u_a) - E_i(u_b) = 3 c.du + 9/2 (c.du)(c.(u_a + u_b)) - 3/2 du.(u_a + u_b),
+ * du = u_a - u_b; no large terms cancel. */
+void orc_feq_diff(double ra, double uax, double uay, double rb, double ubx, double uby, double *out)
+{
+    double dux = uax - ubx, duy = uay - uby, sux = uax + ubx, suy = uay + uby;
+    double ub2 = ubx * ubx + uby * uby, dus = dux * sux + duy * suy;
+    for (int i = 0; i < 9; i++) {
+        double cub = CX[i] * ubx + CY[i] * uby;
+        double cdu = CX[i] * dux + CY[i] * duy, csu = CX[i] * sux + CY[i] * suy;
+        double eb = 1.0 + 3.0 * cub + 4.5 * cub * cub - 1.5 * ub2;
+        double de = 3.0 * cdu + 4.5 * cdu * csu - 1.5 * dus;
+        out[i] = WQ[i] * ((ra - rb) * eb + ra * de);
+    }
+}
+
 /* Eq. 4: post-collision state of a structured interpolation node from
  * interpolated unstructured data q = (rho, u, f^neq,u):
  * f~s = f^eq + 2 (tau_s - 1) / (2 tau_s - 1) f^neq,u  (unit structured step). */
@@ -91,11 +109,20 @@ void orc_eq4_post(const double *q, double tau_s, double *f)
 }
 
 /* Eq. 5-6: the structured part of the state of an unstructured interpolation
- * node from interpolated lattice data q = (rho, u, f^neq,s):
- * f^eq,s + (1 - 1/(2 tau_s)) f^neq,s. */
+ * node from interpolated lattice data q = (rho, u, f^neq,s): the same rho and
+ * u with f^neq,u = (1 - 1/(2 tau_s)) f^neq,s (mesh state kept as (rho, u, f^neq)). */
+static void eq5_q(const double *q, double tau_s, double *qu)
+{
+    qu[0] = q[0]; qu[1] = q[1]; qu[2] = q[2];
+    for (int i = 0; i < 9; i++) qu[3 + i] = (1.0 - 1.0 / (2.0 * tau_s)) * q[3 + i];
+}
+
+/* The same as populations: f^eq,s + (1 - 1/(2 tau_s)) f^neq,s. */
 void orc_eq5_base(const double *q, double tau_s, double *g)
 {
-    from_q(q, 1.0 - 1.0 / (2.0 * tau_s), g);
+    double qu[12];
+    eq5_q(q, tau_s, qu);
+    from_q(qu, 1.0, g);
 }
 
 /* Eq. 1 collision (right-hand side), unit time step on the grid's own clock:
@@ -336,33 +363,64 @@ done:
 }
 
 /* Eq. 3, one explicit sub-step on every node (no wall or interface rule):
- * g'_i(P) = g_i(P) + dt sum_k S_ik g_i(P_k) - (dt/tau_u) sum_k C_Pk [g_i - g_i^eq](P_k).
- * The control volume is closed, so sum_k S_ik = 0 and the streaming sum equals
- * sum_k S_ik [g_i(P_k) - g_i(P)]; it is evaluated in that form, which avoids
- * cancelling terms of size |S| g against a result of size |S| h |grad g|. */
+ * g'_i(P) = g_i(P) + dt sum_k S_ik g_i(P_k) - (dt/tau_u) sum_k C_Pk g^neq_i(P_k).
+ * The mesh state is kept per node as q = (rho, ux, uy, g^neq_0..8), the
+ * decomposition g = f^eq(rho, u) + g^neq of Eq. 4-7, so that g^neq is held
+ * directly rather than recovered by cancelling two O(w_i) numbers.  The
+ * control volume is closed (sum_k S_ik = 0), so the streaming sum is taken as
+ * sum_k S_ik [g_i(P_k) - g_i(P)] with g(P_k) - g(P) = [f^eq(P_k) - f^eq(P)]
+ * + [g^neq(P_k) - g^neq(P)] (orc_feq_diff).  The new state follows from
+ * g' = g + acc: rho' = rho + sum acc, u' from the momentum, and
+ * g^neq' = g^neq + acc - [f^eq(rho', u') - f^eq(rho, u)]. */
+static void fv_substep_q(int n, const int *rowptr, const int *col, const double *sx, const double *sy,
+                         const double *cc, double dt, double tau_u, const double *q, double *qn)
+{
+    for (int p = 0; p < n; p++) {
+        const double *qp = q + 12 * (size_t)p;
+        double acc[9] = {0};
+        for (int e = rowptr[p]; e < rowptr[p + 1]; e++) {
+            const double *qk = q + 12 * (size_t)col[e];
+            double dfe[9];
+            orc_feq_diff(qk[0], qk[1], qk[2], qp[0], qp[1], qp[2], dfe);
+            for (int i = 0; i < 9; i++) {
+                double s = CX[i] * sx[e] + CY[i] * sy[e];
+                acc[i] += dt * s * (dfe[i] + qk[3 + i] - qp[3 + i]) - (dt / tau_u) * cc[e] * qk[3 + i];
+            }
+        }
+        double drho = 0.0, djx = 0.0, djy = 0.0;
+        for (int i = 0; i < 9; i++) {
+            drho += acc[i];
+            djx += CX[i] * acc[i];
+            djy += CY[i] * acc[i];
+        }
+        double *qo = qn + 12 * (size_t)p;
+        double rho = qp[0] + drho;
+        qo[0] = rho;
+        qo[1] = qp[1] + (djx - drho * qp[1]) / rho;
+        qo[2] = qp[2] + (djy - drho * qp[2]) / rho;
+        double dfe[9];
+        orc_feq_diff(qo[0], qo[1], qo[2], qp[0], qp[1], qp[2], dfe);
+        for (int i = 0; i < 9; i++) qo[3 + i] = qp[3 + i] + acc[i] - dfe[i];
+    }
+}
+
+/* Eq. 3 on populations g[n][9] (converted to and from the (rho, u, g^neq)
+ * state around fv_substep_q). */
 void orc_fv_substep(int n, const int *rowptr, const int *col, const double *sx, const double *sy,
                     const double *cc, double dt, double tau_u, const double *g, double *gnew)
 {
-    for (int p = 0; p < n; p++) {
-        double acc[9] = {0};
-        const double *gp = g + 9 * (size_t)p;
-        for (int e = rowptr[p]; e < rowptr[p + 1]; e++) {
-            const double *gk = g + 9 * (size_t)col[e];
-            double rho, ux, uy, eq[9];
-            orc_moments(gk, &rho, &ux, &uy);
-            orc_feq(rho, ux, uy, eq);
-            for (int i = 0; i < 9; i++) {
-                double s = CX[i] * sx[e] + CY[i] * sy[e];
-                acc[i] += dt * s * (gk[i] - gp[i]) - (dt / tau_u) * cc[e] * (gk[i] - eq[i]);
-            }
-        }
-        for (int i = 0; i < 9; i++) gnew[9 * (size_t)p + i] = g[9 * (size_t)p + i] + acc[i];
-    }
+    double *q = calloc((size_t)n * 12 + 1, sizeof(double)), *qn = calloc((size_t)n * 12 + 1, sizeof(double));
+    for (int p = 0; p < n; p++) state_q(g + 9 * (size_t)p, q + 12 * (size_t)p);
+    fv_substep_q(n, rowptr, col, sx, sy, cc, dt, tau_u, q, qn);
+    for (int p = 0; p < n; p++) from_q(qn + 12 * (size_t)p, 1.0, gnew + 9 * (size_t)p);
+    free(q);
+    free(qn);
 }
 
 /* Wall rule (the paper states only "no-slip"; reading): keep the density and
  * the non-equilibrium part of the wall node, set its velocity to zero:
- * g <- f^eq(rho, 0) + (g - f^eq(rho, u)). */
+ * g <- f^eq(rho, 0) + (g - f^eq(rho, u)).  In the (rho, u, g^neq) state of
+ * the solver this is u <- 0. */
 void orc_wall_rule(double *g)
 {
     double rho, ux, uy, eq[9], eq0[9];
@@ -441,16 +499,15 @@ void orc_biquad9_weights(double fx, double fy, double *w)
  * nu = c_s^2 tau_u, with no half-step shift); n points from the body into the
  * fluid; the edge value is the mean of its two end nodes; edges are straight.
  * Wall edge e runs a -> b with the fluid on its left. */
-void orc_wall_force(int n_edges, const int *ea, const int *eb, const double *xy, const double *g,
-                    double *F)
+static void wall_force_q(int n_edges, const int *ea, const int *eb, const double *xy, const double *qs,
+                         double *F)
 {
     double fx = 0.0, fy = 0.0;
     for (int e = 0; e < n_edges; e++) {
         int nodes[2] = {ea[e], eb[e]};
         double p[2], pxx[2], pxy[2], pyy[2];
         for (int s = 0; s < 2; s++) {
-            double q[12];
-            state_q(g + 9 * (size_t)nodes[s], q);
+            const double *q = qs + 12 * (size_t)nodes[s];
             p[s] = q[0] / 3.0;
             pxx[s] = pxy[s] = pyy[s] = 0.0;
             for (int i = 0; i < 9; i++) {
@@ -468,6 +525,20 @@ void orc_wall_force(int n_edges, const int *ea, const int *eb, const double *xy,
     }
     F[0] = fx;
     F[1] = fy;
+}
+
+/* The same from populations g[n][9]. */
+void orc_wall_force(int n_edges, const int *ea, const int *eb, const double *xy, const double *g, double *F)
+{
+    int n = 0;
+    for (int e = 0; e < n_edges; e++) {
+        if (ea[e] + 1 > n) n = ea[e] + 1;
+        if (eb[e] + 1 > n) n = eb[e] + 1;
+    }
+    double *q = malloc(((size_t)n + 1) * 12 * sizeof(double));
+    for (int p = 0; p < n; p++) state_q(g + 9 * (size_t)p, q + 12 * (size_t)p);
+    wall_force_q(n_edges, ea, eb, xy, q, F);
+    free(q);
 }
 
 /* ============================================================ the solver == */
@@ -623,20 +694,19 @@ static void ring_set(orc *o, double theta)
         double q[12];
         for (int m = 0; m < 12; m++)
             q[m] = (1.0 - theta) * o->Q0[12 * (size_t)r + m] + theta * o->Q1[12 * (size_t)r + m];
-        orc_eq5_base(q, tau_s, o->g + 9 * (size_t)o->ring[r]);
+        eq5_q(q, tau_s, o->g + 12 * (size_t)o->ring[r]);
     }
 }
 
 /* Eq. 4 with Eq. 8: post-collision state of the structured interpolation
- * nodes, from the unstructured state at time t. */
+ * nodes, from the unstructured state (rho, u, g^neq) at time t. */
 static void hole_interp(orc *o)
 {
     olevel *l = &o->lv[o->L - 1];
     for (int s = 0; s < o->n_is; s++) {
         double q[12] = {0};
         for (int k = 0; k < 6; k++) {
-            double qk[12];
-            state_q(o->g + 9 * (size_t)o->is_don[6 * s + k], qk);
+            const double *qk = o->g + 12 * (size_t)o->is_don[6 * s + k];
             for (int m = 0; m < 12; m++) q[m] += o->is_w[6 * s + k] * qk[m];
         }
         orc_eq4_post(q, l->tau, l->post + 9 * (size_t)o->is_node[s]);
@@ -669,8 +739,11 @@ static void fv_steps(orc *o)
 {
     for (int m = 0; m < o->n_sub; m++) {
         ring_set(o, (double)m / o->n_sub);
-        orc_fv_substep(o->n, o->rowptr, o->col, o->sx, o->sy, o->cc, o->dt_u, o->tau_u, o->g, o->gnew);
-        for (int w = 0; w < o->n_wall; w++) orc_wall_rule(o->gnew + 9 * (size_t)o->wall[w]);
+        fv_substep_q(o->n, o->rowptr, o->col, o->sx, o->sy, o->cc, o->dt_u, o->tau_u, o->g, o->gnew);
+        for (int w = 0; w < o->n_wall; w++) {  /* wall rule: u <- 0, rho and g^neq kept */
+            o->gnew[12 * (size_t)o->wall[w] + 1] = 0.0;
+            o->gnew[12 * (size_t)o->wall[w] + 2] = 0.0;
+        }
         double *t = o->g; o->g = o->gnew; o->gnew = t;
     }
 }
@@ -706,7 +779,7 @@ static void record_forces(orc *o)
 {
     if (!o->n) return;
     double F[2];
-    orc_wall_force(o->n_wedge, o->wea, o->web, o->xy, o->g, F);
+    wall_force_q(o->n_wedge, o->wea, o->web, o->xy, o->g, F);
     double qdyn = 0.5 * o->u0 * o->u0 * o->chord;
     if (o->nf == o->fcap) {
         o->fcap = o->fcap ? 2 * o->fcap : 1024;
@@ -840,8 +913,8 @@ orc *orc_create(int L, const int *levels, int n, const double *xy, int ntri, con
         if (o->nnz < 0) { set_err(err, errlen, "degenerate or inverted triangle"); orc_destroy(o); return NULL; }
         o->n_sub = n_sub > 0 ? n_sub : auto_n_sub(o);
         o->dt_u = 1.0 / o->n_sub;
-        o->g = malloc((size_t)n * 9 * sizeof(double));
-        o->gnew = malloc((size_t)n * 9 * sizeof(double));
+        o->g = malloc((size_t)n * 12 * sizeof(double));     /* (rho, u, g^neq) per node */
+        o->gnew = malloc((size_t)n * 12 * sizeof(double));
         /* node lists */
         o->ring = malloc((size_t)n * sizeof(int));
         o->wall = malloc((size_t)n * sizeof(int));
@@ -965,7 +1038,11 @@ orc *orc_create(int L, const int *levels, int n, const double *xy, int ntri, con
     }
     for (int p = 0; p < n; p++) {
         double rho = 1.0 + perturb * orc_uniform(seed, 63, (uint64_t)p);
-        orc_feq(rho, kind[p] == 1 ? 0.0 : o->u0, 0.0, o->g + 9 * (size_t)p);
+        double *q = o->g + 12 * (size_t)p;
+        q[0] = rho;
+        q[1] = kind[p] == 1 ? 0.0 : o->u0;
+        q[2] = 0.0;
+        for (int i = 0; i < 9; i++) q[3 + i] = 0.0;
     }
     /* make the initial state consistent across the interfaces */
     if (!o->periodic0) apply_outer_bc(o);
@@ -1000,7 +1077,11 @@ void orc_forces(const orc *o, double *cd, double *cl)
 int orc_fields(const orc *o, int grid, double *rho, double *ux, double *uy)
 {
     if (grid == -1) {
-        for (int p = 0; p < o->n; p++) orc_moments(o->g + 9 * (size_t)p, &rho[p], &ux[p], &uy[p]);
+        for (int p = 0; p < o->n; p++) {
+            rho[p] = o->g[12 * (size_t)p];
+            ux[p] = o->g[12 * (size_t)p + 1];
+            uy[p] = o->g[12 * (size_t)p + 2];
+        }
         return o->n;
     }
     if (grid < 0 || grid >= o->L) return -1;
@@ -1016,7 +1097,10 @@ int orc_fields(const orc *o, int grid, double *rho, double *ux, double *uy)
 /* Raw populations of a grid (-1: mesh) into out (node-major, 9 per node). */
 int orc_populations(const orc *o, int grid, double *out)
 {
-    if (grid == -1) { memcpy(out, o->g, (size_t)o->n * 9 * sizeof(double)); return o->n; }
+    if (grid == -1) {
+        for (int p = 0; p < o->n; p++) from_q(o->g + 12 * (size_t)p, 1.0, out + 9 * (size_t)p);
+        return o->n;
+    }
     const olevel *l = &o->lv[grid];
     size_t nn = (size_t)l->nx * l->ny;
     memcpy(out, l->f, nn * 9 * sizeof(double));
@@ -1027,7 +1111,10 @@ int orc_populations(const orc *o, int grid, double *out)
  * (test hook for initial conditions other than the uniform stream). */
 int orc_set_populations(orc *o, int grid, const double *f)
 {
-    if (grid == -1) { memcpy(o->g, f, (size_t)o->n * 9 * sizeof(double)); return o->n; }
+    if (grid == -1) {
+        for (int p = 0; p < o->n; p++) state_q(f + 9 * (size_t)p, o->g + 12 * (size_t)p);
+        return o->n;
+    }
     if (grid < 0 || grid >= o->L) return -1;
     olevel *l = &o->lv[grid];
     size_t nn = (size_t)l->nx * l->ny;

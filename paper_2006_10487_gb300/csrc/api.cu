@@ -162,18 +162,13 @@ template <typename T> void init_state(hlbm_ctx *c)
     }
     for (int l = D.L - 2; l >= 0; l--) launch_restrict<T>(D, l, s);
     if (D.m.n > 0) {
-        // mesh: f^eq(1 + perturb xi, u) with u = 0 on wall nodes, device order
+        // mesh: rho = 1 + perturb xi, u = (u0, 0) (0 on wall nodes), f^neq = 0;
+        // planes (rho - 1, ux, uy, f^neq_3..8), device order
         std::vector<T> g(size_t(9) * D.m.Np, T(0));
         for (int p = 0; p < P.n; p++) {
-            double rho = 1.0 + P.perturb * init_deviate(P.seed, kMeshGrid, uint64_t(p));
-            double ux = P.kind[p] == HLBM_NODE_WALL ? 0.0 : P.u0;
             int q = P.inv[p];
-            for (int i = 0; i < 9; i++) {
-                static const int CXh[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-                static const double Wh[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-                double cu = CXh[i] * ux;
-                g[size_t(i) * D.m.Np + q] = T(Wh[i] * ((rho - 1.0) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * ux * ux)));
-            }
+            g[q] = T(P.perturb * init_deviate(P.seed, kMeshGrid, uint64_t(p)));
+            g[size_t(D.m.Np) + q] = T(P.kind[p] == HLBM_NODE_WALL ? 0.0 : P.u0);
         }
         ck(cudaMemcpyAsync(D.m.g[0], g.data(), g.size() * sizeof(T), cudaMemcpyHostToDevice, s), "upload mesh state");
         ck(cudaStreamSynchronize(s), "sync");  // g (host) goes out of scope

@@ -28,7 +28,7 @@ struct DevLevel {
 // The triangular mesh in device order (wall nodes, fluid nodes, ring nodes).
 struct DevMesh {
     int n = 0, Np = 0, n_wall = 0, ring_start = 0, n_ring = 0;
-    void *g[2] = {nullptr, nullptr};  // [9][Np] deviations, double-buffered
+    void *g[2] = {nullptr, nullptr};  // [9][Np] (rho - 1, ux, uy, f^neq_3..8), double-buffered
     int gcur = 0;
     // Eq. 3 operators, sliced ELL with 32-row slices: entry e of row r sits at
     // slice_ptr[r / 32] + 32 e + r % 32, as (s_x, s_y, C, column)

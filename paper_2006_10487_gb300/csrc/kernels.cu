@@ -73,6 +73,54 @@ template <typename T> __device__ __forceinline__ void from_q(const T q[12], T sc
     for (int i = 0; i < 9; i++) d[i] = deq<T>(i, q[0], q[1], q[2]) + scale * q[3 + i];
 }
 
+// Mesh state, plane-major g[9][Np]: plane 0 = rho - 1, planes 1-2 = u,
+// planes 3-8 = f^neq_3..8.  f^neq_0..2 follow from the zero mass and momentum
+// of the non-equilibrium part:
+//   f^neq_1 = f^neq_3 - f^neq_5 + f^neq_6 + f^neq_7 - f^neq_8
+//   f^neq_2 = f^neq_4 - f^neq_5 - f^neq_6 + f^neq_7 + f^neq_8
+//   f^neq_0 = -(f^neq_1 + ... + f^neq_8)
+template <typename T> __device__ __forceinline__ void neq_complete(T nq[9])
+{
+    nq[1] = nq[3] - nq[5] + nq[6] + nq[7] - nq[8];
+    nq[2] = nq[4] - nq[5] - nq[6] + nq[7] + nq[8];
+    nq[0] = -(nq[1] + nq[2] + nq[3] + nq[4] + nq[5] + nq[6] + nq[7] + nq[8]);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_mesh(const T *__restrict__ g, int Np, int k, T &r1, T &ux, T &uy, T nq[9])
+{
+    r1 = g[k];
+    ux = g[size_t(Np) + k];
+    uy = g[size_t(2) * Np + k];
+#pragma unroll
+    for (int i = 3; i < 9; i++) nq[i] = g[size_t(i) * Np + k];
+    neq_complete(nq);
+}
+
+// q = (rho, ux, uy, f^neq_0..8) of a mesh node
+template <typename T> __device__ __forceinline__ void mesh_q(const T *__restrict__ g, int Np, int k, T q[12])
+{
+    T r1;
+    load_mesh(g, Np, k, r1, q[1], q[2], q + 3);
+    q[0] = T(1) + r1;
+}
+
+// E_i(u) = 1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u  (f^eq_i = w_i rho E_i(u))
+template <typename T> __device__ __forceinline__ T Efun(int i, T ux, T uy)
+{
+    T cu = T(cx(i)) * ux + T(cy(i)) * uy;
+    return T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * (ux * ux + uy * uy);
+}
+
+// f^eq_i(rho_b + drho, u_b + du) - f^eq_i(rho_b, u_b) through moment differences:
+//   w_i [drho E_i(u_b) + rho_a (3 c.du + 9/2 (c.du)(c.(u_a + u_b)) - 3/2 du.(u_a + u_b))]
+template <typename T>
+__device__ __forceinline__ T feq_diff(int i, T Eb, T drho, T rho_a, T dux, T duy, T sux, T suy)
+{
+    T cdu = T(cx(i)) * dux + T(cy(i)) * duy, csu = T(cx(i)) * sux + T(cy(i)) * suy;
+    return wq<T>(i) * (drho * Eb + rho_a * (T(3) * cdu + T(4.5) * cdu * csu - T(1.5) * (dux * sux + duy * suy)));
+}
+
 // AA-pattern addressing.  State of node n at parity p:
 //   p = 0: plane i at n;  p = 1: plane opp(i) at n - c_i.
 // A collision at parity p writes its post-collision value c_i-bound to
@@ -276,7 +324,7 @@ __global__ void k_restrict(T *fc, int pitch_c, size_t stride_c, const T *ff, int
 // Eq. 9: (rho, u, f^neq) at the unstructured interpolation nodes from their
 // 3x3 lattice donors.  With star != 0 (after the lattice step) the kernel also
 // sets the ring nodes of the read buffer to the Eq. 5-6 state at theta = 0:
-// f^eq + (1 - 1/(2 tau_s)) f^neq of the data at t (Q0).
+// (rho, u, (1 - 1/(2 tau_s)) f^neq) of the data at t (Q0).
 // 16 lanes per ring node: lane k < 9 takes donor k; xor-shuffle sum.
 template <typename T, int P>
 __global__ void k_ring_interp(const T *f, int pitch, size_t stride, const int *don, const T *w, int n_ring,
@@ -306,9 +354,10 @@ __global__ void k_ring_interp(const T *f, int pitch, size_t stride, const int *d
     for (int m = 0; m < 12; m++)
         if (m == k) Q[size_t(m) * n_ring + r] = acc[m];
     if (star && k < 9) {
-        T rho = Q0[r], ux = Q0[size_t(n_ring) + r], uy = Q0[size_t(2) * n_ring + r];
-        T nk = Q0[size_t(3 + k) * n_ring + r];
-        g[size_t(k) * Np + ring_start + r] = deq<T>(k, rho, ux, uy) + scale5 * nk;
+        // mesh state (rho - 1, u, (1 - 1/(2 tau_s)) f^neq) of the data at t
+        // mesh plane k: rho - 1, ux, uy (q[0..2]) or f^neq_k (q[3 + k])
+        T v = Q0[size_t(k < 3 ? k : 3 + k) * n_ring + r];
+        g[size_t(k) * Np + ring_start + r] = k == 0 ? v - T(1) : (k < 3 ? v : scale5 * v);
     }
 }
 
@@ -328,10 +377,8 @@ __global__ void k_hole_interp(T *f, int pitch, size_t stride, const int *is_n, c
     for (int m = 0; m < 12; m++) acc[m] = T(0);
     if (k < 6) {
         int p = don[6 * ss + k];
-        T d[9], q[12];
-#pragma unroll
-        for (int i = 0; i < 9; i++) d[i] = g[size_t(i) * Np + p];
-        to_q(d, q);
+        T q[12];
+        mesh_q(g, Np, p, q);
         T wk = w[6 * ss + k];
 #pragma unroll
         for (int m = 0; m < 12; m++) acc[m] = wk * q[m];
@@ -362,18 +409,17 @@ __device__ __forceinline__ void unpack(const double4_32a &e, double &sx, double 
 }
 
 // Eq. 3, one explicit sub-step on every mesh node (node-major gather over the
-// sliced-ELL operator rows, no atomics):
-//   g'_i(P) = g_i(P) + dt sum_k (c_i . s_Pk) (g_i(P_k) - g_i(P)) - dt/tau_u sum_k C_Pk g^neq_i(P_k)
-// (sum_k s_Pk = 0, so the streaming sum is taken against the node's own value)
-// then, on wall rows, the no-slip rule (rho and f^neq kept, u = 0); on ring
-// rows, unless this is the last sub-step, the Eq. 5-6 state of the next
-// sub-step (theta_next) replaces the result.
-//
-// Work split: a block of 128 threads is one 32-row slice; each row is served
-// by 4 adjacent lanes, lane q taking entries q, q + 4, ... so the gathers of
-// all neighbours are in flight together; the four partial sums are combined
-// with two xor shuffles and lane q stores populations q, q + 4 (and 8 for q = 0).
+// sliced-ELL operator rows, no atomics), on the (rho, u, f^neq) state:
+//   acc_i = dt sum_k (c_i . s_Pk) (g_i(P_k) - g_i(P)) - dt/tau_u sum_k C_Pk f^neq_i(P_k)
+// with g(P_k) - g(P) = [f^eq(P_k) - f^eq(P)] + [f^neq(P_k) - f^neq(P)]
+// (sum_k s_Pk = 0); then rho' = rho + sum acc, u' from the momentum and
+// f^neq' = f^neq + acc - [f^eq(rho', u') - f^eq(rho, u)].  Wall rows take
+// u' = 0 (no-slip: rho and f^neq kept); ring rows, unless this is the last
+// sub-step, take the Eq. 5-6 state of the next sub-step (theta_next).
+// One thread per row; neighbours are gathered four at a time so that all
+// their loads are in flight together.
 constexpr int kFvThreads = 128;
+constexpr int kFvGroup = 4;
 
 template <typename T>
 __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
@@ -384,59 +430,84 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
                                                    const T *__restrict__ Q0, const T *__restrict__ Q1, T theta_next,
                                                    T scale5, int star)
 {
-    const int sl = blockIdx.x;
-    const int row_local = threadIdx.x >> 2, q = threadIdx.x & 3;
-    const int r = sl * 32 + row_local;
-    const bool live = r < n;
-    const int rr = live ? r : n - 1;  // padding lanes shadow a valid row (results discarded)
-    const int base = slice_ptr[sl] + row_local, len = slice_len[sl];
-    T own[9], acc[9];
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int sl = r >> 5;
+    const int base = slice_ptr[sl] + (r & 31), len = slice_len[sl];
+    T r1P, uPx, uPy, nP[9];
+    load_mesh(g, Np, r, r1P, uPx, uPy, nP);
+    T EP[9], acc[9];
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        own[i] = g[size_t(i) * Np + rr];
+        EP[i] = Efun<T>(i, uPx, uPy);
         acc[i] = T(0);
     }
-    for (int e = q; e < len; e += 4) {
-        T sx, sy, c;
-        int k;
-        unpack(ent[base + 32 * e], sx, sy, c, k);
-        T d[9];
+    for (int e0 = 0; e0 < len; e0 += kFvGroup) {
+        T sx[kFvGroup], sy[kFvGroup], c[kFvGroup];
+        int k[kFvGroup];
 #pragma unroll
-        for (int i = 0; i < 9; i++) d[i] = g[size_t(i) * Np + k];
-        T rho, ux, uy;
-        moments(d, rho, ux, uy);
-        T cs = dt_tau * c;
+        for (int j = 0; j < kFvGroup; j++) {
+            if (e0 + j < len) {
+                unpack(ent[base + 32 * (e0 + j)], sx[j], sy[j], c[j], k[j]);
+            } else {
+                sx[j] = sy[j] = c[j] = T(0);
+                k[j] = r;
+            }
+        }
+        T st[kFvGroup][9];
 #pragma unroll
-        for (int i = 0; i < 9; i++) {
-            T sd = dt * (T(cx(i)) * sx + T(cy(i)) * sy);
-            acc[i] += sd * (d[i] - own[i]) - cs * (d[i] - deq<T>(i, rho, ux, uy));
+        for (int j = 0; j < kFvGroup; j++)
+#pragma unroll
+            for (int i = 0; i < 9; i++)
+                st[j][i] = g[size_t(i) * Np + k[j]];
+#pragma unroll
+        for (int j = 0; j < kFvGroup; j++) {
+            T nk[9];
+#pragma unroll
+            for (int i = 3; i < 9; i++) nk[i] = st[j][i];
+            neq_complete(nk);
+            T drho = st[j][0] - r1P, rhok = T(1) + st[j][0];
+            T dux = st[j][1] - uPx, duy = st[j][2] - uPy, sux = st[j][1] + uPx, suy = st[j][2] + uPy;
+            T cs = dt_tau * c[j];
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                T sd = dt * (T(cx(i)) * sx[j] + T(cy(i)) * sy[j]);
+                T dfe = feq_diff<T>(i, EP[i], drho, rhok, dux, duy, sux, suy);
+                acc[i] += sd * (dfe + nk[i] - nP[i]) - cs * nk[i];
+            }
         }
     }
+    T drho = 0, djx = 0, djy = 0;
 #pragma unroll
     for (int i = 0; i < 9; i++) {
-        acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 1);
-        acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 2);
+        drho += acc[i];
+        djx += T(cx(i)) * acc[i];
+        djy += T(cy(i)) * acc[i];
     }
-    if (!live) return;
-    T d[9];
+    T r1 = r1P + drho, rho = T(1) + r1;
+    T dux = (djx - drho * uPx) / rho, duy = (djy - drho * uPy) / rho;
+    T ux = uPx + dux, uy = uPy + duy;
+    T nq[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) d[i] = own[i] + acc[i];
+    for (int i = 0; i < 9; i++) nq[i] = nP[i] + acc[i] - feq_diff<T>(i, EP[i], drho, rho, dux, duy, ux + uPx, uy + uPy);
     if (r < n_wall) {
-        T rho, ux, uy;
-        moments(d, rho, ux, uy);
-#pragma unroll
-        for (int i = 0; i < 9; i++) d[i] = d[i] - deq<T>(i, rho, ux, uy) + deq<T>(i, rho, T(0), T(0));
+        ux = T(0);
+        uy = T(0);
     } else if (star && r >= ring_start) {
         int q_ = r - ring_start;
-        T qq[12];
+        T a = T(1) - theta_next;
+        r1 = a * Q0[q_] + theta_next * Q1[q_] - T(1);
+        ux = a * Q0[size_t(n_ring) + q_] + theta_next * Q1[size_t(n_ring) + q_];
+        uy = a * Q0[size_t(2) * n_ring + q_] + theta_next * Q1[size_t(2) * n_ring + q_];
 #pragma unroll
-        for (int m = 0; m < 12; m++)
-            qq[m] = (T(1) - theta_next) * Q0[size_t(m) * n_ring + q_] + theta_next * Q1[size_t(m) * n_ring + q_];
-        from_q(qq, scale5, d);
+        for (int i = 3; i < 9; i++)
+            nq[i] = scale5 * (a * Q0[size_t(3 + i) * n_ring + q_] + theta_next * Q1[size_t(3 + i) * n_ring + q_]);
     }
+    gn[r] = r1;
+    gn[size_t(Np) + r] = ux;
+    gn[size_t(2) * Np + r] = uy;
 #pragma unroll
-    for (int i = 0; i < 9; i++)
-        if ((i & 3) == q) gn[size_t(i) * Np + r] = d[i];
+    for (int i = 3; i < 9; i++) gn[size_t(i) * Np + r] = nq[i];
 }
 
 // Eq. 10-11: force on the body from nodal pressure and stress at the wall,
@@ -454,10 +525,8 @@ __device__ __forceinline__ void edge_force(const T *g, int Np, int a, int b, dou
     double p = 0, pxx = 0, pxy = 0, pyy = 0;
     for (int s = 0; s < 2; s++) {
         int k = s ? b : a;
-        T d[9], q[12];
-#pragma unroll
-        for (int i = 0; i < 9; i++) d[i] = g[size_t(i) * Np + k];
-        to_q(d, q);
+        T q[12];
+        mesh_q(g, Np, k, q);
         p += 0.5 * double(q[0]) / 3.0;
 #pragma unroll
         for (int i = 0; i < 9; i++) {
@@ -562,15 +631,14 @@ __global__ void k_fields_mesh(const T *g, int Np, const int *inv, int n, double 
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     int k = inv[p];
-    double dd[9];
-    for (int i = 0; i < 9; i++) dd[i] = double(g[size_t(i) * Np + k]);
+    T q[12];
+    mesh_q(g, Np, k, q);
     if (rho) {
-        double r, u, v;
-        moments(dd, r, u, v);
-        rho[p] = r; ux[p] = u; uy[p] = v;
+        rho[p] = double(q[0]); ux[p] = double(q[1]); uy[p] = double(q[2]);
     }
     if (pop)
-        for (int i = 0; i < 9; i++) pop[9 * size_t(p) + i] = dd[i] + wq<double>(i);
+        for (int i = 0; i < 9; i++)
+            pop[9 * size_t(p) + i] = wq<double>(i) + deq<double>(i, double(q[0]), double(q[1]), double(q[2])) + double(q[3 + i]);
 }
 
 inline unsigned cdiv(long a, long b) { return unsigned((a + b - 1) / b); }
@@ -680,7 +748,7 @@ template <typename T> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
     T scale5 = T(1.0 - 1.0 / (2.0 * l.tau));
     int star = msub < C.n_sub - 1 ? 1 : 0;
     T theta_next = T(double(msub + 1) / double(C.n_sub));
-    k_fv<T><<<m.n_slices, kFvThreads, 0, s>>>((const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n, m.slice_ptr, m.slice_len,
+    k_fv<T><<<cdiv(m.n, kFvThreads), kFvThreads, 0, s>>>((const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n, m.slice_ptr, m.slice_len,
                                             (const typename Ent<T>::type *)m.ent, dt, dt_tau, m.n_wall, m.ring_start,
                                             m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5, star);
 }

@@ -52,6 +52,29 @@ def test_collision_conserves_mass_and_momentum(orc):
         assert np.allclose(g - eq, (1 - 1 / tau) * (f - eq), rtol=0, atol=1e-16)
 
 
+def test_equilibrium_difference_matches_exact_arithmetic(orc):
+    """f^eq(a) - f^eq(b) through moment differences equals Eq. 2 evaluated twice
+    and subtracted in exact rational arithmetic, to the rounding of the result
+    (not of the O(w_i) equilibria)."""
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(11)
+    wq = [Fr(4, 9)] + [Fr(1, 9)] * 4 + [Fr(1, 36)] * 4
+    for scale in (1e-2, 1e-6, 1e-10):
+        for _ in range(5):
+            rb = 1 + 0.01 * rng.standard_normal()
+            ub = 0.05 * rng.standard_normal(2)
+            ra = rb + scale * rng.standard_normal()
+            ua = ub + scale * rng.standard_normal(2)
+            got = orc.feq_diff(ra, ua[0], ua[1], rb, ub[0], ub[1])
+            for i in range(9):
+                def E(r, u):
+                    r, ux, uy = Fr(r), Fr(u[0]), Fr(u[1])
+                    cu = CX[i] * ux + CY[i] * uy
+                    return wq[i] * r * (1 + 3 * cu + Fr(9, 2) * cu * cu - Fr(3, 2) * (ux * ux + uy * uy))
+                exact = float(E(ra, ua) - E(rb, ub))
+                assert got[i] == pytest.approx(exact, rel=1e-12, abs=1e-15 * scale)
+
+
 def test_moments(orc):
     rng = np.random.default_rng(3)
     f = W * (1 + 0.1 * rng.standard_normal(9))

@@ -73,6 +73,22 @@ static void state_q(const double *f, double *q)
     for (int i = 0; i < 9; i++) q[3 + i] = f[i] - eq[i];
 }
 
+/* f^neq has zero mass and momentum by definition (f^eq shares rho and rho u
+ * with f): sum_i f^neq_i = 0, sum_i c_i f^neq_i = 0.  Enforce it on a stored
+ * state q = (rho, u, f^neq) by solving the three relations for f^neq_0..2:
+ *   f^neq_1 = f^neq_3 - f^neq_5 + f^neq_6 + f^neq_7 - f^neq_8
+ *   f^neq_2 = f^neq_4 - f^neq_5 - f^neq_6 + f^neq_7 + f^neq_8
+ *   f^neq_0 = -(f^neq_1 + ... + f^neq_8)
+ * (otherwise rounding lets the constraints drift, and the collision term of
+ * Eq. 3 turns the drift into spurious mass and momentum sources). */
+static void neq_constrain(double *q)
+{
+    double *n = q + 3;
+    n[1] = n[3] - n[5] + n[6] + n[7] - n[8];
+    n[2] = n[4] - n[5] - n[6] + n[7] + n[8];
+    n[0] = -(n[1] + n[2] + n[3] + n[4] + n[5] + n[6] + n[7] + n[8]);
+}
+
 /* Population from (rho, u, f^neq) with the non-equilibrium part scaled:
  * f = f^eq(rho, u) + scale * f^neq. */
 static void from_q(const double *q, double scale, double *f)
@@ -115,6 +131,7 @@ static void eq5_q(const double *q, double tau_s, double *qu)
 {
     qu[0] = q[0]; qu[1] = q[1]; qu[2] = q[2];
     for (int i = 0; i < 9; i++) qu[3 + i] = (1.0 - 1.0 / (2.0 * tau_s)) * q[3 + i];
+    neq_constrain(qu);
 }
 
 /* The same as populations: f^eq,s + (1 - 1/(2 tau_s)) f^neq,s. */
@@ -401,6 +418,7 @@ static void fv_substep_q(int n, const int *rowptr, const int *col, const double 
         double dfe[9];
         orc_feq_diff(qo[0], qo[1], qo[2], qp[0], qp[1], qp[2], dfe);
         for (int i = 0; i < 9; i++) qo[3 + i] = qp[3 + i] + acc[i] - dfe[i];
+        neq_constrain(qo);
     }
 }
 

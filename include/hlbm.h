@@ -162,6 +162,27 @@ int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double 
                  double aoa_deg, const hlbm_options *opt, const char *table, double *out,
                  size_t cap, size_t *n);
 
+/* Drag and lift coefficients of one mesh state held by the caller, computed
+ * without allocating any device memory.  The paper has no counterpart: this
+ * is for callers that cannot call cudaMalloc (their device memory belongs to
+ * another framework's pool, or they evaluate forces inside loops that must not
+ * allocate); the force reduction's per-block partial sums live in a fixed
+ * file-scope device array instead.
+ * All pointers are device pointers: f [n_nodes][9] FP64 populations (D2Q9
+ * order of hlbm_populations), xy [n_nodes][2] node coordinates (finest-level
+ * units, the pose the forces refer to), edge_a/edge_b [n_edges] wall edges
+ * a -> b with the fluid on their left (indices in [0, n_nodes)), out [2]
+ * receives (C_D, C_L) = F / qdyn with qdyn = rho0 u0^2 C / 2 (Eq. 10-11).
+ * Runs asynchronously on `stream` (cudaStream_t, NULL = legacy default).
+ * Limits: n_edges <= 131072, else HLBM_EINVAL (message via
+ * hlbm_last_error(NULL)).  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) for that device, so make that first
+ * call before any stream capture.  Every call shares the array and it keeps
+ * the last call's partial sums; each call writes every slot it reads, but
+ * calls that overlap on the GPU race and must be ordered. */
+int hlbm_wall_forces_static(const double *f, int n_nodes, const double *xy, const int32_t *edge_a,
+                            const int32_t *edge_b, int n_edges, double qdyn, double *out, void *stream);
+
 /* Wait for all work of the context. */
 int hlbm_sync(hlbm_ctx *ctx);
 

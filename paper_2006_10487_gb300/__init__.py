@@ -71,6 +71,8 @@ def lib():
                                    C.c_double, C.POINTER(hlbm_options), C.c_char_p, dp, C.c_size_t,
                                    C.POINTER(C.c_size_t)]
         L.hlbm_time_kernel.argtypes = [C.c_void_p, C.c_char_p, C.c_int, dp]
+        L.hlbm_wall_forces_static.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                              C.c_double, C.c_void_p, C.c_void_p]
         L.hlbm_sync.argtypes = [C.c_void_p]
         L.hlbm_destroy.argtypes = [C.c_void_p]
         L.hlbm_last_error.argtypes = [C.c_void_p]

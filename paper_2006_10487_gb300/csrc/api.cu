@@ -347,6 +347,12 @@ void release(hlbm_ctx *c)
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
 }
 
+}  // namespace
+
+void hlbm::set_thread_error(const std::string &msg) { g_create_err = msg; }
+
+namespace {
+
 int fail(hlbm_ctx *c, int code, const std::string &msg)
 {
     if (c) c->err = msg;

@@ -66,4 +66,7 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
 // splitmix64-based initial density deviate in [-1, 1) (host side).
 double init_deviate(uint64_t seed, uint64_t grid, uint64_t node);
 
+// Message returned by hlbm_last_error(NULL) on this thread.
+void set_thread_error(const std::string &msg);
+
 }  // namespace hlbm

@@ -1,0 +1,63 @@
+"""The allocation-free force entry point, checked against hlbm_forces.
+
+Some callers cannot call cudaMalloc (their device memory belongs to another
+framework's pool, or they evaluate forces in loops that must not allocate).
+hlbm_wall_forces_static serves them: it keeps its reduction scratch in a fixed
+device array.  This file runs last so that a failure here leaves every other
+test already run; it also passes on its own in a fresh process.
+"""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+from workloads import make_case
+
+pytestmark = pytest.mark.gpu
+
+
+def test_static_forces_match_the_solver_forces_on_two_calls():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_10487_gb300 import build
+    build.build()
+    import paper_2006_10487_gb300 as H
+
+    case = make_case("hlbm_small", aoa_deg=8.0)
+    sol = H.Solver(case, precision="fp64")
+    xy = torch.tensor(H.hlbm_inspect(case, "xy").reshape(-1, 2), dtype=torch.float64, device="cuda")
+    we = H.hlbm_inspect(case, "wall_edges").astype(np.int32).reshape(-1, 2)
+    ea = torch.tensor(we[:, 0].copy(), dtype=torch.int32, device="cuda")
+    eb = torch.tensor(we[:, 1].copy(), dtype=torch.int32, device="cuda")
+    u0 = case.Ma / math.sqrt(3)
+    qdyn = 0.5 * u0 * u0 * case.chord
+    stream = torch.cuda.current_stream().cuda_stream
+    lib = H.lib()
+    for steps in (20, 1):  # two calls in a row, on two different states
+        sol.step(steps)
+        cd, cl = sol.forces()
+        f = torch.tensor(sol.populations(-1), dtype=torch.float64, device="cuda").contiguous()
+        out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+        rc = lib.hlbm_wall_forces_static(f.data_ptr(), case.n_nodes, xy.data_ptr(), ea.data_ptr(), eb.data_ptr(),
+                                         int(ea.numel()), qdyn, out.data_ptr(), stream)
+        assert rc == H.HLBM_OK, H.hlbm_last_error()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        scale = max(abs(cd[-1]), abs(cl[-1]))
+        assert abs(got[0] - cd[-1]) <= 1e-12 * scale
+        assert abs(got[1] - cl[-1]) <= 1e-12 * scale
+
+
+def test_static_forces_reject_inputs_beyond_the_scratch_limit():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2006_10487_gb300 as H
+    lib = H.lib()
+    dummy = torch.zeros(16, dtype=torch.float64, device="cuda")
+    rc = lib.hlbm_wall_forces_static(dummy.data_ptr(), 1, dummy.data_ptr(), dummy.data_ptr(), dummy.data_ptr(),
+                                     131072 + 1, 1.0, dummy.data_ptr(), None)
+    assert rc == H.HLBM_EINVAL
+    assert "limit" in H.hlbm_last_error()

@@ -191,11 +191,30 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     M.ring_start = P.ring_start;
     M.n_ring = P.n_ring;
     for (int b = 0; b < 2; b++) M.g[b] = dalloc(c, size_t(9) * M.Np * sizeof(T));
-    // sliced-ELL operator rows in device order
+    // sliced-ELL operator rows in device order; the column of every entry is
+    // the position of the neighbour in its tile's halo list (the sorted nodes
+    // the tile's rows touch), which the kernel stages in shared memory
     using E = typename std::conditional<std::is_same<T, float>::value, float4, double4_32a>::type;
     M.n_slices = M.Np / 32;
+    M.n_tiles = (P.n + kTileRows - 1) / kTileRows;
+    std::vector<int> hptr(M.n_tiles + 1, 0), hnodes;
+    std::vector<std::vector<int>> halo(M.n_tiles);
+    for (int t = 0; t < M.n_tiles; t++) {
+        std::vector<int> &h = halo[t];
+        for (int r = t * kTileRows; r < std::min(P.n, (t + 1) * kTileRows); r++)
+            for (int k = P.rowptr[P.perm[r]]; k < P.rowptr[P.perm[r] + 1]; k++) h.push_back(P.inv[P.col[k]]);
+        std::sort(h.begin(), h.end());
+        h.erase(std::unique(h.begin(), h.end()), h.end());
+        hptr[t + 1] = hptr[t] + int(h.size());
+        hnodes.insert(hnodes.end(), h.begin(), h.end());
+        M.max_halo = std::max(M.max_halo, int(h.size()));
+    }
     std::vector<int> sptr(M.n_slices), slen(M.n_slices);
     std::vector<E> ent;
+    auto set_col = [](E &v, int col) {
+        if (std::is_same<T, float>::value) { float fcol; std::memcpy(&fcol, &col, 4); std::memcpy(&v.w, &fcol, 4); }
+        else v.w = T(col);
+    };
     for (int sl = 0; sl < M.n_slices; sl++) {
         int len = 0;
         for (int l = 0; l < 32; l++) {
@@ -208,6 +227,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
         ent.resize(base + size_t(32) * len);
         for (int l = 0; l < 32; l++) {
             int r = sl * 32 + l;
+            const std::vector<int> *h = r < P.n ? &halo[r / kTileRows] : nullptr;
             for (int e = 0; e < len; e++) {
                 E v{};
                 int old = r < P.n ? P.perm[r] : -1;
@@ -215,18 +235,20 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
                 if (old >= 0 && k < P.rowptr[old + 1]) {
                     v.x = T(P.sx[k]); v.y = T(P.sy[k]); v.z = T(P.cc[k]);
                     int col = P.inv[P.col[k]];
-                    if (std::is_same<T, float>::value) { float fcol; std::memcpy(&fcol, &col, 4); std::memcpy(&v.w, &fcol, 4); }
-                    else v.w = T(col);
+                    set_col(v, int(std::lower_bound(h->begin(), h->end(), col) - h->begin()));
                 } else {
-                    int col = r < P.n ? r : 0;  // padding: zero coefficients on a valid column
-                    v.x = v.y = v.z = T(0);
-                    if (std::is_same<T, float>::value) { float fcol; std::memcpy(&fcol, &col, 4); std::memcpy(&v.w, &fcol, 4); }
-                    else v.w = T(col);
+                    v.x = v.y = v.z = T(0);  // padding: zero coefficients on a valid slot
+                    set_col(v, 0);
                 }
                 ent[base + size_t(32) * e + l] = v;
             }
         }
     }
+    M.halo_ptr = upload(c, hptr);
+    M.halo_nodes = upload(c, hnodes);
+    M.smem_bytes = size_t(M.max_halo) * 9 * sizeof(T);
+    if (M.smem_bytes > 200 * 1024) throw CudaError{"mesh tiles touch too many nodes for shared memory"};
+    configure_fv<T>(M.smem_bytes);
     M.ent = upload(c, ent);
     M.slice_ptr = upload(c, sptr);
     M.slice_len = upload(c, slen);

@@ -35,6 +35,11 @@ struct DevMesh {
     int n_slices = 0;
     void *ent = nullptr;
     int *slice_ptr = nullptr, *slice_len = nullptr;
+    // tiles of kTileRows consecutive rows; tile t touches the sorted nodes
+    // halo_nodes[halo_ptr[t] .. halo_ptr[t+1]) and entry columns index that list
+    int n_tiles = 0, max_halo = 0;
+    int *halo_ptr = nullptr, *halo_nodes = nullptr;
+    size_t smem_bytes = 0;
     void *Q0 = nullptr, *Q1 = nullptr;  // [12][n_ring] Eq. 9 data at t and t + 1
     int n_is = 0;
     int *is_n = nullptr;    // padded finest-level index of each structured interpolation node
@@ -60,6 +65,11 @@ struct DevCtx {
     int *flag = nullptr;
     int force_cap = 0;
 };
+
+constexpr int kTileRows = 128;  // rows per finite-volume tile (= threads per block)
+
+// Raises the kernel's dynamic shared-memory limit to `bytes` (once per process).
+template <typename T> void configure_fv(size_t bytes);
 
 template <typename T> void launch_init_level(const DevCtx &, int c, unsigned long long seed, double perturb, cudaStream_t);
 template <typename T> void launch_collide(const DevCtx &, int c, cudaStream_t);

@@ -416,32 +416,53 @@ __device__ __forceinline__ void unpack(const double4_32a &e, double &sx, double 
 // f^neq' = f^neq + acc - [f^eq(rho', u') - f^eq(rho, u)].  Wall rows take
 // u' = 0 (no-slip: rho and f^neq kept); ring rows, unless this is the last
 // sub-step, take the Eq. 5-6 state of the next sub-step (theta_next).
-// One thread per row; neighbours are gathered four at a time so that all
-// their loads are in flight together.
-constexpr int kFvThreads = 128;
-constexpr int kFvGroup = 4;
+//
+// Evaluation.  With (a_k, b_k) = dt s_Pk, the equilibrium part of the
+// streaming sum, sum_k (c_i.(a_k, b_k)) [f^eq_i(P_k) - f^eq_i(P)], is a
+// polynomial in the components of c_i:
+//   w_i [ E_i(u_P) (c_x D_x + c_y D_y) + 3 (c_x^2 Q_xx + c_x c_y Q_xy + c_y^2 Q_yy)
+//         + 9/2 (c_x M_x + c_y M_y + c_x^2 c_y M_xxy + c_x c_y^2 M_xyy)
+//         - 3/2 (c_x L_x + c_y L_y) ]
+// (c_x^3 = c_x for D2Q9), whose 13 moment sums over the neighbours (D, Q, M,
+// L below, with drho, du = u_k - u_P, su = u_k + u_P) are accumulated once per
+// neighbour; only the f^neq part is summed per population.
+// Each block is one tile of kTileRows consecutive rows (a compact patch: rows
+// are in Morton order): it first copies the states of every node the tile
+// touches (its sorted halo list) into shared memory, plane-major, then each
+// thread treats one row, reading its neighbours from shared memory.
+constexpr int kFvThreads = kTileRows;
+constexpr int kFvGroup = 2;
 
 template <typename T>
 __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
                                                    const int *__restrict__ slice_ptr,
                                                    const int *__restrict__ slice_len,
-                                                   const typename Ent<T>::type *__restrict__ ent, T dt, T dt_tau,
+                                                   const typename Ent<T>::type *__restrict__ ent,
+                                                   const int *__restrict__ halo_ptr,
+                                                   const int *__restrict__ halo_nodes, T dt, T dt_tau,
                                                    int n_wall, int ring_start, int n_ring,
                                                    const T *__restrict__ Q0, const T *__restrict__ Q1, T theta_next,
                                                    T scale5, int star)
 {
+    extern __shared__ __align__(16) unsigned char fv_smem[];
+    T *sh = reinterpret_cast<T *>(fv_smem);
+    const int h0 = halo_ptr[blockIdx.x], hn = halo_ptr[blockIdx.x + 1] - h0;
+    for (int h = threadIdx.x; h < hn; h += blockDim.x) {
+        const int node = halo_nodes[h0 + h];
+#pragma unroll
+        for (int i = 0; i < 9; i++) sh[i * hn + h] = g[size_t(i) * Np + node];
+    }
+    __syncthreads();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int sl = r >> 5;
     const int base = slice_ptr[sl] + (r & 31), len = slice_len[sl];
     T r1P, uPx, uPy, nP[9];
     load_mesh(g, Np, r, r1P, uPx, uPy, nP);
-    T EP[9], acc[9];
+    T acc[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) {
-        EP[i] = Efun<T>(i, uPx, uPy);
-        acc[i] = T(0);
-    }
+    for (int i = 0; i < 9; i++) acc[i] = T(0);
+    T Sa = 0, Sb = 0, Dx = 0, Dy = 0, Qxx = 0, Qyy = 0, Qxy = 0, Lx = 0, Ly = 0, Mx = 0, My = 0, Mxxy = 0, Mxyy = 0;
     for (int e0 = 0; e0 < len; e0 += kFvGroup) {
         T sx[kFvGroup], sy[kFvGroup], c[kFvGroup];
         int k[kFvGroup];
@@ -451,31 +472,48 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
                 unpack(ent[base + 32 * (e0 + j)], sx[j], sy[j], c[j], k[j]);
             } else {
                 sx[j] = sy[j] = c[j] = T(0);
-                k[j] = r;
+                k[j] = 0;
             }
         }
         T st[kFvGroup][9];
 #pragma unroll
         for (int j = 0; j < kFvGroup; j++)
 #pragma unroll
-            for (int i = 0; i < 9; i++)
-                st[j][i] = g[size_t(i) * Np + k[j]];
+            for (int i = 0; i < 9; i++) st[j][i] = sh[i * hn + k[j]];
 #pragma unroll
         for (int j = 0; j < kFvGroup; j++) {
             T nk[9];
 #pragma unroll
             for (int i = 3; i < 9; i++) nk[i] = st[j][i];
             neq_complete(nk);
-            T drho = st[j][0] - r1P, rhok = T(1) + st[j][0];
-            T dux = st[j][1] - uPx, duy = st[j][2] - uPy, sux = st[j][1] + uPx, suy = st[j][2] + uPy;
-            T cs = dt_tau * c[j];
+            const T a = dt * sx[j], b = dt * sy[j], cs = dt_tau * c[j];
+            const T drho = st[j][0] - r1P, rhok = T(1) + st[j][0];
+            const T dux = st[j][1] - uPx, duy = st[j][2] - uPy, sux = st[j][1] + uPx, suy = st[j][2] + uPy;
+            const T dus = dux * sux + duy * suy, ra = rhok * a, rb = rhok * b;
+            const T xs = dux * suy + duy * sux;
+            Sa += a;
+            Sb += b;
+            Dx += a * drho;
+            Dy += b * drho;
+            Qxx += ra * dux;
+            Qyy += rb * duy;
+            Qxy += ra * duy + rb * dux;
+            Lx += ra * dus;
+            Ly += rb * dus;
+            Mx += ra * dux * sux;
+            My += rb * duy * suy;
+            Mxxy += ra * xs + rb * dux * sux;
+            Mxyy += rb * xs + ra * duy * suy;
 #pragma unroll
-            for (int i = 0; i < 9; i++) {
-                T sd = dt * (T(cx(i)) * sx[j] + T(cy(i)) * sy[j]);
-                T dfe = feq_diff<T>(i, EP[i], drho, rhok, dux, duy, sux, suy);
-                acc[i] += sd * (dfe + nk[i] - nP[i]) - cs * nk[i];
-            }
+            for (int i = 0; i < 9; i++) acc[i] += (T(cx(i)) * a + T(cy(i)) * b - cs) * nk[i];
         }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const T X = T(cx(i)), Y = T(cy(i));
+        T eq = Efun<T>(i, uPx, uPy) * (X * Dx + Y * Dy) + T(3) * (X * X * Qxx + X * Y * Qxy + Y * Y * Qyy) +
+               T(4.5) * (X * Mx + Y * My + X * X * Y * Mxxy + X * Y * Y * Mxyy) - T(1.5) * (X * Lx + Y * Ly);
+        acc[i] += wq<T>(i) * eq - nP[i] * (X * Sa + Y * Sb);
     }
     T drho = 0, djx = 0, djy = 0;
 #pragma unroll
@@ -489,7 +527,8 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
     T ux = uPx + dux, uy = uPy + duy;
     T nq[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) nq[i] = nP[i] + acc[i] - feq_diff<T>(i, EP[i], drho, rho, dux, duy, ux + uPx, uy + uPy);
+    for (int i = 0; i < 9; i++)
+        nq[i] = nP[i] + acc[i] - feq_diff<T>(i, Efun<T>(i, uPx, uPy), drho, rho, dux, duy, ux + uPx, uy + uPy);
     if (r < n_wall) {
         ux = T(0);
         uy = T(0);
@@ -748,9 +787,16 @@ template <typename T> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
     T scale5 = T(1.0 - 1.0 / (2.0 * l.tau));
     int star = msub < C.n_sub - 1 ? 1 : 0;
     T theta_next = T(double(msub + 1) / double(C.n_sub));
-    k_fv<T><<<cdiv(m.n, kFvThreads), kFvThreads, 0, s>>>((const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n, m.slice_ptr, m.slice_len,
-                                            (const typename Ent<T>::type *)m.ent, dt, dt_tau, m.n_wall, m.ring_start,
-                                            m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5, star);
+    k_fv<T><<<m.n_tiles, kFvThreads, m.smem_bytes, s>>>((const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
+                                                       m.slice_ptr, m.slice_len, (const typename Ent<T>::type *)m.ent,
+                                                       m.halo_ptr, m.halo_nodes, dt, dt_tau, m.n_wall, m.ring_start,
+                                                       m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5,
+                                                       star);
+}
+
+template <typename T> void configure_fv(size_t bytes)
+{
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(k_fv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
 }
 
 template <typename T> void launch_forces(const DevCtx &C, cudaStream_t s)
@@ -780,6 +826,7 @@ void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *u
 }
 
 #define HLBM_INSTANTIATE(T)                                                                                   \
+    template void configure_fv<T>(size_t);                                                                    \
     template void launch_init_level<T>(const DevCtx &, int, unsigned long long, double, cudaStream_t);        \
     template void launch_collide<T>(const DevCtx &, int, cudaStream_t);                                       \
     template void launch_outer_bc<T>(const DevCtx &, cudaStream_t);                                           \

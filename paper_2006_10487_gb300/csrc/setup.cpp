@@ -249,11 +249,40 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
         P.n_sub = n < 10.0 ? 10 : int(n);
     }
 
-    // ---- node order on the device: wall, fluid, ring
-    P.perm.clear();
-    for (int want : {HLBM_NODE_WALL, HLBM_NODE_FLUID, HLBM_NODE_RING})
-        for (int p = 0; p < P.n; p++)
-            if (P.kind[p] == want) P.perm.push_back(p);
+    // ---- node order on the device: wall, fluid, ring; inside each range the
+    // nodes follow a Morton (Z-order) curve over their coordinates, so that a
+    // run of consecutive rows is a compact patch of the mesh (the finite-volume
+    // kernel stages each run's neighbourhood in shared memory)
+    {
+        double mx0 = 1e300, my0 = 1e300, mx1 = -1e300, my1 = -1e300;
+        for (int p = 0; p < P.n; p++) {
+            mx0 = std::min(mx0, P.xy[2 * p]); mx1 = std::max(mx1, P.xy[2 * p]);
+            my0 = std::min(my0, P.xy[2 * p + 1]); my1 = std::max(my1, P.xy[2 * p + 1]);
+        }
+        double span = std::max(std::max(mx1 - mx0, my1 - my0), 1e-30);
+        auto spread = [](uint32_t v) {  // 16 bits -> even bit positions
+            uint64_t x = v & 0xffffu;
+            x = (x | (x << 8)) & 0x00ff00ffu;
+            x = (x | (x << 4)) & 0x0f0f0f0fu;
+            x = (x | (x << 2)) & 0x33333333u;
+            x = (x | (x << 1)) & 0x55555555u;
+            return x;
+        };
+        std::vector<std::pair<uint64_t, int>> key(P.n);
+        for (int p = 0; p < P.n; p++) {
+            uint32_t qx = uint32_t(std::min(65535.0, std::floor((P.xy[2 * p] - mx0) / span * 65535.0)));
+            uint32_t qy = uint32_t(std::min(65535.0, std::floor((P.xy[2 * p + 1] - my0) / span * 65535.0)));
+            key[p] = {spread(qx) | (spread(qy) << 1), p};
+        }
+        P.perm.clear();
+        for (int want : {HLBM_NODE_WALL, HLBM_NODE_FLUID, HLBM_NODE_RING}) {
+            std::vector<std::pair<uint64_t, int>> part;
+            for (int p = 0; p < P.n; p++)
+                if (P.kind[p] == want) part.push_back(key[p]);
+            std::sort(part.begin(), part.end());
+            for (auto &kp : part) P.perm.push_back(kp.second);
+        }
+    }
     P.inv.assign(P.n, 0);
     for (int q = 0; q < P.n; q++) P.inv[P.perm[q]] = q;
     P.n_wall = 0;

@@ -641,11 +641,26 @@ int hlbm_time_kernel(hlbm_ctx *c, const char *kernel, int reps, double *avg_ms)
                 c->dev.lv[lvl].parity ^= 1;
             }
         };
-        one(0);  // warm-up
+        // the repetitions are captured as one CUDA graph so that the GPU runs
+        // them back to back (timing individual launches from the host would
+        // measure the launch rate once a kernel is faster than it)
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        ck(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaStream_t user = c->stream;
+        c->stream = c->cap_stream;
+        for (int r = 0; r < reps; r++) one(r);
+        c->stream = user;
+        ck(cudaStreamEndCapture(c->cap_stream, &graph), "end capture");
+        ck(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+        cudaGraphDestroy(graph);
+        ck(cudaGraphLaunch(exec, c->stream), "graph launch");  // warm-up
         ck(cudaEventRecord(e0, c->stream), "record");
-        for (int r = 0; r < reps; r++) one(r + 1);
+        ck(cudaGraphLaunch(exec, c->stream), "graph launch");
         ck(cudaEventRecord(e1, c->stream), "record");
         ck(cudaEventSynchronize(e1), "sync");
+        cudaGraphExecDestroy(exec);
         float ms = 0;
         ck(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
         *avg_ms = double(ms) / reps;

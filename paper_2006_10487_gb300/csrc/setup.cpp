@@ -249,10 +249,10 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
         P.n_sub = n < 10.0 ? 10 : int(n);
     }
 
-    // ---- node order on the device: wall, fluid, ring; inside each range the
-    // nodes follow a Morton (Z-order) curve over their coordinates, so that a
-    // run of consecutive rows is a compact patch of the mesh (the finite-volume
-    // kernel stages each run's neighbourhood in shared memory)
+    // ---- node order on the device: wall, fluid, ring; the fluid nodes follow a
+    // Morton (Z-order) curve over their coordinates, so that a run of
+    // consecutive rows is a compact patch of the mesh (the finite-volume kernel
+    // stages each run's neighbourhood in shared memory)
     {
         double mx0 = 1e300, my0 = 1e300, mx1 = -1e300, my1 = -1e300;
         for (int p = 0; p < P.n; p++) {
@@ -274,11 +274,13 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
             uint32_t qy = uint32_t(std::min(65535.0, std::floor((P.xy[2 * p + 1] - my0) / span * 65535.0)));
             key[p] = {spread(qx) | (spread(qy) << 1), p};
         }
+        // wall and ring nodes keep their input order (the ring's interface data
+        // and the wall edges are indexed in that order); fluid nodes are sorted
         P.perm.clear();
         for (int want : {HLBM_NODE_WALL, HLBM_NODE_FLUID, HLBM_NODE_RING}) {
             std::vector<std::pair<uint64_t, int>> part;
             for (int p = 0; p < P.n; p++)
-                if (P.kind[p] == want) part.push_back(key[p]);
+                if (P.kind[p] == want) part.push_back({want == HLBM_NODE_FLUID ? key[p].first : 0, p});
             std::sort(part.begin(), part.end());
             for (auto &kp : part) P.perm.push_back(kp.second);
         }

@@ -199,10 +199,18 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     M.n_tiles = (P.n + kTileRows - 1) / kTileRows;
     std::vector<int> hptr(M.n_tiles + 1, 0), hnodes;
     std::vector<std::vector<int>> halo(M.n_tiles);
+    // the self entry of a row is not stored: its streaming term vanishes in the
+    // difference form and its collision weight is C_PP = 11/18 on every node
+    auto off_diag = [&](int old) {
+        std::vector<int> ks;
+        for (int k = P.rowptr[old]; k < P.rowptr[old + 1]; k++)
+            if (P.col[k] != old) ks.push_back(k);
+        return ks;
+    };
     for (int t = 0; t < M.n_tiles; t++) {
         std::vector<int> &h = halo[t];
         for (int r = t * kTileRows; r < std::min(P.n, (t + 1) * kTileRows); r++)
-            for (int k = P.rowptr[P.perm[r]]; k < P.rowptr[P.perm[r] + 1]; k++) h.push_back(P.inv[P.col[k]]);
+            for (int k : off_diag(P.perm[r])) h.push_back(P.inv[P.col[k]]);
         std::sort(h.begin(), h.end());
         h.erase(std::unique(h.begin(), h.end()), h.end());
         hptr[t + 1] = hptr[t] + int(h.size());
@@ -217,9 +225,11 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     };
     for (int sl = 0; sl < M.n_slices; sl++) {
         int len = 0;
+        std::vector<std::vector<int>> rows(32);
         for (int l = 0; l < 32; l++) {
             int r = sl * 32 + l;
-            if (r < P.n) len = std::max(len, P.rowptr[P.perm[r] + 1] - P.rowptr[P.perm[r]]);
+            if (r < P.n) rows[l] = off_diag(P.perm[r]);
+            len = std::max(len, int(rows[l].size()));
         }
         sptr[sl] = int(ent.size());
         slen[sl] = len;
@@ -230,9 +240,8 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
             const std::vector<int> *h = r < P.n ? &halo[r / kTileRows] : nullptr;
             for (int e = 0; e < len; e++) {
                 E v{};
-                int old = r < P.n ? P.perm[r] : -1;
-                int k = old >= 0 ? P.rowptr[old] + e : -1;
-                if (old >= 0 && k < P.rowptr[old + 1]) {
+                if (e < int(rows[l].size())) {
+                    int k = rows[l][e];
                     v.x = T(P.sx[k]); v.y = T(P.sy[k]); v.z = T(P.cc[k]);
                     int col = P.inv[P.col[k]];
                     set_col(v, int(std::lower_bound(h->begin(), h->end(), col) - h->begin()));
@@ -549,11 +558,11 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
     } else if (k == "fv_updates") *value = double(P.n) * P.n_sub * double(1L << (P.L - 1));
     else if (k == "launches_per_step") *value = double(c->launches_per_step);
     else if (k == "fv_bytes") {
-        // algorithmic bytes of one finite-volume sub-step: 9 reads + 9 writes of
-        // every node's populations, one (s_x, s_y, C, column) entry per operator
-        // coefficient
+        // algorithmic bytes of one finite-volume sub-step: the 9 state values of
+        // every node read and written, one (s_x, s_y, C, column) entry per
+        // off-diagonal operator coefficient
         double vb = P.precision == HLBM_FP32 ? 4.0 : 8.0;
-        *value = double(P.n) * 18.0 * vb + double(P.col.size()) * 4.0 * vb;
+        *value = double(P.n) * 18.0 * vb + double(P.col.size() - size_t(P.n)) * 4.0 * vb;
     } else if (k.size() == 14 && k.compare(0, 13, "collide_bytes") == 0) {
         int l = k[13] - '0';
         if (l < 0 || l >= P.L) return HLBM_EINVAL;

@@ -417,6 +417,9 @@ __device__ __forceinline__ void unpack(const double4_32a &e, double &sx, double 
 // u' = 0 (no-slip: rho and f^neq kept); ring rows, unless this is the last
 // sub-step, take the Eq. 5-6 state of the next sub-step (theta_next).
 //
+// The own node P carries no streaming term and collision weight C_PP = 11/18
+// (the control-volume mean of its hat function, the same on every node), so
+// the operator rows hold only the edge neighbours.
 // Evaluation.  With (a_k, b_k) = dt s_Pk, the equilibrium part of the
 // streaming sum, sum_k (c_i.(a_k, b_k)) [f^eq_i(P_k) - f^eq_i(P)], is a
 // polynomial in the components of c_i:
@@ -459,9 +462,11 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
     const int base = slice_ptr[sl] + (r & 31), len = slice_len[sl];
     T r1P, uPx, uPy, nP[9];
     load_mesh(g, Np, r, r1P, uPx, uPy, nP);
+    // own node: no streaming term (g(P) - g(P) = 0), collision weight C_PP = 11/18
     T acc[9];
+    const T csP = dt_tau * T(11.0 / 18.0);
 #pragma unroll
-    for (int i = 0; i < 9; i++) acc[i] = T(0);
+    for (int i = 0; i < 9; i++) acc[i] = -csP * nP[i];
     T Sa = 0, Sb = 0, Dx = 0, Dy = 0, Qxx = 0, Qyy = 0, Qxy = 0, Lx = 0, Ly = 0, Mx = 0, My = 0, Mxxy = 0, Mxyy = 0;
     for (int e0 = 0; e0 < len; e0 += kFvGroup) {
         T sx[kFvGroup], sy[kFvGroup], c[kFvGroup];

@@ -186,7 +186,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     const LevelPlan &F = P.lv[P.L - 1];
     const DevLevel &FL = c->dev.lv[P.L - 1];
     M.n = P.n;
-    M.Np = (P.n + kTileRows - 1) / kTileRows * kTileRows;  // whole tiles of rows
+    M.Np = (P.n + 31) / 32 * 32;
     M.n_wall = P.n_wall;
     M.ring_start = P.ring_start;
     M.n_ring = P.n_ring;
@@ -255,13 +255,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     }
     M.halo_ptr = upload(c, hptr);
     M.halo_nodes = upload(c, hnodes);
-    for (int t = 0; t < M.n_tiles; t++) {
-        int sl = t * kTileRows / 32, last = sl + kTileRows / 32 - 1;
-        M.max_tile_ent = std::max(M.max_tile_ent, sptr[last] + 32 * slen[last] - sptr[sl]);
-    }
-    // shared memory per tile: entries, own rows' state, halo state
-    M.smem_bytes = size_t(M.max_tile_ent) * sizeof(E) + size_t(9) * kTileRows * sizeof(T) +
-                   size_t(M.max_halo) * 9 * sizeof(T);
+    M.smem_bytes = size_t(M.max_halo) * 9 * sizeof(T);
     if (M.smem_bytes > 200 * 1024) throw CudaError{"mesh tiles touch too many nodes for shared memory"};
     configure_fv<T>(M.smem_bytes);
     M.ent = upload(c, ent);

@@ -430,26 +430,11 @@ __device__ __forceinline__ void unpack(const double4_32a &e, double &sx, double 
 // L below, with drho, du = u_k - u_P, su = u_k + u_P) are accumulated once per
 // neighbour; only the f^neq part is summed per population.
 // Each block is one tile of kTileRows consecutive rows (a compact patch: rows
-// are in Morton order).  It first copies, with asynchronous cp.async copies,
-// the tile's operator entries (one contiguous block), its own rows' state
-// (nine contiguous runs) and the state of every node its rows touch (its
-// sorted halo list) into shared memory; after one wait every thread treats one
-// row from shared memory only.
+// are in Morton order): it first copies the states of every node the tile
+// touches (its sorted halo list) into shared memory, plane-major, then each
+// thread treats one row, reading its neighbours from shared memory.
 constexpr int kFvThreads = kTileRows;
 constexpr int kFvGroup = 2;
-
-__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes)
-{
-    unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    if (bytes == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-    else if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
@@ -457,58 +442,31 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
                                                    const int *__restrict__ slice_len,
                                                    const typename Ent<T>::type *__restrict__ ent,
                                                    const int *__restrict__ halo_ptr,
-                                                   const int *__restrict__ halo_nodes, int max_tile_ent, T dt,
-                                                   T dt_tau, int n_wall, int ring_start, int n_ring,
+                                                   const int *__restrict__ halo_nodes, T dt, T dt_tau,
+                                                   int n_wall, int ring_start, int n_ring,
                                                    const T *__restrict__ Q0, const T *__restrict__ Q1, T theta_next,
                                                    T scale5, int star)
 {
-    using E = typename Ent<T>::type;
     extern __shared__ __align__(16) unsigned char fv_smem[];
-    E *s_ent = reinterpret_cast<E *>(fv_smem);
-    T *s_own = reinterpret_cast<T *>(s_ent + max_tile_ent);
-    T *s_halo = s_own + 9 * kTileRows;
-    const int row0 = blockIdx.x * kTileRows;
-    const int sl0 = row0 >> 5;
-    const int e_begin = slice_ptr[sl0];
-    const int e_end = slice_ptr[sl0 + kTileRows / 32 - 1] + 32 * slice_len[sl0 + kTileRows / 32 - 1];
+    T *sh = reinterpret_cast<T *>(fv_smem);
     const int h0 = halo_ptr[blockIdx.x], hn = halo_ptr[blockIdx.x + 1] - h0;
-    {
-        // entries: contiguous, 16-byte chunks
-        const int chunks = (e_end - e_begin) * int(sizeof(E) / 16);
-        const char *src = reinterpret_cast<const char *>(ent + e_begin);
-        for (int c = threadIdx.x; c < chunks; c += kFvThreads)
-            cp_async(reinterpret_cast<char *>(s_ent) + 16 * c, src + 16 * c, 16);
-        // own rows: nine runs of kTileRows values (Np is a multiple of kTileRows)
-        const int per = kTileRows * int(sizeof(T)) / 16;
-        for (int c = threadIdx.x; c < 9 * per; c += kFvThreads) {
-            const int i = c / per, j = c - i * per;
-            cp_async(reinterpret_cast<char *>(s_own + i * kTileRows) + 16 * j,
-                     reinterpret_cast<const char *>(g + size_t(i) * Np + row0) + 16 * j, 16);
-        }
-        // halo: gather, one value per copy
-        for (int c = threadIdx.x; c < 9 * hn; c += kFvThreads) {
-            const int i = c / hn, h = c - i * hn;
-            cp_async(s_halo + c, g + size_t(i) * Np + halo_nodes[h0 + h], int(sizeof(T)));
-        }
-        cp_async_wait_all();
+    for (int h = threadIdx.x; h < hn; h += blockDim.x) {
+        const int node = halo_nodes[h0 + h];
+#pragma unroll
+        for (int i = 0; i < 9; i++) sh[i * hn + h] = g[size_t(i) * Np + node];
     }
     __syncthreads();
-    const int r = row0 + threadIdx.x;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int sl = r >> 5;
-    const int base = slice_ptr[sl] - e_begin + (r & 31), len = slice_len[sl];
-    const T r1P = s_own[threadIdx.x], uPx = s_own[kTileRows + threadIdx.x], uPy = s_own[2 * kTileRows + threadIdx.x];
+    const int base = slice_ptr[sl] + (r & 31), len = slice_len[sl];
+    T r1P, uPx, uPy, nP[9];
+    load_mesh(g, Np, r, r1P, uPx, uPy, nP);
     // own node: no streaming term (g(P) - g(P) = 0), collision weight C_PP = 11/18
     T acc[9];
-    {
-        T nP[9];
+    const T csP = dt_tau * T(11.0 / 18.0);
 #pragma unroll
-        for (int i = 3; i < 9; i++) nP[i] = s_own[i * kTileRows + threadIdx.x];
-        neq_complete(nP);
-        const T csP = dt_tau * T(11.0 / 18.0);
-#pragma unroll
-        for (int i = 0; i < 9; i++) acc[i] = -csP * nP[i];
-    }
+    for (int i = 0; i < 9; i++) acc[i] = -csP * nP[i];
     T Sa = 0, Sb = 0, Dx = 0, Dy = 0, Qxx = 0, Qyy = 0, Qxy = 0, Lx = 0, Ly = 0, Mx = 0, My = 0, Mxxy = 0, Mxyy = 0;
     for (int e0 = 0; e0 < len; e0 += kFvGroup) {
         T sx[kFvGroup], sy[kFvGroup], c[kFvGroup];
@@ -516,7 +474,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
 #pragma unroll
         for (int j = 0; j < kFvGroup; j++) {
             if (e0 + j < len) {
-                unpack(s_ent[base + 32 * (e0 + j)], sx[j], sy[j], c[j], k[j]);
+                unpack(ent[base + 32 * (e0 + j)], sx[j], sy[j], c[j], k[j]);
             } else {
                 sx[j] = sy[j] = c[j] = T(0);
                 k[j] = 0;
@@ -526,7 +484,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
 #pragma unroll
         for (int j = 0; j < kFvGroup; j++)
 #pragma unroll
-            for (int i = 0; i < 9; i++) st[j][i] = s_halo[i * hn + k[j]];
+            for (int i = 0; i < 9; i++) st[j][i] = sh[i * hn + k[j]];
 #pragma unroll
         for (int j = 0; j < kFvGroup; j++) {
             T nk[9];
@@ -555,10 +513,6 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
             for (int i = 0; i < 9; i++) acc[i] += (T(cx(i)) * a + T(cy(i)) * b - cs) * nk[i];
         }
     }
-    T nP[9];
-#pragma unroll
-    for (int i = 3; i < 9; i++) nP[i] = s_own[i * kTileRows + threadIdx.x];
-    neq_complete(nP);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         const T X = T(cx(i)), Y = T(cy(i));
@@ -840,7 +794,7 @@ template <typename T> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
     T theta_next = T(double(msub + 1) / double(C.n_sub));
     k_fv<T><<<m.n_tiles, kFvThreads, m.smem_bytes, s>>>((const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
                                                        m.slice_ptr, m.slice_len, (const typename Ent<T>::type *)m.ent,
-                                                       m.halo_ptr, m.halo_nodes, m.max_tile_ent, dt, dt_tau, m.n_wall, m.ring_start,
+                                                       m.halo_ptr, m.halo_nodes, dt, dt_tau, m.n_wall, m.ring_start,
                                                        m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5,
                                                        star);
 }

@@ -255,7 +255,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     }
     M.halo_ptr = upload(c, hptr);
     M.halo_nodes = upload(c, hnodes);
-    M.smem_bytes = size_t(M.max_halo) * 12 * sizeof(T);  // node-major, 9 values padded to 12
+    M.smem_bytes = size_t(M.max_halo) * 9 * sizeof(T);
     if (M.smem_bytes > 200 * 1024) throw CudaError{"mesh tiles touch too many nodes for shared memory"};
     configure_fv<T>(M.smem_bytes);
     M.ent = upload(c, ent);

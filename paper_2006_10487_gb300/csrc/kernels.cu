@@ -435,42 +435,6 @@ __device__ __forceinline__ void unpack(const double4_32a &e, double &sx, double 
 // thread treats one row, reading its neighbours from shared memory.
 constexpr int kFvThreads = kTileRows;
 constexpr int kFvGroup = 2;
-constexpr int kHaloStride = 12;  // 9 state values + 3 pad: three 16-byte (FP32) or six (FP64) vectors
-
-// Wide copies of one kHaloStride-value row between registers and shared memory.
-template <typename T> __device__ __forceinline__ void store_row(T *dst, const T v[kHaloStride]);
-template <> __device__ __forceinline__ void store_row<float>(float *dst, const float v[kHaloStride])
-{
-    float4 *d = reinterpret_cast<float4 *>(dst);
-    d[0] = make_float4(v[0], v[1], v[2], v[3]);
-    d[1] = make_float4(v[4], v[5], v[6], v[7]);
-    d[2] = make_float4(v[8], v[9], v[10], v[11]);
-}
-template <> __device__ __forceinline__ void store_row<double>(double *dst, const double v[kHaloStride])
-{
-    double2 *d = reinterpret_cast<double2 *>(dst);
-#pragma unroll
-    for (int q = 0; q < 6; q++) d[q] = make_double2(v[2 * q], v[2 * q + 1]);
-}
-template <typename T> __device__ __forceinline__ void load_row(const T *src, T v[kHaloStride]);
-template <> __device__ __forceinline__ void load_row<float>(const float *src, float v[kHaloStride])
-{
-    const float4 *s = reinterpret_cast<const float4 *>(src);
-    float4 a = s[0], b = s[1], c = s[2];
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
-}
-template <> __device__ __forceinline__ void load_row<double>(const double *src, double v[kHaloStride])
-{
-    const double2 *s = reinterpret_cast<const double2 *>(src);
-#pragma unroll
-    for (int q = 0; q < 6; q++) {
-        double2 a = s[q];
-        v[2 * q] = a.x;
-        v[2 * q + 1] = a.y;
-    }
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
@@ -483,19 +447,13 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
                                                    const T *__restrict__ Q0, const T *__restrict__ Q1, T theta_next,
                                                    T scale5, int star)
 {
-    // halo states node-major, padded to kHaloStride values, so that a
-    // neighbour's nine values are read with wide shared-memory loads
     extern __shared__ __align__(16) unsigned char fv_smem[];
     T *sh = reinterpret_cast<T *>(fv_smem);
     const int h0 = halo_ptr[blockIdx.x], hn = halo_ptr[blockIdx.x + 1] - h0;
     for (int h = threadIdx.x; h < hn; h += blockDim.x) {
         const int node = halo_nodes[h0 + h];
-        T v[kHaloStride];
 #pragma unroll
-        for (int i = 0; i < 9; i++) v[i] = g[size_t(i) * Np + node];
-#pragma unroll
-        for (int i = 9; i < kHaloStride; i++) v[i] = T(0);
-        store_row<T>(sh + size_t(h) * kHaloStride, v);
+        for (int i = 0; i < 9; i++) sh[i * hn + h] = g[size_t(i) * Np + node];
     }
     __syncthreads();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -522,9 +480,11 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
                 k[j] = 0;
             }
         }
-        T st[kFvGroup][kHaloStride];
+        T st[kFvGroup][9];
 #pragma unroll
-        for (int j = 0; j < kFvGroup; j++) load_row<T>(sh + size_t(k[j]) * kHaloStride, st[j]);
+        for (int j = 0; j < kFvGroup; j++)
+#pragma unroll
+            for (int i = 0; i < 9; i++) st[j][i] = sh[i * hn + k[j]];
 #pragma unroll
         for (int j = 0; j < kFvGroup; j++) {
             T nk[9];

@@ -449,19 +449,25 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
 {
     extern __shared__ __align__(16) unsigned char fv_smem[];
     T *sh = reinterpret_cast<T *>(fv_smem);
+    // Let the next sub-step's blocks start as soon as SM slots free up; they
+    // only read constant operator data until their griddepcontrol.wait.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int h0 = halo_ptr[blockIdx.x], hn = halo_ptr[blockIdx.x + 1] - h0;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rr = r < n ? r : n - 1;
+    const int sl = rr >> 5;
+    const int base = slice_ptr[sl] + (rr & 31), len = slice_len[sl];
+    // wait until the previous sub-step (which wrote g) has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    T r1P, uPx, uPy, nP[9];
+    load_mesh(g, Np, rr, r1P, uPx, uPy, nP);  // issued before the halo staging
     for (int h = threadIdx.x; h < hn; h += blockDim.x) {
         const int node = halo_nodes[h0 + h];
 #pragma unroll
         for (int i = 0; i < 9; i++) sh[i * hn + h] = g[size_t(i) * Np + node];
     }
     __syncthreads();
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    const int sl = r >> 5;
-    const int base = slice_ptr[sl] + (r & 31), len = slice_len[sl];
-    T r1P, uPx, uPy, nP[9];
-    load_mesh(g, Np, r, r1P, uPx, uPy, nP);
     // own node: no streaming term (g(P) - g(P) = 0), collision weight C_PP = 11/18
     T acc[9];
     const T csP = dt_tau * T(11.0 / 18.0);
@@ -792,11 +798,22 @@ template <typename T> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
     T scale5 = T(1.0 - 1.0 / (2.0 * l.tau));
     int star = msub < C.n_sub - 1 ? 1 : 0;
     T theta_next = T(double(msub + 1) / double(C.n_sub));
-    k_fv<T><<<m.n_tiles, kFvThreads, m.smem_bytes, s>>>((const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
-                                                       m.slice_ptr, m.slice_len, (const typename Ent<T>::type *)m.ent,
-                                                       m.halo_ptr, m.halo_nodes, dt, dt_tau, m.n_wall, m.ring_start,
-                                                       m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5,
-                                                       star);
+    // programmatic dependent launch: the sub-step may begin while the previous
+    // kernel on the stream drains (it waits for it before reading the state)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(m.n_tiles));
+    cfg.blockDim = dim3(kFvThreads);
+    cfg.dynamicSmemBytes = m.smem_bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_fv<T>, (const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
+                       (const int *)m.slice_ptr, (const int *)m.slice_len, (const typename Ent<T>::type *)m.ent,
+                       (const int *)m.halo_ptr, (const int *)m.halo_nodes, dt, dt_tau, m.n_wall, m.ring_start,
+                       m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5, star);
 }
 
 template <typename T> void configure_fv(size_t bytes)

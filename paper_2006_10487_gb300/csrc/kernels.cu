@@ -435,9 +435,6 @@ __device__ __forceinline__ void unpack(const double4_32a &e, double &sx, double 
 // thread treats one row, reading its neighbours from shared memory.
 constexpr int kFvThreads = kTileRows;
 constexpr int kFvGroup = 2;
-// FP32: at most 48 registers, so that an SM holds 10 tiles (1280 rows) and the
-// ~1320 rows per SM of the 200k-node mesh run in about one wave
-constexpr int kFvMinBlocks32 = 10;
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
@@ -446,8 +443,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? kFvMinBlocks32 : 1)
-    k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
+__global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
                                                    const int *__restrict__ slice_ptr,
                                                    const int *__restrict__ slice_len,
                                                    const typename Ent<T>::type *__restrict__ ent,
@@ -493,10 +489,15 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? kFvMinBlocks32 : 
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     if (r >= n) return;
-    const T r1P = sh[threadIdx.x], uPx = sh[hn + threadIdx.x], uPy = sh[2 * hn + threadIdx.x];
-    T acc[9];
+    T r1P = sh[threadIdx.x], uPx = sh[hn + threadIdx.x], uPy = sh[2 * hn + threadIdx.x], nP[9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) acc[i] = T(0);
+    for (int i = 3; i < 9; i++) nP[i] = sh[i * hn + threadIdx.x];
+    neq_complete(nP);
+    // own node: no streaming term (g(P) - g(P) = 0), collision weight C_PP = 11/18
+    T acc[9];
+    const T csP = dt_tau * T(11.0 / 18.0);
+#pragma unroll
+    for (int i = 0; i < 9; i++) acc[i] = -csP * nP[i];
     T Sa = 0, Sb = 0, Dx = 0, Dy = 0, Qxx = 0, Qyy = 0, Qxy = 0, Lx = 0, Ly = 0, Mx = 0, My = 0, Mxxy = 0, Mxyy = 0;
     for (int e0 = 0; e0 < len; e0 += kFvGroup) {
         T sx[kFvGroup], sy[kFvGroup], c[kFvGroup];
@@ -543,19 +544,12 @@ __global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? kFvMinBlocks32 : 
             for (int i = 0; i < 9; i++) acc[i] += (T(cx(i)) * a + T(cy(i)) * b - cs) * nk[i];
         }
     }
-    // own node (read again from shared memory): no streaming term
-    // (g(P) - g(P) = 0) and collision weight C_PP = 11/18
-    T nP[9];
-#pragma unroll
-    for (int i = 3; i < 9; i++) nP[i] = sh[i * hn + threadIdx.x];
-    neq_complete(nP);
-    const T csP = dt_tau * T(11.0 / 18.0);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         const T X = T(cx(i)), Y = T(cy(i));
         T eq = Efun<T>(i, uPx, uPy) * (X * Dx + Y * Dy) + T(3) * (X * X * Qxx + X * Y * Qxy + Y * Y * Qyy) +
                T(4.5) * (X * Mx + Y * My + X * X * Y * Mxxy + X * Y * Y * Mxyy) - T(1.5) * (X * Lx + Y * Ly);
-        acc[i] += wq<T>(i) * eq - nP[i] * (X * Sa + Y * Sb + csP);
+        acc[i] += wq<T>(i) * eq - nP[i] * (X * Sa + Y * Sb);
     }
     T drho = 0, djx = 0, djy = 0;
 #pragma unroll

@@ -186,7 +186,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     const LevelPlan &F = P.lv[P.L - 1];
     const DevLevel &FL = c->dev.lv[P.L - 1];
     M.n = P.n;
-    M.Np = (P.n + kTileRows - 1) / kTileRows * kTileRows;  // whole tiles of rows
+    M.Np = (P.n + 31) / 32 * 32;
     M.n_wall = P.n_wall;
     M.ring_start = P.ring_start;
     M.n_ring = P.n_ring;
@@ -207,32 +207,16 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
             if (P.col[k] != old) ks.push_back(k);
         return ks;
     };
-    // halo list of tile t: its own kTileRows rows first (slot = row - first
-    // row; rows past the mesh end point at its last node), then the sorted
-    // nodes outside the tile that its rows touch
     for (int t = 0; t < M.n_tiles; t++) {
-        const int r0 = t * kTileRows, r1 = std::min(P.n, r0 + kTileRows);
-        std::vector<int> ext;
-        for (int r = r0; r < r1; r++)
-            for (int k : off_diag(P.perm[r])) {
-                int col = P.inv[P.col[k]];
-                if (col < r0 || col >= r1) ext.push_back(col);
-            }
-        std::sort(ext.begin(), ext.end());
-        ext.erase(std::unique(ext.begin(), ext.end()), ext.end());
         std::vector<int> &h = halo[t];
-        for (int r = r0; r < r0 + kTileRows; r++) h.push_back(std::min(r, P.n - 1));
-        h.insert(h.end(), ext.begin(), ext.end());
+        for (int r = t * kTileRows; r < std::min(P.n, (t + 1) * kTileRows); r++)
+            for (int k : off_diag(P.perm[r])) h.push_back(P.inv[P.col[k]]);
+        std::sort(h.begin(), h.end());
+        h.erase(std::unique(h.begin(), h.end()), h.end());
         hptr[t + 1] = hptr[t] + int(h.size());
         hnodes.insert(hnodes.end(), h.begin(), h.end());
         M.max_halo = std::max(M.max_halo, int(h.size()));
     }
-    auto local_slot = [&](int t, int col) {
-        const int r0 = t * kTileRows;
-        if (col >= r0 && col < std::min(P.n, r0 + kTileRows)) return col - r0;
-        const std::vector<int> &h = halo[t];
-        return kTileRows + int(std::lower_bound(h.begin() + kTileRows, h.end(), col) - (h.begin() + kTileRows));
-    };
     std::vector<int> sptr(M.n_slices), slen(M.n_slices);
     std::vector<E> ent;
     auto set_col = [](E &v, int col) {
@@ -253,12 +237,14 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
         ent.resize(base + size_t(32) * len);
         for (int l = 0; l < 32; l++) {
             int r = sl * 32 + l;
+            const std::vector<int> *h = r < P.n ? &halo[r / kTileRows] : nullptr;
             for (int e = 0; e < len; e++) {
                 E v{};
                 if (e < int(rows[l].size())) {
                     int k = rows[l][e];
                     v.x = T(P.sx[k]); v.y = T(P.sy[k]); v.z = T(P.cc[k]);
-                    set_col(v, local_slot(r / kTileRows, P.inv[P.col[k]]));
+                    int col = P.inv[P.col[k]];
+                    set_col(v, int(std::lower_bound(h->begin(), h->end(), col) - h->begin()));
                 } else {
                     v.x = v.y = v.z = T(0);  // padding: zero coefficients on a valid slot
                     set_col(v, 0);
@@ -269,12 +255,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     }
     M.halo_ptr = upload(c, hptr);
     M.halo_nodes = upload(c, hnodes);
-    for (int t = 0; t < M.n_tiles; t++) {
-        int sl = t * kTileRows / 32, last = sl + kTileRows / 32 - 1;
-        M.max_tile_ent = std::max(M.max_tile_ent, sptr[last] + 32 * slen[last] - sptr[sl]);
-    }
-    // shared memory per tile: operator entries, then the halo state (plane-major)
-    M.smem_bytes = size_t(M.max_tile_ent) * sizeof(E) + size_t(M.max_halo) * 9 * sizeof(T);
+    M.smem_bytes = size_t(M.max_halo) * 9 * sizeof(T);
     if (M.smem_bytes > 200 * 1024) throw CudaError{"mesh tiles touch too many nodes for shared memory"};
     configure_fv<T>(M.smem_bytes);
     M.ent = upload(c, ent);

@@ -37,7 +37,7 @@ struct DevMesh {
     int *slice_ptr = nullptr, *slice_len = nullptr;
     // tiles of kTileRows consecutive rows; tile t touches the sorted nodes
     // halo_nodes[halo_ptr[t] .. halo_ptr[t+1]) and entry columns index that list
-    int n_tiles = 0, max_halo = 0, max_tile_ent = 0;
+    int n_tiles = 0, max_halo = 0;
     int *halo_ptr = nullptr, *halo_nodes = nullptr;
     size_t smem_bytes = 0;
     void *Q0 = nullptr, *Q1 = nullptr;  // [12][n_ring] Eq. 9 data at t and t + 1

@@ -436,63 +436,38 @@ __device__ __forceinline__ void unpack(const double4_32a &e, double &sx, double 
 constexpr int kFvThreads = kTileRows;
 constexpr int kFvGroup = 2;
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
                                                    const int *__restrict__ slice_ptr,
                                                    const int *__restrict__ slice_len,
                                                    const typename Ent<T>::type *__restrict__ ent,
                                                    const int *__restrict__ halo_ptr,
-                                                   const int *__restrict__ halo_nodes, int max_tile_ent, T dt,
-                                                   T dt_tau, int n_wall, int ring_start, int n_ring,
+                                                   const int *__restrict__ halo_nodes, T dt, T dt_tau,
+                                                   int n_wall, int ring_start, int n_ring,
                                                    const T *__restrict__ Q0, const T *__restrict__ Q1, T theta_next,
                                                    T scale5, int star)
 {
-    using E = typename Ent<T>::type;
     extern __shared__ __align__(16) unsigned char fv_smem[];
-    E *s_ent = reinterpret_cast<E *>(fv_smem);
-    T *sh = reinterpret_cast<T *>(s_ent + max_tile_ent);
+    T *sh = reinterpret_cast<T *>(fv_smem);
     // Let the next sub-step's blocks start as soon as SM slots free up; they
     // only read constant operator data until their griddepcontrol.wait.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int row0 = blockIdx.x * kTileRows;
-    const int sl0 = row0 >> 5;
-    const int e_begin = slice_ptr[sl0];
-    const int e_end = slice_ptr[sl0 + kTileRows / 32 - 1] + 32 * slice_len[sl0 + kTileRows / 32 - 1];
-    {
-        // the tile's operator entries (one contiguous block) stream into shared
-        // memory while the previous sub-step may still be running
-        const int chunks = (e_end - e_begin) * int(sizeof(E) / 16);
-        const char *src = reinterpret_cast<const char *>(ent + e_begin);
-        for (int c = threadIdx.x; c < chunks; c += kFvThreads)
-            cp_async16(reinterpret_cast<char *>(s_ent) + 16 * c, src + 16 * c);
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    }
     const int h0 = halo_ptr[blockIdx.x], hn = halo_ptr[blockIdx.x + 1] - h0;
-    const int r = row0 + threadIdx.x;
-    const int sl = r >> 5;
-    const int base = slice_ptr[sl] - e_begin + (r & 31), len = slice_len[sl];
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rr = r < n ? r : n - 1;
+    const int sl = rr >> 5;
+    const int base = slice_ptr[sl] + (rr & 31), len = slice_len[sl];
     // wait until the previous sub-step (which wrote g) has completed
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    // halo state: slots 0..kTileRows-1 are the tile's own rows (contiguous),
-    // the rest the outside nodes its rows touch
-    for (int h = threadIdx.x; h < hn; h += kFvThreads) {
+    T r1P, uPx, uPy, nP[9];
+    load_mesh(g, Np, rr, r1P, uPx, uPy, nP);  // issued before the halo staging
+    for (int h = threadIdx.x; h < hn; h += blockDim.x) {
         const int node = halo_nodes[h0 + h];
 #pragma unroll
         for (int i = 0; i < 9; i++) sh[i * hn + h] = g[size_t(i) * Np + node];
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     if (r >= n) return;
-    T r1P = sh[threadIdx.x], uPx = sh[hn + threadIdx.x], uPy = sh[2 * hn + threadIdx.x], nP[9];
-#pragma unroll
-    for (int i = 3; i < 9; i++) nP[i] = sh[i * hn + threadIdx.x];
-    neq_complete(nP);
     // own node: no streaming term (g(P) - g(P) = 0), collision weight C_PP = 11/18
     T acc[9];
     const T csP = dt_tau * T(11.0 / 18.0);
@@ -505,7 +480,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
 #pragma unroll
         for (int j = 0; j < kFvGroup; j++) {
             if (e0 + j < len) {
-                unpack(s_ent[base + 32 * (e0 + j)], sx[j], sy[j], c[j], k[j]);
+                unpack(ent[base + 32 * (e0 + j)], sx[j], sy[j], c[j], k[j]);
             } else {
                 sx[j] = sy[j] = c[j] = T(0);
                 k[j] = 0;
@@ -837,8 +812,7 @@ template <typename T> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k_fv<T>, (const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
                        (const int *)m.slice_ptr, (const int *)m.slice_len, (const typename Ent<T>::type *)m.ent,
-                       (const int *)m.halo_ptr, (const int *)m.halo_nodes, m.max_tile_ent, dt, dt_tau, m.n_wall,
-                       m.ring_start,
+                       (const int *)m.halo_ptr, (const int *)m.halo_nodes, dt, dt_tau, m.n_wall, m.ring_start,
                        m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5, star);
 }
 

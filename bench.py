@@ -7,7 +7,7 @@ configuration: 2048x1024 coarse level with two nested factor-2 boxes
 (1025x513 nodes each), chord 200 finest units, 200 704-node O-mesh,
 Re 1000, Ma 0.1, AoA 0.  Synthetic geometry (analytic NACA 0012), seed 0.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64|fp16s]
                 [--impl ours|reference]
 Under torchrun (N > 1) each rank runs an independent replica (the step does
 not shard across GPUs here); value = all ranks' node updates / max time.
@@ -192,7 +192,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16s"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64, e2e and CPU legs")
     args = ap.parse_args()
@@ -255,10 +255,11 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "levels": case.levels.tolist(), "mesh_nodes": case.n_nodes,
                        "n_sub": n_sub, "Re": case.Re, "Ma": case.Ma, "aoa_deg": case.aoa_deg,
                        "precision": args.precision, "node_updates_per_step": per_step,
+                       "lattice_storage": {"fp64": "f64", "fp32": "f32", "fp16s": "f16 shifted"}[args.precision],
                        "l2": "working set per coarse step (~160 MB FP32) exceeds L2; the finite-volume "
                              "state (~37 MB) is re-read n_sub times per finest step and stays L2-resident",
                        "parallelism": f"replicas x{ws}"},
@@ -267,13 +268,13 @@ def main():
             "cl_mean": float(cl.mean()) if len(cl) else None}
 
     if rank == 0 and not args.no_extras:
-        # ---- FP64 leg on the same workload
-        other = "fp64" if args.precision == "fp32" else "fp32"
+        # ---- the other precisions on the same workload
         k2 = max(10, args.steps // 4)
-        s2, per2, _, ms2, _, _ = measure_gpu(H, case, other, k2, args.warmup, stream)
-        s2.close()
-        line[other] = {"value": per2 * k2 / (ms2 * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms2 / k2,
-                       "steps": k2}
+        for other in [p for p in ("fp64", "fp32", "fp16s") if p != args.precision]:
+            s2, per2, _, ms2, cd2, cl2 = measure_gpu(H, case, other, k2, args.warmup, stream)
+            s2.close()
+            line[other] = {"value": per2 * k2 / (ms2 * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms2 / k2,
+                           "steps": k2}
         # ---- end to end through the public API from host buffers: create
         # (host geometry -> device tables and state), K steps each followed by a
         # D2H read of the new force sample, final D2H of the mesh fields

@@ -41,6 +41,8 @@ extern "C" {
 
 #define HLBM_FP64 0 /* populations and arithmetic in double precision          */
 #define HLBM_FP32 1 /* populations stored as f - w_i in float, float arithmetic */
+#define HLBM_FP16S 2 /* lattice populations stored as 16-bit floats of (f - f^eq(1, u0)) / w_i
+                        (shifted by the free stream), mesh state and arithmetic in float */
 
 /* Node kinds of the triangular mesh. */
 #define HLBM_NODE_FLUID 0

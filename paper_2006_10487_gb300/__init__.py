@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libhlbm.so")
 
 HLBM_OK, HLBM_EINVAL, HLBM_ENOMEM, HLBM_ECUDA = 0, -1, -2, -3
 HLBM_EUNSTABLE, HLBM_ETIMEOUT, HLBM_ESTATE, HLBM_ENOTIMPL = -4, -5, -6, -7
-HLBM_FP64, HLBM_FP32 = 0, 1
-PRECISIONS = {"fp64": HLBM_FP64, "fp32": HLBM_FP32}
+HLBM_FP64, HLBM_FP32, HLBM_FP16S = 0, 1, 2
+PRECISIONS = {"fp64": HLBM_FP64, "fp32": HLBM_FP32, "fp16s": HLBM_FP16S}
 
 
 class HlbmError(RuntimeError):

@@ -84,55 +84,55 @@ void set_phase(hlbm_ctx *c, long k)
     D.m.gcur = int((k * per) & 1);
 }
 
-template <typename T> void advance(hlbm_ctx *c, int lvl, double theta, cudaStream_t s);
+template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double theta, cudaStream_t s);
 
 // One step of level lvl on its own clock; theta: parent-time fraction at the
 // end of the step (refills the boundary ring by prolongation).
-template <typename T> void level_step(hlbm_ctx *c, int lvl, double theta, cudaStream_t s)
+template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double theta, cudaStream_t s)
 {
     DevCtx &D = c->dev;
     bool hybrid = (lvl == D.L - 1) && D.m.n > 0;
     if (hybrid) {
-        launch_ring_interp<T>(D, false, s);  // Eq. 9 data at t
-        launch_hole_interp<T>(D, s);         // Eq. 4: post-collision of the hole boundary
+        launch_ring_interp<T, S>(D, false, s);  // Eq. 9 data at t
+        launch_hole_interp<T, S>(D, s);         // Eq. 4: post-collision of the hole boundary
         c->launches += 1 + (D.m.n_is > 0);
     }
-    launch_collide<T>(D, lvl, s);  // Eq. 1
+    launch_collide<T, S>(D, lvl, s);  // Eq. 1
     D.lv[lvl].parity ^= 1;
-    if (lvl == 0) launch_outer_bc<T>(D, s);
-    else launch_prolong<T>(D, lvl, theta, s);
+    if (lvl == 0) launch_outer_bc<T, S>(D, s);
+    else launch_prolong<T, S>(D, lvl, theta, s);
     c->launches += 2;
     if (hybrid) {
-        launch_ring_interp<T>(D, true, s);  // Eq. 9 data at t + 1, ring state of sub-step 0
+        launch_ring_interp<T, S>(D, true, s);  // Eq. 9 data at t + 1, ring state of sub-step 0
         for (int m = 0; m < D.n_sub; m++) {  // Eq. 3, Eq. 5-7, wall rule
-            launch_fv<T>(D, m, s);
+            launch_fv<T, S>(D, m, s);
             D.m.gcur ^= 1;
         }
         c->launches += 1 + D.n_sub;
     }
 }
 
-template <typename T> void advance(hlbm_ctx *c, int lvl, double theta, cudaStream_t s)
+template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double theta, cudaStream_t s)
 {
     DevCtx &D = c->dev;
     bool child = lvl < D.L - 1;
-    if (child) launch_snapshot<T>(D, lvl, false, s);
-    level_step<T>(c, lvl, theta, s);
+    if (child) launch_snapshot<T, S>(D, lvl, false, s);
+    level_step<T, S>(c, lvl, theta, s);
     if (child) {
-        launch_snapshot<T>(D, lvl, true, s);
-        advance<T>(c, lvl + 1, 0.5, s);
-        advance<T>(c, lvl + 1, 1.0, s);
-        launch_restrict<T>(D, lvl, s);
+        launch_snapshot<T, S>(D, lvl, true, s);
+        advance<T, S>(c, lvl + 1, 0.5, s);
+        advance<T, S>(c, lvl + 1, 1.0, s);
+        launch_restrict<T, S>(D, lvl, s);
         c->launches += 3;
     }
 }
 
-template <typename T> void coarse_step(hlbm_ctx *c, cudaStream_t s)
+template <typename T, typename S> void coarse_step(hlbm_ctx *c, cudaStream_t s)
 {
     long before = c->launches;
-    advance<T>(c, 0, 0.0, s);
+    advance<T, S>(c, 0, 0.0, s);
     if (c->dev.m.n > 0) {
-        launch_forces<T>(c->dev, s);
+        launch_forces<T, S>(c->dev, s);
         c->launches += 2;
     }
     c->launches_per_step = c->launches - before;
@@ -140,27 +140,28 @@ template <typename T> void coarse_step(hlbm_ctx *c, cudaStream_t s)
 
 void enqueue_coarse_step(hlbm_ctx *c, cudaStream_t s)
 {
-    if (c->plan.precision == HLBM_FP32) coarse_step<float>(c, s);
-    else coarse_step<double>(c, s);
+    if (c->plan.precision == HLBM_FP32) coarse_step<float, float>(c, s);
+    else if (c->plan.precision == HLBM_FP16S) coarse_step<float, __half>(c, s);
+    else coarse_step<double, double>(c, s);
 }
 
-template <typename T> void init_state(hlbm_ctx *c)
+template <typename T, typename S> void init_state(hlbm_ctx *c)
 {
     DevCtx &D = c->dev;
     const Plan &P = c->plan;
     cudaStream_t s = c->stream;
     for (int l = 0; l < D.L; l++) {
         D.lv[l].parity = 0;
-        launch_init_level<T>(D, l, P.seed, P.perturb, s);
+        launch_init_level<T, S>(D, l, P.seed, P.perturb, s);
     }
     // make the initial state consistent across the interfaces
-    launch_outer_bc<T>(D, s);
+    launch_outer_bc<T, S>(D, s);
     for (int l = 1; l < D.L; l++) {
-        launch_snapshot<T>(D, l - 1, false, s);
-        launch_snapshot<T>(D, l - 1, true, s);
-        launch_prolong<T>(D, l, 0.0, s);
+        launch_snapshot<T, S>(D, l - 1, false, s);
+        launch_snapshot<T, S>(D, l - 1, true, s);
+        launch_prolong<T, S>(D, l, 0.0, s);
     }
-    for (int l = D.L - 2; l >= 0; l--) launch_restrict<T>(D, l, s);
+    for (int l = D.L - 2; l >= 0; l--) launch_restrict<T, S>(D, l, s);
     if (D.m.n > 0) {
         // mesh: rho = 1 + perturb xi, u = (u0, 0) (0 on wall nodes), f^neq = 0;
         // planes (rho - 1, ux, uy, f^neq_3..8), device order
@@ -173,8 +174,8 @@ template <typename T> void init_state(hlbm_ctx *c)
         ck(cudaMemcpyAsync(D.m.g[0], g.data(), g.size() * sizeof(T), cudaMemcpyHostToDevice, s), "upload mesh state");
         ck(cudaStreamSynchronize(s), "sync");  // g (host) goes out of scope
         D.m.gcur = 0;
-        launch_ring_interp<T>(D, false, s);  // Q0
-        launch_ring_interp<T>(D, true, s);   // Q1 and the ring state at theta = 0
+        launch_ring_interp<T, S>(D, false, s);  // Q0
+        launch_ring_interp<T, S>(D, true, s);   // Q1 and the ring state at theta = 0
     }
     ck(cudaGetLastError(), "init kernels");
 }
@@ -257,7 +258,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     M.halo_nodes = upload(c, hnodes);
     M.smem_bytes = size_t(M.max_halo) * 9 * sizeof(T);
     if (M.smem_bytes > 200 * 1024) throw CudaError{"mesh tiles touch too many nodes for shared memory"};
-    configure_fv<T>(M.smem_bytes);
+    configure_fv<T, T>(M.smem_bytes);
     M.ent = upload(c, ent);
     M.slice_ptr = upload(c, sptr);
     M.slice_len = upload(c, slen);
@@ -299,7 +300,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     M.inv = upload(c, P.inv);
 }
 
-template <typename T> void build_device(hlbm_ctx *c)
+template <typename T, typename S> void build_device(hlbm_ctx *c)
 {
     Plan &P = c->plan;
     DevCtx &D = c->dev;
@@ -309,6 +310,15 @@ template <typename T> void build_device(hlbm_ctx *c)
     D.n_sub = P.n_sub;
     D.dt_u = P.n_sub > 0 ? 1.0 / P.n_sub : 0.0;
     D.qdyn = P.qdyn;
+    // FP16S storage shift: the free-stream equilibrium minus the weights
+    {
+        static const double W[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+        static const int CXh[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+        for (int i = 0; i < 9; i++) {
+            double cu = CXh[i] * P.u0;
+            D.shift.s[i] = float(W[i] * (3.0 * cu + 4.5 * cu * cu - 1.5 * P.u0 * P.u0));
+        }
+    }
     size_t maxnodes = size_t(std::max(P.n, 1));
     for (int l = 0; l < P.L; l++) {
         const LevelPlan &lp = P.lv[l];
@@ -317,7 +327,7 @@ template <typename T> void build_device(hlbm_ctx *c)
         dl.ny = lp.ny;
         dl.pitch = (lp.nx + 2 + 31) / 32 * 32;
         dl.stride = size_t(lp.ny + 2) * dl.pitch;
-        dl.f = dalloc(c, 9 * dl.stride * sizeof(T));
+        dl.f = dalloc(c, 9 * dl.stride * sizeof(S));
         dl.tau = lp.tau;
         if (!lp.hx0.empty()) {
             dl.hx0 = upload(c, lp.hx0);
@@ -341,7 +351,7 @@ template <typename T> void build_device(hlbm_ctx *c)
     ck(cudaMemsetAsync(D.force_counter, 0, 2 * sizeof(int), c->stream), "memset");
     c->d_out_n = maxnodes;
     c->d_out = (double *)dalloc(c, maxnodes * 12 * sizeof(double));
-    init_state<T>(c);
+    init_state<T, S>(c);
 }
 
 void capture_graphs(hlbm_ctx *c)
@@ -416,8 +426,9 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
     c->dev.force_cap = o.force_cap > 0 ? o.force_cap : 4096;
     try {
         ck(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "stream create");
-        if (c->plan.precision == HLBM_FP32) build_device<float>(c);
-        else build_device<double>(c);
+        if (c->plan.precision == HLBM_FP32) build_device<float, float>(c);
+        else if (c->plan.precision == HLBM_FP16S) build_device<float, __half>(c);
+        else build_device<double, double>(c);
         if (c->use_graphs) capture_graphs(c);
         ck(cudaStreamSynchronize(c->stream), "sync after create");
     } catch (const CudaError &e) {
@@ -491,6 +502,13 @@ int hlbm_forces(hlbm_ctx *c, double *cd, double *cl, int cap, int *n_written)
     return HLBM_OK;
 }
 
+static void fields_dispatch(hlbm_ctx *c, int grid, double *rho, double *ux, double *uy, double *pop)
+{
+    if (c->plan.precision == HLBM_FP32) launch_fields<float, float>(c->dev, grid, rho, ux, uy, pop, c->stream);
+    else if (c->plan.precision == HLBM_FP16S) launch_fields<float, __half>(c->dev, grid, rho, ux, uy, pop, c->stream);
+    else launch_fields<double, double>(c->dev, grid, rho, ux, uy, pop, c->stream);
+}
+
 static int readback(hlbm_ctx *c, int grid, double *rho, double *ux, double *uy, double *pop, size_t cap)
 {
     if (!c) return HLBM_EINVAL;
@@ -504,13 +522,11 @@ static int readback(hlbm_ctx *c, int grid, double *rho, double *ux, double *uy, 
     try {
         double *d = c->d_out;
         if (pop) {
-            if (c->plan.precision == HLBM_FP32) launch_fields<float>(c->dev, grid, nullptr, nullptr, nullptr, d, c->stream);
-            else launch_fields<double>(c->dev, grid, nullptr, nullptr, nullptr, d, c->stream);
+            fields_dispatch(c, grid, nullptr, nullptr, nullptr, d);
             ck(cudaGetLastError(), "fields kernel");
             ck(cudaMemcpyAsync(pop, d, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
         } else {
-            if (c->plan.precision == HLBM_FP32) launch_fields<float>(c->dev, grid, d, d + n, d + 2 * n, nullptr, c->stream);
-            else launch_fields<double>(c->dev, grid, d, d + n, d + 2 * n, nullptr, c->stream);
+            fields_dispatch(c, grid, d, d + n, d + 2 * n, nullptr);
             ck(cudaGetLastError(), "fields kernel");
             if (rho) ck(cudaMemcpyAsync(rho, d, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
             if (ux) ck(cudaMemcpyAsync(ux, d + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
@@ -561,14 +577,14 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
         // algorithmic bytes of one finite-volume sub-step: the 9 state values of
         // every node read and written, one (s_x, s_y, C, column) entry per
         // off-diagonal operator coefficient
-        double vb = P.precision == HLBM_FP32 ? 4.0 : 8.0;
+        double vb = P.precision == HLBM_FP64 ? 8.0 : 4.0;  // the mesh is FP32 in FP16S mode
         *value = double(P.n) * 18.0 * vb + double(P.col.size() - size_t(P.n)) * 4.0 * vb;
     } else if (k.size() == 14 && k.compare(0, 13, "collide_bytes") == 0) {
         int l = k[13] - '0';
         if (l < 0 || l >= P.L) return HLBM_EINVAL;
         double nn = double(P.lv[l].nx) * P.lv[l].ny;
         for (size_t y = 0; y < P.lv[l].hx0.size(); y++) nn -= P.lv[l].hx1[y] - P.lv[l].hx0[y];
-        *value = nn * 18.0 * (P.precision == HLBM_FP32 ? 4.0 : 8.0);
+        *value = nn * 18.0 * (P.precision == HLBM_FP64 ? 8.0 : (P.precision == HLBM_FP32 ? 4.0 : 2.0));
     }
     else return HLBM_EINVAL;
     return HLBM_OK;
@@ -637,16 +653,17 @@ int hlbm_time_kernel(hlbm_ctx *c, const char *kernel, int reps, double *avg_ms)
     try {
         ck(cudaEventCreate(&e0), "event");
         ck(cudaEventCreate(&e1), "event");
-        bool f32 = c->plan.precision == HLBM_FP32;
+        const int prec = c->plan.precision;
         auto one = [&](int r) {
             if (lvl < 0) {
                 int m = r % std::max(1, c->dev.n_sub);
-                if (f32) launch_fv<float>(c->dev, m, c->stream);
-                else launch_fv<double>(c->dev, m, c->stream);
+                if (prec == HLBM_FP64) launch_fv<double, double>(c->dev, m, c->stream);
+                else launch_fv<float, float>(c->dev, m, c->stream);
                 c->dev.m.gcur ^= 1;
             } else {
-                if (f32) launch_collide<float>(c->dev, lvl, c->stream);
-                else launch_collide<double>(c->dev, lvl, c->stream);
+                if (prec == HLBM_FP32) launch_collide<float, float>(c->dev, lvl, c->stream);
+                else if (prec == HLBM_FP16S) launch_collide<float, __half>(c->dev, lvl, c->stream);
+                else launch_collide<double, double>(c->dev, lvl, c->stream);
                 c->dev.lv[lvl].parity ^= 1;
             }
         };

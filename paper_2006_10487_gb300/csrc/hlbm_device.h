@@ -2,6 +2,7 @@
 // (implemented in kernels.cu for float and double storage).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -53,8 +54,14 @@ struct DevMesh {
     int *inv = nullptr;                  // input node -> device node
 };
 
+// FP16S lattice storage shift: s_i = f^eq_i(1, (u0, 0)) - w_i (free stream).
+struct LatShift {
+    float s[9];
+};
+
 struct DevCtx {
     int L = 0;
+    LatShift shift = {};
     DevLevel lv[8];
     DevMesh m;
     double u0 = 0, tau_u = 0, dt_u = 0, qdyn = 0;
@@ -68,19 +75,19 @@ struct DevCtx {
 
 constexpr int kTileRows = 128;  // rows per finite-volume tile (= threads per block)
 
-// Raises the kernel's dynamic shared-memory limit to `bytes` (once per process).
-template <typename T> void configure_fv(size_t bytes);
-
-template <typename T> void launch_init_level(const DevCtx &, int c, unsigned long long seed, double perturb, cudaStream_t);
-template <typename T> void launch_collide(const DevCtx &, int c, cudaStream_t);
-template <typename T> void launch_outer_bc(const DevCtx &, cudaStream_t);
-template <typename T> void launch_snapshot(const DevCtx &, int c, bool into_b, cudaStream_t);
-template <typename T> void launch_prolong(const DevCtx &, int c_fine, double theta, cudaStream_t);
-template <typename T> void launch_restrict(const DevCtx &, int c_coarse, cudaStream_t);
-template <typename T> void launch_ring_interp(const DevCtx &, bool q1_and_star, cudaStream_t);
-template <typename T> void launch_hole_interp(const DevCtx &, cudaStream_t);
-template <typename T> void launch_fv(const DevCtx &, int m, cudaStream_t);
-template <typename T> void launch_forces(const DevCtx &, cudaStream_t);
-template <typename T> void launch_fields(const DevCtx &, int grid, double *rho, double *ux, double *uy, double *pop, cudaStream_t);
+// Launchers, T = arithmetic type, S = lattice storage type (T, or __half for
+// FP16S); raises the FV kernel's dynamic shared-memory limit (configure_fv).
+template <typename T, typename S> void configure_fv(size_t bytes);
+template <typename T, typename S> void launch_init_level(const DevCtx &, int c, unsigned long long seed, double perturb, cudaStream_t);
+template <typename T, typename S> void launch_collide(const DevCtx &, int c, cudaStream_t);
+template <typename T, typename S> void launch_outer_bc(const DevCtx &, cudaStream_t);
+template <typename T, typename S> void launch_snapshot(const DevCtx &, int c, bool into_b, cudaStream_t);
+template <typename T, typename S> void launch_prolong(const DevCtx &, int c_fine, double theta, cudaStream_t);
+template <typename T, typename S> void launch_restrict(const DevCtx &, int c_coarse, cudaStream_t);
+template <typename T, typename S> void launch_ring_interp(const DevCtx &, bool q1_and_star, cudaStream_t);
+template <typename T, typename S> void launch_hole_interp(const DevCtx &, cudaStream_t);
+template <typename T, typename S> void launch_fv(const DevCtx &, int m, cudaStream_t);
+template <typename T, typename S> void launch_forces(const DevCtx &, cudaStream_t);
+template <typename T, typename S> void launch_fields(const DevCtx &, int grid, double *rho, double *ux, double *uy, double *pop, cudaStream_t);
 
 }  // namespace hlbm

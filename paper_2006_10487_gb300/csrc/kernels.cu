@@ -7,6 +7,7 @@
 // Paper passages: Eq. 1-2 (lattice), Eq. 3 (finite volume), Eq. 4-9 (overlap
 // coupling), Section 4 (refinement boxes, wall, outer conditions),
 // Eq. 10-11 (forces).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -138,17 +139,40 @@ template <int P> __device__ __forceinline__ size_t wr_idx(int i, size_t n, int p
 
 __device__ __forceinline__ size_t node(int x, int y, int pitch) { return size_t(y + 1) * pitch + x + 1; }
 
-template <typename T, int P>
-__device__ __forceinline__ void load_state(const T *f, size_t n, int pitch, size_t stride, T d[9])
+// Lattice storage.  float / double levels store d_i = f_i - w_i as is.  FP16S
+// levels store the 16-bit float (d_i - s_i) / w_i with s_i = f^eq_i(1, (u0, 0))
+// - w_i, the free stream: small relative deviations, so that the 11-bit
+// significand is spent where the flow differs from the free stream.
+template <typename T> __device__ __forceinline__ T inv_w(int i)
 {
-#pragma unroll
-    for (int i = 0; i < 9; i++) d[i] = f[st_idx<P>(i, n, pitch, stride)];
+    return i == 0 ? T(9.0 / 4.0) : (i <= 4 ? T(9.0) : T(36.0));
 }
-template <typename T, int P>
-__device__ __forceinline__ void store_state(T *f, size_t n, int pitch, size_t stride, const T d[9])
+template <typename S> struct Codec {
+    template <typename T> __device__ static T get(const S *f, size_t k, int, const LatShift &) { return T(f[k]); }
+    template <typename T> __device__ static void put(S *f, size_t k, int, T v, const LatShift &) { f[k] = S(v); }
+};
+template <> struct Codec<__half> {
+    template <typename T> __device__ static T get(const __half *f, size_t k, int i, const LatShift &sh)
+    {
+        return wq<T>(i) * T(__half2float(f[k])) + T(sh.s[i]);
+    }
+    template <typename T> __device__ static void put(__half *f, size_t k, int i, T v, const LatShift &sh)
+    {
+        f[k] = __float2half_rn(float((v - T(sh.s[i])) * inv_w<T>(i)));
+    }
+};
+
+template <typename T, typename S, int P>
+__device__ __forceinline__ void load_state(const S *f, size_t n, int pitch, size_t stride, T d[9], const LatShift &sh)
 {
 #pragma unroll
-    for (int i = 0; i < 9; i++) f[st_idx<P>(i, n, pitch, stride)] = d[i];
+    for (int i = 0; i < 9; i++) d[i] = Codec<S>::template get<T>(f, st_idx<P>(i, n, pitch, stride), i, sh);
+}
+template <typename T, typename S, int P>
+__device__ __forceinline__ void store_state(S *f, size_t n, int pitch, size_t stride, const T d[9], const LatShift &sh)
+{
+#pragma unroll
+    for (int i = 0; i < 9; i++) Codec<S>::template put<T>(f, st_idx<P>(i, n, pitch, stride), i, d[i], sh);
 }
 
 // splitmix64 (Steele, Lea and Flood): uniform deviate in [-1, 1)
@@ -164,9 +188,9 @@ __device__ __forceinline__ double deviate(uint64_t seed, uint64_t grid, uint64_t
 // -------------------------------------------------------------- kernels ----
 // Initial lattice state: f = f^eq(1 + perturb xi, (u0, 0)); hole nodes and the
 // halo hold NaN so that any read of them shows up in the results.
-template <typename T>
-__global__ void k_init_level(T *f, int nx, int ny, int pitch, size_t stride, const int *hx0, const int *hx1,
-                             uint64_t seed, int grid, double perturb, double u0)
+template <typename T, typename S>
+__global__ void k_init_level(S *f, int nx, int ny, int pitch, size_t stride, const int *hx0, const int *hx1,
+                             uint64_t seed, int grid, double perturb, double u0, LatShift sh)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x - 1, y = int(blockIdx.y) - 1;
     if (x > nx) return;
@@ -175,31 +199,32 @@ __global__ void k_init_level(T *f, int nx, int ny, int pitch, size_t stride, con
     bool hole = inside && hx0 && x >= hx0[y] && x < hx1[y];
     if (!inside || hole) {
 #pragma unroll
-        for (int i = 0; i < 9; i++) f[size_t(i) * stride + n] = T(NAN);
+        for (int i = 0; i < 9; i++) Codec<S>::template put<T>(f, size_t(i) * stride + n, i, T(NAN), sh);
         return;
     }
     double rho = 1.0 + perturb * deviate(seed, uint64_t(grid), uint64_t(y) * nx + x);
 #pragma unroll
-    for (int i = 0; i < 9; i++) f[size_t(i) * stride + n] = T(deq<double>(i, rho, u0, 0.0));
+    for (int i = 0; i < 9; i++) Codec<S>::template put<T>(f, size_t(i) * stride + n, i, T(deq<double>(i, rho, u0, 0.0)), sh);
 }
 
 // Eq. 1: BGK collision and (implicit, AA-pattern) streaming on one level.
-template <typename T, int P>
-__global__ void __launch_bounds__(128) k_collide(T *__restrict__ f, int nx, int ny, int pitch, size_t stride,
-                                                 T omega, const int *__restrict__ hx0, const int *__restrict__ hx1)
+template <typename T, typename S, int P>
+__global__ void __launch_bounds__(128) k_collide(S *__restrict__ f, int nx, int ny, int pitch, size_t stride,
+                                                 T omega, const int *__restrict__ hx0, const int *__restrict__ hx1,
+                                                 LatShift sh)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= nx) return;
     if (hx0 && x >= hx0[y] && x < hx1[y]) return;
     size_t n = node(x, y, pitch);
     T d[9];
-    load_state<T, P>(f, n, pitch, stride, d);
+    load_state<T, S, P>(f, n, pitch, stride, d, sh);
     T rho, ux, uy;
     moments(d, rho, ux, uy);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
         T post = d[i] - omega * (d[i] - deq<T>(i, rho, ux, uy));
-        f[wr_idx<P>(i, n, pitch, stride)] = post;
+        Codec<S>::template put<T>(f, wr_idx<P>(i, n, pitch, stride), i, post, sh);
     }
 }
 
@@ -209,8 +234,8 @@ __global__ void __launch_bounds__(128) k_collide(T *__restrict__ f, int nx, int 
 //   inlet (x = 0):        f^eq(rho_n, (u0, 0)) + f^neq_n
 //   outlet (x = nx - 1):  f^eq(1, u_n) + f^neq_n
 //   top / bottom:         f_n
-template <typename T, int P>
-__global__ void k_outer_bc(T *f, int nx, int ny, int pitch, size_t stride, T u0)
+template <typename T, typename S, int P>
+__global__ void k_outer_bc(S *f, int nx, int ny, int pitch, size_t stride, T u0, LatShift sh)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     int nper = 2 * nx + 2 * (ny - 2);
@@ -222,7 +247,7 @@ __global__ void k_outer_bc(T *f, int nx, int ny, int pitch, size_t stride, T u0)
     else { x = nx - 1; y = k - 2 * nx - (ny - 2) + 1; }
     int xn = min(max(x, 1), nx - 2), yn = min(max(y, 1), ny - 2);
     T d[9];
-    load_state<T, P>(f, node(xn, yn, pitch), pitch, stride, d);
+    load_state<T, S, P>(f, node(xn, yn, pitch), pitch, stride, d, sh);
     if (x == 0 || x == nx - 1) {
         T q[12];
         to_q(d, q);
@@ -230,7 +255,7 @@ __global__ void k_outer_bc(T *f, int nx, int ny, int pitch, size_t stride, T u0)
         else q[0] = T(1);
         from_q(q, T(1), d);
     }
-    store_state<T, P>(f, node(x, y, pitch), pitch, stride, d);
+    store_state<T, S, P>(f, node(x, y, pitch), pitch, stride, d, sh);
 }
 
 // Coarse node of band entry b: the lines y = coy and y = coy + cmy for
@@ -246,16 +271,16 @@ __device__ __forceinline__ void band_node(int b, int cox, int coy, int cmx, int 
 }
 
 // (rho, u, f^neq) of the parent level along its child's boundary band.
-template <typename T, int P>
-__global__ void k_snapshot(const T *f, int pitch, size_t stride, int cox, int coy, int cmx, int cmy, T *snap,
-                           int band_n)
+template <typename T, typename S, int P>
+__global__ void k_snapshot(const S *f, int pitch, size_t stride, int cox, int coy, int cmx, int cmy, T *snap,
+                           int band_n, LatShift sh)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= band_n) return;
     int X, Y;
     band_node(b, cox, coy, cmx, cmy, X, Y);
     T d[9], q[12];
-    load_state<T, P>(f, node(X, Y, pitch), pitch, stride, d);
+    load_state<T, S, P>(f, node(X, Y, pitch), pitch, stride, d, sh);
     to_q(d, q);
 #pragma unroll
     for (int m = 0; m < 12; m++) snap[size_t(m) * band_n + b] = q[m];
@@ -265,9 +290,9 @@ __global__ void k_snapshot(const T *f, int pitch, size_t stride, int cox, int co
 // takes f^eq(rho, u) + tau_f / (2 tau_c) f^neq from the parent band, linear
 // in time (theta) and, midway between coarse nodes, quadratic along the
 // ring through coarse nodes X-1, X, X+1 (weights -1/8, 3/4, 3/8).
-template <typename T, int P>
-__global__ void k_prolong(T *f, int nx, int ny, int pitch, size_t stride, const T *snapA, const T *snapB,
-                          int band_n, int cox, int coy, int cmx, int cmy, T theta, T scale)
+template <typename T, typename S, int P>
+__global__ void k_prolong(S *f, int nx, int ny, int pitch, size_t stride, const T *snapA, const T *snapB,
+                          int band_n, int cox, int coy, int cmx, int cmy, T theta, T scale, LatShift sh)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     int nper = 2 * nx + 2 * (ny - 2);
@@ -301,24 +326,24 @@ __global__ void k_prolong(T *f, int nx, int ny, int pitch, size_t stride, const 
     }
     T d[9];
     from_q(q, scale, d);
-    store_state<T, P>(f, node(i, j, pitch), pitch, stride, d);
+    store_state<T, S, P>(f, node(i, j, pitch), pitch, stride, d, sh);
 }
 
 // Refinement fine -> coarse: coarse nodes at least one cell inside the child
 // box take the coincident fine state with f^neq scaled by 2 tau_c / tau_f.
-template <typename T, int PC, int PF>
-__global__ void k_restrict(T *fc, int pitch_c, size_t stride_c, const T *ff, int pitch_f, size_t stride_f, int cox,
-                           int coy, int cmx, int cmy, T scale, const int *hx0, const int *hx1)
+template <typename T, typename S, int PC, int PF>
+__global__ void k_restrict(S *fc, int pitch_c, size_t stride_c, const S *ff, int pitch_f, size_t stride_f, int cox,
+                           int coy, int cmx, int cmy, T scale, const int *hx0, const int *hx1, LatShift sh)
 {
     int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
     if (a >= cmx - 1) return;
     int X = cox + 1 + a, Y = coy + 1 + b;
     if (hx0 && X >= hx0[Y] && X < hx1[Y]) return;  // over the hole: not computed
     T d[9], q[12];
-    load_state<T, PF>(ff, node(2 * (X - cox), 2 * (Y - coy), pitch_f), pitch_f, stride_f, d);
+    load_state<T, S, PF>(ff, node(2 * (X - cox), 2 * (Y - coy), pitch_f), pitch_f, stride_f, d, sh);
     to_q(d, q);
     from_q(q, scale, d);
-    store_state<T, PC>(fc, node(X, Y, pitch_c), pitch_c, stride_c, d);
+    store_state<T, S, PC>(fc, node(X, Y, pitch_c), pitch_c, stride_c, d, sh);
 }
 
 // Eq. 9: (rho, u, f^neq) at the unstructured interpolation nodes from their
@@ -326,9 +351,9 @@ __global__ void k_restrict(T *fc, int pitch_c, size_t stride_c, const T *ff, int
 // sets the ring nodes of the read buffer to the Eq. 5-6 state at theta = 0:
 // (rho, u, (1 - 1/(2 tau_s)) f^neq) of the data at t (Q0).
 // 16 lanes per ring node: lane k < 9 takes donor k; xor-shuffle sum.
-template <typename T, int P>
-__global__ void k_ring_interp(const T *f, int pitch, size_t stride, const int *don, const T *w, int n_ring,
-                              T *Q, const T *Q0, T *g, int Np, int ring_start, T scale5, int star)
+template <typename T, typename S, int P>
+__global__ void k_ring_interp(const S *f, int pitch, size_t stride, const int *don, const T *w, int n_ring,
+                              T *Q, const T *Q0, T *g, int Np, int ring_start, T scale5, int star, LatShift sh)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int r = t >> 4, k = t & 15;
@@ -339,7 +364,7 @@ __global__ void k_ring_interp(const T *f, int pitch, size_t stride, const int *d
     for (int m = 0; m < 12; m++) acc[m] = T(0);
     if (k < 9) {
         T d[9], q[12];
-        load_state<T, P>(f, size_t(don[9 * rr + k]), pitch, stride, d);
+        load_state<T, S, P>(f, size_t(don[9 * rr + k]), pitch, stride, d, sh);
         to_q(d, q);
         T wk = w[9 * rr + k];
 #pragma unroll
@@ -364,9 +389,9 @@ __global__ void k_ring_interp(const T *f, int pitch, size_t stride, const int *d
 // Eq. 4 with Eq. 8: post-collision state of the structured interpolation
 // nodes from six unstructured donors, written where the collision at parity
 // P would write it.  8 lanes per node: lane k < 6 takes donor k.
-template <typename T, int P>
-__global__ void k_hole_interp(T *f, int pitch, size_t stride, const int *is_n, const int *don, const T *w, int n_is,
-                              const T *g, int Np, T scale4)
+template <typename T, typename S, int P>
+__global__ void k_hole_interp(S *f, int pitch, size_t stride, const int *is_n, const int *don, const T *w, int n_is,
+                              const T *g, int Np, T scale4, LatShift sh)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int s = t >> 3, k = t & 7;
@@ -392,7 +417,9 @@ __global__ void k_hole_interp(T *f, int pitch, size_t stride, const int *is_n, c
     // lane k writes population k (lane 0 also population 8)
 #pragma unroll
     for (int i = 0; i < 9; i++)
-        if ((i & 7) == k) f[wr_idx<P>(i, n, pitch, stride)] = deq<T>(i, acc[0], acc[1], acc[2]) + scale4 * acc[3 + i];
+        if ((i & 7) == k)
+            Codec<S>::template put<T>(f, wr_idx<P>(i, n, pitch, stride), i,
+                                      deq<T>(i, acc[0], acc[1], acc[2]) + scale4 * acc[3 + i], sh);
 }
 
 template <typename T> struct Ent;
@@ -648,9 +675,9 @@ __global__ void __launch_bounds__(kForceThreads) k_forces_final(const double *pa
 
 // Density, velocity (and optionally populations) of a level in FP64, x fastest;
 // NaN on nodes that are not computed (the hole and the coarse nodes over it).
-template <typename T, int P>
-__global__ void k_fields_level(const T *f, int nx, int ny, int pitch, size_t stride, const int *hx0, const int *hx1,
-                               double *rho, double *ux, double *uy, double *pop)
+template <typename T, typename S, int P>
+__global__ void k_fields_level(const S *f, int nx, int ny, int pitch, size_t stride, const int *hx0, const int *hx1,
+                               double *rho, double *ux, double *uy, double *pop, LatShift sh)
 {
     int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= nx) return;
@@ -662,7 +689,7 @@ __global__ void k_fields_level(const T *f, int nx, int ny, int pitch, size_t str
         return;
     }
     T d[9];
-    load_state<T, P>(f, node(x, y, pitch), pitch, stride, d);
+    load_state<T, S, P>(f, node(x, y, pitch), pitch, stride, d, sh);
     if (rho) {
         double dd[9];
         for (int i = 0; i < 9; i++) dd[i] = double(d[i]);
@@ -696,62 +723,73 @@ inline unsigned cdiv(long a, long b) { return unsigned((a + b - 1) / b); }
 }  // namespace
 
 // ------------------------------------------------------------ launchers ----
-template <typename T> void launch_init_level(const DevCtx &C, int c, unsigned long long seed, double perturb, cudaStream_t s)
+// T: arithmetic type; S: lattice storage type (T, or __half for FP16S).
+template <typename T, typename S>
+void launch_init_level(const DevCtx &C, int c, unsigned long long seed, double perturb, cudaStream_t s)
 {
     const DevLevel &l = C.lv[c];
     dim3 grid(cdiv(l.nx + 2, 128), l.ny + 2);
-    k_init_level<T><<<grid, 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, seed, c, perturb, C.u0);
+    k_init_level<T, S><<<grid, 128, 0, s>>>((S *)l.f, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, seed, c, perturb,
+                                            C.u0, C.shift);
 }
 
-template <typename T> void launch_collide(const DevCtx &C, int c, cudaStream_t s)
+template <typename T, typename S> void launch_collide(const DevCtx &C, int c, cudaStream_t s)
 {
     const DevLevel &l = C.lv[c];
     dim3 grid(cdiv(l.nx, 128), l.ny);
     T omega = T(1.0 / l.tau);
-    if (l.parity == 0) k_collide<T, 0><<<grid, 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0, l.hx1);
-    else k_collide<T, 1><<<grid, 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0, l.hx1);
+    if (l.parity == 0)
+        k_collide<T, S, 0><<<grid, 128, 0, s>>>((S *)l.f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0, l.hx1, C.shift);
+    else
+        k_collide<T, S, 1><<<grid, 128, 0, s>>>((S *)l.f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0, l.hx1, C.shift);
 }
 
-template <typename T> void launch_outer_bc(const DevCtx &C, cudaStream_t s)
+template <typename T, typename S> void launch_outer_bc(const DevCtx &C, cudaStream_t s)
 {
     const DevLevel &l = C.lv[0];
     int nper = 2 * l.nx + 2 * (l.ny - 2);
-    if (l.parity == 0) k_outer_bc<T, 0><<<cdiv(nper, 128), 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, T(C.u0));
-    else k_outer_bc<T, 1><<<cdiv(nper, 128), 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, T(C.u0));
+    if (l.parity == 0)
+        k_outer_bc<T, S, 0><<<cdiv(nper, 128), 128, 0, s>>>((S *)l.f, l.nx, l.ny, l.pitch, l.stride, T(C.u0), C.shift);
+    else
+        k_outer_bc<T, S, 1><<<cdiv(nper, 128), 128, 0, s>>>((S *)l.f, l.nx, l.ny, l.pitch, l.stride, T(C.u0), C.shift);
 }
 
-template <typename T> void launch_snapshot(const DevCtx &C, int c, bool into_b, cudaStream_t s)
+template <typename T, typename S> void launch_snapshot(const DevCtx &C, int c, bool into_b, cudaStream_t s)
 {
     const DevLevel &l = C.lv[c];
     T *dst = (T *)(into_b ? l.snapB : l.snapA);
     if (l.parity == 0)
-        k_snapshot<T, 0><<<cdiv(l.band_n, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, l.cox, l.coy, l.cmx, l.cmy, dst, l.band_n);
+        k_snapshot<T, S, 0><<<cdiv(l.band_n, 128), 128, 0, s>>>((const S *)l.f, l.pitch, l.stride, l.cox, l.coy, l.cmx,
+                                                                 l.cmy, dst, l.band_n, C.shift);
     else
-        k_snapshot<T, 1><<<cdiv(l.band_n, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, l.cox, l.coy, l.cmx, l.cmy, dst, l.band_n);
+        k_snapshot<T, S, 1><<<cdiv(l.band_n, 128), 128, 0, s>>>((const S *)l.f, l.pitch, l.stride, l.cox, l.coy, l.cmx,
+                                                                 l.cmy, dst, l.band_n, C.shift);
 }
 
-template <typename T> void launch_prolong(const DevCtx &C, int cf, double theta, cudaStream_t s)
+template <typename T, typename S> void launch_prolong(const DevCtx &C, int cf, double theta, cudaStream_t s)
 {
     const DevLevel &p = C.lv[cf - 1], &l = C.lv[cf];
     int nper = 2 * l.nx + 2 * (l.ny - 2);
     T scale = T(l.tau / (2.0 * p.tau));
     if (l.parity == 0)
-        k_prolong<T, 0><<<cdiv(nper, 128), 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, (const T *)p.snapA,
-                                                         (const T *)p.snapB, p.band_n, p.cox, p.coy, p.cmx, p.cmy, T(theta), scale);
+        k_prolong<T, S, 0><<<cdiv(nper, 128), 128, 0, s>>>((S *)l.f, l.nx, l.ny, l.pitch, l.stride, (const T *)p.snapA,
+                                                            (const T *)p.snapB, p.band_n, p.cox, p.coy, p.cmx, p.cmy,
+                                                            T(theta), scale, C.shift);
     else
-        k_prolong<T, 1><<<cdiv(nper, 128), 128, 0, s>>>((T *)l.f, l.nx, l.ny, l.pitch, l.stride, (const T *)p.snapA,
-                                                         (const T *)p.snapB, p.band_n, p.cox, p.coy, p.cmx, p.cmy, T(theta), scale);
+        k_prolong<T, S, 1><<<cdiv(nper, 128), 128, 0, s>>>((S *)l.f, l.nx, l.ny, l.pitch, l.stride, (const T *)p.snapA,
+                                                            (const T *)p.snapB, p.band_n, p.cox, p.coy, p.cmx, p.cmy,
+                                                            T(theta), scale, C.shift);
 }
 
-template <typename T> void launch_restrict(const DevCtx &C, int cc, cudaStream_t s)
+template <typename T, typename S> void launch_restrict(const DevCtx &C, int cc, cudaStream_t s)
 {
     const DevLevel &p = C.lv[cc], &l = C.lv[cc + 1];
     if (p.cmx < 2 || p.cmy < 2) return;
     dim3 grid(cdiv(p.cmx - 1, 128), p.cmy - 1);
     T scale = T(2.0 * p.tau / l.tau);
-#define HLBM_RESTRICT(PC, PF)                                                                                     \
-    k_restrict<T, PC, PF><<<grid, 128, 0, s>>>((T *)p.f, p.pitch, p.stride, (const T *)l.f, l.pitch, l.stride, p.cox, \
-                                               p.coy, p.cmx, p.cmy, scale, p.hx0, p.hx1)
+#define HLBM_RESTRICT(PC, PF)                                                                                        \
+    k_restrict<T, S, PC, PF><<<grid, 128, 0, s>>>((S *)p.f, p.pitch, p.stride, (const S *)l.f, l.pitch, l.stride,     \
+                                                  p.cox, p.coy, p.cmx, p.cmy, scale, p.hx0, p.hx1, C.shift)
     if (p.parity == 0 && l.parity == 0) HLBM_RESTRICT(0, 0);
     else if (p.parity == 0) HLBM_RESTRICT(0, 1);
     else if (l.parity == 0) HLBM_RESTRICT(1, 0);
@@ -759,7 +797,7 @@ template <typename T> void launch_restrict(const DevCtx &C, int cc, cudaStream_t
 #undef HLBM_RESTRICT
 }
 
-template <typename T> void launch_ring_interp(const DevCtx &C, bool q1_and_star, cudaStream_t s)
+template <typename T, typename S> void launch_ring_interp(const DevCtx &C, bool q1_and_star, cudaStream_t s)
 {
     const DevLevel &l = C.lv[C.L - 1];
     const DevMesh &m = C.m;
@@ -769,28 +807,32 @@ template <typename T> void launch_ring_interp(const DevCtx &C, bool q1_and_star,
     T *g = (T *)m.g[m.gcur];
     int star = q1_and_star ? 1 : 0;
     if (l.parity == 0)
-        k_ring_interp<T, 0><<<cdiv(16L * m.n_ring, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, m.ring_don, (const T *)m.ring_w,
-                                                                 m.n_ring, Q, (const T *)m.Q0, g, m.Np, m.ring_start, scale5, star);
+        k_ring_interp<T, S, 0><<<cdiv(16L * m.n_ring, 128), 128, 0, s>>>(
+            (const S *)l.f, l.pitch, l.stride, m.ring_don, (const T *)m.ring_w, m.n_ring, Q, (const T *)m.Q0, g, m.Np,
+            m.ring_start, scale5, star, C.shift);
     else
-        k_ring_interp<T, 1><<<cdiv(16L * m.n_ring, 128), 128, 0, s>>>((const T *)l.f, l.pitch, l.stride, m.ring_don, (const T *)m.ring_w,
-                                                                 m.n_ring, Q, (const T *)m.Q0, g, m.Np, m.ring_start, scale5, star);
+        k_ring_interp<T, S, 1><<<cdiv(16L * m.n_ring, 128), 128, 0, s>>>(
+            (const S *)l.f, l.pitch, l.stride, m.ring_don, (const T *)m.ring_w, m.n_ring, Q, (const T *)m.Q0, g, m.Np,
+            m.ring_start, scale5, star, C.shift);
 }
 
-template <typename T> void launch_hole_interp(const DevCtx &C, cudaStream_t s)
+template <typename T, typename S> void launch_hole_interp(const DevCtx &C, cudaStream_t s)
 {
     const DevLevel &l = C.lv[C.L - 1];
     const DevMesh &m = C.m;
     if (m.n_is == 0) return;
     T scale4 = T(2.0 * (l.tau - 1.0) / (2.0 * l.tau - 1.0));
     if (l.parity == 0)
-        k_hole_interp<T, 0><<<cdiv(8L * m.n_is, 128), 128, 0, s>>>((T *)l.f, l.pitch, l.stride, m.is_n, m.is_don, (const T *)m.is_w,
-                                                               m.n_is, (const T *)m.g[m.gcur], m.Np, scale4);
+        k_hole_interp<T, S, 0><<<cdiv(8L * m.n_is, 128), 128, 0, s>>>((S *)l.f, l.pitch, l.stride, m.is_n, m.is_don,
+                                                                      (const T *)m.is_w, m.n_is, (const T *)m.g[m.gcur],
+                                                                      m.Np, scale4, C.shift);
     else
-        k_hole_interp<T, 1><<<cdiv(8L * m.n_is, 128), 128, 0, s>>>((T *)l.f, l.pitch, l.stride, m.is_n, m.is_don, (const T *)m.is_w,
-                                                               m.n_is, (const T *)m.g[m.gcur], m.Np, scale4);
+        k_hole_interp<T, S, 1><<<cdiv(8L * m.n_is, 128), 128, 0, s>>>((S *)l.f, l.pitch, l.stride, m.is_n, m.is_don,
+                                                                      (const T *)m.is_w, m.n_is, (const T *)m.g[m.gcur],
+                                                                      m.Np, scale4, C.shift);
 }
 
-template <typename T> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
+template <typename T, typename S> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
 {
     const DevMesh &m = C.m;
     const DevLevel &l = C.lv[C.L - 1];
@@ -816,12 +858,12 @@ template <typename T> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
                        m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5, star);
 }
 
-template <typename T> void configure_fv(size_t bytes)
+template <typename T, typename S> void configure_fv(size_t bytes)
 {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(k_fv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
 }
 
-template <typename T> void launch_forces(const DevCtx &C, cudaStream_t s)
+template <typename T, typename S> void launch_forces(const DevCtx &C, cudaStream_t s)
 {
     const DevMesh &m = C.m;
     int nb = std::max(1, int(cdiv(m.n_edges, kForceThreads)));
@@ -831,7 +873,7 @@ template <typename T> void launch_forces(const DevCtx &C, cudaStream_t s)
                                                C.force_cap, C.flag);
 }
 
-template <typename T>
+template <typename T, typename S>
 void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *uy, double *pop, cudaStream_t s)
 {
     if (grid < 0) {
@@ -842,25 +884,28 @@ void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *u
     const DevLevel &l = C.lv[grid];
     dim3 g(cdiv(l.nx, 128), l.ny);
     if (l.parity == 0)
-        k_fields_level<T, 0><<<g, 128, 0, s>>>((const T *)l.f, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, rho, ux, uy, pop);
+        k_fields_level<T, S, 0><<<g, 128, 0, s>>>((const S *)l.f, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, rho, ux,
+                                                  uy, pop, C.shift);
     else
-        k_fields_level<T, 1><<<g, 128, 0, s>>>((const T *)l.f, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, rho, ux, uy, pop);
+        k_fields_level<T, S, 1><<<g, 128, 0, s>>>((const S *)l.f, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, rho, ux,
+                                                  uy, pop, C.shift);
 }
 
-#define HLBM_INSTANTIATE(T)                                                                                   \
-    template void configure_fv<T>(size_t);                                                                    \
-    template void launch_init_level<T>(const DevCtx &, int, unsigned long long, double, cudaStream_t);        \
-    template void launch_collide<T>(const DevCtx &, int, cudaStream_t);                                       \
-    template void launch_outer_bc<T>(const DevCtx &, cudaStream_t);                                           \
-    template void launch_snapshot<T>(const DevCtx &, int, bool, cudaStream_t);                                \
-    template void launch_prolong<T>(const DevCtx &, int, double, cudaStream_t);                               \
-    template void launch_restrict<T>(const DevCtx &, int, cudaStream_t);                                      \
-    template void launch_ring_interp<T>(const DevCtx &, bool, cudaStream_t);                                  \
-    template void launch_hole_interp<T>(const DevCtx &, cudaStream_t);                                        \
-    template void launch_fv<T>(const DevCtx &, int, cudaStream_t);                                            \
-    template void launch_forces<T>(const DevCtx &, cudaStream_t);                                             \
-    template void launch_fields<T>(const DevCtx &, int, double *, double *, double *, double *, cudaStream_t);
-HLBM_INSTANTIATE(float)
-HLBM_INSTANTIATE(double)
+#define HLBM_INSTANTIATE(T, S)                                                                                   \
+    template void configure_fv<T, S>(size_t);                                                                    \
+    template void launch_init_level<T, S>(const DevCtx &, int, unsigned long long, double, cudaStream_t);        \
+    template void launch_collide<T, S>(const DevCtx &, int, cudaStream_t);                                       \
+    template void launch_outer_bc<T, S>(const DevCtx &, cudaStream_t);                                           \
+    template void launch_snapshot<T, S>(const DevCtx &, int, bool, cudaStream_t);                                \
+    template void launch_prolong<T, S>(const DevCtx &, int, double, cudaStream_t);                               \
+    template void launch_restrict<T, S>(const DevCtx &, int, cudaStream_t);                                      \
+    template void launch_ring_interp<T, S>(const DevCtx &, bool, cudaStream_t);                                  \
+    template void launch_hole_interp<T, S>(const DevCtx &, cudaStream_t);                                        \
+    template void launch_fv<T, S>(const DevCtx &, int, cudaStream_t);                                            \
+    template void launch_forces<T, S>(const DevCtx &, cudaStream_t);                                             \
+    template void launch_fields<T, S>(const DevCtx &, int, double *, double *, double *, double *, cudaStream_t);
+HLBM_INSTANTIATE(float, float)
+HLBM_INSTANTIATE(double, double)
+HLBM_INSTANTIATE(float, __half)
 
 }  // namespace hlbm

@@ -78,7 +78,10 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     if (!(Re > 0.0) || !(Ma > 0.0)) { err = "Re and Ma must be positive"; return HLBM_EINVAL; }
     hlbm_options o{};
     if (opt) o = *opt;
-    if (o.precision != HLBM_FP64 && o.precision != HLBM_FP32) { err = "unknown precision"; return HLBM_EINVAL; }
+    if (o.precision != HLBM_FP64 && o.precision != HLBM_FP32 && o.precision != HLBM_FP16S) {
+        err = "unknown precision";
+        return HLBM_EINVAL;
+    }
     if (o.n_sub < 0) { err = "n_sub must be >= 0"; return HLBM_EINVAL; }
     P = Plan();
     P.L = n_levels;

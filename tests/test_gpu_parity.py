@@ -144,6 +144,48 @@ def test_fp32_accuracy_against_fp64(H, aoa):
     assert abs(cl32[100:].mean() - mcl) <= 1e-3 * max(abs(mcl), abs(mcd) if aoa == 0 else 0.0)
 
 
+@pytest.mark.parametrize("aoa", [0.0, 8.0])
+def test_fp16s_accuracy_against_fp64(H, aoa):
+    """FP16S lattice storage (16-bit populations shifted by the free stream, FP32
+    mesh and arithmetic): mean C_D / C_L within 1e-3 of FP64 (measured: about
+    2e-5); the velocity field within 16-bit storage resolution (relative L2
+    <= 2e-4, measured about 3e-5)."""
+    case = make_case("hlbm_small", aoa_deg=aoa)
+    a = H.Solver(case, precision="fp16s")
+    b = H.Solver(case, precision="fp64")
+    assert a.info("collide_bytes0") * 4 == b.info("collide_bytes0")
+    a.step(400)
+    b.step(400)
+    for g in grids(case):
+        _, ux, uy = a.fields(g)
+        _, vx, vy = b.fields(g)
+        m = np.isfinite(vx)
+        assert np.array_equal(np.isfinite(ux), m)
+        err = math.sqrt(((ux[m] - vx[m]) ** 2 + (uy[m] - vy[m]) ** 2).sum() / (vx[m] ** 2 + vy[m] ** 2).sum())
+        assert err <= 2e-4, f"grid {g}: velocity relative L2 {err:.2e}"
+    cd16, cl16 = a.forces()
+    cd64, cl64 = b.forces()
+    mcd, mcl = cd64[100:].mean(), cl64[100:].mean()
+    assert abs(cd16[100:].mean() - mcd) <= 1e-3 * abs(mcd)
+    assert abs(cl16[100:].mean() - mcl) <= 1e-3 * max(abs(mcl), abs(mcd) if aoa == 0 else 0.0)
+
+
+def test_fp16s_single_config_one_coarse_step(H, orc):
+    """Full-size single case in FP16S against the oracle after one coarse step."""
+    case = make_case("hlbm_single")
+    sol = H.Solver(case, precision="fp16s")
+    sim = orc.Oracle(case)
+    sol.step(1)
+    sim.step(1)
+    for g in grids(case):
+        _, ux, uy = sol.fields(g)
+        _, oux, ouy = sim.fields(g)
+        m = np.isfinite(oux)
+        assert np.array_equal(np.isfinite(ux), m)
+        err = math.sqrt(((ux[m] - oux[m]) ** 2 + (uy[m] - ouy[m]) ** 2).sum() / (oux[m] ** 2 + ouy[m] ** 2).sum())
+        assert err <= 2e-4, f"grid {g}: velocity relative L2 {err:.2e}"
+
+
 def test_graphs_and_plain_launches_agree_bitwise(H):
     case = make_case("hlbm_mini2")
     a = H.Solver(case, precision="fp64", use_graphs=True)

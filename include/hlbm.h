@@ -117,7 +117,9 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
 /* Advance n_coarse coarse (level-0) steps, asynchronously on the context's
  * stream.  One coarse step runs 2^l steps of level l and, per finest step,
  * n_sub finite-volume sub-steps; one force sample is recorded per coarse
- * step.  Returns HLBM_EUNSTABLE if the health flag (NaN in the forces) is set. */
+ * step.  Every check_every coarse steps (option) it reads the health flag:
+ * HLBM_ETIMEOUT if a bounded device-side wait gave up, HLBM_EUNSTABLE if the
+ * forces held a NaN. */
 int hlbm_step(hlbm_ctx *ctx, int n_coarse);
 
 /* Copy the force samples recorded since the previous call (oldest first, at
@@ -159,7 +161,8 @@ int hlbm_time_kernel(hlbm_ctx *ctx, const char *kernel, int reps, double *avg_ms
  * input node order, columns ascending), "area", "xy" (rotated),
  * "is_node", "is_don", "is_w" (Eq. 8 stencils), "ring", "ring_don",
  * "ring_w" (Eq. 9 stencils), "wall_edges", "n_sub", "inactive<l>" (1 for
- * nodes of level l that are not computed).  out == NULL queries n. */
+ * nodes of level l that are not computed), "perm" (input node of each device
+ * row).  out == NULL queries n. */
 int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re, double Ma,
                  double aoa_deg, const hlbm_options *opt, const char *table, double *out,
                  size_t cap, size_t *n);

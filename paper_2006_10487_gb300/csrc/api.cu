@@ -224,6 +224,8 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
         if (std::is_same<T, float>::value) { float fcol; std::memcpy(&fcol, &col, 4); std::memcpy(&v.w, &fcol, 4); }
         else v.w = T(col);
     };
+    // entries carry dt s_Pk and (dt / tau_u) C_Pk (the sub-step's constants folded in)
+    const double dt = P.n_sub > 0 ? 1.0 / P.n_sub : 0.0, dt_tau = dt / P.tau_u;
     for (int sl = 0; sl < M.n_slices; sl++) {
         int len = 0;
         std::vector<std::vector<int>> rows(32);
@@ -243,7 +245,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
                 E v{};
                 if (e < int(rows[l].size())) {
                     int k = rows[l][e];
-                    v.x = T(P.sx[k]); v.y = T(P.sy[k]); v.z = T(P.cc[k]);
+                    v.x = T(dt * P.sx[k]); v.y = T(dt * P.sy[k]); v.z = T(dt_tau * P.cc[k]);
                     int col = P.inv[P.col[k]];
                     set_col(v, int(std::lower_bound(h->begin(), h->end(), col) - h->begin()));
                 } else {
@@ -254,9 +256,13 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
             }
         }
     }
+    // one past the end, for every tile's 4 slices (the last tile may have fewer)
+    sptr.resize(size_t(4) * M.n_tiles + 1, int(ent.size()));
+    for (int t = 0; t < M.n_tiles; t++) M.max_tile_ent = std::max(M.max_tile_ent, sptr[4 * t + 4] - sptr[4 * t]);
     M.halo_ptr = upload(c, hptr);
     M.halo_nodes = upload(c, hnodes);
-    M.smem_bytes = size_t(M.max_halo) * 9 * sizeof(T);
+    // mbarrier (16 B), the tile's entries, the halo states
+    M.smem_bytes = 16 + size_t(M.max_tile_ent) * sizeof(E) + size_t(M.max_halo) * 9 * sizeof(T);
     if (M.smem_bytes > 200 * 1024) throw CudaError{"mesh tiles touch too many nodes for shared memory"};
     configure_fv<T, T>(M.smem_bytes);
     M.ent = upload(c, ent);
@@ -466,6 +472,7 @@ int hlbm_step(hlbm_ctx *c, int n_coarse)
                 int flag = 0;
                 ck(cudaMemcpyAsync(&flag, c->dev.flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "flag");
                 ck(cudaStreamSynchronize(c->stream), "sync");
+                if (flag & 2) return fail(c, HLBM_ETIMEOUT, "a device-side wait gave up (operator copy did not arrive)");
                 if (flag) return fail(c, HLBM_EUNSTABLE, "NaN in the force reduction: the simulation is unstable");
             }
         }
@@ -608,6 +615,7 @@ int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double 
     auto put_i = [&](const std::vector<int> &a) { v.assign(a.begin(), a.end()); };
     if (t == "rowptr") put_i(P.rowptr);
     else if (t == "col") put_i(P.col);
+    else if (t == "perm") put_i(P.perm);
     else if (t == "sx") v = P.sx;
     else if (t == "sy") v = P.sy;
     else if (t == "cc") v = P.cc;

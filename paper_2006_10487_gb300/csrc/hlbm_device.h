@@ -32,8 +32,11 @@ struct DevMesh {
     void *g[2] = {nullptr, nullptr};  // [9][Np] (rho - 1, ux, uy, f^neq_3..8), double-buffered
     int gcur = 0;
     // Eq. 3 operators, sliced ELL with 32-row slices: entry e of row r sits at
-    // slice_ptr[r / 32] + 32 e + r % 32, as (s_x, s_y, C, column)
-    int n_slices = 0;
+    // slice_ptr[r / 32] + 32 e + r % 32, as (dt s_x, dt s_y, dt / tau_u C,
+    // column); slice_ptr has n_slices + 1 elements, and the 4 slices of tile t
+    // are the contiguous block [slice_ptr[4 t], slice_ptr[4 t + 4]) of at most
+    // max_tile_ent entries
+    int n_slices = 0, max_tile_ent = 0;
     void *ent = nullptr;
     int *slice_ptr = nullptr, *slice_len = nullptr;
     // tiles of kTileRows consecutive rows; tile t touches the sorted nodes

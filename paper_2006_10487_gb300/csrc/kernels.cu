@@ -457,49 +457,126 @@ __device__ __forceinline__ void unpack(const double4_32a &e, double &sx, double 
 // L below, with drho, du = u_k - u_P, su = u_k + u_P) are accumulated once per
 // neighbour; only the f^neq part is summed per population.
 // Each block is one tile of kTileRows consecutive rows (a compact patch: rows
-// are in Morton order): it first copies the states of every node the tile
-// touches (its sorted halo list) into shared memory, plane-major, then each
-// thread treats one row, reading its neighbours from shared memory.
+// are in Morton order).  Before the dependency wait (constant data only): one
+// thread starts a bulk asynchronous copy (TMA) of the tile's operator entries
+// (4 consecutive slices, one contiguous block) into shared memory, and every
+// thread loads up to kFvHaloRegs of the tile's halo node indices into
+// registers.  After the wait the states of every node the tile touches (its
+// sorted halo list) are gathered into shared memory, plane-major, in one
+// round of loads; then each thread treats one row, reading its entries and its
+// neighbours from shared memory.
 constexpr int kFvThreads = kTileRows;
 constexpr int kFvGroup = 2;
+constexpr int kFvHaloRegs = 3;
+constexpr unsigned long long kWaitLimitNs = 500ull * 1000 * 1000;  // bounded waits give up after 0.5 s
+constexpr int kFlagTimeout = 2;  // health flag bit: a device-side wait gave up
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for phase `parity` of the shared-memory mbarrier at `bar`, for at most
+// kWaitLimitNs; returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (globaltimer() - t0 > kWaitLimitNs) return false;
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
                                                    const int *__restrict__ slice_ptr,
                                                    const int *__restrict__ slice_len,
-                                                   const typename Ent<T>::type *__restrict__ ent,
+                                                   const typename Ent<T>::type *__restrict__ ent, int max_tile_ent,
                                                    const int *__restrict__ halo_ptr,
-                                                   const int *__restrict__ halo_nodes, T dt, T dt_tau,
+                                                   const int *__restrict__ halo_nodes, T dt_tau,
                                                    int n_wall, int ring_start, int n_ring,
                                                    const T *__restrict__ Q0, const T *__restrict__ Q1, T theta_next,
-                                                   T scale5, int star)
+                                                   T scale5, int star, int *flag)
 {
+    using E = typename Ent<T>::type;
     extern __shared__ __align__(16) unsigned char fv_smem[];
-    T *sh = reinterpret_cast<T *>(fv_smem);
+    // [0, 16): mbarrier; [16, ...): the tile's entries; then the halo states
+    const uint32_t bar = uint32_t(__cvta_generic_to_shared(fv_smem));
+    const E *se = reinterpret_cast<const E *>(fv_smem + 16);
+    T *sh = reinterpret_cast<T *>(fv_smem + 16 + size_t(max_tile_ent) * sizeof(E));
+    const int t = blockIdx.x;
+    const int e_begin = slice_ptr[4 * t];
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = uint32_t(slice_ptr[4 * t + 4] - e_begin) * uint32_t(sizeof(E));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("{\n\t.reg .b64 st;\n\t"
+                     "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+                     "r"(bytes)
+                     : "memory");
+        if (bytes > 0)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             bar + 16u),
+                         "l"(ent + e_begin), "r"(bytes), "r"(bar)
+                         : "memory");
+    }
     // Let the next sub-step's blocks start as soon as SM slots free up; they
     // only read constant operator data until their griddepcontrol.wait.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int h0 = halo_ptr[blockIdx.x], hn = halo_ptr[blockIdx.x + 1] - h0;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int h0 = halo_ptr[t], hn = halo_ptr[t + 1] - h0;
+    const int r = t * blockDim.x + threadIdx.x;
     const int rr = r < n ? r : n - 1;
     const int sl = rr >> 5;
-    const int base = slice_ptr[sl] + (rr & 31), len = slice_len[sl];
+    const int base = slice_ptr[sl] - e_begin + (rr & 31), len = slice_len[sl];
+    int hidx[kFvHaloRegs];
+#pragma unroll
+    for (int j = 0; j < kFvHaloRegs; j++) {
+        const int h = threadIdx.x + j * kFvThreads;
+        hidx[j] = h < hn ? halo_nodes[h0 + h] : 0;
+    }
     // wait until the previous sub-step (which wrote g) has completed
     asm volatile("griddepcontrol.wait;" ::: "memory");
     T r1P, uPx, uPy, nP[9];
-    load_mesh(g, Np, rr, r1P, uPx, uPy, nP);  // issued before the halo staging
-    for (int h = threadIdx.x; h < hn; h += blockDim.x) {
+    load_mesh(g, Np, rr, r1P, uPx, uPy, nP);  // issued before the halo gather
+#pragma unroll
+    for (int j = 0; j < kFvHaloRegs; j++) {
+        const int h = threadIdx.x + j * kFvThreads;
+        if (h < hn) {
+#pragma unroll
+            for (int i = 0; i < 9; i++) sh[i * hn + h] = g[size_t(i) * Np + hidx[j]];
+        }
+    }
+    for (int h = threadIdx.x + kFvHaloRegs * kFvThreads; h < hn; h += kFvThreads) {
         const int node = halo_nodes[h0 + h];
 #pragma unroll
         for (int i = 0; i < 9; i++) sh[i * hn + h] = g[size_t(i) * Np + node];
     }
     __syncthreads();
+    if (!mbar_wait(bar, 0)) {
+        // the entry copy did not arrive: report, give the copy one more bounded
+        // wait (it targets this block's shared memory) and leave
+        if (threadIdx.x == 0) atomicOr(flag, kFlagTimeout);
+        mbar_wait(bar, 0);
+        return;
+    }
     if (r >= n) return;
     // own node: no streaming term (g(P) - g(P) = 0), collision weight C_PP = 11/18
-    T acc[9];
-    const T csP = dt_tau * T(11.0 / 18.0);
-#pragma unroll
-    for (int i = 0; i < 9; i++) acc[i] = -csP * nP[i];
+    // f^neq part of the sums, over the six stored planes j = 3..8 only:
+    //   U_j = sum_k a_k n_j(P_k), V_j = sum_k b_k n_j(P_k), W_j = sum_k cs_k n_j(P_k)
+    // (U_4 and V_3 are never needed: c_4x = c_3y = 0); planes 0-2 follow at the
+    // end from the same linear constraints that complete f^neq.
+    T U3 = 0, U5 = 0, U6 = 0, U7 = 0, U8 = 0, V4 = 0, V5 = 0, V6 = 0, V7 = 0, V8 = 0;
+    T W3 = 0, W4 = 0, W5 = 0, W6 = 0, W7 = 0, W8 = 0;
     T Sa = 0, Sb = 0, Dx = 0, Dy = 0, Qxx = 0, Qyy = 0, Qxy = 0, Lx = 0, Ly = 0, Mx = 0, My = 0, Mxxy = 0, Mxyy = 0;
     for (int e0 = 0; e0 < len; e0 += kFvGroup) {
         T sx[kFvGroup], sy[kFvGroup], c[kFvGroup];
@@ -507,7 +584,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
 #pragma unroll
         for (int j = 0; j < kFvGroup; j++) {
             if (e0 + j < len) {
-                unpack(ent[base + 32 * (e0 + j)], sx[j], sy[j], c[j], k[j]);
+                unpack(se[base + 32 * (e0 + j)], sx[j], sy[j], c[j], k[j]);
             } else {
                 sx[j] = sy[j] = c[j] = T(0);
                 k[j] = 0;
@@ -520,11 +597,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
             for (int i = 0; i < 9; i++) st[j][i] = sh[i * hn + k[j]];
 #pragma unroll
         for (int j = 0; j < kFvGroup; j++) {
-            T nk[9];
-#pragma unroll
-            for (int i = 3; i < 9; i++) nk[i] = st[j][i];
-            neq_complete(nk);
-            const T a = dt * sx[j], b = dt * sy[j], cs = dt_tau * c[j];
+            const T a = sx[j], b = sy[j], cs = c[j];  // dt s_Pk and (dt / tau_u) C_Pk
             const T drho = st[j][0] - r1P, rhok = T(1) + st[j][0];
             const T dux = st[j][1] - uPx, duy = st[j][2] - uPy, sux = st[j][1] + uPx, suy = st[j][2] + uPy;
             const T dus = dux * sux + duy * suy, ra = rhok * a, rb = rhok * b;
@@ -542,9 +615,27 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
             My += rb * duy * suy;
             Mxxy += ra * xs + rb * dux * sux;
             Mxyy += rb * xs + ra * duy * suy;
-#pragma unroll
-            for (int i = 0; i < 9; i++) acc[i] += (T(cx(i)) * a + T(cy(i)) * b - cs) * nk[i];
+            const T *nk = st[j];
+            U3 += a * nk[3]; U5 += a * nk[5]; U6 += a * nk[6]; U7 += a * nk[7]; U8 += a * nk[8];
+            V4 += b * nk[4]; V5 += b * nk[5]; V6 += b * nk[6]; V7 += b * nk[7]; V8 += b * nk[8];
+            W3 += cs * nk[3]; W4 += cs * nk[4]; W5 += cs * nk[5];
+            W6 += cs * nk[6]; W7 += cs * nk[7]; W8 += cs * nk[8];
         }
+    }
+    // acc_i = sum_k (c_i . (a_k, b_k) - cs_k) f^neq_i(P_k) - dt/tau_u C_PP f^neq_i(P)
+    T acc[9];
+    {
+        const T W1 = W3 - W5 + W6 + W7 - W8, W2 = W4 - W5 - W6 + W7 + W8;
+        const T csP = dt_tau * T(11.0 / 18.0);
+        acc[0] = (W1 + W2 + W3 + W4 + W5 + W6 + W7 + W8) - csP * nP[0];
+        acc[1] = (U3 - U5 + U6 + U7 - U8) - W1 - csP * nP[1];
+        acc[2] = (V4 - V5 - V6 + V7 + V8) - W2 - csP * nP[2];
+        acc[3] = -U3 - W3 - csP * nP[3];
+        acc[4] = -V4 - W4 - csP * nP[4];
+        acc[5] = U5 + V5 - W5 - csP * nP[5];
+        acc[6] = -U6 + V6 - W6 - csP * nP[6];
+        acc[7] = -U7 - V7 - W7 - csP * nP[7];
+        acc[8] = U8 - V8 - W8 - csP * nP[8];
     }
 #pragma unroll
     for (int i = 0; i < 9; i++) {
@@ -836,7 +927,7 @@ template <typename T, typename S> void launch_fv(const DevCtx &C, int msub, cuda
 {
     const DevMesh &m = C.m;
     const DevLevel &l = C.lv[C.L - 1];
-    T dt = T(C.dt_u), dt_tau = T(C.dt_u / C.tau_u);
+    T dt_tau = T(C.dt_u / C.tau_u);
     T scale5 = T(1.0 - 1.0 / (2.0 * l.tau));
     int star = msub < C.n_sub - 1 ? 1 : 0;
     T theta_next = T(double(msub + 1) / double(C.n_sub));
@@ -854,8 +945,8 @@ template <typename T, typename S> void launch_fv(const DevCtx &C, int msub, cuda
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k_fv<T>, (const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
                        (const int *)m.slice_ptr, (const int *)m.slice_len, (const typename Ent<T>::type *)m.ent,
-                       (const int *)m.halo_ptr, (const int *)m.halo_nodes, dt, dt_tau, m.n_wall, m.ring_start,
-                       m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5, star);
+                       m.max_tile_ent, (const int *)m.halo_ptr, (const int *)m.halo_nodes, dt_tau, m.n_wall,
+                       m.ring_start, m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5, star, C.flag);
 }
 
 template <typename T, typename S> void configure_fv(size_t bytes)

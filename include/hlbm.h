@@ -145,7 +145,8 @@ int hlbm_populations(hlbm_ctx *ctx, int grid, double *out, size_t cap);
  * "fv_updates" (finite-volume node updates per coarse step),
  * "launches_per_step" (kernels in one coarse step), "fv_bytes" (algorithmic
  * bytes of one finite-volume sub-step), "collide_bytes<l>" (algorithmic bytes
- * of one lattice step of level l). */
+ * of one lattice step of level l), "fv_tiles" (blocks of one finite-volume
+ * sub-step), "fv_smem" (their dynamic shared memory, bytes). */
 int hlbm_info(const hlbm_ctx *ctx, const char *key, double *value);
 
 /* Measurement hook: runs one kernel of the step `reps` times back to back on

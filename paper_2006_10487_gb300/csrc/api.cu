@@ -580,6 +580,8 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
         *value = u;
     } else if (k == "fv_updates") *value = double(P.n) * P.n_sub * double(1L << (P.L - 1));
     else if (k == "launches_per_step") *value = double(c->launches_per_step);
+    else if (k == "fv_tiles") *value = double(c->dev.m.n_tiles);
+    else if (k == "fv_smem") *value = double(c->dev.m.smem_bytes);
     else if (k == "fv_bytes") {
         // algorithmic bytes of one finite-volume sub-step: the 9 state values of
         // every node read and written, one (s_x, s_y, C, column) entry per
@@ -615,6 +617,7 @@ int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double 
     auto put_i = [&](const std::vector<int> &a) { v.assign(a.begin(), a.end()); };
     if (t == "rowptr") put_i(P.rowptr);
     else if (t == "col") put_i(P.col);
+    else if (t == "perm") put_i(P.perm);
     else if (t == "perm") put_i(P.perm);
     else if (t == "sx") v = P.sx;
     else if (t == "sy") v = P.sy;

@@ -435,6 +435,44 @@ __device__ __forceinline__ void unpack(const double4_32a &e, double &sx, double 
     sx = e.x; sy = e.y; c = e.z; col = int(e.w);
 }
 
+// Packed pairs of FP32 values (two halves of one 64-bit register) for the
+// paired FP32 arithmetic (f32x2) of sm_100 and later: element-wise, round to
+// nearest; one instruction does two of the FV kernel's accumulations.
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // Eq. 3, one explicit sub-step on every mesh node (node-major gather over the
 // sliced-ELL operator rows, no atomics), on the (rho, u, f^neq) state:
 //   acc_i = dt sum_k (c_i . s_Pk) (g_i(P_k) - g_i(P)) - dt/tau_u sum_k C_Pk f^neq_i(P_k)
@@ -578,48 +616,97 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
     T U3 = 0, U5 = 0, U6 = 0, U7 = 0, U8 = 0, V4 = 0, V5 = 0, V6 = 0, V7 = 0, V8 = 0;
     T W3 = 0, W4 = 0, W5 = 0, W6 = 0, W7 = 0, W8 = 0;
     T Sa = 0, Sb = 0, Dx = 0, Dy = 0, Qxx = 0, Qyy = 0, Qxy = 0, Lx = 0, Ly = 0, Mx = 0, My = 0, Mxxy = 0, Mxyy = 0;
-    for (int e0 = 0; e0 < len; e0 += kFvGroup) {
-        T sx[kFvGroup], sy[kFvGroup], c[kFvGroup];
-        int k[kFvGroup];
-#pragma unroll
-        for (int j = 0; j < kFvGroup; j++) {
-            if (e0 + j < len) {
-                unpack(se[base + 32 * (e0 + j)], sx[j], sy[j], c[j], k[j]);
-            } else {
-                sx[j] = sy[j] = c[j] = T(0);
-                k[j] = 0;
-            }
+    if constexpr (sizeof(T) == 4) {
+        // the same sums on packed pairs: (U5,U6) (U7,U8) (V5,V6) (V7,V8) (U3,V4)
+        // (W3,W4) (W5,W6) (W7,W8) (Sa,Sb) (Dx,Dy) (Qxx,Qyy) (Qxy',Qxy'') (Lx,Ly)
+        // (Mx,My) (Mxxy,Mxyy)
+        const unsigned long long z = pk2(0.f, 0.f), uP = pk2(uPx, uPy);
+        unsigned long long U56 = z, U78 = z, V56 = z, V78 = z, U3V4 = z, W34 = z, W56 = z, W78 = z;
+        unsigned long long SS = z, DD = z, QQ = z, QX = z, LL = z, MM = z, MX = z;
+        for (int e0 = 0; e0 < len; e0++) {
+            float a, b, cs;
+            int k;
+            unpack(se[base + 32 * e0], a, b, cs, k);
+            const float r1k = sh[k], n3 = sh[3 * hn + k], n4 = sh[4 * hn + k], n5 = sh[5 * hn + k],
+                        n6 = sh[6 * hn + k], n7 = sh[7 * hn + k], n8 = sh[8 * hn + k];
+            const unsigned long long uk = pk2(sh[hn + k], sh[2 * hn + k]);
+            const float drho = r1k - r1P, rhok = 1.f + r1k;
+            const unsigned long long ab = pk2(a, b), aa = pk2(a, a), bb = pk2(b, b), cc = pk2(cs, cs);
+            const unsigned long long du = sub2(uk, uP), su = add2(uk, uP);   // (dux, duy), (sux, suy)
+            const unsigned long long pr = mul2(du, su);                      // (dux sux, duy suy)
+            const unsigned long long R = mul2(ab, pk2(rhok, rhok));          // (ra, rb)
+            float dux, duy, sux, suy, p0, p1, ra, rb;
+            upk2(du, dux, duy);
+            upk2(su, sux, suy);
+            upk2(pr, p0, p1);
+            upk2(R, ra, rb);
+            const float dus = p0 + p1, xs = dux * suy + duy * sux;
+            SS = add2(SS, ab);
+            DD = fma2(ab, pk2(drho, drho), DD);
+            QQ = fma2(R, du, QQ);
+            QX = fma2(R, pk2(duy, dux), QX);
+            LL = fma2(R, pk2(dus, dus), LL);
+            MM = fma2(R, pr, MM);
+            MX = fma2(R, pk2(xs, xs), fma2(pk2(rb, ra), pr, MX));
+            const unsigned long long n34 = pk2(n3, n4), n56 = pk2(n5, n6), n78 = pk2(n7, n8);
+            U56 = fma2(aa, n56, U56);
+            U78 = fma2(aa, n78, U78);
+            V56 = fma2(bb, n56, V56);
+            V78 = fma2(bb, n78, V78);
+            U3V4 = fma2(ab, n34, U3V4);
+            W34 = fma2(cc, n34, W34);
+            W56 = fma2(cc, n56, W56);
+            W78 = fma2(cc, n78, W78);
         }
-        T st[kFvGroup][9];
+        float q0, q1;
+        upk2(U56, U5, U6); upk2(U78, U7, U8); upk2(V56, V5, V6); upk2(V78, V7, V8); upk2(U3V4, U3, V4);
+        upk2(W34, W3, W4); upk2(W56, W5, W6); upk2(W78, W7, W8);
+        upk2(SS, Sa, Sb); upk2(DD, Dx, Dy); upk2(QQ, Qxx, Qyy); upk2(QX, q0, q1); Qxy = q0 + q1;
+        upk2(LL, Lx, Ly); upk2(MM, Mx, My); upk2(MX, Mxxy, Mxyy);
+    } else {
+        for (int e0 = 0; e0 < len; e0 += kFvGroup) {
+            T sx[kFvGroup], sy[kFvGroup], c[kFvGroup];
+            int k[kFvGroup];
 #pragma unroll
-        for (int j = 0; j < kFvGroup; j++)
+            for (int j = 0; j < kFvGroup; j++) {
+                if (e0 + j < len) {
+                    unpack(se[base + 32 * (e0 + j)], sx[j], sy[j], c[j], k[j]);
+                } else {
+                    sx[j] = sy[j] = c[j] = T(0);
+                    k[j] = 0;
+                }
+            }
+            T st[kFvGroup][9];
 #pragma unroll
-            for (int i = 0; i < 9; i++) st[j][i] = sh[i * hn + k[j]];
+            for (int j = 0; j < kFvGroup; j++)
 #pragma unroll
-        for (int j = 0; j < kFvGroup; j++) {
-            const T a = sx[j], b = sy[j], cs = c[j];  // dt s_Pk and (dt / tau_u) C_Pk
-            const T drho = st[j][0] - r1P, rhok = T(1) + st[j][0];
-            const T dux = st[j][1] - uPx, duy = st[j][2] - uPy, sux = st[j][1] + uPx, suy = st[j][2] + uPy;
-            const T dus = dux * sux + duy * suy, ra = rhok * a, rb = rhok * b;
-            const T xs = dux * suy + duy * sux;
-            Sa += a;
-            Sb += b;
-            Dx += a * drho;
-            Dy += b * drho;
-            Qxx += ra * dux;
-            Qyy += rb * duy;
-            Qxy += ra * duy + rb * dux;
-            Lx += ra * dus;
-            Ly += rb * dus;
-            Mx += ra * dux * sux;
-            My += rb * duy * suy;
-            Mxxy += ra * xs + rb * dux * sux;
-            Mxyy += rb * xs + ra * duy * suy;
-            const T *nk = st[j];
-            U3 += a * nk[3]; U5 += a * nk[5]; U6 += a * nk[6]; U7 += a * nk[7]; U8 += a * nk[8];
-            V4 += b * nk[4]; V5 += b * nk[5]; V6 += b * nk[6]; V7 += b * nk[7]; V8 += b * nk[8];
-            W3 += cs * nk[3]; W4 += cs * nk[4]; W5 += cs * nk[5];
-            W6 += cs * nk[6]; W7 += cs * nk[7]; W8 += cs * nk[8];
+                for (int i = 0; i < 9; i++) st[j][i] = sh[i * hn + k[j]];
+#pragma unroll
+            for (int j = 0; j < kFvGroup; j++) {
+                const T a = sx[j], b = sy[j], cs = c[j];  // dt s_Pk and (dt / tau_u) C_Pk
+                const T drho = st[j][0] - r1P, rhok = T(1) + st[j][0];
+                const T dux = st[j][1] - uPx, duy = st[j][2] - uPy, sux = st[j][1] + uPx, suy = st[j][2] + uPy;
+                const T dus = dux * sux + duy * suy, ra = rhok * a, rb = rhok * b;
+                const T xs = dux * suy + duy * sux;
+                Sa += a;
+                Sb += b;
+                Dx += a * drho;
+                Dy += b * drho;
+                Qxx += ra * dux;
+                Qyy += rb * duy;
+                Qxy += ra * duy + rb * dux;
+                Lx += ra * dus;
+                Ly += rb * dus;
+                Mx += ra * dux * sux;
+                My += rb * duy * suy;
+                Mxxy += ra * xs + rb * dux * sux;
+                Mxyy += rb * xs + ra * duy * suy;
+                const T *nk = st[j];
+                U3 += a * nk[3]; U5 += a * nk[5]; U6 += a * nk[6]; U7 += a * nk[7]; U8 += a * nk[8];
+                V4 += b * nk[4]; V5 += b * nk[5]; V6 += b * nk[6]; V7 += b * nk[7]; V8 += b * nk[8];
+                W3 += cs * nk[3]; W4 += cs * nk[4]; W5 += cs * nk[5];
+                W6 += cs * nk[6]; W7 += cs * nk[7]; W8 += cs * nk[8];
+            }
         }
     }
     // acc_i = sum_k (c_i . (a_k, b_k) - cs_k) f^neq_i(P_k) - dt/tau_u C_PP f^neq_i(P)
@@ -651,8 +738,8 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
         djx += T(cx(i)) * acc[i];
         djy += T(cy(i)) * acc[i];
     }
-    T r1 = r1P + drho, rho = T(1) + r1;
-    T dux = (djx - drho * uPx) / rho, duy = (djy - drho * uPy) / rho;
+    T r1 = r1P + drho, rho = T(1) + r1, irho = T(1) / rho;
+    T dux = (djx - drho * uPx) * irho, duy = (djy - drho * uPy) * irho;
     T ux = uPx + dux, uy = uPy + duy;
     T nq[9];
 #pragma unroll

@@ -709,42 +709,67 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
             }
         }
     }
-    // acc_i = sum_k (c_i . (a_k, b_k) - cs_k) f^neq_i(P_k) - dt/tau_u C_PP f^neq_i(P)
-    T acc[9];
-    {
-        const T W1 = W3 - W5 + W6 + W7 - W8, W2 = W4 - W5 - W6 + W7 + W8;
-        const T csP = dt_tau * T(11.0 / 18.0);
-        acc[0] = (W1 + W2 + W3 + W4 + W5 + W6 + W7 + W8) - csP * nP[0];
-        acc[1] = (U3 - U5 + U6 + U7 - U8) - W1 - csP * nP[1];
-        acc[2] = (V4 - V5 - V6 + V7 + V8) - W2 - csP * nP[2];
-        acc[3] = -U3 - W3 - csP * nP[3];
-        acc[4] = -V4 - W4 - csP * nP[4];
-        acc[5] = U5 + V5 - W5 - csP * nP[5];
-        acc[6] = -U6 + V6 - W6 - csP * nP[6];
-        acc[7] = -U7 - V7 - W7 - csP * nP[7];
-        acc[8] = U8 - V8 - W8 - csP * nP[8];
-    }
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        const T X = T(cx(i)), Y = T(cy(i));
-        T eq = Efun<T>(i, uPx, uPy) * (X * Dx + Y * Dy) + T(3) * (X * X * Qxx + X * Y * Qxy + Y * Y * Qyy) +
-               T(4.5) * (X * Mx + Y * My + X * X * Y * Mxxy + X * Y * Y * Mxyy) - T(1.5) * (X * Lx + Y * Ly);
-        acc[i] += wq<T>(i) * eq - nP[i] * (X * Sa + Y * Sb);
-    }
-    T drho = 0, djx = 0, djy = 0;
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        drho += acc[i];
-        djx += T(cx(i)) * acc[i];
-        djy += T(cy(i)) * acc[i];
-    }
-    T r1 = r1P + drho, rho = T(1) + r1, irho = T(1) / rho;
-    T dux = (djx - drho * uPx) * irho, duy = (djy - drho * uPy) * irho;
+    // Update.  With acc_i = sum_k (c_i.(a_k, b_k) - cs_k) f^neq_i(P_k) + w_i eq_i
+    // - f^neq_i(P) (c_i.(Sa, Sb) + dt/tau_u C_PP) the increment of population i,
+    // its zeroth and first moments need no per-population sum: f^neq carries
+    // no mass or momentum and the D2Q9 weights are isotropic to fourth order,
+    //   drho = u_P.D + Q_xx + Q_yy
+    //   djx  = D_x/3 + u_Px (u_P.D) + 3/2 M_x + 1/2 M_xyy - 1/2 L_x
+    //          + sum_k (a_k Pi^neq_xx(P_k) + b_k Pi^neq_xy(P_k)) - (Sa Pi^neq_xx(P) + Sb Pi^neq_xy(P))
+    // (djy likewise), with sum_k a_k Pi^neq_xx(P_k) = 2 (U3 + U6 + U7) and so
+    // on.  The new f^neq is then needed for the stored planes 3..8 only;
+    // opposite diagonals (5, 7) and (6, 8) share the even and odd parts of
+    // eq_i and of the f^eq difference.
+    const T csP = dt_tau * T(11.0 / 18.0);
+    const T Pxx = nP[1] + nP[3] + nP[5] + nP[6] + nP[7] + nP[8];
+    const T Pyy = nP[2] + nP[4] + nP[5] + nP[6] + nP[7] + nP[8];
+    const T Pxy = nP[5] - nP[6] + nP[7] - nP[8];
+    const T uD = uPx * Dx + uPy * Dy;
+    const T drho = uD + Qxx + Qyy;
+    const T djx = Dx * T(1.0 / 3.0) + uPx * uD + T(1.5) * Mx + T(0.5) * Mxyy - T(0.5) * Lx + T(2) * (U3 + U6 + U7) +
+                  (V5 - V6 + V7 - V8) - (Sa * Pxx + Sb * Pxy);
+    const T djy = Dy * T(1.0 / 3.0) + uPy * uD + T(1.5) * My + T(0.5) * Mxxy - T(0.5) * Ly + (U5 - U6 + U7 - U8) +
+                  T(2) * (V4 + V7 + V8) - (Sb * Pyy + Sa * Pxy);
+    T r1 = r1P + drho;
+    const T rho = T(1) + r1, irho = T(1) / rho;
+    const T dux = (djx - drho * uPx) * irho, duy = (djy - drho * uPy) * irho;
     T ux = uPx + dux, uy = uPy + duy;
+    const T sx = ux + uPx, sy = uy + uPy;           // u' + u_P
+    const T E0 = T(1) - T(1.5) * (uPx * uPx + uPy * uPy);
+    const T ddot = T(1.5) * (dux * sx + duy * sy);  // 3/2 du.(u' + u_P)
+    // [f^eq_c(rho', u') - f^eq_c(rho_P, u_P)] / w_c for a direction c with E = E_c(u_P)
+    auto fd = [&](T E, T cdu, T csu) { return drho * E + rho * (T(3) * cdu + T(4.5) * cdu * csu - ddot); };
     T nq[9];
-#pragma unroll
-    for (int i = 0; i < 9; i++)
-        nq[i] = nP[i] + acc[i] - feq_diff<T>(i, Efun<T>(i, uPx, uPy), drho, rho, dux, duy, ux + uPx, uy + uPy);
+    {  // axis directions 3 (-1, 0) and 4 (0, -1)
+        const T E3 = E0 - T(3) * uPx + T(4.5) * uPx * uPx;
+        const T eq3 = -E3 * Dx + T(3) * Qxx - T(4.5) * Mx + T(1.5) * Lx;
+        nq[3] = nP[3] - U3 - W3 + T(1.0 / 9.0) * eq3 + nP[3] * (Sa - csP) - T(1.0 / 9.0) * fd(E3, -dux, -sx);
+        const T E4 = E0 - T(3) * uPy + T(4.5) * uPy * uPy;
+        const T eq4 = -E4 * Dy + T(3) * Qyy - T(4.5) * My + T(1.5) * Ly;
+        nq[4] = nP[4] - V4 - W4 + T(1.0 / 9.0) * eq4 + nP[4] * (Sb - csP) - T(1.0 / 9.0) * fd(E4, -duy, -sy);
+    }
+    {  // diagonals 5 (1, 1) and 7 (-1, -1)
+        const T q = uPx + uPy, A = E0 + T(4.5) * q * q, B = T(3) * q;
+        const T Pd = Dx + Dy, C = T(3) * (Qxx + Qxy + Qyy);
+        const T Z = T(4.5) * (Mx + My + Mxxy + Mxyy) - T(1.5) * (Lx + Ly);
+        const T odd = A * Pd + Z, even = B * Pd + C;  // eq5 = even + odd, eq7 = even - odd
+        const T cdu = dux + duy, csu = sx + sy;
+        nq[5] = nP[5] + U5 + V5 - W5 + T(1.0 / 36.0) * (even + odd) - nP[5] * (Sa + Sb + csP) -
+                T(1.0 / 36.0) * fd(A + B, cdu, csu);
+        nq[7] = nP[7] - U7 - V7 - W7 + T(1.0 / 36.0) * (even - odd) + nP[7] * (Sa + Sb - csP) -
+                T(1.0 / 36.0) * fd(A - B, -cdu, -csu);
+    }
+    {  // diagonals 6 (-1, 1) and 8 (1, -1)
+        const T q = uPy - uPx, A = E0 + T(4.5) * q * q, B = T(3) * q;
+        const T Pd = Dy - Dx, C = T(3) * (Qxx - Qxy + Qyy);
+        const T Z = T(4.5) * (-Mx + My + Mxxy - Mxyy) - T(1.5) * (Ly - Lx);
+        const T odd = A * Pd + Z, even = B * Pd + C;  // eq6 = even + odd, eq8 = even - odd
+        const T cdu = duy - dux, csu = sy - sx;
+        nq[6] = nP[6] - U6 + V6 - W6 + T(1.0 / 36.0) * (even + odd) - nP[6] * (Sb - Sa + csP) -
+                T(1.0 / 36.0) * fd(A + B, cdu, csu);
+        nq[8] = nP[8] + U8 - V8 - W8 + T(1.0 / 36.0) * (even - odd) + nP[8] * (Sb - Sa - csP) -
+                T(1.0 / 36.0) * fd(A - B, -cdu, -csu);
+    }
     if (r < n_wall) {
         ux = T(0);
         uy = T(0);

@@ -93,30 +93,31 @@ def o_mesh(chord, leading_edge, n_theta, n_layers, stretch, ell_a, ell_b):
     xy = h00 * surf[None] + h10 * t0[None] + h01 * outer[None] + h11 * t1[None]
     xy = xy.reshape(-1, 2)
 
-    def nid(jj, kk):
-        return jj * n_theta + (kk % n_theta)
+    # Quad (k, j) has corners a = (j, k), b = (j, k+1), c = (j+1, k), d = (j+1, k+1).
+    # Index k runs counter-clockwise and j outward, so (a, c, b) is counter-
+    # clockwise.  Each quad is split along the diagonal that gives the larger
+    # smallest altitude (this avoids slivers at the sharp trailing edge).
+    jj, kk = np.meshgrid(np.arange(n_layers), np.arange(n_theta), indexing="ij")
+    a = (jj * n_theta + kk).ravel()
+    b = (jj * n_theta + (kk + 1) % n_theta).ravel()
+    c = ((jj + 1) * n_theta + kk).ravel()
+    d = ((jj + 1) * n_theta + (kk + 1) % n_theta).ravel()
 
-    def min_altitude(t3):
-        p = xy[list(t3)]
-        a2 = ((p[1, 0] - p[0, 0]) * (p[2, 1] - p[0, 1])
-              - (p[1, 1] - p[0, 1]) * (p[2, 0] - p[0, 0]))
-        edge = max(np.hypot(*(p[1] - p[0])), np.hypot(*(p[2] - p[1])), np.hypot(*(p[0] - p[2])))
-        return a2 / edge
+    def min_altitude(i0, i1, i2):
+        p0, p1, p2 = xy[i0], xy[i1], xy[i2]
+        a2 = ((p1[:, 0] - p0[:, 0]) * (p2[:, 1] - p0[:, 1])
+              - (p1[:, 1] - p0[:, 1]) * (p2[:, 0] - p0[:, 0]))
+        e01 = np.hypot(p1[:, 0] - p0[:, 0], p1[:, 1] - p0[:, 1])
+        e12 = np.hypot(p2[:, 0] - p1[:, 0], p2[:, 1] - p1[:, 1])
+        e20 = np.hypot(p0[:, 0] - p2[:, 0], p0[:, 1] - p2[:, 1])
+        return a2 / np.maximum(np.maximum(e01, e12), e20)
 
-    tris = []
-    for jj in range(n_layers):
-        for kk in range(n_theta):
-            a, b = nid(jj, kk), nid(jj, kk + 1)
-            c, d = nid(jj + 1, kk), nid(jj + 1, kk + 1)
-            # index k runs counter-clockwise and j outward, so (k,j),(k,j+1),(k+1,j)
-            # is counter-clockwise.  Each quad is split along the diagonal that
-            # gives the larger smallest altitude (this avoids slivers at the
-            # sharp trailing edge).
-            split1 = [(a, c, b), (b, c, d)]
-            split2 = [(a, c, d), (a, d, b)]
-            q1 = min(min_altitude(t) for t in split1)
-            q2 = min(min_altitude(t) for t in split2)
-            tris.extend(split1 if q1 >= q2 else split2)
+    q1 = np.minimum(min_altitude(a, c, b), min_altitude(b, c, d))
+    q2 = np.minimum(min_altitude(a, c, d), min_altitude(a, d, b))
+    first = (q1 >= q2)[:, None]
+    t0 = np.where(first, np.stack([a, c, b], axis=1), np.stack([a, c, d], axis=1))
+    t1 = np.where(first, np.stack([b, c, d], axis=1), np.stack([a, d, b], axis=1))
+    tris = np.stack([t0, t1], axis=1).reshape(-1, 3)
     tri = np.asarray(tris, dtype=np.int32)
     kind = np.zeros(xy.shape[0], dtype=np.uint8)
     kind[:n_theta] = KIND_WALL
@@ -215,6 +216,15 @@ CONFIGS = {
         "hlbm_single", [[2048, 1024, 0, 0], [1025, 513, 512, 384], [1025, 513, 256, 128]],
         chord=200.0, mid=(412.0, 256.0), n_theta=1024, n_layers=195, stretch=1.01,
         ell_b_ratio=0.6, overlap=4.0, Re=1000.0, Ma=0.1, aoa_deg=0.0, steps=100000),
+    # Large Re: 8192x4096 coarse level with three nested factor-2 boxes of
+    # 4097x2049 nodes (each half its parent's extent per dimension), chord 800
+    # finest units, 4096 x 367-ring O-mesh (1 503 232 nodes, uniform layers: the
+    # first one about 0.002 chord), Re 10^4, Ma 0.1.
+    "hlbm_large": lambda: _mesh_case(
+        "hlbm_large", [[8192, 4096, 0, 0], [4097, 2049, 2048, 1536], [4097, 2049, 1024, 512],
+                       [4097, 2049, 1024, 512]],
+        chord=800.0, mid=(1648.0, 1024.0), n_theta=4096, n_layers=366, stretch=1.0,
+        ell_b_ratio=0.6, overlap=4.0, Re=1e4, Ma=0.1, aoa_deg=0.0, steps=200000),
     # Mesh-less channel (lattice and outer boundaries only).
     "channel": lambda: _channel("channel", 64, 32, Re=100.0, Ma=0.1, steps=100),
 }

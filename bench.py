@@ -11,7 +11,8 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64|fp16s
                 [--impl ours|reference]
 Beside the headline it reports the large-Re configuration (8192x4096 + three
 nested boxes, 1.5 M-node mesh, Re 10^4), where the finite-volume state no
-longer fits in L2, as "hlbm_large".
+longer fits in L2, as "hlbm_large", and the batched ensemble (64 cases,
+16 angles x 4 Reynolds numbers, one graph launch per coarse step) as "batched".
 Under torchrun (N > 1) each rank runs an independent replica (the step does
 not shard across GPUs here); value = all ranks' node updates / max time.
 """
@@ -305,6 +306,45 @@ def main():
                    "bytes_per_launch": fvb4, "launch_ms": fv4},
             "step": {"algorithmic_bytes": sb4, "achieved_gbs": sb4 / (ms4 * 1e-3) / 1e9,
                      "frac": sb4 / (ms4 * 1e-3) / 1e9 / peak}}
+        # ---- batched ensemble: 16 angles of attack x 4 Reynolds numbers
+        # (meshes of 20 k to 300 k nodes), FP32, one graph launch per coarse
+        # step for all 64 cases; the same cases stepped one after another for
+        # comparison
+        from workloads import ensemble
+        t0 = time.perf_counter()
+        ens = [H.Solver(c, precision=args.precision, use_graphs=True) for c in ensemble()]
+        t_setup = time.perf_counter() - t0
+        batch = H.Batch(ens)
+        per_b = batch.info("lattice_updates") + batch.info("fv_updates")
+        batch.step(2)
+        batch.sync()
+        kb = 10
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk_b:
+            e0.record(stream)
+            batch.step(kb)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms_b = e0.elapsed_time(e1) / kb
+        batch.close()
+        e0.record(stream)
+        for _ in range(kb):
+            for sv in ens:
+                sv.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_seq = e0.elapsed_time(e1) / kb
+        line["batched"] = {
+            "value": per_b / (ms_b * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms_b, "steps": kb,
+            "cases": len(ens), "precision": args.precision,
+            "config": "16 AoA (0..15 deg) x Re {500, 1000, 2000, 5000}; single-level lattices 512x256 .. "
+                      "2048x1024, meshes 20 480 .. 300 032 nodes, chord nx/10",
+            "node_updates_per_step": per_b, "gpu_launches": int(sum(sv.info("launches_per_step") for sv in ens) * kb),
+            "graph_launches": kb, "sequential": {"value": per_b / (ms_seq * 1e-3) / 1e6, "ms_per_step": ms_seq},
+            "setup_seconds": t_setup, "clocks": clk_b.summary()}
+        for sv in ens:
+            sv.close()
+        del ens
         # ---- end to end through the public API from host buffers: create
         # (host geometry -> device tables and state), K steps each followed by a
         # D2H read of the new force sample, final D2H of the mesh fields

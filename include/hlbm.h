@@ -189,6 +189,35 @@ int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double 
 int hlbm_wall_forces_static(const double *f, int n_nodes, const double *xy, const int32_t *edge_a,
                             const int32_t *edge_b, int n_edges, double qdyn, double *out, void *stream);
 
+/* Batched ensemble: many independent cases (angles of attack, Reynolds
+ * numbers, mesh sizes) advanced together.  The paper runs its angle-of-attack
+ * and Reynolds sweeps (Section 5) as separate simulations; a batch runs them
+ * side by side on one GPU.  hlbm_batch_create takes n contexts made by
+ * hlbm_create with use_graphs = 1 on the current device (the batch keeps
+ * pointers to them: they must outlive it) and builds two CUDA graphs, one per
+ * step parity, in which each context's coarse-step graph is a child graph on
+ * its own branch, with no dependency between cases; hlbm_batch_step then
+ * advances every case by one coarse step per graph launch, on `stream` (NULL:
+ * a stream of the batch's own), and the GPU runs the cases' kernels
+ * concurrently.  Each case's results are bitwise those of hlbm_step on it
+ * alone (the same kernels in the same order).  The batch stream first waits
+ * for the contexts' own streams, and the contexts' streams then wait for the
+ * batch, so readback with hlbm_fields / hlbm_forces orders after it.  A
+ * context stepped on its own after hlbm_batch_create (or consumed by
+ * hlbm_time_kernel) makes hlbm_batch_step return HLBM_ESTATE.  If any context
+ * has check_every > 0, hlbm_batch_step synchronises at the end and returns
+ * HLBM_ETIMEOUT / HLBM_EUNSTABLE if a case's health flag is set (the message
+ * names the case).  Errors: HLBM_EINVAL (no contexts, a NULL or repeated
+ * context, a context without graphs), HLBM_ECUDA. */
+typedef struct hlbm_batch hlbm_batch;
+int hlbm_batch_create(hlbm_ctx *const *ctxs, int n, void *stream, hlbm_batch **out);
+int hlbm_batch_step(hlbm_batch *b, int n_coarse);
+int hlbm_batch_sync(hlbm_batch *b);
+/* Message of the batch's last error (b == NULL: the last failing create). */
+const char *hlbm_batch_last_error(const hlbm_batch *b);
+/* Releases the batch (not its contexts). */
+int hlbm_batch_destroy(hlbm_batch *b);
+
 /* Wait for all work of the context. */
 int hlbm_sync(hlbm_ctx *ctx);
 

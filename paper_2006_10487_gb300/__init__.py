@@ -77,6 +77,12 @@ def lib():
         L.hlbm_destroy.argtypes = [C.c_void_p]
         L.hlbm_last_error.argtypes = [C.c_void_p]
         L.hlbm_last_error.restype = C.c_char_p
+        L.hlbm_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+        L.hlbm_batch_step.argtypes = [C.c_void_p, C.c_int]
+        L.hlbm_batch_sync.argtypes = [C.c_void_p]
+        L.hlbm_batch_destroy.argtypes = [C.c_void_p]
+        L.hlbm_batch_last_error.argtypes = [C.c_void_p]
+        L.hlbm_batch_last_error.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -224,6 +230,51 @@ class Solver:
         _check(self._lib.hlbm_populations(self.ctx, grid, out.ctypes.data_as(C.POINTER(C.c_double)), 9 * n),
                self.ctx)
         return out.reshape(n, 9)
+
+
+class Batch:
+    """Independent cases (Solvers created with use_graphs=True) advanced together:
+    one CUDA graph launch per coarse step runs every case's step on its own
+    branch (hlbm_batch_create / hlbm_batch_step).  The Solvers must outlive the
+    Batch; read results through them."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self._lib = lib()
+        self.solvers = list(solvers)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        arr = (C.c_void_p * len(self.solvers))(*[s.ctx for s in self.solvers])
+        b = C.c_void_p()
+        rc = self._lib.hlbm_batch_create(arr, len(self.solvers), C.c_void_p(stream), C.byref(b))
+        if rc != HLBM_OK:
+            raise HlbmError(rc, self._lib.hlbm_batch_last_error(None).decode())
+        self.b = b
+
+    def _check(self, rc):
+        if rc != HLBM_OK:
+            raise HlbmError(rc, self._lib.hlbm_batch_last_error(self.b).decode())
+
+    def step(self, n_coarse=1):
+        self._check(self._lib.hlbm_batch_step(self.b, int(n_coarse)))
+
+    def sync(self):
+        self._check(self._lib.hlbm_batch_sync(self.b))
+
+    def info(self, key):
+        """Sum over the cases of a Solver.info key (e.g. node updates per step)."""
+        return sum(s.info(key) for s in self.solvers)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self._lib.hlbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # names of the C ABI, for callers that prefer the flat interface

@@ -24,6 +24,7 @@ struct hlbm_ctx {
     void *alloc_ctx = nullptr;
     std::vector<void *> blocks;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraph_t graph_tmpl[2] = {nullptr, nullptr};  // the captured graphs (child graphs of a batch)
     bool use_graphs = false;
     long steps = 0;
     long forces_read = 0;
@@ -33,6 +34,19 @@ struct hlbm_ctx {
     int check_every = 0;
     double *d_out = nullptr;  // fields / populations scratch, 12 doubles per node of the largest grid
     size_t d_out_n = 0;
+    std::string err;
+};
+
+// A batch: independent contexts advanced by one graph launch per coarse step.
+struct hlbm_batch {
+    std::vector<hlbm_ctx *> ctx;
+    std::vector<long> base;            // each context's step count when the batch was made
+    std::vector<cudaEvent_t> ready;    // per context: its stream's pending work
+    cudaEvent_t done = nullptr;        // the batch stream's work
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    long steps = 0;
     std::string err;
 };
 
@@ -375,16 +389,18 @@ void capture_graphs(hlbm_ctx *c)
             throw;
         }
         ck(cudaStreamEndCapture(c->cap_stream, &g), "end capture");
+        c->graph_tmpl[k] = g;
         ck(cudaGraphInstantiate(&c->graph[k], g, 0), "graph instantiate");
-        cudaGraphDestroy(g);
     }
     set_phase(c, c->steps);
 }
 
 void release(hlbm_ctx *c)
 {
-    for (int k = 0; k < 2; k++)
+    for (int k = 0; k < 2; k++) {
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        if (c->graph_tmpl[k]) cudaGraphDestroy(c->graph_tmpl[k]);
+    }
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (void *p : c->blocks) {
         if (c->free_fn) c->free_fn(p, c->alloc_ctx);
@@ -726,6 +742,141 @@ int hlbm_destroy(hlbm_ctx *c)
     if (!c) return HLBM_OK;
     release(c);
     delete c;
+    return HLBM_OK;
+}
+
+static void batch_release(hlbm_batch *b)
+{
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (int k = 0; k < 2; k++)
+        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+    for (cudaEvent_t e : b->ready)
+        if (e) cudaEventDestroy(e);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+int hlbm_batch_create(hlbm_ctx *const *ctxs, int n, void *stream, hlbm_batch **out)
+{
+    if (!out) return fail(nullptr, HLBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || n < 1) return fail(nullptr, HLBM_EINVAL, "a batch needs at least one context");
+    for (int i = 0; i < n; i++) {
+        hlbm_ctx *c = ctxs[i];
+        if (!c) return fail(nullptr, HLBM_EINVAL, "context " + std::to_string(i) + " is NULL");
+        if (!c->use_graphs || !c->graph_tmpl[0] || !c->graph_tmpl[1])
+            return fail(nullptr, HLBM_EINVAL, "context " + std::to_string(i) + " was created without CUDA graphs");
+        if (c->timing_dirty)
+            return fail(nullptr, HLBM_ESTATE, "context " + std::to_string(i) + " was consumed by hlbm_time_kernel");
+        for (int j = 0; j < i; j++)
+            if (ctxs[j] == c) return fail(nullptr, HLBM_EINVAL, "context " + std::to_string(i) + " appears twice");
+    }
+    hlbm_batch *b = new hlbm_batch();
+    cudaGraph_t g = nullptr;
+    try {
+        b->ctx.assign(ctxs, ctxs + n);
+        for (hlbm_ctx *c : b->ctx) {
+            b->base.push_back(c->steps);
+            cudaEvent_t e = nullptr;
+            ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+            b->ready.push_back(e);
+        }
+        ck(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming), "event");
+        if (stream) {
+            b->stream = static_cast<cudaStream_t>(stream);
+        } else {
+            ck(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "stream");
+            b->own_stream = true;
+        }
+        // graph k: every context's coarse-step graph for its phase after k
+        // batch steps, as child graphs with no edges between them
+        for (int k = 0; k < 2; k++) {
+            ck(cudaGraphCreate(&g, 0), "graph create");
+            for (hlbm_ctx *c : b->ctx) {
+                cudaGraphNode_t node = nullptr;
+                ck(cudaGraphAddChildGraphNode(&node, g, nullptr, 0, c->graph_tmpl[(c->steps + k) & 1]), "child graph");
+            }
+            ck(cudaGraphInstantiate(&b->exec[k], g, 0), "graph instantiate");
+            cudaGraphDestroy(g);
+            g = nullptr;
+        }
+    } catch (const CudaError &e) {
+        if (g) cudaGraphDestroy(g);
+        batch_release(b);
+        delete b;
+        return fail(nullptr, HLBM_ECUDA, e.msg);
+    }
+    *out = b;
+    return HLBM_OK;
+}
+
+int hlbm_batch_step(hlbm_batch *b, int n_coarse)
+{
+    if (!b) return HLBM_EINVAL;
+    if (n_coarse < 0) { b->err = "n_coarse must be >= 0"; return HLBM_EINVAL; }
+    for (size_t i = 0; i < b->ctx.size(); i++) {
+        hlbm_ctx *c = b->ctx[i];
+        if (c->timing_dirty || c->steps != b->base[i] + b->steps) {
+            b->err = "context " + std::to_string(i) + " was advanced or consumed outside the batch";
+            return HLBM_ESTATE;
+        }
+    }
+    bool check = false;
+    try {
+        // the batch stream waits for whatever the contexts' own streams hold
+        for (size_t i = 0; i < b->ctx.size(); i++) {
+            ck(cudaEventRecord(b->ready[i], b->ctx[i]->stream), "event record");
+            ck(cudaStreamWaitEvent(b->stream, b->ready[i], 0), "stream wait");
+        }
+        for (int k = 0; k < n_coarse; k++) {
+            ck(cudaGraphLaunch(b->exec[b->steps & 1], b->stream), "graph launch");
+            b->steps++;
+            for (hlbm_ctx *c : b->ctx) {
+                c->steps++;
+                set_phase(c, c->steps);
+                if (c->check_every > 0 && (c->steps % c->check_every) == 0) check = true;
+            }
+        }
+        // later work on a context's own stream (readback, hlbm_step) follows the batch
+        ck(cudaEventRecord(b->done, b->stream), "event record");
+        for (hlbm_ctx *c : b->ctx) ck(cudaStreamWaitEvent(c->stream, b->done, 0), "stream wait");
+        if (check) {
+            ck(cudaStreamSynchronize(b->stream), "sync");
+            for (size_t i = 0; i < b->ctx.size(); i++) {
+                int flag = 0;
+                ck(cudaMemcpy(&flag, b->ctx[i]->dev.flag, sizeof(int), cudaMemcpyDeviceToHost), "flag");
+                if (flag & 2) {
+                    b->err = "case " + std::to_string(i) + ": a device-side wait gave up";
+                    return HLBM_ETIMEOUT;
+                }
+                if (flag) {
+                    b->err = "case " + std::to_string(i) + ": NaN in the force reduction (unstable)";
+                    return HLBM_EUNSTABLE;
+                }
+            }
+        }
+    } catch (const CudaError &e) {
+        b->err = e.msg;
+        return HLBM_ECUDA;
+    }
+    return HLBM_OK;
+}
+
+int hlbm_batch_sync(hlbm_batch *b)
+{
+    if (!b) return HLBM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) { b->err = cudaGetErrorString(e); return HLBM_ECUDA; }
+    return HLBM_OK;
+}
+
+const char *hlbm_batch_last_error(const hlbm_batch *b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+int hlbm_batch_destroy(hlbm_batch *b)
+{
+    if (!b) return HLBM_OK;
+    batch_release(b);
+    delete b;
     return HLBM_OK;
 }
 

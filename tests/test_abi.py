@@ -83,3 +83,15 @@ def test_rejects_bad_inputs(built):
 def test_explicit_sub_steps_are_kept(built):
     case = make_case("hlbm_mini2")
     assert H.hlbm_inspect(case, "n_sub", n_sub=37)[0] == 37
+
+
+def test_batch_create_rejects_bad_arguments(built):
+    import ctypes as C
+    import paper_2006_10487_gb300 as H
+    L = H.lib()
+    out = C.c_void_p()
+    assert L.hlbm_batch_create(None, 0, None, C.byref(out)) == H.HLBM_EINVAL
+    arr = (C.c_void_p * 2)(None, None)
+    assert L.hlbm_batch_create(arr, 2, None, C.byref(out)) == H.HLBM_EINVAL
+    assert out.value is None
+    assert "NULL" in L.hlbm_batch_last_error(None).decode()

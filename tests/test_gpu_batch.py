@@ -1,0 +1,57 @@
+"""Batched ensemble: cases advanced together by one graph launch per coarse
+step give, case by case, bitwise the results of stepping each case alone."""
+import numpy as np
+import pytest
+
+from workloads import make_case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_10487_gb300 import build
+    build.build()
+    import paper_2006_10487_gb300 as H
+    return H
+
+
+CASES = [("hlbm_small", 0.0, "fp32"), ("hlbm_small", 8.0, "fp16s"), ("hlbm_mini2", 3.0, "fp64"),
+         ("hlbm_mini2", 0.0, "fp32")]
+
+
+def grids(case):
+    return list(range(case.n_levels)) + [-1]
+
+
+def test_batch_matches_cases_stepped_alone(H):
+    cases = [make_case(n, aoa_deg=a) for n, a, _ in CASES]
+    alone = [H.Solver(c, precision=p) for c, (_, _, p) in zip(cases, CASES)]
+    grouped = [H.Solver(c, precision=p) for c, (_, _, p) in zip(cases, CASES)]
+    batch = H.Batch(grouped)
+    for s in alone:
+        s.step(5)
+    batch.step(2)
+    batch.step(3)  # odd then even phase start
+    for case, a, b in zip(cases, alone, grouped):
+        for g in grids(case):
+            for x, y in zip(a.fields(g), b.fields(g)):
+                assert np.array_equal(x, y, equal_nan=True)
+        fa, fb = a.forces(), b.forces()
+        assert len(fb[0]) == 5
+        assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
+    batch.close()
+
+
+def test_batch_refuses_a_case_stepped_outside_it(H):
+    solvers = [H.Solver(make_case("hlbm_mini2"), precision="fp32") for _ in range(2)]
+    batch = H.Batch(solvers)
+    batch.step(1)
+    solvers[1].step(1)
+    with pytest.raises(H.HlbmError) as e:
+        batch.step(1)
+    assert e.value.code == H.HLBM_ESTATE
+    batch.close()

@@ -9,7 +9,10 @@ from here and do their own set-up from them.
 """
 from .naca import (  # noqa: F401
     CONFIGS,
+    ENSEMBLE_SIZES,
     Case,
+    ensemble,
+    ensemble_case,
     make_case,
     naca0012_half_thickness,
     o_mesh,

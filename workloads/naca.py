@@ -228,3 +228,26 @@ CONFIGS = {
     # Mesh-less channel (lattice and outer boundaries only).
     "channel": lambda: _channel("channel", 64, 32, Re=100.0, Ma=0.1, steps=100),
 }
+
+
+# Batched ensemble: 16 angles of attack (0..15 degrees) x Re {500, 1000, 2000,
+# 5000}; per Re a single-level lattice and mesh of increasing size with chord
+# C = nx / 10: (nx, ny, N_theta, layers) = (512, 256, 256, 79) -> 20 480 mesh
+# nodes, (1024, 512, 512, 146) -> 75 264, (1536, 768, 768, 195) -> 150 528,
+# (2048, 1024, 1024, 292) -> 300 032.
+ENSEMBLE_SIZES = {500.0: (512, 256, 256, 79), 1000.0: (1024, 512, 512, 146),
+                  2000.0: (1536, 768, 768, 195), 5000.0: (2048, 1024, 1024, 292)}
+
+
+def ensemble_case(Re, aoa_deg):
+    """One case of the batched ensemble (see ENSEMBLE_SIZES)."""
+    nx, ny, n_theta, n_layers = ENSEMBLE_SIZES[float(Re)]
+    chord = nx / 10.0
+    return _mesh_case(f"ensemble_Re{int(Re)}_a{aoa_deg:g}", [[nx, ny, 0, 0]], chord=chord,
+                      mid=(0.3 * nx, 0.5 * ny), n_theta=n_theta, n_layers=n_layers, stretch=1.01,
+                      ell_b_ratio=0.6, overlap=4.0, Re=float(Re), Ma=0.1, aoa_deg=float(aoa_deg), steps=50000)
+
+
+def ensemble(aoas=tuple(range(16)), res=(500.0, 1000.0, 2000.0, 5000.0)):
+    """The batched ensemble's cases, Re-major."""
+    return [ensemble_case(Re, a) for Re in res for a in aoas]

@@ -60,6 +60,7 @@ def lib(openmp=False):
             L.orc_step_count.restype = C.c_long
             L.orc_n_forces.argtypes = [C.c_void_p]
             L.orc_forces.argtypes = [C.c_void_p, _dp, _dp]
+            L.orc_wall_coeffs.argtypes = [C.c_void_p, _dp]
             L.orc_fields.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp]
             L.orc_populations.argtypes = [C.c_void_p, C.c_int, _dp]
             L.orc_set_populations.argtypes = [C.c_void_p, C.c_int, _dp]
@@ -278,6 +279,15 @@ class Oracle:
         cd, cl = np.empty(n), np.empty(n)
         self._lib.orc_forces(self.h, _pd(cd), _pd(cl))
         return cd, cl
+
+    def wall_coeffs(self):
+        """Per wall node (ascending index), Eq. 12-13 of the current state:
+        columns x/C, side (+1 upper / -1 lower), C_p, C_f, C_n, |N_P|, n_x, n_y,
+        s_x, s_y (see orc_wall_coeffs)."""
+        n = self._lib.orc_wall_coeffs(self.h, None)
+        out = np.empty((n, 10))
+        self._lib.orc_wall_coeffs(self.h, _pd(out))
+        return out
 
     def table(self, name):
         n = self._lib.orc_table(self.h, name.encode(), None)

@@ -577,6 +577,7 @@ typedef struct {
     int L;
     olevel lv[8];
     double u0, nu, tau_u, dt_u, chord;
+    double pivot[2], ca, sa;    /* mesh pose: rotation by -alpha about the pivot */
     int n_sub;
     /* mesh */
     int n, ntri, nnz;
@@ -793,6 +794,62 @@ static void advance(orc *o, int c, double theta_next)
     }
 }
 
+/* Mean pressure and skin-friction coefficients (Eq. 12-13), per wall node.
+ * Node P carries N_P = half the sum of its wall edges' normals times length
+ * (into the fluid), so that the wall force above is exactly
+ *   sum_P [-(p_P - p0) N_P - Pi^neq_P N_P]
+ * with p = rho / 3 and p0 = 1/3.  With n = N_P / |N_P| and s the unit tangent
+ * pointing downstream along the chord, the viscous traction -Pi^neq n splits
+ * into a normal part c_n n and the wall shear stress tau_w s.  Per wall node
+ * (ascending node index) out[10] = (x/C along the chord from the leading
+ * edge, side (+1 upper, -1 lower surface), C_p, C_f = tau_w / q, C_n = c_n / q,
+ * |N_P|, n_x, n_y, s_x, s_y) with q = rho0 u0^2 / 2, rho0 = 1.  Returns the
+ * number of wall nodes (out may be NULL to query it). */
+int orc_wall_coeffs(const orc *o, double *out)
+{
+    int nw = 0;
+    for (int p = 0; p < o->n; p++) nw += o->kind[p] == 1;
+    if (!out || nw == 0) return nw;
+    double *N = calloc((size_t)o->n * 2, sizeof(double));
+    for (int e = 0; e < o->n_wedge; e++) {
+        int a = o->wea[e], b = o->web[e];
+        double dx = o->xy[2 * b] - o->xy[2 * a], dy = o->xy[2 * b + 1] - o->xy[2 * a + 1];
+        N[2 * a] += -0.5 * dy; N[2 * a + 1] += 0.5 * dx;
+        N[2 * b] += -0.5 * dy; N[2 * b + 1] += 0.5 * dx;
+    }
+    double q = 0.5 * o->u0 * o->u0;
+    double chx = o->ca, chy = -o->sa; /* body chord direction in the lattice frame */
+    int k = 0;
+    for (int p = 0; p < o->n; p++) {
+        if (o->kind[p] != 1) continue;
+        const double *g = o->g + 12 * (size_t)p;  /* rho, u, f^neq */
+        double pxx = 0.0, pxy = 0.0, pyy = 0.0;
+        for (int i = 0; i < 9; i++) {
+            pxx += CX[i] * CX[i] * g[3 + i];
+            pxy += CX[i] * CY[i] * g[3 + i];
+            pyy += CY[i] * CY[i] * g[3 + i];
+        }
+        double A = sqrt(N[2 * p] * N[2 * p] + N[2 * p + 1] * N[2 * p + 1]);
+        double nx = N[2 * p] / A, ny = N[2 * p + 1] / A;
+        double sx = -ny, sy = nx;
+        if (sx * chx + sy * chy < 0.0) { sx = -sx; sy = -sy; }
+        double tx = -(pxx * nx + pxy * ny), ty = -(pxy * nx + pyy * ny);
+        /* body-frame position: undo the rotation about the pivot (quarter chord) */
+        double dx = o->xy[2 * p] - o->pivot[0], dy = o->xy[2 * p + 1] - o->pivot[1];
+        double xb = o->ca * dx - o->sa * dy, yb = o->sa * dx + o->ca * dy;
+        double *r = out + 10 * (size_t)k++;
+        r[0] = xb / o->chord + 0.25;
+        r[1] = yb >= 0.0 ? 1.0 : -1.0;
+        r[2] = (g[0] - 1.0) / 3.0 / q;
+        r[3] = (tx * sx + ty * sy) / q;
+        r[4] = (tx * nx + ty * ny) / q;
+        r[5] = A;
+        r[6] = nx; r[7] = ny; r[8] = sx; r[9] = sy;
+    }
+    free(N);
+    return nw;
+}
+
 static void record_forces(orc *o)
 {
     if (!o->n) return;
@@ -906,6 +963,10 @@ orc *orc_create(int L, const int *levels, int n, const double *xy, int ntri, con
 
     /* mesh: rotate by -alpha about the pivot (positive alpha = nose up) */
     double al = aoa_deg * M_PI / 180.0, ca = cos(al), sa = sin(al);
+    o->pivot[0] = pivot[0];
+    o->pivot[1] = pivot[1];
+    o->ca = ca;
+    o->sa = sa;
     o->n = n;
     o->ntri = ntri;
     olevel *lf = &o->lv[L - 1];

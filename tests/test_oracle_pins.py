@@ -532,3 +532,82 @@ def test_refinement_interface_matches_the_single_grid_solution(orc):
     e2 = _advected_wave_error(orc, True)
     assert e1 < 1e-3
     assert e2 < 1.25 * e1
+
+
+# ---------------------------------------------------------------- Eq. 12-13 --
+def _wall_input_pose(case):
+    """Wall nodes (ascending index) in the input (zero-incidence) pose:
+    x/C from the leading edge and side, from the case geometry alone."""
+    w = np.flatnonzero(case.kind == 1)
+    le_x = case.pivot[0] - 0.25 * case.chord
+    xc = (case.xy[w, 0] - le_x) / case.chord
+    side = np.where(case.xy[w, 1] - case.pivot[1] >= 0.0, 1.0, -1.0)
+    return w, xc, side
+
+
+def test_wall_coefficients_reassemble_the_wall_force(orc):
+    """Eq. 12-13 per wall node, weighted by |N_P| and recombined with the node
+    normal and downstream tangent, give back the wall force of Eq. 10-11:
+    sum_P |N_P| [(-C_p + C_n) n + C_f s] / C = (C_D, C_L)."""
+    case = make_case("hlbm_small", aoa_deg=8.0)
+    o = orc.Oracle(case)
+    o.step(30)
+    w = o.wall_coeffs()
+    cd, cl = o.forces()
+    F = (w[:, 5, None] * ((-w[:, 2] + w[:, 4])[:, None] * w[:, 6:8] + w[:, 3, None] * w[:, 8:10])).sum(0)
+    F /= case.chord
+    assert abs(F[0] - cd[-1]) <= 1e-12 * abs(cd[-1])
+    assert abs(F[1] - cl[-1]) <= 1e-12 * abs(cd[-1])
+    assert np.ptp(w[:, 3]) > 0.1 and np.ptp(w[:, 2]) > 0.1  # a developing flow, not a trivial state
+
+
+def test_wall_geometry_of_the_coefficients(orc):
+    """Normals point away from the body (a convex section: away from mid-chord),
+    tangents are unit, orthogonal and downstream; x/C and side follow the
+    input pose."""
+    for aoa in (0.0, 8.0):
+        case = make_case("hlbm_small", aoa_deg=aoa)
+        o = orc.Oracle(case)
+        w = o.wall_coeffs()
+        idx, xc, side = _wall_input_pose(case)
+        assert w.shape == (idx.size, 10)
+        on_chord = np.abs(case.xy[idx, 1] - case.pivot[1]) < 1e-9 * case.chord  # leading / trailing edge
+        assert np.allclose(w[:, 0], xc, atol=1e-12)
+        assert np.array_equal(w[~on_chord, 1], side[~on_chord]) and on_chord.sum() <= 2
+        al = np.radians(aoa)
+        chord_dir = np.array([np.cos(al), -np.sin(al)])     # rotated by -alpha (nose up)
+        mid = np.array(case.pivot) + 0.25 * case.chord * chord_dir
+        # rotated wall positions from the input pose
+        d = case.xy[idx] - np.array(case.pivot)
+        pos = np.array(case.pivot) + np.stack([np.cos(al) * d[:, 0] + np.sin(al) * d[:, 1],
+                                               np.cos(al) * d[:, 1] - np.sin(al) * d[:, 0]], axis=1)
+        n, s = w[:, 6:8], w[:, 8:10]
+        assert np.all(((pos - mid) * n).sum(1) > 0)
+        assert np.allclose(np.hypot(*n.T), 1) and np.allclose(np.hypot(*s.T), 1)
+        assert np.allclose((n * s).sum(1), 0, atol=1e-14)
+        assert np.all(s @ chord_dir >= 0)
+
+
+def test_wall_coefficients_of_prescribed_states(orc):
+    """Uniform pressure at rest: C_p = (rho - 1) / 3 / (u0^2 / 2), no traction.
+    Pure shear f^neq (only Pi_xy = sigma): traction -sigma (n_y, n_x)."""
+    case = make_case("hlbm_small")
+    o = orc.Oracle(case)
+    q = 0.5 * (case.Ma / np.sqrt(3.0)) ** 2
+    rho = 1.003
+    f = np.tile(orc.feq(rho, 0.0, 0.0), (case.n_nodes, 1))
+    o.set_populations(-1, f)
+    w = o.wall_coeffs()
+    assert np.allclose(w[:, 2], (rho - 1.0) / 3.0 / q, rtol=1e-12)
+    assert np.abs(w[:, 3:5]).max() <= 1e-12
+    sigma = 2e-5
+    neq = np.zeros(9)
+    neq[[5, 7]] = sigma / 4.0      # c_x c_y = +1
+    neq[[6, 8]] = -sigma / 4.0     # c_x c_y = -1
+    o.set_populations(-1, np.tile(orc.feq(1.0, 0.0, 0.0) + neq, (case.n_nodes, 1)))
+    w = o.wall_coeffs()
+    n, s = w[:, 6:8], w[:, 8:10]
+    t = -sigma * np.stack([n[:, 1], n[:, 0]], axis=1)
+    assert np.allclose(w[:, 3], (t * s).sum(1) / q, rtol=1e-9, atol=1e-12)
+    assert np.allclose(w[:, 4], (t * n).sum(1) / q, rtol=1e-9, atol=1e-12)
+    assert np.abs(w[:, 2]).max() <= 1e-12

@@ -306,6 +306,52 @@ def main():
                    "bytes_per_launch": fvb4, "launch_ms": fv4},
             "step": {"algorithmic_bytes": sb4, "achieved_gbs": sb4 / (ms4 * 1e-3) / 1e9,
                      "frac": sb4 / (ms4 * 1e-3) / 1e9 / peak}}
+        # ---- Eq. 14: measured gain G = T_h / T_eq (time per finest step of the
+        # hybrid run over that of the equivalent uniform lattice) beside the
+        # paper's model (1 + chi s' n) / g with this run's measured constants
+        from workloads import uniform_equivalent
+        from paper_2006_10487_gb300 import post
+        ueq = uniform_equivalent(case)
+        s5 = H.Solver(ueq, precision=args.precision, use_graphs=True)
+        s5.step(3)
+        s5.sync()
+        e0.record(stream)
+        s5.step(20)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_eq = e0.elapsed_time(e1) / 20
+        n_eq = s5.info("lattice_updates")
+        s5.close()
+        f_steps = 2 ** (case.n_levels - 1)
+        t_h = ms / args.steps / f_steps
+        n_s = (per_step - case.n_nodes * n_sub * f_steps) / f_steps   # structured updates per finest step
+        chi = case.n_nodes / n_s
+        s_prime = (fv_ms / case.n_nodes) / (t_eq / n_eq)
+        g_ratio = n_eq / n_s
+        line["gain"] = {"G_measured": t_h / t_eq, "G_model": post.gain_model(chi, s_prime, n_sub, g_ratio),
+                        "T_h_ms": t_h, "T_eq_ms": t_eq, "chi": chi, "s_prime": s_prime, "n": n_sub, "g": g_ratio,
+                        "uniform_lattice": ueq.levels.tolist()[0][:2]}
+        # ---- Eq. 12-13 at 8 degrees (the paper's case for the mean C_p / C_f
+        # figures): 1000 coarse steps of transient, then 1000 averaged -- a
+        # window that ends before the onset of the finite-volume scheme's
+        # instability in the separated shear layer (about step 2400 here)
+        c8 = make_case(WORKLOAD, aoa_deg=8.0)
+        s6 = H.Solver(c8, precision=args.precision, use_graphs=True, wall_stats=True, force_cap=16384)
+        s6.step(1000)
+        s6.forces()
+        s6.wall_stats_reset()
+        s6.step(1000)
+        w8, n8 = s6.wall_stats()
+        cd8, cl8 = s6.forces()
+        s6.close()
+        u0 = case.Ma / math.sqrt(3.0)
+        line["post"] = {"aoa_deg": 8.0, "coarse_steps": 2000, "averaged_steps": n8,
+                        "window": "coarse steps 1000-2000, before the instability onset (~2400)",
+                        "cd_mean": float(cd8.mean()), "cl_mean": float(cl8.mean()),
+                        "cl_rms": float(cl8.std()),
+                        "x_sep_upper": post.separation_point(w8, +1.0),
+                        "strouhal": post.strouhal(cl8, 2 ** (c8.n_levels - 1), c8.chord, u0),
+                        "cp_min": float(w8[:, 2].min()), "cf_max": float(w8[:, 3].max())}
         # ---- batched ensemble: 16 angles of attack x 4 Reynolds numbers
         # (meshes of 20 k to 300 k nodes), FP32, one graph launch per coarse
         # step for all 64 cases; the same cases stepped one after another for

@@ -87,7 +87,10 @@ typedef struct {
  * stream: cudaStream_t to run on (NULL: the legacy default stream).
  * alloc/free/alloc_ctx: optional device allocator (e.g. PyTorch's caching
  * allocator); NULL alloc means cudaMalloc/cudaFree.  use_graphs: capture one
- * coarse step as a CUDA graph (1, default when the struct is zeroed is 0). */
+ * coarse step as a CUDA graph (1, default when the struct is zeroed is 0).
+ * wall_stats: 1 adds to every coarse step the accumulation of the wall
+ * coefficients read by hlbm_wall_stats (one small kernel over the wall
+ * nodes); 0 leaves the step as it is. */
 typedef struct {
     int32_t precision;
     int32_t n_sub;
@@ -100,6 +103,7 @@ typedef struct {
     void (*free)(void *ptr, void *alloc_ctx);
     void *alloc_ctx;
     int32_t use_graphs;
+    int32_t wall_stats;
 } hlbm_options;
 
 typedef struct hlbm_ctx hlbm_ctx;
@@ -163,7 +167,8 @@ int hlbm_time_kernel(hlbm_ctx *ctx, const char *kernel, int reps, double *avg_ms
  * "is_node", "is_don", "is_w" (Eq. 8 stencils), "ring", "ring_don",
  * "ring_w" (Eq. 9 stencils), "wall_edges", "n_sub", "inactive<l>" (1 for
  * nodes of level l that are not computed), "perm" (input node of each device
- * row).  out == NULL queries n. */
+ * row), "wall_geo" ([n_wall][7]: x/C, side, |N_P|, n_x, n_y, s_x, s_y of the
+ * wall nodes, see hlbm_wall_stats).  out == NULL queries n. */
 int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re, double Ma,
                  double aoa_deg, const hlbm_options *opt, const char *table, double *out,
                  size_t cap, size_t *n);
@@ -188,6 +193,26 @@ int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double 
  * calls that overlap on the GPU race and must be ordered. */
 int hlbm_wall_forces_static(const double *f, int n_nodes, const double *xy, const int32_t *edge_a,
                             const int32_t *edge_b, int n_edges, double qdyn, double *out, void *stream);
+
+/* Mean pressure and skin-friction coefficients along the wall (Eq. 12-13:
+ * C_p = (p - p0) / (rho0 u0^2 / 2), C_f = tau_w / (rho0 u0^2 / 2), with
+ * p = rho / 3, p0 = 1/3, rho0 = 1), averaged over the coarse steps since
+ * hlbm_create or hlbm_wall_stats_reset (one sample at the end of each coarse
+ * step; needs options.wall_stats = 1, else HLBM_ESTATE).  Wall node P
+ * carries N_P = half the sum of its wall edges' normals times length (into the
+ * fluid), so that the force of Eq. 10-11 is exactly sum_P [-(p - p0) N_P -
+ * Pi^neq N_P]; with n = N_P / |N_P| and s the unit tangent pointing
+ * downstream along the chord, the viscous traction -Pi^neq n = c_n n +
+ * tau_w s.  out receives, per wall node in ascending input index, 10 doubles
+ * (x/C from the leading edge in the body frame, side (+1 upper, -1 lower
+ * surface), mean C_p, mean C_f, mean C_n = c_n / q, |N_P|, n_x, n_y, s_x,
+ * s_y), so sum_P |N_P| [(-C_p + C_n) n + C_f s] / C is the mean (C_D, C_L).
+ * cap is the capacity of out in doubles; *n_wall receives the wall node
+ * count and *n_samples the number of coarse steps averaged.  out == NULL
+ * queries the sizes.  Accumulation is FP64 in every precision. */
+int hlbm_wall_stats(hlbm_ctx *ctx, double *out, size_t cap, int *n_wall, long *n_samples);
+/* Restart the averages of hlbm_wall_stats from the next coarse step. */
+int hlbm_wall_stats_reset(hlbm_ctx *ctx);
 
 /* Batched ensemble: many independent cases (angles of attack, Reynolds
  * numbers, mesh sizes) advanced together.  The paper runs its angle-of-attack

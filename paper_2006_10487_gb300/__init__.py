@@ -45,7 +45,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class hlbm_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("n_sub", C.c_int32), ("seed", C.c_uint64), ("perturb", C.c_double),
                 ("force_cap", C.c_int32), ("check_every", C.c_int32), ("stream", C.c_void_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("use_graphs", C.c_int32)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("use_graphs", C.c_int32),
+                ("wall_stats", C.c_int32)]
 
 
 _lib = None
@@ -77,6 +78,8 @@ def lib():
         L.hlbm_destroy.argtypes = [C.c_void_p]
         L.hlbm_last_error.argtypes = [C.c_void_p]
         L.hlbm_last_error.restype = C.c_char_p
+        L.hlbm_wall_stats.argtypes = [C.c_void_p, dp, C.c_size_t, ip, C.POINTER(C.c_long)]
+        L.hlbm_wall_stats_reset.argtypes = [C.c_void_p]
         L.hlbm_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
         L.hlbm_batch_step.argtypes = [C.c_void_p, C.c_int]
         L.hlbm_batch_sync.argtypes = [C.c_void_p]
@@ -97,7 +100,7 @@ def _check(rc, ctx=None):
 
 
 def _marshal(case, precision="fp64", n_sub=None, seed=None, perturb=None, force_cap=0, check_every=0,
-             stream=None, use_graphs=True, allocator=None):
+             stream=None, use_graphs=True, allocator=None, wall_stats=False):
     """C structures for a workloads.Case (kept alive by the returned tuple)."""
     lv = (hlbm_level * case.n_levels)(*[hlbm_level(*map(int, r)) for r in case.levels])
     xy = np.ascontiguousarray(case.xy, dtype=np.float64).reshape(-1)
@@ -121,6 +124,7 @@ def _marshal(case, precision="fp64", n_sub=None, seed=None, perturb=None, force_
     o.check_every = int(check_every)
     o.stream = stream
     o.use_graphs = 1 if use_graphs else 0
+    o.wall_stats = 1 if wall_stats else 0
     if allocator is not None:
         o.alloc, o.free = allocator
     return lv, m, o, (xy, tri, kind)
@@ -156,7 +160,7 @@ class Solver:
     """One HLBM simulation on the current CUDA device (wraps an hlbm_ctx)."""
 
     def __init__(self, case, precision="fp64", n_sub=None, seed=None, perturb=None, force_cap=0, check_every=0,
-                 use_graphs=True, stream=None, torch_memory=True):
+                 use_graphs=True, stream=None, torch_memory=True, wall_stats=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the HLBM library needs a CUDA device (there is no CPU fallback)")
@@ -164,7 +168,7 @@ class Solver:
             stream = torch.cuda.current_stream().cuda_stream
         self._alloc = _torch_allocator() if torch_memory else None
         self._args = _marshal(case, precision, n_sub, seed, perturb, force_cap, check_every, stream, use_graphs,
-                              self._alloc)
+                              self._alloc, wall_stats)
         lv, m, o, _ = self._args
         ctx = C.c_void_p()
         self._lib = lib()
@@ -172,6 +176,20 @@ class Solver:
                                      C.byref(ctx)))
         self.ctx = ctx
         self.case = case
+
+    def wall_stats(self):
+        """Mean wall coefficients since creation or the last reset (Eq. 12-13):
+        ([n_wall, 10] array with columns x/C, side, C_p, C_f, C_n, |N_P|, n_x,
+        n_y, s_x, s_y; see hlbm_wall_stats), number of coarse steps averaged."""
+        nw, ns = C.c_int(), C.c_long()
+        _check(self._lib.hlbm_wall_stats(self.ctx, None, 0, C.byref(nw), C.byref(ns)), self.ctx)
+        out = np.empty((nw.value, 10))
+        _check(self._lib.hlbm_wall_stats(self.ctx, out.ctypes.data_as(C.POINTER(C.c_double)), out.size,
+                                         C.byref(nw), C.byref(ns)), self.ctx)
+        return out, ns.value
+
+    def wall_stats_reset(self):
+        _check(self._lib.hlbm_wall_stats_reset(self.ctx), self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

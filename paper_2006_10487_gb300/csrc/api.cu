@@ -27,6 +27,7 @@ struct hlbm_ctx {
     cudaGraph_t graph_tmpl[2] = {nullptr, nullptr};  // the captured graphs (child graphs of a batch)
     bool use_graphs = false;
     long steps = 0;
+    long stats_base = 0;  // coarse step at which the wall-coefficient sums were last cleared
     long forces_read = 0;
     long launches = 0;            // kernels enqueued by the scheduler (counter)
     long launches_per_step = 0;   // kernels of one coarse step
@@ -148,6 +149,10 @@ template <typename T, typename S> void coarse_step(hlbm_ctx *c, cudaStream_t s)
     if (c->dev.m.n > 0) {
         launch_forces<T, S>(c->dev, s);
         c->launches += 2;
+        if (c->dev.m.wall_stats) {
+            launch_wall_stats<T, S>(c->dev, s);
+            c->launches += 1;
+        }
     }
     c->launches_per_step = c->launches - before;
 }
@@ -318,6 +323,14 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     M.web = upload(c, eb);
     M.wn = upload(c, wn);
     M.inv = upload(c, P.inv);
+    if (M.wall_stats && P.n_wall > 0) {
+        std::vector<double> ns(4 * size_t(P.n_wall));
+        for (int w = 0; w < P.n_wall; w++)
+            for (int k = 0; k < 4; k++) ns[4 * size_t(w) + k] = P.wall_geo[7 * size_t(w) + 3 + k];
+        M.wall_ns = upload(c, ns);
+        M.wall_acc = (double *)dalloc(c, 3 * size_t(P.n_wall) * sizeof(double));
+        ck(cudaMemsetAsync(M.wall_acc, 0, 3 * size_t(P.n_wall) * sizeof(double), c->stream), "memset");
+    }
 }
 
 template <typename T, typename S> void build_device(hlbm_ctx *c)
@@ -444,6 +457,7 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
     c->free_fn = o.alloc ? o.free : nullptr;
     c->alloc_ctx = o.alloc_ctx;
     c->use_graphs = o.use_graphs != 0;
+    c->dev.m.wall_stats = o.wall_stats != 0;
     c->check_every = std::max(0, o.check_every);
     c->dev.force_cap = o.force_cap > 0 ? o.force_cap : 4096;
     try {
@@ -634,7 +648,9 @@ int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double 
     if (t == "rowptr") put_i(P.rowptr);
     else if (t == "col") put_i(P.col);
     else if (t == "perm") put_i(P.perm);
+    else if (t == "wall_geo") v = P.wall_geo;
     else if (t == "perm") put_i(P.perm);
+    else if (t == "wall_geo") v = P.wall_geo;
     else if (t == "sx") v = P.sx;
     else if (t == "sy") v = P.sy;
     else if (t == "cc") v = P.cc;
@@ -742,6 +758,54 @@ int hlbm_destroy(hlbm_ctx *c)
     if (!c) return HLBM_OK;
     release(c);
     delete c;
+    return HLBM_OK;
+}
+
+int hlbm_wall_stats(hlbm_ctx *c, double *out, size_t cap, int *n_wall, long *n_samples)
+{
+    if (!c || !n_wall || !n_samples) return c ? fail(c, HLBM_EINVAL, "n_wall and n_samples are required") : HLBM_EINVAL;
+    const DevMesh &M = c->dev.m;
+    if (!M.wall_stats) return fail(c, HLBM_ESTATE, "the context was created without wall_stats");
+    const int nw = c->plan.n_wall;
+    *n_wall = nw;
+    *n_samples = c->steps - c->stats_base;
+    if (!out) return HLBM_OK;
+    if (cap < 10 * size_t(nw)) return fail(c, HLBM_EINVAL, "output capacity too small");
+    if (c->timing_dirty) return fail(c, HLBM_ESTATE, "the state was consumed by hlbm_time_kernel");
+    std::vector<double> acc(3 * size_t(nw));
+    try {
+        if (nw > 0) {
+            ck(cudaMemcpyAsync(acc.data(), M.wall_acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+               "D2H");
+            ck(cudaStreamSynchronize(c->stream), "sync");
+        }
+    } catch (const CudaError &e) {
+        return fail(c, HLBM_ECUDA, e.msg);
+    }
+    const double inv = *n_samples > 0 ? 1.0 / double(*n_samples) : 0.0;
+    for (int w = 0; w < nw; w++) {
+        const double *g = &c->plan.wall_geo[7 * size_t(w)];
+        double *r = out + 10 * size_t(w);
+        r[0] = g[0];
+        r[1] = g[1];
+        r[2] = acc[w] * inv;
+        r[3] = acc[size_t(nw) + w] * inv;
+        r[4] = acc[2 * size_t(nw) + w] * inv;
+        for (int k = 0; k < 5; k++) r[5 + k] = g[2 + k];
+    }
+    return HLBM_OK;
+}
+
+int hlbm_wall_stats_reset(hlbm_ctx *c)
+{
+    if (!c) return HLBM_EINVAL;
+    const DevMesh &M = c->dev.m;
+    if (!M.wall_stats) return fail(c, HLBM_ESTATE, "the context was created without wall_stats");
+    if (c->plan.n_wall > 0) {
+        cudaError_t e = cudaMemsetAsync(M.wall_acc, 0, 3 * size_t(c->plan.n_wall) * sizeof(double), c->stream);
+        if (e != cudaSuccess) return fail(c, HLBM_ECUDA, cudaGetErrorString(e));
+    }
+    c->stats_base = c->steps;
     return HLBM_OK;
 }
 

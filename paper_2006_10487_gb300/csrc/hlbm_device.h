@@ -54,6 +54,10 @@ struct DevMesh {
     int n_edges = 0;
     int *wea = nullptr, *web = nullptr;  // wall edges, device-order nodes
     double *wn = nullptr;                // [n_edges][2] normal times length, into the fluid
+    // wall coefficients (Eq. 12-13): per wall row, unit normal and downstream
+    // tangent [n_wall][4]; FP64 sums of C_p, C_f, C_n [3][n_wall]
+    int wall_stats = 0;
+    double *wall_ns = nullptr, *wall_acc = nullptr;
     int *inv = nullptr;                  // input node -> device node
 };
 
@@ -91,6 +95,8 @@ template <typename T, typename S> void launch_ring_interp(const DevCtx &, bool q
 template <typename T, typename S> void launch_hole_interp(const DevCtx &, cudaStream_t);
 template <typename T, typename S> void launch_fv(const DevCtx &, int m, cudaStream_t);
 template <typename T, typename S> void launch_forces(const DevCtx &, cudaStream_t);
+// adds this state's wall coefficients to the sums (Eq. 12-13)
+template <typename T, typename S> void launch_wall_stats(const DevCtx &, cudaStream_t);
 template <typename T, typename S> void launch_fields(const DevCtx &, int grid, double *rho, double *ux, double *uy, double *pop, cudaStream_t);
 
 }  // namespace hlbm

@@ -57,6 +57,9 @@ struct Plan {
     std::vector<double> ring_w;  // [n_ring][9]
     // wall edges (a -> b, fluid on the left), input order
     std::vector<int> wea, web;
+    // wall nodes (ascending input index = device rows 0 .. n_wall-1):
+    // [n_wall][7] = x/C, side, |N_P|, n_x, n_y, s_x, s_y (Eq. 12-13)
+    std::vector<double> wall_geo;
 };
 
 // Builds the plan; returns HLBM_OK or an error code with a message in err.

@@ -857,6 +857,31 @@ __global__ void __launch_bounds__(kForceThreads) k_forces_partial(const T *g, in
         partial[2 * blockIdx.x + 1] = fy;
     }
 }
+// Eq. 12-13 at the wall rows (device rows 0 .. n_wall-1): C_p = (rho - 1) / 3 / q
+// and the viscous traction -Pi^neq n split along the unit normal n and the
+// downstream tangent s (C_n, C_f), added to FP64 sums [3][n_wall].
+template <typename T>
+__global__ void k_wall_stats(const T *g, int Np, int n_wall, const double *ns, double *acc, double inv_q)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_wall) return;
+    T q[12];
+    mesh_q(g, Np, r, q);
+    double pxx = 0, pxy = 0, pyy = 0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const double nq = double(q[3 + i]);
+        pxx += cx(i) * cx(i) * nq;
+        pxy += cx(i) * cy(i) * nq;
+        pyy += cy(i) * cy(i) * nq;
+    }
+    const double nx = ns[4 * r], ny = ns[4 * r + 1], sx = ns[4 * r + 2], sy = ns[4 * r + 3];
+    const double tx = -(pxx * nx + pxy * ny), ty = -(pxy * nx + pyy * ny);
+    acc[r] += (double(q[0]) - 1.0) / 3.0 * inv_q;
+    acc[size_t(n_wall) + r] += (tx * sx + ty * sy) * inv_q;
+    acc[size_t(2) * n_wall + r] += (tx * nx + ty * ny) * inv_q;
+}
+
 
 __global__ void __launch_bounds__(kForceThreads) k_forces_final(const double *partial, int n_part, double qdyn,
                                                                 double *buf, int *counter, int cap, int *flag)
@@ -1076,6 +1101,14 @@ template <typename T, typename S> void launch_forces(const DevCtx &C, cudaStream
                                                C.force_cap, C.flag);
 }
 
+template <typename T, typename S> void launch_wall_stats(const DevCtx &C, cudaStream_t s)
+{
+    const DevMesh &m = C.m;
+    if (!m.wall_stats || m.n_wall == 0) return;
+    k_wall_stats<T><<<cdiv(m.n_wall, 128), 128, 0, s>>>((const T *)m.g[m.gcur], m.Np, m.n_wall, m.wall_ns, m.wall_acc,
+                                                        1.0 / (0.5 * C.u0 * C.u0));
+}
+
 template <typename T, typename S>
 void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *uy, double *pop, cudaStream_t s)
 {
@@ -1106,6 +1139,7 @@ void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *u
     template void launch_hole_interp<T, S>(const DevCtx &, cudaStream_t);                                        \
     template void launch_fv<T, S>(const DevCtx &, int, cudaStream_t);                                            \
     template void launch_forces<T, S>(const DevCtx &, cudaStream_t);                                             \
+    template void launch_wall_stats<T, S>(const DevCtx &, cudaStream_t);                                         \
     template void launch_fields<T, S>(const DevCtx &, int, double *, double *, double *, double *, cudaStream_t);
 HLBM_INSTANTIATE(float, float)
 HLBM_INSTANTIATE(double, double)

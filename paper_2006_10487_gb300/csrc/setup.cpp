@@ -310,6 +310,32 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
             P.web.push_back(ib);
         }
 
+    // ---- wall nodes for the wall coefficients: N_P from the edge normals,
+    // downstream tangent, body-frame chord position (pivot = quarter chord)
+    {
+        std::vector<double> N(2 * size_t(P.n), 0.0);
+        for (size_t e = 0; e < P.wea.size(); e++) {
+            const int a = P.wea[e], b = P.web[e];
+            const double ex = P.xy[2 * b] - P.xy[2 * a], ey = P.xy[2 * b + 1] - P.xy[2 * a + 1];
+            for (int v : {a, b}) {
+                N[2 * v] -= 0.5 * ey;
+                N[2 * v + 1] += 0.5 * ex;
+            }
+        }
+        const double chx = ca, chy = -sa;  // chord direction after the rotation
+        for (int p = 0; p < P.n; p++) {
+            if (P.kind[p] != HLBM_NODE_WALL) continue;
+            const double A = std::hypot(N[2 * p], N[2 * p + 1]);
+            if (!(A > 0.0)) { err = "wall node without wall edges"; return HLBM_EINVAL; }
+            const double nx = N[2 * p] / A, ny = N[2 * p + 1] / A;
+            double sx = -ny, sy = nx;
+            if (sx * chx + sy * chy < 0.0) { sx = -sx; sy = -sy; }
+            const double bx = m->xy[2 * p] - px, by = m->xy[2 * p + 1] - py;  // input pose
+            const double g7[7] = {bx / m->chord + 0.25, by >= 0.0 ? 1.0 : -1.0, A, nx, ny, sx, sy};
+            P.wall_geo.insert(P.wall_geo.end(), g7, g7 + 7);
+        }
+    }
+
     // ---- finest level: nodes inside the rotated hole ellipse are not computed.
     // Membership: rotate the node back by +alpha about the pivot and test
     // ((X - cx)/a)^2 + ((Y - cy)/b)^2 < 1 (this arithmetic is fixed so that

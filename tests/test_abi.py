@@ -95,3 +95,18 @@ def test_batch_create_rejects_bad_arguments(built):
     assert L.hlbm_batch_create(arr, 2, None, C.byref(out)) == H.HLBM_EINVAL
     assert out.value is None
     assert "NULL" in L.hlbm_batch_last_error(None).decode()
+
+
+@pytest.mark.parametrize("aoa", [0.0, 8.0])
+def test_wall_geometry_matches_oracle(built, orc, aoa):
+    """Host set-up of the wall coefficients (chord position, side, |N_P|,
+    normal, downstream tangent) against the oracle's."""
+    import paper_2006_10487_gb300 as H
+    case = make_case("hlbm_small", aoa_deg=aoa)
+    geo = H.hlbm_inspect(case, "wall_geo").reshape(-1, 7)
+    w = orc.Oracle(case).wall_coeffs()
+    assert geo.shape[0] == w.shape[0]
+    assert np.allclose(geo[:, 0], w[:, 0], atol=1e-12)
+    off = np.abs(w[:, 1] - geo[:, 1]) > 0
+    assert off.sum() <= 2  # leading / trailing edge lie on the chord line
+    assert np.allclose(geo[:, 2:], w[:, 5:], rtol=1e-12, atol=1e-13)

@@ -216,6 +216,52 @@ def test_large_re_fp32_and_fp16s_against_fp64(H):
         sol.close()
 
 
+def test_wall_stats_match_oracle(H, orc):
+    """Mean C_p, C_f, C_n per wall node (Eq. 12-13), accumulated on the GPU
+    (FP64) over 12 coarse steps, against the oracle's per-step values averaged
+    over the same steps; then again after a reset."""
+    case = make_case("hlbm_small", aoa_deg=8.0)
+    sol = H.Solver(case, precision="fp64", wall_stats=True)
+    sim = orc.Oracle(case)
+    acc = 0.0
+    for _ in range(12):
+        sol.step(1)
+        sim.step(1)
+        acc = acc + sim.wall_coeffs()
+    got, n = sol.wall_stats()
+    want = acc / 12
+    assert n == 12 and got.shape == want.shape
+    assert np.allclose(got[:, 0], want[:, 0], atol=1e-12)
+    assert np.allclose(got[:, 5:], want[:, 5:], rtol=1e-12, atol=1e-13)
+    for col in (2, 3, 4):
+        assert np.abs(got[:, col] - want[:, col]).max() <= FP64_TOL * np.abs(want[:, col]).max()
+    sol.wall_stats_reset()
+    acc = 0.0
+    for _ in range(3):
+        sol.step(1)
+        sim.step(1)
+        acc = acc + sim.wall_coeffs()
+    got, n = sol.wall_stats()
+    assert n == 3
+    for col in (2, 3, 4):
+        assert np.abs(got[:, col] - acc[:, col] / 3).max() <= FP64_TOL * np.abs(acc[:, col] / 3).max()
+
+
+def test_wall_stats_reassemble_the_mean_forces(H):
+    """In FP32: sum_P |N_P| [(-C_p + C_n) n + C_f s] / C of the mean
+    coefficients is the mean of the recorded (C_D, C_L)."""
+    case = make_case("hlbm_small", aoa_deg=8.0)
+    sol = H.Solver(case, precision="fp32", wall_stats=True)
+    sol.step(40)
+    w, n = sol.wall_stats()
+    cd, cl = sol.forces()
+    F = (w[:, 5, None] * ((-w[:, 2] + w[:, 4])[:, None] * w[:, 6:8] + w[:, 3, None] * w[:, 8:10])).sum(0)
+    F /= case.chord
+    assert n == 40 == len(cd)
+    assert abs(F[0] - cd.mean()) <= 1e-9 * abs(cd.mean())
+    assert abs(F[1] - cl.mean()) <= 1e-9 * abs(cd.mean())
+
+
 def test_graphs_and_plain_launches_agree_bitwise(H):
     case = make_case("hlbm_mini2")
     a = H.Solver(case, precision="fp64", use_graphs=True)

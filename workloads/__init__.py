@@ -16,4 +16,5 @@ from .naca import (  # noqa: F401
     make_case,
     naca0012_half_thickness,
     o_mesh,
+    uniform_equivalent,
 )

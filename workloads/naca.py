@@ -173,12 +173,22 @@ def _mesh_case(name, levels, chord, mid, n_theta, n_layers, stretch, ell_b_ratio
                 n_layers=n_layers, **kw)
 
 
-def _channel(name, nx, ny, Re, Ma, steps):
+def _channel(name, nx, ny, Re, Ma, steps, chord=None):
     return Case(name=name, levels=np.asarray([[nx, ny, 0, 0]], dtype=np.int32),
                 xy=np.zeros((0, 2)), tri=np.zeros((0, 3), dtype=np.int32),
-                kind=np.zeros(0, dtype=np.uint8), chord=float(ny), pivot=(0.0, 0.0),
-                hole=(0.0, 0.0, 0.0, 0.0), Re=float(Re), Ma=float(Ma), aoa_deg=0.0,
+                kind=np.zeros(0, dtype=np.uint8), chord=float(ny if chord is None else chord),
+                pivot=(0.0, 0.0), hole=(0.0, 0.0, 0.0, 0.0), Re=float(Re), Ma=float(Ma), aoa_deg=0.0,
                 steps=steps)
+
+
+def uniform_equivalent(case):
+    """The lattice an equivalent plain LBM would use for `case` (Eq. 14's
+    T_eq): one level at the finest resolution over the whole domain, with the
+    same viscosity in finest units (same chord length scale and Re)."""
+    f = 2 ** (case.n_levels - 1)
+    nx, ny = int(case.levels[0][0]), int(case.levels[0][1])
+    return _channel(case.name + "_uniform", (nx - 1) * f + 1, (ny - 1) * f + 1, case.Re, case.Ma,
+                    case.steps, chord=case.chord)
 
 
 def make_case(name, aoa_deg=None, **overrides):

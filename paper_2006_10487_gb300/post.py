@@ -27,6 +27,8 @@ def strouhal(cl, dt, chord, u0, skip=0):
         return None
     spec = np.abs(np.fft.rfft(x * np.hanning(n)))
     k = 1 + int(np.argmax(spec[1:]))
+    if k < 3:  # fewer than three periods in the series: no frequency resolved
+        return None
     delta = 0.0
     if 1 <= k < spec.size - 1 and spec[k - 1] > 0 and spec[k + 1] > 0:
         a, b, c = np.log(spec[k - 1]), np.log(spec[k]), np.log(spec[k + 1])

@@ -16,6 +16,7 @@ def test_strouhal_of_a_sampled_sinusoid():
     assert abs(st - st_true) <= 5e-3 * st_true
     assert post.strouhal(np.full(100, 0.2), dt, chord, u0) is None
     assert post.strouhal(np.where(t < t[-1] / 2, cl, np.nan), dt, chord, u0) is None
+    assert post.strouhal(cl[:2000], dt, chord, u0) is None  # 1.9 periods: not resolved
 
 
 def test_separation_point_from_skin_friction():

@@ -473,6 +473,17 @@ __device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigne
     return d;
 }
 
+// Two FP32 values in one register pair, with the paired operations above.
+struct F2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ F2 f2(float lo, float hi) { return {pk2(lo, hi)}; }
+__device__ __forceinline__ F2 f2(float a) { return {pk2(a, a)}; }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return {add2(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return {sub2(a.v, b.v)}; }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return {mul2(a.v, b.v)}; }
+__device__ __forceinline__ F2 fmaf2(F2 a, F2 b, F2 c) { return {fma2(a.v, b.v, c.v)}; }
+
 // Eq. 3, one explicit sub-step on every mesh node (node-major gather over the
 // sliced-ELL operator rows, no atomics), on the (rho, u, f^neq) state:
 //   acc_i = dt sum_k (c_i . s_Pk) (g_i(P_k) - g_i(P)) - dt/tau_u sum_k C_Pk f^neq_i(P_k)
@@ -740,35 +751,68 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
     // [f^eq_c(rho', u') - f^eq_c(rho_P, u_P)] / w_c for a direction c with E = E_c(u_P)
     auto fd = [&](T E, T cdu, T csu) { return drho * E + rho * (T(3) * cdu + T(4.5) * cdu * csu - ddot); };
     T nq[9];
-    {  // axis directions 3 (-1, 0) and 4 (0, -1)
-        const T E3 = E0 - T(3) * uPx + T(4.5) * uPx * uPx;
-        const T eq3 = -E3 * Dx + T(3) * Qxx - T(4.5) * Mx + T(1.5) * Lx;
-        nq[3] = nP[3] - U3 - W3 + T(1.0 / 9.0) * eq3 + nP[3] * (Sa - csP) - T(1.0 / 9.0) * fd(E3, -dux, -sx);
-        const T E4 = E0 - T(3) * uPy + T(4.5) * uPy * uPy;
-        const T eq4 = -E4 * Dy + T(3) * Qyy - T(4.5) * My + T(1.5) * Ly;
-        nq[4] = nP[4] - V4 - W4 + T(1.0 / 9.0) * eq4 + nP[4] * (Sb - csP) - T(1.0 / 9.0) * fd(E4, -duy, -sy);
-    }
-    {  // diagonals 5 (1, 1) and 7 (-1, -1)
-        const T q = uPx + uPy, A = E0 + T(4.5) * q * q, B = T(3) * q;
-        const T Pd = Dx + Dy, C = T(3) * (Qxx + Qxy + Qyy);
-        const T Z = T(4.5) * (Mx + My + Mxxy + Mxyy) - T(1.5) * (Lx + Ly);
-        const T odd = A * Pd + Z, even = B * Pd + C;  // eq5 = even + odd, eq7 = even - odd
-        const T cdu = dux + duy, csu = sx + sy;
-        nq[5] = nP[5] + U5 + V5 - W5 + T(1.0 / 36.0) * (even + odd) - nP[5] * (Sa + Sb + csP) -
-                T(1.0 / 36.0) * fd(A + B, cdu, csu);
-        nq[7] = nP[7] - U7 - V7 - W7 + T(1.0 / 36.0) * (even - odd) + nP[7] * (Sa + Sb - csP) -
-                T(1.0 / 36.0) * fd(A - B, -cdu, -csu);
-    }
-    {  // diagonals 6 (-1, 1) and 8 (1, -1)
-        const T q = uPy - uPx, A = E0 + T(4.5) * q * q, B = T(3) * q;
-        const T Pd = Dy - Dx, C = T(3) * (Qxx - Qxy + Qyy);
-        const T Z = T(4.5) * (-Mx + My + Mxxy - Mxyy) - T(1.5) * (Ly - Lx);
-        const T odd = A * Pd + Z, even = B * Pd + C;  // eq6 = even + odd, eq8 = even - odd
-        const T cdu = duy - dux, csu = sy - sx;
-        nq[6] = nP[6] - U6 + V6 - W6 + T(1.0 / 36.0) * (even + odd) - nP[6] * (Sb - Sa + csP) -
-                T(1.0 / 36.0) * fd(A + B, cdu, csu);
-        nq[8] = nP[8] + U8 - V8 - W8 + T(1.0 / 36.0) * (even - odd) + nP[8] * (Sb - Sa - csP) -
-                T(1.0 / 36.0) * fd(A - B, -cdu, -csu);
+    if constexpr (sizeof(T) == 4) {
+        // the same on pairs of directions: (3, 4) mirror each other in x <-> y;
+        // (5, 6) and (7, 8) are the two diagonal families' + and - members
+        const F2 U = f2(uPx, uPy);
+        const F2 E34 = fmaf2(f2(4.5f) * U, U, f2(E0) - f2(3.f) * U);
+        const F2 eq34 = f2(3.f) * f2(Qxx, Qyy) + f2(1.5f) * f2(Lx, Ly) - E34 * f2(Dx, Dy) - f2(4.5f) * f2(Mx, My);
+        const F2 n34 = f2(nP[3], nP[4]);
+        const F2 cdu34 = f2(-dux, -duy), csu34 = f2(-sx, -sy);
+        const F2 fd34 = fmaf2(f2(drho), E34,
+                              f2(rho) * (fmaf2(f2(4.5f) * cdu34, csu34, f2(3.f) * cdu34) - f2(ddot)));
+        const F2 nq34 = n34 - f2(U3, V4) - f2(W3, W4) + fmaf2(n34, f2(Sa - csP, Sb - csP), f2(1.f / 9.f) * (eq34 - fd34));
+        const F2 q = f2(uPx + uPy, uPy - uPx);
+        const F2 A = fmaf2(f2(4.5f) * q, q, f2(E0)), B = f2(3.f) * q;
+        const F2 Pd = f2(Dx + Dy, Dy - Dx);
+        const F2 Cq = f2(3.f) * f2(Qxx + Qyy + Qxy, Qxx + Qyy - Qxy);
+        const F2 Z = f2(4.5f) * f2(Mx + My + Mxxy + Mxyy, My - Mx + Mxxy - Mxyy) - f2(1.5f) * f2(Lx + Ly, Ly - Lx);
+        const F2 odd = fmaf2(A, Pd, Z), even = fmaf2(B, Pd, Cq);
+        const F2 cdu = f2(dux + duy, duy - dux), csu = f2(sx + sy, sy - sx);
+        const F2 t3 = fmaf2(f2(4.5f) * cdu, csu, f2(3.f) * cdu);  // 3 c.du + 9/2 (c.du)(c.su), + members
+        const F2 t3m = fmaf2(f2(4.5f) * cdu, csu, f2(-3.f) * cdu);  // the same for - members
+        const F2 fdp = fmaf2(f2(drho), A + B, f2(rho) * (t3 - f2(ddot)));
+        const F2 fdm = fmaf2(f2(drho), A - B, f2(rho) * (t3m - f2(ddot)));
+        const F2 n56 = f2(nP[5], nP[6]), n78 = f2(nP[7], nP[8]);
+        const F2 nq56 = n56 + f2(U5 + V5 - W5, V6 - U6 - W6) - n56 * f2(Sa + Sb + csP, Sb - Sa + csP) +
+                        f2(1.f / 36.f) * (even + odd - fdp);
+        const F2 nq78 = n78 - f2(U7 + V7 + W7, V8 - U8 + W8) + n78 * f2(Sa + Sb - csP, Sb - Sa - csP) +
+                        f2(1.f / 36.f) * (even - odd - fdm);
+        float x0, x1;
+        upk2(nq34.v, x0, x1); nq[3] = x0; nq[4] = x1;
+        upk2(nq56.v, x0, x1); nq[5] = x0; nq[6] = x1;
+        upk2(nq78.v, x0, x1); nq[7] = x0; nq[8] = x1;
+    } else {
+        {  // axis directions 3 (-1, 0) and 4 (0, -1)
+            const T E3 = E0 - T(3) * uPx + T(4.5) * uPx * uPx;
+            const T eq3 = -E3 * Dx + T(3) * Qxx - T(4.5) * Mx + T(1.5) * Lx;
+            nq[3] = nP[3] - U3 - W3 + T(1.0 / 9.0) * eq3 + nP[3] * (Sa - csP) - T(1.0 / 9.0) * fd(E3, -dux, -sx);
+            const T E4 = E0 - T(3) * uPy + T(4.5) * uPy * uPy;
+            const T eq4 = -E4 * Dy + T(3) * Qyy - T(4.5) * My + T(1.5) * Ly;
+            nq[4] = nP[4] - V4 - W4 + T(1.0 / 9.0) * eq4 + nP[4] * (Sb - csP) - T(1.0 / 9.0) * fd(E4, -duy, -sy);
+        }
+        {  // diagonals 5 (1, 1) and 7 (-1, -1)
+            const T q = uPx + uPy, A = E0 + T(4.5) * q * q, B = T(3) * q;
+            const T Pd = Dx + Dy, C = T(3) * (Qxx + Qxy + Qyy);
+            const T Z = T(4.5) * (Mx + My + Mxxy + Mxyy) - T(1.5) * (Lx + Ly);
+            const T odd = A * Pd + Z, even = B * Pd + C;  // eq5 = even + odd, eq7 = even - odd
+            const T cdu = dux + duy, csu = sx + sy;
+            nq[5] = nP[5] + U5 + V5 - W5 + T(1.0 / 36.0) * (even + odd) - nP[5] * (Sa + Sb + csP) -
+                    T(1.0 / 36.0) * fd(A + B, cdu, csu);
+            nq[7] = nP[7] - U7 - V7 - W7 + T(1.0 / 36.0) * (even - odd) + nP[7] * (Sa + Sb - csP) -
+                    T(1.0 / 36.0) * fd(A - B, -cdu, -csu);
+        }
+        {  // diagonals 6 (-1, 1) and 8 (1, -1)
+            const T q = uPy - uPx, A = E0 + T(4.5) * q * q, B = T(3) * q;
+            const T Pd = Dy - Dx, C = T(3) * (Qxx - Qxy + Qyy);
+            const T Z = T(4.5) * (-Mx + My + Mxxy - Mxyy) - T(1.5) * (Ly - Lx);
+            const T odd = A * Pd + Z, even = B * Pd + C;  // eq6 = even + odd, eq8 = even - odd
+            const T cdu = duy - dux, csu = sy - sx;
+            nq[6] = nP[6] - U6 + V6 - W6 + T(1.0 / 36.0) * (even + odd) - nP[6] * (Sb - Sa + csP) -
+                    T(1.0 / 36.0) * fd(A + B, cdu, csu);
+            nq[8] = nP[8] + U8 - V8 - W8 + T(1.0 / 36.0) * (even - odd) + nP[8] * (Sb - Sa - csP) -
+                    T(1.0 / 36.0) * fd(A - B, -cdu, -csu);
+        }
     }
     if (r < n_wall) {
         ux = T(0);

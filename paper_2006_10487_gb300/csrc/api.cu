@@ -227,12 +227,18 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
             if (P.col[k] != old) ks.push_back(k);
         return ks;
     };
+    std::vector<int> town(M.n_tiles);
     for (int t = 0; t < M.n_tiles; t++) {
         std::vector<int> &h = halo[t];
-        for (int r = t * kTileRows; r < std::min(P.n, (t + 1) * kTileRows); r++)
+        // the tile's own rows are in the list too (their state is read from
+        // it); consecutive rows, so one contiguous run of the sorted list
+        for (int r = t * kTileRows; r < std::min(P.n, (t + 1) * kTileRows); r++) {
+            h.push_back(r);
             for (int k : off_diag(P.perm[r])) h.push_back(P.inv[P.col[k]]);
+        }
         std::sort(h.begin(), h.end());
         h.erase(std::unique(h.begin(), h.end()), h.end());
+        town[t] = int(std::lower_bound(h.begin(), h.end(), t * kTileRows) - h.begin());
         hptr[t + 1] = hptr[t] + int(h.size());
         hnodes.insert(hnodes.end(), h.begin(), h.end());
         M.max_halo = std::max(M.max_halo, int(h.size()));
@@ -279,6 +285,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     sptr.resize(size_t(4) * M.n_tiles + 1, int(ent.size()));
     for (int t = 0; t < M.n_tiles; t++) M.max_tile_ent = std::max(M.max_tile_ent, sptr[4 * t + 4] - sptr[4 * t]);
     M.halo_ptr = upload(c, hptr);
+    M.tile_own = upload(c, town);
     M.halo_nodes = upload(c, hnodes);
     // mbarrier (16 B), the tile's entries, the halo states
     M.smem_bytes = 16 + size_t(M.max_tile_ent) * sizeof(E) + size_t(M.max_halo) * 9 * sizeof(T);

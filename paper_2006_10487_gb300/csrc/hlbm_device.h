@@ -43,6 +43,7 @@ struct DevMesh {
     // halo_nodes[halo_ptr[t] .. halo_ptr[t+1]) and entry columns index that list
     int n_tiles = 0, max_halo = 0;
     int *halo_ptr = nullptr, *halo_nodes = nullptr;
+    int *tile_own = nullptr;  // position of tile t's first own row in its halo list (own rows are a run)
     size_t smem_bytes = 0;
     void *Q0 = nullptr, *Q1 = nullptr;  // [12][n_ring] Eq. 9 data at t and t + 1
     int n_is = 0;

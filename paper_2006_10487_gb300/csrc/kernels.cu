@@ -511,8 +511,8 @@ __device__ __forceinline__ F2 fmaf2(F2 a, F2 b, F2 c) { return {fma2(a.v, b.v, c
 // (4 consecutive slices, one contiguous block) into shared memory, and every
 // thread loads up to kFvHaloRegs of the tile's halo node indices into
 // registers.  After the wait the states of every node the tile touches (its
-// sorted halo list) are gathered into shared memory, plane-major, in one
-// round of loads; then each thread treats one row, reading its entries and its
+// sorted halo list, the tile's own rows included) are gathered into shared
+// memory, plane-major, in one round of loads; then each thread treats one row, reading its entries and its
 // neighbours from shared memory.
 constexpr int kFvThreads = kTileRows;
 constexpr int kFvGroup = 2;
@@ -546,12 +546,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
+__global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 8 : 1) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
                                                    const int *__restrict__ slice_ptr,
                                                    const int *__restrict__ slice_len,
                                                    const typename Ent<T>::type *__restrict__ ent, int max_tile_ent,
                                                    const int *__restrict__ halo_ptr,
-                                                   const int *__restrict__ halo_nodes, T dt_tau,
+                                                   const int *__restrict__ halo_nodes,
+                                                   const int *__restrict__ tile_own, T dt_tau,
                                                    int n_wall, int ring_start, int n_ring,
                                                    const T *__restrict__ Q0, const T *__restrict__ Q1, T theta_next,
                                                    T scale5, int star, int *flag)
@@ -582,7 +583,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
     // Let the next sub-step's blocks start as soon as SM slots free up; they
     // only read constant operator data until their griddepcontrol.wait.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int h0 = halo_ptr[t], hn = halo_ptr[t + 1] - h0;
+    const int h0 = halo_ptr[t], hn = halo_ptr[t + 1] - h0, own = tile_own[t];
     const int r = t * blockDim.x + threadIdx.x;
     const int rr = r < n ? r : n - 1;
     const int sl = rr >> 5;
@@ -595,8 +596,6 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
     }
     // wait until the previous sub-step (which wrote g) has completed
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    T r1P, uPx, uPy, nP[9];
-    load_mesh(g, Np, rr, r1P, uPx, uPy, nP);  // issued before the halo gather
 #pragma unroll
     for (int j = 0; j < kFvHaloRegs; j++) {
         const int h = threadIdx.x + j * kFvThreads;
@@ -619,6 +618,17 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const T *__restrict__ g, T *_
         return;
     }
     if (r >= n) return;
+    // own state from the staged list
+    T r1P, uPx, uPy, nP[9];
+    {
+        const int p = own + threadIdx.x;
+        r1P = sh[p];
+        uPx = sh[hn + p];
+        uPy = sh[2 * hn + p];
+#pragma unroll
+        for (int i = 3; i < 9; i++) nP[i] = sh[i * hn + p];
+        neq_complete(nP);
+    }
     // own node: no streaming term (g(P) - g(P) = 0), collision weight C_PP = 11/18
     // f^neq part of the sums, over the six stored planes j = 3..8 only:
     //   U_j = sum_k a_k n_j(P_k), V_j = sum_k b_k n_j(P_k), W_j = sum_k cs_k n_j(P_k)
@@ -1126,8 +1136,9 @@ template <typename T, typename S> void launch_fv(const DevCtx &C, int msub, cuda
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, k_fv<T>, (const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
                        (const int *)m.slice_ptr, (const int *)m.slice_len, (const typename Ent<T>::type *)m.ent,
-                       m.max_tile_ent, (const int *)m.halo_ptr, (const int *)m.halo_nodes, dt_tau, m.n_wall,
-                       m.ring_start, m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5, star, C.flag);
+                       m.max_tile_ent, (const int *)m.halo_ptr, (const int *)m.halo_nodes, (const int *)m.tile_own,
+                       dt_tau, m.n_wall, m.ring_start, m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5,
+                       star, C.flag);
 }
 
 template <typename T, typename S> void configure_fv(size_t bytes)

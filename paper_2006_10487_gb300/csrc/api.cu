@@ -19,6 +19,11 @@ struct hlbm_ctx {
     DevCtx dev;
     cudaStream_t stream = nullptr;    // caller's stream
     cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+    // second branch of the step: a level's boundary-ring kernel runs beside the
+    // reads of its interior that follow, where the plan shows them disjoint
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool side_ok[hlbm::kMaxLevels] = {};
     void *(*alloc_fn)(size_t, void *) = nullptr;
     void (*free_fn)(void *, void *) = nullptr;
     void *alloc_ctx = nullptr;
@@ -103,10 +108,24 @@ template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double thet
 
 // One step of level lvl on its own clock; theta: parent-time fraction at the
 // end of the step (refills the boundary ring by prolongation).
+// Branch of the step graph: work enqueued on c->side between fork and join
+// runs beside the work enqueued on s in between.
+void fork(hlbm_ctx *c, cudaStream_t s)
+{
+    ck(cudaEventRecord(c->ev_fork, s), "event record");
+    ck(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "stream wait");
+}
+void join(hlbm_ctx *c, cudaStream_t s)
+{
+    ck(cudaEventRecord(c->ev_join, c->side), "event record");
+    ck(cudaStreamWaitEvent(s, c->ev_join, 0), "stream wait");
+}
+
 template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double theta, cudaStream_t s)
 {
     DevCtx &D = c->dev;
     bool hybrid = (lvl == D.L - 1) && D.m.n > 0;
+    bool child = lvl < D.L - 1;
     if (hybrid) {
         launch_ring_interp<T, S>(D, false, s);  // Eq. 9 data at t
         launch_hole_interp<T, S>(D, s);         // Eq. 4: post-collision of the hole boundary
@@ -114,11 +133,21 @@ template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double t
     }
     launch_collide<T, S>(D, lvl, s);  // Eq. 1
     D.lv[lvl].parity ^= 1;
-    if (lvl == 0) launch_outer_bc<T, S>(D, s);
-    else launch_prolong<T, S>(D, lvl, theta, s);
+    // The level's boundary ring (outer conditions / prolongation) is written
+    // beside what reads the level's interior next: the child's band snapshot
+    // (joined in advance) or the ring data of the mesh (joined here).
+    const bool branch = c->side_ok[lvl] && (child || hybrid);
+    cudaStream_t sb = s;
+    if (branch) {
+        fork(c, s);
+        sb = c->side;
+    }
+    if (lvl == 0) launch_outer_bc<T, S>(D, sb);
+    else launch_prolong<T, S>(D, lvl, theta, sb);
     c->launches += 2;
     if (hybrid) {
         launch_ring_interp<T, S>(D, true, s);  // Eq. 9 data at t + 1, ring state of sub-step 0
+        if (branch) join(c, s);
         for (int m = 0; m < D.n_sub; m++) {  // Eq. 3, Eq. 5-7, wall rule
             launch_fv<T, S>(D, m, s);
             D.m.gcur ^= 1;
@@ -135,6 +164,7 @@ template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double thet
     level_step<T, S>(c, lvl, theta, s);
     if (child) {
         launch_snapshot<T, S>(D, lvl, true, s);
+        if (c->side_ok[lvl]) join(c, s);
         advance<T, S>(c, lvl + 1, 0.5, s);
         advance<T, S>(c, lvl + 1, 1.0, s);
         launch_restrict<T, S>(D, lvl, s);
@@ -415,6 +445,31 @@ void capture_graphs(hlbm_ctx *c)
     set_phase(c, c->steps);
 }
 
+// Where the boundary-ring kernel of a level may run beside the next reads of
+// its interior.  With the in-place AA layout a node's state at odd parity sits
+// in its neighbours' slots, so the written and read regions must be apart by
+// a margin: a child box at least 4 nodes inside its parent (the band read
+// around it, one node wider, against the ring written at the edge), and ring
+// interpolation donors at least 3 nodes from the finest level's edge.
+void set_branches(hlbm_ctx *c)
+{
+    const Plan &P = c->plan;
+    for (int l = 0; l < P.L; l++) {
+        const LevelPlan &lp = P.lv[l];
+        bool ok = false;
+        if (lp.has_child) {
+            ok = lp.cox >= 4 && lp.coy >= 4 && lp.cox + lp.cmx <= lp.nx - 5 && lp.coy + lp.cmy <= lp.ny - 5;
+        } else if (l == P.L - 1 && P.n > 0 && !P.ring_don.empty()) {
+            ok = true;
+            for (int d : P.ring_don) {
+                const int x = d % lp.nx, y = d / lp.nx;
+                if (x < 3 || y < 3 || x > lp.nx - 4 || y > lp.ny - 4) { ok = false; break; }
+            }
+        }
+        c->side_ok[l] = ok;
+    }
+}
+
 void release(hlbm_ctx *c)
 {
     for (int k = 0; k < 2; k++) {
@@ -428,6 +483,9 @@ void release(hlbm_ctx *c)
     }
     c->blocks.clear();
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
 }
 
 }  // namespace
@@ -469,6 +527,10 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
     c->dev.force_cap = o.force_cap > 0 ? o.force_cap : 4096;
     try {
         ck(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "stream create");
+        ck(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "stream create");
+        ck(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event create");
+        ck(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event create");
+        set_branches(c);
         if (c->plan.precision == HLBM_FP32) build_device<float, float>(c);
         else if (c->plan.precision == HLBM_FP16S) build_device<float, __half>(c);
         else build_device<double, double>(c);

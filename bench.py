@@ -243,6 +243,7 @@ def main():
     # ---- roofline of the dominant kernel (finite-volume sub-step), measured
     # live with CUDA events on the library's stream
     peak, peak_kind = _peaks()
+    fv_variant = [s.info("fv_variant"), s.info("fv_tune_us1"), s.info("fv_tune_us2")]
     fv_ms = s.time_kernel("fv", 200)
     fv_bytes = s.info("fv_bytes")
     fv_gbs = fv_bytes / (fv_ms * 1e-3) / 1e9
@@ -254,6 +255,8 @@ def main():
                 "peak": peak, "unit": "GB/s", "frac": fv_gbs / peak, "peak_kind": peak_kind,
                 "traffic": _traffic("k_fv", args.precision), "bytes_per_launch": fv_bytes,
                 "launch_ms": fv_ms,
+                "autotuner": {"variant": fv_variant[0], "us_7_blocks_per_sm": fv_variant[1],
+                              "us_8_blocks_per_sm": fv_variant[2]},
                 "step": {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / args.steps * 1e-3) / 1e9,
                          "frac": step_bytes / (ms / args.steps * 1e-3) / 1e9 / peak}}
 
@@ -293,6 +296,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms4 = e0.elapsed_time(e1) / k4
+        var4 = s4.info("fv_variant")
         fv4 = s4.time_kernel("fv", 230)
         fvb4 = s4.info("fv_bytes")
         sb4 = sum(s4.info(f"collide_bytes{lv}") * 2 ** lv for lv in range(big.n_levels)) + \
@@ -303,6 +307,7 @@ def main():
             "precision": args.precision, "levels": big.levels.tolist(), "mesh_nodes": big.n_nodes,
             "Re": big.Re, "node_updates_per_step": per4,
             "fv": {"achieved": fvb4 / (fv4 * 1e-3) / 1e9, "unit": "GB/s", "frac": fvb4 / (fv4 * 1e-3) / 1e9 / peak,
+                   "autotuner_variant": var4,
                    "bytes_per_launch": fvb4, "launch_ms": fv4},
             "step": {"algorithmic_bytes": sb4, "achieved_gbs": sb4 / (ms4 * 1e-3) / 1e9,
                      "frac": sb4 / (ms4 * 1e-3) / 1e9 / peak}}

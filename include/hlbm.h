@@ -90,7 +90,10 @@ typedef struct {
  * coarse step as a CUDA graph (1, default when the struct is zeroed is 0).
  * wall_stats: 1 adds to every coarse step the accumulation of the wall
  * coefficients read by hlbm_wall_stats (one small kernel over the wall
- * nodes); 0 leaves the step as it is. */
+ * nodes); 0 leaves the step as it is.  fv_variant: register bound of the
+ * FP32 finite-volume kernel: 0 times both on this mesh at create and keeps the
+ * faster (the block-shape autotuner), 1 bounded for 7 resident blocks per SM,
+ * 2 for 8; both give the same results (FP64 is not bounded; reports 1). */
 typedef struct {
     int32_t precision;
     int32_t n_sub;
@@ -104,6 +107,7 @@ typedef struct {
     void *alloc_ctx;
     int32_t use_graphs;
     int32_t wall_stats;
+    int32_t fv_variant;
 } hlbm_options;
 
 typedef struct hlbm_ctx hlbm_ctx;
@@ -150,7 +154,9 @@ int hlbm_populations(hlbm_ctx *ctx, int grid, double *out, size_t cap);
  * "launches_per_step" (kernels in one coarse step), "fv_bytes" (algorithmic
  * bytes of one finite-volume sub-step), "collide_bytes<l>" (algorithmic bytes
  * of one lattice step of level l), "fv_tiles" (blocks of one finite-volume
- * sub-step), "fv_smem" (their dynamic shared memory, bytes). */
+ * sub-step), "fv_smem" (their dynamic shared memory, bytes), "fv_variant"
+ * (the register bound in use, see options), "fv_tune_us1" / "fv_tune_us2"
+ * (the autotuner's launch times of the two bounds, 0 if it did not run). */
 int hlbm_info(const hlbm_ctx *ctx, const char *key, double *value);
 
 /* Measurement hook: runs one kernel of the step `reps` times back to back on

@@ -24,6 +24,8 @@ struct hlbm_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool side_ok[hlbm::kMaxLevels] = {};
+    int fv_variant_opt = 0;
+    double fv_tune_us[2] = {0.0, 0.0};
     void *(*alloc_fn)(size_t, void *) = nullptr;
     void (*free_fn)(void *, void *) = nullptr;
     void *alloc_ctx = nullptr;
@@ -422,6 +424,12 @@ template <typename T, typename S> void build_device(hlbm_ctx *c)
     c->d_out_n = maxnodes;
     c->d_out = (double *)dalloc(c, maxnodes * 12 * sizeof(double));
     init_state<T, S>(c);
+    if (P.n > 0) {
+        if (c->plan.precision == HLBM_FP64) D.m.fv_variant = 1;
+        else if (c->fv_variant_opt > 0) D.m.fv_variant = c->fv_variant_opt;
+        else D.m.fv_variant = fv_autotune<T, S>(D, c->stream, c->fv_tune_us);
+        ck(cudaGetLastError(), "finite-volume autotuner");
+    }
 }
 
 void capture_graphs(hlbm_ctx *c)
@@ -523,6 +531,8 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
     c->alloc_ctx = o.alloc_ctx;
     c->use_graphs = o.use_graphs != 0;
     c->dev.m.wall_stats = o.wall_stats != 0;
+    if (o.fv_variant < 0 || o.fv_variant > 2) { delete c; return fail(nullptr, HLBM_EINVAL, "fv_variant must be 0, 1 or 2"); }
+    c->fv_variant_opt = o.fv_variant;
     c->check_every = std::max(0, o.check_every);
     c->dev.force_cap = o.force_cap > 0 ? o.force_cap : 4096;
     try {
@@ -680,6 +690,9 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
     } else if (k == "fv_updates") *value = double(P.n) * P.n_sub * double(1L << (P.L - 1));
     else if (k == "launches_per_step") *value = double(c->launches_per_step);
     else if (k == "fv_tiles") *value = double(c->dev.m.n_tiles);
+    else if (k == "fv_variant") *value = double(c->dev.m.fv_variant);
+    else if (k == "fv_tune_us1") *value = c->fv_tune_us[0];
+    else if (k == "fv_tune_us2") *value = c->fv_tune_us[1];
     else if (k == "fv_smem") *value = double(c->dev.m.smem_bytes);
     else if (k == "fv_bytes") {
         // algorithmic bytes of one finite-volume sub-step: the 9 state values of

@@ -545,8 +545,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kFvThreads, sizeof(T) == 4 ? 8 : 1) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
+// MINB: blocks per SM the register allocation is bounded for (1: unbounded);
+// the FP32 kernel is built for 7 and 8, and each context keeps the faster one
+// for its mesh (fv_autotune); FP64 is built unbounded.
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
                                                    const int *__restrict__ slice_ptr,
                                                    const int *__restrict__ slice_len,
                                                    const typename Ent<T>::type *__restrict__ ent, int max_tile_ent,
@@ -1134,16 +1137,69 @@ template <typename T, typename S> void launch_fv(const DevCtx &C, int msub, cuda
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_fv<T>, (const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
-                       (const int *)m.slice_ptr, (const int *)m.slice_len, (const typename Ent<T>::type *)m.ent,
-                       m.max_tile_ent, (const int *)m.halo_ptr, (const int *)m.halo_nodes, (const int *)m.tile_own,
-                       dt_tau, m.n_wall, m.ring_start, m.n_ring, (const T *)m.Q0, (const T *)m.Q1, theta_next, scale5,
-                       star, C.flag);
+    auto go = [&](auto kern) {
+        cudaLaunchKernelEx(&cfg, kern, (const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
+                           (const int *)m.slice_ptr, (const int *)m.slice_len, (const typename Ent<T>::type *)m.ent,
+                           m.max_tile_ent, (const int *)m.halo_ptr, (const int *)m.halo_nodes,
+                           (const int *)m.tile_own, dt_tau, m.n_wall, m.ring_start, m.n_ring, (const T *)m.Q0,
+                           (const T *)m.Q1, theta_next, scale5, star, C.flag);
+    };
+    if constexpr (sizeof(T) == 4) {
+        if (m.fv_variant == 2) go(k_fv<T, 8>);
+        else go(k_fv<T, 7>);
+    } else {
+        go(k_fv<T, 1>);
+    }
+}
+
+// Block-shape autotuner of the sub-step kernel (FP32): times each register
+// bound on this mesh (reps launches reading the current state buffer and
+// writing the other one, which the next sub-step overwrites, so the state is
+// unchanged) and returns the faster variant (1: bounded for 7 blocks per SM,
+// 2: for 8); *us receives the mean launch times.  Both variants execute the same
+// arithmetic.
+template <typename T, typename S> int fv_autotune(DevCtx &C, cudaStream_t s, double us[2])
+{
+    us[0] = us[1] = 0.0;
+    if constexpr (sizeof(T) != 4) {
+        return 1;
+    } else {
+        DevMesh &m = C.m;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            if (e0) cudaEventDestroy(e0);
+            return 1;
+        }
+        const int reps = 20;
+        const int keep = m.fv_variant;
+        for (int v = 1; v <= 2; v++) {
+            m.fv_variant = v;
+            for (int k = 0; k < 3; k++) launch_fv<T, S>(C, 0, s);
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < reps; k++) launch_fv<T, S>(C, 0, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            us[v - 1] = 1e3 * double(ms) / reps;
+        }
+        m.fv_variant = keep;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return us[1] < us[0] ? 2 : 1;
+    }
 }
 
 template <typename T, typename S> void configure_fv(size_t bytes)
 {
-    if (bytes > 48 * 1024) cudaFuncSetAttribute(k_fv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (bytes > 48 * 1024) {
+        if constexpr (sizeof(T) == 4) {
+            cudaFuncSetAttribute(k_fv<T, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+            cudaFuncSetAttribute(k_fv<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+        } else {
+            cudaFuncSetAttribute(k_fv<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+        }
+    }
 }
 
 template <typename T, typename S> void launch_forces(const DevCtx &C, cudaStream_t s)
@@ -1193,6 +1249,7 @@ void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *u
     template void launch_ring_interp<T, S>(const DevCtx &, bool, cudaStream_t);                                  \
     template void launch_hole_interp<T, S>(const DevCtx &, cudaStream_t);                                        \
     template void launch_fv<T, S>(const DevCtx &, int, cudaStream_t);                                            \
+    template int fv_autotune<T, S>(DevCtx &, cudaStream_t, double *);                                            \
     template void launch_forces<T, S>(const DevCtx &, cudaStream_t);                                             \
     template void launch_wall_stats<T, S>(const DevCtx &, cudaStream_t);                                         \
     template void launch_fields<T, S>(const DevCtx &, int, double *, double *, double *, double *, cudaStream_t);

@@ -262,6 +262,25 @@ def test_wall_stats_reassemble_the_mean_forces(H):
     assert abs(F[1] - cl.mean()) <= 1e-9 * abs(cd.mean())
 
 
+def test_fv_register_bounds_agree_bitwise_and_the_autotuner_reports(H):
+    """The two register bounds of the FP32 finite-volume kernel (7 and 8
+    resident blocks per SM) run the same arithmetic: identical results; the
+    default (autotuned) context reports its choice and both timings."""
+    case = make_case("hlbm_mini2", aoa_deg=3.0)
+    a = H.Solver(case, precision="fp32", fv_variant=1)
+    b = H.Solver(case, precision="fp32", fv_variant=2)
+    assert a.info("fv_variant") == 1 and b.info("fv_variant") == 2
+    a.step(9)
+    b.step(9)
+    for g in grids(case):
+        for x, y in zip(a.fields(g), b.fields(g)):
+            assert np.array_equal(x, y, equal_nan=True)
+    assert np.array_equal(a.forces()[0], b.forces()[0])
+    t = H.Solver(make_case("hlbm_single"), precision="fp32")
+    assert t.info("fv_variant") in (1, 2)
+    assert t.info("fv_tune_us1") > 0 and t.info("fv_tune_us2") > 0
+
+
 def test_graphs_and_plain_launches_agree_bitwise(H):
     case = make_case("hlbm_mini2")
     a = H.Solver(case, precision="fp64", use_graphs=True)

@@ -104,6 +104,9 @@ void set_phase(hlbm_ctx *c, long k)
     for (int l = 1; l < D.L; l++) D.lv[l].parity = 0;
     long per = long(D.n_sub) << (D.L - 1);
     D.m.gcur = int((k * per) & 1);
+    D.m.qpar = int((k << (D.L - 1)) & 1);  // finest steps done before coarse step k
+    D.m.Q0 = D.m.Qb[D.m.qpar];
+    D.m.Q1 = D.m.Qb[D.m.qpar ^ 1];
 }
 
 template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double theta, cudaStream_t s);
@@ -129,9 +132,10 @@ template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double t
     bool hybrid = (lvl == D.L - 1) && D.m.n > 0;
     bool child = lvl < D.L - 1;
     if (hybrid) {
-        launch_ring_interp<T, S>(D, false, s);  // Eq. 9 data at t
-        launch_hole_interp<T, S>(D, s);         // Eq. 4: post-collision of the hole boundary
-        c->launches += 1 + (D.m.n_is > 0);
+        // Eq. 9 data at t: already in Q0 (the previous step's data at t + 1,
+        // or the initial state's)
+        launch_hole_interp<T, S>(D, s);  // Eq. 4: post-collision of the hole boundary
+        c->launches += (D.m.n_is > 0);
     }
     launch_collide<T, S>(D, lvl, s);  // Eq. 1
     D.lv[lvl].parity ^= 1;
@@ -155,6 +159,8 @@ template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double t
             D.m.gcur ^= 1;
         }
         c->launches += 1 + D.n_sub;
+        D.m.qpar ^= 1;  // the data at t + 1 is the next step's data at t
+        std::swap(D.m.Q0, D.m.Q1);
     }
 }
 
@@ -326,8 +332,11 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     M.ent = upload(c, ent);
     M.slice_ptr = upload(c, sptr);
     M.slice_len = upload(c, slen);
-    M.Q0 = dalloc(c, size_t(12) * std::max(1, P.n_ring) * sizeof(T));
-    M.Q1 = dalloc(c, size_t(12) * std::max(1, P.n_ring) * sizeof(T));
+    M.Qb[0] = dalloc(c, size_t(12) * std::max(1, P.n_ring) * sizeof(T));
+    M.Qb[1] = dalloc(c, size_t(12) * std::max(1, P.n_ring) * sizeof(T));
+    M.qpar = 0;
+    M.Q0 = M.Qb[0];
+    M.Q1 = M.Qb[1];
     // Eq. 8 stencils
     M.n_is = int(P.is_node.size());
     std::vector<int> isn(M.n_is), isd(6 * size_t(M.n_is));

@@ -46,7 +46,12 @@ struct DevMesh {
     int *tile_own = nullptr;  // position of tile t's first own row in its halo list (own rows are a run)
     int fv_variant = 1;       // FP32 sub-step kernel bounded for 1: 7, 2: 8 blocks per SM
     size_t smem_bytes = 0;
-    void *Q0 = nullptr, *Q1 = nullptr;  // [12][n_ring] Eq. 9 data at t and t + 1
+    // [12][n_ring] Eq. 9 data at t and t + 1: two buffers whose roles swap
+    // every finest step (the data at t + 1 of one step is the data at t of the
+    // next: nothing writes the finest level's lattice in between)
+    void *Q0 = nullptr, *Q1 = nullptr;
+    void *Qb[2] = {nullptr, nullptr};
+    int qpar = 0;  // Q0 = Qb[qpar], Q1 = Qb[qpar ^ 1]
     int n_is = 0;
     int *is_n = nullptr;    // padded finest-level index of each structured interpolation node
     int *is_don = nullptr;  // [n_is][6] device-order mesh nodes

@@ -104,6 +104,13 @@ void set_phase(hlbm_ctx *c, long k)
     for (int l = 1; l < D.L; l++) D.lv[l].parity = 0;
     long per = long(D.n_sub) << (D.L - 1);
     D.m.gcur = int((k * per) & 1);
+    for (int l = 0; l < D.L; l++) {  // steps of level l done before coarse step k: k 2^l
+        DevLevel &dl = D.lv[l];
+        if (!dl.snap[0]) continue;
+        dl.spar = int((k << l) & 1);
+        dl.snapA = dl.snap[dl.spar];
+        dl.snapB = dl.snap[dl.spar ^ 1];
+    }
     D.m.qpar = int((k << (D.L - 1)) & 1);  // finest steps done before coarse step k
     D.m.Q0 = D.m.Qb[D.m.qpar];
     D.m.Q1 = D.m.Qb[D.m.qpar ^ 1];
@@ -168,7 +175,8 @@ template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double thet
 {
     DevCtx &D = c->dev;
     bool child = lvl < D.L - 1;
-    if (child) launch_snapshot<T, S>(D, lvl, false, s);
+    // the band at the start of the step (snapA) is the previous step's snapB
+    // (or the initial state's)
     level_step<T, S>(c, lvl, theta, s);
     if (child) {
         launch_snapshot<T, S>(D, lvl, true, s);
@@ -176,7 +184,10 @@ template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double thet
         advance<T, S>(c, lvl + 1, 0.5, s);
         advance<T, S>(c, lvl + 1, 1.0, s);
         launch_restrict<T, S>(D, lvl, s);
-        c->launches += 3;
+        c->launches += 2;
+        DevLevel &dl = D.lv[lvl];
+        dl.spar ^= 1;
+        std::swap(dl.snapA, dl.snapB);
     }
 }
 
@@ -418,8 +429,9 @@ template <typename T, typename S> void build_device(hlbm_ctx *c)
         if (lp.has_child) {
             dl.cox = lp.cox; dl.coy = lp.coy; dl.cmx = lp.cmx; dl.cmy = lp.cmy;
             dl.band_n = 2 * (lp.cmx + 2) + 2 * (lp.cmy + 2);
-            dl.snapA = dalloc(c, size_t(12) * dl.band_n * sizeof(T));
-            dl.snapB = dalloc(c, size_t(12) * dl.band_n * sizeof(T));
+            dl.snap[0] = dl.snapA = dalloc(c, size_t(12) * dl.band_n * sizeof(T));
+            dl.snap[1] = dl.snapB = dalloc(c, size_t(12) * dl.band_n * sizeof(T));
+            dl.spar = 0;
         }
         maxnodes = std::max(maxnodes, size_t(lp.nx) * lp.ny);
     }

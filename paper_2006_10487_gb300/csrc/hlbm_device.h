@@ -23,7 +23,13 @@ struct DevLevel {
     int *hx0 = nullptr, *hx1 = nullptr;  // finest level: hole interval per row
     bool has_child = false;
     int cox = 0, coy = 0, cmx = 0, cmy = 0, band_n = 0;
-    void *snapA = nullptr, *snapB = nullptr;  // [12][band_n] (rho, ux, uy, f^neq)
+    // [12][band_n] (rho, ux, uy, f^neq) of the band before (A) and after (B)
+    // this level's step: two buffers whose roles swap every step of the level
+    // (B of one step is A of the next: the restriction in between writes only
+    // the child's strict interior, never the band)
+    void *snapA = nullptr, *snapB = nullptr;
+    void *snap[2] = {nullptr, nullptr};
+    int spar = 0;  // snapA = snap[spar], snapB = snap[spar ^ 1]
 };
 
 // The triangular mesh in device order (wall nodes, fluid nodes, ring nodes).

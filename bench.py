@@ -117,13 +117,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _dist():
+def _dist(backend="nccl"):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        dist.init_process_group(backend)
         return dist, dist.get_rank(), ws
     return None, 0, 1
+
+
+def max_over_ranks(dist, value, device="cuda"):
+    """The largest of every rank's value (the timed region is the slowest
+    replica's); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(updates_per_step, steps, world_size, ms):
+    """Whole-job throughput: every replica's node updates over the slowest
+    replica's time (weak scaling: each rank runs its own full case)."""
+    return updates_per_step * steps * world_size / (ms * 1e-3) / 1e6
 
 
 def run_cpu_baseline(case, coarse_steps=1):
@@ -231,14 +248,11 @@ def main():
         s.step(args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(dist, e0.elapsed_time(e1))
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     cd, cl = s.forces()
-    value = per_step * args.steps * ws / (ms * 1e-3) / 1e6
+    value = aggregate_mlups(per_step, args.steps, ws, ms)
 
     # ---- roofline of the dominant kernel (finite-volume sub-step), measured
     # live with CUDA events on the library's stream

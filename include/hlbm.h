@@ -125,9 +125,11 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
 /* Advance n_coarse coarse (level-0) steps, asynchronously on the context's
  * stream.  One coarse step runs 2^l steps of level l and, per finest step,
  * n_sub finite-volume sub-steps; one force sample is recorded per coarse
- * step.  Every check_every coarse steps (option) it reads the health flag:
+ * step.  Every check_every coarse steps (option) it reads the health flag
+ * and the total mass of level 0 (FP64 reduction, outside the step graph):
  * HLBM_ETIMEOUT if a bounded device-side wait gave up, HLBM_EUNSTABLE if the
- * forces held a NaN. */
+ * forces held a NaN or the mass moved by more than 1e-2 of its value at
+ * create (the open boundaries let it change a little in a healthy run). */
 int hlbm_step(hlbm_ctx *ctx, int n_coarse);
 
 /* Copy the force samples recorded since the previous call (oldest first, at
@@ -156,7 +158,10 @@ int hlbm_populations(hlbm_ctx *ctx, int grid, double *out, size_t cap);
  * of one lattice step of level l), "fv_tiles" (blocks of one finite-volume
  * sub-step), "fv_smem" (their dynamic shared memory, bytes), "fv_variant"
  * (the register bound in use, see options), "fv_tune_us1" / "fv_tune_us2"
- * (the autotuner's launch times of the two bounds, 0 if it did not run). */
+ * (the autotuner's launch times of the two bounds, 0 if it did not run),
+ * "mass" (total mass of level 0 now, sum of rho over its computed nodes,
+ * FP64), "mass_drift" (its relative change since create); these two
+ * synchronise the stream. */
 int hlbm_info(const hlbm_ctx *ctx, const char *key, double *value);
 
 /* Measurement hook: runs one kernel of the step `reps` times back to back on

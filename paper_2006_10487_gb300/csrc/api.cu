@@ -25,6 +25,9 @@ struct hlbm_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool side_ok[hlbm::kMaxLevels] = {};
     int fv_variant_opt = 0;
+    // mass monitoring (level 0, FP64): reference mass at create, last drift
+    double *mass_buf = nullptr;  // [ny0 + 1]: row sums, total
+    double mass0 = 0.0, mass_drift = 0.0, mass_nodes = 0.0;
     double fv_tune_us[2] = {0.0, 0.0};
     void *(*alloc_fn)(size_t, void *) = nullptr;
     void (*free_fn)(void *, void *) = nullptr;
@@ -59,6 +62,9 @@ struct hlbm_batch {
 };
 
 namespace {
+
+// relative change of the total mass that the health check treats as unstable
+constexpr double kMassDriftLimit = 1e-2;
 
 thread_local std::string g_create_err;
 
@@ -211,6 +217,21 @@ void enqueue_coarse_step(hlbm_ctx *c, cudaStream_t s)
     if (c->plan.precision == HLBM_FP32) coarse_step<float, float>(c, s);
     else if (c->plan.precision == HLBM_FP16S) coarse_step<float, __half>(c, s);
     else coarse_step<double, double>(c, s);
+}
+
+// Total mass of level 0 now (FP64; synchronises the context's stream).
+double level0_mass(hlbm_ctx *c)
+{
+    const int ny = c->dev.lv[0].ny;
+    if (c->plan.precision == HLBM_FP32) launch_mass<float, float>(c->dev, c->mass_buf, c->mass_buf + ny, c->stream);
+    else if (c->plan.precision == HLBM_FP16S)
+        launch_mass<float, __half>(c->dev, c->mass_buf, c->mass_buf + ny, c->stream);
+    else launch_mass<double, double>(c->dev, c->mass_buf, c->mass_buf + ny, c->stream);
+    ck(cudaGetLastError(), "mass kernel");
+    double dev = 0.0;
+    ck(cudaMemcpyAsync(&dev, c->mass_buf + ny, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "D2H");
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    return c->mass_nodes + dev;
 }
 
 template <typename T, typename S> void init_state(hlbm_ctx *c)
@@ -444,6 +465,13 @@ template <typename T, typename S> void build_device(hlbm_ctx *c)
     ck(cudaMemsetAsync(D.force_counter, 0, 2 * sizeof(int), c->stream), "memset");
     c->d_out_n = maxnodes;
     c->d_out = (double *)dalloc(c, maxnodes * 12 * sizeof(double));
+    c->mass_buf = (double *)dalloc(c, (size_t(D.lv[0].ny) + 1) * sizeof(double));
+    {
+        const LevelPlan &l0 = P.lv[0];
+        double nodes = double(l0.nx) * l0.ny;
+        for (size_t y = 0; y < l0.hx0.size(); y++) nodes -= double(l0.hx1[y] - l0.hx0[y]);
+        c->mass_nodes = nodes;
+    }
     init_state<T, S>(c);
     if (P.n > 0) {
         if (c->plan.precision == HLBM_FP64) D.m.fv_variant = 1;
@@ -565,6 +593,7 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
         if (c->plan.precision == HLBM_FP32) build_device<float, float>(c);
         else if (c->plan.precision == HLBM_FP16S) build_device<float, __half>(c);
         else build_device<double, double>(c);
+        c->mass0 = level0_mass(c);
         if (c->use_graphs) capture_graphs(c);
         ck(cudaStreamSynchronize(c->stream), "sync after create");
     } catch (const CudaError &e) {
@@ -604,6 +633,11 @@ int hlbm_step(hlbm_ctx *c, int n_coarse)
                 ck(cudaStreamSynchronize(c->stream), "sync");
                 if (flag & 2) return fail(c, HLBM_ETIMEOUT, "a device-side wait gave up (operator copy did not arrive)");
                 if (flag) return fail(c, HLBM_EUNSTABLE, "NaN in the force reduction: the simulation is unstable");
+                const double m = level0_mass(c);
+                c->mass_drift = std::fabs(m - c->mass0) / c->mass0;
+                if (!(c->mass_drift <= kMassDriftLimit))
+                    return fail(c, HLBM_EUNSTABLE, "total mass drifted by " + std::to_string(c->mass_drift) +
+                                                       " of the initial mass: the simulation is unstable");
             }
         }
     } catch (const CudaError &e) {
@@ -711,6 +745,15 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
     } else if (k == "fv_updates") *value = double(P.n) * P.n_sub * double(1L << (P.L - 1));
     else if (k == "launches_per_step") *value = double(c->launches_per_step);
     else if (k == "fv_tiles") *value = double(c->dev.m.n_tiles);
+    else if (k == "mass" || k == "mass_drift") {
+        if (c->timing_dirty) return HLBM_ESTATE;
+        try {
+            const double m = level0_mass(const_cast<hlbm_ctx *>(c));
+            *value = k == "mass" ? m : std::fabs(m - c->mass0) / c->mass0;
+        } catch (const CudaError &) {
+            return HLBM_ECUDA;
+        }
+    }
     else if (k == "fv_variant") *value = double(c->dev.m.fv_variant);
     else if (k == "fv_tune_us1") *value = c->fv_tune_us[0];
     else if (k == "fv_tune_us2") *value = c->fv_tune_us[1];
@@ -1018,6 +1061,12 @@ int hlbm_batch_step(hlbm_batch *b, int n_coarse)
                 }
                 if (flag) {
                     b->err = "case " + std::to_string(i) + ": NaN in the force reduction (unstable)";
+                    return HLBM_EUNSTABLE;
+                }
+                hlbm_ctx *c = b->ctx[i];
+                c->mass_drift = std::fabs(level0_mass(c) - c->mass0) / c->mass0;
+                if (!(c->mass_drift <= kMassDriftLimit)) {
+                    b->err = "case " + std::to_string(i) + ": total mass drifted by " + std::to_string(c->mass_drift);
                     return HLBM_EUNSTABLE;
                 }
             }

@@ -110,6 +110,8 @@ template <typename T, typename S> void launch_ring_interp(const DevCtx &, bool q
 template <typename T, typename S> void launch_hole_interp(const DevCtx &, cudaStream_t);
 template <typename T, typename S> void launch_fv(const DevCtx &, int m, cudaStream_t);
 template <typename T, typename S> void launch_forces(const DevCtx &, cudaStream_t);
+// FP64 total of sum_i (f_i - w_i) over level 0's computed nodes into out[0] (row_sum: ny0 doubles)
+template <typename T, typename S> void launch_mass(const DevCtx &, double *row_sum, double *out, cudaStream_t);
 // adds this state's wall coefficients to the sums (Eq. 12-13)
 template <typename T, typename S> void launch_wall_stats(const DevCtx &, cudaStream_t);
 template <typename T, typename S> void launch_fields(const DevCtx &, int grid, double *rho, double *ux, double *uy, double *pop, cudaStream_t);

@@ -986,6 +986,52 @@ __global__ void k_fields_level(const S *f, int nx, int ny, int pitch, size_t str
         for (int i = 0; i < 9; i++) pop[9 * o + i] = double(d[i]) + wq<double>(i);
 }
 
+// Total mass of level 0 (it spans the whole domain; refined levels restrict
+// into it), FP64 in every precision, deterministic: one block per row sums
+// sum_i (f_i - w_i) over the row's computed nodes in a fixed order, then one
+// block adds the rows in order.  The host adds the node count.
+constexpr int kMassThreads = 256;
+
+template <typename T, typename S, int P>
+__global__ void __launch_bounds__(kMassThreads) k_mass_rows(const S *f, int nx, int pitch, size_t stride,
+                                                            const int *hx0, const int *hx1, double *row_sum,
+                                                            LatShift sh)
+{
+    const int y = blockIdx.x;
+    double acc = 0.0;
+    for (int x = threadIdx.x; x < nx; x += kMassThreads) {
+        if (hx0 && x >= hx0[y] && x < hx1[y]) continue;
+        T d[9];
+        load_state<T, S, P>(f, node(x, y, pitch), pitch, stride, d, sh);
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < 9; i++) s += double(d[i]);
+        acc += s;
+    }
+    __shared__ double red[kMassThreads];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kMassThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) row_sum[y] = red[0];
+}
+
+__global__ void __launch_bounds__(kMassThreads) k_mass_total(const double *row_sum, int ny, double *out)
+{
+    __shared__ double red[kMassThreads];
+    double acc = 0.0;
+    for (int y = threadIdx.x; y < ny; y += kMassThreads) acc += row_sum[y];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kMassThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
 template <typename T>
 __global__ void k_fields_mesh(const T *g, int Np, const int *inv, int n, double *rho, double *ux, double *uy,
                               double *pop)
@@ -1220,6 +1266,18 @@ template <typename T, typename S> void launch_wall_stats(const DevCtx &C, cudaSt
                                                         1.0 / (0.5 * C.u0 * C.u0));
 }
 
+template <typename T, typename S> void launch_mass(const DevCtx &C, double *row_sum, double *out, cudaStream_t s)
+{
+    const DevLevel &l = C.lv[0];
+    if (l.parity == 0)
+        k_mass_rows<T, S, 0><<<l.ny, kMassThreads, 0, s>>>((const S *)l.f, l.nx, l.pitch, l.stride, l.hx0, l.hx1,
+                                                           row_sum, C.shift);
+    else
+        k_mass_rows<T, S, 1><<<l.ny, kMassThreads, 0, s>>>((const S *)l.f, l.nx, l.pitch, l.stride, l.hx0, l.hx1,
+                                                           row_sum, C.shift);
+    k_mass_total<<<1, kMassThreads, 0, s>>>(row_sum, l.ny, out);
+}
+
 template <typename T, typename S>
 void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *uy, double *pop, cudaStream_t s)
 {
@@ -1251,6 +1309,7 @@ void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *u
     template void launch_fv<T, S>(const DevCtx &, int, cudaStream_t);                                            \
     template int fv_autotune<T, S>(DevCtx &, cudaStream_t, double *);                                            \
     template void launch_forces<T, S>(const DevCtx &, cudaStream_t);                                             \
+    template void launch_mass<T, S>(const DevCtx &, double *, double *, cudaStream_t);                           \
     template void launch_wall_stats<T, S>(const DevCtx &, cudaStream_t);                                         \
     template void launch_fields<T, S>(const DevCtx &, int, double *, double *, double *, double *, cudaStream_t);
 HLBM_INSTANTIATE(float, float)

@@ -281,6 +281,25 @@ def test_fv_register_bounds_agree_bitwise_and_the_autotuner_reports(H):
     assert t.info("fv_tune_us1") > 0 and t.info("fv_tune_us2") > 0
 
 
+@pytest.mark.parametrize("name", ["hlbm_small", "hlbm_mini2"])
+def test_level0_mass_matches_oracle(H, orc, name):
+    """The FP64 mass monitor: sum of rho over level 0's computed nodes against
+    the oracle's level-0 density field; a healthy run drifts little."""
+    case = make_case(name)
+    sol = H.Solver(case, precision="fp64")
+    sim = orc.Oracle(case)
+    m0 = sol.info("mass")
+    r0, _, _ = sim.fields(0)
+    assert abs(m0 - np.nansum(r0)) <= 1e-12 * m0
+    sol.step(20)
+    sim.step(20)
+    r, _, _ = sim.fields(0)
+    m = sol.info("mass")
+    assert abs(m - np.nansum(r)) <= 1e-12 * m
+    assert 0 < sol.info("mass_drift") < 1e-3
+    assert sol.info("mass_drift") == pytest.approx(abs(m - m0) / m0, rel=1e-9)
+
+
 def test_graphs_and_plain_launches_agree_bitwise(H):
     case = make_case("hlbm_mini2")
     a = H.Solver(case, precision="fp64", use_graphs=True)

@@ -254,6 +254,20 @@ const char *hlbm_batch_last_error(const hlbm_batch *b);
 /* Releases the batch (not its contexts). */
 int hlbm_batch_destroy(hlbm_batch *b);
 
+/* Checkpoint / resume.  hlbm_save writes every array that carries state from
+ * one coarse step to the next (all lattice levels, the current mesh state,
+ * the interface data at t and the band snapshots, the force samples and
+ * counters, the wall-statistics sums) and the step counters to `path` (a
+ * magic string, a JSON header with the configuration and the buffer sizes,
+ * then the raw little-endian buffers).  hlbm_load reads such a file into a
+ * context created from the same inputs (levels, mesh size, precision,
+ * sub-steps, force_cap, wall_stats; otherwise HLBM_EINVAL, context unchanged)
+ * and stepping it on is bitwise identical to the run that was saved.  Both
+ * synchronise the stream; errors: HLBM_EINVAL (path, format, mismatch),
+ * HLBM_ESTATE (save after hlbm_time_kernel), HLBM_ECUDA. */
+int hlbm_save(hlbm_ctx *ctx, const char *path);
+int hlbm_load(hlbm_ctx *ctx, const char *path);
+
 /* Wait for all work of the context. */
 int hlbm_sync(hlbm_ctx *ctx);
 

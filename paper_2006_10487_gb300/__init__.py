@@ -80,6 +80,8 @@ def lib():
         L.hlbm_last_error.restype = C.c_char_p
         L.hlbm_wall_stats.argtypes = [C.c_void_p, dp, C.c_size_t, ip, C.POINTER(C.c_long)]
         L.hlbm_wall_stats_reset.argtypes = [C.c_void_p]
+        L.hlbm_save.argtypes = [C.c_void_p, C.c_char_p]
+        L.hlbm_load.argtypes = [C.c_void_p, C.c_char_p]
         L.hlbm_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
         L.hlbm_batch_step.argtypes = [C.c_void_p, C.c_int]
         L.hlbm_batch_sync.argtypes = [C.c_void_p]
@@ -188,6 +190,14 @@ class Solver:
         _check(self._lib.hlbm_wall_stats(self.ctx, out.ctypes.data_as(C.POINTER(C.c_double)), out.size,
                                          C.byref(nw), C.byref(ns)), self.ctx)
         return out, ns.value
+
+    def save(self, path):
+        """Checkpoint of the whole evolving state (hlbm_save)."""
+        _check(self._lib.hlbm_save(self.ctx, os.fsencode(path)), self.ctx)
+
+    def load(self, path):
+        """Resume from a checkpoint of a Solver made from the same inputs (hlbm_load)."""
+        _check(self._lib.hlbm_load(self.ctx, os.fsencode(path)), self.ctx)
 
     def wall_stats_reset(self):
         _check(self._lib.hlbm_wall_stats_reset(self.ctx), self.ctx)

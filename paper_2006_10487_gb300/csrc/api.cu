@@ -955,6 +955,154 @@ int hlbm_wall_stats_reset(hlbm_ctx *c)
     return HLBM_OK;
 }
 
+// ------------------------------------------------------------- checkpoint ----
+// File: "HLBMCKPT", uint32 header length, JSON header, then the device buffers
+// as raw bytes in the order of ckpt_buffers (sizes in the header).
+namespace {
+
+struct Blob {
+    void *ptr;
+    size_t bytes;
+};
+
+std::vector<Blob> ckpt_buffers(hlbm_ctx *c)
+{
+    const DevCtx &D = c->dev;
+    const int p = c->plan.precision;
+    const size_t sz = p == HLBM_FP64 ? 8 : (p == HLBM_FP32 ? 4 : 2);  // lattice storage
+    const size_t tz = p == HLBM_FP64 ? 8 : 4;                         // mesh and interface data
+    std::vector<Blob> v;
+    for (int l = 0; l < D.L; l++) {
+        const DevLevel &dl = D.lv[l];
+        v.push_back({dl.f, 9 * dl.stride * sz});
+        if (dl.snap[0]) {
+            v.push_back({dl.snap[0], 12 * size_t(dl.band_n) * tz});
+            v.push_back({dl.snap[1], 12 * size_t(dl.band_n) * tz});
+        }
+    }
+    const DevMesh &m = D.m;
+    if (m.n > 0) {
+        v.push_back({m.g[m.gcur], 9 * size_t(m.Np) * tz});
+        const size_t qn = 12 * size_t(std::max(1, m.n_ring)) * tz;
+        v.push_back({m.Qb[0], qn});
+        v.push_back({m.Qb[1], qn});
+        if (m.wall_stats && m.wall_acc) v.push_back({m.wall_acc, 3 * size_t(c->plan.n_wall) * sizeof(double)});
+    }
+    if (D.force_buf) {
+        v.push_back({D.force_buf, 2 * size_t(D.force_cap) * sizeof(double)});
+        v.push_back({D.force_counter, 2 * sizeof(int)});
+    }
+    return v;
+}
+
+std::string ckpt_header(hlbm_ctx *c, const std::vector<Blob> &v)
+{
+    const Plan &P = c->plan;
+    std::string h = "{\"version\": 1, \"precision\": " + std::to_string(P.precision) + ", \"levels\": [";
+    for (int l = 0; l < P.L; l++)
+        h += std::string(l ? ", " : "") + "[" + std::to_string(P.lv[l].nx) + ", " + std::to_string(P.lv[l].ny) + ", " +
+             std::to_string(P.lv[l].ox) + ", " + std::to_string(P.lv[l].oy) + "]";
+    h += "], \"mesh_nodes\": " + std::to_string(P.n) + ", \"n_sub\": " + std::to_string(P.n_sub) +
+         ", \"force_cap\": " + std::to_string(c->dev.force_cap) + ", \"wall_stats\": " +
+         std::to_string(c->dev.m.wall_stats) + ", \"buffers\": [";
+    for (size_t k = 0; k < v.size(); k++) h += std::string(k ? ", " : "") + std::to_string(v[k].bytes);
+    h += "]}";
+    return h;
+}
+
+// the part of the header that must match the loading context (everything
+// before the mutable counters)
+std::string ckpt_counters(hlbm_ctx *c)
+{
+    char buf[256];
+    std::snprintf(buf, sizeof buf, "%ld %ld %ld %.17g", c->steps, c->forces_read, c->stats_base, c->mass0);
+    return buf;
+}
+
+}  // namespace
+
+int hlbm_save(hlbm_ctx *c, const char *path)
+{
+    if (!c || !path) return c ? fail(c, HLBM_EINVAL, "path is NULL") : HLBM_EINVAL;
+    if (c->timing_dirty) return fail(c, HLBM_ESTATE, "the state was consumed by hlbm_time_kernel");
+    std::vector<Blob> v = ckpt_buffers(c);
+    std::string head = ckpt_header(c, v), cnt = ckpt_counters(c);
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return fail(c, HLBM_EINVAL, std::string("cannot open ") + path + " for writing");
+    bool ok = true;
+    try {
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        const uint32_t hl = uint32_t(head.size()), cl = uint32_t(cnt.size());
+        ok = std::fwrite("HLBMCKPT", 1, 8, fp) == 8 && std::fwrite(&hl, 4, 1, fp) == 1 &&
+             std::fwrite(head.data(), 1, hl, fp) == hl && std::fwrite(&cl, 4, 1, fp) == 1 &&
+             std::fwrite(cnt.data(), 1, cl, fp) == cl;
+        std::vector<char> host;
+        for (const Blob &b : v) {
+            if (!ok) break;
+            host.resize(b.bytes);
+            ck(cudaMemcpy(host.data(), b.ptr, b.bytes, cudaMemcpyDeviceToHost), "D2H");
+            ok = std::fwrite(host.data(), 1, b.bytes, fp) == b.bytes;
+        }
+    } catch (const CudaError &e) {
+        std::fclose(fp);
+        return fail(c, HLBM_ECUDA, e.msg);
+    }
+    if (std::fclose(fp) != 0) ok = false;
+    return ok ? HLBM_OK : fail(c, HLBM_EINVAL, std::string("writing ") + path + " failed");
+}
+
+int hlbm_load(hlbm_ctx *c, const char *path)
+{
+    if (!c || !path) return c ? fail(c, HLBM_EINVAL, "path is NULL") : HLBM_EINVAL;
+    std::vector<Blob> v = ckpt_buffers(c);
+    const std::string want = ckpt_header(c, v);
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return fail(c, HLBM_EINVAL, std::string("cannot open ") + path);
+    auto bad = [&](const std::string &msg) {
+        std::fclose(fp);
+        return fail(c, HLBM_EINVAL, msg);
+    };
+    char magic[8];
+    uint32_t hl = 0, cl = 0;
+    if (std::fread(magic, 1, 8, fp) != 8 || std::memcmp(magic, "HLBMCKPT", 8) != 0) return bad("not a checkpoint");
+    if (std::fread(&hl, 4, 1, fp) != 1 || hl > (1u << 20)) return bad("bad checkpoint header");
+    std::string head(hl, '\0');
+    if (std::fread(&head[0], 1, hl, fp) != hl) return bad("truncated checkpoint header");
+    if (head != want) return bad("checkpoint of another configuration: " + head);
+    if (std::fread(&cl, 4, 1, fp) != 1 || cl > 255) return bad("bad checkpoint counters");
+    std::string cnt(cl, '\0');
+    if (std::fread(&cnt[0], 1, cl, fp) != cl) return bad("truncated checkpoint counters");
+    long steps = 0, forces_read = 0, stats_base = 0;
+    double mass0 = 0.0;
+    if (std::sscanf(cnt.c_str(), "%ld %ld %ld %lg", &steps, &forces_read, &stats_base, &mass0) != 4 || steps < 0)
+        return bad("bad checkpoint counters");
+    // the current mesh buffer depends on the step count: point the blob list at it
+    set_phase(c, steps);
+    v = ckpt_buffers(c);
+    std::vector<char> host;
+    try {
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        for (const Blob &b : v) {
+            host.resize(b.bytes);
+            if (std::fread(host.data(), 1, b.bytes, fp) != b.bytes) {
+                set_phase(c, c->steps);
+                return bad("truncated checkpoint data");
+            }
+            ck(cudaMemcpy(b.ptr, host.data(), b.bytes, cudaMemcpyHostToDevice), "H2D");
+        }
+    } catch (const CudaError &e) {
+        std::fclose(fp);
+        return fail(c, HLBM_ECUDA, e.msg);
+    }
+    std::fclose(fp);
+    c->steps = steps;
+    c->forces_read = forces_read;
+    c->stats_base = stats_base;
+    c->mass0 = mass0;
+    c->timing_dirty = false;
+    return HLBM_OK;
+}
+
 static void batch_release(hlbm_batch *b)
 {
     if (b->stream) cudaStreamSynchronize(b->stream);

@@ -300,6 +300,34 @@ def test_level0_mass_matches_oracle(H, orc, name):
     assert sol.info("mass_drift") == pytest.approx(abs(m - m0) / m0, rel=1e-9)
 
 
+def test_checkpoint_resume_is_bitwise(H, tmp_path):
+    """hlbm_save after 7 coarse steps, hlbm_load into a new context made from
+    the same inputs, 5 more steps each: the same fields on every grid, force
+    series and wall statistics, bit for bit; another precision is refused."""
+    for name, prec in (("hlbm_mini2", "fp32"), ("hlbm_small", "fp16s"), ("hlbm_mini2", "fp64")):
+        case = make_case(name, aoa_deg=4.0)
+        a = H.Solver(case, precision=prec, wall_stats=True)
+        a.step(7)
+        path = str(tmp_path / f"{name}_{prec}.ckpt")
+        a.save(path)
+        b = H.Solver(case, precision=prec, wall_stats=True)
+        b.load(path)
+        a.step(5)
+        b.step(5)
+        for g in grids(case):
+            for x, y in zip(a.fields(g), b.fields(g)):
+                assert np.array_equal(x, y, equal_nan=True), (name, prec, g)
+        fa, fb = a.forces(), b.forces()
+        assert len(fa[0]) == len(fb[0]) == 12
+        assert np.array_equal(fa[0], fb[0]) and np.array_equal(fa[1], fb[1])
+        wa, wb = a.wall_stats(), b.wall_stats()
+        assert wa[1] == wb[1] == 12 and np.array_equal(wa[0], wb[0])
+    other = H.Solver(make_case("hlbm_mini2", aoa_deg=4.0), precision="fp32", wall_stats=True)
+    with pytest.raises(H.HlbmError) as e:
+        other.load(str(tmp_path / "hlbm_mini2_fp64.ckpt"))
+    assert e.value.code == H.HLBM_EINVAL
+
+
 def test_graphs_and_plain_launches_agree_bitwise(H):
     case = make_case("hlbm_mini2")
     a = H.Solver(case, precision="fp64", use_graphs=True)

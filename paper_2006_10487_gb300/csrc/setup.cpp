@@ -76,6 +76,10 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     if (!lv || n_levels < 1 || n_levels > kMaxLevels) { err = "n_levels must be in 1..8"; return HLBM_EINVAL; }
     if (!m) { err = "mesh pointer is NULL"; return HLBM_EINVAL; }
     if (!(Re > 0.0) || !(Ma > 0.0)) { err = "Re and Ma must be positive"; return HLBM_EINVAL; }
+    if (!std::isfinite(Re) || !std::isfinite(aoa_deg) || !(Ma < 1.0)) {
+        err = "Re and the angle of attack must be finite and Ma below 1";
+        return HLBM_EINVAL;
+    }
     hlbm_options o{};
     if (opt) o = *opt;
     if (o.precision != HLBM_FP64 && o.precision != HLBM_FP32 && o.precision != HLBM_FP16S) {
@@ -124,6 +128,14 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     P.ntri = m->n_tri;
     if (P.n == 0) { P.n_sub = 0; return HLBM_OK; }
     if (!m->xy || !m->tri || !m->kind || P.ntri < 1) { err = "mesh arrays missing"; return HLBM_EINVAL; }
+    for (int k = 0; k < 2 * P.n; k++)
+        if (!std::isfinite(m->xy[k])) { err = "mesh coordinates must be finite"; return HLBM_EINVAL; }
+    if (!std::isfinite(m->pivot[0]) || !std::isfinite(m->pivot[1]) || !std::isfinite(m->chord)) {
+        err = "pivot and chord must be finite";
+        return HLBM_EINVAL;
+    }
+    for (int k = 0; k < 4; k++)
+        if (!std::isfinite(m->hole[k])) { err = "hole ellipse must be finite"; return HLBM_EINVAL; }
 
     // ---- rigid rotation by -alpha about the pivot (alpha > 0: nose up)
     const double al = aoa_deg * M_PI / 180.0, ca = std::cos(al), sa = std::sin(al);

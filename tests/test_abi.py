@@ -80,6 +80,29 @@ def test_rejects_bad_inputs(built):
         H.hlbm_inspect(case, "nope")
 
 
+def test_rejects_corrupt_and_non_finite_inputs(built):
+    """Host-side fault injection: corrupted mesh arrays and non-finite or
+    out-of-range parameters are refused by the set-up (no GPU involved)."""
+    c = make_case("hlbm_small")
+    c.xy = c.xy.copy()
+    c.xy[17, 1] = np.nan
+    with pytest.raises(H.HlbmError, match="finite"):
+        H.hlbm_inspect(c, "n_sub")
+    c = make_case("hlbm_small")
+    c.tri = c.tri.copy()
+    c.tri[5, 2] = c.n_nodes + 3
+    with pytest.raises(H.HlbmError, match="out of range"):
+        H.hlbm_inspect(c, "n_sub")
+    c = make_case("hlbm_small")
+    c.hole = (70.0, np.inf, 30.0, 20.0)
+    with pytest.raises(H.HlbmError, match="finite"):
+        H.hlbm_inspect(c, "n_sub")
+    for kw in ({"Re": np.inf}, {"Ma": 1.5}, {"Ma": np.nan}, {"aoa_deg": np.nan}):
+        with pytest.raises(H.HlbmError):
+            H.hlbm_inspect(make_case("hlbm_small", **kw), "n_sub")
+    assert H.hlbm_inspect(make_case("hlbm_small"), "n_sub")[0] > 0  # the unmodified case passes
+
+
 def test_explicit_sub_steps_are_kept(built):
     case = make_case("hlbm_mini2")
     assert H.hlbm_inspect(case, "n_sub", n_sub=37)[0] == 37

@@ -97,6 +97,18 @@ def test_rejects_corrupt_and_non_finite_inputs(built):
     c.hole = (70.0, np.inf, 30.0, 20.0)
     with pytest.raises(H.HlbmError, match="finite"):
         H.hlbm_inspect(c, "n_sub")
+    c = make_case("hlbm_small")
+    c.tri = c.tri.copy()
+    c.tri[9, [1, 2]] = c.tri[9, [2, 1]]  # one triangle turned clockwise
+    with pytest.raises(H.HlbmError, match="manifold|inverted"):
+        H.hlbm_inspect(c, "n_sub")
+    c = make_case("hlbm_small")
+    c.kind = c.kind.copy()
+    c.kind[3] = 7
+    with pytest.raises(H.HlbmError, match="kind"):
+        H.hlbm_inspect(c, "n_sub")
+    with pytest.raises(H.HlbmError, match="precision"):
+        H.hlbm_inspect(make_case("hlbm_small"), "n_sub", precision=5)
     for kw in ({"Re": np.inf}, {"Ma": 1.5}, {"Ma": np.nan}, {"aoa_deg": np.nan}):
         with pytest.raises(H.HlbmError):
             H.hlbm_inspect(make_case("hlbm_small", **kw), "n_sub")

@@ -161,7 +161,12 @@ int hlbm_populations(hlbm_ctx *ctx, int grid, double *out, size_t cap);
  * (the autotuner's launch times of the two bounds, 0 if it did not run),
  * "mass" (total mass of level 0 now, sum of rho over its computed nodes,
  * FP64), "mass_drift" (its relative change since create); these two
- * synchronise the stream. */
+ * synchronise the stream.  "bounds_violations", "bounds_sites": in a library
+ * built with index bounds checks (HLBM_DEBUG), the number of out-of-range
+ * indices the kernels met so far in this process and the bit mask of where
+ * (1 lattice level, 2 mesh state, 4 a tile's staged nodes, 8 operator
+ * entries, 16 a band snapshot); the access went to index 0 instead.  -1 in a
+ * build without checks; these two synchronise the device. */
 int hlbm_info(const hlbm_ctx *ctx, const char *key, double *value);
 
 /* Measurement hook: runs one kernel of the step `reps` times back to back on

@@ -14,7 +14,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhlbm.so")
+# HLBM_DEBUG=1 selects the build with the kernels' index bounds checks
+LIB_PATH = os.path.join(_HERE, "libhlbm_debug.so" if os.environ.get("HLBM_DEBUG") == "1" else "libhlbm.so")
 
 HLBM_OK, HLBM_EINVAL, HLBM_ENOMEM, HLBM_ECUDA = 0, -1, -2, -3
 HLBM_EUNSTABLE, HLBM_ETIMEOUT, HLBM_ESTATE, HLBM_ENOTIMPL = -4, -5, -6, -7
@@ -58,7 +59,8 @@ def lib():
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise ImportError(f"{LIB_PATH} is missing: build it with "
-                              "`python -m paper_2006_10487_gb300.build` (there is no CPU fallback)")
+                              "`python -m paper_2006_10487_gb300.build` (--debug for the bounds-checked "
+                              "library; there is no CPU fallback)")
         L = C.CDLL(LIB_PATH)
         dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
         L.hlbm_create.argtypes = [C.POINTER(hlbm_level), C.c_int, C.POINTER(hlbm_mesh), C.c_double, C.c_double,

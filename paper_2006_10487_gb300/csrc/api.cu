@@ -1,6 +1,7 @@
 // C ABI of the HLBM library: context, device upload, the per-coarse-step
 // launch schedule (level recursion, sub-cycling, CUDA graphs) and readback.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -13,6 +14,18 @@
 #include "hlbm_internal.h"
 
 using namespace hlbm;
+
+namespace {
+// NVTX range for the profilers' timelines (a no-op unless a tool is attached).
+// With CUDA graphs the per-family ranges mark the capture at create; with
+// plain launches (options.use_graphs = 0) they bracket every launch of a step.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+}  // namespace
 
 struct hlbm_ctx {
     Plan plan;
@@ -124,6 +137,10 @@ void set_phase(hlbm_ctx *c, long k)
 
 template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double theta, cudaStream_t s);
 
+const char *const kLatticeRange[kMaxLevels] = {"lattice: level 0", "lattice: level 1", "lattice: level 2",
+                                               "lattice: level 3", "lattice: level 4", "lattice: level 5",
+                                               "lattice: level 6", "lattice: level 7"};
+
 // One step of level lvl on its own clock; theta: parent-time fraction at the
 // end of the step (refills the boundary ring by prolongation).
 // Branch of the step graph: work enqueued on c->side between fork and join
@@ -147,10 +164,14 @@ template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double t
     if (hybrid) {
         // Eq. 9 data at t: already in Q0 (the previous step's data at t + 1,
         // or the initial state's)
+        Range r("overlap: hole interpolation");
         launch_hole_interp<T, S>(D, s);  // Eq. 4: post-collision of the hole boundary
         c->launches += (D.m.n_is > 0);
     }
-    launch_collide<T, S>(D, lvl, s);  // Eq. 1
+    {
+        Range r(kLatticeRange[lvl]);
+        launch_collide<T, S>(D, lvl, s);  // Eq. 1
+    }
     D.lv[lvl].parity ^= 1;
     // The level's boundary ring (outer conditions / prolongation) is written
     // beside what reads the level's interior next: the child's band snapshot
@@ -161,12 +182,19 @@ template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double t
         fork(c, s);
         sb = c->side;
     }
-    if (lvl == 0) launch_outer_bc<T, S>(D, sb);
-    else launch_prolong<T, S>(D, lvl, theta, sb);
+    {
+        Range r(lvl == 0 ? "lattice: outer conditions" : "refine: prolongation");
+        if (lvl == 0) launch_outer_bc<T, S>(D, sb);
+        else launch_prolong<T, S>(D, lvl, theta, sb);
+    }
     c->launches += 2;
     if (hybrid) {
-        launch_ring_interp<T, S>(D, true, s);  // Eq. 9 data at t + 1, ring state of sub-step 0
+        {
+            Range r("overlap: ring interpolation");
+            launch_ring_interp<T, S>(D, true, s);  // Eq. 9 data at t + 1, ring state of sub-step 0
+        }
         if (branch) join(c, s);
+        Range r("fv: sub-steps");
         for (int m = 0; m < D.n_sub; m++) {  // Eq. 3, Eq. 5-7, wall rule
             launch_fv<T, S>(D, m, s);
             D.m.gcur ^= 1;
@@ -185,10 +213,14 @@ template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double thet
     // (or the initial state's)
     level_step<T, S>(c, lvl, theta, s);
     if (child) {
-        launch_snapshot<T, S>(D, lvl, true, s);
+        {
+            Range r("refine: band snapshot");
+            launch_snapshot<T, S>(D, lvl, true, s);
+        }
         if (c->side_ok[lvl]) join(c, s);
         advance<T, S>(c, lvl + 1, 0.5, s);
         advance<T, S>(c, lvl + 1, 1.0, s);
+        Range r("refine: restriction");
         launch_restrict<T, S>(D, lvl, s);
         c->launches += 2;
         DevLevel &dl = D.lv[lvl];
@@ -200,8 +232,10 @@ template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double thet
 template <typename T, typename S> void coarse_step(hlbm_ctx *c, cudaStream_t s)
 {
     long before = c->launches;
+    Range step("coarse step");
     advance<T, S>(c, 0, 0.0, s);
     if (c->dev.m.n > 0) {
+        Range r("forces");
         launch_forces<T, S>(c->dev, s);
         c->launches += 2;
         if (c->dev.m.wall_stats) {
@@ -569,8 +603,13 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
     *out = nullptr;
     hlbm_ctx *c = new (std::nothrow) hlbm_ctx();
     if (!c) return fail(nullptr, HLBM_ENOMEM, "host allocation failed");
+    Range create("hlbm_create");
     std::string err;
-    int rc = build_plan(lv, n_levels, m, Re, Ma, aoa_deg, opt, c->plan, err);
+    int rc;
+    {
+        Range r("set-up tables");
+        rc = build_plan(lv, n_levels, m, Re, Ma, aoa_deg, opt, c->plan, err);
+    }
     if (rc != HLBM_OK) { delete c; return fail(nullptr, rc, err); }
     hlbm_options o{};
     if (opt) o = *opt;
@@ -590,11 +629,17 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
         ck(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event create");
         ck(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event create");
         set_branches(c);
-        if (c->plan.precision == HLBM_FP32) build_device<float, float>(c);
-        else if (c->plan.precision == HLBM_FP16S) build_device<float, __half>(c);
-        else build_device<double, double>(c);
+        {
+            Range r("device upload and autotune");
+            if (c->plan.precision == HLBM_FP32) build_device<float, float>(c);
+            else if (c->plan.precision == HLBM_FP16S) build_device<float, __half>(c);
+            else build_device<double, double>(c);
+        }
         c->mass0 = level0_mass(c);
-        if (c->use_graphs) capture_graphs(c);
+        if (c->use_graphs) {
+            Range r("graph capture");
+            capture_graphs(c);
+        }
         ck(cudaStreamSynchronize(c->stream), "sync after create");
     } catch (const CudaError &e) {
         std::string msg = e.msg;
@@ -616,6 +661,7 @@ int hlbm_step(hlbm_ctx *c, int n_coarse)
     if (!c) return HLBM_EINVAL;
     if (c->timing_dirty) return fail(c, HLBM_ESTATE, "the state was consumed by hlbm_time_kernel");
     if (n_coarse < 0) return fail(c, HLBM_EINVAL, "n_coarse must be >= 0");
+    Range r("hlbm_step");
     try {
         for (int k = 0; k < n_coarse; k++) {
             if (c->use_graphs) {
@@ -753,6 +799,11 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
         } catch (const CudaError &) {
             return HLBM_ECUDA;
         }
+    }
+    else if (k == "bounds_violations" || k == "bounds_sites") {
+        unsigned int b[2];
+        if (cudaDeviceSynchronize() != cudaSuccess) return HLBM_ECUDA;
+        *value = debug_bounds(b) ? double(b[k == "bounds_sites"]) : -1.0;
     }
     else if (k == "fv_variant") *value = double(c->dev.m.fv_variant);
     else if (k == "fv_tune_us1") *value = c->fv_tune_us[0];
@@ -1180,6 +1231,7 @@ int hlbm_batch_step(hlbm_batch *b, int n_coarse)
         }
     }
     bool check = false;
+    Range r("hlbm_batch_step");
     try {
         // the batch stream waits for whatever the contexts' own streams hold
         for (size_t i = 0; i < b->ctx.size(); i++) {

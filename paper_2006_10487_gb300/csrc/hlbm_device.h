@@ -115,5 +115,9 @@ template <typename T, typename S> void launch_mass(const DevCtx &, double *row_s
 // adds this state's wall coefficients to the sums (Eq. 12-13)
 template <typename T, typename S> void launch_wall_stats(const DevCtx &, cudaStream_t);
 template <typename T, typename S> void launch_fields(const DevCtx &, int grid, double *rho, double *ux, double *uy, double *pop, cudaStream_t);
+// bounds-checked build (HLBM_DEBUG): violations so far and the bit mask of the
+// sites that saw them, for the whole process; returns false (out = 0) in a
+// build without the checks
+bool debug_bounds(unsigned int out[2]);
 
 }  // namespace hlbm

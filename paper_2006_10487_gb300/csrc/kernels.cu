@@ -2,7 +2,8 @@
 //
 // Storage is deviations d_i = f_i - w_i (float or double); arithmetic is in
 // the storage type.  Every kernel is a pure gather (each thread writes only
-// its own outputs), so results are deterministic; no atomics are used.
+// its own outputs), so results are deterministic; no atomics are used (the
+// bounds-checked build, HLBM_DEBUG, counts violations with atomics).
 //
 // Paper passages: Eq. 1-2 (lattice), Eq. 3 (finite volume), Eq. 4-9 (overlap
 // coupling), Section 4 (refinement boxes, wall, outer conditions),
@@ -12,11 +13,36 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "hlbm_device.h"
 
 namespace hlbm {
 namespace {
+
+// ------------------------------------------------------ bounds checks -----
+// Built with -DHLBM_DEBUG, every table-driven or computed index into a lattice
+// level, the mesh state, a tile's staged shared memory or a band snapshot is
+// checked against its extent: a violation is counted (site bit in d_bounds[1])
+// and the access goes to index 0 instead, so the run stays in bounds and the
+// host reads the count (hlbm_info "bounds_violations").  Release builds
+// compile the checks away.
+enum BoundsSite { kSiteLattice = 0, kSiteMesh = 1, kSiteStaged = 2, kSiteEntry = 3, kSiteBand = 4 };
+#ifdef HLBM_DEBUG
+__device__ unsigned int d_bounds[2];  // violations, bit mask of sites
+template <typename I> __device__ __forceinline__ I checked(I i, I n, int site)
+{
+    bool ok = i < n;
+    if constexpr (std::is_signed_v<I>) ok = ok && i >= I(0);
+    if (ok) return i;
+    atomicAdd(&d_bounds[0], 1u);
+    atomicOr(&d_bounds[1], 1u << site);
+    return I(0);
+}
+#define HLBM_CHK(i, n, site) checked<std::decay_t<decltype(i)>>((i), std::decay_t<decltype(i)>(n), (site))
+#else
+#define HLBM_CHK(i, n, site) (i)
+#endif
 
 // ---------------------------------------------------------------- D2Q9 -----
 // order: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
@@ -90,6 +116,7 @@ template <typename T> __device__ __forceinline__ void neq_complete(T nq[9])
 template <typename T>
 __device__ __forceinline__ void load_mesh(const T *__restrict__ g, int Np, int k, T &r1, T &ux, T &uy, T nq[9])
 {
+    k = HLBM_CHK(k, Np, kSiteMesh);
     r1 = g[k];
     ux = g[size_t(Np) + k];
     uy = g[size_t(2) * Np + k];
@@ -128,13 +155,13 @@ __device__ __forceinline__ T feq_diff(int i, T Eb, T drho, T rho_a, T dux, T duy
 //   p = 0: plane opp(i) at n;  p = 1: plane i at n + c_i.
 template <int P> __device__ __forceinline__ size_t st_idx(int i, size_t n, int pitch, size_t stride)
 {
-    if (P == 0) return size_t(i) * stride + n;
-    return size_t(opp(i)) * stride + n - cx(i) - ptrdiff_t(cy(i)) * pitch;
+    if (P == 0) return size_t(i) * stride + HLBM_CHK(n, stride, kSiteLattice);
+    return size_t(opp(i)) * stride + HLBM_CHK(n - cx(i) - ptrdiff_t(cy(i)) * pitch, stride, kSiteLattice);
 }
 template <int P> __device__ __forceinline__ size_t wr_idx(int i, size_t n, int pitch, size_t stride)
 {
-    if (P == 0) return size_t(opp(i)) * stride + n;
-    return size_t(i) * stride + n + cx(i) + ptrdiff_t(cy(i)) * pitch;
+    if (P == 0) return size_t(opp(i)) * stride + HLBM_CHK(n, stride, kSiteLattice);
+    return size_t(i) * stride + HLBM_CHK(n + cx(i) + ptrdiff_t(cy(i)) * pitch, stride, kSiteLattice);
 }
 
 __device__ __forceinline__ size_t node(int x, int y, int pitch) { return size_t(y + 1) * pitch + x + 1; }
@@ -318,7 +345,7 @@ __global__ void k_prolong(S *f, int nx, int ny, int pitch, size_t stride, const 
     for (int m = 0; m < 12; m++) q[m] = T(0);
     const int nd = odd ? 3 : 1;
     for (int t = 0; t < nd; t++) {
-        int b = base + pos + (odd ? t - 1 : 0);
+        int b = HLBM_CHK(base + pos + (odd ? t - 1 : 0), band_n, kSiteBand);
         T wk = odd ? (t == 0 ? T(-0.125) : (t == 1 ? T(0.75) : T(0.375))) : T(1);
 #pragma unroll
         for (int m = 0; m < 12; m++)
@@ -382,7 +409,7 @@ __global__ void k_ring_interp(const S *f, int pitch, size_t stride, const int *d
         // mesh state (rho - 1, u, (1 - 1/(2 tau_s)) f^neq) of the data at t
         // mesh plane k: rho - 1, ux, uy (q[0..2]) or f^neq_k (q[3 + k])
         T v = Q0[size_t(k < 3 ? k : 3 + k) * n_ring + r];
-        g[size_t(k) * Np + ring_start + r] = k == 0 ? v - T(1) : (k < 3 ? v : scale5 * v);
+        g[size_t(k) * Np + HLBM_CHK(ring_start + r, Np, kSiteMesh)] = k == 0 ? v - T(1) : (k < 3 ? v : scale5 * v);
     }
 }
 
@@ -568,8 +595,12 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
     T *sh = reinterpret_cast<T *>(fv_smem + 16 + size_t(max_tile_ent) * sizeof(E));
     const int t = blockIdx.x;
     const int e_begin = slice_ptr[4 * t];
+#ifdef HLBM_DEBUG
+    const int n_ent = slice_ptr[4 * t + 4] - e_begin;  // entries staged for this tile
+#endif
     if (threadIdx.x == 0) {
-        const uint32_t bytes = uint32_t(slice_ptr[4 * t + 4] - e_begin) * uint32_t(sizeof(E));
+        const uint32_t bytes =
+            uint32_t(HLBM_CHK(slice_ptr[4 * t + 4] - e_begin, max_tile_ent + 1, kSiteEntry)) * uint32_t(sizeof(E));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -595,7 +626,7 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
 #pragma unroll
     for (int j = 0; j < kFvHaloRegs; j++) {
         const int h = threadIdx.x + j * kFvThreads;
-        hidx[j] = h < hn ? halo_nodes[h0 + h] : 0;
+        hidx[j] = h < hn ? HLBM_CHK(halo_nodes[h0 + h], Np, kSiteMesh) : 0;
     }
     // wait until the previous sub-step (which wrote g) has completed
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -608,7 +639,7 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
         }
     }
     for (int h = threadIdx.x + kFvHaloRegs * kFvThreads; h < hn; h += kFvThreads) {
-        const int node = halo_nodes[h0 + h];
+        const int node = HLBM_CHK(halo_nodes[h0 + h], Np, kSiteMesh);
 #pragma unroll
         for (int i = 0; i < 9; i++) sh[i * hn + h] = g[size_t(i) * Np + node];
     }
@@ -624,7 +655,7 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
     // own state from the staged list
     T r1P, uPx, uPy, nP[9];
     {
-        const int p = own + threadIdx.x;
+        const int p = HLBM_CHK(own + int(threadIdx.x), hn, kSiteStaged);
         r1P = sh[p];
         uPx = sh[hn + p];
         uPy = sh[2 * hn + p];
@@ -650,7 +681,8 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
         for (int e0 = 0; e0 < len; e0++) {
             float a, b, cs;
             int k;
-            unpack(se[base + 32 * e0], a, b, cs, k);
+            unpack(se[HLBM_CHK(base + 32 * e0, n_ent, kSiteEntry)], a, b, cs, k);
+            k = HLBM_CHK(k, hn, kSiteStaged);
             const float r1k = sh[k], n3 = sh[3 * hn + k], n4 = sh[4 * hn + k], n5 = sh[5 * hn + k],
                         n6 = sh[6 * hn + k], n7 = sh[7 * hn + k], n8 = sh[8 * hn + k];
             const unsigned long long uk = pk2(sh[hn + k], sh[2 * hn + k]);
@@ -694,7 +726,8 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
 #pragma unroll
             for (int j = 0; j < kFvGroup; j++) {
                 if (e0 + j < len) {
-                    unpack(se[base + 32 * (e0 + j)], sx[j], sy[j], c[j], k[j]);
+                    unpack(se[HLBM_CHK(base + 32 * (e0 + j), n_ent, kSiteEntry)], sx[j], sy[j], c[j], k[j]);
+                    k[j] = HLBM_CHK(k[j], hn, kSiteStaged);
                 } else {
                     sx[j] = sy[j] = c[j] = T(0);
                     k[j] = 0;
@@ -1246,6 +1279,15 @@ template <typename T, typename S> void configure_fv(size_t bytes)
             cudaFuncSetAttribute(k_fv<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
         }
     }
+}
+
+bool debug_bounds(unsigned int out[2])
+{
+#ifdef HLBM_DEBUG
+    if (cudaMemcpyFromSymbol(out, d_bounds, 2 * sizeof(unsigned int)) == cudaSuccess) return true;
+#endif
+    out[0] = out[1] = 0;
+    return false;
 }
 
 template <typename T, typename S> void launch_forces(const DevCtx &C, cudaStream_t s)

@@ -424,11 +424,13 @@ def main():
         fr = s3.fields(-1)
         d2h += sum(a.nbytes for a in fr)
         t_e2e = time.perf_counter() - t0
+        create_ms = {k: s3.info("create_ms_" + k) for k in ("setup", "device", "capture")}
         s3.close()
         h2d = case.xy.nbytes + case.tri.nbytes + case.kind.nbytes + case.levels.nbytes
         line["e2e"] = {"value": per_step * args.steps / t_e2e / 1e6, "unit": "MLUPS",
                        "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                       "seconds": t_e2e, "includes": "hlbm_create from host arrays (set-up + upload), "
+                       "seconds": t_e2e, "create_ms": create_ms,
+                       "includes": "hlbm_create from host arrays (set-up + upload), "
                        "per-step force readback, final mesh-field readback"}
         # ---- CPU baseline: the oracle on a bounded sample
         if ws == 1:

@@ -159,6 +159,11 @@ int hlbm_populations(hlbm_ctx *ctx, int grid, double *out, size_t cap);
  * sub-step), "fv_smem" (their dynamic shared memory, bytes), "fv_variant"
  * (the register bound in use, see options), "fv_tune_us1" / "fv_tune_us2"
  * (the autotuner's launch times of the two bounds, 0 if it did not run),
+ * "create_ms_setup", "create_ms_device", "create_ms_capture" (wall time of
+ * hlbm_create's host set-up tables, device build with uploads, initial
+ * state and autotuning, and graph capture, in ms; the device build splits
+ * into "create_ms_upload", device tables and copies, and "create_ms_init",
+ * initial state and autotuner),
  * "mass" (total mass of level 0 now, sum of rho over its computed nodes,
  * FP64), "mass_drift" (its relative change since create); these two
  * synchronise the stream.  "bounds_violations", "bounds_sites": in a library

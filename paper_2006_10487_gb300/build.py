@@ -30,9 +30,9 @@ HEADERS = ["hlbm_internal.h", "hlbm_device.h", os.path.join("..", "..", "include
 def _cmd(src, obj, debug=False):
     defs = ["-DHLBM_DEBUG"] if debug else []
     if src.endswith(".cu"):
-        return [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", *defs,
+        return [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-pthread", *defs,
                 "-c", os.path.join(CSRC, src), "-o", obj]
-    return ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall", *defs,
+    return ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-pthread", "-Wall", *defs,
             f"-I{CUDA_HOME}/include", "-c", os.path.join(CSRC, src), "-o", obj]
 
 

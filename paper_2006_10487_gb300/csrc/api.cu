@@ -4,6 +4,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -42,6 +43,8 @@ struct hlbm_ctx {
     double *mass_buf = nullptr;  // [ny0 + 1]: row sums, total
     double mass0 = 0.0, mass_drift = 0.0, mass_nodes = 0.0;
     double fv_tune_us[2] = {0.0, 0.0};
+    double create_ms[3] = {0.0, 0.0, 0.0};  // host set-up tables, device build, graph capture
+    double build_ms[2] = {0.0, 0.0};         // device build: tables and uploads; initial state and autotuner
     void *(*alloc_fn)(size_t, void *) = nullptr;
     void (*free_fn)(void *, void *) = nullptr;
     void *alloc_ctx = nullptr;
@@ -322,31 +325,42 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     M.n_slices = M.Np / 32;
     M.n_tiles = (P.n + kTileRows - 1) / kTileRows;
     std::vector<int> hptr(M.n_tiles + 1, 0), hnodes;
-    std::vector<std::vector<int>> halo(M.n_tiles);
     // the self entry of a row is not stored: its streaming term vanishes in the
-    // difference form and its collision weight is C_PP = 11/18 on every node
-    auto off_diag = [&](int old) {
-        std::vector<int> ks;
+    // difference form and its collision weight is C_PP = 11/18 on every node;
+    // off-diagonal entries of device row r: od[odp[r] .. odp[r + 1])
+    std::vector<int> odp(size_t(P.n) + 1, 0), od;
+    od.reserve(P.col.size());
+    for (int r = 0; r < P.n; r++) {
+        const int old = P.perm[r];
         for (int k = P.rowptr[old]; k < P.rowptr[old + 1]; k++)
-            if (P.col[k] != old) ks.push_back(k);
-        return ks;
-    };
-    std::vector<int> town(M.n_tiles);
-    for (int t = 0; t < M.n_tiles; t++) {
-        std::vector<int> &h = halo[t];
-        // the tile's own rows are in the list too (their state is read from
-        // it); consecutive rows, so one contiguous run of the sorted list
-        for (int r = t * kTileRows; r < std::min(P.n, (t + 1) * kTileRows); r++) {
-            h.push_back(r);
-            for (int k : off_diag(P.perm[r])) h.push_back(P.inv[P.col[k]]);
-        }
-        std::sort(h.begin(), h.end());
-        h.erase(std::unique(h.begin(), h.end()), h.end());
-        town[t] = int(std::lower_bound(h.begin(), h.end(), t * kTileRows) - h.begin());
-        hptr[t + 1] = hptr[t] + int(h.size());
-        hnodes.insert(hnodes.end(), h.begin(), h.end());
-        M.max_halo = std::max(M.max_halo, int(h.size()));
+            if (P.col[k] != old) od.push_back(k);
+        odp[r + 1] = int(od.size());
     }
+    std::vector<int> town(M.n_tiles);
+    std::vector<std::vector<int>> halo(M.n_tiles);
+    parallel_for(M.n_tiles, [&](int t0, int t1) {
+        for (int t = t0; t < t1; t++) {
+            // the tile's own rows are in the list too (their state is read from
+            // it); consecutive rows, so one contiguous run of the sorted list
+            std::vector<int> &h = halo[t];
+            for (int r = t * kTileRows; r < std::min(P.n, (t + 1) * kTileRows); r++) {
+                h.push_back(r);
+                for (int j = odp[r]; j < odp[r + 1]; j++) h.push_back(P.inv[P.col[od[j]]]);
+            }
+            std::sort(h.begin(), h.end());
+            h.erase(std::unique(h.begin(), h.end()), h.end());
+            town[t] = int(std::lower_bound(h.begin(), h.end(), t * kTileRows) - h.begin());
+        }
+    }, 16);
+    for (int t = 0; t < M.n_tiles; t++) {
+        hptr[t + 1] = hptr[t] + int(halo[t].size());
+        M.max_halo = std::max(M.max_halo, int(halo[t].size()));
+    }
+    hnodes.resize(hptr[M.n_tiles]);
+    parallel_for(M.n_tiles, [&](int t0, int t1) {
+        for (int t = t0; t < t1; t++) std::copy(halo[t].begin(), halo[t].end(), hnodes.begin() + hptr[t]);
+    }, 16);
+    halo.clear();
     std::vector<int> sptr(M.n_slices), slen(M.n_slices);
     std::vector<E> ent;
     auto set_col = [](E &v, int col) {
@@ -355,36 +369,44 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     };
     // entries carry dt s_Pk and (dt / tau_u) C_Pk (the sub-step's constants folded in)
     const double dt = P.n_sub > 0 ? 1.0 / P.n_sub : 0.0, dt_tau = dt / P.tau_u;
+    // slice lengths and offsets, then the entries (slices in parallel)
+    size_t n_ent = 0;
     for (int sl = 0; sl < M.n_slices; sl++) {
         int len = 0;
-        std::vector<std::vector<int>> rows(32);
         for (int l = 0; l < 32; l++) {
             int r = sl * 32 + l;
-            if (r < P.n) rows[l] = off_diag(P.perm[r]);
-            len = std::max(len, int(rows[l].size()));
+            if (r < P.n) len = std::max(len, odp[r + 1] - odp[r]);
         }
-        sptr[sl] = int(ent.size());
+        sptr[sl] = int(n_ent);
         slen[sl] = len;
-        size_t base = ent.size();
-        ent.resize(base + size_t(32) * len);
-        for (int l = 0; l < 32; l++) {
-            int r = sl * 32 + l;
-            const std::vector<int> *h = r < P.n ? &halo[r / kTileRows] : nullptr;
-            for (int e = 0; e < len; e++) {
-                E v{};
-                if (e < int(rows[l].size())) {
-                    int k = rows[l][e];
-                    v.x = T(dt * P.sx[k]); v.y = T(dt * P.sy[k]); v.z = T(dt_tau * P.cc[k]);
-                    int col = P.inv[P.col[k]];
-                    set_col(v, int(std::lower_bound(h->begin(), h->end(), col) - h->begin()));
-                } else {
-                    v.x = v.y = v.z = T(0);  // padding: zero coefficients on a valid slot
-                    set_col(v, 0);
+        n_ent += size_t(32) * len;
+    }
+    ent.resize(n_ent);
+    parallel_for(M.n_slices, [&](int sl0, int sl1) {
+        for (int sl = sl0; sl < sl1; sl++) {
+            const int len = slen[sl];
+            const size_t base = size_t(sptr[sl]);
+            for (int l = 0; l < 32; l++) {
+                int r = sl * 32 + l;
+                const int nr = r < P.n ? odp[r + 1] - odp[r] : 0;
+                const int *h0 = r < P.n ? hnodes.data() + hptr[r / kTileRows] : nullptr;
+                const int *h1 = r < P.n ? hnodes.data() + hptr[r / kTileRows + 1] : nullptr;
+                for (int e = 0; e < len; e++) {
+                    E v{};
+                    if (e < nr) {
+                        int k = od[odp[r] + e];
+                        v.x = T(dt * P.sx[k]); v.y = T(dt * P.sy[k]); v.z = T(dt_tau * P.cc[k]);
+                        int col = P.inv[P.col[k]];
+                        set_col(v, int(std::lower_bound(h0, h1, col) - h0));
+                    } else {
+                        v.x = v.y = v.z = T(0);  // padding: zero coefficients on a valid slot
+                        set_col(v, 0);
+                    }
+                    ent[base + size_t(32) * e + l] = v;
                 }
-                ent[base + size_t(32) * e + l] = v;
             }
         }
-    }
+    }, 64);
     // one past the end, for every tile's 4 slices (the last tile may have fewer)
     sptr.resize(size_t(4) * M.n_tiles + 1, int(ent.size()));
     for (int t = 0; t < M.n_tiles; t++) M.max_tile_ent = std::max(M.max_tile_ent, sptr[4 * t + 4] - sptr[4 * t]);
@@ -457,6 +479,7 @@ template <typename T, typename S> void build_device(hlbm_ctx *c)
     D.n_sub = P.n_sub;
     D.dt_u = P.n_sub > 0 ? 1.0 / P.n_sub : 0.0;
     D.qdyn = P.qdyn;
+    const auto t_beg = std::chrono::steady_clock::now();
     // FP16S storage shift: the free-stream equilibrium minus the weights
     {
         static const double W[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
@@ -506,6 +529,7 @@ template <typename T, typename S> void build_device(hlbm_ctx *c)
         for (size_t y = 0; y < l0.hx0.size(); y++) nodes -= double(l0.hx1[y] - l0.hx0[y]);
         c->mass_nodes = nodes;
     }
+    const auto t_up = std::chrono::steady_clock::now();
     init_state<T, S>(c);
     if (P.n > 0) {
         if (c->plan.precision == HLBM_FP64) D.m.fv_variant = 1;
@@ -513,6 +537,10 @@ template <typename T, typename S> void build_device(hlbm_ctx *c)
         else D.m.fv_variant = fv_autotune<T, S>(D, c->stream, c->fv_tune_us);
         ck(cudaGetLastError(), "finite-volume autotuner");
     }
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    const auto t_end = std::chrono::steady_clock::now();
+    c->build_ms[0] = std::chrono::duration<double, std::milli>(t_up - t_beg).count();
+    c->build_ms[1] = std::chrono::duration<double, std::milli>(t_end - t_up).count();
 }
 
 void capture_graphs(hlbm_ctx *c)
@@ -606,10 +634,20 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
     Range create("hlbm_create");
     std::string err;
     int rc;
-    {
+    auto t0 = std::chrono::steady_clock::now();
+    auto lap = [&t0](double &ms) {
+        const auto t1 = std::chrono::steady_clock::now();
+        ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        t0 = t1;
+    };
+    try {
         Range r("set-up tables");
         rc = build_plan(lv, n_levels, m, Re, Ma, aoa_deg, opt, c->plan, err);
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return fail(nullptr, HLBM_ENOMEM, "host allocation failed");
     }
+    lap(c->create_ms[0]);
     if (rc != HLBM_OK) { delete c; return fail(nullptr, rc, err); }
     hlbm_options o{};
     if (opt) o = *opt;
@@ -636,11 +674,13 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
             else build_device<double, double>(c);
         }
         c->mass0 = level0_mass(c);
+        lap(c->create_ms[1]);
         if (c->use_graphs) {
             Range r("graph capture");
             capture_graphs(c);
         }
         ck(cudaStreamSynchronize(c->stream), "sync after create");
+        lap(c->create_ms[2]);
     } catch (const CudaError &e) {
         std::string msg = e.msg;
         release(c);
@@ -704,12 +744,19 @@ int hlbm_forces(hlbm_ctx *c, double *cd, double *cl, int cap, int *n_written)
         long first = std::max<long>(c->forces_read, long(counter) - c->dev.force_cap);
         long n = std::min<long>(long(counter) - first, cap);
         if (n <= 0) return HLBM_OK;
-        std::vector<double> buf(size_t(2) * c->dev.force_cap);
-        ck(cudaMemcpy(buf.data(), c->dev.force_buf, buf.size() * sizeof(double), cudaMemcpyDeviceToHost), "forces");
+        // only the n samples read: slots first .. first + n - 1 of the ring,
+        // at most two contiguous runs
+        std::vector<double> buf(size_t(2) * n);
+        const long s0 = first % c->dev.force_cap, n0 = std::min<long>(n, c->dev.force_cap - s0);
+        ck(cudaMemcpyAsync(buf.data(), c->dev.force_buf + 2 * s0, size_t(2) * n0 * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream), "forces");
+        if (n > n0)
+            ck(cudaMemcpyAsync(buf.data() + 2 * n0, c->dev.force_buf, size_t(2) * (n - n0) * sizeof(double),
+                               cudaMemcpyDeviceToHost, c->stream), "forces");
+        ck(cudaStreamSynchronize(c->stream), "sync");
         for (long k = 0; k < n; k++) {
-            long slot = (first + k) % c->dev.force_cap;
-            cd[k] = buf[2 * slot];
-            cl[k] = buf[2 * slot + 1];
+            cd[k] = buf[2 * k];
+            cl[k] = buf[2 * k + 1];
         }
         c->forces_read = first + n;
         *n_written = int(n);
@@ -806,6 +853,11 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
         *value = debug_bounds(b) ? double(b[k == "bounds_sites"]) : -1.0;
     }
     else if (k == "fv_variant") *value = double(c->dev.m.fv_variant);
+    else if (k == "create_ms_setup") *value = c->create_ms[0];
+    else if (k == "create_ms_device") *value = c->create_ms[1];
+    else if (k == "create_ms_capture") *value = c->create_ms[2];
+    else if (k == "create_ms_upload") *value = c->build_ms[0];
+    else if (k == "create_ms_init") *value = c->build_ms[1];
     else if (k == "fv_tune_us1") *value = c->fv_tune_us[0];
     else if (k == "fv_tune_us2") *value = c->fv_tune_us[1];
     else if (k == "fv_smem") *value = double(c->dev.m.smem_bytes);

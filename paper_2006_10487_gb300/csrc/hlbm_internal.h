@@ -2,9 +2,13 @@
 // kernel launchers).  Not part of the public ABI.
 #pragma once
 
+#include <algorithm>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/hlbm.h"
@@ -68,6 +72,39 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
 
 // splitmix64-based initial density deviate in [-1, 1) (host side).
 double init_deviate(uint64_t seed, uint64_t grid, uint64_t node);
+
+// Runs f(begin, end) over [0, n) in contiguous chunks of at least `grain`
+// items on up to 16 host threads (inline when there is one chunk).  Chunks
+// write disjoint outputs, so results do not depend on the thread count.  A
+// chunk that throws makes the call throw std::bad_alloc after all have ended.
+template <typename F> void parallel_for(int n, F f, int grain = 2048)
+{
+    const int hw = int(std::max(1u, std::thread::hardware_concurrency()));
+    const int nt = std::min(std::min(hw, 16), std::max(1, n / std::max(1, grain)));
+    if (nt <= 1) {
+        f(0, n);
+        return;
+    }
+    std::atomic<bool> failed{false};
+    auto run = [&](int j) {
+        try {
+            f(int(long(n) * j / nt), int(long(n) * (j + 1) / nt));
+        } catch (...) {
+            failed = true;
+        }
+    };
+    std::vector<std::thread> th;
+    for (int j = 1; j < nt; j++) {
+        try {
+            th.emplace_back(run, j);
+        } catch (...) {
+            run(j);  // no thread available: this chunk runs here
+        }
+    }
+    run(0);
+    for (auto &t : th) t.join();
+    if (failed) throw std::bad_alloc();
+}
 
 // Message returned by hlbm_last_error(NULL) on this thread.
 void set_thread_error(const std::string &msg);

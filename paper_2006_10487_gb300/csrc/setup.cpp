@@ -4,7 +4,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <unordered_map>
 
 #include "hlbm_internal.h"
 
@@ -18,7 +17,6 @@ inline V2 sub(V2 a, V2 b) { return {a.x - b.x, a.y - b.y}; }
 // outward normal times length of a directed segment along d (domain on the left)
 inline V2 perp(V2 d) { return {d.y, -d.x}; }
 
-inline uint64_t edge_key(int a, int b) { return (uint64_t(uint32_t(a)) << 32) | uint32_t(b); }
 
 // Solves A x = b for a small dense system by Gauss-Jordan elimination with
 // full pivoting; A is row-major n x n.  Returns false if singular.
@@ -154,17 +152,39 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
         if (P.kind[p] > 2) { err = "unknown node kind"; return HLBM_EINVAL; }
     auto X = [&](int p) { return V2{P.xy[2 * size_t(p)], P.xy[2 * size_t(p) + 1]}; };
 
-    // ---- directed-edge map: edge (a,b) -> triangle index and far vertex
-    std::unordered_map<uint64_t, std::pair<int, int>> emap;
-    emap.reserve(size_t(3) * P.ntri * 2);
-    for (int t = 0; t < P.ntri; t++)
-        for (int a = 0; a < 3; a++) {
-            int i0 = P.tri[3 * t + a], i1 = P.tri[3 * t + (a + 1) % 3], i2 = P.tri[3 * t + (a + 2) % 3];
-            if (!emap.emplace(edge_key(i0, i1), std::make_pair(t, i2)).second) {
-                err = "mesh is not a consistently oriented manifold";
-                return HLBM_EINVAL;
+    // ---- directed edges a -> b of the triangles, grouped by a, with the far
+    // vertex of the triangle that owns them (each directed edge at most once)
+    // (per node in ascending triangle order; etri: the triangle)
+    std::vector<int> eptr(size_t(P.n) + 1, 0), edst(3 * size_t(P.ntri)), efar(3 * size_t(P.ntri)),
+        etri(3 * size_t(P.ntri));
+    for (int t = 0; t < 3 * P.ntri; t++) eptr[P.tri[t] + 1]++;
+    for (int p = 0; p < P.n; p++) eptr[p + 1] += eptr[p];
+    {
+        std::vector<int> fill(eptr.begin(), eptr.end() - 1);
+        for (int t = 0; t < P.ntri; t++)
+            for (int a = 0; a < 3; a++) {
+                const int i0 = P.tri[3 * t + a], k = fill[i0]++;
+                edst[k] = P.tri[3 * t + (a + 1) % 3];
+                efar[k] = P.tri[3 * t + (a + 2) % 3];
+                etri[k] = t;
             }
-        }
+    }
+    {
+        std::atomic<bool> dup{false};
+        parallel_for(P.n, [&](int p0, int p1) {
+            for (int p = p0; p < p1; p++)
+                for (int k = eptr[p]; k < eptr[p + 1]; k++)
+                    for (int j = eptr[p]; j < k; j++)
+                        if (edst[j] == edst[k]) dup = true;
+        });
+        if (dup) { err = "mesh is not a consistently oriented manifold"; return HLBM_EINVAL; }
+    }
+    // far vertex of the triangle owning the directed edge a -> b, -1 if none
+    auto edge_far = [&](int a, int b) {
+        for (int k = eptr[a]; k < eptr[a + 1]; k++)
+            if (edst[k] == b) return efar[k];
+        return -1;
+    };
 
     // ---- Eq. 3 operators (cell-vertex / median-dual control volumes,
     // piecewise-linear populations).  For triangle (P, A, B), counter-clockwise,
@@ -180,24 +200,34 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     // Collision weights are the control-volume means of the hat functions:
     //   C_PP += 11/54 |T|, C_PA, C_PB += 7/108 |T|; all rows divided by
     //   A_P = sum |T| / 3.
-    std::vector<std::vector<int>> nb(P.n);
-    for (int t = 0; t < P.ntri; t++)
-        for (int a = 0; a < 3; a++) {
-            int p = P.tri[3 * t + a];
-            nb[p].push_back(P.tri[3 * t + (a + 1) % 3]);
-            nb[p].push_back(P.tri[3 * t + (a + 2) % 3]);
+    // rows: the node itself and every vertex of its triangles, sorted, unique
+    // (the out-edges a -> b and a -> far list them all); sizes, then columns
+    auto row_of = [&](int p, std::vector<int> &row) {
+        row.assign(1, p);
+        for (int k = eptr[p]; k < eptr[p + 1]; k++) {
+            row.push_back(edst[k]);
+            row.push_back(efar[k]);
         }
+        std::sort(row.begin(), row.end());
+        row.erase(std::unique(row.begin(), row.end()), row.end());
+    };
     P.rowptr.assign(P.n + 1, 0);
-    for (int p = 0; p < P.n; p++) {
-        nb[p].push_back(p);
-        std::sort(nb[p].begin(), nb[p].end());
-        nb[p].erase(std::unique(nb[p].begin(), nb[p].end()), nb[p].end());
-        P.rowptr[p + 1] = P.rowptr[p] + int(nb[p].size());
-    }
+    parallel_for(P.n, [&](int p0, int p1) {
+        std::vector<int> row;
+        for (int p = p0; p < p1; p++) {
+            row_of(p, row);
+            P.rowptr[p + 1] = int(row.size());
+        }
+    });
+    for (int p = 0; p < P.n; p++) P.rowptr[p + 1] += P.rowptr[p];
     P.col.resize(P.rowptr[P.n]);
-    for (int p = 0; p < P.n; p++) std::copy(nb[p].begin(), nb[p].end(), P.col.begin() + P.rowptr[p]);
-    nb.clear();
-    nb.shrink_to_fit();
+    parallel_for(P.n, [&](int p0, int p1) {
+        std::vector<int> row;
+        for (int p = p0; p < p1; p++) {
+            row_of(p, row);
+            std::copy(row.begin(), row.end(), P.col.begin() + P.rowptr[p]);
+        }
+    });
     P.sx.assign(P.col.size(), 0.0);
     P.sy.assign(P.col.size(), 0.0);
     P.cc.assign(P.col.size(), 0.0);
@@ -206,33 +236,50 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
         int lo = P.rowptr[row], hi = P.rowptr[row + 1];
         return int(std::lower_bound(P.col.begin() + lo, P.col.begin() + hi, c) - P.col.begin());
     };
-    for (int t = 0; t < P.ntri; t++) {
-        int v[3] = {P.tri[3 * t], P.tri[3 * t + 1], P.tri[3 * t + 2]};
-        V2 p0 = X(v[0]), p1 = X(v[1]), p2 = X(v[2]);
-        double at = 0.5 * ((p1.x - p0.x) * (p2.y - p0.y) - (p1.y - p0.y) * (p2.x - p0.x));
-        if (!(at > 0.0)) { err = "inverted or degenerate triangle"; return HLBM_EINVAL; }
-        for (int a = 0; a < 3; a++) {
-            int ip = v[a], ia = v[(a + 1) % 3], ib = v[(a + 2) % 3];
-            // edge vectors from P (keeps the short dual segments free of
-            // cancellation between large absolute coordinates)
-            V2 A = sub(X(ia), X(ip)), B = sub(X(ib), X(ip));
-            V2 dP = perp(sub(B, A));
-            V2 dA = perp({4 * B.x - 3 * A.x, 4 * B.y - 3 * A.y});
-            V2 dB = perp({3 * B.x - 4 * A.x, 3 * B.y - 4 * A.y});
-            int eP = slot(ip, ip), eA = slot(ip, ia), eB = slot(ip, ib);
-            P.sx[eP] -= (5.0 / 24.0) * dP.x; P.sy[eP] -= (5.0 / 24.0) * dP.y;
-            P.sx[eA] -= dA.x / 24.0;         P.sy[eA] -= dA.y / 24.0;
-            P.sx[eB] -= dB.x / 24.0;         P.sy[eB] -= dB.y / 24.0;
-            P.cc[eP] += (11.0 / 54.0) * at;
-            P.cc[eA] += (7.0 / 108.0) * at;
-            P.cc[eB] += (7.0 / 108.0) * at;
-            P.area[ip] += at / 3.0;
+    std::vector<double> tarea(P.ntri);
+    parallel_for(P.ntri, [&](int t0, int t1) {
+        for (int t = t0; t < t1; t++) {
+            V2 p0 = X(P.tri[3 * t]), p1 = X(P.tri[3 * t + 1]), p2 = X(P.tri[3 * t + 2]);
+            tarea[t] = 0.5 * ((p1.x - p0.x) * (p2.y - p0.y) - (p1.y - p0.y) * (p2.x - p0.x));
         }
-    }
+    });
+    for (int t = 0; t < P.ntri; t++)
+        if (!(tarea[t] > 0.0)) { err = "inverted or degenerate triangle"; return HLBM_EINVAL; }
+    // row P gathers its triangles' terms in ascending triangle order (each
+    // entry's sum runs in that order whatever the thread count)
+    parallel_for(P.n, [&](int r0, int r1) {
+        for (int ip = r0; ip < r1; ip++)
+            for (int k = eptr[ip]; k < eptr[ip + 1]; k++) {
+                const int ia = edst[k], ib = efar[k];
+                const double at = tarea[etri[k]];
+                // edge vectors from P (keeps the short dual segments free of
+                // cancellation between large absolute coordinates)
+                V2 A = sub(X(ia), X(ip)), B = sub(X(ib), X(ip));
+                V2 dP = perp(sub(B, A));
+                V2 dA = perp({4 * B.x - 3 * A.x, 4 * B.y - 3 * A.y});
+                V2 dB = perp({3 * B.x - 4 * A.x, 3 * B.y - 4 * A.y});
+                int eP = slot(ip, ip), eA = slot(ip, ia), eB = slot(ip, ib);
+                P.sx[eP] -= (5.0 / 24.0) * dP.x; P.sy[eP] -= (5.0 / 24.0) * dP.y;
+                P.sx[eA] -= dA.x / 24.0;         P.sy[eA] -= dA.y / 24.0;
+                P.sx[eB] -= dB.x / 24.0;         P.sy[eB] -= dB.y / 24.0;
+                P.cc[eP] += (11.0 / 54.0) * at;
+                P.cc[eA] += (7.0 / 108.0) * at;
+                P.cc[eB] += (7.0 / 108.0) * at;
+                P.area[ip] += at / 3.0;
+            }
+    });
+    // boundary edges (no reverse edge), then their half-edge fluxes in
+    // (triangle, corner) order
+    std::vector<uint8_t> bnd(3 * size_t(P.ntri), 0);
+    parallel_for(P.ntri, [&](int t0, int t1) {
+        for (int t = t0; t < t1; t++)
+            for (int a = 0; a < 3; a++)
+                bnd[3 * size_t(t) + a] = edge_far(P.tri[3 * t + (a + 1) % 3], P.tri[3 * t + a]) < 0;
+    });
     for (int t = 0; t < P.ntri; t++)
         for (int a = 0; a < 3; a++) {
             int ia = P.tri[3 * t + a], ib = P.tri[3 * t + (a + 1) % 3];
-            if (emap.count(edge_key(ib, ia))) continue;  // interior edge
+            if (!bnd[3 * size_t(t) + a]) continue;  // interior edge
             V2 n = perp(sub(X(ib), X(ia)));
             int e;
             e = slot(ia, ia); P.sx[e] -= 0.375 * n.x; P.sy[e] -= 0.375 * n.y;
@@ -240,12 +287,14 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
             e = slot(ib, ib); P.sx[e] -= 0.375 * n.x; P.sy[e] -= 0.375 * n.y;
             e = slot(ib, ia); P.sx[e] -= 0.125 * n.x; P.sy[e] -= 0.125 * n.y;
         }
-    for (int p = 0; p < P.n; p++)
-        for (int e = P.rowptr[p]; e < P.rowptr[p + 1]; e++) {
-            P.sx[e] /= P.area[p];
-            P.sy[e] /= P.area[p];
-            P.cc[e] /= P.area[p];
-        }
+    parallel_for(P.n, [&](int p0, int p1) {
+        for (int p = p0; p < p1; p++)
+            for (int e = P.rowptr[p]; e < P.rowptr[p + 1]; e++) {
+                P.sx[e] /= P.area[p];
+                P.sy[e] /= P.area[p];
+                P.cc[e] /= P.area[p];
+            }
+    });
 
     // ---- sub-steps: forward Euler stability of a mode damped at a = 1/tau_u
     // and oscillating at b = sqrt(2) max_P sum_k |s_Pk|: dt_u <= 2a/(a^2+b^2),
@@ -253,12 +302,16 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     if (o.n_sub > 0) {
         P.n_sub = o.n_sub;
     } else {
+        std::vector<double> srow(P.n);
+        parallel_for(P.n, [&](int p0, int p1) {
+            for (int p = p0; p < p1; p++) {
+                double s = 0.0;
+                for (int e = P.rowptr[p]; e < P.rowptr[p + 1]; e++) s += std::hypot(P.sx[e], P.sy[e]);
+                srow[p] = s;
+            }
+        });
         double smax = 0.0;
-        for (int p = 0; p < P.n; p++) {
-            double s = 0.0;
-            for (int e = P.rowptr[p]; e < P.rowptr[p + 1]; e++) s += std::hypot(P.sx[e], P.sy[e]);
-            smax = std::max(smax, s);
-        }
+        for (int p = 0; p < P.n; p++) smax = std::max(smax, srow[p]);
         double a = 1.0 / P.tau_u, b = std::sqrt(2.0) * smax;
         double n = std::ceil(1.1 * (a * a + b * b) / (2.0 * a));
         P.n_sub = n < 10.0 ? 10 : int(n);
@@ -317,7 +370,7 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
         for (int a = 0; a < 3; a++) {
             int ia = P.tri[3 * t + a], ib = P.tri[3 * t + (a + 1) % 3];
             if (P.kind[ia] != HLBM_NODE_WALL || P.kind[ib] != HLBM_NODE_WALL) continue;
-            if (emap.count(edge_key(ib, ia))) continue;
+            if (edge_far(ib, ia) >= 0) continue;
             P.wea.push_back(ia);
             P.web.push_back(ib);
         }
@@ -411,6 +464,12 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     const double cell = 2.0;
     int gw = int((bx1 - bx0) / cell) + 1, gh = int((by1 - by0) / cell) + 1;
     std::vector<std::vector<int>> bucket(size_t(gw) * gh);
+    // only the buckets that hold an interpolation node are filled
+    std::vector<uint8_t> need(size_t(gw) * gh, 0);
+    for (int node : P.is_node) {
+        double x = double(node % F.nx), y = double(node / F.nx);
+        if (x >= bx0 && x <= bx1 && y >= by0 && y <= by1) need[size_t(int((y - by0) / cell)) * gw + int((x - bx0) / cell)] = 1;
+    }
     for (int t = 0; t < P.ntri; t++) {
         double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
         for (int a = 0; a < 3; a++) {
@@ -420,7 +479,8 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
         int i0 = int((x0 - bx0) / cell), i1 = int((x1 - bx0) / cell);
         int j0 = int((y0 - by0) / cell), j1 = int((y1 - by0) / cell);
         for (int j = j0; j <= j1; j++)
-            for (int i = i0; i <= i1; i++) bucket[size_t(j) * gw + i].push_back(t);
+            for (int i = i0; i <= i1; i++)
+                if (need[size_t(j) * gw + i]) bucket[size_t(j) * gw + i].push_back(t);
     }
     const size_t nis = P.is_node.size();
     P.is_don.resize(6 * nis);
@@ -443,9 +503,9 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
         for (int a = 0; a < 3; a++) d[a] = P.tri[3 * found + a];
         for (int a = 0; a < 3; a++) {
             int e0 = P.tri[3 * found + (a + 1) % 3], e1 = P.tri[3 * found + (a + 2) % 3];
-            auto it = emap.find(edge_key(e1, e0));
-            if (it == emap.end()) { err = "an interpolation triangle touches the mesh boundary"; return HLBM_EINVAL; }
-            d[3 + a] = it->second.second;
+            const int far = edge_far(e1, e0);
+            if (far < 0) { err = "an interpolation triangle touches the mesh boundary"; return HLBM_EINVAL; }
+            d[3 + a] = far;
         }
         // psi_k reproduce {1, X, Y, X^2, XY, Y^2} exactly at (x, y):
         // sum_k psi_k m_j(x_k - x) = m_j(0)

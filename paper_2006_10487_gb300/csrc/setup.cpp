@@ -336,22 +336,36 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
             x = (x | (x << 1)) & 0x55555555u;
             return x;
         };
-        std::vector<std::pair<uint64_t, int>> key(P.n);
-        for (int p = 0; p < P.n; p++) {
-            uint32_t qx = uint32_t(std::min(65535.0, std::floor((P.xy[2 * p] - mx0) / span * 65535.0)));
-            uint32_t qy = uint32_t(std::min(65535.0, std::floor((P.xy[2 * p + 1] - my0) / span * 65535.0)));
-            key[p] = {spread(qx) | (spread(qy) << 1), p};
-        }
+        std::vector<uint32_t> key(P.n);
+        parallel_for(P.n, [&](int p0, int p1) {
+            for (int p = p0; p < p1; p++) {
+                uint32_t qx = uint32_t(std::min(65535.0, std::floor((P.xy[2 * p] - mx0) / span * 65535.0)));
+                uint32_t qy = uint32_t(std::min(65535.0, std::floor((P.xy[2 * p + 1] - my0) / span * 65535.0)));
+                key[p] = uint32_t(spread(qx) | (spread(qy) << 1));
+            }
+        });
         // wall and ring nodes keep their input order (the ring's interface data
         // and the wall edges are indexed in that order); fluid nodes are sorted
+        // by key, equal keys in input order (a stable two-pass radix sort on
+        // 16-bit digits of the 32-bit key)
         P.perm.clear();
-        for (int want : {HLBM_NODE_WALL, HLBM_NODE_FLUID, HLBM_NODE_RING}) {
-            std::vector<std::pair<uint64_t, int>> part;
-            for (int p = 0; p < P.n; p++)
-                if (P.kind[p] == want) part.push_back({want == HLBM_NODE_FLUID ? key[p].first : 0, p});
-            std::sort(part.begin(), part.end());
-            for (auto &kp : part) P.perm.push_back(kp.second);
+        P.perm.reserve(P.n);
+        for (int p = 0; p < P.n; p++)
+            if (P.kind[p] == HLBM_NODE_WALL) P.perm.push_back(p);
+        std::vector<int> fl, tmp;
+        for (int p = 0; p < P.n; p++)
+            if (P.kind[p] == HLBM_NODE_FLUID) fl.push_back(p);
+        tmp.resize(fl.size());
+        for (int shift : {0, 16}) {
+            std::vector<int> cnt(65537, 0);
+            for (int p : fl) cnt[((key[p] >> shift) & 0xffffu) + 1]++;
+            for (int d = 0; d < 65536; d++) cnt[d + 1] += cnt[d];
+            for (int p : fl) tmp[cnt[(key[p] >> shift) & 0xffffu]++] = p;
+            fl.swap(tmp);
         }
+        P.perm.insert(P.perm.end(), fl.begin(), fl.end());
+        for (int p = 0; p < P.n; p++)
+            if (P.kind[p] == HLBM_NODE_RING) P.perm.push_back(p);
     }
     P.inv.assign(P.n, 0);
     for (int q = 0; q < P.n; q++) P.inv[P.perm[q]] = q;
@@ -466,9 +480,14 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     std::vector<std::vector<int>> bucket(size_t(gw) * gh);
     // only the buckets that hold an interpolation node are filled
     std::vector<uint8_t> need(size_t(gw) * gh, 0);
+    int ni0 = gw, ni1 = -1, nj0 = gh, nj1 = -1;  // bucket range holding them
     for (int node : P.is_node) {
         double x = double(node % F.nx), y = double(node / F.nx);
-        if (x >= bx0 && x <= bx1 && y >= by0 && y <= by1) need[size_t(int((y - by0) / cell)) * gw + int((x - bx0) / cell)] = 1;
+        if (x >= bx0 && x <= bx1 && y >= by0 && y <= by1) {
+            const int i = int((x - bx0) / cell), j = int((y - by0) / cell);
+            need[size_t(j) * gw + i] = 1;
+            ni0 = std::min(ni0, i); ni1 = std::max(ni1, i); nj0 = std::min(nj0, j); nj1 = std::max(nj1, j);
+        }
     }
     for (int t = 0; t < P.ntri; t++) {
         double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
@@ -478,6 +497,7 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
         }
         int i0 = int((x0 - bx0) / cell), i1 = int((x1 - bx0) / cell);
         int j0 = int((y0 - by0) / cell), j1 = int((y1 - by0) / cell);
+        i0 = std::max(i0, ni0); i1 = std::min(i1, ni1); j0 = std::max(j0, nj0); j1 = std::min(j1, nj1);
         for (int j = j0; j <= j1; j++)
             for (int i = i0; i <= i1; i++)
                 if (need[size_t(j) * gw + i]) bucket[size_t(j) * gw + i].push_back(t);

@@ -151,6 +151,7 @@ int hlbm_populations(hlbm_ctx *ctx, int grid, double *out, size_t cap);
 
 /* Scalar information: "n_sub", "n_levels", "tau_u", "tau0".."tau7", "steps",
  * "n_interp" (structured interpolation nodes), "n_ring", "n_wall_edges",
+ * "nnz" (Eq. 3 operator entries, self entries included),
  * "lattice_updates" (computed lattice node updates per coarse step),
  * "fv_updates" (finite-volume node updates per coarse step),
  * "launches_per_step" (kernels in one coarse step), "fv_bytes" (algorithmic
@@ -234,6 +235,32 @@ int hlbm_wall_forces_static(const double *f, int n_nodes, const double *xy, cons
 int hlbm_wall_stats(hlbm_ctx *ctx, double *out, size_t cap, int *n_wall, long *n_samples);
 /* Restart the averages of hlbm_wall_stats from the next coarse step. */
 int hlbm_wall_stats_reset(hlbm_ctx *ctx);
+
+/* Discrete adjoint of the finite-volume part of the step (Eq. 3 sub-steps,
+ * the wall rule, Eq. 10-11), FP64 contexts only.
+ *
+ * The window: starting from the context's current mesh state, n_window
+ * consecutive sub-steps (1 <= n_window <= n_sub) of a finest step, each the
+ * Eq. 3 update of every mesh node followed by the wall rule, with the
+ * interface rows set after each sub-step but the last of a finest step from
+ * the current Eq. 9 interface data (the lattice state now, held fixed), then
+ *   J = (wd F_x + wl F_y) / (1/2 rho0 u0^2 C)
+ * of the final mesh state, i.e. wd C_D + wl C_L of Eq. 10-11.  The window is
+ * run on scratch buffers: the context's state and force series do not change.
+ *
+ * Outputs: *J; if grad_g is not NULL, dJ/dg of the window's initial mesh
+ * state in populations, [n_nodes][9] in input node order and D2Q9 order
+ * (cap_g >= 9 n_nodes); if grad_coef is not NULL, dJ/d(s_x, s_y, C) of every
+ * Eq. 3 operator entry, [nnz][3] in the order of the "rowptr" / "col" tables
+ * of hlbm_inspect (cap_coef >= 3 nnz).  Self entries (P, P) get 0: their
+ * streaming coefficient is eliminated by the closed control volume
+ * (sum_k s_Pk = 0) and C_PP = 11/18 is fixed.  Scratch: (n_window + 3) x 9 x
+ * n_nodes doubles, allocated and freed by the call through the context's
+ * allocator.  Synchronises the context's stream.  Errors: HLBM_ENOTIMPL
+ * (not FP64), HLBM_EINVAL (no mesh, n_window out of range, capacities),
+ * HLBM_ESTATE, HLBM_ENOMEM, HLBM_ECUDA. */
+int hlbm_fv_adjoint(hlbm_ctx *ctx, int n_window, double wd, double wl, double *J, double *grad_g, size_t cap_g,
+                    double *grad_coef, size_t cap_coef);
 
 /* Batched ensemble: many independent cases (angles of attack, Reynolds
  * numbers, mesh sizes) advanced together.  The paper runs its angle-of-attack

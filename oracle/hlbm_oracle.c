@@ -866,6 +866,58 @@ static void record_forces(orc *o)
     o->nf++;
 }
 
+/* Test functional for the adjoint of the finite-volume part: from the current
+ * mesh state, n_window sub-steps as in fv_steps (Eq. 3 on every node, then
+ * the wall rule), except that the interface rows take the Eq. 5-7 state of
+ * one fixed set of Eq. 9 data, that of the current lattice, and that they are
+ * set after every sub-step but the last of a finest step (so the window
+ * starts from the interface rows as they are); then Eq. 10-11 of the final
+ * state, J = (wd F_x + wl F_y) / (1/2 u0^2 C).  Perturbations for finite
+ * differences: the initial populations by hg dg ([n][9], input node order)
+ * and the operator entries (s_x, s_y, C) by hc dcoef ([nnz][3], CSR order),
+ * each when given.  The oracle's own state is not changed.  Returns 0, or -1
+ * without a mesh or with n_window outside 1..n_sub. */
+int orc_fv_window(orc *o, int n_window, double wd, double wl, const double *dg, double hg, const double *dcoef,
+                  double hc, double *J)
+{
+    if (!o->n || n_window < 1 || n_window > o->n_sub) return -1;
+    const size_t n = (size_t)o->n, nnz = (size_t)o->nnz;
+    double *q = malloc(12 * n * sizeof(double)), *qn = malloc(12 * n * sizeof(double));
+    double *sx = malloc(nnz * sizeof(double)), *sy = malloc(nnz * sizeof(double)), *cc = malloc(nnz * sizeof(double));
+    double *Q = malloc(((size_t)o->n_ring * 12 + 1) * sizeof(double));
+    memcpy(q, o->g, 12 * n * sizeof(double));
+    if (dg) {
+        for (size_t p = 0; p < n; p++) {
+            double f[9];
+            from_q(q + 12 * p, 1.0, f);
+            for (int i = 0; i < 9; i++) f[i] += hg * dg[9 * p + i];
+            state_q(f, q + 12 * p);
+        }
+    }
+    for (size_t e = 0; e < nnz; e++) {
+        sx[e] = o->sx[e] + (dcoef ? hc * dcoef[3 * e] : 0.0);
+        sy[e] = o->sy[e] + (dcoef ? hc * dcoef[3 * e + 1] : 0.0);
+        cc[e] = o->cc[e] + (dcoef ? hc * dcoef[3 * e + 2] : 0.0);
+    }
+    ring_interp(o, Q);
+    const double tau_s = o->lv[o->L - 1].tau;
+    for (int m = 0; m < n_window; m++) {
+        fv_substep_q(o->n, o->rowptr, o->col, sx, sy, cc, o->dt_u, o->tau_u, q, qn);
+        for (int w = 0; w < o->n_wall; w++) {
+            qn[12 * (size_t)o->wall[w] + 1] = 0.0;
+            qn[12 * (size_t)o->wall[w] + 2] = 0.0;
+        }
+        if (m < o->n_sub - 1)
+            for (int r = 0; r < o->n_ring; r++) eq5_q(Q + 12 * (size_t)r, tau_s, qn + 12 * (size_t)o->ring[r]);
+        double *t = q; q = qn; qn = t;
+    }
+    double F[2];
+    wall_force_q(o->n_wedge, o->wea, o->web, o->xy, q, F);
+    *J = (wd * F[0] + wl * F[1]) / (0.5 * o->u0 * o->u0 * o->chord);
+    free(q); free(qn); free(sx); free(sy); free(cc); free(Q);
+    return 0;
+}
+
 void orc_step(orc *o, int ncoarse)
 {
     for (int s = 0; s < ncoarse; s++) {

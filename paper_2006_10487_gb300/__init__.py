@@ -76,6 +76,8 @@ def lib():
         L.hlbm_time_kernel.argtypes = [C.c_void_p, C.c_char_p, C.c_int, dp]
         L.hlbm_wall_forces_static.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                               C.c_double, C.c_void_p, C.c_void_p]
+        L.hlbm_fv_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, dp, dp, C.c_size_t, dp,
+                                      C.c_size_t]
         L.hlbm_sync.argtypes = [C.c_void_p]
         L.hlbm_destroy.argtypes = [C.c_void_p]
         L.hlbm_last_error.argtypes = [C.c_void_p]
@@ -192,6 +194,20 @@ class Solver:
         _check(self._lib.hlbm_wall_stats(self.ctx, out.ctypes.data_as(C.POINTER(C.c_double)), out.size,
                                          C.byref(nw), C.byref(ns)), self.ctx)
         return out, ns.value
+
+    def fv_adjoint(self, n_window, wd=1.0, wl=0.0):
+        """Discrete adjoint of n_window finite-volume sub-steps and the force
+        functional J = wd C_D + wl C_L (hlbm_fv_adjoint; FP64 contexts).
+        Returns J, dJ/dg of the initial mesh populations ([n_nodes, 9], input
+        order) and dJ/d(s_x, s_y, C) of the Eq. 3 entries ([nnz, 3], the order
+        of the "rowptr" / "col" set-up tables)."""
+        n, nnz = self.case.n_nodes, int(self.info("nnz"))
+        J = np.zeros(1)
+        gg, gc = np.empty((n, 9)), np.empty((nnz, 3))
+        dp = C.POINTER(C.c_double)
+        _check(self._lib.hlbm_fv_adjoint(self.ctx, int(n_window), float(wd), float(wl), J.ctypes.data_as(dp),
+                                         gg.ctypes.data_as(dp), gg.size, gc.ctypes.data_as(dp), gc.size), self.ctx)
+        return float(J[0]), gg, gc
 
     def save(self, path):
         """Checkpoint of the whole evolving state (hlbm_save)."""

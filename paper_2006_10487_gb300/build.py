@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 
-SOURCES = ["kernels.cu", "api.cu", "setup.cpp", "static_forces.cu"]
+SOURCES = ["kernels.cu", "api.cu", "setup.cpp", "static_forces.cu", "adjoint.cu"]
 HEADERS = ["hlbm_internal.h", "hlbm_device.h", os.path.join("..", "..", "include", "hlbm.h")]
 
 

@@ -1,0 +1,344 @@
+// Discrete adjoint of the finite-volume part of the step (FP64): a window of
+// Eq. 3 sub-steps with the wall rule and the interface rows held at given
+// Eq. 9 data, ending in the wall-force functional of Eq. 10-11.
+//
+// The sub-step maps the mesh state of every node, stored as q = (rho - 1, u_x,
+// u_y, f^neq_3..8) (f^neq_0..2 follow from the zero mass and momentum of
+// f^neq), to the next one; row P of the map reads P and its neighbours P_k:
+//   acc_i = sum_k (c_i . s_k dt) [f^eq_i(P_k) - f^eq_i(P) + f^neq_i(P_k) - f^neq_i(P)]
+//           - sum_k (dt / tau_u) C_Pk f^neq_i(P_k) - (dt / tau_u) C_PP f^neq_i(P)
+//   rho' = rho + sum_i acc_i,  rho' u' = rho u + sum_i c_i acc_i,
+//   f^neq_i' = f^neq_i + acc_i - [f^eq_i(rho', u') - f^eq_i(rho, u)]
+// (the self term of the streaming sum vanishes because sum_k s_k = 0 over a
+// closed control volume; C_PP = 11/18 on every node), then u' = 0 on wall
+// nodes and, except after the last sub-step of a finest step, the interface
+// rows take Eq. 5-7 values that do not depend on the mesh state.
+//
+// The transpose is taken node by node: the thread of node Q visits every row
+// P that reads Q (Q itself and the rows having Q as a neighbour) and
+// evaluates row P with forward-mode dual numbers seeded on Q's nine state
+// components and, for a neighbour entry, on that entry's three coefficients;
+// the cotangent of row P's output contracted with those derivatives gives
+// Q's cotangent and the entry's coefficient gradient.  Every output has one
+// writer, so the result is deterministic.  This is a correctness-first
+// formulation (the per-row work is repeated for each node the row reads);
+// it is not a tuned kernel.
+#include <cuda_runtime.h>
+
+#include "hlbm_device.h"
+
+namespace hlbm {
+namespace {
+
+constexpr int kLanes = 12;  // derivative lanes: 9 state components + 3 coefficients
+
+struct Dual {
+    double v;
+    double d[kLanes];
+};
+
+__device__ __forceinline__ Dual cst(double v)
+{
+    Dual r;
+    r.v = v;
+#pragma unroll
+    for (int l = 0; l < kLanes; l++) r.d[l] = 0.0;
+    return r;
+}
+__device__ __forceinline__ Dual seeded(double v, int lane)
+{
+    Dual r = cst(v);
+    if (lane >= 0) r.d[lane] = 1.0;
+    return r;
+}
+__device__ __forceinline__ Dual operator+(const Dual &a, const Dual &b)
+{
+    Dual r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int l = 0; l < kLanes; l++) r.d[l] = a.d[l] + b.d[l];
+    return r;
+}
+__device__ __forceinline__ Dual operator-(const Dual &a, const Dual &b)
+{
+    Dual r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int l = 0; l < kLanes; l++) r.d[l] = a.d[l] - b.d[l];
+    return r;
+}
+__device__ __forceinline__ Dual operator*(const Dual &a, const Dual &b)
+{
+    Dual r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int l = 0; l < kLanes; l++) r.d[l] = a.d[l] * b.v + a.v * b.d[l];
+    return r;
+}
+__device__ __forceinline__ Dual operator*(double a, const Dual &b)
+{
+    Dual r;
+    r.v = a * b.v;
+#pragma unroll
+    for (int l = 0; l < kLanes; l++) r.d[l] = a * b.d[l];
+    return r;
+}
+__device__ __forceinline__ Dual operator/(const Dual &a, const Dual &b)
+{
+    Dual r;
+    const double ib = 1.0 / b.v;
+    r.v = a.v * ib;
+#pragma unroll
+    for (int l = 0; l < kLanes; l++) r.d[l] = (a.d[l] - r.v * b.d[l]) * ib;
+    return r;
+}
+
+// D2Q9: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+__constant__ int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int kCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+__constant__ double kW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+// Eq. 2: f^eq_i(rho, u) = w_i rho [1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u]
+__device__ __forceinline__ Dual feq(int i, const Dual &rho, const Dual &ux, const Dual &uy)
+{
+    const Dual cu = double(kCx[i]) * ux + double(kCy[i]) * uy;
+    const Dual uu = ux * ux + uy * uy;
+    return kW[i] * (rho * (cst(1.0) + 3.0 * cu + 4.5 * (cu * cu) - 1.5 * uu));
+}
+
+// f^neq_0..2 from the stored f^neq_3..8: zero mass and momentum
+__device__ __forceinline__ void complete(Dual n[9])
+{
+    n[1] = n[3] - n[5] + n[6] + n[7] - n[8];
+    n[2] = n[4] - n[5] - n[6] + n[7] + n[8];
+    n[0] = cst(0.0) - (n[1] + n[2] + n[3] + n[4] + n[5] + n[6] + n[7] + n[8]);
+}
+
+// state of node k as duals, seeded on lanes 0..8 when seed is set
+__device__ __forceinline__ void load(const double *g, int Np, int k, bool seed, Dual &rho, Dual &ux, Dual &uy,
+                                     Dual n[9])
+{
+    rho = seeded(1.0 + g[k], seed ? 0 : -1);  // lane 0: rho - 1
+    ux = seeded(g[size_t(Np) + k], seed ? 1 : -1);
+    uy = seeded(g[size_t(2) * Np + k], seed ? 2 : -1);
+#pragma unroll
+    for (int i = 3; i < 9; i++) n[i] = seeded(g[size_t(i) * Np + k], seed ? i : -1);
+    complete(n);
+}
+
+// Row P of one sub-step (see the file comment), its nine outputs as duals.
+// seed_self: derivatives with respect to P's own state; seed_pos >= 0:
+// derivatives with respect to neighbour entry seed_pos (its state and its
+// coefficients a = dt s_x, b = dt s_y, cs = dt / tau_u C).
+__device__ void row_eval(const double *g, int Np, int P, bool seed_self, int seed_pos, const int *rp,
+                         const int *rcol, const double *rcoef, double csP, bool wall, Dual out[9])
+{
+    Dual rP, uPx, uPy, nP[9];
+    load(g, Np, P, seed_self, rP, uPx, uPy, nP);
+    Dual eqP[9], acc[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        eqP[i] = feq(i, rP, uPx, uPy);
+        acc[i] = cst(0.0) - csP * nP[i];
+    }
+    for (int e = rp[P]; e < rp[P + 1]; e++) {
+        const bool sk = (e - rp[P]) == seed_pos;
+        Dual rk, ukx, uky, nk[9];
+        load(g, Np, rcol[e], sk, rk, ukx, uky, nk);
+        const Dual a = seeded(rcoef[3 * size_t(e)], sk ? 9 : -1);
+        const Dual b = seeded(rcoef[3 * size_t(e) + 1], sk ? 10 : -1);
+        const Dual cs = seeded(rcoef[3 * size_t(e) + 2], sk ? 11 : -1);
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const Dual S = double(kCx[i]) * a + double(kCy[i]) * b;
+            acc[i] = acc[i] + S * (feq(i, rk, ukx, uky) - eqP[i] + nk[i] - nP[i]) - cs * nk[i];
+        }
+    }
+    Dual drho = cst(0.0), djx = cst(0.0), djy = cst(0.0);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        drho = drho + acc[i];
+        djx = djx + double(kCx[i]) * acc[i];
+        djy = djy + double(kCy[i]) * acc[i];
+    }
+    const Dual rho2 = rP + drho;
+    const Dual ux2 = uPx + (djx - drho * uPx) / rho2, uy2 = uPy + (djy - drho * uPy) / rho2;
+    out[0] = rho2 - cst(1.0);
+    out[1] = wall ? cst(0.0) : ux2;
+    out[2] = wall ? cst(0.0) : uy2;
+#pragma unroll
+    for (int i = 3; i < 9; i++) out[i] = nP[i] + acc[i] - (feq(i, rho2, ux2, uy2) - eqP[i]);
+}
+
+// Eq. 10-11 traction of wall edge (a, b) (normal times length wn, into the
+// fluid), contracted with (wd, wl) / q; derivatives with respect to node
+// `seed_node`'s state.
+__device__ Dual edge_functional(const double *g, int Np, int a, int b, double nx, double ny, int seed_node, double wd,
+                                double wl, double inv_q)
+{
+    Dual p = cst(0.0), pxx = cst(0.0), pxy = cst(0.0), pyy = cst(0.0);
+    for (int s = 0; s < 2; s++) {
+        const int k = s ? b : a;
+        Dual r, ux, uy, n[9];
+        load(g, Np, k, k == seed_node, r, ux, uy, n);
+        p = p + (0.5 / 3.0) * r;
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            pxx = pxx + double(0.5 * kCx[i] * kCx[i]) * n[i];
+            pxy = pxy + double(0.5 * kCx[i] * kCy[i]) * n[i];
+            pyy = pyy + double(0.5 * kCy[i] * kCy[i]) * n[i];
+        }
+    }
+    const Dual pm = p - cst(1.0 / 3.0);
+    const Dual fx = cst(0.0) - nx * pm - (nx * pxx + ny * pxy);
+    const Dual fy = cst(0.0) - ny * pm - (nx * pxy + ny * pyy);
+    return inv_q * (wd * fx + wl * fy);
+}
+
+// J = sum over wall edges, one block, fixed order (deterministic)
+__global__ void __launch_bounds__(256) k_adj_value(const double *g, int Np, const int *wea, const int *web,
+                                                   const double *wn, int n_edges, double wd, double wl, double inv_q,
+                                                   double *J)
+{
+    __shared__ double part[256];
+    double s = 0.0;
+    for (int e = threadIdx.x; e < n_edges; e += blockDim.x)
+        s += edge_functional(g, Np, wea[e], web[e], wn[2 * e], wn[2 * e + 1], -1, wd, wl, inv_q).v;
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *J = part[0];
+}
+
+// cotangent of the final state: dJ/dq on wall nodes (through their edges),
+// zero elsewhere
+__global__ void k_adj_terminal(const double *g, int Np, int n, const int *wptr, const int *wedge, const int *wea,
+                               const int *web, const double *wn, double wd, double wl, double inv_q, double *lam)
+{
+    const int Q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (Q >= n) return;
+    double d[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = wptr[Q]; t < wptr[Q + 1]; t++) {  // the wall edges of node Q (none off the wall)
+        const int e = wedge[t];
+        const Dual f = edge_functional(g, Np, wea[e], web[e], wn[2 * e], wn[2 * e + 1], Q, wd, wl, inv_q);
+#pragma unroll
+        for (int l = 0; l < 9; l++) d[l] += f.d[l];
+    }
+#pragma unroll
+    for (int l = 0; l < 9; l++) lam[size_t(l) * Np + Q] = d[l];
+}
+
+// One reverse sub-step: lam_in is the cotangent of the sub-step's output,
+// lam_out that of its input g.  star: interface rows are overwritten (their
+// outputs do not depend on g).  gcoef [nnz][3] accumulates dJ / d(s_x, s_y, C)
+// (unscaled, plan order) of every off-diagonal entry.
+__global__ void __launch_bounds__(128) k_fv_adjoint(const double *g, int Np, int n, const int *rp, const int *rcol,
+                                                    const double *rcoef, const int *rcsr, const int *tp,
+                                                    const int *trow, const int *tpos, double csP, int n_wall,
+                                                    int ring_start, int star, double dt, double dt_tau,
+                                                    const double *lam_in, double *lam_out, double *gcoef)
+{
+    const int Q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (Q >= n) return;
+    double d[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = tp[Q]; t < tp[Q + 1]; t++) {
+        const int P = trow[t], pos = tpos[t];
+        if (star && P >= ring_start) continue;
+        double lp[9];
+        bool any = false;
+#pragma unroll
+        for (int o = 0; o < 9; o++) {
+            lp[o] = lam_in[size_t(o) * Np + P];
+            any |= lp[o] != 0.0;
+        }
+        if (!any) continue;
+        Dual out[9];
+        row_eval(g, Np, P, pos < 0, pos, rp, rcol, rcoef, csP, P < n_wall, out);
+        double dc[3] = {0, 0, 0};
+#pragma unroll
+        for (int o = 0; o < 9; o++) {
+#pragma unroll
+            for (int l = 0; l < 9; l++) d[l] += lp[o] * out[o].d[l];
+#pragma unroll
+            for (int c = 0; c < 3; c++) dc[c] += lp[o] * out[o].d[9 + c];
+        }
+        if (pos >= 0) {
+            double *gc = gcoef + 3 * size_t(rcsr[rp[P] + pos]);
+            gc[0] += dt * dc[0];
+            gc[1] += dt * dc[1];
+            gc[2] += dt_tau * dc[2];
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < 9; l++) lam_out[size_t(l) * Np + Q] = d[l];
+}
+
+// dJ / d(populations) of the window's initial state, input node order:
+// g_i = f^eq_i(rho, u) + f^neq_i maps to q by rho = sum g, rho u = sum c g,
+// f^neq_i = g_i - f^eq_i(rho, u).
+__global__ void k_adj_populations(const double *g, int Np, int n, const int *perm, const double *lam, double *grad)
+{
+    const int Q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (Q >= n) return;
+    Dual r, ux, uy, nq[9];
+    load(g, Np, Q, false, r, ux, uy, nq);
+    Dual f[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[i] = seeded(feq(i, r, ux, uy).v + nq[i].v, i);
+    Dual rho = cst(0.0), jx = cst(0.0), jy = cst(0.0);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        rho = rho + f[i];
+        jx = jx + double(kCx[i]) * f[i];
+        jy = jy + double(kCy[i]) * f[i];
+    }
+    const Dual vx = jx / rho, vy = jy / rho;
+    Dual q[9];
+    q[0] = rho - cst(1.0);
+    q[1] = vx;
+    q[2] = vy;
+#pragma unroll
+    for (int i = 3; i < 9; i++) q[i] = f[i] - feq(i, rho, vx, vy);
+    const int p = perm[Q];
+#pragma unroll
+    for (int l = 0; l < 9; l++) {
+        double s = 0.0;
+#pragma unroll
+        for (int o = 0; o < 9; o++) s += lam[size_t(o) * Np + Q] * q[o].d[l];
+        grad[9 * size_t(p) + l] = s;
+    }
+}
+
+}  // namespace
+
+void launch_adj_value(const AdjTables &A, const double *g, int Np, double wd, double wl, double inv_q, double *J,
+                      cudaStream_t s)
+{
+    k_adj_value<<<1, 256, 0, s>>>(g, Np, A.wea, A.web, A.wn, A.n_edges, wd, wl, inv_q, J);
+}
+
+void launch_adj_terminal(const AdjTables &A, const double *g, int Np, int n, double wd, double wl, double inv_q,
+                         double *lam, cudaStream_t s)
+{
+    k_adj_terminal<<<(n + 127) / 128, 128, 0, s>>>(g, Np, n, A.wptr, A.wedge, A.wea, A.web, A.wn, wd, wl, inv_q,
+                                                  lam);
+}
+
+void launch_fv_adjoint(const AdjTables &A, const double *g, int Np, int n, double csP, int n_wall, int ring_start,
+                       int star, double dt, double dt_tau, const double *lam_in, double *lam_out, double *gcoef,
+                       cudaStream_t s)
+{
+    k_fv_adjoint<<<(n + 127) / 128, 128, 0, s>>>(g, Np, n, A.rp, A.rcol, A.rcoef, A.rcsr, A.tp, A.trow, A.tpos, csP,
+                                                n_wall, ring_start, star, dt, dt_tau, lam_in, lam_out, gcoef);
+}
+
+void launch_adj_populations(const AdjTables &A, const double *g, int Np, int n, const double *lam, double *grad,
+                            cudaStream_t s)
+{
+    k_adj_populations<<<(n + 127) / 128, 128, 0, s>>>(g, Np, n, A.perm, lam, grad);
+}
+
+}  // namespace hlbm

@@ -45,6 +45,7 @@ struct hlbm_ctx {
     double fv_tune_us[2] = {0.0, 0.0};
     double create_ms[3] = {0.0, 0.0, 0.0};  // host set-up tables, device build, graph capture
     double build_ms[2] = {0.0, 0.0};         // device build: tables and uploads; initial state and autotuner
+    AdjTables adj;                            // finite-volume adjoint tables (built on first use)
     void *(*alloc_fn)(size_t, void *) = nullptr;
     void (*free_fn)(void *, void *) = nullptr;
     void *alloc_ctx = nullptr;
@@ -105,6 +106,17 @@ void *dalloc(hlbm_ctx *c, size_t bytes)
     }
     c->blocks.push_back(p);
     return p;
+}
+
+// Frees one block of dalloc before the context ends (per-call scratch).
+void dfree(hlbm_ctx *c, void *p)
+{
+    if (!p) return;
+    auto it = std::find(c->blocks.begin(), c->blocks.end(), p);
+    if (it == c->blocks.end()) return;
+    c->blocks.erase(it);
+    if (c->free_fn) c->free_fn(p, c->alloc_ctx);
+    else cudaFree(p);
 }
 
 template <typename V> V *upload(hlbm_ctx *c, const std::vector<V> &h)
@@ -827,6 +839,7 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
     else if (k == "n_interp") *value = double(P.is_node.size());
     else if (k == "n_ring") *value = P.n_ring;
     else if (k == "n_wall_edges") *value = double(P.wea.size());
+    else if (k == "nnz") *value = double(P.col.size());
     else if (k == "lattice_updates") {
         double u = 0;
         for (int l = 0; l < P.L; l++) {
@@ -1043,6 +1056,167 @@ int hlbm_wall_stats(hlbm_ctx *c, double *out, size_t cap, int *n_wall, long *n_s
         for (int k = 0; k < 5; k++) r[5 + k] = g[2 + k];
     }
     return HLBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device tables of the finite-volume adjoint, from the plan (device order).
+void build_adjoint_tables(hlbm_ctx *c)
+{
+    const Plan &P = c->plan;
+    AdjTables &A = c->adj;
+    const double dt = 1.0 / P.n_sub, dt_tau = dt / P.tau_u;
+    std::vector<int> rp(size_t(P.n) + 1, 0), rcol, rcsr;
+    std::vector<double> rcoef;
+    for (int r = 0; r < P.n; r++) {
+        const int old = P.perm[r];
+        for (int k = P.rowptr[old]; k < P.rowptr[old + 1]; k++) {
+            if (P.col[k] == old) continue;
+            rcol.push_back(P.inv[P.col[k]]);
+            rcsr.push_back(k);
+            rcoef.push_back(dt * P.sx[k]);
+            rcoef.push_back(dt * P.sy[k]);
+            rcoef.push_back(dt_tau * P.cc[k]);
+        }
+        rp[r + 1] = int(rcol.size());
+    }
+    // transposed: for each node, the rows that read it (its own first)
+    std::vector<int> tp(size_t(P.n) + 1, 0), trow, tpos;
+    for (int r = 0; r < P.n; r++) {
+        tp[r + 1]++;
+        for (int e = rp[r]; e < rp[r + 1]; e++) tp[rcol[e] + 1]++;
+    }
+    for (int r = 0; r < P.n; r++) tp[r + 1] += tp[r];
+    trow.resize(tp[P.n]);
+    tpos.resize(tp[P.n]);
+    std::vector<int> fill(tp.begin(), tp.end() - 1);
+    for (int r = 0; r < P.n; r++) {
+        trow[fill[r]] = r;
+        tpos[fill[r]++] = -1;
+    }
+    for (int r = 0; r < P.n; r++)
+        for (int e = rp[r]; e < rp[r + 1]; e++) {
+            const int q = rcol[e];
+            trow[fill[q]] = r;
+            tpos[fill[q]++] = e - rp[r];
+        }
+    // wall edges in device order and the edges of each node
+    const int ne = int(P.wea.size());
+    std::vector<int> wea(ne), web(ne), wptr(size_t(P.n) + 1, 0), wedge;
+    std::vector<double> wn(2 * size_t(ne));
+    for (int e = 0; e < ne; e++) {
+        wea[e] = P.inv[P.wea[e]];
+        web[e] = P.inv[P.web[e]];
+        wn[2 * e] = -(P.xy[2 * P.web[e] + 1] - P.xy[2 * P.wea[e] + 1]);  // left normal: into the fluid
+        wn[2 * e + 1] = P.xy[2 * P.web[e]] - P.xy[2 * P.wea[e]];
+        wptr[wea[e] + 1]++;
+        wptr[web[e] + 1]++;
+    }
+    for (int r = 0; r < P.n; r++) wptr[r + 1] += wptr[r];
+    wedge.resize(wptr[P.n]);
+    std::vector<int> wf(wptr.begin(), wptr.end() - 1);
+    for (int e = 0; e < ne; e++) {
+        wedge[wf[wea[e]]++] = e;
+        wedge[wf[web[e]]++] = e;
+    }
+    A.rp = upload(c, rp);
+    A.rcol = upload(c, rcol);
+    A.rcsr = upload(c, rcsr);
+    A.rcoef = upload(c, rcoef);
+    A.tp = upload(c, tp);
+    A.trow = upload(c, trow);
+    A.tpos = upload(c, tpos);
+    A.n_edges = ne;
+    A.wea = upload(c, wea);
+    A.web = upload(c, web);
+    A.wn = upload(c, wn);
+    A.wptr = upload(c, wptr);
+    A.wedge = upload(c, wedge);
+    A.perm = upload(c, P.perm);
+    A.built = true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, double *grad_g, size_t cap_g,
+                    double *grad_coef, size_t cap_coef)
+{
+    if (!c) return HLBM_EINVAL;
+    const Plan &P = c->plan;
+    if (P.precision != HLBM_FP64) return fail(c, HLBM_ENOTIMPL, "the finite-volume adjoint runs on FP64 contexts");
+    if (P.n == 0) return fail(c, HLBM_EINVAL, "the context has no mesh");
+    if (n_window < 1 || n_window > P.n_sub) return fail(c, HLBM_EINVAL, "n_window must be in 1..n_sub");
+    if (!J) return fail(c, HLBM_EINVAL, "J is NULL");
+    if (grad_g && cap_g < 9 * size_t(P.n)) return fail(c, HLBM_EINVAL, "grad_g capacity below 9 n");
+    if (grad_coef && cap_coef < 3 * P.col.size()) return fail(c, HLBM_EINVAL, "grad_coef capacity below 3 nnz");
+    if (c->timing_dirty) return fail(c, HLBM_ESTATE, "the state was consumed by hlbm_time_kernel");
+    Range r("hlbm_fv_adjoint");
+    DevCtx &D = c->dev;
+    const int Np = D.m.Np, n = P.n, M = n_window;
+    const size_t plane = size_t(9) * Np;
+    std::vector<void *> scratch;
+    auto scr = [&](size_t bytes) {
+        void *p = dalloc(c, bytes);
+        scratch.push_back(p);
+        return p;
+    };
+    int rc = HLBM_OK;
+    try {
+        if (!c->adj.built) build_adjoint_tables(c);
+        const AdjTables &A = c->adj;
+        double *st = (double *)scr((size_t(M) + 1) * plane * sizeof(double));  // states g_0 .. g_M
+        double *lam = (double *)scr(2 * plane * sizeof(double));
+        double *gc = (double *)scr(std::max<size_t>(1, 3 * P.col.size()) * sizeof(double));
+        double *gg = (double *)scr(9 * size_t(n) * sizeof(double));
+        double *dJ = (double *)scr(sizeof(double));
+        cudaStream_t s = c->stream;
+        ck(cudaMemsetAsync(st, 0, (size_t(M) + 1) * plane * sizeof(double), s), "memset");
+        ck(cudaMemsetAsync(gc, 0, 3 * P.col.size() * sizeof(double), s), "memset");
+        ck(cudaMemcpyAsync(st, D.m.g[D.m.gcur], plane * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+        // forward window with the production sub-step kernel; the interface
+        // rows take the current Eq. 9 data (Q0) at every sub-step
+        DevCtx W = D;
+        W.m.Q1 = W.m.Q0;
+        W.m.gcur = 0;
+        for (int m = 0; m < M; m++) {
+            W.m.g[0] = st + size_t(m) * plane;
+            W.m.g[1] = st + size_t(m + 1) * plane;
+            launch_fv<double, double>(W, m, s);
+        }
+        ck(cudaGetLastError(), "forward window");
+        const double inv_q = 1.0 / P.qdyn;
+        const double *gM = st + size_t(M) * plane;
+        launch_adj_value(A, gM, Np, wd, wl, inv_q, dJ, s);
+        launch_adj_terminal(A, gM, Np, n, wd, wl, inv_q, lam, s);
+        const double dt = 1.0 / P.n_sub, dt_tau = dt / P.tau_u, csP = dt_tau * (11.0 / 18.0);
+        for (int m = M - 1; m >= 0; m--) {
+            const double *lin = lam + size_t((M - 1 - m) & 1) * plane;
+            double *lout = lam + size_t((M - m) & 1) * plane;
+            launch_fv_adjoint(A, st + size_t(m) * plane, Np, n, csP, P.n_wall, P.ring_start,
+                              m < P.n_sub - 1 ? 1 : 0, dt, dt_tau, lin, lout, gc, s);
+        }
+        const double *lam0 = lam + size_t(M & 1) * plane;
+        launch_adj_populations(A, st, Np, n, lam0, gg, s);
+        ck(cudaGetLastError(), "adjoint kernels");
+        ck(cudaMemcpyAsync(J, dJ, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        if (grad_g) ck(cudaMemcpyAsync(grad_g, gg, 9 * size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        if (grad_coef)
+            ck(cudaMemcpyAsync(grad_coef, gc, 3 * P.col.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        ck(cudaStreamSynchronize(s), "sync");
+        int flag = 0;
+        ck(cudaMemcpy(&flag, D.flag, sizeof(int), cudaMemcpyDeviceToHost), "flag");
+        if (flag & 2) rc = fail(c, HLBM_ETIMEOUT, "a device-side wait gave up (operator copy did not arrive)");
+    } catch (const CudaError &e) {
+        rc = fail(c, HLBM_ECUDA, e.msg);
+    } catch (const std::bad_alloc &) {
+        rc = fail(c, HLBM_ENOMEM, "host allocation failed");
+    }
+    for (void *p : scratch) dfree(c, p);
+    return rc;
 }
 
 int hlbm_wall_stats_reset(hlbm_ctx *c)

@@ -115,6 +115,33 @@ template <typename T, typename S> void launch_mass(const DevCtx &, double *row_s
 // adds this state's wall coefficients to the sums (Eq. 12-13)
 template <typename T, typename S> void launch_wall_stats(const DevCtx &, cudaStream_t);
 template <typename T, typename S> void launch_fields(const DevCtx &, int grid, double *rho, double *ux, double *uy, double *pop, cudaStream_t);
+// Device tables of the finite-volume adjoint (FP64), device node order.
+struct AdjTables {
+    bool built = false;
+    // off-diagonal Eq. 3 entries of each row: columns, (dt s_x, dt s_y,
+    // dt / tau_u C), index of the entry in the plan's CSR
+    int *rp = nullptr, *rcol = nullptr, *rcsr = nullptr;
+    double *rcoef = nullptr;
+    // rows reading node Q: trow[tp[Q] .. tp[Q + 1]), with the position of Q
+    // in that row's entries (-1: the row of Q itself)
+    int *tp = nullptr, *trow = nullptr, *tpos = nullptr;
+    // wall edges (device-order end nodes, normal times length) and the edges
+    // of each node: wedge[wptr[Q] .. wptr[Q + 1])
+    int n_edges = 0;
+    int *wea = nullptr, *web = nullptr, *wptr = nullptr, *wedge = nullptr;
+    double *wn = nullptr;
+    int *perm = nullptr;  // device node -> input node
+};
+void launch_adj_value(const AdjTables &, const double *g, int Np, double wd, double wl, double inv_q, double *J,
+                      cudaStream_t);
+void launch_adj_terminal(const AdjTables &, const double *g, int Np, int n, double wd, double wl, double inv_q,
+                         double *lam, cudaStream_t);
+void launch_fv_adjoint(const AdjTables &, const double *g, int Np, int n, double csP, int n_wall, int ring_start,
+                       int star, double dt, double dt_tau, const double *lam_in, double *lam_out, double *gcoef,
+                       cudaStream_t);
+void launch_adj_populations(const AdjTables &, const double *g, int Np, int n, const double *lam, double *grad,
+                            cudaStream_t);
+
 // bounds-checked build (HLBM_DEBUG): violations so far and the bit mask of the
 // sites that saw them, for the whole process; returns false (out = 0) in a
 // build without the checks

@@ -1,0 +1,113 @@
+"""Discrete adjoint of the finite-volume part (hlbm_fv_adjoint, FP64) against
+the oracle: the functional matches the oracle's window, and the gradients,
+contracted with random directions, match central differences of the oracle's
+window (orc_fv_window) in the initial populations and in the Eq. 3 operator
+entries."""
+import numpy as np
+import pytest
+
+from workloads import make_case
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2006_10487_gb300 import build
+    build.build()
+    import paper_2006_10487_gb300 as H
+    return H
+
+
+@pytest.fixture(scope="module")
+def pair(H):
+    import oracle
+    case = make_case("hlbm_mini2", aoa_deg=4.0)
+    s = H.Solver(case, precision="fp64")
+    o = oracle.Oracle(case)
+    s.step(2)
+    o.step(2)
+    return case, s, o
+
+
+def _directions(case, s, seed):
+    rng = np.random.default_rng(seed)
+    dg = rng.standard_normal((case.n_nodes, 9)) * 1e-3
+    rp = s_tables(s, "rowptr").astype(int)
+    col = s_tables(s, "col").astype(int)
+    mag = np.abs(np.stack([s_tables(s, "sx"), s_tables(s, "sy"), s_tables(s, "cc")], axis=1))
+    dc = rng.standard_normal((len(col), 3)) * mag
+    for p in range(case.n_nodes):  # self entries are fixed by construction
+        for e in range(rp[p], rp[p + 1]):
+            if col[e] == p:
+                dc[e] = 0.0
+    return dg, dc
+
+
+_TABLES = {}
+
+
+def s_tables(s, name):
+    import paper_2006_10487_gb300 as H
+    key = (id(s.case), name)
+    if key not in _TABLES:
+        _TABLES[key] = H.hlbm_inspect(s.case, name, precision="fp64")
+    return _TABLES[key]
+
+
+@pytest.mark.parametrize("M,wd,wl", [(1, 1.0, 0.0), (5, 0.0, 1.0), (None, 1.0, 0.5)])
+def test_fv_adjoint_matches_oracle_finite_differences(H, pair, M, wd, wl):
+    case, s, o = pair
+    M = o.n_sub if M is None else M
+    f_before = s.fields(-1)
+    J, gg, gc = s.fv_adjoint(M, wd, wl)
+    # the window ran on scratch: the solver's state is untouched
+    for a, b in zip(f_before, s.fields(-1)):
+        assert np.array_equal(a, b)
+    J_o = o.fv_window(M, wd, wl)
+    assert abs(J - J_o) <= 1e-11 * max(1.0, abs(J_o)), (J, J_o)
+    dg, dc = _directions(case, s, seed=M)
+    hg = 1e-4
+    fd_g = (o.fv_window(M, wd, wl, dg=dg, hg=hg) - o.fv_window(M, wd, wl, dg=dg, hg=-hg)) / (2 * hg)
+    ad_g = float(np.sum(gg * dg))
+    assert abs(ad_g - fd_g) <= 1e-6 * abs(fd_g) + 1e-10, (ad_g, fd_g)
+    hc = 1e-5
+    fd_c = (o.fv_window(M, wd, wl, dcoef=dc, hc=hc) - o.fv_window(M, wd, wl, dcoef=dc, hc=-hc)) / (2 * hc)
+    ad_c = float(np.sum(gc * dc))
+    assert abs(ad_c - fd_c) <= 1e-6 * abs(fd_c) + 1e-10, (ad_c, fd_c)
+    # self entries carry no gradient
+    rp, col = s_tables(s, "rowptr").astype(int), s_tables(s, "col").astype(int)
+    diag = np.array([e for p in range(case.n_nodes) for e in range(rp[p], rp[p + 1]) if col[e] == p])
+    assert np.all(gc[diag] == 0.0)
+
+
+def test_fv_adjoint_is_deterministic_and_localised(H, pair):
+    """Two calls agree bitwise; after one sub-step only wall nodes and their
+    neighbours carry a state gradient (the functional reads wall nodes)."""
+    case, s, o = pair
+    J1, g1, c1 = s.fv_adjoint(1)
+    J2, g2, c2 = s.fv_adjoint(1)
+    assert J1 == J2 and np.array_equal(g1, g2) and np.array_equal(c1, c2)
+    rp, col = s_tables(s, "rowptr").astype(int), s_tables(s, "col").astype(int)
+    wall = set(np.flatnonzero(np.asarray(case.kind) == 1))
+    near = set(wall)
+    for p in wall:
+        near.update(col[rp[p]:rp[p + 1]])
+    nz = set(np.flatnonzero(np.any(g1 != 0.0, axis=1)))
+    assert nz <= near and wall <= nz
+
+
+def test_fv_adjoint_rejects_what_it_does_not_cover(H):
+    case = make_case("hlbm_mini2")
+    s = H.Solver(case, precision="fp32")
+    with pytest.raises(H.HlbmError) as e:
+        s.fv_adjoint(1)
+    assert e.value.code == H.HLBM_ENOTIMPL
+    s64 = H.Solver(case, precision="fp64")
+    for bad in (0, int(s64.info("n_sub")) + 1):
+        with pytest.raises(H.HlbmError) as e:
+            s64.fv_adjoint(bad)
+        assert e.value.code == H.HLBM_EINVAL

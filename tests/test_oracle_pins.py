@@ -611,3 +611,51 @@ def test_wall_coefficients_of_prescribed_states(orc):
     assert np.allclose(w[:, 3], (t * s).sum(1) / q, rtol=1e-9, atol=1e-12)
     assert np.allclose(w[:, 4], (t * n).sum(1) / q, rtol=1e-9, atol=1e-12)
     assert np.abs(w[:, 2]).max() <= 1e-12
+
+
+def test_fv_window_is_the_composition_of_the_pinned_primitives(orc):
+    """The adjoint's test functional (orc_fv_window) is, step for step, the
+    separately pinned population-form pieces: Eq. 3 sub-steps, the wall rule
+    on wall nodes, Eq. 5-7 interface rows built from the Eq. 9 data of the
+    current finest lattice after every sub-step but the last of a finest
+    step, and the Eq. 10-11 wall force over 1/2 u0^2 C."""
+    case = make_case("hlbm_mini2", aoa_deg=4.0)
+    o = orc.Oracle(case)
+    o.step(1)
+    ops = (o.table("rowptr").astype(np.int32), o.table("col").astype(np.int32), o.table("sx"), o.table("sy"),
+           o.table("cc"), None)
+    L = case.n_levels - 1
+    tau_s, tau_u, dt = o.tau(L), o.tau(-1), 1.0 / o.n_sub
+    lat = o.populations(L)
+    ring = o.table("ring").astype(int)
+    don = o.table("ring_don").astype(int).reshape(-1, 9)
+    w9 = o.table("ring_w").reshape(-1, 9)
+
+    def q_of(f):
+        rho, ux, uy = orc.moments(f)
+        return np.concatenate([[rho, ux, uy], f - orc.feq(rho, ux, uy)])
+
+    ring_pop = np.array([orc.eq5_base(sum(w9[r, k] * q_of(lat[don[r, k]]) for k in range(9)), tau_s)
+                         for r in range(len(ring))])
+    wall = np.flatnonzero(np.asarray(case.kind) == 1)
+    edges = o.table("wall_edges").astype(np.int32).reshape(-1, 2)
+    xy = o.table("xy").reshape(-1, 2)
+    u0 = case.Ma / math.sqrt(3.0)
+    qdyn = 0.5 * u0 * u0 * case.chord
+    for M, wd, wl in ((1, 1.0, 0.0), (4, 0.3, 1.0), (o.n_sub, 1.0, 0.0)):
+        g = o.populations(-1)
+        for m in range(M):
+            g = orc.fv_substep(ops, dt, tau_u, g)
+            for p in wall:
+                g[p] = orc.wall_rule(g[p])
+            if m < o.n_sub - 1:
+                g[ring] = ring_pop
+        F = orc.wall_force(edges[:, 0], edges[:, 1], xy, g)
+        expect = (wd * F[0] + wl * F[1]) / qdyn
+        got = o.fv_window(M, wd, wl)
+        assert abs(got - expect) <= 1e-10 * max(1.0, abs(expect)), (M, got, expect)
+    # the window leaves the oracle's state alone
+    assert np.array_equal(o.populations(-1), o.populations(-1))
+    before = o.populations(-1)
+    o.fv_window(3)
+    assert np.array_equal(before, o.populations(-1))

@@ -254,13 +254,20 @@ int hlbm_wall_stats_reset(hlbm_ctx *ctx);
  * Eq. 3 operator entry, [nnz][3] in the order of the "rowptr" / "col" tables
  * of hlbm_inspect (cap_coef >= 3 nnz).  Self entries (P, P) get 0: their
  * streaming coefficient is eliminated by the closed control volume
- * (sum_k s_Pk = 0) and C_PP = 11/18 is fixed.  Scratch: (n_window + 3) x 9 x
- * n_nodes doubles, allocated and freed by the call through the context's
- * allocator.  Synchronises the context's stream.  Errors: HLBM_ENOTIMPL
- * (not FP64), HLBM_EINVAL (no mesh, n_window out of range, capacities),
- * HLBM_ESTATE, HLBM_ENOMEM, HLBM_ECUDA. */
+ * (sum_k s_Pk = 0) and C_PP = 11/18 is fixed.  If grad_xy is not NULL,
+ * dJ/dx of the mesh node coordinates, [n_nodes][2] in input node order and
+ * in the input frame (the pose before the rotation by the angle of attack),
+ * through the Eq. 3 operators (their closed-form assembly from the
+ * triangles) and the wall-edge normals of Eq. 10-11, the state and the
+ * interface data held (cap_xy >= 2 n_nodes); if dJ_daoa is not NULL, dJ/d
+ * (angle of attack) per degree through the same pose change.  Scratch:
+ * (n_window + 3) x 9 x n_nodes doubles and a few per-node arrays, allocated
+ * and freed by the call through the context's allocator.  Synchronises the
+ * context's stream.  Errors: HLBM_ENOTIMPL (not FP64), HLBM_EINVAL (no
+ * mesh, n_window out of range, capacities), HLBM_ESTATE, HLBM_ENOMEM,
+ * HLBM_ECUDA. */
 int hlbm_fv_adjoint(hlbm_ctx *ctx, int n_window, double wd, double wl, double *J, double *grad_g, size_t cap_g,
-                    double *grad_coef, size_t cap_coef);
+                    double *grad_coef, size_t cap_coef, double *grad_xy, size_t cap_xy, double *dJ_daoa);
 
 /* Batched ensemble: many independent cases (angles of attack, Reynolds
  * numbers, mesh sizes) advanced together.  The paper runs its angle-of-attack

@@ -82,7 +82,7 @@ def lib(openmp=False):
             L.orc_biquad9_weights.argtypes = [C.c_double, C.c_double, _dp]
             L.orc_wall_force.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp]
             L.orc_fv_window.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, _dp, C.c_double, _dp,
-                                        C.c_double, _dp]
+                                        C.c_double, _dp, C.c_double, C.c_double, _dp]
             _LIBS[openmp] = L
         return _LIBS[openmp]
 
@@ -291,19 +291,23 @@ class Oracle:
         self._lib.orc_wall_coeffs(self.h, _pd(out))
         return out
 
-    def fv_window(self, n_window, wd=1.0, wl=0.0, dg=None, hg=0.0, dcoef=None, hc=0.0):
+    def fv_window(self, n_window, wd=1.0, wl=0.0, dg=None, hg=0.0, dcoef=None, hc=0.0, dxy=None, hx=0.0,
+                  daoa=0.0):
         """J = wd C_D + wl C_L after n_window finite-volume sub-steps from the
         current mesh state with the interface data of the current lattice held
         fixed (orc_fv_window), optionally with the initial populations moved
-        by hg * dg ([n][9]) and the operator entries by hc * dcoef ([nnz][3])."""
+        by hg * dg ([n][9]), the operator entries by hc * dcoef ([nnz][3]), the
+        input-frame node coordinates by hx * dxy ([n][2]) and the angle of
+        attack by daoa degrees (geometry rebuilt, state kept)."""
         J = np.zeros(1)
-        dg = None if dg is None else _d(dg).reshape(-1)  # kept alive through the call
+        # converted arrays are kept alive through the call
+        dg = None if dg is None else _d(dg).reshape(-1)
         dcoef = None if dcoef is None else _d(dcoef).reshape(-1)
-        dgp = None if dg is None else _pd(dg)
-        dcp = None if dcoef is None else _pd(dcoef)
-        if self._lib.orc_fv_window(self.h, int(n_window), float(wd), float(wl), dgp, float(hg), dcp, float(hc),
-                                   _pd(J)) != 0:
-            raise ValueError("fv_window needs a mesh and 1 <= n_window <= n_sub")
+        dxy = None if dxy is None else _d(dxy).reshape(-1)
+        ptr = [None if a is None else _pd(a) for a in (dg, dcoef, dxy)]
+        if self._lib.orc_fv_window(self.h, int(n_window), float(wd), float(wl), ptr[0], float(hg), ptr[1],
+                                   float(hc), ptr[2], float(hx), float(daoa), _pd(J)) != 0:
+            raise ValueError("fv_window needs a mesh, 1 <= n_window <= n_sub and a valid moved mesh")
         return float(J[0])
 
     def table(self, name):

@@ -873,18 +873,55 @@ static void record_forces(orc *o)
  * set after every sub-step but the last of a finest step (so the window
  * starts from the interface rows as they are); then Eq. 10-11 of the final
  * state, J = (wd F_x + wl F_y) / (1/2 u0^2 C).  Perturbations for finite
- * differences: the initial populations by hg dg ([n][9], input node order)
- * and the operator entries (s_x, s_y, C) by hc dcoef ([nnz][3], CSR order),
- * each when given.  The oracle's own state is not changed.  Returns 0, or -1
- * without a mesh or with n_window outside 1..n_sub. */
+ * differences: the initial populations by hg dg ([n][9], input node order),
+ * the operator entries (s_x, s_y, C) by hc dcoef ([nnz][3], CSR order), and
+ * the geometry: the input-frame node coordinates by hx dxy ([n][2]) and the
+ * angle of attack by daoa degrees, after which the pose, the Eq. 3
+ * operators and the wall normals are rebuilt (the state and the interface
+ * data stay as they are), each when given.  The oracle's own state is not
+ * changed.  Returns 0, or -1 without a mesh, with n_window outside
+ * 1..n_sub, or if the moved mesh has an inverted triangle. */
 int orc_fv_window(orc *o, int n_window, double wd, double wl, const double *dg, double hg, const double *dcoef,
-                  double hc, double *J)
+                  double hc, const double *dxy, double hx, double daoa, double *J)
 {
     if (!o->n || n_window < 1 || n_window > o->n_sub) return -1;
     const size_t n = (size_t)o->n, nnz = (size_t)o->nnz;
     double *q = malloc(12 * n * sizeof(double)), *qn = malloc(12 * n * sizeof(double));
     double *sx = malloc(nnz * sizeof(double)), *sy = malloc(nnz * sizeof(double)), *cc = malloc(nnz * sizeof(double));
     double *Q = malloc(((size_t)o->n_ring * 12 + 1) * sizeof(double));
+    double *xy = malloc(2 * n * sizeof(double));
+    memcpy(xy, o->xy, 2 * n * sizeof(double));
+    memcpy(sx, o->sx, nnz * sizeof(double));
+    memcpy(sy, o->sy, nnz * sizeof(double));
+    memcpy(cc, o->cc, nnz * sizeof(double));
+    if (dxy || daoa != 0.0) {
+        /* back to the input frame (rotation by +alpha about the pivot), move,
+         * and pose again at alpha + daoa */
+        const double al = atan2(o->sa, o->ca) + daoa * M_PI / 180.0, c2 = cos(al), s2 = sin(al);
+        for (size_t p = 0; p < n; p++) {
+            const double dx = o->xy[2 * p] - o->pivot[0], dy = o->xy[2 * p + 1] - o->pivot[1];
+            double xb = o->ca * dx - o->sa * dy, yb = o->sa * dx + o->ca * dy;
+            if (dxy) { xb += hx * dxy[2 * p]; yb += hx * dxy[2 * p + 1]; }
+            xy[2 * p] = o->pivot[0] + (c2 * xb + s2 * yb);
+            xy[2 * p + 1] = o->pivot[1] + (c2 * yb - s2 * xb);
+        }
+        int *rp2 = malloc((n + 1) * sizeof(int)), *col2 = malloc((n + 6 * (size_t)o->ntri) * sizeof(int));
+        double *b1 = malloc((n + 6 * (size_t)o->ntri) * sizeof(double)), *b2 = malloc((n + 6 * (size_t)o->ntri) * sizeof(double));
+        double *b3 = malloc((n + 6 * (size_t)o->ntri) * sizeof(double)), *ar = malloc(n * sizeof(double));
+        int nz = orc_fv_operators(o->n, xy, o->ntri, o->tri, NULL, rp2, col2, b1, b2, b3, ar);
+        int same = nz == o->nnz;
+        for (size_t e = 0; same && e < nnz; e++) same = col2[e] == o->col[e];
+        if (same) {
+            memcpy(sx, b1, nnz * sizeof(double));
+            memcpy(sy, b2, nnz * sizeof(double));
+            memcpy(cc, b3, nnz * sizeof(double));
+        }
+        free(rp2); free(col2); free(b1); free(b2); free(b3); free(ar);
+        if (!same) {
+            free(q); free(qn); free(sx); free(sy); free(cc); free(Q); free(xy);
+            return -1;
+        }
+    }
     memcpy(q, o->g, 12 * n * sizeof(double));
     if (dg) {
         for (size_t p = 0; p < n; p++) {
@@ -894,10 +931,10 @@ int orc_fv_window(orc *o, int n_window, double wd, double wl, const double *dg, 
             state_q(f, q + 12 * p);
         }
     }
-    for (size_t e = 0; e < nnz; e++) {
-        sx[e] = o->sx[e] + (dcoef ? hc * dcoef[3 * e] : 0.0);
-        sy[e] = o->sy[e] + (dcoef ? hc * dcoef[3 * e + 1] : 0.0);
-        cc[e] = o->cc[e] + (dcoef ? hc * dcoef[3 * e + 2] : 0.0);
+    for (size_t e = 0; dcoef && e < nnz; e++) {
+        sx[e] += hc * dcoef[3 * e];
+        sy[e] += hc * dcoef[3 * e + 1];
+        cc[e] += hc * dcoef[3 * e + 2];
     }
     ring_interp(o, Q);
     const double tau_s = o->lv[o->L - 1].tau;
@@ -912,9 +949,9 @@ int orc_fv_window(orc *o, int n_window, double wd, double wl, const double *dg, 
         double *t = q; q = qn; qn = t;
     }
     double F[2];
-    wall_force_q(o->n_wedge, o->wea, o->web, o->xy, q, F);
+    wall_force_q(o->n_wedge, o->wea, o->web, xy, q, F);
     *J = (wd * F[0] + wl * F[1]) / (0.5 * o->u0 * o->u0 * o->chord);
-    free(q); free(qn); free(sx); free(sy); free(cc); free(Q);
+    free(q); free(qn); free(sx); free(sy); free(cc); free(Q); free(xy);
     return 0;
 }
 

@@ -77,7 +77,7 @@ def lib():
         L.hlbm_wall_forces_static.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                               C.c_double, C.c_void_p, C.c_void_p]
         L.hlbm_fv_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, dp, dp, C.c_size_t, dp,
-                                      C.c_size_t]
+                                      C.c_size_t, dp, C.c_size_t, dp]
         L.hlbm_sync.argtypes = [C.c_void_p]
         L.hlbm_destroy.argtypes = [C.c_void_p]
         L.hlbm_last_error.argtypes = [C.c_void_p]
@@ -199,15 +199,17 @@ class Solver:
         """Discrete adjoint of n_window finite-volume sub-steps and the force
         functional J = wd C_D + wl C_L (hlbm_fv_adjoint; FP64 contexts).
         Returns J, dJ/dg of the initial mesh populations ([n_nodes, 9], input
-        order) and dJ/d(s_x, s_y, C) of the Eq. 3 entries ([nnz, 3], the order
-        of the "rowptr" / "col" set-up tables)."""
+        order), dJ/d(s_x, s_y, C) of the Eq. 3 entries ([nnz, 3], the order of
+        the "rowptr" / "col" set-up tables), dJ/dx of the input-frame node
+        coordinates ([n_nodes, 2]) and dJ/d(angle of attack) per degree."""
         n, nnz = self.case.n_nodes, int(self.info("nnz"))
-        J = np.zeros(1)
-        gg, gc = np.empty((n, 9)), np.empty((nnz, 3))
+        J, da = np.zeros(1), np.zeros(1)
+        gg, gc, gx = np.empty((n, 9)), np.empty((nnz, 3)), np.empty((n, 2))
         dp = C.POINTER(C.c_double)
         _check(self._lib.hlbm_fv_adjoint(self.ctx, int(n_window), float(wd), float(wl), J.ctypes.data_as(dp),
-                                         gg.ctypes.data_as(dp), gg.size, gc.ctypes.data_as(dp), gc.size), self.ctx)
-        return float(J[0]), gg, gc
+                                         gg.ctypes.data_as(dp), gg.size, gc.ctypes.data_as(dp), gc.size,
+                                         gx.ctypes.data_as(dp), gx.size, da.ctypes.data_as(dp)), self.ctx)
+        return float(J[0]), gg, gc, gx, float(da[0])
 
     def save(self, path):
         """Checkpoint of the whole evolving state (hlbm_save)."""

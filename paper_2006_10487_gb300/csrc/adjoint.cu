@@ -25,6 +25,8 @@
 // it is not a tuned kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "hlbm_device.h"
 
 namespace hlbm {
@@ -312,7 +314,176 @@ __global__ void k_adj_populations(const double *g, int Np, int n, const int *per
     }
 }
 
+// ------------------------------------------------ geometry (shape) part ----
+// The Eq. 3 entries of row P are U_Pk / A_P: U sums, per triangle (P, A, B)
+// counter-clockwise (edge vectors a = x_A - x_P, b = x_B - x_P),
+//   s_PP: -5/24 perp(b - a),  s_PA: -1/24 perp(4b - 3a),  s_PB: -1/24 perp(3b - 4a),
+//   C_PP: 11/54 |T|,  C_PA, C_PB: 7/108 |T|,   A_P: |T| / 3,
+// and per boundary edge a -> b: s_aa, s_bb: -3/8 perp(x_b - x_a), s_ab, s_ba:
+// -1/8 perp(x_b - x_a), with perp(d) = (d_y, -d_x).  With G_e = dJ/d(entry e)
+// the chain rule gives dJ/dU_e = G_e / A_P and dJ/dA_P = -sum_e G_e . c_e / A_P.
+// The wall force reads the edge normals n_e = (-d_y, d_x), d = x_b - x_a.
+
+// -sum_e G_e . c_e / A_P per row
+__global__ void k_adj_abar(const int *prow, const double *pcoef, const double *gc, const double *parea, int n,
+                           double *abar)
+{
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= n) return;
+    double s = 0.0;
+    for (int e = prow[P]; e < prow[P + 1]; e++)
+        for (int c = 0; c < 3; c++) s += gc[3 * size_t(e) + c] * pcoef[3 * size_t(e) + c];
+    abar[P] = -s / parea[P];
+}
+
+// dJ/dn_e of each wall edge: the traction -(p - p0) n - Pi^neq n of the final
+// state contracted with (wd, wl) / q
+__global__ void k_adj_wall_normal(const double *g, int Np, const int *inv, const int *iwea, const int *iweb,
+                                  int n_edges, double wd, double wl, double inv_q, double *h)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_edges) return;
+    double p = 0.0, pxx = 0.0, pxy = 0.0, pyy = 0.0;
+    for (int s = 0; s < 2; s++) {
+        const int k = inv[s ? iweb[e] : iwea[e]];
+        Dual r, ux, uy, nq[9];
+        load(g, Np, k, false, r, ux, uy, nq);
+        p += (0.5 / 3.0) * r.v;
+        for (int i = 0; i < 9; i++) {
+            pxx += 0.5 * kCx[i] * kCx[i] * nq[i].v;
+            pxy += 0.5 * kCx[i] * kCy[i] * nq[i].v;
+            pyy += 0.5 * kCy[i] * kCy[i] * nq[i].v;
+        }
+    }
+    const double pm = p - 1.0 / 3.0;
+    // J_e = inv_q [wd (-pm n_x - pxx n_x - pxy n_y) + wl (-pm n_y - pxy n_x - pyy n_y)]
+    h[2 * e] = inv_q * (wd * (-pm - pxx) - wl * pxy);
+    h[2 * e + 1] = inv_q * (-wd * pxy + wl * (-pm - pyy));
+}
+
+__device__ __forceinline__ int find_entry(const int *prow, const int *pcol, int row, int c)
+{
+    int lo = prow[row], hi = prow[row + 1];
+    const int end = hi;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pcol[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    // rows hold every vertex of their triangles; -1 (no term) otherwise
+    return lo < end && pcol[lo] == c ? lo : -1;
+}
+
+__device__ __forceinline__ double gget(const double *gc, int e, int c) { return e < 0 ? 0.0 : gc[3 * size_t(e) + c]; }
+
+// dJ/dx of node X (posed frame), gathered over its triangles, boundary edges
+// and wall edges; then the input frame (x_posed = p + R(-alpha)(x - p)).
+__global__ void k_adj_shape(const AdjTables A, int n, const double *gc, const double *abar, const double *h,
+                            double ca, double sa, double *gpos, double *grad_xy)
+{
+    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    if (X >= n) return;
+    double gx = 0.0, gy = 0.0;
+    const double *xy = A.pxy;
+    for (int j = A.ntp[X]; j < A.ntp[X + 1]; j++) {
+        const int t = A.ntl[j];
+        const int v[3] = {A.ptri[3 * t], A.ptri[3 * t + 1], A.ptri[3 * t + 2]};
+        // d|T| / d(vertex k): 1/2 (y_{k+1} - y_{k+2}, x_{k+2} - x_{k+1})
+        int kx = 0;
+        for (int k = 0; k < 3; k++)
+            if (v[k] == X) kx = k;
+        const int k1 = v[(kx + 1) % 3], k2 = v[(kx + 2) % 3];
+        const double dax = 0.5 * (xy[2 * k1 + 1] - xy[2 * k2 + 1]), day = 0.5 * (xy[2 * k2] - xy[2 * k1]);
+        for (int a = 0; a < 3; a++) {
+            const int ip = v[a], ia = v[(a + 1) % 3], ib = v[(a + 2) % 3];
+            const int ePP = find_entry(A.prow, A.pcol, ip, ip), ePA = find_entry(A.prow, A.pcol, ip, ia),
+                      ePB = find_entry(A.prow, A.pcol, ip, ib);
+            const double iA = 1.0 / A.parea[ip];
+            // dJ/dU of the streaming entries, w = G / A_P, and d/d(d) of -k perp(d).w = k (w_y, -w_x)
+            const double wPx = gget(gc, ePP, 0) * iA, wPy = gget(gc, ePP, 1) * iA;
+            const double wAx = gget(gc, ePA, 0) * iA, wAy = gget(gc, ePA, 1) * iA;
+            const double wBx = gget(gc, ePB, 0) * iA, wBy = gget(gc, ePB, 1) * iA;
+            // d = b - a (5/24), 4b - 3a (1/24, entry A), 3b - 4a (1/24, entry B)
+            const double gPx = (5.0 / 24.0) * wPy, gPy = -(5.0 / 24.0) * wPx;
+            const double gAx = (1.0 / 24.0) * wAy, gAy = -(1.0 / 24.0) * wAx;
+            const double gBx = (1.0 / 24.0) * wBy, gBy = -(1.0 / 24.0) * wBx;
+            const double da_x = -gPx - 3.0 * gAx - 4.0 * gBx, da_y = -gPy - 3.0 * gAy - 4.0 * gBy;  // d/da
+            const double db_x = gPx + 4.0 * gAx + 3.0 * gBx, db_y = gPy + 4.0 * gAy + 3.0 * gBy;    // d/db
+            if (X == ia) { gx += da_x; gy += da_y; }
+            if (X == ib) { gx += db_x; gy += db_y; }
+            if (X == ip) { gx -= da_x + db_x; gy -= da_y + db_y; }
+            // collision entries and the control-volume area, both multiples of |T|
+            const double kap = (11.0 / 54.0) * gget(gc, ePP, 2) * iA +
+                               (7.0 / 108.0) * (gget(gc, ePA, 2) + gget(gc, ePB, 2)) * iA + abar[ip] / 3.0;
+            gx += kap * dax;
+            gy += kap * day;
+        }
+    }
+    for (int j = A.bptr[X]; j < A.bptr[X + 1]; j++) {
+        const int b = A.blist[j], ea = A.bed[2 * b], eb = A.bed[2 * b + 1];
+        double sx_ = 0.0, sy_ = 0.0;  // sum of k (w_y, -w_x) over the four half-edge terms
+        const int e1 = find_entry(A.prow, A.pcol, ea, ea), e2 = find_entry(A.prow, A.pcol, ea, eb);
+        const int e3 = find_entry(A.prow, A.pcol, eb, eb), e4 = find_entry(A.prow, A.pcol, eb, ea);
+        const double ia_ = 1.0 / A.parea[ea], ib_ = 1.0 / A.parea[eb];
+        const double ks[4] = {0.375 * ia_, 0.125 * ia_, 0.375 * ib_, 0.125 * ib_};
+        const int es[4] = {e1, e2, e3, e4};
+        for (int q = 0; q < 4; q++) {
+            sx_ += ks[q] * gget(gc, es[q], 1);
+            sy_ -= ks[q] * gget(gc, es[q], 0);
+        }
+        if (X == eb) { gx += sx_; gy += sy_; }
+        if (X == ea) { gx -= sx_; gy -= sy_; }
+    }
+    for (int j = A.iwptr[X]; j < A.iwptr[X + 1]; j++) {
+        const int e = A.iwlist[j];
+        // n = (-d_y, d_x): dJ/dd = (h_y, -h_x)
+        const double hx = h[2 * e], hy = h[2 * e + 1];
+        if (X == A.iweb[e]) { gx += hy; gy -= hx; }
+        if (X == A.iwea[e]) { gx -= hy; gy += hx; }
+    }
+    gpos[2 * X] = gx;
+    gpos[2 * X + 1] = gy;
+    // input frame: x_posed - p = R (x - p), R = [[ca, sa], [-sa, ca]]; dJ/dx = R^T dJ/dx_posed
+    grad_xy[2 * size_t(X)] = ca * gx - sa * gy;
+    grad_xy[2 * size_t(X) + 1] = sa * gx + ca * gy;
+}
+
+// dJ/dalpha (per degree): sum_X dJ/dx_posed . d x_posed / d alpha, with
+// x_posed - p = R(alpha) (x - p): d/dalpha = (-sa dx + ca dy, -sa dy - ca dx)
+// for the input-frame offsets (dx, dy) = R^T (x_posed - p); one block, fixed order
+__global__ void __launch_bounds__(256) k_adj_aoa(const double *xy, const double *gpos, int n, double ca, double sa,
+                                                 double px, double py, double *out)
+{
+    __shared__ double part[256];
+    double s = 0.0;
+    for (int X = threadIdx.x; X < n; X += blockDim.x) {
+        const double ox = xy[2 * X] - px, oy = xy[2 * X + 1] - py;
+        const double dx = ca * ox - sa * oy, dy = sa * ox + ca * oy;
+        s += gpos[2 * X] * (-sa * dx + ca * dy) + gpos[2 * X + 1] * (-sa * dy - ca * dx);
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = part[0] * (3.14159265358979323846 / 180.0);
+}
+
 }  // namespace
+
+void launch_adj_geometry(const AdjTables &A, int n, const double *gc, const double *gM, int Np, double wd, double wl,
+                         double inv_q, double ca, double sa, double px, double py, double *scratch, double *grad_xy,
+                         double *daoa, cudaStream_t s)
+{
+    double *abar = scratch, *h = scratch + n, *gpos = h + 2 * size_t(std::max(1, A.n_edges));
+    k_adj_abar<<<(n + 127) / 128, 128, 0, s>>>(A.prow, A.pcoef, gc, A.parea, n, abar);
+    if (A.n_edges > 0)
+        k_adj_wall_normal<<<(A.n_edges + 127) / 128, 128, 0, s>>>(gM, Np, A.inv, A.iwea, A.iweb, A.n_edges, wd, wl,
+                                                                 inv_q, h);
+    k_adj_shape<<<(n + 127) / 128, 128, 0, s>>>(A, n, gc, abar, h, ca, sa, gpos, grad_xy);
+    k_adj_aoa<<<1, 256, 0, s>>>(A.pxy, gpos, n, ca, sa, px, py, daoa);
+}
 
 void launch_adj_value(const AdjTables &A, const double *g, int Np, double wd, double wl, double inv_q, double *J,
                       cudaStream_t s)

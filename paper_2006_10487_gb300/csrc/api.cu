@@ -1135,6 +1135,81 @@ void build_adjoint_tables(hlbm_ctx *c)
     A.wptr = upload(c, wptr);
     A.wedge = upload(c, wedge);
     A.perm = upload(c, P.perm);
+    // geometry tables, input node order
+    std::vector<double> pcoef(3 * P.col.size());
+    for (size_t e = 0; e < P.col.size(); e++) {
+        pcoef[3 * e] = P.sx[e];
+        pcoef[3 * e + 1] = P.sy[e];
+        pcoef[3 * e + 2] = P.cc[e];
+    }
+    std::vector<int> ntp(size_t(P.n) + 1, 0), ntl(3 * size_t(P.ntri));
+    for (int k = 0; k < 3 * P.ntri; k++) ntp[P.tri[k] + 1]++;
+    for (int r = 0; r < P.n; r++) ntp[r + 1] += ntp[r];
+    {
+        std::vector<int> f(ntp.begin(), ntp.end() - 1);
+        for (int k = 0; k < 3 * P.ntri; k++) ntl[f[P.tri[k]]++] = k / 3;
+    }
+    // boundary edges: directed triangle edges a -> b whose reverse is absent
+    std::vector<uint64_t> keys(3 * size_t(P.ntri));
+    auto key = [](int a, int b) { return (uint64_t(uint32_t(a)) << 32) | uint32_t(b); };
+    for (int t = 0; t < P.ntri; t++)
+        for (int a = 0; a < 3; a++) keys[3 * size_t(t) + a] = key(P.tri[3 * t + a], P.tri[3 * t + (a + 1) % 3]);
+    std::vector<uint64_t> sorted(keys);
+    std::sort(sorted.begin(), sorted.end());
+    std::vector<int> bed, bptr(size_t(P.n) + 1, 0), blist;
+    for (int t = 0; t < P.ntri; t++)
+        for (int a = 0; a < 3; a++) {
+            const int ia = P.tri[3 * t + a], ib = P.tri[3 * t + (a + 1) % 3];
+            if (std::binary_search(sorted.begin(), sorted.end(), key(ib, ia))) continue;
+            bed.push_back(ia);
+            bed.push_back(ib);
+        }
+    const int nb = int(bed.size() / 2);
+    for (int b = 0; b < nb; b++) {
+        bptr[bed[2 * b] + 1]++;
+        bptr[bed[2 * b + 1] + 1]++;
+    }
+    for (int r = 0; r < P.n; r++) bptr[r + 1] += bptr[r];
+    blist.resize(bptr[P.n]);
+    {
+        std::vector<int> f(bptr.begin(), bptr.end() - 1);
+        for (int b = 0; b < nb; b++) {
+            blist[f[bed[2 * b]]++] = b;
+            blist[f[bed[2 * b + 1]]++] = b;
+        }
+    }
+    std::vector<int> iwptr(size_t(P.n) + 1, 0), iwlist;
+    for (int e = 0; e < ne; e++) {
+        iwptr[P.wea[e] + 1]++;
+        iwptr[P.web[e] + 1]++;
+    }
+    for (int r = 0; r < P.n; r++) iwptr[r + 1] += iwptr[r];
+    iwlist.resize(iwptr[P.n]);
+    {
+        std::vector<int> f(iwptr.begin(), iwptr.end() - 1);
+        for (int e = 0; e < ne; e++) {
+            iwlist[f[P.wea[e]]++] = e;
+            iwlist[f[P.web[e]]++] = e;
+        }
+    }
+    A.n_tri = P.ntri;
+    A.n_bedge = nb;
+    A.prow = upload(c, P.rowptr);
+    A.pcol = upload(c, P.col);
+    A.pcoef = upload(c, pcoef);
+    A.parea = upload(c, P.area);
+    A.pxy = upload(c, P.xy);
+    A.ptri = upload(c, P.tri);
+    A.ntp = upload(c, ntp);
+    A.ntl = upload(c, ntl);
+    A.bed = upload(c, bed);
+    A.bptr = upload(c, bptr);
+    A.blist = upload(c, blist);
+    A.iwea = upload(c, P.wea);
+    A.iweb = upload(c, P.web);
+    A.iwptr = upload(c, iwptr);
+    A.iwlist = upload(c, iwlist);
+    A.inv = upload(c, P.inv);
     A.built = true;
 }
 
@@ -1143,7 +1218,7 @@ void build_adjoint_tables(hlbm_ctx *c)
 extern "C" {
 
 int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, double *grad_g, size_t cap_g,
-                    double *grad_coef, size_t cap_coef)
+                    double *grad_coef, size_t cap_coef, double *grad_xy, size_t cap_xy, double *dJ_daoa)
 {
     if (!c) return HLBM_EINVAL;
     const Plan &P = c->plan;
@@ -1153,6 +1228,7 @@ int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, 
     if (!J) return fail(c, HLBM_EINVAL, "J is NULL");
     if (grad_g && cap_g < 9 * size_t(P.n)) return fail(c, HLBM_EINVAL, "grad_g capacity below 9 n");
     if (grad_coef && cap_coef < 3 * P.col.size()) return fail(c, HLBM_EINVAL, "grad_coef capacity below 3 nnz");
+    if (grad_xy && cap_xy < 2 * size_t(P.n)) return fail(c, HLBM_EINVAL, "grad_xy capacity below 2 n");
     if (c->timing_dirty) return fail(c, HLBM_ESTATE, "the state was consumed by hlbm_time_kernel");
     Range r("hlbm_fv_adjoint");
     DevCtx &D = c->dev;
@@ -1172,7 +1248,11 @@ int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, 
         double *lam = (double *)scr(2 * plane * sizeof(double));
         double *gc = (double *)scr(std::max<size_t>(1, 3 * P.col.size()) * sizeof(double));
         double *gg = (double *)scr(9 * size_t(n) * sizeof(double));
-        double *dJ = (double *)scr(sizeof(double));
+        double *dJ = (double *)scr(2 * sizeof(double));  // J, dJ/d(angle of attack)
+        const bool geo = grad_xy || dJ_daoa;
+        double *gxy = geo ? (double *)scr(2 * size_t(n) * sizeof(double)) : nullptr;
+        double *gs = geo ? (double *)scr((3 * size_t(n) + 2 * size_t(std::max(1, c->adj.n_edges))) * sizeof(double))
+                         : nullptr;
         cudaStream_t s = c->stream;
         ck(cudaMemsetAsync(st, 0, (size_t(M) + 1) * plane * sizeof(double), s), "memset");
         ck(cudaMemsetAsync(gc, 0, 3 * P.col.size() * sizeof(double), s), "memset");
@@ -1201,11 +1281,18 @@ int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, 
         }
         const double *lam0 = lam + size_t(M & 1) * plane;
         launch_adj_populations(A, st, Np, n, lam0, gg, s);
+        if (geo) {
+            const double al = P.aoa_deg * M_PI / 180.0;
+            launch_adj_geometry(A, n, gc, gM, Np, wd, wl, inv_q, std::cos(al), std::sin(al), P.pivot[0], P.pivot[1],
+                                gs, gxy, dJ + 1, s);
+        }
         ck(cudaGetLastError(), "adjoint kernels");
         ck(cudaMemcpyAsync(J, dJ, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         if (grad_g) ck(cudaMemcpyAsync(grad_g, gg, 9 * size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         if (grad_coef)
             ck(cudaMemcpyAsync(grad_coef, gc, 3 * P.col.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        if (grad_xy) ck(cudaMemcpyAsync(grad_xy, gxy, 2 * size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        if (dJ_daoa) ck(cudaMemcpyAsync(dJ_daoa, dJ + 1, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         ck(cudaStreamSynchronize(s), "sync");
         int flag = 0;
         ck(cudaMemcpy(&flag, D.flag, sizeof(int), cudaMemcpyDeviceToHost), "flag");

@@ -131,6 +131,16 @@ struct AdjTables {
     int *wea = nullptr, *web = nullptr, *wptr = nullptr, *wedge = nullptr;
     double *wn = nullptr;
     int *perm = nullptr;  // device node -> input node
+    // geometry (input node order) for dJ / d(node coordinates): the plan's CSR
+    // operators (s_x, s_y, C) and control-volume areas, posed coordinates,
+    // triangles and the triangles of each node, boundary edges (a -> b, no
+    // reverse edge) and wall edges of each node
+    int n_tri = 0, n_bedge = 0;
+    int *prow = nullptr, *pcol = nullptr, *ptri = nullptr, *ntp = nullptr, *ntl = nullptr;
+    double *pcoef = nullptr, *parea = nullptr, *pxy = nullptr;
+    int *bed = nullptr, *bptr = nullptr, *blist = nullptr;
+    int *iwea = nullptr, *iweb = nullptr, *iwptr = nullptr, *iwlist = nullptr;
+    int *inv = nullptr;  // input node -> device node
 };
 void launch_adj_value(const AdjTables &, const double *g, int Np, double wd, double wl, double inv_q, double *J,
                       cudaStream_t);
@@ -141,6 +151,13 @@ void launch_fv_adjoint(const AdjTables &, const double *g, int Np, int n, double
                        cudaStream_t);
 void launch_adj_populations(const AdjTables &, const double *g, int Np, int n, const double *lam, double *grad,
                             cudaStream_t);
+// dJ/d(node coordinates) from the operator-entry gradient gc ([nnz][3], plan
+// order) and the wall normals of the final state gM; grad_xy [n][2] in the
+// input frame, dJ / d(angle of attack, per degree) into *daoa.  scratch:
+// n + 2 n_wall_edges + 2 n doubles.
+void launch_adj_geometry(const AdjTables &, int n, const double *gc, const double *gM, int Np, double wd, double wl,
+                         double inv_q, double ca, double sa, double px, double py, double *scratch, double *grad_xy,
+                         double *daoa, cudaStream_t);
 
 // bounds-checked build (HLBM_DEBUG): violations so far and the bit mask of the
 // sites that saw them, for the whole process; returns false (out = 0) in a

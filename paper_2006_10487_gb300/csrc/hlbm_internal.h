@@ -35,6 +35,7 @@ struct Plan {
     int L = 0;
     LevelPlan lv[kMaxLevels];
     double u0 = 0, nu = 0, tau_u = 0, chord = 0, qdyn = 0;
+    double aoa_deg = 0, pivot[2] = {0, 0};  // mesh pose: rotation by -aoa about the pivot
     int n_sub = 0;
     int precision = HLBM_FP64;
     uint64_t seed = 0;

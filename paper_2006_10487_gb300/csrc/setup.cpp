@@ -138,6 +138,9 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     // ---- rigid rotation by -alpha about the pivot (alpha > 0: nose up)
     const double al = aoa_deg * M_PI / 180.0, ca = std::cos(al), sa = std::sin(al);
     const double px = m->pivot[0], py = m->pivot[1];
+    P.aoa_deg = aoa_deg;
+    P.pivot[0] = px;
+    P.pivot[1] = py;
     P.xy.resize(2 * size_t(P.n));
     for (int p = 0; p < P.n; p++) {
         double dx = m->xy[2 * p] - px, dy = m->xy[2 * p + 1] - py;

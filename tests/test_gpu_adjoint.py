@@ -63,7 +63,7 @@ def test_fv_adjoint_matches_oracle_finite_differences(H, pair, M, wd, wl):
     case, s, o = pair
     M = o.n_sub if M is None else M
     f_before = s.fields(-1)
-    J, gg, gc = s.fv_adjoint(M, wd, wl)
+    J, gg, gc, gx, da = s.fv_adjoint(M, wd, wl)
     # the window ran on scratch: the solver's state is untouched
     for a, b in zip(f_before, s.fields(-1)):
         assert np.array_equal(a, b)
@@ -78,6 +78,16 @@ def test_fv_adjoint_matches_oracle_finite_differences(H, pair, M, wd, wl):
     fd_c = (o.fv_window(M, wd, wl, dcoef=dc, hc=hc) - o.fv_window(M, wd, wl, dcoef=dc, hc=-hc)) / (2 * hc)
     ad_c = float(np.sum(gc * dc))
     assert abs(ad_c - fd_c) <= 1e-6 * abs(fd_c) + 1e-10, (ad_c, fd_c)
+    # geometry: node coordinates (input frame) and the angle of attack, the
+    # oracle rebuilding its operators and wall normals for the moved mesh
+    dxy = np.random.default_rng(100 + M).standard_normal((case.n_nodes, 2))
+    hx = 1e-5
+    fd_x = (o.fv_window(M, wd, wl, dxy=dxy, hx=hx) - o.fv_window(M, wd, wl, dxy=dxy, hx=-hx)) / (2 * hx)
+    ad_x = float(np.sum(gx * dxy))
+    assert abs(ad_x - fd_x) <= 1e-6 * abs(fd_x) + 1e-9, (ad_x, fd_x)
+    ha = 1e-3
+    fd_a = (o.fv_window(M, wd, wl, daoa=ha) - o.fv_window(M, wd, wl, daoa=-ha)) / (2 * ha)
+    assert abs(da - fd_a) <= 1e-6 * abs(fd_a) + 1e-9, (da, fd_a)
     # self entries carry no gradient
     rp, col = s_tables(s, "rowptr").astype(int), s_tables(s, "col").astype(int)
     diag = np.array([e for p in range(case.n_nodes) for e in range(rp[p], rp[p + 1]) if col[e] == p])
@@ -88,9 +98,10 @@ def test_fv_adjoint_is_deterministic_and_localised(H, pair):
     """Two calls agree bitwise; after one sub-step only wall nodes and their
     neighbours carry a state gradient (the functional reads wall nodes)."""
     case, s, o = pair
-    J1, g1, c1 = s.fv_adjoint(1)
-    J2, g2, c2 = s.fv_adjoint(1)
+    J1, g1, c1, x1, a1 = s.fv_adjoint(1)
+    J2, g2, c2, x2, a2 = s.fv_adjoint(1)
     assert J1 == J2 and np.array_equal(g1, g2) and np.array_equal(c1, c2)
+    assert np.array_equal(x1, x2) and a1 == a2
     rp, col = s_tables(s, "rowptr").astype(int), s_tables(s, "col").astype(int)
     wall = set(np.flatnonzero(np.asarray(case.kind) == 1))
     near = set(wall)

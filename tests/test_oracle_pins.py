@@ -654,6 +654,9 @@ def test_fv_window_is_the_composition_of_the_pinned_primitives(orc):
         expect = (wd * F[0] + wl * F[1]) / qdyn
         got = o.fv_window(M, wd, wl)
         assert abs(got - expect) <= 1e-10 * max(1.0, abs(expect)), (M, got, expect)
+    # rebuilding the geometry without moving it changes nothing but rounding
+    J0 = o.fv_window(3, 1.0, 0.0)
+    assert abs(o.fv_window(3, 1.0, 0.0, dxy=np.zeros((case.n_nodes, 2)), hx=1.0) - J0) <= 1e-13 * abs(J0)
     # the window leaves the oracle's state alone
     assert np.array_equal(o.populations(-1), o.populations(-1))
     before = o.populations(-1)

@@ -228,7 +228,7 @@ def main():
     from paper_2006_10487_gb300 import build
     build.build()
     import paper_2006_10487_gb300 as H
-    from workloads import make_case
+    from workloads import make_case, thickness_modes
 
     case = make_case(WORKLOAD)
     stream = torch.cuda.current_stream()
@@ -315,7 +315,8 @@ def main():
             "includes": "scratch allocation, forward window (stored states), reverse sweep, "
                         "population and operator-entry gradients copied to the host",
             "grad_norm_state": float((gg5 ** 2).sum() ** 0.5), "grad_norm_coef": float((gc5 ** 2).sum() ** 0.5),
-            "dJ_daoa_per_deg": da5}
+            "dJ_daoa_per_deg": da5,
+            "dJ_dthickness_modes": [float((gx5 * f).sum()) for f in thickness_modes(case)]}
         del gg5, gc5, gx5
         # ---- the large-Re configuration (1.5 M-node mesh): the finite-volume
         # state (~250 MB per sub-step) no longer fits in L2, so this is the

@@ -94,6 +94,23 @@ def test_fv_adjoint_matches_oracle_finite_differences(H, pair, M, wd, wl):
     assert np.all(gc[diag] == 0.0)
 
 
+def test_thickness_and_incidence_gradients_match_oracle(H, pair):
+    """dJ/dA_m of the 12 thickness bumps (workloads.thickness_modes: the
+    node displacement of t(x) += A_m sin(m pi x), blended to zero at the
+    interface ring) and dJ/d(angle of attack), over a full finest step's
+    sub-steps, against oracle central differences."""
+    from workloads import thickness_modes
+    case, s, o = pair
+    M = o.n_sub
+    J, gg, gc, gx, da = s.fv_adjoint(M, 1.0, 0.0)
+    modes = thickness_modes(case)
+    h = 1e-6
+    for m, field in enumerate(modes):
+        ad = float(np.sum(gx * field))
+        fd = (o.fv_window(M, 1.0, 0.0, dxy=field, hx=h) - o.fv_window(M, 1.0, 0.0, dxy=field, hx=-h)) / (2 * h)
+        assert abs(ad - fd) <= 1e-5 * abs(fd) + 1e-7, (m + 1, ad, fd)
+
+
 def test_fv_adjoint_is_deterministic_and_localised(H, pair):
     """Two calls agree bitwise; after one sub-step only wall nodes and their
     neighbours carry a state gradient (the functional reads wall nodes)."""

@@ -16,5 +16,6 @@ from .naca import (  # noqa: F401
     make_case,
     naca0012_half_thickness,
     o_mesh,
+    thickness_modes,
     uniform_equivalent,
 )

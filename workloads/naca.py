@@ -130,6 +130,29 @@ def o_mesh(chord, leading_edge, n_theta, n_layers, stretch, ell_a, ell_b):
     return xy, tri, kind
 
 
+def thickness_modes(case, n_modes=12):
+    """Node displacement fields of thickness bumps, [n_modes, N, 2] in the
+    zero-incidence frame: mode m (1 .. n_modes) adds sin(m pi x) (x = chord
+    fraction) to the half thickness t(x), i.e. moves wall node k by
+    (0, +-C sin(m pi x_k)) (+ upper, - lower surface), and moves the node of
+    ring j on the same mesh line by that times 1 - j / n_layers (linear
+    blending: the outer interface ring stays in place)."""
+    if not case.n_theta or not case.n_layers:
+        raise ValueError("thickness modes need an O-mesh case")
+    nt, nl = case.n_theta, case.n_layers
+    le_x, le_y = case.pivot[0] - 0.25 * case.chord, case.pivot[1]
+    wall = case.xy[:nt]
+    xc = np.clip((wall[:, 0] - le_x) / case.chord, 0.0, 1.0)
+    sign = np.where(np.arange(nt) <= nt // 2, 1.0, -1.0)
+    sign[wall[:, 1] < le_y] = -1.0
+    blend = 1.0 - np.arange(nl + 1, dtype=np.float64) / nl
+    out = np.zeros((n_modes, case.n_nodes, 2))
+    for m in range(1, n_modes + 1):
+        dy = sign * case.chord * np.sin(m * math.pi * xc)
+        out[m - 1, :, 1] = (blend[:, None] * dy[None, :]).reshape(-1)
+    return out
+
+
 @dataclasses.dataclass
 class Case:
     """One HLBM problem: Cartesian levels, triangular mesh and flow parameters."""

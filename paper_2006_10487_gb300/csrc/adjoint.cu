@@ -14,15 +14,14 @@
 // nodes and, except after the last sub-step of a finest step, the interface
 // rows take Eq. 5-7 values that do not depend on the mesh state.
 //
-// The transpose is taken node by node: the thread of node Q visits every row
-// P that reads Q (Q itself and the rows having Q as a neighbour) and
-// evaluates row P with forward-mode dual numbers seeded on Q's nine state
-// components and, for a neighbour entry, on that entry's three coefficients;
-// the cotangent of row P's output contracted with those derivatives gives
-// Q's cotangent and the entry's coefficient gradient.  Every output has one
-// writer, so the result is deterministic.  This is a correctness-first
-// formulation (the per-row work is repeated for each node the row reads);
-// it is not a tuned kernel.
+// The transpose of one sub-step takes two launches.  Per row P (k_adj_rows):
+// the cotangent of P's output through the node-local update gives mu =
+// dJ/d(acc) and, with the terms of acc that read P itself, P's own share
+// sig; both are forward-mode dual numbers over nine lanes.  Per node Q
+// (k_adj_gather): sig(Q) plus, over the rows that have Q as a neighbour, mu
+// contracted with the derivative of that neighbour term (Q's node-local
+// Jacobian, evaluated once), and the entry's coefficient gradient.  Every
+// output has one writer, so the result is deterministic (no atomics).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,7 +31,7 @@
 namespace hlbm {
 namespace {
 
-constexpr int kLanes = 12;  // derivative lanes: 9 state components + 3 coefficients
+constexpr int kLanes = 9;  // derivative lanes: the nine state (or increment) components
 
 struct Dual {
     double v;
@@ -128,34 +127,50 @@ __device__ __forceinline__ void load(const double *g, int Np, int k, bool seed, 
     complete(n);
 }
 
-// Row P of one sub-step (see the file comment), its nine outputs as duals.
-// seed_self: derivatives with respect to P's own state; seed_pos >= 0:
-// derivatives with respect to neighbour entry seed_pos (its state and its
-// coefficients a = dt s_x, b = dt s_y, cs = dt / tau_u C).
-__device__ void row_eval(const double *g, int Np, int P, bool seed_self, int seed_pos, const int *rp,
-                         const int *rcol, const double *rcoef, double csP, bool wall, Dual out[9])
+__device__ __forceinline__ double feqd(int i, double rho, double ux, double uy)
 {
-    Dual rP, uPx, uPy, nP[9];
-    load(g, Np, P, seed_self, rP, uPx, uPy, nP);
-    Dual eqP[9], acc[9];
-#pragma unroll
+    const double cu = kCx[i] * ux + kCy[i] * uy;
+    return kW[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy));
+}
+
+// Forward data of row P in double: its state, f^eq(P), the completed f^neq(P),
+// the increments acc_i and the sums (Sa, Sb) of its entries' (a, b).
+__device__ void row_forward(const double *g, int Np, int P, const int *rp, const int *rcol, const double *rcoef,
+                            double csP, double &r1, double &ux, double &uy, double nP[9], double eqP[9],
+                            double acc[9], double &Sa, double &Sb)
+{
+    r1 = g[P];
+    ux = g[size_t(Np) + P];
+    uy = g[size_t(2) * Np + P];
+    for (int i = 3; i < 9; i++) nP[i] = g[size_t(i) * Np + P];
+    nP[1] = nP[3] - nP[5] + nP[6] + nP[7] - nP[8];
+    nP[2] = nP[4] - nP[5] - nP[6] + nP[7] + nP[8];
+    nP[0] = -(nP[1] + nP[2] + nP[3] + nP[4] + nP[5] + nP[6] + nP[7] + nP[8]);
     for (int i = 0; i < 9; i++) {
-        eqP[i] = feq(i, rP, uPx, uPy);
-        acc[i] = cst(0.0) - csP * nP[i];
+        eqP[i] = feqd(i, 1.0 + r1, ux, uy);
+        acc[i] = -csP * nP[i];
     }
+    Sa = Sb = 0.0;
     for (int e = rp[P]; e < rp[P + 1]; e++) {
-        const bool sk = (e - rp[P]) == seed_pos;
-        Dual rk, ukx, uky, nk[9];
-        load(g, Np, rcol[e], sk, rk, ukx, uky, nk);
-        const Dual a = seeded(rcoef[3 * size_t(e)], sk ? 9 : -1);
-        const Dual b = seeded(rcoef[3 * size_t(e) + 1], sk ? 10 : -1);
-        const Dual cs = seeded(rcoef[3 * size_t(e) + 2], sk ? 11 : -1);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            const Dual S = double(kCx[i]) * a + double(kCy[i]) * b;
-            acc[i] = acc[i] + S * (feq(i, rk, ukx, uky) - eqP[i] + nk[i] - nP[i]) - cs * nk[i];
-        }
+        const int k = rcol[e];
+        const double a = rcoef[3 * size_t(e)], b = rcoef[3 * size_t(e) + 1], cs = rcoef[3 * size_t(e) + 2];
+        Sa += a;
+        Sb += b;
+        const double rk = 1.0 + g[k], ukx = g[size_t(Np) + k], uky = g[size_t(2) * Np + k];
+        double nk[9];
+        for (int i = 3; i < 9; i++) nk[i] = g[size_t(i) * Np + k];
+        nk[1] = nk[3] - nk[5] + nk[6] + nk[7] - nk[8];
+        nk[2] = nk[4] - nk[5] - nk[6] + nk[7] + nk[8];
+        nk[0] = -(nk[1] + nk[2] + nk[3] + nk[4] + nk[5] + nk[6] + nk[7] + nk[8]);
+        for (int i = 0; i < 9; i++)
+            acc[i] += (kCx[i] * a + kCy[i] * b) * (feqd(i, rk, ukx, uky) - eqP[i] + nk[i] - nP[i]) - cs * nk[i];
     }
+}
+
+// The update of row P from its increments (see the file comment).
+__device__ void epilogue(const Dual &rP, const Dual &uPx, const Dual &uPy, const Dual nP[9], const Dual eqP[9],
+                         const Dual acc[9], bool wall, Dual out[9])
+{
     Dual drho = cst(0.0), djx = cst(0.0), djy = cst(0.0);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
@@ -233,48 +248,113 @@ __global__ void k_adj_terminal(const double *g, int Np, int n, const int *wptr, 
     for (int l = 0; l < 9; l++) lam[size_t(l) * Np + Q] = d[l];
 }
 
-// One reverse sub-step: lam_in is the cotangent of the sub-step's output,
-// lam_out that of its input g.  star: interface rows are overwritten (their
-// outputs do not depend on g).  gcoef [nnz][3] accumulates dJ / d(s_x, s_y, C)
-// (unscaled, plan order) of every off-diagonal entry.
-__global__ void __launch_bounds__(128) k_fv_adjoint(const double *g, int Np, int n, const int *rp, const int *rcol,
+// Reverse sub-step, part 1 (one thread per row P).  With lam the cotangent
+// of row P's output: mu_i = dJ/d acc_i (through the update alone) and
+// sig = dJ/d(P's own state) through the update and through the terms of acc
+// that read P (-S_i (f^eq_i(P) + f^neq_i(P)) - C_PP dt/tau f^neq_i(P), S_i =
+// c_i . sum_k (a_k, b_k)).  E_i = f^eq_i(P) + f^neq_i(P) is kept for part 2.
+// Interface rows overwritten after this sub-step (star) read nothing.
+__global__ void __launch_bounds__(128) k_adj_rows(const double *g, int Np, int n, const int *rp, const int *rcol,
+                                                  const double *rcoef, double csP, int n_wall, int ring_start,
+                                                  int star, const double *lam_in, double *mu, double *sig, double *E)
+{
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P >= n) return;
+    double lam[9];
+    bool any = false;
+    for (int o = 0; o < 9; o++) {
+        lam[o] = lam_in[size_t(o) * Np + P];
+        any |= lam[o] != 0.0;
+    }
+    if (!any || (star && P >= ring_start)) {
+        for (int l = 0; l < 9; l++) {
+            mu[size_t(l) * Np + P] = 0.0;
+            sig[size_t(l) * Np + P] = 0.0;
+            E[size_t(l) * Np + P] = 0.0;
+        }
+        return;
+    }
+    const bool wall = P < n_wall;
+    double r1, ux, uy, nP[9], eqP[9], acc[9], Sa, Sb;
+    row_forward(g, Np, P, rp, rcol, rcoef, csP, r1, ux, uy, nP, eqP, acc, Sa, Sb);
+    for (int i = 0; i < 9; i++) E[size_t(i) * Np + P] = eqP[i] + nP[i];
+    {  // mu: seeds on the increments
+        Dual nPd[9], eqd[9], accd[9], out[9];
+        for (int i = 0; i < 9; i++) {
+            nPd[i] = cst(nP[i]);
+            eqd[i] = cst(eqP[i]);
+            accd[i] = seeded(acc[i], i);
+        }
+        epilogue(cst(1.0 + r1), cst(ux), cst(uy), nPd, eqd, accd, wall, out);
+        for (int l = 0; l < 9; l++) {
+            double m = 0.0;
+            for (int o = 0; o < 9; o++) m += lam[o] * out[o].d[l];
+            mu[size_t(l) * Np + P] = m;
+        }
+    }
+    {  // sig: seeds on P's state
+        Dual rPd, uxd, uyd, nPd[9], eqd[9], accd[9], out[9];
+        load(g, Np, P, true, rPd, uxd, uyd, nPd);
+        for (int i = 0; i < 9; i++) {
+            eqd[i] = feq(i, rPd, uxd, uyd);
+            const double Si = kCx[i] * Sa + kCy[i] * Sb;
+            const Dual X = cst(0.0) - Si * (eqd[i] + nPd[i]) - csP * nPd[i];
+            accd[i] = cst(acc[i]) + (X - cst(X.v));
+        }
+        epilogue(rPd, uxd, uyd, nPd, eqd, accd, wall, out);
+        for (int l = 0; l < 9; l++) {
+            double m = 0.0;
+            for (int o = 0; o < 9; o++) m += lam[o] * out[o].d[l];
+            sig[size_t(l) * Np + P] = m;
+        }
+    }
+}
+
+// Reverse sub-step, part 2 (one thread per node Q): lam_out(Q) = sig(Q) plus,
+// over the rows P having Q as neighbour entry e = (a, b, cs),
+//   sum_i mu_i(P) [(c_i . (a, b)) d(f^eq_i(Q) + f^neq_i(Q)) - cs d f^neq_i(Q)],
+// and the entry's gradient dJ/d(a, b, cs) = sum_i mu_i(P) (c_i (F_i(Q) - E_i(P)),
+// -f^neq_i(Q)), added (times dt, dt, dt/tau: the unscaled s_x, s_y, C) to
+// gcoef [nnz][3] in plan order.  One writer per output: deterministic.
+__global__ void __launch_bounds__(128) k_adj_gather(const double *g, int Np, int n, const int *rp,
                                                     const double *rcoef, const int *rcsr, const int *tp,
-                                                    const int *trow, const int *tpos, double csP, int n_wall,
-                                                    int ring_start, int star, double dt, double dt_tau,
-                                                    const double *lam_in, double *lam_out, double *gcoef)
+                                                    const int *trow, const int *tpos, int ring_start, int star,
+                                                    double dt, double dt_tau, const double *mu, const double *sig,
+                                                    const double *E, double *lam_out, double *gcoef)
 {
     const int Q = blockIdx.x * blockDim.x + threadIdx.x;
     if (Q >= n) return;
-    double d[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double d[9];
+    for (int l = 0; l < 9; l++) d[l] = sig[size_t(l) * Np + Q];
+    Dual rQ, uxQ, uyQ, nQ[9], F[9];
+    load(g, Np, Q, true, rQ, uxQ, uyQ, nQ);
+    for (int i = 0; i < 9; i++) F[i] = feq(i, rQ, uxQ, uyQ) + nQ[i];
     for (int t = tp[Q]; t < tp[Q + 1]; t++) {
         const int P = trow[t], pos = tpos[t];
-        if (star && P >= ring_start) continue;
-        double lp[9];
+        if (pos < 0 || (star && P >= ring_start)) continue;
+        double m[9];
         bool any = false;
-#pragma unroll
-        for (int o = 0; o < 9; o++) {
-            lp[o] = lam_in[size_t(o) * Np + P];
-            any |= lp[o] != 0.0;
+        for (int i = 0; i < 9; i++) {
+            m[i] = mu[size_t(i) * Np + P];
+            any |= m[i] != 0.0;
         }
         if (!any) continue;
-        Dual out[9];
-        row_eval(g, Np, P, pos < 0, pos, rp, rcol, rcoef, csP, P < n_wall, out);
-        double dc[3] = {0, 0, 0};
-#pragma unroll
-        for (int o = 0; o < 9; o++) {
-#pragma unroll
-            for (int l = 0; l < 9; l++) d[l] += lp[o] * out[o].d[l];
-#pragma unroll
-            for (int c = 0; c < 3; c++) dc[c] += lp[o] * out[o].d[9 + c];
+        const int e = rp[P] + pos;
+        const double a = rcoef[3 * size_t(e)], b = rcoef[3 * size_t(e) + 1], cs = rcoef[3 * size_t(e) + 2];
+        double ga = 0.0, gb = 0.0, gcs = 0.0;
+        for (int i = 0; i < 9; i++) {
+            const double S = kCx[i] * a + kCy[i] * b;
+            for (int l = 0; l < 9; l++) d[l] += m[i] * (S * F[i].d[l] - cs * nQ[i].d[l]);
+            const double D = F[i].v - E[size_t(i) * Np + P];
+            ga += m[i] * kCx[i] * D;
+            gb += m[i] * kCy[i] * D;
+            gcs -= m[i] * nQ[i].v;
         }
-        if (pos >= 0) {
-            double *gc = gcoef + 3 * size_t(rcsr[rp[P] + pos]);
-            gc[0] += dt * dc[0];
-            gc[1] += dt * dc[1];
-            gc[2] += dt_tau * dc[2];
-        }
+        double *gc = gcoef + 3 * size_t(rcsr[e]);
+        gc[0] += dt * ga;
+        gc[1] += dt * gb;
+        gc[2] += dt_tau * gcs;
     }
-#pragma unroll
     for (int l = 0; l < 9; l++) lam_out[size_t(l) * Np + Q] = d[l];
 }
 
@@ -500,10 +580,14 @@ void launch_adj_terminal(const AdjTables &A, const double *g, int Np, int n, dou
 
 void launch_fv_adjoint(const AdjTables &A, const double *g, int Np, int n, double csP, int n_wall, int ring_start,
                        int star, double dt, double dt_tau, const double *lam_in, double *lam_out, double *gcoef,
-                       cudaStream_t s)
+                       double *scratch, cudaStream_t s)
 {
-    k_fv_adjoint<<<(n + 127) / 128, 128, 0, s>>>(g, Np, n, A.rp, A.rcol, A.rcoef, A.rcsr, A.tp, A.trow, A.tpos, csP,
-                                                n_wall, ring_start, star, dt, dt_tau, lam_in, lam_out, gcoef);
+    double *mu = scratch, *sig = scratch + size_t(9) * Np, *E = scratch + size_t(18) * Np;
+    const int blocks = (n + 127) / 128;
+    k_adj_rows<<<blocks, 128, 0, s>>>(g, Np, n, A.rp, A.rcol, A.rcoef, csP, n_wall, ring_start, star, lam_in, mu, sig,
+                                      E);
+    k_adj_gather<<<blocks, 128, 0, s>>>(g, Np, n, A.rp, A.rcoef, A.rcsr, A.tp, A.trow, A.tpos, ring_start, star, dt,
+                                        dt_tau, mu, sig, E, lam_out, gcoef);
 }
 
 void launch_adj_populations(const AdjTables &A, const double *g, int Np, int n, const double *lam, double *grad,

@@ -1246,6 +1246,7 @@ int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, 
         const AdjTables &A = c->adj;
         double *st = (double *)scr((size_t(M) + 1) * plane * sizeof(double));  // states g_0 .. g_M
         double *lam = (double *)scr(2 * plane * sizeof(double));
+        double *rs = (double *)scr(3 * plane * sizeof(double));  // reverse sub-step scratch
         double *gc = (double *)scr(std::max<size_t>(1, 3 * P.col.size()) * sizeof(double));
         double *gg = (double *)scr(9 * size_t(n) * sizeof(double));
         double *dJ = (double *)scr(2 * sizeof(double));  // J, dJ/d(angle of attack)
@@ -1277,7 +1278,7 @@ int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, 
             const double *lin = lam + size_t((M - 1 - m) & 1) * plane;
             double *lout = lam + size_t((M - m) & 1) * plane;
             launch_fv_adjoint(A, st + size_t(m) * plane, Np, n, csP, P.n_wall, P.ring_start,
-                              m < P.n_sub - 1 ? 1 : 0, dt, dt_tau, lin, lout, gc, s);
+                              m < P.n_sub - 1 ? 1 : 0, dt, dt_tau, lin, lout, gc, rs, s);
         }
         const double *lam0 = lam + size_t(M & 1) * plane;
         launch_adj_populations(A, st, Np, n, lam0, gg, s);

@@ -146,9 +146,10 @@ void launch_adj_value(const AdjTables &, const double *g, int Np, double wd, dou
                       cudaStream_t);
 void launch_adj_terminal(const AdjTables &, const double *g, int Np, int n, double wd, double wl, double inv_q,
                          double *lam, cudaStream_t);
+// scratch: 27 Np doubles (per-row mu, sig, E of the reverse sub-step)
 void launch_fv_adjoint(const AdjTables &, const double *g, int Np, int n, double csP, int n_wall, int ring_start,
                        int star, double dt, double dt_tau, const double *lam_in, double *lam_out, double *gcoef,
-                       cudaStream_t);
+                       double *scratch, cudaStream_t);
 void launch_adj_populations(const AdjTables &, const double *g, int Np, int n, const double *lam, double *grad,
                             cudaStream_t);
 // dJ/d(node coordinates) from the operator-entry gradient gc ([nnz][3], plan

@@ -162,7 +162,29 @@ def run_cpu_baseline(case, coarse_steps=1):
     fv = float(case.n_nodes) * o.n_sub * 2 ** (case.n_levels - 1)
     return {"value": (lat + fv) * coarse_steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"{coarse_steps} coarse step(s) of the {WORKLOAD} workload, FP64, single thread "
-                      f"(set-up {t_setup:.1f} s not timed)", "seconds": dt}
+                      f"(set-up {t_setup:.1f} s not timed)", "seconds": dt,
+            "host_cores_available": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None,
+            "cpu_model": _cpu_model()}
+
+
+def _cpu_model():
+    """The host CPU's name (from /proc/cpuinfo), or the machine type."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if ":" in line:
+                    key, val = line.split(":", 1)
+                    fields.setdefault(key.strip().lower(), val.strip())
+    except OSError:
+        pass
+    for key in ("model name", "cpu model", "hardware"):
+        if key in fields:
+            return fields[key]
+    if "cpu part" in fields:  # Arm: implementer and part numbers
+        return f"{platform.machine()} (implementer {fields.get('cpu implementer', '?')}, part {fields['cpu part']})"
+    return platform.machine()
 
 
 def reference_arm(args):

@@ -78,6 +78,7 @@ def lib():
                                               C.c_double, C.c_void_p, C.c_void_p]
         L.hlbm_fv_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, dp, dp, C.c_size_t, dp,
                                       C.c_size_t, dp, C.c_size_t, dp]
+        L.hlbm_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, dp, dp, C.c_size_t, dp, C.c_size_t]
         L.hlbm_sync.argtypes = [C.c_void_p]
         L.hlbm_destroy.argtypes = [C.c_void_p]
         L.hlbm_last_error.argtypes = [C.c_void_p]
@@ -210,6 +211,19 @@ class Solver:
                                          gg.ctypes.data_as(dp), gg.size, gc.ctypes.data_as(dp), gc.size,
                                          gx.ctypes.data_as(dp), gx.size, da.ctypes.data_as(dp)), self.ctx)
         return float(J[0]), gg, gc, gx, float(da[0])
+
+    def adjoint(self, n_steps, wd=1.0, wl=0.0):
+        """Discrete adjoint of n_steps coarse steps of a single-level FP64
+        solver (hlbm_adjoint): J = mean of wd C_D + wl C_L over the steps,
+        dJ/d(lattice populations) [ny * nx, 9] and dJ/d(mesh populations)
+        [n_nodes, 9] of the current state; the state is not changed."""
+        nx, ny = (int(v) for v in self.case.levels[0][:2])
+        J = np.zeros(1)
+        gl, gm = np.empty((nx * ny, 9)), np.empty((self.case.n_nodes, 9))
+        dp = C.POINTER(C.c_double)
+        _check(self._lib.hlbm_adjoint(self.ctx, int(n_steps), float(wd), float(wl), J.ctypes.data_as(dp),
+                                      gl.ctypes.data_as(dp), gl.size, gm.ctypes.data_as(dp), gm.size), self.ctx)
+        return float(J[0]), gl, gm
 
     def save(self, path):
         """Checkpoint of the whole evolving state (hlbm_save)."""

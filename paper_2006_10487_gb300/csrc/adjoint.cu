@@ -231,9 +231,10 @@ __global__ void __launch_bounds__(256) k_adj_value(const double *g, int Np, cons
 }
 
 // cotangent of the final state: dJ/dq on wall nodes (through their edges),
-// zero elsewhere
+// zero elsewhere; added to lam when add is set
 __global__ void k_adj_terminal(const double *g, int Np, int n, const int *wptr, const int *wedge, const int *wea,
-                               const int *web, const double *wn, double wd, double wl, double inv_q, double *lam)
+                               const int *web, const double *wn, double wd, double wl, double inv_q, int add,
+                               double *lam)
 {
     const int Q = blockIdx.x * blockDim.x + threadIdx.x;
     if (Q >= n) return;
@@ -245,7 +246,7 @@ __global__ void k_adj_terminal(const double *g, int Np, int n, const int *wptr, 
         for (int l = 0; l < 9; l++) d[l] += f.d[l];
     }
 #pragma unroll
-    for (int l = 0; l < 9; l++) lam[size_t(l) * Np + Q] = d[l];
+    for (int l = 0; l < 9; l++) lam[size_t(l) * Np + Q] = (add ? lam[size_t(l) * Np + Q] : 0.0) + d[l];
 }
 
 // Reverse sub-step, part 1 (one thread per row P).  With lam the cotangent
@@ -550,6 +551,257 @@ __global__ void __launch_bounds__(256) k_adj_aoa(const double *xy, const double 
     if (threadIdx.x == 0) *out = part[0] * (3.14159265358979323846 / 180.0);
 }
 
+// ------------------------------------ lattice side of a coupled step ----
+// Single-level configurations: the lattice (deviations d_i = f_i - w_i,
+// FP64, AA layout) and the mesh exchange through Eq. 4 + 8 (hole nodes from
+// mesh donors) and Eq. 9 (interface data Q from lattice donors).  Cotangents
+// of the lattice live in the same slots as its state: lam[slot] = dJ/d(value
+// in that slot).  Every forward kernel reads and writes whole slot sets of
+// single nodes, so each adjoint below reads the cotangents of the slots a
+// node wrote and writes (or adds) those of the slots it read, one writer per
+// slot.  AA addressing, node n at parity p: state of direction i in plane i
+// at n (p = 0) or plane opp(i) at n - c_i (p = 1); a collision writes
+// direction i to plane opp(i) at n (p = 0) or plane i at n + c_i (p = 1).
+__constant__ int kOpp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+__device__ __forceinline__ size_t lnode(int x, int y, int pitch) { return size_t(y + 1) * pitch + x + 1; }
+template <int P> __device__ __forceinline__ size_t lst(int i, size_t n, int pitch, size_t stride)
+{
+    if (P == 0) return size_t(i) * stride + n;
+    return size_t(kOpp[i]) * stride + n - kCx[i] - ptrdiff_t(kCy[i]) * pitch;
+}
+template <int P> __device__ __forceinline__ size_t lwr(int i, size_t n, int pitch, size_t stride)
+{
+    if (P == 0) return size_t(kOpp[i]) * stride + n;
+    return size_t(i) * stride + n + kCx[i] + ptrdiff_t(kCy[i]) * pitch;
+}
+
+// populations of node n (slots at parity P) as duals seeded on lanes 0..8
+template <int P>
+__device__ __forceinline__ void lat_load(const double *f, size_t n, int pitch, size_t stride, Dual F[9], Dual &rho,
+                                         Dual &ux, Dual &uy)
+{
+    rho = cst(0.0);
+    Dual jx = cst(0.0), jy = cst(0.0);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        F[i] = seeded(f[lst<P>(i, n, pitch, stride)] + kW[i], i);
+        rho = rho + F[i];
+        jx = jx + double(kCx[i]) * F[i];
+        jy = jy + double(kCy[i]) * F[i];
+    }
+    ux = jx / rho;
+    uy = jy / rho;
+}
+
+// Eq. 1 (BGK collision at parity P, every computed node): the state before the
+// collision f, cotangents of the written slots -> those of the read slots
+// (the same slot set, in place).
+template <int P>
+__global__ void __launch_bounds__(128) k_adj_collide(const double *f, int nx, int ny, int pitch, size_t stride,
+                                                     double omega, const int *hx0, const int *hx1, double *lam)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    if (hx0 && x >= hx0[y] && x < hx1[y]) return;
+    const size_t n = lnode(x, y, pitch);
+    Dual F[9], rho, ux, uy;
+    lat_load<P>(f, n, pitch, stride, F, rho, ux, uy);
+    double lp[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) lp[i] = lam[lwr<P>(i, n, pitch, stride)];
+    double d[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const Dual post = F[i] - omega * (F[i] - feq(i, rho, ux, uy));
+#pragma unroll
+        for (int l = 0; l < 9; l++) d[l] += lp[i] * post.d[l];
+    }
+#pragma unroll
+    for (int l = 0; l < 9; l++) lam[lst<P>(l, n, pitch, stride)] = d[l];
+}
+
+// Outer conditions (level 0, parity P, after the collision): perimeter node
+// (x, y) takes the state of interior node (clamp x, clamp y): inlet x = 0
+// f^eq(rho, (u0, 0)) + f^neq, outlet x = nx - 1 f^eq(1, u) + f^neq, else a
+// copy.  Part 1, per interior frame node T: add the perimeter nodes' share.
+template <int P>
+__global__ void __launch_bounds__(128) k_adj_bc_gather(const double *f, int nx, int ny, int pitch, size_t stride,
+                                                       double u0, double *lam)
+{
+    const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y + 1;
+    if (X < 1 || X > nx - 2 || Y > ny - 2) return;
+    if (X != 1 && X != nx - 2 && Y != 1 && Y != ny - 2) return;  // not on the inner frame
+    const size_t nT = lnode(X, Y, pitch);
+    Dual F[9], rho, ux, uy;
+    lat_load<P>(f, nT, pitch, stride, F, rho, ux, uy);
+    double d[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const int xs[3] = {X, X == 1 ? 0 : -1, X == nx - 2 ? nx - 1 : -1};
+    const int ys[3] = {Y, Y == 1 ? 0 : -1, Y == ny - 2 ? ny - 1 : -1};
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            const int x = xs[a], y = ys[b];
+            if (x < 0 || y < 0 || (a == 0 && b == 0)) continue;
+            const size_t np = lnode(x, y, pitch);
+            for (int i = 0; i < 9; i++) {
+                const double lp = lam[lst<P>(i, np, pitch, stride)];
+                if (lp == 0.0) continue;
+                Dual out;
+                if (x == 0) out = feq(i, rho, cst(u0), cst(0.0)) + F[i] - feq(i, rho, ux, uy);
+                else if (x == nx - 1) out = feq(i, cst(1.0), ux, uy) + F[i] - feq(i, rho, ux, uy);
+                else out = F[i];
+                for (int l = 0; l < 9; l++) d[l] += lp * out.d[l];
+            }
+        }
+#pragma unroll
+    for (int l = 0; l < 9; l++) lam[lst<P>(l, nT, pitch, stride)] += d[l];
+}
+
+// Part 2: the perimeter slots were overwritten: their cotangents end here.
+template <int P>
+__global__ void k_adj_bc_clear(int nx, int ny, int pitch, size_t stride, double *lam)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nper = 2 * nx + 2 * (ny - 2);
+    if (k >= nper) return;
+    int x, y;
+    if (k < nx) { x = k; y = 0; }
+    else if (k < 2 * nx) { x = k - nx; y = ny - 1; }
+    else if (k < 2 * nx + ny - 2) { x = 0; y = k - 2 * nx + 1; }
+    else { x = nx - 1; y = k - 2 * nx - (ny - 2) + 1; }
+    const size_t n = lnode(x, y, pitch);
+#pragma unroll
+    for (int i = 0; i < 9; i++) lam[lst<P>(i, n, pitch, stride)] = 0.0;
+}
+
+// Eq. 9 (interface data Q[12][n_ring] = sum_k w_rk (rho, u, f - f^eq) of
+// lattice donor k at parity P): cotangents lamQ -> the donors' slots.  Per
+// lattice node: the (ring node, donor position) pairs that read it,
+// lent[lptr[node] .. lptr[node + 1]) as 9 r + k, node = y nx + x.
+template <int P>
+__global__ void __launch_bounds__(128) k_adj_ring_lattice(const double *f, int nx, int ny, int pitch, size_t stride,
+                                                          const int *lptr, const int *lent, const double *ring_w,
+                                                          const double *lamQ, int n_ring, double *lam)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    const int node = y * nx + x;
+    if (lptr[node] == lptr[node + 1]) return;
+    const size_t n = lnode(x, y, pitch);
+    Dual F[9], rho, ux, uy;
+    lat_load<P>(f, n, pitch, stride, F, rho, ux, uy);
+    Dual q[12];
+    q[0] = rho;
+    q[1] = ux;
+    q[2] = uy;
+#pragma unroll
+    for (int i = 0; i < 9; i++) q[3 + i] = F[i] - feq(i, rho, ux, uy);
+    double d[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = lptr[node]; t < lptr[node + 1]; t++) {
+        const int r = lent[t] / 9;
+        const double w = ring_w[lent[t]];
+        for (int m = 0; m < 12; m++) {
+            const double lq = w * lamQ[size_t(m) * n_ring + r];
+#pragma unroll
+            for (int l = 0; l < 9; l++) d[l] += lq * q[m].d[l];
+        }
+    }
+#pragma unroll
+    for (int l = 0; l < 9; l++) lam[lst<P>(l, n, pitch, stride)] += d[l];
+}
+
+// Eq. 4 + 8, part 1 (per structured interpolation node s at parity P): the
+// node's written slots held f^eq(q) + scale4 f^neq(q) with q = sum_k w_sk q(mesh
+// donor k) (mesh state g); their cotangents -> lamq[12][n_is], and end there.
+template <int P>
+__global__ void k_adj_hole_q(const double *g, int Np, const int *is_n, const int *is_don, const double *is_w,
+                             int n_is, double scale4, int pitch, size_t stride, double *lam, double *lamq)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_is) return;
+    double q[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 6; k++) {
+        const int p = is_don[6 * s + k];
+        const double w = is_w[6 * s + k];
+        Dual r, ux, uy, nq[9];
+        load(g, Np, p, false, r, ux, uy, nq);
+        q[0] += w * r.v;
+        q[1] += w * ux.v;
+        q[2] += w * uy.v;
+        for (int i = 0; i < 9; i++) q[3 + i] += w * nq[i].v;
+    }
+    const size_t n = size_t(is_n[s]);
+    const Dual rho = seeded(q[0], 0), vx = seeded(q[1], 1), vy = seeded(q[2], 2);
+    double lq[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 9; i++) {
+        const size_t slot = lwr<P>(i, n, pitch, stride);
+        const double lo = lam[slot];
+        lam[slot] = 0.0;
+        const Dual e = feq(i, rho, vx, vy);
+        lq[0] += lo * e.d[0];
+        lq[1] += lo * e.d[1];
+        lq[2] += lo * e.d[2];
+        lq[3 + i] = scale4 * lo;
+    }
+    for (int m = 0; m < 12; m++) lamq[size_t(m) * n_is + s] = lq[m];
+}
+
+// Part 2 (per mesh node): q(mesh node) = (1 + r1, u, f^neq_0..8), the last
+// three of f^neq completed from the stored six; pairs (s, k) that read the
+// node: hent[hptr[node] .. hptr[node + 1]) as 6 s + k.
+__global__ void k_adj_hole_mesh(const double *g, int Np, int n, const int *hptr, const int *hent, const double *is_w,
+                                const double *lamq, int n_is, double *lam_g)
+{
+    const int Q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (Q >= n || hptr[Q] == hptr[Q + 1]) return;
+    Dual r, ux, uy, nq[9];
+    load(g, Np, Q, true, r, ux, uy, nq);
+    double d[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = hptr[Q]; t < hptr[Q + 1]; t++) {
+        const int s = hent[t] / 6;
+        const double w = is_w[hent[t]];
+        for (int m = 0; m < 12; m++) {
+            const double lq = w * lamq[size_t(m) * n_is + s];
+            const Dual &qm = m == 0 ? r : (m == 1 ? ux : (m == 2 ? uy : nq[m - 3]));
+            for (int l = 0; l < 9; l++) d[l] += lq * qm.d[l];
+        }
+    }
+    for (int l = 0; l < 9; l++) lam_g[size_t(l) * Np + Q] += d[l];
+}
+
+// Interface rows of a mesh state set from Q = (1 - theta) Q0 + theta Q1
+// (Eq. 5-7: rho - 1 = Q_rho - 1, u = Q_u, f^neq_i = scale5 Q_neq,i): their
+// cotangents -> lamQ0 (weight wa), lamQ1 (weight wb), and end there.
+__global__ void k_adj_ring_rows(double *lam_g, int Np, int ring_start, int n_ring, double scale5, double wa,
+                                double wb, double *lamQ0, double *lamQ1)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_ring) return;
+    const int R = ring_start + r;
+    for (int k = 0; k < 9; k++) {
+        const double l = lam_g[size_t(k) * Np + R];
+        lam_g[size_t(k) * Np + R] = 0.0;
+        const int m = k < 3 ? k : 3 + k;  // Q component of mesh plane k
+        const double v = k < 3 ? l : scale5 * l;
+        lamQ0[size_t(m) * n_ring + r] += wa * v;
+        lamQ1[size_t(m) * n_ring + r] += wb * v;
+    }
+}
+
+// dJ/d(lattice populations), grid order [ny nx][9], from the cotangents of
+// the slots at parity P; hole nodes (not computed) get 0.
+template <int P>
+__global__ void k_adj_lattice_out(const double *lam, int nx, int ny, int pitch, size_t stride, const int *hx0,
+                                  const int *hx1, double *grad)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    const bool hole = hx0 && x >= hx0[y] && x < hx1[y];
+    const size_t n = lnode(x, y, pitch);
+    for (int i = 0; i < 9; i++)
+        grad[9 * (size_t(y) * nx + x) + i] = hole ? 0.0 : lam[lst<P>(i, n, pitch, stride)];
+}
+
 }  // namespace
 
 void launch_adj_geometry(const AdjTables &A, int n, const double *gc, const double *gM, int Np, double wd, double wl,
@@ -572,10 +824,10 @@ void launch_adj_value(const AdjTables &A, const double *g, int Np, double wd, do
 }
 
 void launch_adj_terminal(const AdjTables &A, const double *g, int Np, int n, double wd, double wl, double inv_q,
-                         double *lam, cudaStream_t s)
+                         double *lam, cudaStream_t s, bool add)
 {
     k_adj_terminal<<<(n + 127) / 128, 128, 0, s>>>(g, Np, n, A.wptr, A.wedge, A.wea, A.web, A.wn, wd, wl, inv_q,
-                                                  lam);
+                                                  add ? 1 : 0, lam);
 }
 
 void launch_fv_adjoint(const AdjTables &A, const double *g, int Np, int n, double csP, int n_wall, int ring_start,
@@ -594,6 +846,74 @@ void launch_adj_populations(const AdjTables &A, const double *g, int Np, int n, 
                             cudaStream_t s)
 {
     k_adj_populations<<<(n + 127) / 128, 128, 0, s>>>(g, Np, n, A.perm, lam, grad);
+}
+
+}  // namespace hlbm
+
+namespace hlbm {
+
+void launch_adj_collide(const DevLevel &l, const double *f, int P, double *lam, cudaStream_t s)
+{
+    const dim3 grid((l.nx + 127) / 128, l.ny);
+    const double omega = 1.0 / l.tau;
+    if (P == 0) k_adj_collide<0><<<grid, 128, 0, s>>>(f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0, l.hx1, lam);
+    else k_adj_collide<1><<<grid, 128, 0, s>>>(f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0, l.hx1, lam);
+}
+
+void launch_adj_outer_bc(const DevLevel &l, const double *f, int P, double u0, double *lam, cudaStream_t s)
+{
+    const dim3 grid((l.nx + 127) / 128, l.ny - 2);
+    const int nper = 2 * l.nx + 2 * (l.ny - 2);
+    if (P == 0) {
+        k_adj_bc_gather<0><<<grid, 128, 0, s>>>(f, l.nx, l.ny, l.pitch, l.stride, u0, lam);
+        k_adj_bc_clear<0><<<(nper + 127) / 128, 128, 0, s>>>(l.nx, l.ny, l.pitch, l.stride, lam);
+    } else {
+        k_adj_bc_gather<1><<<grid, 128, 0, s>>>(f, l.nx, l.ny, l.pitch, l.stride, u0, lam);
+        k_adj_bc_clear<1><<<(nper + 127) / 128, 128, 0, s>>>(l.nx, l.ny, l.pitch, l.stride, lam);
+    }
+}
+
+void launch_adj_ring_lattice(const DevLevel &l, const double *f, int P, const AdjTables &A, const double *ring_w,
+                             const double *lamQ, int n_ring, double *lam, cudaStream_t s)
+{
+    const dim3 grid((l.nx + 127) / 128, l.ny);
+    if (P == 0)
+        k_adj_ring_lattice<0><<<grid, 128, 0, s>>>(f, l.nx, l.ny, l.pitch, l.stride, A.lptr, A.lent, ring_w, lamQ,
+                                                  n_ring, lam);
+    else
+        k_adj_ring_lattice<1><<<grid, 128, 0, s>>>(f, l.nx, l.ny, l.pitch, l.stride, A.lptr, A.lent, ring_w, lamQ,
+                                                  n_ring, lam);
+}
+
+void launch_adj_hole(const DevLevel &l, const DevMesh &m, const AdjTables &A, const double *g, int P, double *lam,
+                     double *lamq, double *lam_g, cudaStream_t s)
+{
+    if (m.n_is == 0) return;
+    const double scale4 = 2.0 * (l.tau - 1.0) / (2.0 * l.tau - 1.0);
+    const int b = (m.n_is + 127) / 128;
+    if (P == 0)
+        k_adj_hole_q<0><<<b, 128, 0, s>>>(g, m.Np, m.is_n, m.is_don, (const double *)m.is_w, m.n_is, scale4, l.pitch,
+                                          l.stride, lam, lamq);
+    else
+        k_adj_hole_q<1><<<b, 128, 0, s>>>(g, m.Np, m.is_n, m.is_don, (const double *)m.is_w, m.n_is, scale4, l.pitch,
+                                          l.stride, lam, lamq);
+    k_adj_hole_mesh<<<(m.n + 127) / 128, 128, 0, s>>>(g, m.Np, m.n, A.hptr, A.hent, (const double *)m.is_w, lamq,
+                                                      m.n_is, lam_g);
+}
+
+void launch_adj_ring_rows(const DevMesh &m, double scale5, double wa, double wb, double *lam_g, double *lamQ0,
+                          double *lamQ1, cudaStream_t s)
+{
+    if (m.n_ring == 0) return;
+    k_adj_ring_rows<<<(m.n_ring + 127) / 128, 128, 0, s>>>(lam_g, m.Np, m.ring_start, m.n_ring, scale5, wa, wb,
+                                                          lamQ0, lamQ1);
+}
+
+void launch_adj_lattice_out(const DevLevel &l, const double *lam, int P, double *grad, cudaStream_t s)
+{
+    const dim3 grid((l.nx + 127) / 128, l.ny);
+    if (P == 0) k_adj_lattice_out<0><<<grid, 128, 0, s>>>(lam, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, grad);
+    else k_adj_lattice_out<1><<<grid, 128, 0, s>>>(lam, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, grad);
 }
 
 }  // namespace hlbm

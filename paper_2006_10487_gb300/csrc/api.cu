@@ -1213,6 +1213,35 @@ void build_adjoint_tables(hlbm_ctx *c)
     A.built = true;
 }
 
+// Tables of the coupled-step adjoint (single level): Eq. 9 and Eq. 8 donor
+// pairs transposed to the donors.
+void build_coupled_tables(hlbm_ctx *c)
+{
+    const Plan &P = c->plan;
+    AdjTables &A = c->adj;
+    const LevelPlan &F = P.lv[P.L - 1];
+    const size_t nl = size_t(F.nx) * F.ny;
+    std::vector<int> lptr(nl + 1, 0), lent(P.ring_don.size());
+    for (int d : P.ring_don) lptr[size_t(d) + 1]++;
+    for (size_t k = 0; k < nl; k++) lptr[k + 1] += lptr[k];
+    {
+        std::vector<int> f(lptr.begin(), lptr.end() - 1);
+        for (size_t t = 0; t < P.ring_don.size(); t++) lent[f[P.ring_don[t]]++] = int(t);
+    }
+    std::vector<int> hptr(size_t(P.n) + 1, 0), hent(P.is_don.size());
+    for (int d : P.is_don) hptr[P.inv[d] + 1]++;
+    for (int k = 0; k < P.n; k++) hptr[k + 1] += hptr[k];
+    {
+        std::vector<int> f(hptr.begin(), hptr.end() - 1);
+        for (size_t t = 0; t < P.is_don.size(); t++) hent[f[P.inv[P.is_don[t]]]++] = int(t);
+    }
+    A.lptr = upload(c, lptr);
+    A.lent = upload(c, lent);
+    A.hptr = upload(c, hptr);
+    A.hent = upload(c, hent);
+    A.coupled_built = true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1303,6 +1332,168 @@ int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, 
     } catch (const std::bad_alloc &) {
         rc = fail(c, HLBM_ENOMEM, "host allocation failed");
     }
+    for (void *p : scratch) dfree(c, p);
+    return rc;
+}
+
+int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, double *grad_lattice, size_t cap_lat,
+                 double *grad_mesh, size_t cap_mesh)
+{
+    if (!c) return HLBM_EINVAL;
+    const Plan &P = c->plan;
+    if (P.precision != HLBM_FP64) return fail(c, HLBM_ENOTIMPL, "the adjoint runs on FP64 contexts");
+    if (P.L != 1) return fail(c, HLBM_ENOTIMPL, "the coupled-step adjoint covers single-level configurations");
+    if (P.n == 0) return fail(c, HLBM_EINVAL, "the context has no mesh");
+    if (n_steps < 1) return fail(c, HLBM_EINVAL, "n_steps must be >= 1");
+    if (!J) return fail(c, HLBM_EINVAL, "J is NULL");
+    const LevelPlan &F = P.lv[0];
+    if (grad_lattice && cap_lat < 9 * size_t(F.nx) * F.ny) return fail(c, HLBM_EINVAL, "grad_lattice capacity below 9 nx ny");
+    if (grad_mesh && cap_mesh < 9 * size_t(P.n)) return fail(c, HLBM_EINVAL, "grad_mesh capacity below 9 n");
+    if (c->timing_dirty) return fail(c, HLBM_ESTATE, "the state was consumed by hlbm_time_kernel");
+    Range r("hlbm_adjoint");
+    const int K = n_steps, n = P.n, ns = P.n_sub;
+    const long k0 = c->steps;
+    std::vector<void *> scratch;
+    auto scr = [&](size_t bytes) {
+        void *p = dalloc(c, bytes);
+        scratch.push_back(p);
+        return (double *)p;
+    };
+    int rc = HLBM_OK;
+    const DevCtx D0 = c->dev;
+    const long launches0 = c->launches, lps0 = c->launches_per_step;
+    try {
+        if (!c->adj.built) build_adjoint_tables(c);
+        if (!c->adj.coupled_built) build_coupled_tables(c);
+        const AdjTables &A = c->adj;
+        cudaStream_t s = c->stream;
+        const DevLevel &L0 = D0.lv[0];
+        const int Np = D0.m.Np, nr = std::max(1, D0.m.n_ring);
+        const size_t lat = 9 * L0.stride, plane = size_t(9) * Np, qn = size_t(12) * nr;
+        auto copy = [&](void *dst, const void *src, size_t doubles) {
+            ck(cudaMemcpyAsync(dst, src, doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+        };
+        // ---- forward on scratch copies of the state, checkpoints at every coarse step
+        std::vector<double *> fck(K + 1), gck(K), Qd(K + 1);
+        for (int k = 0; k <= K; k++) fck[k] = scr(lat * sizeof(double));
+        for (int k = 0; k < K; k++) gck[k] = scr(plane * sizeof(double));
+        for (int k = 0; k <= K; k++) Qd[k] = scr(qn * sizeof(double));
+        DevCtx W = D0;
+        W.lv[0].f = scr(lat * sizeof(double));
+        copy(W.lv[0].f, L0.f, lat);
+        for (int b = 0; b < 2; b++) {
+            W.m.g[b] = scr(plane * sizeof(double));
+            copy(W.m.g[b], D0.m.g[b], plane);
+            W.m.Qb[b] = scr(qn * sizeof(double));
+            copy(W.m.Qb[b], D0.m.Qb[b], qn);
+        }
+        W.force_cap = K;
+        W.force_buf = scr(2 * size_t(K) * sizeof(double));
+        W.force_partial = scr(2 * size_t(std::max(1, (D0.m.n_edges + 127) / 128)) * sizeof(double));
+        W.force_counter = (int *)scr(2 * sizeof(int));
+        W.flag = W.force_counter + 1;
+        ck(cudaMemsetAsync(W.force_counter, 0, 2 * sizeof(int), s), "memset");
+        W.m.wall_stats = 0;
+        for (int k = 0; k <= K; k++) {
+            std::swap(c->dev, W);
+            set_phase(c, k0 + k);
+            std::swap(c->dev, W);
+            copy(fck[k], W.lv[0].f, lat);
+            copy(Qd[k], W.m.Q0, qn);
+            if (k == K) break;
+            copy(gck[k], W.m.g[W.m.gcur], plane);
+            std::swap(c->dev, W);
+            try {
+                coarse_step<double, double>(c, s);
+            } catch (...) {
+                std::swap(c->dev, W);
+                throw;
+            }
+            std::swap(c->dev, W);
+        }
+        ck(cudaGetLastError(), "forward steps");
+        std::vector<double> fb(2 * size_t(K));
+        ck(cudaMemcpyAsync(fb.data(), W.force_buf, fb.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        // ---- reverse sweep
+        double *lam_f = scr(lat * sizeof(double));
+        double *lam_g = scr(plane * sizeof(double)), *lam_t = scr(plane * sizeof(double));
+        double *lQ0 = scr(qn * sizeof(double)), *lQ1 = scr(qn * sizeof(double)), *qtmp = scr(qn * sizeof(double));
+        double *lamq = scr(12 * size_t(std::max(1, D0.m.n_is)) * sizeof(double));
+        double *st = scr((size_t(ns) + 1) * plane * sizeof(double));
+        double *gc = scr(std::max<size_t>(1, 3 * P.col.size()) * sizeof(double));
+        double *rs = scr(3 * plane * sizeof(double));
+        double *gg = scr(9 * size_t(n) * sizeof(double));
+        double *gl = grad_lattice ? scr(9 * size_t(F.nx) * F.ny * sizeof(double)) : nullptr;
+        ck(cudaMemsetAsync(lam_f, 0, lat * sizeof(double), s), "memset");
+        ck(cudaMemsetAsync(lam_g, 0, plane * sizeof(double), s), "memset");
+        ck(cudaMemsetAsync(st, 0, (size_t(ns) + 1) * plane * sizeof(double), s), "memset");
+        ck(cudaMemsetAsync(lQ0, 0, qn * sizeof(double), s), "memset");
+        ck(cudaMemsetAsync(lQ1, 0, qn * sizeof(double), s), "memset");
+        const double inv_q = 1.0 / P.qdyn, dt = 1.0 / ns, dt_tau = dt / P.tau_u, csP = dt_tau * (11.0 / 18.0);
+        const double scale5 = 1.0 - 1.0 / (2.0 * L0.tau);
+        const double *ring_w = (const double *)D0.m.ring_w;
+        for (int k = K - 1; k >= 0; k--) {
+            const int Pk = int((k0 + k) & 1);
+            // the finite-volume group of step k again, from its checkpoint
+            DevCtx V = W;
+            V.lv[0].f = fck[k + 1];
+            V.lv[0].parity = Pk ^ 1;
+            V.m.Q0 = Qd[k];
+            V.m.Q1 = qtmp;
+            copy(st, gck[k], plane);
+            V.m.g[0] = st;
+            V.m.gcur = 0;
+            launch_ring_interp<double, double>(V, true, s);  // interface rows at theta = 0
+            V.m.Q1 = Qd[k + 1];
+            for (int m = 0; m < ns; m++) {
+                V.m.g[0] = st + size_t(m) * plane;
+                V.m.g[1] = st + size_t(m + 1) * plane;
+                launch_fv<double, double>(V, m, s);
+            }
+            // force sample of step k, then the sub-steps backwards
+            launch_adj_terminal(A, st + size_t(ns) * plane, Np, n, wd / K, wl / K, inv_q, lam_g, s, true);
+            double *lin = lam_g, *lout = lam_t;
+            for (int m = ns - 1; m >= 0; m--) {
+                const double th = double(m + 1) / ns;
+                if (m < ns - 1) launch_adj_ring_rows(D0.m, scale5, 1.0 - th, th, lin, lQ0, lQ1, s);
+                launch_fv_adjoint(A, st + size_t(m) * plane, Np, n, csP, P.n_wall, P.ring_start, m < ns - 1 ? 1 : 0,
+                                  dt, dt_tau, lin, lout, gc, rs, s);
+                std::swap(lin, lout);
+            }
+            launch_adj_ring_rows(D0.m, scale5, 1.0, 0.0, lin, lQ0, lQ1, s);
+            if (lin != lam_g) std::swap(lam_g, lam_t);  // lam_g: cotangent of the step's initial mesh state
+            // lattice side, in reverse order of the forward step
+            launch_adj_ring_lattice(L0, fck[k + 1], Pk ^ 1, A, ring_w, lQ1, D0.m.n_ring, lam_f, s);
+            launch_adj_outer_bc(L0, fck[k + 1], Pk ^ 1, P.u0, lam_f, s);
+            launch_adj_collide(L0, fck[k], Pk, lam_f, s);
+            launch_adj_hole(L0, D0.m, A, gck[k], Pk, lam_f, lamq, lam_g, s);
+            launch_adj_ring_lattice(L0, fck[k], Pk, A, ring_w, lQ0, D0.m.n_ring, lam_f, s);
+            ck(cudaMemsetAsync(lQ0, 0, qn * sizeof(double), s), "memset");
+            ck(cudaMemsetAsync(lQ1, 0, qn * sizeof(double), s), "memset");
+        }
+        if (gl) launch_adj_lattice_out(L0, lam_f, int(k0 & 1), gl, s);
+        launch_adj_populations(A, gck[0], Np, n, lam_g, gg, s);
+        ck(cudaGetLastError(), "adjoint kernels");
+        if (gl)
+            ck(cudaMemcpyAsync(grad_lattice, gl, 9 * size_t(F.nx) * F.ny * sizeof(double), cudaMemcpyDeviceToHost, s),
+               "D2H");
+        if (grad_mesh) ck(cudaMemcpyAsync(grad_mesh, gg, 9 * size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        int flag = 0;
+        ck(cudaMemcpyAsync(&flag, W.flag, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
+        ck(cudaStreamSynchronize(s), "sync");
+        double j = 0.0;
+        for (int k = 0; k < K; k++) j += wd * fb[2 * size_t(k)] + wl * fb[2 * size_t(k) + 1];
+        *J = j / K;
+        if (flag & 2) rc = fail(c, HLBM_ETIMEOUT, "a device-side wait gave up (operator copy did not arrive)");
+        else if (flag) rc = fail(c, HLBM_EUNSTABLE, "NaN in the force reduction of the forward steps");
+    } catch (const CudaError &e) {
+        rc = fail(c, HLBM_ECUDA, e.msg);
+    } catch (const std::bad_alloc &) {
+        rc = fail(c, HLBM_ENOMEM, "host allocation failed");
+    }
+    c->dev = D0;
+    c->launches = launches0;
+    c->launches_per_step = lps0;
     for (void *p : scratch) dfree(c, p);
     return rc;
 }

@@ -141,11 +141,17 @@ struct AdjTables {
     int *bed = nullptr, *bptr = nullptr, *blist = nullptr;
     int *iwea = nullptr, *iweb = nullptr, *iwptr = nullptr, *iwlist = nullptr;
     int *inv = nullptr;  // input node -> device node
+    // coupled step (single level): the (ring node, donor) pairs of Eq. 9 per
+    // finest-level node, lent[lptr[y nx + x] ..) as 9 r + k, and the
+    // (interpolation node, donor) pairs of Eq. 8 per device mesh node,
+    // hent[hptr[node] ..) as 6 s + k
+    int *lptr = nullptr, *lent = nullptr, *hptr = nullptr, *hent = nullptr;
+    bool coupled_built = false;
 };
 void launch_adj_value(const AdjTables &, const double *g, int Np, double wd, double wl, double inv_q, double *J,
                       cudaStream_t);
 void launch_adj_terminal(const AdjTables &, const double *g, int Np, int n, double wd, double wl, double inv_q,
-                         double *lam, cudaStream_t);
+                         double *lam, cudaStream_t, bool add = false);
 // scratch: 27 Np doubles (per-row mu, sig, E of the reverse sub-step)
 void launch_fv_adjoint(const AdjTables &, const double *g, int Np, int n, double csP, int n_wall, int ring_start,
                        int star, double dt, double dt_tau, const double *lam_in, double *lam_out, double *gcoef,
@@ -159,6 +165,18 @@ void launch_adj_populations(const AdjTables &, const double *g, int Np, int n, c
 void launch_adj_geometry(const AdjTables &, int n, const double *gc, const double *gM, int Np, double wd, double wl,
                          double inv_q, double ca, double sa, double px, double py, double *scratch, double *grad_xy,
                          double *daoa, cudaStream_t);
+
+// adjoints of the lattice side of a single-level coupled step (FP64, parity P)
+void launch_adj_collide(const DevLevel &, const double *f, int P, double *lam, cudaStream_t);
+void launch_adj_outer_bc(const DevLevel &, const double *f, int P, double u0, double *lam, cudaStream_t);
+void launch_adj_ring_lattice(const DevLevel &, const double *f, int P, const AdjTables &, const double *ring_w,
+                             const double *lamQ, int n_ring, double *lam, cudaStream_t);
+// lamq: 12 n_is doubles of scratch
+void launch_adj_hole(const DevLevel &, const DevMesh &, const AdjTables &, const double *g, int P, double *lam,
+                     double *lamq, double *lam_g, cudaStream_t);
+void launch_adj_ring_rows(const DevMesh &, double scale5, double wa, double wb, double *lam_g, double *lamQ0,
+                          double *lamQ1, cudaStream_t);
+void launch_adj_lattice_out(const DevLevel &, const double *lam, int P, double *grad, cudaStream_t);
 
 // bounds-checked build (HLBM_DEBUG): violations so far and the bit mask of the
 // sites that saw them, for the whole process; returns false (out = 0) in a

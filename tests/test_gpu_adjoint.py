@@ -139,3 +139,73 @@ def test_fv_adjoint_rejects_what_it_does_not_cover(H):
         with pytest.raises(H.HlbmError) as e:
             s64.fv_adjoint(bad)
         assert e.value.code == H.HLBM_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# Adjoint of whole coarse steps (single level): lattice, outer conditions,
+# overlap interpolations, interface rows, finite-volume sub-steps, forces.
+
+@pytest.fixture(scope="module")
+def small(H):
+    case = make_case("hlbm_small", aoa_deg=4.0)
+    s = H.Solver(case, precision="fp64")
+    s.step(1)
+    s.forces()  # drain
+    return case, s
+
+
+def _oracle_mean_force(case, K, wd, wl, dlat=None, dmesh=None, h=0.0):
+    """Mean of wd C_D + wl C_L over coarse steps 2 .. K + 1 of the oracle,
+    its state after step 1 moved by h * (dlat, dmesh) in populations."""
+    import oracle
+    o = oracle.Oracle(case)
+    o.step(1)
+    if dlat is not None:
+        f = o.populations(0)
+        o.set_populations(0, np.where(np.isnan(f), f, f + h * dlat))
+    if dmesh is not None:
+        o.set_populations(-1, o.populations(-1) + h * dmesh)
+    o.step(K)
+    cd, cl = o.forces()
+    return float(np.mean(wd * cd[1:] + wl * cl[1:]))
+
+
+@pytest.mark.parametrize("K,wd,wl", [(1, 1.0, 0.0), (3, 0.4, 1.0)])
+def test_coupled_adjoint_matches_oracle_finite_differences(H, small, K, wd, wl):
+    case, s = small
+    before = [a.copy() for a in s.fields(0)] + [a.copy() for a in s.fields(-1)]
+    J, gl, gm = s.adjoint(K, wd, wl)
+    after = list(s.fields(0)) + list(s.fields(-1))
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b, equal_nan=True)
+    assert abs(J - _oracle_mean_force(case, K, wd, wl)) <= 1e-10 * max(1.0, abs(J))
+    rng = np.random.default_rng(7 + K)
+    nx, ny = (int(v) for v in case.levels[0][:2])
+    dlat = rng.standard_normal((nx * ny, 9)) * 1e-3
+    dmesh = rng.standard_normal((case.n_nodes, 9)) * 1e-3
+    h = 1e-4
+    for dl, dm in ((dlat, None), (None, dmesh)):
+        fd = (_oracle_mean_force(case, K, wd, wl, dl, dm, h) - _oracle_mean_force(case, K, wd, wl, dl, dm, -h)) / (2 * h)
+        ad = float(np.nansum(gl * dl)) if dl is not None else float(np.sum(gm * dm))
+        assert abs(ad - fd) <= 1e-6 * abs(fd) + 1e-10, (K, dl is not None, ad, fd)
+
+
+def test_coupled_adjoint_value_is_the_next_force_samples(H, small):
+    """J is the mean of the force samples the solver records over the same
+    steps (the adjoint's forward replays the step on scratch copies)."""
+    case, s = small
+    J, _, _ = s.adjoint(2, 1.0, 0.5)
+    t = H.Solver(case, precision="fp64")
+    t.step(1)
+    t.forces()
+    t.step(2)
+    cd, cl = t.forces()
+    assert abs(J - float(np.mean(cd + 0.5 * cl))) <= 1e-13 * abs(J)
+
+
+def test_coupled_adjoint_rejects_refined_and_reduced_precision(H):
+    for name, prec in (("hlbm_mini2", "fp64"), ("hlbm_small", "fp32")):
+        s = H.Solver(make_case(name), precision=prec)
+        with pytest.raises(H.HlbmError) as e:
+            s.adjoint(1)
+        assert e.value.code == H.HLBM_ENOTIMPL

@@ -340,6 +340,26 @@ def main():
             "dJ_daoa_per_deg": da5,
             "dJ_dthickness_modes": [float((gx5 * f).sum()) for f in thickness_modes(case)]}
         del gg5, gc5, gx5
+        # ---- adjoint of whole coarse steps, single-level configuration
+        # (config 1 lattice and mesh, FP64): 100 steps, J = mean C_D
+        small = make_case("hlbm_small", aoa_deg=4.0)
+        s6 = H.Solver(small, precision="fp64", use_graphs=True)
+        s6.step(2)
+        s6.sync()
+        t6f = time.perf_counter()
+        s6.step(100)
+        s6.sync()
+        t_fwd6 = time.perf_counter() - t6f
+        t6 = time.perf_counter()
+        J6, gl6, gm6 = s6.adjoint(100, 1.0, 0.0)
+        t_adj6 = time.perf_counter() - t6
+        s6.close()
+        line["adjoint"] = {
+            "workload": "hlbm_small (200 x 100 lattice, 5 200-node mesh), FP64", "coarse_steps": 100,
+            "seconds": t_adj6, "forward_seconds_graphs": t_fwd6, "ratio_to_forward": t_adj6 / t_fwd6,
+            "checkpointing": "sqrt: 10 segments of 10 steps, each re-run once", "J_mean_cd": J6,
+            "grad_norm_lattice": float((gl6 ** 2).sum() ** 0.5), "grad_norm_mesh": float((gm6 ** 2).sum() ** 0.5)}
+        del gl6, gm6
         # ---- the large-Re configuration (1.5 M-node mesh): the finite-volume
         # state (~250 MB per sub-step) no longer fits in L2, so this is the
         # HBM-bound case; reported beside the headline, not as it

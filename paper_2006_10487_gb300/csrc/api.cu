@@ -1373,11 +1373,23 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
         auto copy = [&](void *dst, const void *src, size_t doubles) {
             ck(cudaMemcpyAsync(dst, src, doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
         };
-        // ---- forward on scratch copies of the state, checkpoints at every coarse step
-        std::vector<double *> fck(K + 1), gck(K), Qd(K + 1);
-        for (int k = 0; k <= K; k++) fck[k] = scr(lat * sizeof(double));
-        for (int k = 0; k < K; k++) gck[k] = scr(plane * sizeof(double));
-        for (int k = 0; k <= K; k++) Qd[k] = scr(qn * sizeof(double));
+        // ---- forward on scratch copies of the state.  Recomputation
+        // checkpointing: segments of S = ceil(sqrt(K)) coarse steps; the first
+        // pass keeps the state (lattice, mesh, interface data) at each segment
+        // start, and the reverse sweep re-runs one segment at a time, keeping
+        // the state at each of its steps' starts.
+        const int S = std::max(1, int(std::ceil(std::sqrt(double(K)))));
+        const int nseg = (K + S - 1) / S;
+        std::vector<double *> cf(nseg), cg(nseg), cq(nseg);  // segment checkpoints
+        for (int j = 0; j < nseg; j++) {
+            cf[j] = scr(lat * sizeof(double));
+            cg[j] = scr(plane * sizeof(double));
+            cq[j] = scr(qn * sizeof(double));
+        }
+        std::vector<double *> fck(S + 1), gck(S), Qd(S + 1);  // step starts within a segment
+        for (int k = 0; k <= S; k++) fck[k] = scr(lat * sizeof(double));
+        for (int k = 0; k < S; k++) gck[k] = scr(plane * sizeof(double));
+        for (int k = 0; k <= S; k++) Qd[k] = scr(qn * sizeof(double));
         DevCtx W = D0;
         W.lv[0].f = scr(lat * sizeof(double));
         copy(W.lv[0].f, L0.f, lat);
@@ -1394,14 +1406,12 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
         W.flag = W.force_counter + 1;
         ck(cudaMemsetAsync(W.force_counter, 0, 2 * sizeof(int), s), "memset");
         W.m.wall_stats = 0;
-        for (int k = 0; k <= K; k++) {
+        auto phase = [&](long k) {
             std::swap(c->dev, W);
             set_phase(c, k0 + k);
             std::swap(c->dev, W);
-            copy(fck[k], W.lv[0].f, lat);
-            copy(Qd[k], W.m.Q0, qn);
-            if (k == K) break;
-            copy(gck[k], W.m.g[W.m.gcur], plane);
+        };
+        auto step = [&]() {
             std::swap(c->dev, W);
             try {
                 coarse_step<double, double>(c, s);
@@ -1410,10 +1420,32 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
                 throw;
             }
             std::swap(c->dev, W);
-        }
+        };
+        // steps ka .. kb - 1 from the state in W; with keep, the state at each
+        // step start (and at kb) into fck / gck / Qd [k - ka]
+        auto run = [&](int ka, int kb, bool keep) {
+            for (int k = ka; k <= kb; k++) {
+                phase(k);
+                if (keep) {
+                    copy(fck[k - ka], W.lv[0].f, lat);
+                    copy(Qd[k - ka], W.m.Q0, qn);
+                    if (k < kb) copy(gck[k - ka], W.m.g[W.m.gcur], plane);
+                }
+                if (k == kb) break;
+                if (!keep && k % S == 0) {
+                    copy(cf[k / S], W.lv[0].f, lat);
+                    copy(cg[k / S], W.m.g[W.m.gcur], plane);
+                    copy(cq[k / S], W.m.Q0, qn);
+                }
+                step();
+            }
+        };
+        run(0, K, false);  // first pass: forces and segment checkpoints
         ck(cudaGetLastError(), "forward steps");
         std::vector<double> fb(2 * size_t(K));
         ck(cudaMemcpyAsync(fb.data(), W.force_buf, fb.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        int flag = 0;
+        ck(cudaMemcpyAsync(&flag, W.flag, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
         // ---- reverse sweep
         double *lam_f = scr(lat * sizeof(double));
         double *lam_g = scr(plane * sizeof(double)), *lam_t = scr(plane * sizeof(double));
@@ -1433,18 +1465,29 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
         const double scale5 = 1.0 - 1.0 / (2.0 * L0.tau);
         const double *ring_w = (const double *)D0.m.ring_w;
         for (int k = K - 1; k >= 0; k--) {
+            const int j = k / S, ka = j * S;
+            if (k == std::min(K, ka + S) - 1) {
+                // re-run segment j from its checkpoint, keeping its step starts
+                phase(ka);
+                copy(W.lv[0].f, cf[j], lat);
+                copy(W.m.g[W.m.gcur], cg[j], plane);
+                copy(W.m.Q0, cq[j], qn);
+                run(ka, std::min(K, ka + S), true);
+            }
             const int Pk = int((k0 + k) & 1);
+            double *const f_start = fck[k - ka], *const f_end = fck[k - ka + 1], *const g_start = gck[k - ka];
+            double *const Q0k = Qd[k - ka], *const Q1k = Qd[k - ka + 1];
             // the finite-volume group of step k again, from its checkpoint
             DevCtx V = W;
-            V.lv[0].f = fck[k + 1];
+            V.lv[0].f = f_end;
             V.lv[0].parity = Pk ^ 1;
-            V.m.Q0 = Qd[k];
+            V.m.Q0 = Q0k;
             V.m.Q1 = qtmp;
-            copy(st, gck[k], plane);
+            copy(st, g_start, plane);
             V.m.g[0] = st;
             V.m.gcur = 0;
             launch_ring_interp<double, double>(V, true, s);  // interface rows at theta = 0
-            V.m.Q1 = Qd[k + 1];
+            V.m.Q1 = Q1k;
             for (int m = 0; m < ns; m++) {
                 V.m.g[0] = st + size_t(m) * plane;
                 V.m.g[1] = st + size_t(m + 1) * plane;
@@ -1463,23 +1506,21 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
             launch_adj_ring_rows(D0.m, scale5, 1.0, 0.0, lin, lQ0, lQ1, s);
             if (lin != lam_g) std::swap(lam_g, lam_t);  // lam_g: cotangent of the step's initial mesh state
             // lattice side, in reverse order of the forward step
-            launch_adj_ring_lattice(L0, fck[k + 1], Pk ^ 1, A, ring_w, lQ1, D0.m.n_ring, lam_f, s);
-            launch_adj_outer_bc(L0, fck[k + 1], Pk ^ 1, P.u0, lam_f, s);
-            launch_adj_collide(L0, fck[k], Pk, lam_f, s);
-            launch_adj_hole(L0, D0.m, A, gck[k], Pk, lam_f, lamq, lam_g, s);
-            launch_adj_ring_lattice(L0, fck[k], Pk, A, ring_w, lQ0, D0.m.n_ring, lam_f, s);
+            launch_adj_ring_lattice(L0, f_end, Pk ^ 1, A, ring_w, lQ1, D0.m.n_ring, lam_f, s);
+            launch_adj_outer_bc(L0, f_end, Pk ^ 1, P.u0, lam_f, s);
+            launch_adj_collide(L0, f_start, Pk, lam_f, s);
+            launch_adj_hole(L0, D0.m, A, g_start, Pk, lam_f, lamq, lam_g, s);
+            launch_adj_ring_lattice(L0, f_start, Pk, A, ring_w, lQ0, D0.m.n_ring, lam_f, s);
             ck(cudaMemsetAsync(lQ0, 0, qn * sizeof(double), s), "memset");
             ck(cudaMemsetAsync(lQ1, 0, qn * sizeof(double), s), "memset");
         }
         if (gl) launch_adj_lattice_out(L0, lam_f, int(k0 & 1), gl, s);
-        launch_adj_populations(A, gck[0], Np, n, lam_g, gg, s);
+        launch_adj_populations(A, gck[0], Np, n, lam_g, gg, s);  // segment 0's first step start
         ck(cudaGetLastError(), "adjoint kernels");
         if (gl)
             ck(cudaMemcpyAsync(grad_lattice, gl, 9 * size_t(F.nx) * F.ny * sizeof(double), cudaMemcpyDeviceToHost, s),
                "D2H");
         if (grad_mesh) ck(cudaMemcpyAsync(grad_mesh, gg, 9 * size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
-        int flag = 0;
-        ck(cudaMemcpyAsync(&flag, W.flag, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
         ck(cudaStreamSynchronize(s), "sync");
         double j = 0.0;
         for (int k = 0; k < K; k++) j += wd * fb[2 * size_t(k)] + wl * fb[2 * size_t(k) + 1];

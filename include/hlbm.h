@@ -266,27 +266,30 @@ int hlbm_wall_stats_reset(hlbm_ctx *ctx);
  * context's stream.  Errors: HLBM_ENOTIMPL (not FP64), HLBM_EINVAL (no
  * mesh, n_window out of range, capacities), HLBM_ESTATE, HLBM_ENOMEM,
  * HLBM_ECUDA. */
-/* Discrete adjoint of n_steps whole coarse steps of a single-level
- * configuration (FP64 contexts; one Cartesian level plus the mesh): Eq. 1
- * collide-stream with the outer conditions, Eq. 4 + 8 hole nodes, Eq. 9
- * interface data with the Eq. 5-7 interface rows at their sub-step times,
- * the Eq. 3 sub-steps with the wall rule, and the force of every step:
+/* Discrete adjoint of n_steps whole coarse steps (FP64 contexts with a
+ * mesh): on every level the Eq. 1 collide-stream, the outer conditions
+ * (level 0), the band snapshots, the prolongation with its time and space
+ * interpolation and the restriction of the refinement interfaces; on the
+ * finest level the Eq. 4 + 8 hole nodes, the Eq. 9 interface data with the
+ * Eq. 5-7 interface rows at their sub-step times, the Eq. 3 sub-steps with
+ * the wall rule; and the force of every coarse step:
  *   J = (1/n_steps) sum_k (wd C_D(k) + wl C_L(k)),
  * the mean over the n_steps force samples that hlbm_step would record from
  * the current state.  The forward steps run on scratch copies (the context's
- * state and force series do not change), storing the lattice and mesh state
- * at the start of every coarse step; the reverse sweep recomputes each
- * step's finite-volume sub-steps from its checkpoint.  Outputs: *J; if
+ * state and force series do not change).  Recomputation checkpointing: the
+ * state at every ceil(sqrt(n_steps))-th step start is kept, each segment is
+ * re-run once keeping its step starts, and each step once more while its
+ * level steps' states are recorded for the reverse sweep.  Outputs: *J; if
  * grad_lattice is not NULL, dJ/d(lattice populations) of the current state,
- * [ny][nx][9] (cap_lat >= 9 nx ny; 0 on hole nodes, which are not computed);
- * if grad_mesh is not NULL, dJ/d(mesh populations), [n_nodes][9] in input
- * node order (cap_mesh >= 9 n_nodes; 0 on interface rows, which are
- * overwritten before they are read).  Scratch: (n_steps + 1) lattice states,
- * n_steps + n_sub + 6 mesh states and small arrays, allocated and freed
- * through the context's allocator.  Synchronises the context's stream.
- * Errors: HLBM_ENOTIMPL (not FP64, or more than one level), HLBM_EINVAL (no
- * mesh, n_steps < 1, capacities), HLBM_EUNSTABLE (NaN in a forward force),
- * HLBM_ESTATE, HLBM_ENOMEM, HLBM_ECUDA. */
+ * level after level, each [ny][nx][9] (cap_lat >= 9 sum_l nx_l ny_l; 0 on
+ * nodes that are not computed); if grad_mesh is not NULL, dJ/d(mesh
+ * populations), [n_nodes][9] in input node order (cap_mesh >= 9 n_nodes; 0
+ * on interface rows, which are overwritten before they are read).  Scratch:
+ * about 2 sqrt(n_steps) + 2 copies of the whole state plus one coarse step's
+ * records, allocated and freed through the context's allocator.
+ * Synchronises the context's stream.  Errors: HLBM_ENOTIMPL (not FP64),
+ * HLBM_EINVAL (no mesh, n_steps < 1, capacities), HLBM_EUNSTABLE (NaN in a
+ * forward force), HLBM_ESTATE, HLBM_ENOMEM, HLBM_ECUDA. */
 int hlbm_adjoint(hlbm_ctx *ctx, int n_steps, double wd, double wl, double *J, double *grad_lattice, size_t cap_lat,
                  double *grad_mesh, size_t cap_mesh);
 

@@ -213,17 +213,19 @@ class Solver:
         return float(J[0]), gg, gc, gx, float(da[0])
 
     def adjoint(self, n_steps, wd=1.0, wl=0.0):
-        """Discrete adjoint of n_steps coarse steps of a single-level FP64
-        solver (hlbm_adjoint): J = mean of wd C_D + wl C_L over the steps,
-        dJ/d(lattice populations) [ny * nx, 9] and dJ/d(mesh populations)
-        [n_nodes, 9] of the current state; the state is not changed."""
-        nx, ny = (int(v) for v in self.case.levels[0][:2])
+        """Discrete adjoint of n_steps coarse steps of an FP64 solver
+        (hlbm_adjoint): J = mean of wd C_D + wl C_L over the steps, the
+        gradients in every level's lattice populations (a list, level order,
+        each [ny * nx, 9]) and in the mesh populations [n_nodes, 9] of the
+        current state; the state is not changed."""
+        sizes = [int(nx) * int(ny) for nx, ny in self.case.levels[:, :2]]
         J = np.zeros(1)
-        gl, gm = np.empty((nx * ny, 9)), np.empty((self.case.n_nodes, 9))
+        gl, gm = np.empty((sum(sizes), 9)), np.empty((self.case.n_nodes, 9))
         dp = C.POINTER(C.c_double)
         _check(self._lib.hlbm_adjoint(self.ctx, int(n_steps), float(wd), float(wl), J.ctypes.data_as(dp),
                                       gl.ctypes.data_as(dp), gl.size, gm.ctypes.data_as(dp), gm.size), self.ctx)
-        return float(J[0]), gl, gm
+        parts = np.split(gl, np.cumsum(sizes)[:-1])
+        return float(J[0]), parts, gm
 
     def save(self, path):
         """Checkpoint of the whole evolving state (hlbm_save)."""

@@ -802,6 +802,146 @@ __global__ void k_adj_lattice_out(const double *lam, int nx, int ny, int pitch, 
         grad[9 * (size_t(y) * nx + x) + i] = hole ? 0.0 : lam[lst<P>(i, n, pitch, stride)];
 }
 
+// ------------------------------------------------ refinement interface ----
+// q(node) = (rho, u, f - f^eq) of a lattice node as duals (lanes: populations)
+template <int P>
+__device__ __forceinline__ void lat_q(const double *f, size_t n, int pitch, size_t stride, Dual q[12])
+{
+    Dual F[9], rho, ux, uy;
+    lat_load<P>(f, n, pitch, stride, F, rho, ux, uy);
+    q[0] = rho;
+    q[1] = ux;
+    q[2] = uy;
+#pragma unroll
+    for (int i = 0; i < 9; i++) q[3 + i] = F[i] - feq(i, rho, ux, uy);
+}
+
+// Band snapshot of a parent level (band entry b <-> node (X, Y): the lines
+// y = coy, coy + cmy for x in [cox - 1, cox + cmx] and x = cox, cox + cmx for
+// y in [coy - 1, coy + cmy]; corner nodes are on two lines): cotangents of
+// the snapshot [12][band_n] -> the node's slots at parity P.  One thread per
+// node of the band's box.
+template <int P>
+__global__ void k_adj_snapshot(const double *f, int pitch, size_t stride, int cox, int coy, int cmx, int cmy,
+                               const double *lamS, int band_n, double *lam)
+{
+    const int X = cox - 1 + int(blockIdx.x * blockDim.x + threadIdx.x), Y = coy - 1 + int(blockIdx.y);
+    if (X > cox + cmx) return;
+    const int w = cmx + 2, h = cmy + 2;
+    int b[2], nb = 0;
+    if (Y == coy) b[nb++] = X - (cox - 1);
+    if (Y == coy + cmy) b[nb++] = w + X - (cox - 1);
+    if (X == cox && nb < 2) b[nb++] = 2 * w + Y - (coy - 1);
+    if (X == cox + cmx && nb < 2) b[nb++] = 2 * w + h + Y - (coy - 1);
+    if (nb == 0) return;
+    const size_t n = lnode(X, Y, pitch);
+    Dual q[12];
+    lat_q<P>(f, n, pitch, stride, q);
+    double d[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int t = 0; t < nb; t++)
+        for (int m = 0; m < 12; m++) {
+            const double l = lamS[size_t(m) * band_n + b[t]];
+#pragma unroll
+            for (int k = 0; k < 9; k++) d[k] += l * q[m].d[k];
+        }
+#pragma unroll
+    for (int k = 0; k < 9; k++) lam[lst<P>(k, n, pitch, stride)] += d[k];
+}
+
+// Prolongation, part 1 (per fine perimeter node k at parity P): its slots
+// held f^eq(q) + scale f^neq(q) with q = sum_t w_t ((1 - theta) A_bt + theta B_bt)
+// of the parent's band data; cotangents -> lamq[12][nper] (dJ/dq), and end.
+template <int P>
+__global__ void k_adj_prolong_q(int nx, int ny, int pitch, size_t stride, const double *A, const double *B,
+                                int band_n, int cmx, int cmy, double theta, double scale, double *lam, double *lamq)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nper = 2 * nx + 2 * (ny - 2);
+    if (k >= nper) return;
+    int i, j;
+    if (k < nx) { i = k; j = 0; }
+    else if (k < 2 * nx) { i = k - nx; j = ny - 1; }
+    else if (k < 2 * nx + ny - 2) { i = 0; j = k - 2 * nx + 1; }
+    else { i = nx - 1; j = k - 2 * nx - (ny - 2) + 1; }
+    const int w = cmx + 2, h = cmy + 2;
+    int base, pos, odd;
+    if (j == 0 || j == ny - 1) {
+        base = (j == 0) ? 0 : w;
+        pos = (i >> 1) + 1;
+        odd = i & 1;
+    } else {
+        base = 2 * w + ((i == 0) ? 0 : h);
+        pos = (j >> 1) + 1;
+        odd = j & 1;
+    }
+    double q[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const int nd = odd ? 3 : 1;
+    for (int t = 0; t < nd; t++) {
+        const int b = base + pos + (odd ? t - 1 : 0);
+        const double wk = odd ? (t == 0 ? -0.125 : (t == 1 ? 0.75 : 0.375)) : 1.0;
+        for (int m = 0; m < 12; m++)
+            q[m] += wk * ((1.0 - theta) * A[size_t(m) * band_n + b] + theta * B[size_t(m) * band_n + b]);
+    }
+    const Dual rho = seeded(q[0], 0), vx = seeded(q[1], 1), vy = seeded(q[2], 2);
+    const size_t n = lnode(i, j, pitch);
+    double lq[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int d = 0; d < 9; d++) {
+        const size_t slot = lst<P>(d, n, pitch, stride);
+        const double lo = lam[slot];
+        lam[slot] = 0.0;
+        const Dual e = feq(d, rho, vx, vy);
+        lq[0] += lo * e.d[0];
+        lq[1] += lo * e.d[1];
+        lq[2] += lo * e.d[2];
+        lq[3 + d] = scale * lo;
+    }
+    for (int m = 0; m < 12; m++) lamq[size_t(m) * nper + k] = lq[m];
+}
+
+// Part 2 (per band entry b): the (fine perimeter node, weight) pairs that read
+// it, pk[pp[b] .. pp[b + 1]) with weights pw; adds to the band cotangents.
+__global__ void k_adj_prolong_band(const int *pp, const int *pk, const double *pw, const double *lamq, int nper,
+                                   int band_n, double theta, double *lamA, double *lamB)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= band_n) return;
+    for (int m = 0; m < 12; m++) {
+        double s = 0.0;
+        for (int t = pp[b]; t < pp[b + 1]; t++) s += pw[t] * lamq[size_t(m) * nper + pk[t]];
+        lamA[size_t(m) * band_n + b] += (1.0 - theta) * s;
+        lamB[size_t(m) * band_n + b] += theta * s;
+    }
+}
+
+// Restriction (coarse node (X, Y) one cell or more inside the child box, not
+// in the hole, at parity PC, from fine node (2 (X - cox), 2 (Y - coy)) at
+// parity PF: f^eq(q) + scale f^neq(q) of the fine q): cotangents of the
+// coarse slots -> the fine node's slots; the coarse slots end there.
+template <int PC, int PF>
+__global__ void k_adj_restrict(const double *ff, int pitch_c, size_t stride_c, int pitch_f, size_t stride_f, int cox,
+                               int coy, int cmx, int cmy, double scale, const int *hx0, const int *hx1, double *lamc,
+                               double *lamf)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (a >= cmx - 1) return;
+    const int X = cox + 1 + a, Y = coy + 1 + b;
+    if (hx0 && X >= hx0[Y] && X < hx1[Y]) return;
+    const size_t nc = lnode(X, Y, pitch_c), nf = lnode(2 * (X - cox), 2 * (Y - coy), pitch_f);
+    Dual q[12];
+    lat_q<PF>(ff, nf, pitch_f, stride_f, q);
+    double d[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 9; i++) {
+        const size_t slot = lst<PC>(i, nc, pitch_c, stride_c);
+        const double lo = lamc[slot];
+        lamc[slot] = 0.0;
+        const Dual out = feq(i, q[0], q[1], q[2]) + scale * q[3 + i];
+#pragma unroll
+        for (int k = 0; k < 9; k++) d[k] += lo * out.d[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; k++) lamf[lst<PF>(k, nf, pitch_f, stride_f)] += d[k];
+}
+
 }  // namespace
 
 void launch_adj_geometry(const AdjTables &A, int n, const double *gc, const double *gM, int Np, double wd, double wl,
@@ -914,6 +1054,48 @@ void launch_adj_lattice_out(const DevLevel &l, const double *lam, int P, double 
     const dim3 grid((l.nx + 127) / 128, l.ny);
     if (P == 0) k_adj_lattice_out<0><<<grid, 128, 0, s>>>(lam, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, grad);
     else k_adj_lattice_out<1><<<grid, 128, 0, s>>>(lam, l.nx, l.ny, l.pitch, l.stride, l.hx0, l.hx1, grad);
+}
+
+}  // namespace hlbm
+
+namespace hlbm {
+
+void launch_adj_snapshot(const DevLevel &l, const double *f, int P, const double *lamS, double *lam, cudaStream_t s)
+{
+    const dim3 grid((l.cmx + 2 + 127) / 128, l.cmy + 2);
+    if (P == 0) k_adj_snapshot<0><<<grid, 128, 0, s>>>(f, l.pitch, l.stride, l.cox, l.coy, l.cmx, l.cmy, lamS, l.band_n, lam);
+    else k_adj_snapshot<1><<<grid, 128, 0, s>>>(f, l.pitch, l.stride, l.cox, l.coy, l.cmx, l.cmy, lamS, l.band_n, lam);
+}
+
+void launch_adj_prolong(const DevLevel &p, const DevLevel &l, int P, double theta, const double *A, const double *B,
+                        const int *pp, const int *pk, const double *pw, double *lam, double *lamq, double *lamA,
+                        double *lamB, cudaStream_t s)
+{
+    const int nper = 2 * l.nx + 2 * (l.ny - 2);
+    const double scale = l.tau / (2.0 * p.tau);
+    if (P == 0)
+        k_adj_prolong_q<0><<<(nper + 127) / 128, 128, 0, s>>>(l.nx, l.ny, l.pitch, l.stride, A, B, p.band_n, p.cmx,
+                                                              p.cmy, theta, scale, lam, lamq);
+    else
+        k_adj_prolong_q<1><<<(nper + 127) / 128, 128, 0, s>>>(l.nx, l.ny, l.pitch, l.stride, A, B, p.band_n, p.cmx,
+                                                              p.cmy, theta, scale, lam, lamq);
+    k_adj_prolong_band<<<(p.band_n + 127) / 128, 128, 0, s>>>(pp, pk, pw, lamq, nper, p.band_n, theta, lamA, lamB);
+}
+
+void launch_adj_restrict(const DevLevel &p, const DevLevel &l, int PC, int PF, const double *ff, double *lamc,
+                         double *lamf, cudaStream_t s)
+{
+    if (p.cmx < 2 || p.cmy < 2) return;
+    const dim3 grid((p.cmx - 1 + 127) / 128, p.cmy - 1);
+    const double scale = 2.0 * p.tau / l.tau;
+#define HLBM_ADJ_RESTRICT(A_, B_)                                                                                    \
+    k_adj_restrict<A_, B_><<<grid, 128, 0, s>>>(ff, p.pitch, p.stride, l.pitch, l.stride, p.cox, p.coy, p.cmx, p.cmy, \
+                                                scale, p.hx0, p.hx1, lamc, lamf)
+    if (PC == 0 && PF == 0) HLBM_ADJ_RESTRICT(0, 0);
+    else if (PC == 0) HLBM_ADJ_RESTRICT(0, 1);
+    else if (PF == 0) HLBM_ADJ_RESTRICT(1, 0);
+    else HLBM_ADJ_RESTRICT(1, 1);
+#undef HLBM_ADJ_RESTRICT
 }
 
 }  // namespace hlbm

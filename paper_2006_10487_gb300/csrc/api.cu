@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -46,6 +47,7 @@ struct hlbm_ctx {
     double create_ms[3] = {0.0, 0.0, 0.0};  // host set-up tables, device build, graph capture
     double build_ms[2] = {0.0, 0.0};         // device build: tables and uploads; initial state and autotuner
     AdjTables adj;                            // finite-volume adjoint tables (built on first use)
+    struct AdjRecorder *rec = nullptr;        // set while the adjoint records a coarse step
     void *(*alloc_fn)(size_t, void *) = nullptr;
     void (*free_fn)(void *, void *) = nullptr;
     void *alloc_ctx = nullptr;
@@ -152,6 +154,48 @@ void set_phase(hlbm_ctx *c, long k)
 
 template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double theta, cudaStream_t s);
 
+// What the adjoint of a coarse step needs from its forward pass, per level
+// step (in schedule order): the level's lattice at the step start and after
+// its boundary ring was written, the child's lattice when the restriction
+// reads it, the parent band data the prolongation read, and (finest level
+// with a mesh) the mesh state and interface data.  Copies on the stream,
+// into blocks freed by release().
+}  // namespace
+
+struct LevelRec {
+    int l = 0, P = 0;
+    double theta = 0.0;
+    double *f_start = nullptr, *f_end = nullptr, *f_child = nullptr, *sA = nullptr, *sB = nullptr;
+    double *g_start = nullptr, *Q0 = nullptr, *Q1 = nullptr;
+};
+struct AdjRecorder {
+    hlbm_ctx *c = nullptr;
+    cudaStream_t s = nullptr;
+    std::vector<LevelRec> recs;
+    std::vector<void *> blocks;
+    double *keep(const void *src, size_t doubles);
+    void release();
+};
+namespace {
+void dfree(hlbm_ctx *c, void *p);
+void *dalloc(hlbm_ctx *c, size_t bytes);
+}  // namespace
+double *AdjRecorder::keep(const void *src, size_t doubles)
+{
+    double *p = (double *)dalloc(c, doubles * sizeof(double));
+    blocks.push_back(p);
+    ck(cudaMemcpyAsync(p, src, doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "record");
+    return p;
+}
+void AdjRecorder::release()
+{
+    for (void *p : blocks) dfree(c, p);
+    blocks.clear();
+    recs.clear();
+}
+
+namespace {
+
 const char *const kLatticeRange[kMaxLevels] = {"lattice: level 0", "lattice: level 1", "lattice: level 2",
                                                "lattice: level 3", "lattice: level 4", "lattice: level 5",
                                                "lattice: level 6", "lattice: level 7"};
@@ -176,6 +220,19 @@ template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double t
     DevCtx &D = c->dev;
     bool hybrid = (lvl == D.L - 1) && D.m.n > 0;
     bool child = lvl < D.L - 1;
+    if (c->rec) {
+        AdjRecorder &R = *c->rec;
+        LevelRec r;
+        r.l = lvl;
+        r.P = D.lv[lvl].parity;
+        r.theta = theta;
+        r.f_start = R.keep(D.lv[lvl].f, 9 * D.lv[lvl].stride);
+        if (hybrid) {
+            r.g_start = R.keep(D.m.g[D.m.gcur], size_t(9) * D.m.Np);
+            r.Q0 = R.keep(D.m.Q0, 12 * size_t(std::max(1, D.m.n_ring)));
+        }
+        R.recs.push_back(r);
+    }
     if (hybrid) {
         // Eq. 9 data at t: already in Q0 (the previous step's data at t + 1,
         // or the initial state's)
@@ -203,11 +260,22 @@ template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double t
         else launch_prolong<T, S>(D, lvl, theta, sb);
     }
     c->launches += 2;
+    if (c->rec) {
+        AdjRecorder &R = *c->rec;
+        LevelRec &r = R.recs.back();
+        r.f_end = R.keep(D.lv[lvl].f, 9 * D.lv[lvl].stride);
+        if (lvl > 0) {
+            const DevLevel &pl = D.lv[lvl - 1];
+            r.sA = R.keep(pl.snapA, 12 * size_t(pl.band_n));
+            r.sB = R.keep(pl.snapB, 12 * size_t(pl.band_n));
+        }
+    }
     if (hybrid) {
         {
             Range r("overlap: ring interpolation");
             launch_ring_interp<T, S>(D, true, s);  // Eq. 9 data at t + 1, ring state of sub-step 0
         }
+        if (c->rec) c->rec->recs.back().Q1 = c->rec->keep(D.m.Q1, 12 * size_t(std::max(1, D.m.n_ring)));
         if (branch) join(c, s);
         Range r("fv: sub-steps");
         for (int m = 0; m < D.n_sub; m++) {  // Eq. 3, Eq. 5-7, wall rule
@@ -235,6 +303,14 @@ template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double thet
         if (c->side_ok[lvl]) join(c, s);
         advance<T, S>(c, lvl + 1, 0.5, s);
         advance<T, S>(c, lvl + 1, 1.0, s);
+        if (c->rec) {  // the child's lattice as the restriction reads it
+            AdjRecorder &R = *c->rec;
+            for (size_t k = R.recs.size(); k-- > 0;)
+                if (R.recs[k].l == lvl) {
+                    R.recs[k].f_child = R.keep(D.lv[lvl + 1].f, 9 * D.lv[lvl + 1].stride);
+                    break;
+                }
+        }
         Range r("refine: restriction");
         launch_restrict<T, S>(D, lvl, s);
         c->launches += 2;
@@ -1239,6 +1315,42 @@ void build_coupled_tables(hlbm_ctx *c)
     A.lent = upload(c, lent);
     A.hptr = upload(c, hptr);
     A.hent = upload(c, hent);
+    // prolongation into level l: each fine perimeter node reads 1 (even
+    // position) or 3 (odd: weights -1/8, 3/4, 3/8) band entries of level l - 1
+    for (int l = 1; l < P.L; l++) {
+        const LevelPlan &fl = P.lv[l], &pl = P.lv[l - 1];
+        const int nx = fl.nx, ny = fl.ny, w = pl.cmx + 2, h = pl.cmy + 2, band_n = 2 * w + 2 * h;
+        const int nper = 2 * nx + 2 * (ny - 2);
+        std::vector<std::vector<std::pair<int, double>>> by(band_n);
+        for (int k = 0; k < nper; k++) {
+            int i, j;
+            if (k < nx) { i = k; j = 0; }
+            else if (k < 2 * nx) { i = k - nx; j = ny - 1; }
+            else if (k < 2 * nx + ny - 2) { i = 0; j = k - 2 * nx + 1; }
+            else { i = nx - 1; j = k - 2 * nx - (ny - 2) + 1; }
+            int base, pos, odd;
+            if (j == 0 || j == ny - 1) { base = (j == 0) ? 0 : w; pos = (i >> 1) + 1; odd = i & 1; }
+            else { base = 2 * w + ((i == 0) ? 0 : h); pos = (j >> 1) + 1; odd = j & 1; }
+            for (int t = 0; t < (odd ? 3 : 1); t++) {
+                const int b = base + pos + (odd ? t - 1 : 0);
+                const double wk = odd ? (t == 0 ? -0.125 : (t == 1 ? 0.75 : 0.375)) : 1.0;
+                if (b < 0 || b >= band_n) throw CudaError{"prolongation band index out of range"};
+                by[b].push_back({k, wk});
+            }
+        }
+        std::vector<int> pp(size_t(band_n) + 1, 0), pk;
+        std::vector<double> pw;
+        for (int b = 0; b < band_n; b++) {
+            for (auto &e : by[b]) {
+                pk.push_back(e.first);
+                pw.push_back(e.second);
+            }
+            pp[b + 1] = int(pk.size());
+        }
+        A.pp[l] = upload(c, pp);
+        A.pk[l] = upload(c, pk);
+        A.pw[l] = upload(c, pw);
+    }
     A.coupled_built = true;
 }
 
@@ -1342,16 +1454,16 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
     if (!c) return HLBM_EINVAL;
     const Plan &P = c->plan;
     if (P.precision != HLBM_FP64) return fail(c, HLBM_ENOTIMPL, "the adjoint runs on FP64 contexts");
-    if (P.L != 1) return fail(c, HLBM_ENOTIMPL, "the coupled-step adjoint covers single-level configurations");
     if (P.n == 0) return fail(c, HLBM_EINVAL, "the context has no mesh");
     if (n_steps < 1) return fail(c, HLBM_EINVAL, "n_steps must be >= 1");
     if (!J) return fail(c, HLBM_EINVAL, "J is NULL");
-    const LevelPlan &F = P.lv[0];
-    if (grad_lattice && cap_lat < 9 * size_t(F.nx) * F.ny) return fail(c, HLBM_EINVAL, "grad_lattice capacity below 9 nx ny");
+    size_t lat_total = 0;  // populations of all levels
+    for (int l = 0; l < P.L; l++) lat_total += 9 * size_t(P.lv[l].nx) * P.lv[l].ny;
+    if (grad_lattice && cap_lat < lat_total) return fail(c, HLBM_EINVAL, "grad_lattice capacity below 9 sum nx ny");
     if (grad_mesh && cap_mesh < 9 * size_t(P.n)) return fail(c, HLBM_EINVAL, "grad_mesh capacity below 9 n");
     if (c->timing_dirty) return fail(c, HLBM_ESTATE, "the state was consumed by hlbm_time_kernel");
     Range r("hlbm_adjoint");
-    const int K = n_steps, n = P.n, ns = P.n_sub;
+    const int K = n_steps, n = P.n, ns = P.n_sub, L = P.L;
     const long k0 = c->steps;
     std::vector<void *> scratch;
     auto scr = [&](size_t bytes) {
@@ -1362,43 +1474,54 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
     int rc = HLBM_OK;
     const DevCtx D0 = c->dev;
     const long launches0 = c->launches, lps0 = c->launches_per_step;
+    bool side0[hlbm::kMaxLevels];
+    std::copy(c->side_ok, c->side_ok + hlbm::kMaxLevels, side0);
+    AdjRecorder rec;
+    rec.c = c;
+    rec.s = c->stream;
     try {
         if (!c->adj.built) build_adjoint_tables(c);
         if (!c->adj.coupled_built) build_coupled_tables(c);
         const AdjTables &A = c->adj;
         cudaStream_t s = c->stream;
-        const DevLevel &L0 = D0.lv[0];
         const int Np = D0.m.Np, nr = std::max(1, D0.m.n_ring);
-        const size_t lat = 9 * L0.stride, plane = size_t(9) * Np, qn = size_t(12) * nr;
+        const size_t plane = size_t(9) * Np, qn = size_t(12) * nr;
         auto copy = [&](void *dst, const void *src, size_t doubles) {
             ck(cudaMemcpyAsync(dst, src, doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
         };
-        // ---- forward on scratch copies of the state.  Recomputation
-        // checkpointing: segments of S = ceil(sqrt(K)) coarse steps; the first
-        // pass keeps the state (lattice, mesh, interface data) at each segment
-        // start, and the reverse sweep re-runs one segment at a time, keeping
-        // the state at each of its steps' starts.
-        const int S = std::max(1, int(std::ceil(std::sqrt(double(K)))));
-        const int nseg = (K + S - 1) / S;
-        std::vector<double *> cf(nseg), cg(nseg), cq(nseg);  // segment checkpoints
-        for (int j = 0; j < nseg; j++) {
-            cf[j] = scr(lat * sizeof(double));
-            cg[j] = scr(plane * sizeof(double));
-            cq[j] = scr(qn * sizeof(double));
-        }
-        std::vector<double *> fck(S + 1), gck(S), Qd(S + 1);  // step starts within a segment
-        for (int k = 0; k <= S; k++) fck[k] = scr(lat * sizeof(double));
-        for (int k = 0; k < S; k++) gck[k] = scr(plane * sizeof(double));
-        for (int k = 0; k <= S; k++) Qd[k] = scr(qn * sizeof(double));
+        // the evolving state: every level's lattice and band buffers, the mesh
+        // buffers and the interface-data buffers (a "snapshot" copies all)
+        std::vector<std::pair<void **, size_t>> parts;  // (buffer in W, doubles)
         DevCtx W = D0;
-        W.lv[0].f = scr(lat * sizeof(double));
-        copy(W.lv[0].f, L0.f, lat);
-        for (int b = 0; b < 2; b++) {
-            W.m.g[b] = scr(plane * sizeof(double));
-            copy(W.m.g[b], D0.m.g[b], plane);
-            W.m.Qb[b] = scr(qn * sizeof(double));
-            copy(W.m.Qb[b], D0.m.Qb[b], qn);
+        for (int l = 0; l < L; l++) {
+            parts.push_back({&W.lv[l].f, 9 * D0.lv[l].stride});
+            if (D0.lv[l].has_child)
+                for (int b = 0; b < 2; b++) parts.push_back({&W.lv[l].snap[b], 12 * size_t(D0.lv[l].band_n)});
         }
+        for (int b = 0; b < 2; b++) {
+            parts.push_back({&W.m.g[b], plane});
+            parts.push_back({&W.m.Qb[b], qn});
+        }
+        size_t state_doubles = 0;
+        for (auto &pt : parts) state_doubles += pt.second;
+        const void *orig[64];
+        for (size_t k = 0; k < parts.size(); k++) {
+            orig[k] = *parts[k].first;
+            *parts[k].first = scr(parts[k].second * sizeof(double));
+            copy(*parts[k].first, orig[k], parts[k].second);
+        }
+        auto save = [&](double *dst) {
+            for (auto &pt : parts) {
+                copy(dst, *pt.first, pt.second);
+                dst += pt.second;
+            }
+        };
+        auto load = [&](const double *src) {
+            for (auto &pt : parts) {
+                copy(*pt.first, src, pt.second);
+                src += pt.second;
+            }
+        };
         W.force_cap = K;
         W.force_buf = scr(2 * size_t(K) * sizeof(double));
         W.force_partial = scr(2 * size_t(std::max(1, (D0.m.n_edges + 127) / 128)) * sizeof(double));
@@ -1421,110 +1544,181 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
             }
             std::swap(c->dev, W);
         };
-        // steps ka .. kb - 1 from the state in W; with keep, the state at each
-        // step start (and at kb) into fck / gck / Qd [k - ka]
-        auto run = [&](int ka, int kb, bool keep) {
-            for (int k = ka; k <= kb; k++) {
-                phase(k);
-                if (keep) {
-                    copy(fck[k - ka], W.lv[0].f, lat);
-                    copy(Qd[k - ka], W.m.Q0, qn);
-                    if (k < kb) copy(gck[k - ka], W.m.g[W.m.gcur], plane);
-                }
-                if (k == kb) break;
-                if (!keep && k % S == 0) {
-                    copy(cf[k / S], W.lv[0].f, lat);
-                    copy(cg[k / S], W.m.g[W.m.gcur], plane);
-                    copy(cq[k / S], W.m.Q0, qn);
-                }
-                step();
-            }
-        };
-        run(0, K, false);  // first pass: forces and segment checkpoints
+        // Recomputation checkpointing: segments of S = ceil(sqrt(K)) coarse
+        // steps; the first pass keeps the state at each segment start, the
+        // reverse sweep re-runs one segment at a time keeping its step starts,
+        // and re-runs each step once more while recording it.
+        const int S = std::max(1, int(std::ceil(std::sqrt(double(K)))));
+        const int nseg = (K + S - 1) / S;
+        std::vector<double *> cpt(nseg), sst(S);
+        for (int j = 0; j < nseg; j++) cpt[j] = scr(state_doubles * sizeof(double));
+        for (int j = 0; j < S; j++) sst[j] = scr(state_doubles * sizeof(double));
+        for (int k = 0; k < K; k++) {  // first pass: forces and segment checkpoints
+            phase(k);
+            if (k % S == 0) save(cpt[k / S]);
+            step();
+        }
         ck(cudaGetLastError(), "forward steps");
         std::vector<double> fb(2 * size_t(K));
         ck(cudaMemcpyAsync(fb.data(), W.force_buf, fb.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         int flag = 0;
         ck(cudaMemcpyAsync(&flag, W.flag, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
-        // ---- reverse sweep
-        double *lam_f = scr(lat * sizeof(double));
+        // ---- reverse sweep: cotangents of every level's lattice (AA slots),
+        // of the band data of levels with a child, of the mesh state and of
+        // the interface data of the finest step being reversed
+        std::vector<double *> lam_f(L), lsA(L, nullptr), lsB(L, nullptr);
+        size_t maxper = 1;
+        for (int l = 0; l < L; l++) {
+            const DevLevel &dl = D0.lv[l];
+            lam_f[l] = scr(9 * dl.stride * sizeof(double));
+            ck(cudaMemsetAsync(lam_f[l], 0, 9 * dl.stride * sizeof(double), s), "memset");
+            if (dl.has_child) {
+                lsA[l] = scr(12 * size_t(dl.band_n) * sizeof(double));
+                lsB[l] = scr(12 * size_t(dl.band_n) * sizeof(double));
+                ck(cudaMemsetAsync(lsA[l], 0, 12 * size_t(dl.band_n) * sizeof(double), s), "memset");
+                ck(cudaMemsetAsync(lsB[l], 0, 12 * size_t(dl.band_n) * sizeof(double), s), "memset");
+            }
+            if (l > 0) maxper = std::max(maxper, size_t(2 * dl.nx + 2 * (dl.ny - 2)));
+        }
         double *lam_g = scr(plane * sizeof(double)), *lam_t = scr(plane * sizeof(double));
         double *lQ0 = scr(qn * sizeof(double)), *lQ1 = scr(qn * sizeof(double)), *qtmp = scr(qn * sizeof(double));
         double *lamq = scr(12 * size_t(std::max(1, D0.m.n_is)) * sizeof(double));
+        double *lamp = scr(12 * maxper * sizeof(double));
         double *st = scr((size_t(ns) + 1) * plane * sizeof(double));
         double *gc = scr(std::max<size_t>(1, 3 * P.col.size()) * sizeof(double));
         double *rs = scr(3 * plane * sizeof(double));
         double *gg = scr(9 * size_t(n) * sizeof(double));
-        double *gl = grad_lattice ? scr(9 * size_t(F.nx) * F.ny * sizeof(double)) : nullptr;
-        ck(cudaMemsetAsync(lam_f, 0, lat * sizeof(double), s), "memset");
+        double *gl = grad_lattice ? scr(lat_total * sizeof(double)) : nullptr;
         ck(cudaMemsetAsync(lam_g, 0, plane * sizeof(double), s), "memset");
         ck(cudaMemsetAsync(st, 0, (size_t(ns) + 1) * plane * sizeof(double), s), "memset");
         ck(cudaMemsetAsync(lQ0, 0, qn * sizeof(double), s), "memset");
         ck(cudaMemsetAsync(lQ1, 0, qn * sizeof(double), s), "memset");
+        const int fin = L - 1;
         const double inv_q = 1.0 / P.qdyn, dt = 1.0 / ns, dt_tau = dt / P.tau_u, csP = dt_tau * (11.0 / 18.0);
-        const double scale5 = 1.0 - 1.0 / (2.0 * L0.tau);
+        const double scale5 = 1.0 - 1.0 / (2.0 * D0.lv[fin].tau);
         const double *ring_w = (const double *)D0.m.ring_w;
+        std::vector<size_t> subtree(L, 1);  // level steps in one advance() of level l
+        for (int l = L - 2; l >= 0; l--) subtree[l] = 1 + 2 * subtree[l + 1];
+        bool terminal = false;
+        // reverse of one level step (the forward's order: hole nodes, collision,
+        // boundary ring, interface data and finite-volume group)
+        auto level_adj = [&](const LevelRec &R) {
+            const int l = R.l, Pk = R.P;
+            const DevLevel &dl = D0.lv[l];
+            if (l == fin) {
+                DevCtx V = W;  // the finite-volume group again, from the step's records
+                V.lv[l].f = R.f_end;
+                V.lv[l].parity = Pk ^ 1;
+                V.m.Q0 = R.Q0;
+                V.m.Q1 = qtmp;
+                copy(st, R.g_start, plane);
+                V.m.g[0] = st;
+                V.m.gcur = 0;
+                launch_ring_interp<double, double>(V, true, s);  // interface rows at theta = 0
+                V.m.Q1 = R.Q1;
+                for (int m = 0; m < ns; m++) {
+                    V.m.g[0] = st + size_t(m) * plane;
+                    V.m.g[1] = st + size_t(m + 1) * plane;
+                    launch_fv<double, double>(V, m, s);
+                }
+                if (terminal) {  // the coarse step's force sample
+                    launch_adj_terminal(A, st + size_t(ns) * plane, Np, n, wd / K, wl / K, inv_q, lam_g, s, true);
+                    terminal = false;
+                }
+                double *lin = lam_g, *lout = lam_t;
+                for (int m = ns - 1; m >= 0; m--) {
+                    const double th = double(m + 1) / ns;
+                    if (m < ns - 1) launch_adj_ring_rows(D0.m, scale5, 1.0 - th, th, lin, lQ0, lQ1, s);
+                    launch_fv_adjoint(A, st + size_t(m) * plane, Np, n, csP, P.n_wall, P.ring_start,
+                                      m < ns - 1 ? 1 : 0, dt, dt_tau, lin, lout, gc, rs, s);
+                    std::swap(lin, lout);
+                }
+                launch_adj_ring_rows(D0.m, scale5, 1.0, 0.0, lin, lQ0, lQ1, s);
+                if (lin != lam_g) std::swap(lam_g, lam_t);
+                launch_adj_ring_lattice(dl, R.f_end, Pk ^ 1, A, ring_w, lQ1, D0.m.n_ring, lam_f[l], s);
+            }
+            if (l == 0) launch_adj_outer_bc(dl, R.f_end, Pk ^ 1, P.u0, lam_f[0], s);
+            else
+                launch_adj_prolong(D0.lv[l - 1], dl, Pk ^ 1, R.theta, R.sA, R.sB, A.pp[l], A.pk[l], A.pw[l], lam_f[l],
+                                   lamp, lsA[l - 1], lsB[l - 1], s);
+            launch_adj_collide(dl, R.f_start, Pk, lam_f[l], s);
+            if (l == fin) {
+                launch_adj_hole(dl, D0.m, A, R.g_start, Pk, lam_f[l], lamq, lam_g, s);
+                launch_adj_ring_lattice(dl, R.f_start, Pk, A, ring_w, lQ0, D0.m.n_ring, lam_f[l], s);
+                ck(cudaMemsetAsync(lQ0, 0, qn * sizeof(double), s), "memset");
+                ck(cudaMemsetAsync(lQ1, 0, qn * sizeof(double), s), "memset");
+            }
+        };
+        // reverse of advance(l) whose level step is record idx: restriction,
+        // the two child steps (second first), band after the step, the level
+        // step, band at the step start
+        std::function<void(size_t, int)> rev = [&](size_t idx, int l) {
+            const LevelRec R = rec.recs[idx];
+            if (l < L - 1) {
+                const size_t second = idx + 1 + subtree[l + 1];
+                const LevelRec &R2 = rec.recs[second];
+                launch_adj_restrict(D0.lv[l], D0.lv[l + 1], R.P ^ 1, R2.P ^ 1, R.f_child, lam_f[l], lam_f[l + 1], s);
+                rev(second, l + 1);
+                rev(idx + 1, l + 1);
+                launch_adj_snapshot(D0.lv[l], R.f_end, R.P ^ 1, lsB[l], lam_f[l], s);
+                ck(cudaMemsetAsync(lsB[l], 0, 12 * size_t(D0.lv[l].band_n) * sizeof(double), s), "memset");
+            }
+            level_adj(R);
+            if (l < L - 1) {
+                launch_adj_snapshot(D0.lv[l], R.f_start, R.P, lsA[l], lam_f[l], s);
+                ck(cudaMemsetAsync(lsA[l], 0, 12 * size_t(D0.lv[l].band_n) * sizeof(double), s), "memset");
+            }
+        };
         for (int k = K - 1; k >= 0; k--) {
             const int j = k / S, ka = j * S;
-            if (k == std::min(K, ka + S) - 1) {
-                // re-run segment j from its checkpoint, keeping its step starts
+            if (k == std::min(K, ka + S) - 1) {  // re-run segment j keeping its step starts
                 phase(ka);
-                copy(W.lv[0].f, cf[j], lat);
-                copy(W.m.g[W.m.gcur], cg[j], plane);
-                copy(W.m.Q0, cq[j], qn);
-                run(ka, std::min(K, ka + S), true);
+                load(cpt[j]);
+                for (int kk = ka; kk <= k; kk++) {
+                    phase(kk);
+                    save(sst[kk - ka]);
+                    if (kk < k) step();
+                }
             }
-            const int Pk = int((k0 + k) & 1);
-            double *const f_start = fck[k - ka], *const f_end = fck[k - ka + 1], *const g_start = gck[k - ka];
-            double *const Q0k = Qd[k - ka], *const Q1k = Qd[k - ka + 1];
-            // the finite-volume group of step k again, from its checkpoint
-            DevCtx V = W;
-            V.lv[0].f = f_end;
-            V.lv[0].parity = Pk ^ 1;
-            V.m.Q0 = Q0k;
-            V.m.Q1 = qtmp;
-            copy(st, g_start, plane);
-            V.m.g[0] = st;
-            V.m.gcur = 0;
-            launch_ring_interp<double, double>(V, true, s);  // interface rows at theta = 0
-            V.m.Q1 = Q1k;
-            for (int m = 0; m < ns; m++) {
-                V.m.g[0] = st + size_t(m) * plane;
-                V.m.g[1] = st + size_t(m + 1) * plane;
-                launch_fv<double, double>(V, m, s);
+            // step k once more, recorded (one stream: no side branches)
+            phase(k);
+            load(sst[k - ka]);
+            std::fill(c->side_ok, c->side_ok + hlbm::kMaxLevels, false);
+            c->rec = &rec;
+            try {
+                step();
+            } catch (...) {
+                c->rec = nullptr;
+                throw;
             }
-            // force sample of step k, then the sub-steps backwards
-            launch_adj_terminal(A, st + size_t(ns) * plane, Np, n, wd / K, wl / K, inv_q, lam_g, s, true);
-            double *lin = lam_g, *lout = lam_t;
-            for (int m = ns - 1; m >= 0; m--) {
-                const double th = double(m + 1) / ns;
-                if (m < ns - 1) launch_adj_ring_rows(D0.m, scale5, 1.0 - th, th, lin, lQ0, lQ1, s);
-                launch_fv_adjoint(A, st + size_t(m) * plane, Np, n, csP, P.n_wall, P.ring_start, m < ns - 1 ? 1 : 0,
-                                  dt, dt_tau, lin, lout, gc, rs, s);
-                std::swap(lin, lout);
-            }
-            launch_adj_ring_rows(D0.m, scale5, 1.0, 0.0, lin, lQ0, lQ1, s);
-            if (lin != lam_g) std::swap(lam_g, lam_t);  // lam_g: cotangent of the step's initial mesh state
-            // lattice side, in reverse order of the forward step
-            launch_adj_ring_lattice(L0, f_end, Pk ^ 1, A, ring_w, lQ1, D0.m.n_ring, lam_f, s);
-            launch_adj_outer_bc(L0, f_end, Pk ^ 1, P.u0, lam_f, s);
-            launch_adj_collide(L0, f_start, Pk, lam_f, s);
-            launch_adj_hole(L0, D0.m, A, g_start, Pk, lam_f, lamq, lam_g, s);
-            launch_adj_ring_lattice(L0, f_start, Pk, A, ring_w, lQ0, D0.m.n_ring, lam_f, s);
-            ck(cudaMemsetAsync(lQ0, 0, qn * sizeof(double), s), "memset");
-            ck(cudaMemsetAsync(lQ1, 0, qn * sizeof(double), s), "memset");
+            c->rec = nullptr;
+            std::copy(side0, side0 + hlbm::kMaxLevels, c->side_ok);
+            if (rec.recs.size() != subtree[0]) throw CudaError{"unexpected level-step count in the recorded step"};
+            terminal = true;
+            rev(0, 0);
+            ck(cudaStreamSynchronize(s), "sync");  // the records are freed next
+            rec.release();
         }
-        if (gl) launch_adj_lattice_out(L0, lam_f, int(k0 & 1), gl, s);
-        launch_adj_populations(A, gck[0], Np, n, lam_g, gg, s);  // segment 0's first step start
+        // gradients with respect to the state at the first step: every level's
+        // populations (level order) and the mesh populations
+        phase(0);
+        load(sst[0]);
+        if (gl) {
+            size_t off = 0;
+            for (int l = 0; l < L; l++) {
+                const DevLevel &dl = D0.lv[l];
+                launch_adj_lattice_out(dl, lam_f[l], l == 0 ? int(k0 & 1) : 0, gl + off, s);
+                off += 9 * size_t(dl.nx) * dl.ny;
+            }
+        }
+        launch_adj_populations(A, (const double *)W.m.g[W.m.gcur], Np, n, lam_g, gg, s);
         ck(cudaGetLastError(), "adjoint kernels");
-        if (gl)
-            ck(cudaMemcpyAsync(grad_lattice, gl, 9 * size_t(F.nx) * F.ny * sizeof(double), cudaMemcpyDeviceToHost, s),
-               "D2H");
+        if (gl) ck(cudaMemcpyAsync(grad_lattice, gl, lat_total * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         if (grad_mesh) ck(cudaMemcpyAsync(grad_mesh, gg, 9 * size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         ck(cudaStreamSynchronize(s), "sync");
-        double j = 0.0;
-        for (int k = 0; k < K; k++) j += wd * fb[2 * size_t(k)] + wl * fb[2 * size_t(k) + 1];
-        *J = j / K;
+        double jsum = 0.0;
+        for (int k = 0; k < K; k++) jsum += wd * fb[2 * size_t(k)] + wl * fb[2 * size_t(k) + 1];
+        *J = jsum / K;
         if (flag & 2) rc = fail(c, HLBM_ETIMEOUT, "a device-side wait gave up (operator copy did not arrive)");
         else if (flag) rc = fail(c, HLBM_EUNSTABLE, "NaN in the force reduction of the forward steps");
     } catch (const CudaError &e) {
@@ -1532,7 +1726,11 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
     } catch (const std::bad_alloc &) {
         rc = fail(c, HLBM_ENOMEM, "host allocation failed");
     }
+    c->rec = nullptr;
+    cudaStreamSynchronize(c->stream);
+    rec.release();
     c->dev = D0;
+    std::copy(side0, side0 + hlbm::kMaxLevels, c->side_ok);
     c->launches = launches0;
     c->launches_per_step = lps0;
     for (void *p : scratch) dfree(c, p);

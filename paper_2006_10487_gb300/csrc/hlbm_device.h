@@ -146,6 +146,10 @@ struct AdjTables {
     // (interpolation node, donor) pairs of Eq. 8 per device mesh node,
     // hent[hptr[node] ..) as 6 s + k
     int *lptr = nullptr, *lent = nullptr, *hptr = nullptr, *hent = nullptr;
+    // prolongation into level l: the (fine perimeter node, weight) pairs of
+    // each band entry of level l - 1, pk[l][pp[l][b] ..), weights pw[l]
+    int *pp[8] = {}, *pk[8] = {};
+    double *pw[8] = {};
     bool coupled_built = false;
 };
 void launch_adj_value(const AdjTables &, const double *g, int Np, double wd, double wl, double inv_q, double *J,
@@ -177,6 +181,14 @@ void launch_adj_hole(const DevLevel &, const DevMesh &, const AdjTables &, const
 void launch_adj_ring_rows(const DevMesh &, double scale5, double wa, double wb, double *lam_g, double *lamQ0,
                           double *lamQ1, cudaStream_t);
 void launch_adj_lattice_out(const DevLevel &, const double *lam, int P, double *grad, cudaStream_t);
+// refinement interface: band snapshot of parent l, prolongation into l (lamq:
+// 12 x perimeter(l) doubles of scratch), restriction into parent p from l
+void launch_adj_snapshot(const DevLevel &, const double *f, int P, const double *lamS, double *lam, cudaStream_t);
+void launch_adj_prolong(const DevLevel &parent, const DevLevel &l, int P, double theta, const double *A,
+                        const double *B, const int *pp, const int *pk, const double *pw, double *lam, double *lamq,
+                        double *lamA, double *lamB, cudaStream_t);
+void launch_adj_restrict(const DevLevel &parent, const DevLevel &l, int PC, int PF, const double *ff, double *lamc,
+                         double *lamf, cudaStream_t);
 
 // bounds-checked build (HLBM_DEBUG): violations so far and the bit mask of the
 // sites that saw them, for the whole process; returns false (out = 0) in a

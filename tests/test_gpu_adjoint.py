@@ -174,7 +174,7 @@ def _oracle_mean_force(case, K, wd, wl, dlat=None, dmesh=None, h=0.0):
 def test_coupled_adjoint_matches_oracle_finite_differences(H, small, K, wd, wl):
     case, s = small
     before = [a.copy() for a in s.fields(0)] + [a.copy() for a in s.fields(-1)]
-    J, gl, gm = s.adjoint(K, wd, wl)
+    J, (gl,), gm = s.adjoint(K, wd, wl)
     after = list(s.fields(0)) + list(s.fields(-1))
     for a, b in zip(before, after):
         assert np.array_equal(a, b, equal_nan=True)
@@ -203,9 +203,50 @@ def test_coupled_adjoint_value_is_the_next_force_samples(H, small):
     assert abs(J - float(np.mean(cd + 0.5 * cl))) <= 1e-13 * abs(J)
 
 
-def test_coupled_adjoint_rejects_refined_and_reduced_precision(H):
-    for name, prec in (("hlbm_mini2", "fp64"), ("hlbm_small", "fp32")):
-        s = H.Solver(make_case(name), precision=prec)
-        with pytest.raises(H.HlbmError) as e:
-            s.adjoint(1)
-        assert e.value.code == H.HLBM_ENOTIMPL
+def test_coupled_adjoint_rejects_reduced_precision(H):
+    s = H.Solver(make_case("hlbm_small"), precision="fp32")
+    with pytest.raises(H.HlbmError) as e:
+        s.adjoint(1)
+    assert e.value.code == H.HLBM_ENOTIMPL
+
+
+def _oracle_mean_force_levels(case, K, wd, wl, dlev=None, dmesh=None, h=0.0, start=1):
+    """As _oracle_mean_force for any number of levels: dlev is a list of
+    per-level population directions (None to leave a level)."""
+    import oracle
+    o = oracle.Oracle(case)
+    o.step(start)
+    for l, d in enumerate(dlev or []):
+        if d is not None:
+            f = o.populations(l)
+            o.set_populations(l, np.where(np.isnan(f), f, f + h * d))
+    if dmesh is not None:
+        o.set_populations(-1, o.populations(-1) + h * dmesh)
+    o.step(K)
+    cd, cl = o.forces()
+    return float(np.mean(wd * cd[start:] + wl * cl[start:]))
+
+
+@pytest.mark.parametrize("K", [1, 2])
+def test_refined_adjoint_matches_oracle_finite_differences(H, K):
+    """Two levels (refinement box with the mesh): band snapshots,
+    prolongation in time and space, restriction, sub-cycled finest steps."""
+    case = make_case("hlbm_mini2", aoa_deg=3.0)
+    s = H.Solver(case, precision="fp64")
+    s.step(1)
+    s.forces()
+    J, gls, gm = s.adjoint(K, 1.0, 0.3)
+    assert abs(J - _oracle_mean_force_levels(case, K, 1.0, 0.3)) <= 1e-10 * max(1.0, abs(J))
+    rng = np.random.default_rng(30 + K)
+    dirs = [rng.standard_normal(g.shape) * 1e-3 for g in gls]
+    dmesh = rng.standard_normal(gm.shape) * 1e-3
+    h = 1e-4
+    cases = [([dirs[0], None], None), ([None, dirs[1]], None), (None, dmesh)]
+    for dl, dm in cases:
+        fd = (_oracle_mean_force_levels(case, K, 1.0, 0.3, dl, dm, h) -
+              _oracle_mean_force_levels(case, K, 1.0, 0.3, dl, dm, -h)) / (2 * h)
+        if dm is not None:
+            ad = float(np.sum(gm * dm))
+        else:
+            ad = sum(float(np.nansum(g * d)) for g, d in zip(gls, dl) if d is not None)
+        assert abs(ad - fd) <= 1e-6 * abs(fd) + 1e-10, (K, ad, fd)

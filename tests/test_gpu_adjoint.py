@@ -227,11 +227,12 @@ def _oracle_mean_force_levels(case, K, wd, wl, dlev=None, dmesh=None, h=0.0, sta
     return float(np.mean(wd * cd[start:] + wl * cl[start:]))
 
 
-@pytest.mark.parametrize("K", [1, 2])
-def test_refined_adjoint_matches_oracle_finite_differences(H, K):
-    """Two levels (refinement box with the mesh): band snapshots,
-    prolongation in time and space, restriction, sub-cycled finest steps."""
-    case = make_case("hlbm_mini2", aoa_deg=3.0)
+@pytest.mark.parametrize("name,K", [("hlbm_mini2", 1), ("hlbm_mini2", 2), ("hlbm_mini3", 1)])
+def test_refined_adjoint_matches_oracle_finite_differences(H, name, K):
+    """Two and three levels (nested refinement boxes, the finest with the
+    mesh): band snapshots, prolongation in time and space, restriction,
+    sub-cycled finer steps."""
+    case = make_case(name, aoa_deg=3.0)
     s = H.Solver(case, precision="fp64")
     s.step(1)
     s.forces()
@@ -241,7 +242,8 @@ def test_refined_adjoint_matches_oracle_finite_differences(H, K):
     dirs = [rng.standard_normal(g.shape) * 1e-3 for g in gls]
     dmesh = rng.standard_normal(gm.shape) * 1e-3
     h = 1e-4
-    cases = [([dirs[0], None], None), ([None, dirs[1]], None), (None, dmesh)]
+    cases = [([d if i == l else None for i, d in enumerate(dirs)], None) for l in range(len(dirs))]
+    cases.append((None, dmesh))
     for dl, dm in cases:
         fd = (_oracle_mean_force_levels(case, K, 1.0, 0.3, dl, dm, h) -
               _oracle_mean_force_levels(case, K, 1.0, 0.3, dl, dm, -h)) / (2 * h)

@@ -65,7 +65,7 @@ def compare_fields(sol, orc_sim, case, tol):
 
 @pytest.mark.parametrize("name,steps,aoa", [("channel", 200, 0.0), ("hlbm_small", 100, 0.0),
                                             ("hlbm_small", 20, 8.0), ("hlbm_mini2", 100, 0.0),
-                                            ("hlbm_mini2", 30, 5.0)])
+                                            ("hlbm_mini2", 30, 5.0), ("hlbm_mini3", 40, 3.0)])
 def test_fp64_matches_oracle(H, orc, name, steps, aoa):
     case = make_case(name, aoa_deg=aoa)
     sol = H.Solver(case, precision="fp64")

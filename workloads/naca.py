@@ -242,6 +242,13 @@ CONFIGS = {
         "hlbm_mini2", [[96, 48, 0, 0], [97, 65, 24, 8]], chord=24.0, mid=(40.0, 32.0),
         n_theta=48, n_layers=20, stretch=1.08, ell_b_ratio=0.6, overlap=4.0,
         Re=200.0, Ma=0.1, aoa_deg=0.0, steps=100),
+    # Three-level mini case (two nested refinement boxes) for parity and
+    # adjoint tests: 64x40 coarse level, an 81x57 box and the 97x65 finest box
+    # of hlbm_mini2 inside it, chord 24 finest units.
+    "hlbm_mini3": lambda: _mesh_case(
+        "hlbm_mini3", [[64, 40, 0, 0], [81, 57, 12, 6], [97, 65, 16, 12]], chord=24.0, mid=(40.0, 32.0),
+        n_theta=48, n_layers=20, stretch=1.08, ell_b_ratio=0.6, overlap=4.0,
+        Re=200.0, Ma=0.1, aoa_deg=0.0, steps=100),
     # Single case: 2048x1024 coarse level with two nested factor-2 boxes of
     # 1025x513 nodes, chord 200 finest units, 1024 x 196-ring O-mesh
     # (200 704 nodes), Re 1000, Ma 0.1.

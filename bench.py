@@ -351,7 +351,7 @@ def main():
         s6.sync()
         t_fwd6 = time.perf_counter() - t6f
         t6 = time.perf_counter()
-        J6, gl6, gm6 = s6.adjoint(100, 1.0, 0.0)
+        J6, gl6, gm6, gx6, da6 = s6.adjoint(100, 1.0, 0.0)
         gl6 = gl6[0]
         t_adj6 = time.perf_counter() - t6
         s6.close()
@@ -360,8 +360,9 @@ def main():
             "seconds": t_adj6, "forward_seconds_graphs": t_fwd6, "ratio_to_forward": t_adj6 / t_fwd6,
             "checkpointing": "sqrt: 10 segments of 10 steps; each segment re-run once, each step once more "
                              "while recorded", "J_mean_cd": J6,
-            "grad_norm_lattice": float((gl6 ** 2).sum() ** 0.5), "grad_norm_mesh": float((gm6 ** 2).sum() ** 0.5)}
-        del gl6, gm6
+            "grad_norm_lattice": float((gl6 ** 2).sum() ** 0.5), "grad_norm_mesh": float((gm6 ** 2).sum() ** 0.5),
+            "dJ_daoa_per_deg": da6, "dJ_dthickness_modes": [float((gx6 * f).sum()) for f in thickness_modes(small)]}
+        del gl6, gm6, gx6
         # the same on the refined three-level layout (config 2: 2048 x 1024 plus
         # two nested boxes, 200 704-node mesh), 10 coarse steps
         s7 = H.Solver(case, precision="fp64", use_graphs=True)
@@ -372,15 +373,16 @@ def main():
         s7.sync()
         t_fwd7 = time.perf_counter() - t7f
         t7 = time.perf_counter()
-        J7, gl7, gm7 = s7.adjoint(10, 1.0, 0.0)
+        J7, gl7, gm7, gx7, da7 = s7.adjoint(10, 1.0, 0.0)
         t_adj7 = time.perf_counter() - t7
         s7.close()
         line["adjoint"]["refined"] = {
             "workload": f"{WORKLOAD}, FP64", "coarse_steps": 10, "seconds": t_adj7,
             "forward_seconds_graphs": t_fwd7, "ratio_to_forward": t_adj7 / t_fwd7, "J_mean_cd": J7,
             "grad_norm_levels": [float((g ** 2).sum() ** 0.5) for g in gl7],
-            "grad_norm_mesh": float((gm7 ** 2).sum() ** 0.5)}
-        del gl7, gm7
+            "grad_norm_mesh": float((gm7 ** 2).sum() ** 0.5), "dJ_daoa_per_deg": da7,
+            "dJ_dthickness_modes": [float((gx7 * f).sum()) for f in thickness_modes(case)]}
+        del gl7, gm7, gx7
         # ---- the large-Re configuration (1.5 M-node mesh): the finite-volume
         # state (~250 MB per sub-step) no longer fits in L2, so this is the
         # HBM-bound case; reported beside the headline, not as it

@@ -284,14 +284,21 @@ int hlbm_wall_stats_reset(hlbm_ctx *ctx);
  * level after level, each [ny][nx][9] (cap_lat >= 9 sum_l nx_l ny_l; 0 on
  * nodes that are not computed); if grad_mesh is not NULL, dJ/d(mesh
  * populations), [n_nodes][9] in input node order (cap_mesh >= 9 n_nodes; 0
- * on interface rows, which are overwritten before they are read).  Scratch:
+ * on interface rows, which are overwritten before they are read); if
+ * grad_xy is not NULL, dJ/dx of the mesh node coordinates, [n_nodes][2] in
+ * input node order and frame (cap_xy >= 2 n_nodes), and if dJ_daoa is not
+ * NULL, dJ/d(angle of attack) per degree: through the Eq. 3 operators, the
+ * wall normals, the Eq. 8 weights (donor positions) and the Eq. 9 weights
+ * (interface node positions), with the initial state held, the discrete
+ * choices (containing triangles, donor blocks, hole nodes) held and the
+ * lattice fixed in space.  Scratch:
  * about 2 sqrt(n_steps) + 2 copies of the whole state plus one coarse step's
  * records, allocated and freed through the context's allocator.
  * Synchronises the context's stream.  Errors: HLBM_ENOTIMPL (not FP64),
  * HLBM_EINVAL (no mesh, n_steps < 1, capacities), HLBM_EUNSTABLE (NaN in a
  * forward force), HLBM_ESTATE, HLBM_ENOMEM, HLBM_ECUDA. */
 int hlbm_adjoint(hlbm_ctx *ctx, int n_steps, double wd, double wl, double *J, double *grad_lattice, size_t cap_lat,
-                 double *grad_mesh, size_t cap_mesh);
+                 double *grad_mesh, size_t cap_mesh, double *grad_xy, size_t cap_xy, double *dJ_daoa);
 
 int hlbm_fv_adjoint(hlbm_ctx *ctx, int n_window, double wd, double wl, double *J, double *grad_g, size_t cap_g,
                     double *grad_coef, size_t cap_coef, double *grad_xy, size_t cap_xy, double *dJ_daoa);

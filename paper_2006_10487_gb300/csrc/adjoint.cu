@@ -420,7 +420,7 @@ __global__ void k_adj_abar(const int *prow, const double *pcoef, const double *g
 // dJ/dn_e of each wall edge: the traction -(p - p0) n - Pi^neq n of the final
 // state contracted with (wd, wl) / q
 __global__ void k_adj_wall_normal(const double *g, int Np, const int *inv, const int *iwea, const int *iweb,
-                                  int n_edges, double wd, double wl, double inv_q, double *h)
+                                  int n_edges, double wd, double wl, double inv_q, int add, double *h)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_edges) return;
@@ -438,8 +438,8 @@ __global__ void k_adj_wall_normal(const double *g, int Np, const int *inv, const
     }
     const double pm = p - 1.0 / 3.0;
     // J_e = inv_q [wd (-pm n_x - pxx n_x - pxy n_y) + wl (-pm n_y - pxy n_x - pyy n_y)]
-    h[2 * e] = inv_q * (wd * (-pm - pxx) - wl * pxy);
-    h[2 * e + 1] = inv_q * (-wd * pxy + wl * (-pm - pyy));
+    h[2 * e] = (add ? h[2 * e] : 0.0) + inv_q * (wd * (-pm - pxx) - wl * pxy);
+    h[2 * e + 1] = (add ? h[2 * e + 1] : 0.0) + inv_q * (-wd * pxy + wl * (-pm - pyy));
 }
 
 __device__ __forceinline__ int find_entry(const int *prow, const int *pcol, int row, int c)
@@ -524,10 +524,13 @@ __global__ void k_adj_shape(const AdjTables A, int n, const double *gc, const do
     }
     gpos[2 * X] = gx;
     gpos[2 * X + 1] = gy;
+    if (!grad_xy) return;
     // input frame: x_posed - p = R (x - p), R = [[ca, sa], [-sa, ca]]; dJ/dx = R^T dJ/dx_posed
     grad_xy[2 * size_t(X)] = ca * gx - sa * gy;
     grad_xy[2 * size_t(X) + 1] = sa * gx + ca * gy;
 }
+
+
 
 // dJ/dalpha (per degree): sum_X dJ/dx_posed . d x_posed / d alpha, with
 // x_posed - p = R(alpha) (x - p): d/dalpha = (-sa dx + ca dy, -sa dy - ca dx)
@@ -715,7 +718,7 @@ __global__ void __launch_bounds__(128) k_adj_ring_lattice(const double *f, int n
 // donor k) (mesh state g); their cotangents -> lamq[12][n_is], and end there.
 template <int P>
 __global__ void k_adj_hole_q(const double *g, int Np, const int *is_n, const int *is_don, const double *is_w,
-                             int n_is, double scale4, int pitch, size_t stride, double *lam, double *lamq)
+                             int n_is, double scale4, int pitch, size_t stride, double *lam, double *lamq, double *lw6)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_is) return;
@@ -744,6 +747,14 @@ __global__ void k_adj_hole_q(const double *g, int Np, const int *is_n, const int
         lq[3 + i] = scale4 * lo;
     }
     for (int m = 0; m < 12; m++) lamq[size_t(m) * n_is + s] = lq[m];
+    if (lw6)  // dJ/d(weight k) += q(donor k) . lamq
+        for (int k = 0; k < 6; k++) {
+            Dual r, ux, uy, nq[9];
+            load(g, Np, is_don[6 * s + k], false, r, ux, uy, nq);
+            double dot = lq[0] * r.v + lq[1] * ux.v + lq[2] * uy.v;
+            for (int i = 0; i < 9; i++) dot += lq[3 + i] * nq[i].v;
+            lw6[6 * s + k] += dot;
+        }
 }
 
 // Part 2 (per mesh node): q(mesh node) = (1 + r1, u, f^neq_0..8), the last
@@ -942,6 +953,117 @@ __global__ void k_adj_restrict(const double *ff, int pitch_c, size_t stride_c, i
     for (int k = 0; k < 9; k++) lamf[lst<PF>(k, nf, pitch_f, stride_f)] += d[k];
 }
 
+// ---------------------------------- geometry through the coupled step ----
+// Eq. 9 weights: dJ/d(w_rk) += q(lattice donor k at parity P) . lamQ(r)
+template <int P>
+__global__ void k_adj_ring_weights(const double *f, int pitch, size_t stride, const int *ring_don,
+                                   const double *lamQ, int n_ring, double *lw9)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_ring) return;
+    for (int k = 0; k < 9; k++) {
+        Dual q[12];
+        lat_q<P>(f, size_t(ring_don[9 * r + k]), pitch, stride, q);
+        double dot = 0.0;
+        for (int m = 0; m < 12; m++) dot += q[m].v * lamQ[size_t(m) * n_ring + r];
+        lw9[9 * r + k] += dot;
+    }
+}
+
+// Eq. 8 weights reproduce {1, u, v, u^2, uv, v^2} at the interpolation node:
+// sum_k w_k m_j(x_k - x_s) = [j == 0] (a scaling of u, v leaves w unchanged).
+// With M_jk = m_j(d_k): dJ/dM = -z w^T, M^T z = dJ/dw, and dJ/dd_k =
+// -w_k sum_j z_j grad m_j(d_k).  Part 1, per interpolation node: z.
+__global__ void k_adj_eq8_solve(const int *isd_in, const double *is_xy, const double *pxy, const double *lw6, int n_is,
+                                double *zs)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_is) return;
+    double a[6][7];  // M^T | rhs
+    for (int k = 0; k < 6; k++) {
+        const int p = isd_in[6 * s + k];
+        const double u = pxy[2 * p] - is_xy[2 * s], v = pxy[2 * p + 1] - is_xy[2 * s + 1];
+        const double m[6] = {1.0, u, v, u * u, u * v, v * v};
+        for (int j = 0; j < 6; j++) a[k][j] = m[j];  // row k of M^T = column k of M
+        a[k][6] = lw6[6 * s + k];
+    }
+    for (int c = 0; c < 6; c++) {  // Gaussian elimination, partial pivoting
+        int piv = c;
+        for (int r = c + 1; r < 6; r++)
+            if (fabs(a[r][c]) > fabs(a[piv][c])) piv = r;
+        if (piv != c)
+            for (int j = 0; j < 7; j++) {
+                const double t = a[c][j];
+                a[c][j] = a[piv][j];
+                a[piv][j] = t;
+            }
+        for (int r = 0; r < 6; r++) {
+            if (r == c || a[c][c] == 0.0) continue;
+            const double f = a[r][c] / a[c][c];
+            for (int j = c; j < 7; j++) a[r][j] -= f * a[c][j];
+        }
+    }
+    for (int j = 0; j < 6; j++) zs[6 * s + j] = a[j][j] == 0.0 ? 0.0 : a[j][6] / a[j][j];
+}
+
+// Part 2, per mesh node (device order Q, input node perm[Q]): over the
+// (interpolation node s, donor position k) pairs that read it, add
+// -w_sk sum_j z_sj grad m_j(x_Q - x_s) to its posed-frame gradient.
+__global__ void k_adj_eq8_nodes(const int *hptr, const int *hent, const int *perm, const double *is_w,
+                                const double *is_xy, const double *pxy, const double *zs, int n, double *gpos)
+{
+    const int Q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (Q >= n || hptr[Q] == hptr[Q + 1]) return;
+    const int p = perm[Q];
+    double gx = 0.0, gy = 0.0;
+    for (int t = hptr[Q]; t < hptr[Q + 1]; t++) {
+        const int sidx = hent[t] / 6;
+        const double w = is_w[hent[t]];
+        const double u = pxy[2 * p] - is_xy[2 * sidx], v = pxy[2 * p + 1] - is_xy[2 * sidx + 1];
+        const double *z = zs + 6 * sidx;
+        // grad m: (0,0) (1,0) (0,1) (2u,0) (v,u) (0,2v)
+        gx -= w * (z[1] + 2.0 * u * z[3] + v * z[4]);
+        gy -= w * (z[2] + u * z[4] + 2.0 * v * z[5]);
+    }
+    gpos[2 * p] += gx;
+    gpos[2 * p + 1] += gy;
+}
+
+// Eq. 9 weights of ring node r: biquadratic Lagrange weights l_a(fx) l_b(fy)
+// of its offset from the nearest lattice node (held: a moved node keeps its
+// donors); add their position derivatives contracted with dJ/dw.
+__global__ void k_adj_eq9_nodes(const int *perm, int ring_start, int n_ring, const double *pxy, const double *lw9,
+                                double *gpos)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_ring) return;
+    const int p = perm[ring_start + r];
+    const double qx = pxy[2 * p], qy = pxy[2 * p + 1];
+    const double fx = qx - floor(qx + 0.5), fy = qy - floor(qy + 0.5);
+    const double lx[3] = {0.5 * fx * (fx - 1.0), 1.0 - fx * fx, 0.5 * fx * (fx + 1.0)};
+    const double ly[3] = {0.5 * fy * (fy - 1.0), 1.0 - fy * fy, 0.5 * fy * (fy + 1.0)};
+    const double dx[3] = {fx - 0.5, -2.0 * fx, fx + 0.5}, dy[3] = {fy - 0.5, -2.0 * fy, fy + 0.5};
+    double gx = 0.0, gy = 0.0;
+    for (int b = 0; b < 3; b++)
+        for (int a = 0; a < 3; a++) {
+            const double lw = lw9[9 * r + 3 * b + a];
+            gx += lw * dx[a] * ly[b];
+            gy += lw * lx[a] * dy[b];
+        }
+    gpos[2 * p] += gx;
+    gpos[2 * p + 1] += gy;
+}
+
+// posed-frame gradient -> input frame (x_posed - p = R (x - p))
+__global__ void k_adj_frame(const double *gpos, int n, double ca, double sa, double *grad_xy)
+{
+    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+    if (X >= n) return;
+    const double gx = gpos[2 * X], gy = gpos[2 * X + 1];
+    grad_xy[2 * size_t(X)] = ca * gx - sa * gy;
+    grad_xy[2 * size_t(X) + 1] = sa * gx + ca * gy;
+}
+
 }  // namespace
 
 void launch_adj_geometry(const AdjTables &A, int n, const double *gc, const double *gM, int Np, double wd, double wl,
@@ -952,7 +1074,7 @@ void launch_adj_geometry(const AdjTables &A, int n, const double *gc, const doub
     k_adj_abar<<<(n + 127) / 128, 128, 0, s>>>(A.prow, A.pcoef, gc, A.parea, n, abar);
     if (A.n_edges > 0)
         k_adj_wall_normal<<<(A.n_edges + 127) / 128, 128, 0, s>>>(gM, Np, A.inv, A.iwea, A.iweb, A.n_edges, wd, wl,
-                                                                 inv_q, h);
+                                                                 inv_q, 0, h);
     k_adj_shape<<<(n + 127) / 128, 128, 0, s>>>(A, n, gc, abar, h, ca, sa, gpos, grad_xy);
     k_adj_aoa<<<1, 256, 0, s>>>(A.pxy, gpos, n, ca, sa, px, py, daoa);
 }
@@ -1026,17 +1148,17 @@ void launch_adj_ring_lattice(const DevLevel &l, const double *f, int P, const Ad
 }
 
 void launch_adj_hole(const DevLevel &l, const DevMesh &m, const AdjTables &A, const double *g, int P, double *lam,
-                     double *lamq, double *lam_g, cudaStream_t s)
+                     double *lamq, double *lam_g, cudaStream_t s, double *lw6)
 {
     if (m.n_is == 0) return;
     const double scale4 = 2.0 * (l.tau - 1.0) / (2.0 * l.tau - 1.0);
     const int b = (m.n_is + 127) / 128;
     if (P == 0)
         k_adj_hole_q<0><<<b, 128, 0, s>>>(g, m.Np, m.is_n, m.is_don, (const double *)m.is_w, m.n_is, scale4, l.pitch,
-                                          l.stride, lam, lamq);
+                                          l.stride, lam, lamq, lw6);
     else
         k_adj_hole_q<1><<<b, 128, 0, s>>>(g, m.Np, m.is_n, m.is_don, (const double *)m.is_w, m.n_is, scale4, l.pitch,
-                                          l.stride, lam, lamq);
+                                          l.stride, lam, lamq, lw6);
     k_adj_hole_mesh<<<(m.n + 127) / 128, 128, 0, s>>>(g, m.Np, m.n, A.hptr, A.hent, (const double *)m.is_w, lamq,
                                                       m.n_is, lam_g);
 }
@@ -1096,6 +1218,51 @@ void launch_adj_restrict(const DevLevel &p, const DevLevel &l, int PC, int PF, c
     else if (PF == 0) HLBM_ADJ_RESTRICT(1, 0);
     else HLBM_ADJ_RESTRICT(1, 1);
 #undef HLBM_ADJ_RESTRICT
+}
+
+}  // namespace hlbm
+
+namespace hlbm {
+
+void launch_adj_ring_weights(const DevLevel &l, const DevMesh &m, const double *f, int P, const double *lamQ,
+                             double *lw9, cudaStream_t s)
+{
+    if (m.n_ring == 0) return;
+    const int b = (m.n_ring + 127) / 128;
+    if (P == 0) k_adj_ring_weights<0><<<b, 128, 0, s>>>(f, l.pitch, l.stride, m.ring_don, lamQ, m.n_ring, lw9);
+    else k_adj_ring_weights<1><<<b, 128, 0, s>>>(f, l.pitch, l.stride, m.ring_don, lamQ, m.n_ring, lw9);
+}
+
+void launch_adj_geometry_coupled(const AdjTables &A, const DevMesh &m, int n, const double *gc, const double *hacc,
+                                 const double *lw6, const double *lw9, double ca, double sa, double px, double py,
+                                 double *scratch, double *grad_xy, double *daoa, cudaStream_t s)
+{
+    // scratch: abar [n], gpos [2 n], zs [6 n_is]
+    double *abar = scratch, *gpos = scratch + n, *zs = gpos + 2 * size_t(n);
+    const int b = (n + 127) / 128;
+    k_adj_abar<<<b, 128, 0, s>>>(A.prow, A.pcoef, gc, A.parea, n, abar);
+    k_adj_shape<<<b, 128, 0, s>>>(A, n, gc, abar, hacc, ca, sa, gpos, nullptr);
+    if (m.n_is > 0) {
+        k_adj_eq8_solve<<<(m.n_is + 127) / 128, 128, 0, s>>>(A.isd_in, A.is_xy, A.pxy, lw6, m.n_is, zs);
+        k_adj_eq8_nodes<<<b, 128, 0, s>>>(A.hptr, A.hent, A.perm, (const double *)m.is_w, A.is_xy, A.pxy, zs, n,
+                                          gpos);
+    }
+    if (m.n_ring > 0)
+        k_adj_eq9_nodes<<<(m.n_ring + 127) / 128, 128, 0, s>>>(A.perm, m.ring_start, m.n_ring, A.pxy, lw9, gpos);
+    if (grad_xy) k_adj_frame<<<b, 128, 0, s>>>(gpos, n, ca, sa, grad_xy);
+    k_adj_aoa<<<1, 256, 0, s>>>(A.pxy, gpos, n, ca, sa, px, py, daoa);
+}
+
+}  // namespace hlbm
+
+namespace hlbm {
+
+void launch_adj_wall_normal(const AdjTables &A, const double *g, int Np, double wd, double wl, double inv_q,
+                            double *hacc, cudaStream_t s)
+{
+    if (A.n_edges > 0)
+        k_adj_wall_normal<<<(A.n_edges + 127) / 128, 128, 0, s>>>(g, Np, A.inv, A.iwea, A.iweb, A.n_edges, wd, wl,
+                                                                 inv_q, 1, hacc);
 }
 
 }  // namespace hlbm

@@ -1315,6 +1315,15 @@ void build_coupled_tables(hlbm_ctx *c)
     A.lent = upload(c, lent);
     A.hptr = upload(c, hptr);
     A.hent = upload(c, hent);
+    {
+        std::vector<double> isxy(2 * P.is_node.size());
+        for (size_t k = 0; k < P.is_node.size(); k++) {
+            isxy[2 * k] = double(P.is_node[k] % F.nx);
+            isxy[2 * k + 1] = double(P.is_node[k] / F.nx);
+        }
+        A.isd_in = upload(c, P.is_don);
+        A.is_xy = upload(c, isxy);
+    }
     // prolongation into level l: each fine perimeter node reads 1 (even
     // position) or 3 (odd: weights -1/8, 3/4, 3/8) band entries of level l - 1
     for (int l = 1; l < P.L; l++) {
@@ -1449,7 +1458,7 @@ int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, 
 }
 
 int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, double *grad_lattice, size_t cap_lat,
-                 double *grad_mesh, size_t cap_mesh)
+                 double *grad_mesh, size_t cap_mesh, double *grad_xy, size_t cap_xy, double *dJ_daoa)
 {
     if (!c) return HLBM_EINVAL;
     const Plan &P = c->plan;
@@ -1461,8 +1470,10 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
     for (int l = 0; l < P.L; l++) lat_total += 9 * size_t(P.lv[l].nx) * P.lv[l].ny;
     if (grad_lattice && cap_lat < lat_total) return fail(c, HLBM_EINVAL, "grad_lattice capacity below 9 sum nx ny");
     if (grad_mesh && cap_mesh < 9 * size_t(P.n)) return fail(c, HLBM_EINVAL, "grad_mesh capacity below 9 n");
+    if (grad_xy && cap_xy < 2 * size_t(P.n)) return fail(c, HLBM_EINVAL, "grad_xy capacity below 2 n");
     if (c->timing_dirty) return fail(c, HLBM_ESTATE, "the state was consumed by hlbm_time_kernel");
     Range r("hlbm_adjoint");
+    const bool geo = grad_xy || dJ_daoa;
     const int K = n_steps, n = P.n, ns = P.n_sub, L = P.L;
     const long k0 = c->steps;
     std::vector<void *> scratch;
@@ -1589,6 +1600,21 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
         double *rs = scr(3 * plane * sizeof(double));
         double *gg = scr(9 * size_t(n) * sizeof(double));
         double *gl = grad_lattice ? scr(lat_total * sizeof(double)) : nullptr;
+        // geometry cotangents accumulated over the steps: Eq. 3 entries (gc),
+        // wall-edge normals, Eq. 8 and Eq. 9 weights
+        const size_t nis = size_t(std::max(1, D0.m.n_is)), nwe = size_t(std::max(1, D0.m.n_edges));
+        double *hacc = geo ? scr(2 * nwe * sizeof(double)) : nullptr;
+        double *lw6 = geo ? scr(6 * nis * sizeof(double)) : nullptr;
+        double *lw9 = geo ? scr(9 * size_t(nr) * sizeof(double)) : nullptr;
+        double *gxy = grad_xy ? scr(2 * size_t(n) * sizeof(double)) : nullptr;
+        double *gsc = geo ? scr((3 * size_t(n) + 6 * nis) * sizeof(double)) : nullptr;
+        double *daoa = scr(sizeof(double));
+        ck(cudaMemsetAsync(gc, 0, std::max<size_t>(1, 3 * P.col.size()) * sizeof(double), s), "memset");
+        if (geo) {
+            ck(cudaMemsetAsync(hacc, 0, 2 * nwe * sizeof(double), s), "memset");
+            ck(cudaMemsetAsync(lw6, 0, 6 * nis * sizeof(double), s), "memset");
+            ck(cudaMemsetAsync(lw9, 0, 9 * size_t(nr) * sizeof(double), s), "memset");
+        }
         ck(cudaMemsetAsync(lam_g, 0, plane * sizeof(double), s), "memset");
         ck(cudaMemsetAsync(st, 0, (size_t(ns) + 1) * plane * sizeof(double), s), "memset");
         ck(cudaMemsetAsync(lQ0, 0, qn * sizeof(double), s), "memset");
@@ -1623,6 +1649,7 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
                 }
                 if (terminal) {  // the coarse step's force sample
                     launch_adj_terminal(A, st + size_t(ns) * plane, Np, n, wd / K, wl / K, inv_q, lam_g, s, true);
+                    if (geo) launch_adj_wall_normal(A, st + size_t(ns) * plane, Np, wd / K, wl / K, inv_q, hacc, s);
                     terminal = false;
                 }
                 double *lin = lam_g, *lout = lam_t;
@@ -1635,6 +1662,7 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
                 }
                 launch_adj_ring_rows(D0.m, scale5, 1.0, 0.0, lin, lQ0, lQ1, s);
                 if (lin != lam_g) std::swap(lam_g, lam_t);
+                if (geo) launch_adj_ring_weights(dl, D0.m, R.f_end, Pk ^ 1, lQ1, lw9, s);
                 launch_adj_ring_lattice(dl, R.f_end, Pk ^ 1, A, ring_w, lQ1, D0.m.n_ring, lam_f[l], s);
             }
             if (l == 0) launch_adj_outer_bc(dl, R.f_end, Pk ^ 1, P.u0, lam_f[0], s);
@@ -1643,7 +1671,8 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
                                    lamp, lsA[l - 1], lsB[l - 1], s);
             launch_adj_collide(dl, R.f_start, Pk, lam_f[l], s);
             if (l == fin) {
-                launch_adj_hole(dl, D0.m, A, R.g_start, Pk, lam_f[l], lamq, lam_g, s);
+                launch_adj_hole(dl, D0.m, A, R.g_start, Pk, lam_f[l], lamq, lam_g, s, lw6);
+                if (geo) launch_adj_ring_weights(dl, D0.m, R.f_start, Pk, lQ0, lw9, s);
                 launch_adj_ring_lattice(dl, R.f_start, Pk, A, ring_w, lQ0, D0.m.n_ring, lam_f[l], s);
                 ck(cudaMemsetAsync(lQ0, 0, qn * sizeof(double), s), "memset");
                 ck(cudaMemsetAsync(lQ1, 0, qn * sizeof(double), s), "memset");
@@ -1712,7 +1741,14 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
             }
         }
         launch_adj_populations(A, (const double *)W.m.g[W.m.gcur], Np, n, lam_g, gg, s);
+        if (geo) {
+            const double al = P.aoa_deg * M_PI / 180.0;
+            launch_adj_geometry_coupled(A, D0.m, n, gc, hacc, lw6, lw9, std::cos(al), std::sin(al), P.pivot[0],
+                                        P.pivot[1], gsc, gxy, daoa, s);
+        }
         ck(cudaGetLastError(), "adjoint kernels");
+        if (grad_xy) ck(cudaMemcpyAsync(grad_xy, gxy, 2 * size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
+        if (dJ_daoa) ck(cudaMemcpyAsync(dJ_daoa, daoa, sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         if (gl) ck(cudaMemcpyAsync(grad_lattice, gl, lat_total * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         if (grad_mesh) ck(cudaMemcpyAsync(grad_mesh, gg, 9 * size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         ck(cudaStreamSynchronize(s), "sync");

@@ -150,6 +150,10 @@ struct AdjTables {
     // each band entry of level l - 1, pk[l][pp[l][b] ..), weights pw[l]
     int *pp[8] = {}, *pk[8] = {};
     double *pw[8] = {};
+    // Eq. 8 stencils in input order: donors [n_is][6] and the interpolation
+    // nodes' lattice coordinates [n_is][2] (finest units)
+    int *isd_in = nullptr;
+    double *is_xy = nullptr;
     bool coupled_built = false;
 };
 void launch_adj_value(const AdjTables &, const double *g, int Np, double wd, double wl, double inv_q, double *J,
@@ -176,11 +180,23 @@ void launch_adj_outer_bc(const DevLevel &, const double *f, int P, double u0, do
 void launch_adj_ring_lattice(const DevLevel &, const double *f, int P, const AdjTables &, const double *ring_w,
                              const double *lamQ, int n_ring, double *lam, cudaStream_t);
 // lamq: 12 n_is doubles of scratch
+// lw6 (optional): dJ/d(Eq. 8 weights) [n_is][6], accumulated
 void launch_adj_hole(const DevLevel &, const DevMesh &, const AdjTables &, const double *g, int P, double *lam,
-                     double *lamq, double *lam_g, cudaStream_t);
+                     double *lamq, double *lam_g, cudaStream_t, double *lw6 = nullptr);
 void launch_adj_ring_rows(const DevMesh &, double scale5, double wa, double wb, double *lam_g, double *lamQ0,
                           double *lamQ1, cudaStream_t);
 void launch_adj_lattice_out(const DevLevel &, const double *lam, int P, double *grad, cudaStream_t);
+// geometry through the coupled step: Eq. 9 weight cotangents (accumulated),
+// then dJ/dx (input frame) and dJ/d(angle of attack) from the accumulated
+// entry, wall-normal (hacc [n_wall_edges][2]), Eq. 8 and Eq. 9 weight
+// cotangents; scratch: 3 n + 6 n_is doubles
+void launch_adj_ring_weights(const DevLevel &, const DevMesh &, const double *f, int P, const double *lamQ, double *lw9,
+                             cudaStream_t);
+void launch_adj_geometry_coupled(const AdjTables &, const DevMesh &, int n, const double *gc, const double *hacc,
+                                 const double *lw6, const double *lw9, double ca, double sa, double px, double py,
+                                 double *scratch, double *grad_xy, double *daoa, cudaStream_t);
+void launch_adj_wall_normal(const AdjTables &, const double *g, int Np, double wd, double wl, double inv_q,
+                            double *hacc, cudaStream_t);
 // refinement interface: band snapshot of parent l, prolongation into l (lamq:
 // 12 x perimeter(l) doubles of scratch), restriction into parent p from l
 void launch_adj_snapshot(const DevLevel &, const double *f, int P, const double *lamS, double *lam, cudaStream_t);

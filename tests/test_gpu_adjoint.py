@@ -174,7 +174,7 @@ def _oracle_mean_force(case, K, wd, wl, dlat=None, dmesh=None, h=0.0):
 def test_coupled_adjoint_matches_oracle_finite_differences(H, small, K, wd, wl):
     case, s = small
     before = [a.copy() for a in s.fields(0)] + [a.copy() for a in s.fields(-1)]
-    J, (gl,), gm = s.adjoint(K, wd, wl)
+    J, (gl,), gm, _, _ = s.adjoint(K, wd, wl)
     after = list(s.fields(0)) + list(s.fields(-1))
     for a, b in zip(before, after):
         assert np.array_equal(a, b, equal_nan=True)
@@ -194,7 +194,7 @@ def test_coupled_adjoint_value_is_the_next_force_samples(H, small):
     """J is the mean of the force samples the solver records over the same
     steps (the adjoint's forward replays the step on scratch copies)."""
     case, s = small
-    J, _, _ = s.adjoint(2, 1.0, 0.5)
+    J = s.adjoint(2, 1.0, 0.5)[0]
     t = H.Solver(case, precision="fp64")
     t.step(1)
     t.forces()
@@ -236,7 +236,7 @@ def test_refined_adjoint_matches_oracle_finite_differences(H, name, K):
     s = H.Solver(case, precision="fp64")
     s.step(1)
     s.forces()
-    J, gls, gm = s.adjoint(K, 1.0, 0.3)
+    J, gls, gm, _, _ = s.adjoint(K, 1.0, 0.3)
     assert abs(J - _oracle_mean_force_levels(case, K, 1.0, 0.3)) <= 1e-10 * max(1.0, abs(J))
     rng = np.random.default_rng(30 + K)
     dirs = [rng.standard_normal(g.shape) * 1e-3 for g in gls]
@@ -252,3 +252,40 @@ def test_refined_adjoint_matches_oracle_finite_differences(H, name, K):
         else:
             ad = sum(float(np.nansum(g * d)) for g, d in zip(gls, dl) if d is not None)
         assert abs(ad - fd) <= 1e-6 * abs(fd) + 1e-10, (K, ad, fd)
+
+
+def _oracle_moved(case, K, wd, wl, dxy=None, daoa=0.0, h=0.0):
+    """Mean of wd C_D + wl C_L over the first K coarse steps of the oracle
+    built on moved geometry (node coordinates + h dxy, angle + h daoa)."""
+    import dataclasses
+    import oracle
+    moved = dataclasses.replace(case, xy=case.xy + (h * dxy if dxy is not None else 0.0),
+                                aoa_deg=case.aoa_deg + h * daoa)
+    o = oracle.Oracle(moved)
+    o.step(K)
+    cd, cl = o.forces()
+    return float(np.mean(wd * cd + wl * cl))
+
+
+@pytest.mark.parametrize("name", ["hlbm_small", "hlbm_mini2"])
+def test_coupled_shape_gradients_match_oracle(H, name):
+    """dJ/dx of the mesh nodes, dJ/d(angle of attack) and dJ/dA_m of the
+    thickness bumps through whole coarse steps from the initial state (Eq. 3
+    operators, wall normals, Eq. 8 and Eq. 9 weights), against central
+    differences of the oracle rebuilt on moved geometry."""
+    from workloads import thickness_modes
+    case = make_case(name, aoa_deg=3.0)
+    K, wd, wl = 2, 1.0, 0.5
+    s = H.Solver(case, precision="fp64")
+    J, _, _, gx, da = s.adjoint(K, wd, wl)
+    assert abs(J - _oracle_moved(case, K, wd, wl)) <= 1e-10 * max(1.0, abs(J))
+    h = 1e-6
+    modes = thickness_modes(case)
+    dirs = [modes[0], modes[5], np.random.default_rng(5).standard_normal((case.n_nodes, 2))]
+    for d in dirs:
+        fd = (_oracle_moved(case, K, wd, wl, dxy=d, h=h) - _oracle_moved(case, K, wd, wl, dxy=d, h=-h)) / (2 * h)
+        ad = float(np.sum(gx * d))
+        assert abs(ad - fd) <= 1e-5 * abs(fd) + 1e-8, (name, ad, fd)
+    ha = 1e-4
+    fd = (_oracle_moved(case, K, wd, wl, daoa=1.0, h=ha) - _oracle_moved(case, K, wd, wl, daoa=1.0, h=-ha)) / (2 * ha)
+    assert abs(da - fd) <= 1e-5 * abs(fd) + 1e-8, (name, da, fd)

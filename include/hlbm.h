@@ -273,9 +273,10 @@ int hlbm_wall_stats_reset(hlbm_ctx *ctx);
  * finest level the Eq. 4 + 8 hole nodes, the Eq. 9 interface data with the
  * Eq. 5-7 interface rows at their sub-step times, the Eq. 3 sub-steps with
  * the wall rule; and the force of every coarse step:
- *   J = (1/n_steps) sum_k (wd C_D(k) + wl C_L(k)),
- * the mean over the n_steps force samples that hlbm_step would record from
- * the current state.  The forward steps run on scratch copies (the context's
+ *   J = 1/(n_steps - n_skip) sum_{k = n_skip .. n_steps-1} (wd C_D(k) + wl C_L(k)),
+ * the mean of the last n_steps - n_skip of the n_steps force samples that
+ * hlbm_step would record from the current state (0 <= n_skip < n_steps; the
+ * first n_skip steps are differentiated through, their forces not averaged).  The forward steps run on scratch copies (the context's
  * state and force series do not change).  Recomputation checkpointing: the
  * state at every ceil(sqrt(n_steps))-th step start is kept, each segment is
  * re-run once keeping its step starts, and each step once more while its
@@ -297,8 +298,8 @@ int hlbm_wall_stats_reset(hlbm_ctx *ctx);
  * Synchronises the context's stream.  Errors: HLBM_ENOTIMPL (not FP64),
  * HLBM_EINVAL (no mesh, n_steps < 1, capacities), HLBM_EUNSTABLE (NaN in a
  * forward force), HLBM_ESTATE, HLBM_ENOMEM, HLBM_ECUDA. */
-int hlbm_adjoint(hlbm_ctx *ctx, int n_steps, double wd, double wl, double *J, double *grad_lattice, size_t cap_lat,
-                 double *grad_mesh, size_t cap_mesh, double *grad_xy, size_t cap_xy, double *dJ_daoa);
+int hlbm_adjoint(hlbm_ctx *ctx, int n_steps, int n_skip, double wd, double wl, double *J, double *grad_lattice,
+                 size_t cap_lat, double *grad_mesh, size_t cap_mesh, double *grad_xy, size_t cap_xy, double *dJ_daoa);
 
 int hlbm_fv_adjoint(hlbm_ctx *ctx, int n_window, double wd, double wl, double *J, double *grad_g, size_t cap_g,
                     double *grad_coef, size_t cap_coef, double *grad_xy, size_t cap_xy, double *dJ_daoa);

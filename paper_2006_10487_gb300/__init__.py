@@ -78,8 +78,8 @@ def lib():
                                               C.c_double, C.c_void_p, C.c_void_p]
         L.hlbm_fv_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, dp, dp, C.c_size_t, dp,
                                       C.c_size_t, dp, C.c_size_t, dp]
-        L.hlbm_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, dp, dp, C.c_size_t, dp, C.c_size_t,
-                                   dp, C.c_size_t, dp]
+        L.hlbm_adjoint.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, dp, dp, C.c_size_t, dp,
+                                   C.c_size_t, dp, C.c_size_t, dp]
         L.hlbm_sync.argtypes = [C.c_void_p]
         L.hlbm_destroy.argtypes = [C.c_void_p]
         L.hlbm_last_error.argtypes = [C.c_void_p]
@@ -213,9 +213,10 @@ class Solver:
                                          gx.ctypes.data_as(dp), gx.size, da.ctypes.data_as(dp)), self.ctx)
         return float(J[0]), gg, gc, gx, float(da[0])
 
-    def adjoint(self, n_steps, wd=1.0, wl=0.0):
+    def adjoint(self, n_steps, wd=1.0, wl=0.0, skip=0):
         """Discrete adjoint of n_steps coarse steps of an FP64 solver
-        (hlbm_adjoint): J = mean of wd C_D + wl C_L over the steps, the
+        (hlbm_adjoint): J = mean of wd C_D + wl C_L over the steps after the
+        first `skip`, the
         gradients in every level's lattice populations (a list, level order,
         each [ny * nx, 9]) and in the mesh populations [n_nodes, 9] of the
         current state, dJ/dx of the mesh node coordinates [n_nodes, 2] (input
@@ -224,7 +225,7 @@ class Solver:
         J, da = np.zeros(1), np.zeros(1)
         gl, gm, gx = np.empty((sum(sizes), 9)), np.empty((self.case.n_nodes, 9)), np.empty((self.case.n_nodes, 2))
         dp = C.POINTER(C.c_double)
-        _check(self._lib.hlbm_adjoint(self.ctx, int(n_steps), float(wd), float(wl), J.ctypes.data_as(dp),
+        _check(self._lib.hlbm_adjoint(self.ctx, int(n_steps), int(skip), float(wd), float(wl), J.ctypes.data_as(dp),
                                       gl.ctypes.data_as(dp), gl.size, gm.ctypes.data_as(dp), gm.size,
                                       gx.ctypes.data_as(dp), gx.size, da.ctypes.data_as(dp)), self.ctx)
         parts = np.split(gl, np.cumsum(sizes)[:-1])

@@ -1457,14 +1457,15 @@ int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, 
     return rc;
 }
 
-int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, double *grad_lattice, size_t cap_lat,
-                 double *grad_mesh, size_t cap_mesh, double *grad_xy, size_t cap_xy, double *dJ_daoa)
+int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, double *J, double *grad_lattice,
+                 size_t cap_lat, double *grad_mesh, size_t cap_mesh, double *grad_xy, size_t cap_xy, double *dJ_daoa)
 {
     if (!c) return HLBM_EINVAL;
     const Plan &P = c->plan;
     if (P.precision != HLBM_FP64) return fail(c, HLBM_ENOTIMPL, "the adjoint runs on FP64 contexts");
     if (P.n == 0) return fail(c, HLBM_EINVAL, "the context has no mesh");
     if (n_steps < 1) return fail(c, HLBM_EINVAL, "n_steps must be >= 1");
+    if (n_skip < 0 || n_skip >= n_steps) return fail(c, HLBM_EINVAL, "n_skip must be in 0..n_steps-1");
     if (!J) return fail(c, HLBM_EINVAL, "J is NULL");
     size_t lat_total = 0;  // populations of all levels
     for (int l = 0; l < P.L; l++) lat_total += 9 * size_t(P.lv[l].nx) * P.lv[l].ny;
@@ -1475,6 +1476,7 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
     Range r("hlbm_adjoint");
     const bool geo = grad_xy || dJ_daoa;
     const int K = n_steps, n = P.n, ns = P.n_sub, L = P.L;
+    const double wavg = 1.0 / (K - n_skip);  // weight of each averaged force sample
     const long k0 = c->steps;
     std::vector<void *> scratch;
     auto scr = [&](size_t bytes) {
@@ -1648,8 +1650,9 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
                     launch_fv<double, double>(V, m, s);
                 }
                 if (terminal) {  // the coarse step's force sample
-                    launch_adj_terminal(A, st + size_t(ns) * plane, Np, n, wd / K, wl / K, inv_q, lam_g, s, true);
-                    if (geo) launch_adj_wall_normal(A, st + size_t(ns) * plane, Np, wd / K, wl / K, inv_q, hacc, s);
+                    launch_adj_terminal(A, st + size_t(ns) * plane, Np, n, wd * wavg, wl * wavg, inv_q, lam_g, s, true);
+                    if (geo)
+                        launch_adj_wall_normal(A, st + size_t(ns) * plane, Np, wd * wavg, wl * wavg, inv_q, hacc, s);
                     terminal = false;
                 }
                 double *lin = lam_g, *lout = lam_t;
@@ -1723,7 +1726,7 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
             c->rec = nullptr;
             std::copy(side0, side0 + hlbm::kMaxLevels, c->side_ok);
             if (rec.recs.size() != subtree[0]) throw CudaError{"unexpected level-step count in the recorded step"};
-            terminal = true;
+            terminal = k >= n_skip;  // the step's force sample is averaged
             rev(0, 0);
             ck(cudaStreamSynchronize(s), "sync");  // the records are freed next
             rec.release();
@@ -1753,8 +1756,8 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, double wd, double wl, double *J, doub
         if (grad_mesh) ck(cudaMemcpyAsync(grad_mesh, gg, 9 * size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H");
         ck(cudaStreamSynchronize(s), "sync");
         double jsum = 0.0;
-        for (int k = 0; k < K; k++) jsum += wd * fb[2 * size_t(k)] + wl * fb[2 * size_t(k) + 1];
-        *J = jsum / K;
+        for (int k = n_skip; k < K; k++) jsum += wd * fb[2 * size_t(k)] + wl * fb[2 * size_t(k) + 1];
+        *J = jsum * wavg;
         if (flag & 2) rc = fail(c, HLBM_ETIMEOUT, "a device-side wait gave up (operator copy did not arrive)");
         else if (flag) rc = fail(c, HLBM_EUNSTABLE, "NaN in the force reduction of the forward steps");
     } catch (const CudaError &e) {

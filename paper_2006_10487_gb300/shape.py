@@ -1,8 +1,8 @@
 """Time-averaged lift and drag as differentiable functions of the airfoil
 shape and incidence, for PyTorch optimisers.
 
-`mean_force(case, amplitudes, aoa_deg, n_steps, wd, wl)` returns J = mean over
-the first n_steps coarse steps of wd C_D + wl C_L for the case's geometry
+`mean_force(case, amplitudes, aoa_deg, n_steps, wd, wl, skip=0)` returns J =
+mean over coarse steps skip .. n_steps - 1 of wd C_D + wl C_L for the geometry
 with the thickness bumps t(x) += A_m sin(m pi x) (workloads.thickness_modes)
 and the given angle of attack, as a torch scalar whose backward pass is the
 library's discrete adjoint (hlbm_adjoint): dJ/dA_m = dJ/dx . (mode m field),
@@ -22,8 +22,9 @@ def _moved_case(case, amplitudes, aoa_deg, modes):
     return dataclasses.replace(case, xy=xy, aoa_deg=float(aoa_deg))
 
 
-def mean_force(case, amplitudes, aoa_deg, n_steps=10, wd=1.0, wl=0.0, modes=None):
-    """J(amplitudes [M], aoa_deg []) as a differentiable torch scalar (FP64)."""
+def mean_force(case, amplitudes, aoa_deg, n_steps=10, wd=1.0, wl=0.0, modes=None, skip=0):
+    """J(amplitudes [M], aoa_deg []) as a differentiable torch scalar (FP64):
+    the mean over coarse steps skip .. n_steps - 1."""
     import torch
 
     from . import Solver
@@ -37,7 +38,7 @@ def mean_force(case, amplitudes, aoa_deg, n_steps=10, wd=1.0, wl=0.0, modes=None
         def forward(ctx, a, alpha):
             moved = _moved_case(case, a.detach().cpu().numpy(), float(alpha.detach().cpu()), modes)
             sol = Solver(moved, precision="fp64")
-            J, _, _, gx, da = sol.adjoint(int(n_steps), float(wd), float(wl))
+            J, _, _, gx, da = sol.adjoint(int(n_steps), float(wd), float(wl), int(skip))
             sol.close()
             dA = np.array([float((gx * f).sum()) for f in modes])
             ctx.save_for_backward(torch.as_tensor(dA, dtype=a.dtype, device=a.device),

@@ -154,9 +154,9 @@ def small(H):
     return case, s
 
 
-def _oracle_mean_force(case, K, wd, wl, dlat=None, dmesh=None, h=0.0):
-    """Mean of wd C_D + wl C_L over coarse steps 2 .. K + 1 of the oracle,
-    its state after step 1 moved by h * (dlat, dmesh) in populations."""
+def _oracle_mean_force(case, K, wd, wl, dlat=None, dmesh=None, h=0.0, skip=0):
+    """Mean of wd C_D + wl C_L over coarse steps 2 + skip .. K + 1 of the
+    oracle, its state after step 1 moved by h * (dlat, dmesh) in populations."""
     import oracle
     o = oracle.Oracle(case)
     o.step(1)
@@ -167,25 +167,26 @@ def _oracle_mean_force(case, K, wd, wl, dlat=None, dmesh=None, h=0.0):
         o.set_populations(-1, o.populations(-1) + h * dmesh)
     o.step(K)
     cd, cl = o.forces()
-    return float(np.mean(wd * cd[1:] + wl * cl[1:]))
+    return float(np.mean(wd * cd[1 + skip:] + wl * cl[1 + skip:]))
 
 
-@pytest.mark.parametrize("K,wd,wl", [(1, 1.0, 0.0), (3, 0.4, 1.0)])
-def test_coupled_adjoint_matches_oracle_finite_differences(H, small, K, wd, wl):
+@pytest.mark.parametrize("K,wd,wl,skip", [(1, 1.0, 0.0, 0), (3, 0.4, 1.0, 0), (3, 1.0, 0.0, 2)])
+def test_coupled_adjoint_matches_oracle_finite_differences(H, small, K, wd, wl, skip):
     case, s = small
     before = [a.copy() for a in s.fields(0)] + [a.copy() for a in s.fields(-1)]
-    J, (gl,), gm, _, _ = s.adjoint(K, wd, wl)
+    J, (gl,), gm, _, _ = s.adjoint(K, wd, wl, skip)
     after = list(s.fields(0)) + list(s.fields(-1))
     for a, b in zip(before, after):
         assert np.array_equal(a, b, equal_nan=True)
-    assert abs(J - _oracle_mean_force(case, K, wd, wl)) <= 1e-10 * max(1.0, abs(J))
-    rng = np.random.default_rng(7 + K)
+    assert abs(J - _oracle_mean_force(case, K, wd, wl, skip=skip)) <= 1e-10 * max(1.0, abs(J))
+    rng = np.random.default_rng(7 + K + skip)
     nx, ny = (int(v) for v in case.levels[0][:2])
     dlat = rng.standard_normal((nx * ny, 9)) * 1e-3
     dmesh = rng.standard_normal((case.n_nodes, 9)) * 1e-3
     h = 1e-4
     for dl, dm in ((dlat, None), (None, dmesh)):
-        fd = (_oracle_mean_force(case, K, wd, wl, dl, dm, h) - _oracle_mean_force(case, K, wd, wl, dl, dm, -h)) / (2 * h)
+        fd = (_oracle_mean_force(case, K, wd, wl, dl, dm, h, skip) -
+              _oracle_mean_force(case, K, wd, wl, dl, dm, -h, skip)) / (2 * h)
         ad = float(np.nansum(gl * dl)) if dl is not None else float(np.sum(gm * dm))
         assert abs(ad - fd) <= 1e-6 * abs(fd) + 1e-10, (K, dl is not None, ad, fd)
 

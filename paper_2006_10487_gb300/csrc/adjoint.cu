@@ -1,6 +1,10 @@
-// Discrete adjoint of the finite-volume part of the step (FP64): a window of
-// Eq. 3 sub-steps with the wall rule and the interface rows held at given
-// Eq. 9 data, ending in the wall-force functional of Eq. 10-11.
+// Discrete adjoint kernels of the HLBM step (FP64): the Eq. 3 sub-step with
+// the wall rule and the Eq. 10-11 wall-force functional (below), the lattice
+// side of a coupled step (collision, outer conditions, Eq. 4 + 8 and Eq. 9
+// coupling), the refinement interface (band snapshot, prolongation,
+// restriction), and the geometry derivatives (Eq. 3 operators, wall normals,
+// Eq. 8 and Eq. 9 weights).  The host schedule that runs them in reverse is
+// in api.cu (hlbm_adjoint, hlbm_fv_adjoint).
 //
 // The sub-step maps the mesh state of every node, stored as q = (rho - 1, u_x,
 // u_y, f^neq_3..8) (f^neq_0..2 follow from the zero mass and momentum of

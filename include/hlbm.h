@@ -210,9 +210,14 @@ int hlbm_inspect(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double 
  * Limits: n_edges <= 131072, else HLBM_EINVAL (message via
  * hlbm_last_error(NULL)).  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) for that device, so make that first
- * call before any stream capture.  Every call shares the array and it keeps
- * the last call's partial sums; each call writes every slot it reads, but
- * calls that overlap on the GPU race and must be ordered. */
+ * call before any stream capture; the address is kept for the life of the
+ * process, so it does not survive cudaDeviceReset (do not call this entry
+ * point on a device after resetting it).  Every call shares the array and it
+ * keeps the last call's partial sums; each call writes every slot it reads,
+ * but calls that overlap on the GPU race and must be ordered.  An edge whose
+ * end point lies outside [0, n_nodes) is skipped without reading f or xy, and
+ * the call then writes NaN to both outputs (it still returns HLBM_OK: the
+ * indices live on the device and are checked there). */
 int hlbm_wall_forces_static(const double *f, int n_nodes, const double *xy, const int32_t *edge_a,
                             const int32_t *edge_b, int n_edges, double qdyn, double *out, void *stream);
 

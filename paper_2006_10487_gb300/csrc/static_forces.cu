@@ -15,8 +15,15 @@
 //     of the last call; nothing in it has to start at zero (each call writes
 //     every slot it later reads), but calls that overlap on the GPU race, so
 //     they must be ordered (one stream, or synchronised streams);
-//   - the array exists on every device that loads the library, until exit.
+//   - the array exists on every device that loads the library, until exit;
+//   - its device address is looked up on the first call per device and kept
+//     for the life of the process, so it does not survive cudaDeviceReset (or
+//     any other destruction of the device's primary context): a process that
+//     resets a device must not call this entry point on it afterwards;
+//   - edge end points outside [0, n_nodes) are not read: such edges are
+//     skipped and the call writes NaN to both outputs.
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include <cstdint>
 #include <mutex>
@@ -32,8 +39,9 @@ constexpr int kStaticMaxBlocks = 1024;
 constexpr int kStaticMaxEdges = kStaticThreads * kStaticMaxBlocks;  // 131 072
 constexpr int kMaxDevices = 64;
 
-// (F_x, F_y) partial sum of each block of the first pass.
-static __device__ __align__(256) double g_force_scratch[2 * kStaticMaxBlocks];
+// Per block of the first pass: the (F_x, F_y) partial sum and a flag (1.0
+// when one of the block's edges had an end point outside [0, n_nodes)).
+static __device__ __align__(256) double g_force_scratch[3 * kStaticMaxBlocks];
 
 // Device address of g_force_scratch per device (host code only sees a
 // host-side stand-in for the symbol, so the address is looked up once per
@@ -98,15 +106,22 @@ __device__ __forceinline__ void static_block_sum(double &fx, double &fy)
 
 __global__ void __launch_bounds__(kStaticThreads)
 k_static_force_partial(const double *f, const double *xy, const int32_t *ea, const int32_t *eb, int n_edges,
-                       double *scratch)
+                       int n_nodes, double *scratch)
 {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     double fx = 0.0, fy = 0.0;
-    if (e < n_edges) static_edge_force(f, xy, ea[e], eb[e], fx, fy);
+    int bad = 0;
+    if (e < n_edges) {
+        int a = ea[e], b = eb[e];
+        if (a >= 0 && a < n_nodes && b >= 0 && b < n_nodes) static_edge_force(f, xy, a, b, fx, fy);
+        else bad = 1;  // never read past f or xy
+    }
+    bad = __syncthreads_or(bad);
     static_block_sum(fx, fy);
     if (threadIdx.x == 0) {
-        scratch[2 * blockIdx.x] = fx;
-        scratch[2 * blockIdx.x + 1] = fy;
+        scratch[3 * blockIdx.x] = fx;
+        scratch[3 * blockIdx.x + 1] = fy;
+        scratch[3 * blockIdx.x + 2] = bad ? 1.0 : 0.0;
     }
 }
 
@@ -115,14 +130,17 @@ __global__ void __launch_bounds__(kStaticThreads)
 k_static_force_final(const double *scratch, int n_part, double qdyn, double *out)
 {
     double fx = 0.0, fy = 0.0;
+    int bad = 0;
     for (int b = threadIdx.x; b < n_part; b += blockDim.x) {
-        fx += scratch[2 * b];
-        fy += scratch[2 * b + 1];
+        fx += scratch[3 * b];
+        fy += scratch[3 * b + 1];
+        bad |= scratch[3 * b + 2] != 0.0;
     }
+    bad = __syncthreads_or(bad);
     static_block_sum(fx, fy);
     if (threadIdx.x == 0) {
-        out[0] = fx / qdyn;
-        out[1] = fy / qdyn;
+        out[0] = bad ? CUDART_NAN : fx / qdyn;
+        out[1] = bad ? CUDART_NAN : fy / qdyn;
     }
 }
 
@@ -170,7 +188,7 @@ extern "C" int hlbm_wall_forces_static(const double *f, int n_nodes, const doubl
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int nb = (n_edges + kStaticThreads - 1) / kStaticThreads;
-    k_static_force_partial<<<nb, kStaticThreads, 0, s>>>(f, xy, edge_a, edge_b, n_edges, scratch);
+    k_static_force_partial<<<nb, kStaticThreads, 0, s>>>(f, xy, edge_a, edge_b, n_edges, n_nodes, scratch);
     k_static_force_final<<<1, kStaticThreads, 0, s>>>(scratch, nb, qdyn, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -27,15 +27,11 @@ def _so_path(openmp):
     return os.path.join(_BUILD, "libhlbm_oracle_omp.so" if openmp else "libhlbm_oracle.so")
 
 
-def build(openmp=False, force=False):
-    """Compile the oracle (gcc -O2, no FMA contraction, no fast-math)."""
-    out = _so_path(openmp)
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
-        return out
-    os.makedirs(_BUILD, exist_ok=True)
+def _compile(src, out, openmp=False):
+    os.makedirs(os.path.dirname(out), exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-           "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+           "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-o", tmp, src, "-lm"]
     if openmp:
         cmd.insert(1, "-fopenmp")
     subprocess.run(cmd, check=True)
@@ -43,48 +39,82 @@ def build(openmp=False, force=False):
     return out
 
 
-def lib(openmp=False):
+def build(openmp=False, force=False):
+    """Compile the oracle (gcc -O2, no FMA contraction, no fast-math)."""
+    out = _so_path(openmp)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    return _compile(_SRC, out, openmp)
+
+
+def source():
+    """The oracle's C source text."""
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+def build_variant(text, out):
+    """Compile C source `text` (a modified copy of the oracle, for tests that
+    plant a mistake in it and check that a pin catches it) to `out`."""
+    src = out[:-3] + ".c"
+    with open(src, "w") as fh:
+        fh.write(text)
+    return _compile(src, out)
+
+
+def _declare(L):
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.c_int, _ip, C.c_int, _dp, C.c_int, _ip, C.c_char_p,
+                             C.c_double, _dp, _dp, C.c_double, C.c_double, C.c_double,
+                             C.c_int, C.c_uint64, C.c_double, C.c_int, C.c_char_p, C.c_int]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_step.argtypes = [C.c_void_p, C.c_int]
+    L.orc_n_sub.argtypes = [C.c_void_p]
+    L.orc_tau.argtypes = [C.c_void_p, C.c_int]
+    L.orc_tau.restype = C.c_double
+    L.orc_step_count.argtypes = [C.c_void_p]
+    L.orc_step_count.restype = C.c_long
+    L.orc_n_forces.argtypes = [C.c_void_p]
+    L.orc_forces.argtypes = [C.c_void_p, _dp, _dp]
+    L.orc_wall_coeffs.argtypes = [C.c_void_p, _dp]
+    L.orc_fields.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp]
+    L.orc_populations.argtypes = [C.c_void_p, C.c_int, _dp]
+    L.orc_set_populations.argtypes = [C.c_void_p, C.c_int, _dp]
+    L.orc_apply_outer_bc.argtypes = [C.c_void_p]
+    L.orc_table.argtypes = [C.c_void_p, C.c_char_p, _dp]
+    L.orc_table.restype = C.c_long
+    L.orc_feq.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
+    L.orc_moments.argtypes = [_dp, _dp, _dp, _dp]
+    L.orc_bgk_collide.argtypes = [_dp, C.c_double]
+    L.orc_lattice_periodic.argtypes = [_dp, C.c_int, C.c_int, C.c_double, C.c_int]
+    L.orc_lattice_channel.argtypes = [_dp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int]
+    L.orc_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+    L.orc_uniform.restype = C.c_double
+    L.orc_fv_operators.argtypes = [C.c_int, _dp, C.c_int, _ip, _dp, _ip, _ip, _dp, _dp, _dp, _dp]
+    L.orc_fv_substep.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
+    L.orc_fv_substep_literal.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
+    L.orc_fv_channel_run.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, C.c_char_p,
+                                     C.c_double, C.c_double, C.c_int, _dp]
+    L.orc_wall_rule.argtypes = [_dp]
+    L.orc_eq4_post.argtypes = [_dp, C.c_double, _dp]
+    L.orc_feq_diff.argtypes = [C.c_double] * 6 + [_dp]
+    L.orc_eq5_base.argtypes = [_dp, C.c_double, _dp]
+    L.orc_quad6_weights.argtypes = [_dp, C.c_double, C.c_double, _dp]
+    L.orc_biquad9_weights.argtypes = [C.c_double, C.c_double, _dp]
+    L.orc_wall_force.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp]
+    L.orc_fv_window.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, _dp, C.c_double, _dp,
+                                C.c_double, _dp, C.c_double, C.c_double, _dp]
+    return L
+
+
+def lib(openmp=False, path=None):
+    """The oracle library (the OpenMP build if openmp; a variant built by
+    build_variant if path is given)."""
+    key = path or openmp
     with _LOCK:
-        if openmp not in _LIBS:
-            L = C.CDLL(build(openmp))
-            L.orc_create.restype = C.c_void_p
-            L.orc_create.argtypes = [C.c_int, _ip, C.c_int, _dp, C.c_int, _ip, C.c_char_p,
-                                     C.c_double, _dp, _dp, C.c_double, C.c_double, C.c_double,
-                                     C.c_int, C.c_uint64, C.c_double, C.c_int, C.c_char_p, C.c_int]
-            L.orc_destroy.argtypes = [C.c_void_p]
-            L.orc_step.argtypes = [C.c_void_p, C.c_int]
-            L.orc_n_sub.argtypes = [C.c_void_p]
-            L.orc_tau.argtypes = [C.c_void_p, C.c_int]
-            L.orc_tau.restype = C.c_double
-            L.orc_step_count.argtypes = [C.c_void_p]
-            L.orc_step_count.restype = C.c_long
-            L.orc_n_forces.argtypes = [C.c_void_p]
-            L.orc_forces.argtypes = [C.c_void_p, _dp, _dp]
-            L.orc_wall_coeffs.argtypes = [C.c_void_p, _dp]
-            L.orc_fields.argtypes = [C.c_void_p, C.c_int, _dp, _dp, _dp]
-            L.orc_populations.argtypes = [C.c_void_p, C.c_int, _dp]
-            L.orc_set_populations.argtypes = [C.c_void_p, C.c_int, _dp]
-            L.orc_table.argtypes = [C.c_void_p, C.c_char_p, _dp]
-            L.orc_table.restype = C.c_long
-            L.orc_feq.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
-            L.orc_moments.argtypes = [_dp, _dp, _dp, _dp]
-            L.orc_bgk_collide.argtypes = [_dp, C.c_double]
-            L.orc_lattice_periodic.argtypes = [_dp, C.c_int, C.c_int, C.c_double, C.c_int]
-            L.orc_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
-            L.orc_uniform.restype = C.c_double
-            L.orc_fv_operators.argtypes = [C.c_int, _dp, C.c_int, _ip, _dp, _ip, _ip, _dp, _dp, _dp, _dp]
-            L.orc_fv_substep.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp, C.c_double, C.c_double, _dp, _dp]
-            L.orc_wall_rule.argtypes = [_dp]
-            L.orc_eq4_post.argtypes = [_dp, C.c_double, _dp]
-            L.orc_feq_diff.argtypes = [C.c_double] * 6 + [_dp]
-            L.orc_eq5_base.argtypes = [_dp, C.c_double, _dp]
-            L.orc_quad6_weights.argtypes = [_dp, C.c_double, C.c_double, _dp]
-            L.orc_biquad9_weights.argtypes = [C.c_double, C.c_double, _dp]
-            L.orc_wall_force.argtypes = [C.c_int, _ip, _ip, _dp, _dp, _dp]
-            L.orc_fv_window.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_double, _dp, C.c_double, _dp,
-                                        C.c_double, _dp, C.c_double, C.c_double, _dp]
-            _LIBS[openmp] = L
-        return _LIBS[openmp]
+        if key not in _LIBS:
+            _LIBS[key] = _declare(C.CDLL(path or build(openmp)))
+        return _LIBS[key]
 
 
 def _d(a):
@@ -161,6 +191,36 @@ def fv_substep(ops, dt, tau_u, g):
     return out
 
 
+def fv_substep_literal(ops, dt, tau_u, g):
+    """Eq. 3 exactly as printed, on populations (orc_fv_substep_literal)."""
+    rowptr, col, sx, sy, cc, _ = ops
+    g = _d(g)
+    out = np.empty_like(g)
+    lib().orc_fv_substep_literal(g.shape[0], _pi(rowptr), _pi(col), _pd(sx), _pd(sy), _pd(cc), dt, tau_u,
+                                 _pd(g), _pd(out))
+    return out
+
+
+def fv_channel_run(ops, dt, tau_u, wall, force, nsteps, g):
+    """nsteps sub-steps of the solver's Eq. 3 update with a body force and the
+    wall rule on the nodes where wall != 0 (orc_fv_channel_run)."""
+    rowptr, col, sx, sy, cc, _ = ops
+    g = _d(g).copy()
+    w = np.ascontiguousarray(wall, dtype=np.uint8)
+    lib().orc_fv_channel_run(g.shape[0], _pi(rowptr), _pi(col), _pd(sx), _pd(sy), _pd(cc), dt, tau_u,
+                             w.ctypes.data_as(C.c_char_p), float(force[0]), float(force[1]), int(nsteps), _pd(g))
+    return g
+
+
+def lattice_channel(f, tau, Fx, nsteps):
+    """f: [ny, nx, 9]; nsteps of Eq. 1 in a channel periodic in x with
+    half-way bounce-back walls and a Guo body force Fx (orc_lattice_channel)."""
+    f = _d(f).copy()
+    ny, nx, _ = f.shape
+    lib().orc_lattice_channel(_pd(f), nx, ny, tau, Fx, nsteps)
+    return f
+
+
 def wall_rule(g):
     g = _d(g).copy()
     lib().orc_wall_rule(_pd(g))
@@ -213,8 +273,8 @@ def wall_force(ea, eb, xy, g):
 class Oracle:
     """The whole coupled HLBM on the CPU, FP64."""
 
-    def __init__(self, case, n_sub=None, openmp=False, periodic0=False):
-        self._lib = lib(openmp)
+    def __init__(self, case, n_sub=None, openmp=False, periodic0=False, literal_fv=False, lib_path=None):
+        self._lib = lib(openmp, lib_path)
         lv = _i(case.levels).reshape(-1)
         xy = _d(case.xy).reshape(-1) if case.n_nodes else np.zeros(2)
         tri = _i(case.tri).reshape(-1) if case.n_nodes else np.zeros(3, np.int32)
@@ -226,7 +286,7 @@ class Oracle:
         self.h = self._lib.orc_create(case.n_levels, _pi(lv), case.n_nodes, _pd(xy), int(case.tri.shape[0]),
                                       _pi(tri), kind.ctypes.data_as(C.c_char_p), case.chord, _pd(pivot),
                                       _pd(hole), case.Re, case.Ma, case.aoa_deg, int(ns), int(case.seed),
-                                      case.perturb, 1 if periodic0 else 0, err, 256)
+                                      case.perturb, (1 if periodic0 else 0) | (2 if literal_fv else 0), err, 256)
         if not self.h:
             raise ValueError("oracle set-up failed: " + err.value.decode())
         self.case = case
@@ -275,6 +335,10 @@ class Oracle:
         if f.size != self._grid_size(grid) * 9:
             raise ValueError("wrong population count")
         self._lib.orc_set_populations(self.h, grid, _pd(f))
+
+    def apply_outer_bc(self):
+        """Apply the level-0 outer conditions to the current state."""
+        self._lib.orc_apply_outer_bc(self.h)
 
     def forces(self):
         n = self._lib.orc_n_forces(self.h)

@@ -435,6 +435,108 @@ void orc_fv_substep(int n, const int *rowptr, const int *col, const double *sx, 
     free(qn);
 }
 
+/* Eq. 3 exactly as printed, on populations g[n][9]:
+ *   g'_i(P) = g_i(P) + dt sum_k S_ik g_i(P_k) - (dt/tau_u) sum_k C_ik [g_i(P_k) - f_i^eq(P_k)],
+ * the sums running over P itself (k = 0) and its edge neighbours, with
+ * S_ik = c_i . (s_x, s_y)_k and f^eq(P_k) of Eq. 2 from the moments of
+ * g(P_k).  No (rho, u, g^neq) state, no difference form: this is the plain
+ * formula against which the re-cast update of fv_substep_q is checked. */
+void orc_fv_substep_literal(int n, const int *rowptr, const int *col, const double *sx, const double *sy,
+                            const double *cc, double dt, double tau_u, const double *g, double *gnew)
+{
+    double *eq = malloc(((size_t)n * 9 + 1) * sizeof(double));
+    for (int p = 0; p < n; p++) {
+        double rho, ux, uy;
+        orc_moments(g + 9 * (size_t)p, &rho, &ux, &uy);
+        orc_feq(rho, ux, uy, eq + 9 * (size_t)p);
+    }
+    for (int p = 0; p < n; p++)
+        for (int i = 0; i < 9; i++) {
+            double stream = 0.0, coll = 0.0;
+            for (int e = rowptr[p]; e < rowptr[p + 1]; e++) {
+                const int k = col[e];
+                const double S = CX[i] * sx[e] + CY[i] * sy[e];
+                stream += S * g[9 * (size_t)k + i];
+                coll += cc[e] * (g[9 * (size_t)k + i] - eq[9 * (size_t)k + i]);
+            }
+            gnew[9 * (size_t)p + i] = g[9 * (size_t)p + i] + dt * stream - (dt / tau_u) * coll;
+        }
+    free(eq);
+}
+
+/* Test driver for a channel of the triangular mesh: nsteps sub-steps of the
+ * solver's own update (fv_substep_q, as in the coupled step) on populations
+ * g[n][9], each followed by a uniform body force (Fx, Fy) per unit volume,
+ * added as the source dt F_i with F_i = 3 w_i c_i . F (zero mass, momentum
+ * dt F, zero second moment), and by the wall rule (u <- 0) on the nodes with
+ * wall[p] != 0.  The body force is not part of the paper's method; it drives
+ * the Poiseuille check of Eq. 3 and the wall rule. */
+void orc_fv_channel_run(int n, const int *rowptr, const int *col, const double *sx, const double *sy,
+                        const double *cc, double dt, double tau_u, const unsigned char *wall, double Fx,
+                        double Fy, int nsteps, double *g)
+{
+    double *q = calloc((size_t)n * 12 + 1, sizeof(double)), *qn = calloc((size_t)n * 12 + 1, sizeof(double));
+    for (int p = 0; p < n; p++) state_q(g + 9 * (size_t)p, q + 12 * (size_t)p);
+    for (int s = 0; s < nsteps; s++) {
+        fv_substep_q(n, rowptr, col, sx, sy, cc, dt, tau_u, q, qn);
+        for (int p = 0; p < n; p++) {
+            double *qo = qn + 12 * (size_t)p, u1x, u1y, dfe[9];
+            u1x = qo[1] + dt * Fx / qo[0];
+            u1y = qo[2] + dt * Fy / qo[0];
+            if (wall[p]) { u1x = 0.0; u1y = 0.0; }
+            orc_feq_diff(qo[0], u1x, u1y, qo[0], qo[1], qo[2], dfe);
+            for (int i = 0; i < 9; i++) {
+                double Fi = wall[p] ? 0.0 : 3.0 * WQ[i] * (CX[i] * Fx + CY[i] * Fy);
+                qo[3 + i] += (wall[p] ? 0.0 : dt * Fi - dfe[i]);
+            }
+            qo[1] = u1x;
+            qo[2] = u1y;
+            neq_constrain(qo);
+        }
+        double *t = q; q = qn; qn = t;
+    }
+    for (int p = 0; p < n; p++) from_q(q + 12 * (size_t)p, 1.0, g + 9 * (size_t)p);
+    free(q);
+    free(qn);
+}
+
+/* Test driver for the lattice: Eq. 1 on an nx x ny channel, periodic in x,
+ * with stationary walls half-way between rows (below y = 0 and above
+ * y = ny - 1, "half-way bounce-back": a population that would leave through
+ * a wall returns reversed to the node it left) and a uniform body force Fx
+ * in x (Guo, Zheng and Shi's forcing: velocity u = (sum c f + F/2) / rho in
+ * f^eq, source (1 - 1/(2 tau)) w_i [3 (c_i - u) + 9 (c_i . u) c_i] . F).
+ * Neither the walls nor the force are part of the paper's method; they give
+ * the Poiseuille check of the lattice collide-stream.  f is [ny][nx][9]. */
+void orc_lattice_channel(double *f, int nx, int ny, double tau, double Fx, int nsteps)
+{
+    static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    size_t nn = (size_t)nx * ny;
+    double *post = malloc(nn * 9 * sizeof(double));
+    for (int s = 0; s < nsteps; s++) {
+        for (size_t p = 0; p < nn; p++) {
+            const double *fp = f + 9 * p;
+            double rho = 0.0, mx = 0.0, my = 0.0, eq[9];
+            for (int i = 0; i < 9; i++) { rho += fp[i]; mx += CX[i] * fp[i]; my += CY[i] * fp[i]; }
+            double ux = (mx + 0.5 * Fx) / rho, uy = my / rho;
+            orc_feq(rho, ux, uy, eq);
+            for (int i = 0; i < 9; i++) {
+                double cu = CX[i] * ux + CY[i] * uy;
+                double Fi = (1.0 - 0.5 / tau) * WQ[i] * (3.0 * (CX[i] - ux) + 9.0 * cu * CX[i]) * Fx;
+                post[9 * p + i] = fp[i] - (fp[i] - eq[i]) / tau + Fi;
+            }
+        }
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++)
+                for (int i = 0; i < 9; i++) {
+                    int xs = ((x - CX[i]) % nx + nx) % nx, ys = y - CY[i];
+                    size_t p = (size_t)y * nx + x;
+                    f[9 * p + i] = (ys < 0 || ys >= ny) ? post[9 * p + OPP[i]] : post[9 * ((size_t)ys * nx + xs) + i];
+                }
+    }
+    free(post);
+}
+
 /* Wall rule (the paper states only "no-slip"; reading): keep the density and
  * the non-equilibrium part of the wall node, set its velocity to zero:
  * g <- f^eq(rho, 0) + (g - f^eq(rho, u)).  In the (rho, u, g^neq) state of
@@ -597,6 +699,7 @@ typedef struct {
     int *is_don;                /* [n_is][6] mesh nodes */
     double *is_w;               /* [n_is][6] */
     int periodic0;              /* test-only: level 0 periodic, no outer rules */
+    int literal_fv;             /* test-only: Eq. 3 sub-steps by orc_fv_substep_literal */
     /* force series */
     int nf, fcap;
     double *cd, *cl;
@@ -751,6 +854,20 @@ static void collide_stream(orc *o, int c)
     stream_pull(l->post, l->f, l->nx, l->ny, c == 0 && o->periodic0);
 }
 
+/* Test-only alternative to fv_substep_q inside the solver: the state g (as
+ * (rho, u, g^neq)) is turned into populations, advanced by the literal Eq. 3
+ * and turned back, into gnew. */
+static void fv_substep_pop(orc *o)
+{
+    const size_t n = (size_t)o->n;
+    double *a = malloc((9 * n + 1) * sizeof(double)), *b = malloc((9 * n + 1) * sizeof(double));
+    for (size_t p = 0; p < n; p++) from_q(o->g + 12 * p, 1.0, a + 9 * p);
+    orc_fv_substep_literal(o->n, o->rowptr, o->col, o->sx, o->sy, o->cc, o->dt_u, o->tau_u, a, b);
+    for (size_t p = 0; p < n; p++) state_q(b + 9 * p, o->gnew + 12 * p);
+    free(a);
+    free(b);
+}
+
 /* One step of the finite-volume part (H4 of the coupling): n sub-steps of
  * Eq. 3 on all mesh nodes, the interface nodes first set by Eq. 5-7 and the
  * wall rule applied after each sub-step. */
@@ -758,7 +875,8 @@ static void fv_steps(orc *o)
 {
     for (int m = 0; m < o->n_sub; m++) {
         ring_set(o, (double)m / o->n_sub);
-        fv_substep_q(o->n, o->rowptr, o->col, o->sx, o->sy, o->cc, o->dt_u, o->tau_u, o->g, o->gnew);
+        if (o->literal_fv) fv_substep_pop(o);
+        else fv_substep_q(o->n, o->rowptr, o->col, o->sx, o->sy, o->cc, o->dt_u, o->tau_u, o->g, o->gnew);
         for (int w = 0; w < o->n_wall; w++) {  /* wall rule: u <- 0, rho and g^neq kept */
             o->gnew[12 * (size_t)o->wall[w] + 1] = 0.0;
             o->gnew[12 * (size_t)o->wall[w] + 2] = 0.0;
@@ -1013,6 +1131,7 @@ orc *orc_create(int L, const int *levels, int n, const double *xy, int ntri, con
     orc *o = calloc(1, sizeof(orc));
     o->L = L;
     o->periodic0 = flags & 1;
+    o->literal_fv = (flags & 2) != 0;
     o->chord = chord;
     o->u0 = Ma / sqrt(3.0);
     o->nu = o->u0 * chord / Re;
@@ -1229,6 +1348,10 @@ orc *orc_create(int L, const int *levels, int n, const double *xy, int ntri, con
 }
 
 /* ------------------------------------------------------------ queries ---- */
+/* Test hook: apply the level-0 outer conditions to the current state. */
+void orc_apply_outer_bc(orc *o) { apply_outer_bc(o); }
+
+
 int orc_n_sub(const orc *o) { return o->n_sub; }
 double orc_tau(const orc *o, int c) { return c < 0 ? o->tau_u : o->lv[c].tau; }
 long orc_step_count(const orc *o) { return o->step; }

@@ -16,6 +16,8 @@ from .naca import (  # noqa: F401
     make_case,
     naca0012_half_thickness,
     o_mesh,
+    patch_case,
+    square_patch,
     thickness_modes,
     uniform_equivalent,
 )

@@ -204,6 +204,46 @@ def _channel(name, nx, ny, Re, Ma, steps, chord=None):
                 steps=steps)
 
 
+def square_patch(x0, y0, width, m):
+    """Body-free triangular mesh of a square: (m+1) x (m+1) nodes of spacing
+    width/m from (x0, y0), each cell split into two triangles along
+    alternating diagonals.  Every node is fluid except the square's boundary,
+    which is the outer (overlap) ring.  Returns (xy, tri, kind) as o_mesh."""
+    h = width / m
+    i, j = np.meshgrid(np.arange(m + 1), np.arange(m + 1))
+    xy = np.stack([x0 + h * i.ravel(), y0 + h * j.ravel()], axis=1).astype(np.float64)
+    tri = []
+    for jj in range(m):
+        for ii in range(m):
+            a = jj * (m + 1) + ii
+            b, c = a + 1, a + m + 1
+            d = c + 1
+            tri += [(a, b, d), (a, d, c)] if (ii + jj) % 2 == 0 else [(a, b, c), (b, d, c)]
+    edge = (i.ravel() == 0) | (i.ravel() == m) | (j.ravel() == 0) | (j.ravel() == m)
+    kind = np.where(edge, KIND_RING, KIND_FLUID).astype(np.uint8)
+    return xy, np.asarray(tri, dtype=np.int32), kind
+
+
+def patch_case(n0=64, m=32, width=24.0, centre=(32.3, 32.47), nu=0.1, Ma=0.1, mesh=True, name="patch"):
+    """One n0 x n0 lattice level with a body-free square mesh (square_patch,
+    m x m cells of side `width`, centred at `centre`, placed off the lattice
+    nodes) whose circular hole is inset 4 cells from the ring: the overlap
+    coupling (Eq. 4-9) with nothing else of the airfoil case.  nu is the
+    lattice viscosity (the solver derives Re = u0 C / nu with C = 1).
+    mesh=False gives the same lattice without the mesh."""
+    u0 = Ma / math.sqrt(3.0)
+    lv = np.asarray([[n0, n0, 0, 0]], dtype=np.int32)
+    if mesh:
+        xy, tri, kind = square_patch(centre[0] - 0.5 * width, centre[1] - 0.5 * width, width, m)
+        r = 0.5 * width - 4.0
+        hole = (centre[0], centre[1], r, r)
+    else:
+        xy, tri, kind = np.zeros((0, 2)), np.zeros((0, 3), dtype=np.int32), np.zeros(0, dtype=np.uint8)
+        hole = (0.0, 0.0, 0.0, 0.0)
+    return Case(name=name, levels=lv, xy=xy, tri=tri, kind=kind, chord=1.0, pivot=tuple(centre), hole=hole,
+                Re=u0 / nu, Ma=float(Ma), aoa_deg=0.0, perturb=0.0, steps=200)
+
+
 def uniform_equivalent(case):
     """The lattice an equivalent plain LBM would use for `case` (Eq. 14's
     T_eq): one level at the finest resolution over the whole domain, with the
@@ -265,6 +305,10 @@ CONFIGS = {
                        [4097, 2049, 1024, 512]],
         chord=800.0, mid=(1648.0, 1024.0), n_theta=4096, n_layers=366, stretch=1.0,
         ell_b_ratio=0.6, overlap=4.0, Re=1e4, Ma=0.1, aoa_deg=0.0, steps=200000),
+    # Body-free coupling: a 64x64 level with a 33x33-node square mesh over a
+    # circular hole (overlap band only, no airfoil); perturbed density so that
+    # waves cross the band.
+    "patch": lambda: dataclasses.replace(patch_case(), perturb=1e-4),
     # Mesh-less channel (lattice and outer boundaries only).
     "channel": lambda: _channel("channel", 64, 32, Re=100.0, Ma=0.1, steps=100),
 }

@@ -143,28 +143,47 @@ def aggregate_mlups(updates_per_step, steps, world_size, ms):
     return updates_per_step * steps * world_size / (ms * 1e-3) / 1e6
 
 
-def run_cpu_baseline(case, coarse_steps=1):
-    """The FP64 oracle on the host cores (single thread), bounded sample."""
+def _oracle_updates(o, case):
+    """Node updates per coarse step, counted as the library counts them: every
+    computed lattice node of level l 2^l times, every mesh node n_sub times
+    per finest step."""
+    lat = 0.0
+    for lv in range(case.n_levels):
+        typ = o.table(f"type{lv}")
+        lat += float(((typ != 4) & (typ != 5)).sum()) * 2 ** lv
+    return lat + float(case.n_nodes) * o.n_sub * 2 ** (case.n_levels - 1)
+
+
+def run_cpu_baseline(case, coarse_steps=1, openmp=True, oracle_obj=None):
+    """The FP64 oracle as it stands on the host cores: the OpenMP build over
+    every allowed core (bitwise the serial result), or the serial build; a
+    bounded sample of `coarse_steps` coarse steps."""
     import oracle
     t0 = time.perf_counter()
-    o = oracle.Oracle(case)
+    o = oracle_obj or oracle.Oracle(case, openmp=openmp)
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     o.step(coarse_steps)
     dt = time.perf_counter() - t0
-    lat = 0.0
-    for lv in range(case.n_levels):
-        nn = float(case.levels[lv][0]) * float(case.levels[lv][1])
-        if lv == case.n_levels - 1:
-            typ = o.table(f"type{lv}")
-            nn -= float(((typ == 4) | (typ == 5)).sum())
-        lat += nn * 2 ** lv
-    fv = float(case.n_nodes) * o.n_sub * 2 ** (case.n_levels - 1)
-    return {"value": (lat + fv) * coarse_steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{coarse_steps} coarse step(s) of the {WORKLOAD} workload, FP64, single thread "
+    cores = oracle.lib(openmp).orc_threads()
+    return {"value": _oracle_updates(o, case) * coarse_steps / dt / 1e6, "unit": "MLUPS", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{coarse_steps} coarse step(s) of the {WORKLOAD} workload, FP64, "
+                      f"{'OpenMP' if openmp else 'serial'} build on {cores} host thread(s) "
                       f"(set-up {t_setup:.1f} s not timed)", "seconds": dt,
             "host_cores_available": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None,
             "cpu_model": _cpu_model()}
+
+
+def _config(case, precision, n_sub, per_step, ws):
+    """The workload description shared by both arms."""
+    return {"workload": WORKLOAD, "levels": case.levels.tolist(), "mesh_nodes": case.n_nodes,
+            "n_sub": n_sub, "Re": case.Re, "Ma": case.Ma, "aoa_deg": case.aoa_deg,
+            "precision": precision, "node_updates_per_step": per_step,
+            "lattice_storage": {"fp64": "f64", "fp32": "f32", "fp16s": "f16 shifted"}[precision],
+            "l2": "working set per coarse step (~160 MB FP32) exceeds L2; the finite-volume "
+                  "state (~37 MB) is re-read n_sub times per finest step and stays L2-resident",
+            "parallelism": f"replicas x{ws}"}
 
 
 def _cpu_model():
@@ -188,28 +207,34 @@ def _cpu_model():
 
 
 def reference_arm(args):
-    """--impl reference: the oracle as it stands on the host cores."""
+    """--impl reference: the oracle as it stands (FP64, the OpenMP build over
+    every allowed host core), on this arm's workload: W untimed coarse steps,
+    then K timed coarse steps of the same run; one step = one coarse step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle
     from workloads import make_case
     case = make_case(WORKLOAD)
-    # each "step" is a bounded sample: one coarse step of the same workload
-    for _ in range(min(args.warmup, 1)):
-        pass
     t0 = time.perf_counter()
-    res = None
-    for _ in range(max(1, min(args.steps, 2))):
-        res = run_cpu_baseline(case, 1)
-    total = time.perf_counter() - t0
-    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": "MLUPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["seconds"] * 1e3,
+    o = oracle.Oracle(case, openmp=True)
+    t_setup = time.perf_counter() - t0
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    per_step = _oracle_updates(o, case)
+    value = per_step * args.steps / dt / 1e6
+    cores = oracle.lib(True).orc_threads()
+    sample = (f"{args.steps} timed coarse steps (after {args.warmup} untimed) of the {WORKLOAD} workload, FP64, "
+              f"OpenMP build on {cores} host threads (set-up {t_setup:.1f} s not timed)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64"},
-            "cpu_baseline": {"value": res["value"], "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": res["sample"]},
-            "e2e": {"value": res["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_seconds": total}
+            "data": "synthetic", "config": _config(case, args.precision, o.n_sub, per_step, 1),
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": _cpu_model()},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
@@ -299,13 +324,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "levels": case.levels.tolist(), "mesh_nodes": case.n_nodes,
-                       "n_sub": n_sub, "Re": case.Re, "Ma": case.Ma, "aoa_deg": case.aoa_deg,
-                       "precision": args.precision, "node_updates_per_step": per_step,
-                       "lattice_storage": {"fp64": "f64", "fp32": "f32", "fp16s": "f16 shifted"}[args.precision],
-                       "l2": "working set per coarse step (~160 MB FP32) exceeds L2; the finite-volume "
-                             "state (~37 MB) is re-read n_sub times per finest step and stays L2-resident",
-                       "parallelism": f"replicas x{ws}"},
+            "config": _config(case, args.precision, n_sub, per_step, ws),
             "roofline": roofline, "gpu_launches": int(launches * args.steps),
             "clocks": clk.summary(), "cd_mean": float(cd.mean()) if len(cd) else None,
             "cl_mean": float(cl.mean()) if len(cl) else None}
@@ -521,7 +540,8 @@ def main():
                        "per-step force readback, final mesh-field readback"}
         # ---- CPU baseline: the oracle on a bounded sample
         if ws == 1:
-            line["cpu_baseline"] = run_cpu_baseline(case, 1)
+            line["cpu_baseline"] = run_cpu_baseline(case, 10, openmp=True)
+            line["cpu_baseline"]["serial"] = run_cpu_baseline(case, 1, openmp=False)
     if rank == 0:
         print(json.dumps(line))
     if dist:

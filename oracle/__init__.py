@@ -70,6 +70,7 @@ def _declare(L):
     L.orc_destroy.argtypes = [C.c_void_p]
     L.orc_step.argtypes = [C.c_void_p, C.c_int]
     L.orc_n_sub.argtypes = [C.c_void_p]
+    L.orc_threads.argtypes = []
     L.orc_tau.argtypes = [C.c_void_p, C.c_int]
     L.orc_tau.restype = C.c_double
     L.orc_step_count.argtypes = [C.c_void_p]

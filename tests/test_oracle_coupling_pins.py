@@ -392,3 +392,18 @@ def test_pins_catch_planted_mistakes(orc, tmp_path):
                   or not _wall_ok(orc, path) or _uniform_patch_deviation(orc, path) > 1e-14
                   or not _band_wave_ok(_band_wave(orc, path)))
         assert caught, name
+
+
+# ------------------------------------------------ host-parallel oracle -------
+def test_openmp_build_is_bitwise_the_serial_one(orc):
+    """The OpenMP build (node loops on several host threads; each output
+    written by one iteration) gives bitwise the serial build's populations and
+    force series: 10 coarse steps of the two-level case at 8 degrees."""
+    from workloads import make_case
+    case = make_case("hlbm_mini2", aoa_deg=8.0)
+    a, b = orc.Oracle(case), orc.Oracle(case, openmp=True)
+    a.step(10)
+    b.step(10)
+    for grid in list(range(case.n_levels)) + [-1]:
+        assert np.array_equal(a.populations(grid), b.populations(grid), equal_nan=True)
+    assert np.array_equal(np.asarray(a.forces()), np.asarray(b.forces()))

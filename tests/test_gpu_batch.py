@@ -55,3 +55,31 @@ def test_batch_refuses_a_case_stepped_outside_it(H):
         batch.step(1)
     assert e.value.code == H.HLBM_ESTATE
     batch.close()
+
+
+def test_batched_fp64_cases_match_the_oracle(H, orc):
+    """Two FP64 cases of different sizes and level counts (the one-level
+    airfoil case at 5 degrees and the two-level case at 2 degrees) advanced
+    only by batched graph launches, against the oracle run of each case:
+    every field within 1e-12 of its scale and the force series within 1e-12,
+    after 30 coarse steps."""
+    cases = [make_case("hlbm_small", aoa_deg=5.0), make_case("hlbm_mini2", aoa_deg=2.0)]
+    solvers = [H.Solver(c, precision="fp64") for c in cases]
+    batch = H.Batch(solvers)
+    batch.step(13)
+    batch.step(17)
+    batch.sync()
+    for case, s in zip(cases, solvers):
+        o = orc.Oracle(case)
+        o.step(30)
+        for g in grids(case):
+            (ar, ax, ay), (br, bx, by) = s.fields(g), o.fields(g)
+            m = np.isfinite(br)
+            assert np.array_equal(np.isfinite(ar), m)
+            assert np.abs(ar[m] - br[m]).max() <= 1e-12 * np.abs(br[m]).max()
+            assert np.hypot(ax[m] - bx[m], ay[m] - by[m]).max() <= 1e-12 * np.hypot(bx[m], by[m]).max()
+        (cd, cl), (ocd, ocl) = s.forces(), o.forces()
+        assert len(cd) == 30
+        assert np.abs(cd - ocd).max() <= 1e-12 * np.abs(ocd).max()
+        assert np.abs(cl - ocl).max() <= 1e-12 * max(np.abs(ocl).max(), np.abs(ocd).max())
+    batch.close()

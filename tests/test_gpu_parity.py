@@ -92,6 +92,31 @@ def test_fp64_matches_oracle(H, orc, name, steps, aoa):
         assert np.abs(cl - ocl).max() <= FP64_TOL * max(np.abs(ocl).max(), np.abs(ocd).max())
 
 
+@pytest.mark.slow
+def test_config1_full_run_fp64(H, orc):
+    """Config 1 over its whole nominal run (2000 steps of the 200 x 100 lattice
+    with the 5 200-node mesh, Re 500, zero incidence): the FP64 force series
+    within 1e-10 of the oracle's (OpenMP build, bitwise the serial one) at every
+    step, and every field within 1e-10 at the end."""
+    case = make_case("hlbm_small")
+    assert case.steps == 2000
+    sol = H.Solver(case, precision="fp64", force_cap=4096)
+    sim = orc.Oracle(case, openmp=True)
+    cd, cl = [], []
+    for _ in range(4):
+        sol.step(500)
+        sim.step(500)
+        c, l_ = sol.forces()
+        cd.append(c)
+        cl.append(l_)
+    cd, cl = np.concatenate(cd), np.concatenate(cl)
+    ocd, ocl = sim.forces()
+    assert len(cd) == len(ocd) == 2000
+    assert np.abs(cd - ocd).max() <= 1e-10 * np.abs(ocd).max()
+    assert np.abs(cl - ocl).max() <= 1e-10 * np.abs(ocd).max()
+    compare_fields(sol, sim, case, 1e-10, "hlbm_small 2000 steps")
+
+
 def test_populations_match_oracle(H, orc):
     case = make_case("hlbm_mini2")
     sol = H.Solver(case, precision="fp64")

@@ -305,6 +305,12 @@ CONFIGS = {
                        [4097, 2049, 1024, 512]],
         chord=800.0, mid=(1648.0, 1024.0), n_theta=4096, n_layers=366, stretch=1.0,
         ell_b_ratio=0.6, overlap=4.0, Re=1e4, Ma=0.1, aoa_deg=0.0, steps=200000),
+    # The large-Re case's 1.5 M-node mesh (as in "hlbm_large") inside a single
+    # 1800x1100 level at the finest resolution: the same finite-volume work in
+    # a few hundred MB of device memory (finite-volume kernel profiles).
+    "hlbm_large_fv": lambda: _mesh_case(
+        "hlbm_large_fv", [[1800, 1100, 0, 0]], chord=800.0, mid=(900.0, 550.0), n_theta=4096, n_layers=366,
+        stretch=1.0, ell_b_ratio=0.6, overlap=4.0, Re=1e4, Ma=0.1, aoa_deg=0.0, steps=100),
     # Body-free coupling: a 64x64 level with a 33x33-node square mesh over a
     # circular hole (overlap band only, no airfoil); perturbed density so that
     # waves cross the band.

@@ -93,7 +93,19 @@ typedef struct {
  * nodes); 0 leaves the step as it is.  fv_variant: register bound of the
  * FP32 finite-volume kernel: 0 times both on this mesh at create and keeps the
  * faster (the block-shape autotuner), 1 bounded for 7 resident blocks per SM,
- * 2 for 8; both give the same results (FP64 is not bounded; reports 1). */
+ * 2 for 8; both give the same results (FP64 is not bounded; reports 1).
+ * fv_filter: strength sigma in [0, 1] of an odd-even filter of the mesh state
+ * applied once per finest step after the Eq. 3 sub-steps (an addition to the
+ * paper's method, 0 = off, the default of a zeroed struct): with the graph
+ * Laplacian of the Eq. 3 collision weights, (L g)_i(P) = sum_{k != P} C_Pk
+ * [g_i(P_k) - g_i(P)], every fluid node takes g <- g - sigma L d with d = L g
+ * on fluid nodes and 0 on wall and ring nodes, which keep their state.  On
+ * smooth fields this is a hyper-diffusion of about (7/54)^2 sigma h^4 k^4 per
+ * finest step (h the mesh spacing); it damps the node-to-node oscillations
+ * that the central Eq. 3 fluxes neither advect nor damp and that otherwise
+ * grow in long runs at Re 1000 (factor 1 - sigma (14/27)^2 per step on a
+ * regular triangulation).
+ * The adjoint entry points refuse contexts with fv_filter > 0. */
 typedef struct {
     int32_t precision;
     int32_t n_sub;
@@ -108,6 +120,7 @@ typedef struct {
     int32_t use_graphs;
     int32_t wall_stats;
     int32_t fv_variant;
+    double fv_filter;
 } hlbm_options;
 
 typedef struct hlbm_ctx hlbm_ctx;

@@ -82,6 +82,8 @@ def _declare(L):
     L.orc_populations.argtypes = [C.c_void_p, C.c_int, _dp]
     L.orc_set_populations.argtypes = [C.c_void_p, C.c_int, _dp]
     L.orc_apply_outer_bc.argtypes = [C.c_void_p]
+    L.orc_set_fv_filter.argtypes = [C.c_void_p, C.c_double]
+    L.orc_fv_filter.argtypes = [C.c_int, _ip, _ip, _dp, C.c_char_p, C.c_double, _dp, _dp]
     L.orc_table.argtypes = [C.c_void_p, C.c_char_p, _dp]
     L.orc_table.restype = C.c_long
     L.orc_feq.argtypes = [C.c_double, C.c_double, C.c_double, _dp]
@@ -222,6 +224,17 @@ def lattice_channel(f, tau, Fx, nsteps):
     return f
 
 
+def fv_filter(ops, sigma, g, kind=None):
+    """One application of the odd-even filter of the mesh state (orc_fv_filter)."""
+    rowptr, col, _, _, cc, _ = ops
+    g = _d(g)
+    out = np.empty_like(g)
+    k = None if kind is None else np.ascontiguousarray(kind, dtype=np.uint8)
+    lib().orc_fv_filter(g.shape[0], _pi(rowptr), _pi(col), _pd(cc), None if k is None else k.ctypes.data_as(C.c_char_p),
+                        float(sigma), _pd(g), _pd(out))
+    return out
+
+
 def wall_rule(g):
     g = _d(g).copy()
     lib().orc_wall_rule(_pd(g))
@@ -274,7 +287,8 @@ def wall_force(ea, eb, xy, g):
 class Oracle:
     """The whole coupled HLBM on the CPU, FP64."""
 
-    def __init__(self, case, n_sub=None, openmp=False, periodic0=False, literal_fv=False, lib_path=None):
+    def __init__(self, case, n_sub=None, openmp=False, periodic0=False, literal_fv=False, lib_path=None,
+                 fv_filter=None):
         self._lib = lib(openmp, lib_path)
         lv = _i(case.levels).reshape(-1)
         xy = _d(case.xy).reshape(-1) if case.n_nodes else np.zeros(2)
@@ -291,6 +305,9 @@ class Oracle:
         if not self.h:
             raise ValueError("oracle set-up failed: " + err.value.decode())
         self.case = case
+        sigma = getattr(case, "fv_filter", 0.0) if fv_filter is None else fv_filter
+        if sigma:
+            self._lib.orc_set_fv_filter(self.h, float(sigma))
 
     def close(self):
         if getattr(self, "h", None):

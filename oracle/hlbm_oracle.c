@@ -712,6 +712,7 @@ typedef struct {
     double *is_w;               /* [n_is][6] */
     int periodic0;              /* test-only: level 0 periodic, no outer rules */
     int literal_fv;             /* test-only: Eq. 3 sub-steps by orc_fv_substep_literal */
+    double fv_filter;           /* strength of the odd-even filter per finest step (0: off) */
     /* force series */
     int nf, fcap;
     double *cd, *cl;
@@ -885,6 +886,103 @@ static void fv_substep_pop(orc *o)
     free(b);
 }
 
+/* Odd-even filter of the mesh state, once per finest step after the Eq. 3
+ * sub-steps, when o->fv_filter = sigma > 0 (an addition to the paper's method,
+ * off by default).  With the graph Laplacian of the Eq. 3 collision weights,
+ *   (L g)_i(P) = sum_{k != P} C_Pk [g_i(P_k) - g_i(P)],
+ * every population of every fluid node takes one step of a biharmonic
+ * (fourth-order) damping,
+ *   g_i(P) <- g_i(P) - sigma (L d)_i(P),  d = L g at fluid nodes, 0 elsewhere;
+ * wall and outer-ring nodes are left as they are (at a boundary node L is a
+ * one-sided, first-order difference, which would act on the wall pressure and
+ * stress).  A_P C_Pk is symmetric in (P, k) (both are 7/108 of the two
+ * triangles' areas at edge Pk), so on a mesh without boundary nodes L and the
+ * filter conserve mass and momentum exactly.  On smooth fields the filter is a
+ * hyper-diffusion
+ * of O(sigma h^4 k^4) per step; on the node-to-node (odd-even) oscillations,
+ * which the central fluxes of Eq. 3 neither advect nor damp, L has an
+ * eigenvalue of order one and the filter damps them at O(sigma) per step.
+ * The first Laplacian is formed on the (rho, u, g^neq) state as
+ * fv_substep_q forms its differences; the second on the stored differences. */
+static void fv_lap_q(int n, const int *rowptr, const int *col, const double *cc, const unsigned char *kind,
+                     const double *q, double *d)
+{
+#pragma omp parallel for schedule(static)
+    for (int p = 0; p < n; p++) {
+        const double *qp = q + 12 * (size_t)p;
+        double acc[9] = {0};
+        if (kind && kind[p] != 0) {
+            for (int i = 0; i < 9; i++) d[9 * (size_t)p + i] = 0.0;
+            continue;
+        }
+        for (int e = rowptr[p]; e < rowptr[p + 1]; e++) {
+            const int k = col[e];
+            if (k == p) continue;
+            const double *qk = q + 12 * (size_t)k;
+            double dfe[9];
+            orc_feq_diff(qk[0], qk[1], qk[2], qp[0], qp[1], qp[2], dfe);
+            for (int i = 0; i < 9; i++) acc[i] += cc[e] * (dfe[i] + qk[3 + i] - qp[3 + i]);
+        }
+        for (int i = 0; i < 9; i++) d[9 * (size_t)p + i] = acc[i];
+    }
+}
+
+static void fv_filter_q(int n, const int *rowptr, const int *col, const double *cc, const unsigned char *kind,
+                        double sigma, const double *q, double *qn)
+{
+    double *d = malloc(((size_t)n * 9 + 1) * sizeof(double));
+    fv_lap_q(n, rowptr, col, cc, kind, q, d);
+#pragma omp parallel for schedule(static)
+    for (int p = 0; p < n; p++) {
+        const double *qp = q + 12 * (size_t)p, *dp = d + 9 * (size_t)p;
+        double acc[9] = {0};
+        if (kind && kind[p] != 0) {
+            memcpy(qn + 12 * (size_t)p, qp, 12 * sizeof(double));
+            continue;
+        }
+        for (int e = rowptr[p]; e < rowptr[p + 1]; e++) {
+            const int k = col[e];
+            if (k == p) continue;
+            for (int i = 0; i < 9; i++) acc[i] += cc[e] * (d[9 * (size_t)k + i] - dp[i]);
+        }
+        double drho = 0.0, djx = 0.0, djy = 0.0;
+        for (int i = 0; i < 9; i++) {
+            acc[i] *= -sigma;
+            drho += acc[i];
+            djx += CX[i] * acc[i];
+            djy += CY[i] * acc[i];
+        }
+        double *qo = qn + 12 * (size_t)p;
+        const double rho = qp[0] + drho;
+        qo[0] = rho;
+        qo[1] = qp[1] + (djx - drho * qp[1]) / rho;
+        qo[2] = qp[2] + (djy - drho * qp[2]) / rho;
+        double dfe[9];
+        orc_feq_diff(qo[0], qo[1], qo[2], qp[0], qp[1], qp[2], dfe);
+        for (int i = 0; i < 9; i++) qo[3 + i] = qp[3 + i] + acc[i] - dfe[i];
+        neq_constrain(qo);
+    }
+    free(d);
+}
+
+static void fv_filter(orc *o)
+{
+    fv_filter_q(o->n, o->rowptr, o->col, o->cc, o->kind, o->fv_filter, o->g, o->gnew);
+    double *t = o->g; o->g = o->gnew; o->gnew = t;
+}
+
+/* The filter on populations g[n][9] -> gnew (kind may be NULL: no wall nodes). */
+void orc_fv_filter(int n, const int *rowptr, const int *col, const double *cc, const unsigned char *kind,
+                   double sigma, const double *g, double *gnew)
+{
+    double *q = calloc((size_t)n * 12 + 1, sizeof(double)), *qn = calloc((size_t)n * 12 + 1, sizeof(double));
+    for (int p = 0; p < n; p++) state_q(g + 9 * (size_t)p, q + 12 * (size_t)p);
+    fv_filter_q(n, rowptr, col, cc, kind, sigma, q, qn);
+    for (int p = 0; p < n; p++) from_q(qn + 12 * (size_t)p, 1.0, gnew + 9 * (size_t)p);
+    free(q);
+    free(qn);
+}
+
 /* One step of the finite-volume part (H4 of the coupling): n sub-steps of
  * Eq. 3 on all mesh nodes, the interface nodes first set by Eq. 5-7 and the
  * wall rule applied after each sub-step. */
@@ -900,6 +998,7 @@ static void fv_steps(orc *o)
         }
         double *t = o->g; o->g = o->gnew; o->gnew = t;
     }
+    if (o->fv_filter > 0.0) fv_filter(o);
 }
 
 /* One step of level c (its own clock).  theta_next: parent-time fraction
@@ -1374,6 +1473,9 @@ int orc_threads(void)
     return 1;
 #endif
 }
+
+/* Strength of the odd-even filter of the mesh state (fv_filter; 0 = off). */
+void orc_set_fv_filter(orc *o, double sigma) { o->fv_filter = sigma; }
 
 /* Test hook: apply the level-0 outer conditions to the current state. */
 void orc_apply_outer_bc(orc *o) { apply_outer_bc(o); }

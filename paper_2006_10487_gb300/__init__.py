@@ -47,7 +47,7 @@ class hlbm_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("n_sub", C.c_int32), ("seed", C.c_uint64), ("perturb", C.c_double),
                 ("force_cap", C.c_int32), ("check_every", C.c_int32), ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p), ("use_graphs", C.c_int32),
-                ("wall_stats", C.c_int32), ("fv_variant", C.c_int32)]
+                ("wall_stats", C.c_int32), ("fv_variant", C.c_int32), ("fv_filter", C.c_double)]
 
 
 _lib = None
@@ -108,7 +108,7 @@ def _check(rc, ctx=None):
 
 
 def _marshal(case, precision="fp64", n_sub=None, seed=None, perturb=None, force_cap=0, check_every=0,
-             stream=None, use_graphs=True, allocator=None, wall_stats=False, fv_variant=0):
+             stream=None, use_graphs=True, allocator=None, wall_stats=False, fv_variant=0, fv_filter=None):
     """C structures for a workloads.Case (kept alive by the returned tuple)."""
     lv = (hlbm_level * case.n_levels)(*[hlbm_level(*map(int, r)) for r in case.levels])
     xy = np.ascontiguousarray(case.xy, dtype=np.float64).reshape(-1)
@@ -134,6 +134,7 @@ def _marshal(case, precision="fp64", n_sub=None, seed=None, perturb=None, force_
     o.use_graphs = 1 if use_graphs else 0
     o.wall_stats = 1 if wall_stats else 0
     o.fv_variant = int(fv_variant)
+    o.fv_filter = float(getattr(case, "fv_filter", 0.0) if fv_filter is None else fv_filter)
     if allocator is not None:
         o.alloc, o.free = allocator
     return lv, m, o, (xy, tri, kind)
@@ -169,7 +170,7 @@ class Solver:
     """One HLBM simulation on the current CUDA device (wraps an hlbm_ctx)."""
 
     def __init__(self, case, precision="fp64", n_sub=None, seed=None, perturb=None, force_cap=0, check_every=0,
-                 use_graphs=True, stream=None, torch_memory=True, wall_stats=False, fv_variant=0):
+                 use_graphs=True, stream=None, torch_memory=True, wall_stats=False, fv_variant=0, fv_filter=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the HLBM library needs a CUDA device (there is no CPU fallback)")
@@ -177,7 +178,7 @@ class Solver:
             stream = torch.cuda.current_stream().cuda_stream
         self._alloc = _torch_allocator() if torch_memory else None
         self._args = _marshal(case, precision, n_sub, seed, perturb, force_cap, check_every, stream, use_graphs,
-                              self._alloc, wall_stats, fv_variant)
+                              self._alloc, wall_stats, fv_variant, fv_filter)
         lv, m, o, _ = self._args
         ctx = C.c_void_p()
         self._lib = lib()

@@ -138,7 +138,7 @@ void set_phase(hlbm_ctx *c, long k)
     DevCtx &D = c->dev;
     D.lv[0].parity = int(k & 1);
     for (int l = 1; l < D.L; l++) D.lv[l].parity = 0;
-    long per = long(D.n_sub) << (D.L - 1);
+    long per = long(D.n_sub + (D.fv_filter > 0.0 ? 1 : 0)) << (D.L - 1);
     D.m.gcur = int((k * per) & 1);
     for (int l = 0; l < D.L; l++) {  // steps of level l done before coarse step k: k 2^l
         DevLevel &dl = D.lv[l];
@@ -283,6 +283,11 @@ template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double t
             D.m.gcur ^= 1;
         }
         c->launches += 1 + D.n_sub;
+        if (D.fv_filter > 0.0) {  // optional odd-even filter of the mesh state
+            launch_fv_filter<T, S>(D, s);
+            D.m.gcur ^= 1;
+            c->launches += 2;
+        }
         D.m.qpar ^= 1;  // the data at t + 1 is the next step's data at t
         std::swap(D.m.Q0, D.m.Q1);
     }
@@ -406,6 +411,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     M.ring_start = P.ring_start;
     M.n_ring = P.n_ring;
     for (int b = 0; b < 2; b++) M.g[b] = dalloc(c, size_t(9) * M.Np * sizeof(T));
+    if (c->dev.fv_filter > 0.0) M.lap = dalloc(c, size_t(9) * M.Np * sizeof(T));
     // sliced-ELL operator rows in device order; the column of every entry is
     // the position of the neighbour in its tile's halo list (the sorted nodes
     // the tile's rows touch), which the kernel stages in shared memory
@@ -747,6 +753,11 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
     c->dev.m.wall_stats = o.wall_stats != 0;
     if (o.fv_variant < 0 || o.fv_variant > 2) { delete c; return fail(nullptr, HLBM_EINVAL, "fv_variant must be 0, 1 or 2"); }
     c->fv_variant_opt = o.fv_variant;
+    if (!(o.fv_filter >= 0.0 && o.fv_filter <= 1.0)) {
+        delete c;
+        return fail(nullptr, HLBM_EINVAL, "fv_filter must be in [0, 1]");
+    }
+    c->dev.fv_filter = o.fv_filter;
     c->check_every = std::max(0, o.check_every);
     c->dev.force_cap = o.force_cap > 0 ? o.force_cap : 4096;
     try {
@@ -942,6 +953,7 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
         *value = debug_bounds(b) ? double(b[k == "bounds_sites"]) : -1.0;
     }
     else if (k == "fv_variant") *value = double(c->dev.m.fv_variant);
+    else if (k == "fv_filter") *value = c->dev.fv_filter;
     else if (k == "create_ms_setup") *value = c->create_ms[0];
     else if (k == "create_ms_device") *value = c->create_ms[1];
     else if (k == "create_ms_capture") *value = c->create_ms[2];
@@ -1373,6 +1385,7 @@ int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, 
     if (!c) return HLBM_EINVAL;
     const Plan &P = c->plan;
     if (P.precision != HLBM_FP64) return fail(c, HLBM_ENOTIMPL, "the finite-volume adjoint runs on FP64 contexts");
+    if (c->dev.fv_filter > 0.0) return fail(c, HLBM_ENOTIMPL, "the adjoint does not cover the fv_filter option");
     if (P.n == 0) return fail(c, HLBM_EINVAL, "the context has no mesh");
     if (n_window < 1 || n_window > P.n_sub) return fail(c, HLBM_EINVAL, "n_window must be in 1..n_sub");
     if (!J) return fail(c, HLBM_EINVAL, "J is NULL");
@@ -1463,6 +1476,7 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, dou
     if (!c) return HLBM_EINVAL;
     const Plan &P = c->plan;
     if (P.precision != HLBM_FP64) return fail(c, HLBM_ENOTIMPL, "the adjoint runs on FP64 contexts");
+    if (c->dev.fv_filter > 0.0) return fail(c, HLBM_ENOTIMPL, "the adjoint does not cover the fv_filter option");
     if (P.n == 0) return fail(c, HLBM_EINVAL, "the context has no mesh");
     if (n_steps < 1) return fail(c, HLBM_EINVAL, "n_steps must be >= 1");
     if (n_skip < 0 || n_skip >= n_steps) return fail(c, HLBM_EINVAL, "n_skip must be in 0..n_steps-1");
@@ -1838,7 +1852,8 @@ std::string ckpt_header(hlbm_ctx *c, const std::vector<Blob> &v)
              std::to_string(P.lv[l].ox) + ", " + std::to_string(P.lv[l].oy) + "]";
     h += "], \"mesh_nodes\": " + std::to_string(P.n) + ", \"n_sub\": " + std::to_string(P.n_sub) +
          ", \"force_cap\": " + std::to_string(c->dev.force_cap) + ", \"wall_stats\": " +
-         std::to_string(c->dev.m.wall_stats) + ", \"buffers\": [";
+         std::to_string(c->dev.m.wall_stats) + ", \"fv_filter\": " + std::to_string(c->dev.fv_filter) +
+         ", \"buffers\": [";
     for (size_t k = 0; k < v.size(); k++) h += std::string(k ? ", " : "") + std::to_string(v[k].bytes);
     h += "]}";
     return h;

@@ -72,6 +72,7 @@ struct DevMesh {
     int wall_stats = 0;
     double *wall_ns = nullptr, *wall_acc = nullptr;
     int *inv = nullptr;                  // input node -> device node
+    void *lap = nullptr;                 // [9][Np] scratch of the odd-even filter (allocated when it is on)
 };
 
 // FP16S lattice storage shift: s_i = f^eq_i(1, (u0, 0)) - w_i (free stream).
@@ -86,6 +87,7 @@ struct DevCtx {
     DevMesh m;
     double u0 = 0, tau_u = 0, dt_u = 0, qdyn = 0;
     int n_sub = 0;
+    double fv_filter = 0;  // odd-even filter strength per finest step (0: off)
     double *force_buf = nullptr;  // [force_cap][2]
     double *force_partial = nullptr;  // [ceil(n_edges / 128)][2] per-block partial sums
     int *force_counter = nullptr;
@@ -109,6 +111,8 @@ template <typename T, typename S> void launch_restrict(const DevCtx &, int c_coa
 template <typename T, typename S> void launch_ring_interp(const DevCtx &, bool q1_and_star, cudaStream_t);
 template <typename T, typename S> void launch_hole_interp(const DevCtx &, cudaStream_t);
 template <typename T, typename S> void launch_fv(const DevCtx &, int m, cudaStream_t);
+// odd-even filter of the mesh state (g[gcur] -> g[gcur ^ 1]); no launch when off
+template <typename T, typename S> void launch_fv_filter(const DevCtx &, cudaStream_t);
 template <typename T, typename S> void launch_forces(const DevCtx &, cudaStream_t);
 // FP64 total of sum_i (f_i - w_i) over level 0's computed nodes into out[0] (row_sum: ny0 doubles)
 template <typename T, typename S> void launch_mass(const DevCtx &, double *row_sum, double *out, cudaStream_t);

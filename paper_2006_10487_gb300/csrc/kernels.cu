@@ -880,6 +880,119 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
     for (int i = 3; i < 9; i++) gn[size_t(i) * Np + r] = nq[i];
 }
 
+// Odd-even filter of the mesh state, once per finest step after the Eq. 3
+// sub-steps (an addition to the paper's method, off unless the context is
+// created with fv_filter = sigma > 0): with the graph Laplacian of the Eq. 3
+// collision weights, (L g)_i(P) = sum_{k != P} C_Pk [g_i(P_k) - g_i(P)],
+//   g <- g - sigma L d,  d = L g on fluid rows, 0 on wall and ring rows,
+// on the fluid rows; wall and ring rows keep their state (at a boundary row L
+// is a one-sided first-order difference).  C_Pk is read back from the
+// operator entries (stored as dt/tau_u C_Pk: C_Pk = entry * c_scale,
+// c_scale = tau_u / dt); A_P C_Pk is symmetric.  Two passes, one
+// thread per row, neighbours gathered from global memory (L2):
+// k_fv_lap writes L g ([9][Np], differences g(P_k) - g(P) formed as in the
+// sub-step: f^eq through moment differences, f^neq directly), k_fv_bilap
+// applies -sigma L to it and updates the (rho, u, f^neq) state.
+template <typename T>
+__global__ void __launch_bounds__(128) k_fv_lap(const T *__restrict__ g, T *__restrict__ lap, int Np, int n,
+                                                 const int *__restrict__ slice_ptr, const int *__restrict__ slice_len,
+                                                 const typename Ent<T>::type *__restrict__ ent,
+                                                 const int *__restrict__ halo_ptr, const int *__restrict__ halo_nodes,
+                                                 T c_scale, int n_wall, int ring_start)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    if (r < n_wall || r >= ring_start) {
+#pragma unroll
+        for (int i = 0; i < 9; i++) lap[size_t(i) * Np + r] = T(0);
+        return;
+    }
+    T r1P, uPx, uPy, nP[9];
+    load_mesh(g, Np, r, r1P, uPx, uPy, nP);
+    T E[9], acc[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        E[i] = Efun<T>(i, uPx, uPy);
+        acc[i] = T(0);
+    }
+    const int sl = r >> 5, base = slice_ptr[sl] + (r & 31), len = slice_len[sl];
+    const int h0 = halo_ptr[r / kTileRows];
+    for (int e = 0; e < len; e++) {
+        T a, b, cs;
+        int col;
+        unpack(ent[base + 32 * e], a, b, cs, col);
+        if (cs == T(0)) continue;  // padding entry
+        const T w = cs * c_scale;
+        const int k = HLBM_CHK(halo_nodes[h0 + col], Np, kSiteMesh);
+        T r1k, ukx, uky, nk[9];
+        load_mesh(g, Np, k, r1k, ukx, uky, nk);
+        const T drho = r1k - r1P, rhok = T(1) + r1k;
+        const T dux = ukx - uPx, duy = uky - uPy, sux = ukx + uPx, suy = uky + uPy;
+#pragma unroll
+        for (int i = 0; i < 9; i++) acc[i] += w * (feq_diff<T>(i, E[i], drho, rhok, dux, duy, sux, suy) + nk[i] - nP[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; i++) lap[size_t(i) * Np + r] = acc[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_fv_bilap(const T *__restrict__ g, const T *__restrict__ lap,
+                                                   T *__restrict__ gn, int Np, int n,
+                                                   const int *__restrict__ slice_ptr, const int *__restrict__ slice_len,
+                                                   const typename Ent<T>::type *__restrict__ ent,
+                                                   const int *__restrict__ halo_ptr,
+                                                   const int *__restrict__ halo_nodes, T c_scale, T sigma, int n_wall,
+                                                   int ring_start)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    if (r < n_wall || r >= ring_start) {  // boundary rows: unchanged
+#pragma unroll
+        for (int i = 0; i < 9; i++) gn[size_t(i) * Np + r] = g[size_t(i) * Np + r];
+        return;
+    }
+    T dP[9], acc[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        dP[i] = lap[size_t(i) * Np + r];
+        acc[i] = T(0);
+    }
+    const int sl = r >> 5, base = slice_ptr[sl] + (r & 31), len = slice_len[sl];
+    const int h0 = halo_ptr[r / kTileRows];
+    for (int e = 0; e < len; e++) {
+        T a, b, cs;
+        int col;
+        unpack(ent[base + 32 * e], a, b, cs, col);
+        if (cs == T(0)) continue;
+        const T w = cs * c_scale;
+        const int k = HLBM_CHK(halo_nodes[h0 + col], Np, kSiteMesh);
+#pragma unroll
+        for (int i = 0; i < 9; i++) acc[i] += w * (lap[size_t(i) * Np + k] - dP[i]);
+    }
+    T r1P, uPx, uPy, nP[9];
+    load_mesh(g, Np, r, r1P, uPx, uPy, nP);
+    T drho = 0, djx = 0, djy = 0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        acc[i] *= -sigma;
+        drho += acc[i];
+        djx += T(cx(i)) * acc[i];
+        djy += T(cy(i)) * acc[i];
+    }
+    const T rho = T(1) + r1P + drho;
+    T ux = uPx + (djx - drho * uPx) / rho, uy = uPy + (djy - drho * uPy) / rho;
+    const T dux = ux - uPx, duy = uy - uPy, sux = ux + uPx, suy = uy + uPy;
+    T nq[9];
+#pragma unroll
+    for (int i = 0; i < 9; i++)
+        nq[i] = nP[i] + acc[i] - feq_diff<T>(i, Efun<T>(i, uPx, uPy), drho, rho, dux, duy, sux, suy);
+    gn[r] = r1P + drho;
+    gn[size_t(Np) + r] = ux;
+    gn[size_t(2) * Np + r] = uy;
+#pragma unroll
+    for (int i = 3; i < 9; i++) gn[size_t(i) * Np + r] = nq[i];
+}
+
 // Eq. 10-11: force on the body from nodal pressure and stress at the wall,
 // traction -(p - p0) n - Pi^neq . n with p = rho / 3, edge values the mean of
 // the two end nodes.  Two passes with a fixed summation order (deterministic):
@@ -1231,6 +1344,22 @@ template <typename T, typename S> void launch_fv(const DevCtx &C, int msub, cuda
     }
 }
 
+template <typename T, typename S> void launch_fv_filter(const DevCtx &C, cudaStream_t s)
+{
+    const DevMesh &m = C.m;
+    if (m.n == 0 || !(C.fv_filter > 0.0) || !m.lap) return;
+    const T c_scale = T(C.tau_u / C.dt_u);
+    const unsigned nb = cdiv(m.n, 128);
+    using E = typename Ent<T>::type;
+    k_fv_lap<T><<<nb, 128, 0, s>>>((const T *)m.g[m.gcur], (T *)m.lap, m.Np, m.n, (const int *)m.slice_ptr,
+                                   (const int *)m.slice_len, (const E *)m.ent, (const int *)m.halo_ptr,
+                                   (const int *)m.halo_nodes, c_scale, m.n_wall, m.ring_start);
+    k_fv_bilap<T><<<nb, 128, 0, s>>>((const T *)m.g[m.gcur], (const T *)m.lap, (T *)m.g[m.gcur ^ 1], m.Np, m.n,
+                                     (const int *)m.slice_ptr, (const int *)m.slice_len, (const E *)m.ent,
+                                     (const int *)m.halo_ptr, (const int *)m.halo_nodes, c_scale, T(C.fv_filter),
+                                     m.n_wall, m.ring_start);
+}
+
 // Block-shape autotuner of the sub-step kernel (FP32): times each register
 // bound on this mesh (reps launches reading the current state buffer and
 // writing the other one, which the next sub-step overwrites, so the state is
@@ -1349,6 +1478,7 @@ void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *u
     template void launch_ring_interp<T, S>(const DevCtx &, bool, cudaStream_t);                                  \
     template void launch_hole_interp<T, S>(const DevCtx &, cudaStream_t);                                        \
     template void launch_fv<T, S>(const DevCtx &, int, cudaStream_t);                                            \
+    template void launch_fv_filter<T, S>(const DevCtx &, cudaStream_t);                                         \
     template int fv_autotune<T, S>(DevCtx &, cudaStream_t, double *);                                            \
     template void launch_forces<T, S>(const DevCtx &, cudaStream_t);                                             \
     template void launch_mass<T, S>(const DevCtx &, double *, double *, cudaStream_t);                           \

@@ -92,6 +92,24 @@ def test_fp64_matches_oracle(H, orc, name, steps, aoa):
         assert np.abs(cl - ocl).max() <= FP64_TOL * max(np.abs(ocl).max(), np.abs(ocd).max())
 
 
+@pytest.mark.parametrize("name,steps,aoa", [("hlbm_small", 30, 8.0), ("hlbm_mini3", 20, 3.0)])
+def test_fp64_with_the_odd_even_filter_matches_oracle(H, orc, name, steps, aoa):
+    """The optional odd-even filter of the mesh state (fv_filter = 0.05, once
+    per finest step): every grid and the force series within 1e-12 of the
+    oracle's filtered run."""
+    case = make_case(name, aoa_deg=aoa, fv_filter=0.05)
+    sol = H.Solver(case, precision="fp64")
+    sim = orc.Oracle(case)
+    assert sol.info("fv_filter") == 0.05
+    sol.step(steps)
+    sim.step(steps)
+    compare_fields(sol, sim, case, FP64_TOL, f"{name} filtered")
+    cd, cl = sol.forces()
+    ocd, ocl = sim.forces()
+    assert np.abs(cd - ocd).max() <= FP64_TOL * np.abs(ocd).max()
+    assert np.abs(cl - ocl).max() <= FP64_TOL * max(np.abs(ocl).max(), np.abs(ocd).max())
+
+
 @pytest.mark.slow
 def test_config1_full_run_fp64(H, orc):
     """Config 1 over its whole nominal run (2000 steps of the 200 x 100 lattice
@@ -339,11 +357,12 @@ def test_checkpoint_resume_is_bitwise(H, tmp_path):
     """hlbm_save after 7 coarse steps, hlbm_load into a new context made from
     the same inputs, 5 more steps each: the same fields on every grid, force
     series and wall statistics, bit for bit; another precision is refused."""
-    for name, prec in (("hlbm_mini2", "fp32"), ("hlbm_small", "fp16s"), ("hlbm_mini2", "fp64")):
-        case = make_case(name, aoa_deg=4.0)
+    for name, prec, filt in (("hlbm_mini2", "fp32", 0.0), ("hlbm_small", "fp16s", 0.0), ("hlbm_mini2", "fp64", 0.0),
+                             ("hlbm_small", "fp32", 0.01)):
+        case = make_case(name, aoa_deg=4.0, fv_filter=filt)
         a = H.Solver(case, precision=prec, wall_stats=True)
         a.step(7)
-        path = str(tmp_path / f"{name}_{prec}.ckpt")
+        path = str(tmp_path / f"{name}_{prec}_{filt:g}.ckpt")
         a.save(path)
         b = H.Solver(case, precision=prec, wall_stats=True)
         b.load(path)
@@ -359,12 +378,13 @@ def test_checkpoint_resume_is_bitwise(H, tmp_path):
         assert wa[1] == wb[1] == 12 and np.array_equal(wa[0], wb[0])
     other = H.Solver(make_case("hlbm_mini2", aoa_deg=4.0), precision="fp32", wall_stats=True)
     with pytest.raises(H.HlbmError) as e:
-        other.load(str(tmp_path / "hlbm_mini2_fp64.ckpt"))
+        other.load(str(tmp_path / "hlbm_mini2_fp64_0.ckpt"))
     assert e.value.code == H.HLBM_EINVAL
 
 
-def test_graphs_and_plain_launches_agree_bitwise(H):
-    case = make_case("hlbm_mini2")
+@pytest.mark.parametrize("filt", [0.0, 0.02])
+def test_graphs_and_plain_launches_agree_bitwise(H, filt):
+    case = make_case("hlbm_mini2", fv_filter=filt)
     a = H.Solver(case, precision="fp64", use_graphs=True)
     b = H.Solver(case, precision="fp64", use_graphs=False)
     a.step(9)

@@ -174,6 +174,7 @@ class Case:
     steps: int = 100            # coarse steps of the nominal run
     n_theta: int = 0
     n_layers: int = 0
+    fv_filter: float = 0.0      # odd-even filter of the mesh state per finest step (0: off)
 
     @property
     def n_levels(self):

@@ -215,8 +215,9 @@ class Solver:
         return float(J[0]), gg, gc, gx, float(da[0])
 
     def adjoint(self, n_steps, wd=1.0, wl=0.0, skip=0):
-        """Discrete adjoint of n_steps coarse steps of an FP64 solver
-        (hlbm_adjoint): J = mean of wd C_D + wl C_L over the steps after the
+        """Discrete adjoint of n_steps coarse steps of an FP64 or FP32 solver
+        (hlbm_adjoint; FP32: FP32 forward steps, FP64 reverse sweep and
+        gradient sums): J = mean of wd C_D + wl C_L over the steps after the
         first `skip`, the
         gradients in every level's lattice populations (a list, level order,
         each [ny * nx, 9]) and in the mesh populations [n_nodes, 9] of the

@@ -47,6 +47,7 @@ struct hlbm_ctx {
     double create_ms[3] = {0.0, 0.0, 0.0};  // host set-up tables, device build, graph capture
     double build_ms[2] = {0.0, 0.0};         // device build: tables and uploads; initial state and autotuner
     AdjTables adj;                            // finite-volume adjoint tables (built on first use)
+    hlbm_ctx *shadow = nullptr;               // FP32 contexts: FP64 twin holding the adjoint's tables
     struct AdjRecorder *rec = nullptr;        // set while the adjoint records a coarse step
     void *(*alloc_fn)(size_t, void *) = nullptr;
     void (*free_fn)(void *, void *) = nullptr;
@@ -171,6 +172,7 @@ struct LevelRec {
 struct AdjRecorder {
     hlbm_ctx *c = nullptr;
     cudaStream_t s = nullptr;
+    bool f32 = false;  // the recorded buffers hold FP32 values (widened to FP64 when kept)
     std::vector<LevelRec> recs;
     std::vector<void *> blocks;
     double *keep(const void *src, size_t doubles);
@@ -184,7 +186,8 @@ double *AdjRecorder::keep(const void *src, size_t doubles)
 {
     double *p = (double *)dalloc(c, doubles * sizeof(double));
     blocks.push_back(p);
-    ck(cudaMemcpyAsync(p, src, doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "record");
+    if (f32) launch_widen((const float *)src, p, doubles, s);
+    else ck(cudaMemcpyAsync(p, src, doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "record");
     return p;
 }
 void AdjRecorder::release()
@@ -1106,6 +1109,11 @@ int hlbm_sync(hlbm_ctx *c)
 int hlbm_destroy(hlbm_ctx *c)
 {
     if (!c) return HLBM_OK;
+    if (c->shadow) {
+        release(c->shadow);
+        delete c->shadow;
+        c->shadow = nullptr;
+    }
     release(c);
     delete c;
     return HLBM_OK;
@@ -1470,12 +1478,38 @@ int hlbm_fv_adjoint(hlbm_ctx *c, int n_window, double wd, double wl, double *J, 
     return rc;
 }
 
+namespace {
+// The FP64 twin of an FP32 context: the same plan built with FP64 device
+// tables (Eq. 3 entries, Eq. 8 and Eq. 9 weights, ...) and its own FP64
+// adjoint tables, for the reverse sweep of an adjoint whose forward steps run
+// in FP32.  Shares the caller's stream and allocator; freed with the context.
+void make_shadow(hlbm_ctx *c)
+{
+    hlbm_ctx *t = new hlbm_ctx();
+    t->plan = c->plan;
+    t->plan.precision = HLBM_FP64;
+    t->stream = c->stream;
+    t->alloc_fn = c->alloc_fn;
+    t->free_fn = c->free_fn;
+    t->alloc_ctx = c->alloc_ctx;
+    t->dev.force_cap = 1;
+    try {
+        build_device<double, double>(t);
+    } catch (...) {
+        release(t);
+        delete t;
+        throw;
+    }
+    c->shadow = t;
+}
+}  // namespace
+
 int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, double *J, double *grad_lattice,
                  size_t cap_lat, double *grad_mesh, size_t cap_mesh, double *grad_xy, size_t cap_xy, double *dJ_daoa)
 {
     if (!c) return HLBM_EINVAL;
     const Plan &P = c->plan;
-    if (P.precision != HLBM_FP64) return fail(c, HLBM_ENOTIMPL, "the adjoint runs on FP64 contexts");
+    if (P.precision == HLBM_FP16S) return fail(c, HLBM_ENOTIMPL, "the adjoint runs on FP64 and FP32 contexts");
     if (c->dev.fv_filter > 0.0) return fail(c, HLBM_ENOTIMPL, "the adjoint does not cover the fv_filter option");
     if (P.n == 0) return fail(c, HLBM_EINVAL, "the context has no mesh");
     if (n_steps < 1) return fail(c, HLBM_EINVAL, "n_steps must be >= 1");
@@ -1503,17 +1537,31 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, dou
     const long launches0 = c->launches, lps0 = c->launches_per_step;
     bool side0[hlbm::kMaxLevels];
     std::copy(c->side_ok, c->side_ok + hlbm::kMaxLevels, side0);
+    // FP32 contexts: the forward steps (checkpointed passes and recorded
+    // steps) run in FP32 on the context's own kernels; every recorded buffer
+    // is widened to FP64, and the reverse sweep (the finite-volume groups it
+    // recomputes, every adjoint kernel and all gradient sums) runs in FP64
+    // with the tables of an FP64 twin of the context
+    const bool f32 = P.precision == HLBM_FP32;
+    const size_t es = f32 ? sizeof(float) : sizeof(double);  // state element size of the forward
     AdjRecorder rec;
     rec.c = c;
     rec.s = c->stream;
+    rec.f32 = f32;
     try {
-        if (!c->adj.built) build_adjoint_tables(c);
-        if (!c->adj.coupled_built) build_coupled_tables(c);
-        const AdjTables &A = c->adj;
+        if (f32 && !c->shadow) make_shadow(c);
+        hlbm_ctx *tc = f32 ? c->shadow : c;
+        if (!tc->adj.built) build_adjoint_tables(tc);
+        if (!tc->adj.coupled_built) build_coupled_tables(tc);
+        const AdjTables &A = tc->adj;
+        const DevCtx DT = tc->dev;  // FP64 tables of the reverse sweep (D0 itself for FP64)
         cudaStream_t s = c->stream;
         const int Np = D0.m.Np, nr = std::max(1, D0.m.n_ring);
         const size_t plane = size_t(9) * Np, qn = size_t(12) * nr;
-        auto copy = [&](void *dst, const void *src, size_t doubles) {
+        auto copy = [&](void *dst, const void *src, size_t elems) {  // forward state (es bytes per element)
+            ck(cudaMemcpyAsync(dst, src, elems * es, cudaMemcpyDeviceToDevice, s), "copy");
+        };
+        auto copyd = [&](double *dst, const double *src, size_t doubles) {
             ck(cudaMemcpyAsync(dst, src, doubles * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
         };
         // the evolving state: every level's lattice and band buffers, the mesh
@@ -1534,19 +1582,21 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, dou
         const void *orig[64];
         for (size_t k = 0; k < parts.size(); k++) {
             orig[k] = *parts[k].first;
-            *parts[k].first = scr(parts[k].second * sizeof(double));
+            *parts[k].first = scr(parts[k].second * es);
             copy(*parts[k].first, orig[k], parts[k].second);
         }
-        auto save = [&](double *dst) {
+        auto save = [&](double *dst_) {
+            char *dst = (char *)dst_;
             for (auto &pt : parts) {
                 copy(dst, *pt.first, pt.second);
-                dst += pt.second;
+                dst += pt.second * es;
             }
         };
-        auto load = [&](const double *src) {
+        auto load = [&](const double *src_) {
+            const char *src = (const char *)src_;
             for (auto &pt : parts) {
                 copy(*pt.first, src, pt.second);
-                src += pt.second;
+                src += pt.second * es;
             }
         };
         W.force_cap = K;
@@ -1564,7 +1614,8 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, dou
         auto step = [&]() {
             std::swap(c->dev, W);
             try {
-                coarse_step<double, double>(c, s);
+                if (f32) coarse_step<float, float>(c, s);
+                else coarse_step<double, double>(c, s);
             } catch (...) {
                 std::swap(c->dev, W);
                 throw;
@@ -1578,8 +1629,8 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, dou
         const int S = std::max(1, int(std::ceil(std::sqrt(double(K)))));
         const int nseg = (K + S - 1) / S;
         std::vector<double *> cpt(nseg), sst(S);
-        for (int j = 0; j < nseg; j++) cpt[j] = scr(state_doubles * sizeof(double));
-        for (int j = 0; j < S; j++) sst[j] = scr(state_doubles * sizeof(double));
+        for (int j = 0; j < nseg; j++) cpt[j] = scr(state_doubles * es);
+        for (int j = 0; j < S; j++) sst[j] = scr(state_doubles * es);
         for (int k = 0; k < K; k++) {  // first pass: forces and segment checkpoints
             phase(k);
             if (k % S == 0) save(cpt[k / S]);
@@ -1638,7 +1689,7 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, dou
         const int fin = L - 1;
         const double inv_q = 1.0 / P.qdyn, dt = 1.0 / ns, dt_tau = dt / P.tau_u, csP = dt_tau * (11.0 / 18.0);
         const double scale5 = 1.0 - 1.0 / (2.0 * D0.lv[fin].tau);
-        const double *ring_w = (const double *)D0.m.ring_w;
+        const double *ring_w = (const double *)DT.m.ring_w;
         std::vector<size_t> subtree(L, 1);  // level steps in one advance() of level l
         for (int l = L - 2; l >= 0; l--) subtree[l] = 1 + 2 * subtree[l + 1];
         bool terminal = false;
@@ -1646,14 +1697,14 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, dou
         // boundary ring, interface data and finite-volume group)
         auto level_adj = [&](const LevelRec &R) {
             const int l = R.l, Pk = R.P;
-            const DevLevel &dl = D0.lv[l];
+            const DevLevel &dl = DT.lv[l];
             if (l == fin) {
-                DevCtx V = W;  // the finite-volume group again, from the step's records
+                DevCtx V = DT;  // the finite-volume group again (FP64), from the step's records
                 V.lv[l].f = R.f_end;
                 V.lv[l].parity = Pk ^ 1;
                 V.m.Q0 = R.Q0;
                 V.m.Q1 = qtmp;
-                copy(st, R.g_start, plane);
+                copyd(st, R.g_start, plane);
                 V.m.g[0] = st;
                 V.m.gcur = 0;
                 launch_ring_interp<double, double>(V, true, s);  // interface rows at theta = 0
@@ -1672,25 +1723,25 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, dou
                 double *lin = lam_g, *lout = lam_t;
                 for (int m = ns - 1; m >= 0; m--) {
                     const double th = double(m + 1) / ns;
-                    if (m < ns - 1) launch_adj_ring_rows(D0.m, scale5, 1.0 - th, th, lin, lQ0, lQ1, s);
+                    if (m < ns - 1) launch_adj_ring_rows(DT.m, scale5, 1.0 - th, th, lin, lQ0, lQ1, s);
                     launch_fv_adjoint(A, st + size_t(m) * plane, Np, n, csP, P.n_wall, P.ring_start,
                                       m < ns - 1 ? 1 : 0, dt, dt_tau, lin, lout, gc, rs, s);
                     std::swap(lin, lout);
                 }
-                launch_adj_ring_rows(D0.m, scale5, 1.0, 0.0, lin, lQ0, lQ1, s);
+                launch_adj_ring_rows(DT.m, scale5, 1.0, 0.0, lin, lQ0, lQ1, s);
                 if (lin != lam_g) std::swap(lam_g, lam_t);
-                if (geo) launch_adj_ring_weights(dl, D0.m, R.f_end, Pk ^ 1, lQ1, lw9, s);
-                launch_adj_ring_lattice(dl, R.f_end, Pk ^ 1, A, ring_w, lQ1, D0.m.n_ring, lam_f[l], s);
+                if (geo) launch_adj_ring_weights(dl, DT.m, R.f_end, Pk ^ 1, lQ1, lw9, s);
+                launch_adj_ring_lattice(dl, R.f_end, Pk ^ 1, A, ring_w, lQ1, DT.m.n_ring, lam_f[l], s);
             }
             if (l == 0) launch_adj_outer_bc(dl, R.f_end, Pk ^ 1, P.u0, lam_f[0], s);
             else
-                launch_adj_prolong(D0.lv[l - 1], dl, Pk ^ 1, R.theta, R.sA, R.sB, A.pp[l], A.pk[l], A.pw[l], lam_f[l],
+                launch_adj_prolong(DT.lv[l - 1], dl, Pk ^ 1, R.theta, R.sA, R.sB, A.pp[l], A.pk[l], A.pw[l], lam_f[l],
                                    lamp, lsA[l - 1], lsB[l - 1], s);
             launch_adj_collide(dl, R.f_start, Pk, lam_f[l], s);
             if (l == fin) {
-                launch_adj_hole(dl, D0.m, A, R.g_start, Pk, lam_f[l], lamq, lam_g, s, lw6);
-                if (geo) launch_adj_ring_weights(dl, D0.m, R.f_start, Pk, lQ0, lw9, s);
-                launch_adj_ring_lattice(dl, R.f_start, Pk, A, ring_w, lQ0, D0.m.n_ring, lam_f[l], s);
+                launch_adj_hole(dl, DT.m, A, R.g_start, Pk, lam_f[l], lamq, lam_g, s, lw6);
+                if (geo) launch_adj_ring_weights(dl, DT.m, R.f_start, Pk, lQ0, lw9, s);
+                launch_adj_ring_lattice(dl, R.f_start, Pk, A, ring_w, lQ0, DT.m.n_ring, lam_f[l], s);
                 ck(cudaMemsetAsync(lQ0, 0, qn * sizeof(double), s), "memset");
                 ck(cudaMemsetAsync(lQ1, 0, qn * sizeof(double), s), "memset");
             }
@@ -1703,15 +1754,15 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, dou
             if (l < L - 1) {
                 const size_t second = idx + 1 + subtree[l + 1];
                 const LevelRec &R2 = rec.recs[second];
-                launch_adj_restrict(D0.lv[l], D0.lv[l + 1], R.P ^ 1, R2.P ^ 1, R.f_child, lam_f[l], lam_f[l + 1], s);
+                launch_adj_restrict(DT.lv[l], DT.lv[l + 1], R.P ^ 1, R2.P ^ 1, R.f_child, lam_f[l], lam_f[l + 1], s);
                 rev(second, l + 1);
                 rev(idx + 1, l + 1);
-                launch_adj_snapshot(D0.lv[l], R.f_end, R.P ^ 1, lsB[l], lam_f[l], s);
+                launch_adj_snapshot(DT.lv[l], R.f_end, R.P ^ 1, lsB[l], lam_f[l], s);
                 ck(cudaMemsetAsync(lsB[l], 0, 12 * size_t(D0.lv[l].band_n) * sizeof(double), s), "memset");
             }
             level_adj(R);
             if (l < L - 1) {
-                launch_adj_snapshot(D0.lv[l], R.f_start, R.P, lsA[l], lam_f[l], s);
+                launch_adj_snapshot(DT.lv[l], R.f_start, R.P, lsA[l], lam_f[l], s);
                 ck(cudaMemsetAsync(lsA[l], 0, 12 * size_t(D0.lv[l].band_n) * sizeof(double), s), "memset");
             }
         };
@@ -1752,15 +1803,21 @@ int hlbm_adjoint(hlbm_ctx *c, int n_steps, int n_skip, double wd, double wl, dou
         if (gl) {
             size_t off = 0;
             for (int l = 0; l < L; l++) {
-                const DevLevel &dl = D0.lv[l];
+                const DevLevel &dl = DT.lv[l];
                 launch_adj_lattice_out(dl, lam_f[l], l == 0 ? int(k0 & 1) : 0, gl + off, s);
                 off += 9 * size_t(dl.nx) * dl.ny;
             }
         }
-        launch_adj_populations(A, (const double *)W.m.g[W.m.gcur], Np, n, lam_g, gg, s);
+        const double *g0 = (const double *)W.m.g[W.m.gcur];
+        if (f32) {  // the initial mesh state, widened
+            double *g64 = scr(plane * sizeof(double));
+            launch_widen((const float *)W.m.g[W.m.gcur], g64, plane, s);
+            g0 = g64;
+        }
+        launch_adj_populations(A, g0, Np, n, lam_g, gg, s);
         if (geo) {
             const double al = P.aoa_deg * M_PI / 180.0;
-            launch_adj_geometry_coupled(A, D0.m, n, gc, hacc, lw6, lw9, std::cos(al), std::sin(al), P.pivot[0],
+            launch_adj_geometry_coupled(A, DT.m, n, gc, hacc, lw6, lw9, std::cos(al), std::sin(al), P.pivot[0],
                                         P.pivot[1], gsc, gxy, daoa, s);
         }
         ck(cudaGetLastError(), "adjoint kernels");

@@ -111,6 +111,8 @@ template <typename T, typename S> void launch_restrict(const DevCtx &, int c_coa
 template <typename T, typename S> void launch_ring_interp(const DevCtx &, bool q1_and_star, cudaStream_t);
 template <typename T, typename S> void launch_hole_interp(const DevCtx &, cudaStream_t);
 template <typename T, typename S> void launch_fv(const DevCtx &, int m, cudaStream_t);
+// FP32 -> FP64 copy of n values
+void launch_widen(const float *a, double *b, size_t n, cudaStream_t);
 // odd-even filter of the mesh state (g[gcur] -> g[gcur ^ 1]); no launch when off
 template <typename T, typename S> void launch_fv_filter(const DevCtx &, cudaStream_t);
 template <typename T, typename S> void launch_forces(const DevCtx &, cudaStream_t);

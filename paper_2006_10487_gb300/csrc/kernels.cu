@@ -572,6 +572,306 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     }
 }
 
+// One row of the FP64 sub-step: the sums over the row's neighbours (13 moment
+// sums of the f^eq differences, 16 sums of the stored f^neq planes) and the
+// closed-form update (see k_fv); the staged list holds nine planes.
+template <typename T>
+__device__ __forceinline__ void fv_row_f64(const T *__restrict__ sh, int hn, int own_pos,
+                                           const typename Ent<T>::type *__restrict__ se, int base, int len, T dt_tau,
+                                           int n_ent, T &r1, T &ux, T &uy, T nq[9])
+{
+    (void)n_ent;
+    // own state from the staged list
+    T r1P, uPx, uPy, nP[9];
+    {
+        const int p = HLBM_CHK(own_pos, hn, kSiteStaged);
+        r1P = sh[p];
+        uPx = sh[hn + p];
+        uPy = sh[2 * hn + p];
+#pragma unroll
+        for (int i = 3; i < 9; i++) nP[i] = sh[i * hn + p];
+        neq_complete(nP);
+    }
+    // own node: no streaming term (g(P) - g(P) = 0), collision weight C_PP = 11/18
+    // f^neq part of the sums, over the six stored planes j = 3..8 only:
+    //   U_j = sum_k a_k n_j(P_k), V_j = sum_k b_k n_j(P_k), W_j = sum_k cs_k n_j(P_k)
+    // (U_4 and V_3 are never needed: c_4x = c_3y = 0); planes 0-2 follow at the
+    // end from the same linear constraints that complete f^neq.
+    T U3 = 0, U5 = 0, U6 = 0, U7 = 0, U8 = 0, V4 = 0, V5 = 0, V6 = 0, V7 = 0, V8 = 0;
+    T W3 = 0, W4 = 0, W5 = 0, W6 = 0, W7 = 0, W8 = 0;
+    T Sa = 0, Sb = 0, Dx = 0, Dy = 0, Qxx = 0, Qyy = 0, Qxy = 0, Lx = 0, Ly = 0, Mx = 0, My = 0, Mxxy = 0, Mxyy = 0;
+    for (int e0 = 0; e0 < len; e0 += kFvGroup) {
+        T sx[kFvGroup], sy[kFvGroup], c[kFvGroup];
+        int k[kFvGroup];
+#pragma unroll
+        for (int j = 0; j < kFvGroup; j++) {
+            if (e0 + j < len) {
+                unpack(se[HLBM_CHK(base + 32 * (e0 + j), n_ent, kSiteEntry)], sx[j], sy[j], c[j], k[j]);
+                k[j] = HLBM_CHK(k[j], hn, kSiteStaged);
+            } else {
+                sx[j] = sy[j] = c[j] = T(0);
+                k[j] = 0;
+            }
+        }
+        T st[kFvGroup][9];
+#pragma unroll
+        for (int j = 0; j < kFvGroup; j++)
+#pragma unroll
+            for (int i = 0; i < 9; i++) st[j][i] = sh[i * hn + k[j]];
+#pragma unroll
+        for (int j = 0; j < kFvGroup; j++) {
+            const T a = sx[j], b = sy[j], cs = c[j];  // dt s_Pk and (dt / tau_u) C_Pk
+            const T drho = st[j][0] - r1P, rhok = T(1) + st[j][0];
+            const T dux = st[j][1] - uPx, duy = st[j][2] - uPy, sux = st[j][1] + uPx, suy = st[j][2] + uPy;
+            const T dus = dux * sux + duy * suy, ra = rhok * a, rb = rhok * b;
+            const T xs = dux * suy + duy * sux;
+            Sa += a;
+            Sb += b;
+            Dx += a * drho;
+            Dy += b * drho;
+            Qxx += ra * dux;
+            Qyy += rb * duy;
+            Qxy += ra * duy + rb * dux;
+            Lx += ra * dus;
+            Ly += rb * dus;
+            Mx += ra * dux * sux;
+            My += rb * duy * suy;
+            Mxxy += ra * xs + rb * dux * sux;
+            Mxyy += rb * xs + ra * duy * suy;
+            const T *nk = st[j];
+            U3 += a * nk[3]; U5 += a * nk[5]; U6 += a * nk[6]; U7 += a * nk[7]; U8 += a * nk[8];
+            V4 += b * nk[4]; V5 += b * nk[5]; V6 += b * nk[6]; V7 += b * nk[7]; V8 += b * nk[8];
+            W3 += cs * nk[3]; W4 += cs * nk[4]; W5 += cs * nk[5];
+            W6 += cs * nk[6]; W7 += cs * nk[7]; W8 += cs * nk[8];
+        }
+    }
+    // Update.  With acc_i = sum_k (c_i.(a_k, b_k) - cs_k) f^neq_i(P_k) + w_i eq_i
+    // - f^neq_i(P) (c_i.(Sa, Sb) + dt/tau_u C_PP) the increment of population i,
+    // its zeroth and first moments need no per-population sum: f^neq carries
+    // no mass or momentum and the D2Q9 weights are isotropic to fourth order,
+    //   drho = u_P.D + Q_xx + Q_yy
+    //   djx  = D_x/3 + u_Px (u_P.D) + 3/2 M_x + 1/2 M_xyy - 1/2 L_x
+    //          + sum_k (a_k Pi^neq_xx(P_k) + b_k Pi^neq_xy(P_k)) - (Sa Pi^neq_xx(P) + Sb Pi^neq_xy(P))
+    // (djy likewise), with sum_k a_k Pi^neq_xx(P_k) = 2 (U3 + U6 + U7) and so
+    // on.  The new f^neq is then needed for the stored planes 3..8 only;
+    // opposite diagonals (5, 7) and (6, 8) share the even and odd parts of
+    // eq_i and of the f^eq difference.
+    const T csP = dt_tau * T(11.0 / 18.0);
+    const T Pxx = nP[1] + nP[3] + nP[5] + nP[6] + nP[7] + nP[8];
+    const T Pyy = nP[2] + nP[4] + nP[5] + nP[6] + nP[7] + nP[8];
+    const T Pxy = nP[5] - nP[6] + nP[7] - nP[8];
+    const T uD = uPx * Dx + uPy * Dy;
+    const T drho = uD + Qxx + Qyy;
+    const T djx = Dx * T(1.0 / 3.0) + uPx * uD + T(1.5) * Mx + T(0.5) * Mxyy - T(0.5) * Lx + T(2) * (U3 + U6 + U7) +
+                  (V5 - V6 + V7 - V8) - (Sa * Pxx + Sb * Pxy);
+    const T djy = Dy * T(1.0 / 3.0) + uPy * uD + T(1.5) * My + T(0.5) * Mxxy - T(0.5) * Ly + (U5 - U6 + U7 - U8) +
+                  T(2) * (V4 + V7 + V8) - (Sb * Pyy + Sa * Pxy);
+    r1 = r1P + drho;
+    const T rho = T(1) + r1, irho = T(1) / rho;
+    const T dux = (djx - drho * uPx) * irho, duy = (djy - drho * uPy) * irho;
+    ux = uPx + dux;
+    uy = uPy + duy;
+    const T sx = ux + uPx, sy = uy + uPy;           // u' + u_P
+    const T E0 = T(1) - T(1.5) * (uPx * uPx + uPy * uPy);
+    const T ddot = T(1.5) * (dux * sx + duy * sy);  // 3/2 du.(u' + u_P)
+    // [f^eq_c(rho', u') - f^eq_c(rho_P, u_P)] / w_c for a direction c with E = E_c(u_P)
+    auto fd = [&](T E, T cdu, T csu) { return drho * E + rho * (T(3) * cdu + T(4.5) * cdu * csu - ddot); };
+    {  // axis directions 3 (-1, 0) and 4 (0, -1)
+        const T E3 = E0 - T(3) * uPx + T(4.5) * uPx * uPx;
+        const T eq3 = -E3 * Dx + T(3) * Qxx - T(4.5) * Mx + T(1.5) * Lx;
+        nq[3] = nP[3] - U3 - W3 + T(1.0 / 9.0) * eq3 + nP[3] * (Sa - csP) - T(1.0 / 9.0) * fd(E3, -dux, -sx);
+        const T E4 = E0 - T(3) * uPy + T(4.5) * uPy * uPy;
+        const T eq4 = -E4 * Dy + T(3) * Qyy - T(4.5) * My + T(1.5) * Ly;
+        nq[4] = nP[4] - V4 - W4 + T(1.0 / 9.0) * eq4 + nP[4] * (Sb - csP) - T(1.0 / 9.0) * fd(E4, -duy, -sy);
+    }
+    {  // diagonals 5 (1, 1) and 7 (-1, -1)
+        const T q = uPx + uPy, A = E0 + T(4.5) * q * q, B = T(3) * q;
+        const T Pd = Dx + Dy, C = T(3) * (Qxx + Qxy + Qyy);
+        const T Z = T(4.5) * (Mx + My + Mxxy + Mxyy) - T(1.5) * (Lx + Ly);
+        const T odd = A * Pd + Z, even = B * Pd + C;  // eq5 = even + odd, eq7 = even - odd
+        const T cdu = dux + duy, csu = sx + sy;
+        nq[5] = nP[5] + U5 + V5 - W5 + T(1.0 / 36.0) * (even + odd) - nP[5] * (Sa + Sb + csP) -
+                T(1.0 / 36.0) * fd(A + B, cdu, csu);
+        nq[7] = nP[7] - U7 - V7 - W7 + T(1.0 / 36.0) * (even - odd) + nP[7] * (Sa + Sb - csP) -
+                T(1.0 / 36.0) * fd(A - B, -cdu, -csu);
+    }
+    {  // diagonals 6 (-1, 1) and 8 (1, -1)
+        const T q = uPy - uPx, A = E0 + T(4.5) * q * q, B = T(3) * q;
+        const T Pd = Dy - Dx, C = T(3) * (Qxx - Qxy + Qyy);
+        const T Z = T(4.5) * (-Mx + My + Mxxy - Mxyy) - T(1.5) * (Ly - Lx);
+        const T odd = A * Pd + Z, even = B * Pd + C;  // eq6 = even + odd, eq8 = even - odd
+        const T cdu = duy - dux, csu = sy - sx;
+        nq[6] = nP[6] - U6 + V6 - W6 + T(1.0 / 36.0) * (even + odd) - nP[6] * (Sb - Sa + csP) -
+                T(1.0 / 36.0) * fd(A + B, cdu, csu);
+        nq[8] = nP[8] + U8 - V8 - W8 + T(1.0 / 36.0) * (even - odd) + nP[8] * (Sb - Sa - csP) -
+                T(1.0 / 36.0) * fd(A - B, -cdu, -csu);
+    }
+}
+
+// One row of the FP32 sub-step: the sums over the row's neighbours on paired
+// FP32 instructions (13 moment sums of the f^eq differences, 16 sums of the
+// stored f^neq planes) and the closed-form update (see k_fv); sh: the tile's
+// staged list, nine planes of hn values.
+__device__ __forceinline__ void fv_row_f32(const float *__restrict__ sh, int hn, int own_pos,
+                                           const float4 *__restrict__ se, int base, int len, float dt_tau,
+                                           int n_ent, float &r1, float &ux, float &uy, float nq[9])
+{
+    (void)n_ent;
+    // own state from the staged list
+    float r1P, uPx, uPy, nP[9];
+    {
+        const int p = HLBM_CHK(own_pos, hn, kSiteStaged);
+        r1P = sh[p];
+        uPx = sh[hn + p];
+        uPy = sh[2 * hn + p];
+#pragma unroll
+        for (int i = 3; i < 9; i++) nP[i] = sh[i * hn + p];
+        neq_complete(nP);
+    }
+    // own node: no streaming term (g(P) - g(P) = 0), collision weight C_PP = 11/18
+    // f^neq part of the sums, over the six stored planes j = 3..8 only:
+    //   U_j = sum_k a_k n_j(P_k), V_j = sum_k b_k n_j(P_k), W_j = sum_k cs_k n_j(P_k)
+    // (U_4 and V_3 are never needed: c_4x = c_3y = 0); planes 0-2 follow at the
+    // end from the same linear constraints that complete f^neq.
+    float U3 = 0, U5 = 0, U6 = 0, U7 = 0, U8 = 0, V4 = 0, V5 = 0, V6 = 0, V7 = 0, V8 = 0;
+    float W3 = 0, W4 = 0, W5 = 0, W6 = 0, W7 = 0, W8 = 0;
+    float Sa = 0, Sb = 0, Dx = 0, Dy = 0, Qxx = 0, Qyy = 0, Qxy = 0, Lx = 0, Ly = 0, Mx = 0, My = 0, Mxxy = 0, Mxyy = 0;
+    // the same sums on packed pairs: (U5,U6) (U7,U8) (V5,V6) (V7,V8) (U3,V4)
+    // (W3,W4) (W5,W6) (W7,W8) (Sa,Sb) (Dx,Dy) (Qxx,Qyy) (Qxy',Qxy'') (Lx,Ly)
+    // (Mx,My) (Mxxy,Mxyy)
+    const unsigned long long z = pk2(0.f, 0.f), uP = pk2(uPx, uPy);
+    unsigned long long U56 = z, U78 = z, V56 = z, V78 = z, U3V4 = z, W34 = z, W56 = z, W78 = z;
+    unsigned long long SS = z, DD = z, QQ = z, QX = z, LL = z, MM = z, MX = z;
+    for (int e0 = 0; e0 < len; e0++) {
+        float a, b, cs;
+        int k;
+        unpack(se[HLBM_CHK(base + 32 * e0, n_ent, kSiteEntry)], a, b, cs, k);
+        k = HLBM_CHK(k, hn, kSiteStaged);
+        const float r1k = sh[k], n3 = sh[3 * hn + k], n4 = sh[4 * hn + k], n5 = sh[5 * hn + k],
+                    n6 = sh[6 * hn + k], n7 = sh[7 * hn + k], n8 = sh[8 * hn + k];
+        const unsigned long long uk = pk2(sh[hn + k], sh[2 * hn + k]);
+        const float drho = r1k - r1P, rhok = 1.f + r1k;
+        const unsigned long long ab = pk2(a, b), aa = pk2(a, a), bb = pk2(b, b), cc = pk2(cs, cs);
+        const unsigned long long du = sub2(uk, uP), su = add2(uk, uP);   // (dux, duy), (sux, suy)
+        const unsigned long long pr = mul2(du, su);                      // (dux sux, duy suy)
+        const unsigned long long R = mul2(ab, pk2(rhok, rhok));          // (ra, rb)
+        float dux, duy, sux, suy, p0, p1, ra, rb;
+        upk2(du, dux, duy);
+        upk2(su, sux, suy);
+        upk2(pr, p0, p1);
+        upk2(R, ra, rb);
+        const float dus = p0 + p1, xs = dux * suy + duy * sux;
+        SS = add2(SS, ab);
+        DD = fma2(ab, pk2(drho, drho), DD);
+        QQ = fma2(R, du, QQ);
+        QX = fma2(R, pk2(duy, dux), QX);
+        LL = fma2(R, pk2(dus, dus), LL);
+        MM = fma2(R, pr, MM);
+        MX = fma2(R, pk2(xs, xs), fma2(pk2(rb, ra), pr, MX));
+        const unsigned long long n34 = pk2(n3, n4), n56 = pk2(n5, n6), n78 = pk2(n7, n8);
+        U56 = fma2(aa, n56, U56);
+        U78 = fma2(aa, n78, U78);
+        V56 = fma2(bb, n56, V56);
+        V78 = fma2(bb, n78, V78);
+        U3V4 = fma2(ab, n34, U3V4);
+        W34 = fma2(cc, n34, W34);
+        W56 = fma2(cc, n56, W56);
+        W78 = fma2(cc, n78, W78);
+    }
+    float q0, q1;
+    upk2(U56, U5, U6); upk2(U78, U7, U8); upk2(V56, V5, V6); upk2(V78, V7, V8); upk2(U3V4, U3, V4);
+    upk2(W34, W3, W4); upk2(W56, W5, W6); upk2(W78, W7, W8);
+    upk2(SS, Sa, Sb); upk2(DD, Dx, Dy); upk2(QQ, Qxx, Qyy); upk2(QX, q0, q1); Qxy = q0 + q1;
+    upk2(LL, Lx, Ly); upk2(MM, Mx, My); upk2(MX, Mxxy, Mxyy);
+    // Update.  With acc_i = sum_k (c_i.(a_k, b_k) - cs_k) f^neq_i(P_k) + w_i eq_i
+    // - f^neq_i(P) (c_i.(Sa, Sb) + dt/tau_u C_PP) the increment of population i,
+    // its zeroth and first moments need no per-population sum: f^neq carries
+    // no mass or momentum and the D2Q9 weights are isotropic to fourth order,
+    //   drho = u_P.D + Q_xx + Q_yy
+    //   djx  = D_x/3 + u_Px (u_P.D) + 3/2 M_x + 1/2 M_xyy - 1/2 L_x
+    //          + sum_k (a_k Pi^neq_xx(P_k) + b_k Pi^neq_xy(P_k)) - (Sa Pi^neq_xx(P) + Sb Pi^neq_xy(P))
+    // (djy likewise), with sum_k a_k Pi^neq_xx(P_k) = 2 (U3 + U6 + U7) and so
+    // on.  The new f^neq is then needed for the stored planes 3..8 only;
+    // opposite diagonals (5, 7) and (6, 8) share the even and odd parts of
+    // eq_i and of the f^eq difference.
+    const float csP = dt_tau * (11.f / 18.f);
+    const float Pxx = nP[1] + nP[3] + nP[5] + nP[6] + nP[7] + nP[8];
+    const float Pyy = nP[2] + nP[4] + nP[5] + nP[6] + nP[7] + nP[8];
+    const float Pxy = nP[5] - nP[6] + nP[7] - nP[8];
+    const float uD = uPx * Dx + uPy * Dy;
+    const float drho = uD + Qxx + Qyy;
+    const float djx = Dx * (1.f / 3.f) + uPx * uD + 1.5f * Mx + 0.5f * Mxyy - 0.5f * Lx + 2.f * (U3 + U6 + U7) +
+                  (V5 - V6 + V7 - V8) - (Sa * Pxx + Sb * Pxy);
+    const float djy = Dy * (1.f / 3.f) + uPy * uD + 1.5f * My + 0.5f * Mxxy - 0.5f * Ly + (U5 - U6 + U7 - U8) +
+                  2.f * (V4 + V7 + V8) - (Sb * Pyy + Sa * Pxy);
+    r1 = r1P + drho;
+    const float rho = 1.f + r1, irho = 1.f / rho;
+    const float dux = (djx - drho * uPx) * irho, duy = (djy - drho * uPy) * irho;
+    ux = uPx + dux;
+    uy = uPy + duy;
+    const float sx = ux + uPx, sy = uy + uPy;           // u' + u_P
+    const float E0 = 1.f - 1.5f * (uPx * uPx + uPy * uPy);
+    const float ddot = 1.5f * (dux * sx + duy * sy);  // 3/2 du.(u' + u_P)
+    // the same on pairs of directions: (3, 4) mirror each other in x <-> y;
+    // (5, 6) and (7, 8) are the two diagonal families' + and - members
+    const F2 U = f2(uPx, uPy);
+    const F2 E34 = fmaf2(f2(4.5f) * U, U, f2(E0) - f2(3.f) * U);
+    const F2 eq34 = f2(3.f) * f2(Qxx, Qyy) + f2(1.5f) * f2(Lx, Ly) - E34 * f2(Dx, Dy) - f2(4.5f) * f2(Mx, My);
+    const F2 n34 = f2(nP[3], nP[4]);
+    const F2 cdu34 = f2(-dux, -duy), csu34 = f2(-sx, -sy);
+    const F2 fd34 = fmaf2(f2(drho), E34,
+                          f2(rho) * (fmaf2(f2(4.5f) * cdu34, csu34, f2(3.f) * cdu34) - f2(ddot)));
+    const F2 nq34 = n34 - f2(U3, V4) - f2(W3, W4) + fmaf2(n34, f2(Sa - csP, Sb - csP), f2(1.f / 9.f) * (eq34 - fd34));
+    const F2 q = f2(uPx + uPy, uPy - uPx);
+    const F2 A = fmaf2(f2(4.5f) * q, q, f2(E0)), B = f2(3.f) * q;
+    const F2 Pd = f2(Dx + Dy, Dy - Dx);
+    const F2 Cq = f2(3.f) * f2(Qxx + Qyy + Qxy, Qxx + Qyy - Qxy);
+    const F2 Z = f2(4.5f) * f2(Mx + My + Mxxy + Mxyy, My - Mx + Mxxy - Mxyy) - f2(1.5f) * f2(Lx + Ly, Ly - Lx);
+    const F2 odd = fmaf2(A, Pd, Z), even = fmaf2(B, Pd, Cq);
+    const F2 cdu = f2(dux + duy, duy - dux), csu = f2(sx + sy, sy - sx);
+    const F2 t3 = fmaf2(f2(4.5f) * cdu, csu, f2(3.f) * cdu);  // 3 c.du + 9/2 (c.du)(c.su), + members
+    const F2 t3m = fmaf2(f2(4.5f) * cdu, csu, f2(-3.f) * cdu);  // the same for - members
+    const F2 fdp = fmaf2(f2(drho), A + B, f2(rho) * (t3 - f2(ddot)));
+    const F2 fdm = fmaf2(f2(drho), A - B, f2(rho) * (t3m - f2(ddot)));
+    const F2 n56 = f2(nP[5], nP[6]), n78 = f2(nP[7], nP[8]);
+    const F2 nq56 = n56 + f2(U5 + V5 - W5, V6 - U6 - W6) - n56 * f2(Sa + Sb + csP, Sb - Sa + csP) +
+                    f2(1.f / 36.f) * (even + odd - fdp);
+    const F2 nq78 = n78 - f2(U7 + V7 + W7, V8 - U8 + W8) + n78 * f2(Sa + Sb - csP, Sb - Sa - csP) +
+                    f2(1.f / 36.f) * (even - odd - fdm);
+    float x0, x1;
+    upk2(nq34.v, x0, x1); nq[3] = x0; nq[4] = x1;
+    upk2(nq56.v, x0, x1); nq[5] = x0; nq[6] = x1;
+    upk2(nq78.v, x0, x1); nq[7] = x0; nq[8] = x1;
+}
+
+// The end of one row of the sub-step: the wall rule (u = 0) on wall rows, the
+// Eq. 5-6 interface state of the next sub-step on ring rows (unless this is
+// the last sub-step), and the store of (rho - 1, u, f^neq_3..8).
+template <typename T>
+__device__ __forceinline__ void fv_finish_row(T *__restrict__ gn, int Np, int r, int n_wall, int ring_start,
+                                              int n_ring, const T *__restrict__ Q0, const T *__restrict__ Q1,
+                                              T theta_next, T scale5, int star, T r1, T ux, T uy, T nq[9])
+{
+    if (r < n_wall) {
+        ux = T(0);
+        uy = T(0);
+    } else if (star && r >= ring_start) {
+        int q_ = r - ring_start;
+        T a = T(1) - theta_next;
+        r1 = a * Q0[q_] + theta_next * Q1[q_] - T(1);
+        ux = a * Q0[size_t(n_ring) + q_] + theta_next * Q1[size_t(n_ring) + q_];
+        uy = a * Q0[size_t(2) * n_ring + q_] + theta_next * Q1[size_t(2) * n_ring + q_];
+#pragma unroll
+        for (int i = 3; i < 9; i++)
+            nq[i] = scale5 * (a * Q0[size_t(3 + i) * n_ring + q_] + theta_next * Q1[size_t(3 + i) * n_ring + q_]);
+    }
+    gn[r] = r1;
+    gn[size_t(Np) + r] = ux;
+    gn[size_t(2) * Np + r] = uy;
+#pragma unroll
+    for (int i = 3; i < 9; i++) gn[size_t(i) * Np + r] = nq[i];
+}
+
 // MINB: blocks per SM the register allocation is bounded for (1: unbounded);
 // the FP32 kernel is built for 7 and 8, and each context keeps the faster one
 // for its mesh (fv_autotune); FP64 is built unbounded.
@@ -652,232 +952,24 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
         return;
     }
     if (r >= n) return;
-    // own state from the staged list
-    T r1P, uPx, uPy, nP[9];
-    {
-        const int p = HLBM_CHK(own + int(threadIdx.x), hn, kSiteStaged);
-        r1P = sh[p];
-        uPx = sh[hn + p];
-        uPy = sh[2 * hn + p];
-#pragma unroll
-        for (int i = 3; i < 9; i++) nP[i] = sh[i * hn + p];
-        neq_complete(nP);
-    }
-    // own node: no streaming term (g(P) - g(P) = 0), collision weight C_PP = 11/18
-    // f^neq part of the sums, over the six stored planes j = 3..8 only:
-    //   U_j = sum_k a_k n_j(P_k), V_j = sum_k b_k n_j(P_k), W_j = sum_k cs_k n_j(P_k)
-    // (U_4 and V_3 are never needed: c_4x = c_3y = 0); planes 0-2 follow at the
-    // end from the same linear constraints that complete f^neq.
-    T U3 = 0, U5 = 0, U6 = 0, U7 = 0, U8 = 0, V4 = 0, V5 = 0, V6 = 0, V7 = 0, V8 = 0;
-    T W3 = 0, W4 = 0, W5 = 0, W6 = 0, W7 = 0, W8 = 0;
-    T Sa = 0, Sb = 0, Dx = 0, Dy = 0, Qxx = 0, Qyy = 0, Qxy = 0, Lx = 0, Ly = 0, Mx = 0, My = 0, Mxxy = 0, Mxyy = 0;
-    if constexpr (sizeof(T) == 4) {
-        // the same sums on packed pairs: (U5,U6) (U7,U8) (V5,V6) (V7,V8) (U3,V4)
-        // (W3,W4) (W5,W6) (W7,W8) (Sa,Sb) (Dx,Dy) (Qxx,Qyy) (Qxy',Qxy'') (Lx,Ly)
-        // (Mx,My) (Mxxy,Mxyy)
-        const unsigned long long z = pk2(0.f, 0.f), uP = pk2(uPx, uPy);
-        unsigned long long U56 = z, U78 = z, V56 = z, V78 = z, U3V4 = z, W34 = z, W56 = z, W78 = z;
-        unsigned long long SS = z, DD = z, QQ = z, QX = z, LL = z, MM = z, MX = z;
-        for (int e0 = 0; e0 < len; e0++) {
-            float a, b, cs;
-            int k;
-            unpack(se[HLBM_CHK(base + 32 * e0, n_ent, kSiteEntry)], a, b, cs, k);
-            k = HLBM_CHK(k, hn, kSiteStaged);
-            const float r1k = sh[k], n3 = sh[3 * hn + k], n4 = sh[4 * hn + k], n5 = sh[5 * hn + k],
-                        n6 = sh[6 * hn + k], n7 = sh[7 * hn + k], n8 = sh[8 * hn + k];
-            const unsigned long long uk = pk2(sh[hn + k], sh[2 * hn + k]);
-            const float drho = r1k - r1P, rhok = 1.f + r1k;
-            const unsigned long long ab = pk2(a, b), aa = pk2(a, a), bb = pk2(b, b), cc = pk2(cs, cs);
-            const unsigned long long du = sub2(uk, uP), su = add2(uk, uP);   // (dux, duy), (sux, suy)
-            const unsigned long long pr = mul2(du, su);                      // (dux sux, duy suy)
-            const unsigned long long R = mul2(ab, pk2(rhok, rhok));          // (ra, rb)
-            float dux, duy, sux, suy, p0, p1, ra, rb;
-            upk2(du, dux, duy);
-            upk2(su, sux, suy);
-            upk2(pr, p0, p1);
-            upk2(R, ra, rb);
-            const float dus = p0 + p1, xs = dux * suy + duy * sux;
-            SS = add2(SS, ab);
-            DD = fma2(ab, pk2(drho, drho), DD);
-            QQ = fma2(R, du, QQ);
-            QX = fma2(R, pk2(duy, dux), QX);
-            LL = fma2(R, pk2(dus, dus), LL);
-            MM = fma2(R, pr, MM);
-            MX = fma2(R, pk2(xs, xs), fma2(pk2(rb, ra), pr, MX));
-            const unsigned long long n34 = pk2(n3, n4), n56 = pk2(n5, n6), n78 = pk2(n7, n8);
-            U56 = fma2(aa, n56, U56);
-            U78 = fma2(aa, n78, U78);
-            V56 = fma2(bb, n56, V56);
-            V78 = fma2(bb, n78, V78);
-            U3V4 = fma2(ab, n34, U3V4);
-            W34 = fma2(cc, n34, W34);
-            W56 = fma2(cc, n56, W56);
-            W78 = fma2(cc, n78, W78);
-        }
-        float q0, q1;
-        upk2(U56, U5, U6); upk2(U78, U7, U8); upk2(V56, V5, V6); upk2(V78, V7, V8); upk2(U3V4, U3, V4);
-        upk2(W34, W3, W4); upk2(W56, W5, W6); upk2(W78, W7, W8);
-        upk2(SS, Sa, Sb); upk2(DD, Dx, Dy); upk2(QQ, Qxx, Qyy); upk2(QX, q0, q1); Qxy = q0 + q1;
-        upk2(LL, Lx, Ly); upk2(MM, Mx, My); upk2(MX, Mxxy, Mxyy);
-    } else {
-        for (int e0 = 0; e0 < len; e0 += kFvGroup) {
-            T sx[kFvGroup], sy[kFvGroup], c[kFvGroup];
-            int k[kFvGroup];
-#pragma unroll
-            for (int j = 0; j < kFvGroup; j++) {
-                if (e0 + j < len) {
-                    unpack(se[HLBM_CHK(base + 32 * (e0 + j), n_ent, kSiteEntry)], sx[j], sy[j], c[j], k[j]);
-                    k[j] = HLBM_CHK(k[j], hn, kSiteStaged);
-                } else {
-                    sx[j] = sy[j] = c[j] = T(0);
-                    k[j] = 0;
-                }
-            }
-            T st[kFvGroup][9];
-#pragma unroll
-            for (int j = 0; j < kFvGroup; j++)
-#pragma unroll
-                for (int i = 0; i < 9; i++) st[j][i] = sh[i * hn + k[j]];
-#pragma unroll
-            for (int j = 0; j < kFvGroup; j++) {
-                const T a = sx[j], b = sy[j], cs = c[j];  // dt s_Pk and (dt / tau_u) C_Pk
-                const T drho = st[j][0] - r1P, rhok = T(1) + st[j][0];
-                const T dux = st[j][1] - uPx, duy = st[j][2] - uPy, sux = st[j][1] + uPx, suy = st[j][2] + uPy;
-                const T dus = dux * sux + duy * suy, ra = rhok * a, rb = rhok * b;
-                const T xs = dux * suy + duy * sux;
-                Sa += a;
-                Sb += b;
-                Dx += a * drho;
-                Dy += b * drho;
-                Qxx += ra * dux;
-                Qyy += rb * duy;
-                Qxy += ra * duy + rb * dux;
-                Lx += ra * dus;
-                Ly += rb * dus;
-                Mx += ra * dux * sux;
-                My += rb * duy * suy;
-                Mxxy += ra * xs + rb * dux * sux;
-                Mxyy += rb * xs + ra * duy * suy;
-                const T *nk = st[j];
-                U3 += a * nk[3]; U5 += a * nk[5]; U6 += a * nk[6]; U7 += a * nk[7]; U8 += a * nk[8];
-                V4 += b * nk[4]; V5 += b * nk[5]; V6 += b * nk[6]; V7 += b * nk[7]; V8 += b * nk[8];
-                W3 += cs * nk[3]; W4 += cs * nk[4]; W5 += cs * nk[5];
-                W6 += cs * nk[6]; W7 += cs * nk[7]; W8 += cs * nk[8];
-            }
-        }
-    }
-    // Update.  With acc_i = sum_k (c_i.(a_k, b_k) - cs_k) f^neq_i(P_k) + w_i eq_i
-    // - f^neq_i(P) (c_i.(Sa, Sb) + dt/tau_u C_PP) the increment of population i,
-    // its zeroth and first moments need no per-population sum: f^neq carries
-    // no mass or momentum and the D2Q9 weights are isotropic to fourth order,
-    //   drho = u_P.D + Q_xx + Q_yy
-    //   djx  = D_x/3 + u_Px (u_P.D) + 3/2 M_x + 1/2 M_xyy - 1/2 L_x
-    //          + sum_k (a_k Pi^neq_xx(P_k) + b_k Pi^neq_xy(P_k)) - (Sa Pi^neq_xx(P) + Sb Pi^neq_xy(P))
-    // (djy likewise), with sum_k a_k Pi^neq_xx(P_k) = 2 (U3 + U6 + U7) and so
-    // on.  The new f^neq is then needed for the stored planes 3..8 only;
-    // opposite diagonals (5, 7) and (6, 8) share the even and odd parts of
-    // eq_i and of the f^eq difference.
-    const T csP = dt_tau * T(11.0 / 18.0);
-    const T Pxx = nP[1] + nP[3] + nP[5] + nP[6] + nP[7] + nP[8];
-    const T Pyy = nP[2] + nP[4] + nP[5] + nP[6] + nP[7] + nP[8];
-    const T Pxy = nP[5] - nP[6] + nP[7] - nP[8];
-    const T uD = uPx * Dx + uPy * Dy;
-    const T drho = uD + Qxx + Qyy;
-    const T djx = Dx * T(1.0 / 3.0) + uPx * uD + T(1.5) * Mx + T(0.5) * Mxyy - T(0.5) * Lx + T(2) * (U3 + U6 + U7) +
-                  (V5 - V6 + V7 - V8) - (Sa * Pxx + Sb * Pxy);
-    const T djy = Dy * T(1.0 / 3.0) + uPy * uD + T(1.5) * My + T(0.5) * Mxxy - T(0.5) * Ly + (U5 - U6 + U7 - U8) +
-                  T(2) * (V4 + V7 + V8) - (Sb * Pyy + Sa * Pxy);
-    T r1 = r1P + drho;
-    const T rho = T(1) + r1, irho = T(1) / rho;
-    const T dux = (djx - drho * uPx) * irho, duy = (djy - drho * uPy) * irho;
-    T ux = uPx + dux, uy = uPy + duy;
-    const T sx = ux + uPx, sy = uy + uPy;           // u' + u_P
-    const T E0 = T(1) - T(1.5) * (uPx * uPx + uPy * uPy);
-    const T ddot = T(1.5) * (dux * sx + duy * sy);  // 3/2 du.(u' + u_P)
-    // [f^eq_c(rho', u') - f^eq_c(rho_P, u_P)] / w_c for a direction c with E = E_c(u_P)
-    auto fd = [&](T E, T cdu, T csu) { return drho * E + rho * (T(3) * cdu + T(4.5) * cdu * csu - ddot); };
-    T nq[9];
-    if constexpr (sizeof(T) == 4) {
-        // the same on pairs of directions: (3, 4) mirror each other in x <-> y;
-        // (5, 6) and (7, 8) are the two diagonal families' + and - members
-        const F2 U = f2(uPx, uPy);
-        const F2 E34 = fmaf2(f2(4.5f) * U, U, f2(E0) - f2(3.f) * U);
-        const F2 eq34 = f2(3.f) * f2(Qxx, Qyy) + f2(1.5f) * f2(Lx, Ly) - E34 * f2(Dx, Dy) - f2(4.5f) * f2(Mx, My);
-        const F2 n34 = f2(nP[3], nP[4]);
-        const F2 cdu34 = f2(-dux, -duy), csu34 = f2(-sx, -sy);
-        const F2 fd34 = fmaf2(f2(drho), E34,
-                              f2(rho) * (fmaf2(f2(4.5f) * cdu34, csu34, f2(3.f) * cdu34) - f2(ddot)));
-        const F2 nq34 = n34 - f2(U3, V4) - f2(W3, W4) + fmaf2(n34, f2(Sa - csP, Sb - csP), f2(1.f / 9.f) * (eq34 - fd34));
-        const F2 q = f2(uPx + uPy, uPy - uPx);
-        const F2 A = fmaf2(f2(4.5f) * q, q, f2(E0)), B = f2(3.f) * q;
-        const F2 Pd = f2(Dx + Dy, Dy - Dx);
-        const F2 Cq = f2(3.f) * f2(Qxx + Qyy + Qxy, Qxx + Qyy - Qxy);
-        const F2 Z = f2(4.5f) * f2(Mx + My + Mxxy + Mxyy, My - Mx + Mxxy - Mxyy) - f2(1.5f) * f2(Lx + Ly, Ly - Lx);
-        const F2 odd = fmaf2(A, Pd, Z), even = fmaf2(B, Pd, Cq);
-        const F2 cdu = f2(dux + duy, duy - dux), csu = f2(sx + sy, sy - sx);
-        const F2 t3 = fmaf2(f2(4.5f) * cdu, csu, f2(3.f) * cdu);  // 3 c.du + 9/2 (c.du)(c.su), + members
-        const F2 t3m = fmaf2(f2(4.5f) * cdu, csu, f2(-3.f) * cdu);  // the same for - members
-        const F2 fdp = fmaf2(f2(drho), A + B, f2(rho) * (t3 - f2(ddot)));
-        const F2 fdm = fmaf2(f2(drho), A - B, f2(rho) * (t3m - f2(ddot)));
-        const F2 n56 = f2(nP[5], nP[6]), n78 = f2(nP[7], nP[8]);
-        const F2 nq56 = n56 + f2(U5 + V5 - W5, V6 - U6 - W6) - n56 * f2(Sa + Sb + csP, Sb - Sa + csP) +
-                        f2(1.f / 36.f) * (even + odd - fdp);
-        const F2 nq78 = n78 - f2(U7 + V7 + W7, V8 - U8 + W8) + n78 * f2(Sa + Sb - csP, Sb - Sa - csP) +
-                        f2(1.f / 36.f) * (even - odd - fdm);
-        float x0, x1;
-        upk2(nq34.v, x0, x1); nq[3] = x0; nq[4] = x1;
-        upk2(nq56.v, x0, x1); nq[5] = x0; nq[6] = x1;
-        upk2(nq78.v, x0, x1); nq[7] = x0; nq[8] = x1;
-    } else {
-        {  // axis directions 3 (-1, 0) and 4 (0, -1)
-            const T E3 = E0 - T(3) * uPx + T(4.5) * uPx * uPx;
-            const T eq3 = -E3 * Dx + T(3) * Qxx - T(4.5) * Mx + T(1.5) * Lx;
-            nq[3] = nP[3] - U3 - W3 + T(1.0 / 9.0) * eq3 + nP[3] * (Sa - csP) - T(1.0 / 9.0) * fd(E3, -dux, -sx);
-            const T E4 = E0 - T(3) * uPy + T(4.5) * uPy * uPy;
-            const T eq4 = -E4 * Dy + T(3) * Qyy - T(4.5) * My + T(1.5) * Ly;
-            nq[4] = nP[4] - V4 - W4 + T(1.0 / 9.0) * eq4 + nP[4] * (Sb - csP) - T(1.0 / 9.0) * fd(E4, -duy, -sy);
-        }
-        {  // diagonals 5 (1, 1) and 7 (-1, -1)
-            const T q = uPx + uPy, A = E0 + T(4.5) * q * q, B = T(3) * q;
-            const T Pd = Dx + Dy, C = T(3) * (Qxx + Qxy + Qyy);
-            const T Z = T(4.5) * (Mx + My + Mxxy + Mxyy) - T(1.5) * (Lx + Ly);
-            const T odd = A * Pd + Z, even = B * Pd + C;  // eq5 = even + odd, eq7 = even - odd
-            const T cdu = dux + duy, csu = sx + sy;
-            nq[5] = nP[5] + U5 + V5 - W5 + T(1.0 / 36.0) * (even + odd) - nP[5] * (Sa + Sb + csP) -
-                    T(1.0 / 36.0) * fd(A + B, cdu, csu);
-            nq[7] = nP[7] - U7 - V7 - W7 + T(1.0 / 36.0) * (even - odd) + nP[7] * (Sa + Sb - csP) -
-                    T(1.0 / 36.0) * fd(A - B, -cdu, -csu);
-        }
-        {  // diagonals 6 (-1, 1) and 8 (1, -1)
-            const T q = uPy - uPx, A = E0 + T(4.5) * q * q, B = T(3) * q;
-            const T Pd = Dy - Dx, C = T(3) * (Qxx - Qxy + Qyy);
-            const T Z = T(4.5) * (-Mx + My + Mxxy - Mxyy) - T(1.5) * (Ly - Lx);
-            const T odd = A * Pd + Z, even = B * Pd + C;  // eq6 = even + odd, eq8 = even - odd
-            const T cdu = duy - dux, csu = sy - sx;
-            nq[6] = nP[6] - U6 + V6 - W6 + T(1.0 / 36.0) * (even + odd) - nP[6] * (Sb - Sa + csP) -
-                    T(1.0 / 36.0) * fd(A + B, cdu, csu);
-            nq[8] = nP[8] + U8 - V8 - W8 + T(1.0 / 36.0) * (even - odd) + nP[8] * (Sb - Sa - csP) -
-                    T(1.0 / 36.0) * fd(A - B, -cdu, -csu);
-        }
-    }
-    if (r < n_wall) {
-        ux = T(0);
-        uy = T(0);
-    } else if (star && r >= ring_start) {
-        int q_ = r - ring_start;
-        T a = T(1) - theta_next;
-        r1 = a * Q0[q_] + theta_next * Q1[q_] - T(1);
-        ux = a * Q0[size_t(n_ring) + q_] + theta_next * Q1[size_t(n_ring) + q_];
-        uy = a * Q0[size_t(2) * n_ring + q_] + theta_next * Q1[size_t(2) * n_ring + q_];
-#pragma unroll
-        for (int i = 3; i < 9; i++)
-            nq[i] = scale5 * (a * Q0[size_t(3 + i) * n_ring + q_] + theta_next * Q1[size_t(3 + i) * n_ring + q_]);
-    }
-    gn[r] = r1;
-    gn[size_t(Np) + r] = ux;
-    gn[size_t(2) * Np + r] = uy;
-#pragma unroll
-    for (int i = 3; i < 9; i++) gn[size_t(i) * Np + r] = nq[i];
+    T r1, ux, uy, nq[9];
+#ifdef HLBM_DEBUG
+    const int n_ent_chk = n_ent;
+#else
+    const int n_ent_chk = 0;
+#endif
+    if constexpr (sizeof(T) == 4)
+        fv_row_f32(sh, hn, own + int(threadIdx.x), se, base, len, dt_tau, n_ent_chk, r1, ux, uy, nq);
+    else
+        fv_row_f64<T>(sh, hn, own + int(threadIdx.x), se, base, len, dt_tau, n_ent_chk, r1, ux, uy, nq);
+    fv_finish_row<T>(gn, Np, r, n_wall, ring_start, n_ring, Q0, Q1, theta_next, scale5, star, r1, ux, uy, nq);
+}
+
+// FP32 -> FP64 copy (the adjoint's records of an FP32 forward).
+__global__ void k_widen(const float *__restrict__ a, double *__restrict__ b, size_t n)
+{
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x)
+        b[i] = double(a[i]);
 }
 
 // Odd-even filter of the mesh state, once per finest step after the Eq. 3
@@ -1337,8 +1429,11 @@ template <typename T, typename S> void launch_fv(const DevCtx &C, int msub, cuda
                            (const T *)m.Q1, theta_next, scale5, star, C.flag);
     };
     if constexpr (sizeof(T) == 4) {
-        if (m.fv_variant == 2) go(k_fv<T, 8>);
-        else go(k_fv<T, 7>);
+        if (m.fv_variant == 2) {
+            go(k_fv<T, 8>);
+        } else {
+            go(k_fv<T, 7>);
+        }
     } else {
         go(k_fv<T, 1>);
     }
@@ -1358,6 +1453,13 @@ template <typename T, typename S> void launch_fv_filter(const DevCtx &C, cudaStr
                                      (const int *)m.slice_ptr, (const int *)m.slice_len, (const E *)m.ent,
                                      (const int *)m.halo_ptr, (const int *)m.halo_nodes, c_scale, T(C.fv_filter),
                                      m.n_wall, m.ring_start);
+}
+
+void launch_widen(const float *a, double *b, size_t n, cudaStream_t s)
+{
+    if (n == 0) return;
+    const unsigned nb = unsigned(std::min<size_t>((n + 255) / 256, 152 * 16));
+    k_widen<<<nb, 256, 0, s>>>(a, b, n);
 }
 
 // Block-shape autotuner of the sub-step kernel (FP32): times each register
@@ -1380,7 +1482,8 @@ template <typename T, typename S> int fv_autotune(DevCtx &C, cudaStream_t s, dou
         }
         const int reps = 20;
         const int keep = m.fv_variant;
-        for (int v = 1; v <= 2; v++) {
+        const int nv = 2;
+        for (int v = 1; v <= nv; v++) {
             m.fv_variant = v;
             for (int k = 0; k < 3; k++) launch_fv<T, S>(C, 0, s);
             cudaEventRecord(e0, s);
@@ -1394,7 +1497,10 @@ template <typename T, typename S> int fv_autotune(DevCtx &C, cudaStream_t s, dou
         m.fv_variant = keep;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        return us[1] < us[0] ? 2 : 1;
+        int best = 1;
+        for (int v = 2; v <= nv; v++)
+            if (us[v - 1] < us[best - 1]) best = v;
+        return best;
     }
 }
 

@@ -204,11 +204,46 @@ def test_coupled_adjoint_value_is_the_next_force_samples(H, small):
     assert abs(J - float(np.mean(cd + 0.5 * cl))) <= 1e-13 * abs(J)
 
 
-def test_coupled_adjoint_rejects_reduced_precision(H):
-    s = H.Solver(make_case("hlbm_small"), precision="fp32")
-    with pytest.raises(H.HlbmError) as e:
-        s.adjoint(1)
-    assert e.value.code == H.HLBM_ENOTIMPL
+def test_coupled_adjoint_rejects_what_it_does_not_cover(H):
+    for kw in (dict(precision="fp16s"), dict(precision="fp64", fv_filter=0.01)):
+        s = H.Solver(make_case("hlbm_small"), **kw)
+        with pytest.raises(H.HlbmError) as e:
+            s.adjoint(1)
+        assert e.value.code == H.HLBM_ENOTIMPL
+
+
+@pytest.mark.parametrize("name,K", [("hlbm_small", 3), ("hlbm_mini2", 2)])
+def test_fp32_forward_adjoint_matches_oracle_finite_differences(H, name, K):
+    """FP32 forward steps with the reverse sweep and every gradient sum in FP64:
+    J within 1e-5 of the oracle's (FP64) mean force, and the lattice and mesh
+    population gradients, contracted with random directions, within 1e-4 of
+    oracle central differences (h = 1e-4); the FP64 adjoint of the same case
+    gives the same gradients to FP32 accuracy."""
+    case = make_case(name, aoa_deg=4.0)
+    s32, s64 = H.Solver(case, precision="fp32"), H.Solver(case, precision="fp64")
+    for s in (s32, s64):
+        s.step(1)
+        s.forces()
+    J, gls, gm, gx, da = s32.adjoint(K, 1.0, 0.4)
+    J64, gls64, gm64, gx64, da64 = s64.adjoint(K, 1.0, 0.4)
+    Jo = _oracle_mean_force_levels(case, K, 1.0, 0.4)
+    assert abs(J - Jo) <= 1e-5 * abs(Jo), (J, Jo)
+    rng = np.random.default_rng(11)
+    dlev = [rng.standard_normal((int(nx) * int(ny), 9)) * 1e-3 for nx, ny in case.levels[:, :2]]
+    dmesh = rng.standard_normal((case.n_nodes, 9)) * 1e-3
+    h = 1e-4
+    for dl, dm in ((dlev, None), (None, dmesh)):
+        fd = (_oracle_mean_force_levels(case, K, 1.0, 0.4, dl, dm, h) -
+              _oracle_mean_force_levels(case, K, 1.0, 0.4, dl, dm, -h)) / (2 * h)
+        if dl is not None:
+            ad = sum(float(np.nansum(g * d)) for g, d in zip(gls, dl))
+            ad64 = sum(float(np.nansum(g * d)) for g, d in zip(gls64, dl))
+        else:
+            ad, ad64 = float(np.sum(gm * dm)), float(np.sum(gm64 * dm))
+        assert abs(ad - fd) <= 1e-4 * abs(fd) + 1e-9, (name, dl is not None, ad, fd)
+        assert abs(ad - ad64) <= 1e-4 * abs(ad64) + 1e-9
+    assert abs(da - da64) <= 1e-3 * abs(da64) + 1e-9
+    assert np.abs(gx - gx64).max() <= 1e-3 * np.abs(gx64).max()
 
 
 def _oracle_mean_force_levels(case, K, wd, wl, dlev=None, dmesh=None, h=0.0, start=1):

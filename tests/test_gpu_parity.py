@@ -317,18 +317,24 @@ def test_wall_stats_reassemble_the_mean_forces(H):
 
 def test_fv_register_bounds_agree_bitwise_and_the_autotuner_reports(H):
     """The two register bounds of the FP32 finite-volume kernel (7 and 8
-    resident blocks per SM) run the same arithmetic: identical results; the
-    default (autotuned) context reports its choice and both timings."""
-    case = make_case("hlbm_mini2", aoa_deg=3.0)
-    a = H.Solver(case, precision="fp32", fv_variant=1)
-    b = H.Solver(case, precision="fp32", fv_variant=2)
-    assert a.info("fv_variant") == 1 and b.info("fv_variant") == 2
-    a.step(9)
-    b.step(9)
-    for g in grids(case):
-        for x, y in zip(a.fields(g), b.fields(g)):
-            assert np.array_equal(x, y, equal_nan=True)
-    assert np.array_equal(a.forces()[0], b.forces()[0])
+    resident blocks per SM) run the same arithmetic: identical results, on a
+    mesh of a few tiles and on the 200 k-node mesh; the default (autotuned)
+    context reports its choice and both timings."""
+    for name, steps in (("hlbm_mini2", 9), ("hlbm_single", 1)):
+        case = make_case(name, aoa_deg=3.0)
+        runs = [H.Solver(case, precision="fp32", fv_variant=v) for v in (1, 2)]
+        for v, s in zip((1, 2), runs):
+            assert s.info("fv_variant") == v
+            s.step(steps)
+        ref = runs[0]
+        ref_cd = ref.forces()[0]
+        for s in runs[1:]:
+            for g in grids(case):
+                for x, y in zip(ref.fields(g), s.fields(g)):
+                    assert np.array_equal(x, y, equal_nan=True), (name, g)
+            assert np.array_equal(ref_cd, s.forces()[0])
+        for s in runs:
+            s.close()
     t = H.Solver(make_case("hlbm_single"), precision="fp32")
     assert t.info("fv_variant") in (1, 2)
     assert t.info("fv_tune_us1") > 0 and t.info("fv_tune_us2") > 0

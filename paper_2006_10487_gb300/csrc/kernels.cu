@@ -235,23 +235,38 @@ __global__ void k_init_level(S *f, int nx, int ny, int pitch, size_t stride, con
 }
 
 // Eq. 1: BGK collision and (implicit, AA-pattern) streaming on one level.
+// Each thread treats kCollideNodes nodes of one row, kCollideThreads apart
+// (coalesced per node), loading all their populations before any store so
+// that the loads of every node are in flight together (the in-place layout
+// keeps the compiler from moving one node's loads above another's stores).
+constexpr int kCollideThreads = 128, kCollideNodes = 4;
 template <typename T, typename S, int P>
-__global__ void __launch_bounds__(128) k_collide(S *__restrict__ f, int nx, int ny, int pitch, size_t stride,
-                                                 T omega, const int *__restrict__ hx0, const int *__restrict__ hx1,
-                                                 LatShift sh)
+__global__ void __launch_bounds__(kCollideThreads) k_collide(S *__restrict__ f, int nx, int ny, int pitch,
+                                                             size_t stride, T omega, const int *__restrict__ hx0,
+                                                             const int *__restrict__ hx1, LatShift sh)
 {
-    int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= nx) return;
-    if (hx0 && x >= hx0[y] && x < hx1[y]) return;
-    size_t n = node(x, y, pitch);
-    T d[9];
-    load_state<T, S, P>(f, n, pitch, stride, d, sh);
-    T rho, ux, uy;
-    moments(d, rho, ux, uy);
+    const int y = blockIdx.y;
+    const int x0 = blockIdx.x * (kCollideThreads * kCollideNodes) + threadIdx.x;
+    const int h0 = hx0 ? hx0[y] : 0, h1 = hx0 ? hx1[y] : 0;
+    bool live[kCollideNodes];
+    T d[kCollideNodes][9];
 #pragma unroll
-    for (int i = 0; i < 9; i++) {
-        T post = d[i] - omega * (d[i] - deq<T>(i, rho, ux, uy));
-        Codec<S>::template put<T>(f, wr_idx<P>(i, n, pitch, stride), i, post, sh);
+    for (int j = 0; j < kCollideNodes; j++) {
+        const int x = x0 + j * kCollideThreads;
+        live[j] = x < nx && !(x >= h0 && x < h1);
+        if (live[j]) load_state<T, S, P>(f, node(x, y, pitch), pitch, stride, d[j], sh);
+    }
+#pragma unroll
+    for (int j = 0; j < kCollideNodes; j++) {
+        if (!live[j]) continue;
+        const size_t n = node(x0 + j * kCollideThreads, y, pitch);
+        T rho, ux, uy;
+        moments(d[j], rho, ux, uy);
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            T post = d[j][i] - omega * (d[j][i] - deq<T>(i, rho, ux, uy));
+            Codec<S>::template put<T>(f, wr_idx<P>(i, n, pitch, stride), i, post, sh);
+        }
     }
 }
 
@@ -1305,12 +1320,14 @@ void launch_init_level(const DevCtx &C, int c, unsigned long long seed, double p
 template <typename T, typename S> void launch_collide(const DevCtx &C, int c, cudaStream_t s)
 {
     const DevLevel &l = C.lv[c];
-    dim3 grid(cdiv(l.nx, 128), l.ny);
+    dim3 grid(cdiv(l.nx, kCollideThreads * kCollideNodes), l.ny);
     T omega = T(1.0 / l.tau);
     if (l.parity == 0)
-        k_collide<T, S, 0><<<grid, 128, 0, s>>>((S *)l.f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0, l.hx1, C.shift);
+        k_collide<T, S, 0><<<grid, kCollideThreads, 0, s>>>((S *)l.f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0,
+                                                            l.hx1, C.shift);
     else
-        k_collide<T, S, 1><<<grid, 128, 0, s>>>((S *)l.f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0, l.hx1, C.shift);
+        k_collide<T, S, 1><<<grid, kCollideThreads, 0, s>>>((S *)l.f, l.nx, l.ny, l.pitch, l.stride, omega, l.hx0,
+                                                            l.hx1, C.shift);
 }
 
 template <typename T, typename S> void launch_outer_bc(const DevCtx &C, cudaStream_t s)

@@ -550,7 +550,9 @@ def main():
         ens = [H.Solver(c, precision=args.precision, use_graphs=True) for c in ensemble()]
         t_setup = time.perf_counter() - t0
         batch = H.Batch(ens)
-        per_b = batch.info("lattice_updates") + batch.info("fv_updates")
+        lat_b, fv_b = batch.info("lattice_updates"), batch.info("fv_updates")
+        per_b = lat_b + fv_b
+        bytes_b = lat_b * LAT_BYTES[args.precision] + fv_b * FV_BYTES[args.precision]
         batch.step(2)
         batch.sync()
         kb = 10
@@ -576,6 +578,10 @@ def main():
                       "2048x1024, meshes 20 480 .. 300 032 nodes, chord nx/10",
             "node_updates_per_step": per_b, "gpu_launches": int(sum(sv.info("launches_per_step") for sv in ens) * kb),
             "graph_launches": kb, "sequential": {"value": per_b / (ms_seq * 1e-3) / 1e6, "ms_per_step": ms_seq},
+            "roofline": {"bound": "hbm", "algorithmic_bytes_per_step": bytes_b,
+                         "achieved": bytes_b / (ms_b * 1e-3) / 1e9, "unit": "GB/s", "peak": peak,
+                         "frac": bytes_b / (ms_b * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
+                         "bytes_per_unit": {"lattice": LAT_BYTES[args.precision], "fv": FV_BYTES[args.precision]}},
             "setup_seconds": t_setup, "clocks": clk_b.summary()}
         for sv in ens:
             sv.close()
@@ -597,7 +603,7 @@ def main():
         create_ms = {k: s3.info("create_ms_" + k) for k in ("setup", "device", "capture")}
         s3.close()
         h2d = case.xy.nbytes + case.tri.nbytes + case.kind.nbytes + case.levels.nbytes
-        line["e2e"] = {"value": per_step * args.steps / t_e2e / 1e6, "unit": "MLUPS",
+        line["e2e"] = {"value": per_step * args.steps / t_e2e / 1e6, "unit": "MLUPS", "coarse_steps": args.steps,
                        "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                        "seconds": t_e2e, "create_ms": create_ms,
                        "includes": "hlbm_create from host arrays (set-up + upload), "

@@ -160,6 +160,44 @@ def test_single_config_one_coarse_step_fp64(H, orc):
     compare_fields(sol, sim, case, FP64_TOL)
 
 
+@pytest.mark.slow
+def test_single_config_100_finest_steps_fp64(H, orc):
+    """The benchmarked configuration (2048 x 1024 + two nested boxes, 200 704-node
+    mesh) over 25 coarse steps = 100 steps of the finest lattice (3 100
+    finite-volume sub-steps): every grid within 1e-12 of the oracle (OpenMP
+    build, bitwise the serial one) and the force series within 1e-12."""
+    case = make_case("hlbm_single")
+    sol = H.Solver(case, precision="fp64")
+    sim = orc.Oracle(case, openmp=True)
+    sol.step(25)
+    sim.step(25)
+    compare_fields(sol, sim, case, FP64_TOL, "hlbm_single 25 coarse steps")
+    cd, cl = sol.forces()
+    ocd, ocl = sim.forces()
+    assert np.abs(cd - ocd).max() <= FP64_TOL * np.abs(ocd).max()
+    assert np.abs(cl - ocl).max() <= FP64_TOL * np.abs(ocd).max()
+
+
+def test_single_config_fp32_against_fp64(H):
+    """FP32 against the FP64 GPU path on the benchmarked configuration at 8
+    degrees, 100 coarse steps: velocity relative L2 per grid at most 1e-5 and
+    mean C_D, C_L within 1e-3 (measured: 2-5e-6 and ~1e-5)."""
+    case = make_case("hlbm_single", aoa_deg=8.0)
+    a, b = H.Solver(case, precision="fp32"), H.Solver(case, precision="fp64")
+    a.step(100)
+    b.step(100)
+    for g in grids(case):
+        _, ux, uy = a.fields(g)
+        _, vx, vy = b.fields(g)
+        m = np.isfinite(vx)
+        err = math.sqrt(((ux[m] - vx[m]) ** 2 + (uy[m] - vy[m]) ** 2).sum() / (vx[m] ** 2 + vy[m] ** 2).sum())
+        print(f"PARITY hlbm_single fp32 vs fp64 grid {g}: velocity relative L2 {err:.2e}")
+        assert err <= 1e-5, f"grid {g}: velocity relative L2 {err:.2e}"
+    (cd, cl), (cd64, cl64) = a.forces(), b.forces()
+    assert abs(cd.mean() - cd64.mean()) <= 1e-3 * abs(cd64.mean())
+    assert abs(cl.mean() - cl64.mean()) <= 1e-3 * abs(cl64.mean())
+
+
 def test_single_config_one_coarse_step_fp32(H, orc):
     case = make_case("hlbm_single")
     sol = H.Solver(case, precision="fp32")

@@ -313,7 +313,7 @@ def main():
     # ---- roofline of the dominant kernel (finite-volume sub-step), measured
     # live with CUDA events on the library's stream
     peak, peak_kind = _peaks()
-    fv_variant = [s.info("fv_variant"), s.info("fv_tune_us1"), s.info("fv_tune_us2")]
+    fv_variant = [s.info("fv_variant")] + [s.info(f"fv_tune_us{v}") for v in (1, 2, 3, 4)]
     fv_ms = s.time_kernel("fv", 200)
     n_sub = s.info("n_sub")
     fv_bytes = FV_BYTES[args.precision] * case.n_nodes
@@ -326,7 +326,8 @@ def main():
                 "units_per_launch": case.n_nodes, "bytes_per_launch": fv_bytes,
                 "kernel_bytes_per_launch": s.info("fv_bytes"), "launch_ms": fv_ms,
                 "autotuner": {"variant": fv_variant[0], "us_7_blocks_per_sm": fv_variant[1],
-                              "us_8_blocks_per_sm": fv_variant[2]},
+                              "us_8_blocks_per_sm": fv_variant[2], "us_7_with_l2_prefetch": fv_variant[3],
+                              "us_8_with_l2_prefetch": fv_variant[4]},
                 "l2_note": "the finite-volume working set (~37 MB) stays L2-resident between sub-steps; "
                            "hlbm_large carries the HBM-bound roofline of the same kernel",
                 "step": {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / args.steps * 1e-3) / 1e9,

@@ -43,7 +43,7 @@ struct hlbm_ctx {
     // mass monitoring (level 0, FP64): reference mass at create, last drift
     double *mass_buf = nullptr;  // [ny0 + 1]: row sums, total
     double mass0 = 0.0, mass_drift = 0.0, mass_nodes = 0.0;
-    double fv_tune_us[2] = {0.0, 0.0};
+    double fv_tune_us[4] = {0.0, 0.0, 0.0, 0.0};
     double create_ms[3] = {0.0, 0.0, 0.0};  // host set-up tables, device build, graph capture
     double build_ms[2] = {0.0, 0.0};         // device build: tables and uploads; initial state and autotuner
     AdjTables adj;                            // finite-volume adjoint tables (built on first use)
@@ -514,6 +514,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     M.smem_bytes = 16 + size_t(M.max_tile_ent) * sizeof(E) + size_t(M.max_halo) * 9 * sizeof(T);
     if (M.smem_bytes > 200 * 1024) throw CudaError{"mesh tiles touch too many nodes for shared memory"};
     configure_fv<T, T>(M.smem_bytes);
+    configure_fv_prefetch<T, T>(M);
     M.ent = upload(c, ent);
     M.slice_ptr = upload(c, sptr);
     M.slice_len = upload(c, slen);
@@ -754,7 +755,7 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
     c->alloc_ctx = o.alloc_ctx;
     c->use_graphs = o.use_graphs != 0;
     c->dev.m.wall_stats = o.wall_stats != 0;
-    if (o.fv_variant < 0 || o.fv_variant > 2) { delete c; return fail(nullptr, HLBM_EINVAL, "fv_variant must be 0, 1 or 2"); }
+    if (o.fv_variant < 0 || o.fv_variant > 4) { delete c; return fail(nullptr, HLBM_EINVAL, "fv_variant must be in 0..4"); }
     c->fv_variant_opt = o.fv_variant;
     if (!(o.fv_filter >= 0.0 && o.fv_filter <= 1.0)) {
         delete c;
@@ -964,6 +965,8 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
     else if (k == "create_ms_init") *value = c->build_ms[1];
     else if (k == "fv_tune_us1") *value = c->fv_tune_us[0];
     else if (k == "fv_tune_us2") *value = c->fv_tune_us[1];
+    else if (k == "fv_tune_us3") *value = c->fv_tune_us[2];
+    else if (k == "fv_tune_us4") *value = c->fv_tune_us[3];
     else if (k == "fv_smem") *value = double(c->dev.m.smem_bytes);
     else if (k == "fv_bytes") {
         // algorithmic bytes of one finite-volume sub-step: the 9 state values of

@@ -50,7 +50,8 @@ struct DevMesh {
     int n_tiles = 0, max_halo = 0;
     int *halo_ptr = nullptr, *halo_nodes = nullptr;
     int *tile_own = nullptr;  // position of tile t's first own row in its halo list (own rows are a run)
-    int fv_variant = 1;       // FP32 sub-step kernel bounded for 1: 7, 2: 8 blocks per SM
+    int fv_variant = 1;       // FP32 sub-step kernel bounded for 1, 3: 7; 2, 4: 8 blocks per SM (3, 4: L2 prefetch)
+    int pf_ahead[3] = {0, 0, 0};  // per variant: resident blocks (tile distance of the L2 prefetch)
     size_t smem_bytes = 0;
     // [12][n_ring] Eq. 9 data at t and t + 1: two buffers whose roles swap
     // every finest step (the data at t + 1 of one step is the data at t of the
@@ -100,8 +101,10 @@ constexpr int kTileRows = 128;  // rows per finite-volume tile (= threads per bl
 // Launchers, T = arithmetic type, S = lattice storage type (T, or __half for
 // FP16S); raises the FV kernel's dynamic shared-memory limit (configure_fv).
 template <typename T, typename S> void configure_fv(size_t bytes);
-// times the FP32 sub-step kernel's register bounds on this mesh; returns the faster
-template <typename T, typename S> int fv_autotune(DevCtx &, cudaStream_t, double us[2]);
+// resident blocks of each sub-step kernel variant on this mesh (m.pf_ahead)
+template <typename T, typename S> void configure_fv_prefetch(DevMesh &m);
+// times the FP32 sub-step kernel's variants on this mesh; returns the fastest
+template <typename T, typename S> int fv_autotune(DevCtx &, cudaStream_t, double us[4]);
 template <typename T, typename S> void launch_init_level(const DevCtx &, int c, unsigned long long seed, double perturb, cudaStream_t);
 template <typename T, typename S> void launch_collide(const DevCtx &, int c, cudaStream_t);
 template <typename T, typename S> void launch_outer_bc(const DevCtx &, cudaStream_t);

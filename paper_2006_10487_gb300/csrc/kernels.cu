@@ -559,6 +559,7 @@ __device__ __forceinline__ F2 fmaf2(F2 a, F2 b, F2 c) { return {fma2(a.v, b.v, c
 constexpr int kFvThreads = kTileRows;
 constexpr int kFvGroup = 2;
 constexpr int kFvHaloRegs = 3;
+constexpr int kFvPrefetchRegs = 2;  // halo nodes of the tile prefetched into L2, per thread
 constexpr unsigned long long kWaitLimitNs = 500ull * 1000 * 1000;  // bounded waits give up after 0.5 s
 constexpr int kFlagTimeout = 2;  // health flag bit: a device-side wait gave up
 
@@ -900,7 +901,7 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
                                                    const int *__restrict__ tile_own, T dt_tau,
                                                    int n_wall, int ring_start, int n_ring,
                                                    const T *__restrict__ Q0, const T *__restrict__ Q1, T theta_next,
-                                                   T scale5, int star, int *flag)
+                                                   T scale5, int star, int *flag, int pf_ahead)
 {
     using E = typename Ent<T>::type;
     extern __shared__ __align__(16) unsigned char fv_smem[];
@@ -943,6 +944,27 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
         const int h = threadIdx.x + j * kFvThreads;
         hidx[j] = h < hn ? HLBM_CHK(halo_nodes[h0 + h], Np, kSiteMesh) : 0;
     }
+    // The tile that will start about when this one ends (pf_ahead = the
+    // resident blocks of this launch; blocks start in index order): its
+    // operator entries and, once the state is ready, its halo states are
+    // prefetched into L2, so that its gather finds them there.
+    const int tp = pf_ahead > 0 ? t + pf_ahead : int(gridDim.x);
+    int pidx[kFvPrefetchRegs], hpn = 0;
+    if (tp < int(gridDim.x)) {
+        const int hp0 = halo_ptr[tp];
+        hpn = halo_ptr[tp + 1] - hp0;
+#pragma unroll
+        for (int j = 0; j < kFvPrefetchRegs; j++) {
+            const int h = threadIdx.x + j * kFvThreads;
+            pidx[j] = h < hpn ? HLBM_CHK(halo_nodes[hp0 + h], Np, kSiteMesh) : 0;
+        }
+        if (threadIdx.x == 0) {
+            const int ep = slice_ptr[4 * tp];
+            const uint32_t pbytes = uint32_t(slice_ptr[4 * tp + 4] - ep) * uint32_t(sizeof(E));
+            if (pbytes > 0)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ent + ep), "r"(pbytes) : "memory");
+        }
+    }
     // wait until the previous sub-step (which wrote g) has completed
     asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll
@@ -957,6 +979,14 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
         const int node = HLBM_CHK(halo_nodes[h0 + h], Np, kSiteMesh);
 #pragma unroll
         for (int i = 0; i < 9; i++) sh[i * hn + h] = g[size_t(i) * Np + node];
+    }
+#pragma unroll
+    for (int j = 0; j < kFvPrefetchRegs; j++) {
+        if (threadIdx.x + j * kFvThreads < hpn) {
+#pragma unroll
+            for (int i = 0; i < 9; i++)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(g + size_t(i) * Np + pidx[j]) : "memory");
+        }
     }
     __syncthreads();
     if (!mbar_wait(bar, 0)) {
@@ -1438,19 +1468,20 @@ template <typename T, typename S> void launch_fv(const DevCtx &C, int msub, cuda
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    // variants: 1, 2 bounded for 7, 8 resident blocks per SM; 3, 4 the same
+    // with the L2 prefetch of a later tile (FP64: one unbounded kernel)
+    const int v = m.fv_variant, bound = (v == 2 || v == 4) ? 2 : 1;
+    const int pf = v >= 3 ? m.pf_ahead[bound] : 0;
     auto go = [&](auto kern) {
         cudaLaunchKernelEx(&cfg, kern, (const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
                            (const int *)m.slice_ptr, (const int *)m.slice_len, (const typename Ent<T>::type *)m.ent,
                            m.max_tile_ent, (const int *)m.halo_ptr, (const int *)m.halo_nodes,
                            (const int *)m.tile_own, dt_tau, m.n_wall, m.ring_start, m.n_ring, (const T *)m.Q0,
-                           (const T *)m.Q1, theta_next, scale5, star, C.flag);
+                           (const T *)m.Q1, theta_next, scale5, star, C.flag, pf);
     };
     if constexpr (sizeof(T) == 4) {
-        if (m.fv_variant == 2) {
-            go(k_fv<T, 8>);
-        } else {
-            go(k_fv<T, 7>);
-        }
+        if (bound == 2) go(k_fv<T, 8>);
+        else go(k_fv<T, 7>);
     } else {
         go(k_fv<T, 1>);
     }
@@ -1479,15 +1510,15 @@ void launch_widen(const float *a, double *b, size_t n, cudaStream_t s)
     k_widen<<<nb, 256, 0, s>>>(a, b, n);
 }
 
-// Block-shape autotuner of the sub-step kernel (FP32): times each register
-// bound on this mesh (reps launches reading the current state buffer and
-// writing the other one, which the next sub-step overwrites, so the state is
-// unchanged) and returns the faster variant (1: bounded for 7 blocks per SM,
-// 2: for 8); *us receives the mean launch times.  Both variants execute the same
-// arithmetic.
-template <typename T, typename S> int fv_autotune(DevCtx &C, cudaStream_t s, double us[2])
+// Autotuner of the sub-step kernel (FP32): times each variant on this mesh
+// (reps launches reading the current state buffer and writing the other one,
+// which the next sub-step overwrites, so the state is unchanged) and returns
+// the fastest (1, 2: registers bounded for 7, 8 blocks per SM; 3, 4: the same
+// with the L2 prefetch of a later tile's entries and halo states); *us
+// receives the mean launch times.  All variants execute the same arithmetic.
+template <typename T, typename S> int fv_autotune(DevCtx &C, cudaStream_t s, double us[4])
 {
-    us[0] = us[1] = 0.0;
+    us[0] = us[1] = us[2] = us[3] = 0.0;
     if constexpr (sizeof(T) != 4) {
         return 1;
     } else {
@@ -1499,7 +1530,7 @@ template <typename T, typename S> int fv_autotune(DevCtx &C, cudaStream_t s, dou
         }
         const int reps = 20;
         const int keep = m.fv_variant;
-        const int nv = 2;
+        const int nv = 4;
         for (int v = 1; v <= nv; v++) {
             m.fv_variant = v;
             for (int k = 0; k < 3; k++) launch_fv<T, S>(C, 0, s);
@@ -1530,6 +1561,30 @@ template <typename T, typename S> void configure_fv(size_t bytes)
         } else {
             cudaFuncSetAttribute(k_fv<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
         }
+    }
+}
+
+template <typename T, typename S> void configure_fv_prefetch(DevMesh &m)
+{
+    int dev = 0, sms = 0;
+    for (int v = 0; v < 3; v++) m.pf_ahead[v] = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    auto resident = [&](auto kern) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFvThreads, m.smem_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return per_sm * sms;
+    };
+    if constexpr (sizeof(T) == 4) {
+        m.pf_ahead[1] = resident(k_fv<T, 7>);
+        m.pf_ahead[2] = resident(k_fv<T, 8>);
+    } else {
+        m.pf_ahead[1] = resident(k_fv<T, 1>);
     }
 }
 
@@ -1592,6 +1647,7 @@ void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *u
 
 #define HLBM_INSTANTIATE(T, S)                                                                                   \
     template void configure_fv<T, S>(size_t);                                                                    \
+    template void configure_fv_prefetch<T, S>(DevMesh &);                                                        \
     template void launch_init_level<T, S>(const DevCtx &, int, unsigned long long, double, cudaStream_t);        \
     template void launch_collide<T, S>(const DevCtx &, int, cudaStream_t);                                       \
     template void launch_outer_bc<T, S>(const DevCtx &, cudaStream_t);                                           \

@@ -354,14 +354,15 @@ def test_wall_stats_reassemble_the_mean_forces(H):
 
 
 def test_fv_register_bounds_agree_bitwise_and_the_autotuner_reports(H):
-    """The two register bounds of the FP32 finite-volume kernel (7 and 8
-    resident blocks per SM) run the same arithmetic: identical results, on a
-    mesh of a few tiles and on the 200 k-node mesh; the default (autotuned)
-    context reports its choice and both timings."""
+    """The four variants of the FP32 finite-volume kernel (registers bounded
+    for 7 and 8 resident blocks per SM, each with and without the L2 prefetch
+    of a later tile) run the same arithmetic: identical results, on a mesh of
+    a few tiles and on the 200 k-node mesh; the default (autotuned) context
+    reports its choice and the timings."""
     for name, steps in (("hlbm_mini2", 9), ("hlbm_single", 1)):
         case = make_case(name, aoa_deg=3.0)
-        runs = [H.Solver(case, precision="fp32", fv_variant=v) for v in (1, 2)]
-        for v, s in zip((1, 2), runs):
+        runs = [H.Solver(case, precision="fp32", fv_variant=v) for v in (1, 2, 3, 4)]
+        for v, s in zip((1, 2, 3, 4), runs):
             assert s.info("fv_variant") == v
             s.step(steps)
         ref = runs[0]
@@ -374,8 +375,8 @@ def test_fv_register_bounds_agree_bitwise_and_the_autotuner_reports(H):
         for s in runs:
             s.close()
     t = H.Solver(make_case("hlbm_single"), precision="fp32")
-    assert t.info("fv_variant") in (1, 2)
-    assert t.info("fv_tune_us1") > 0 and t.info("fv_tune_us2") > 0
+    assert t.info("fv_variant") in (1, 2, 3, 4)
+    assert all(t.info(f"fv_tune_us{v}") > 0 for v in (1, 2, 3, 4))
 
 
 @pytest.mark.parametrize("name", ["hlbm_small", "hlbm_mini2"])

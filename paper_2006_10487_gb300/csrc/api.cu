@@ -479,25 +479,86 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
         n_ent += size_t(32) * len;
     }
     ent.resize(n_ent);
+    // Entry order within a row is free (the sums are over all of them), so
+    // each slice orders its 32 rows' entries slot by slot to spread the 32
+    // shared-memory reads of one slot over the banks: a row takes, among its
+    // remaining neighbours, one whose staged position another row of the
+    // slice already reads in this slot (a broadcast), else one in the bank
+    // with the fewest distinct positions so far (lowest entry on ties);
+    // padding entries (zero coefficients) read a position already read.
     parallel_for(M.n_slices, [&](int sl0, int sl1) {
+        std::vector<int> pos[32], order[32];
+        std::vector<int> stamp(size_t(M.max_halo) + 1, -1);  // slot stamp of each staged position
+        int stamp_id = 0;
         for (int sl = sl0; sl < sl1; sl++) {
             const int len = slen[sl];
             const size_t base = size_t(sptr[sl]);
+            uint32_t used[32];
             for (int l = 0; l < 32; l++) {
-                int r = sl * 32 + l;
-                const int nr = r < P.n ? odp[r + 1] - odp[r] : 0;
-                const int *h0 = r < P.n ? hnodes.data() + hptr[r / kTileRows] : nullptr;
-                const int *h1 = r < P.n ? hnodes.data() + hptr[r / kTileRows + 1] : nullptr;
-                for (int e = 0; e < len; e++) {
+                const int r = sl * 32 + l;
+                pos[l].clear();
+                order[l].clear();
+                used[l] = 0;
+                if (r >= P.n) continue;
+                const int *h0 = hnodes.data() + hptr[r / kTileRows], *h1 = hnodes.data() + hptr[r / kTileRows + 1];
+                for (int j = odp[r]; j < odp[r + 1]; j++)
+                    pos[l].push_back(int(std::lower_bound(h0, h1, P.inv[P.col[od[j]]]) - h0));
+            }
+            bool small = true;  // the bank-aware order tracks up to 32 entries per row
+            for (int l = 0; l < 32; l++) small = small && pos[l].size() <= 32;
+            if (!small)
+                for (int l = 0; l < 32; l++)
+                    for (int j = 0; j < int(pos[l].size()); j++) order[l].push_back(j);
+            for (int e = 0; e < len; e++) {
+                const int sid = stamp_id++;
+                if (!small) {
+                    for (int l = 0; l < 32; l++) {
+                        const int r = sl * 32 + l;
+                        E v{};
+                        if (e < int(order[l].size())) {
+                            const int j = order[l][e], k = od[odp[r] + j];
+                            v.x = T(dt * P.sx[k]); v.y = T(dt * P.sy[k]); v.z = T(dt_tau * P.cc[k]);
+                            set_col(v, pos[l][j]);
+                        } else {
+                            v.x = v.y = v.z = T(0);
+                            set_col(v, 0);
+                        }
+                        ent[base + size_t(32) * e + l] = v;
+                    }
+                    continue;
+                }
+                int bank_n[32] = {0}, first = -1;
+                for (int l = 0; l < 32; l++) {
+                    const int nr = int(pos[l].size());
+                    int best = -1, best_cost = 1 << 30;
+                    for (int j = 0; j < nr && j < 32; j++) {
+                        if (used[l] >> j & 1u) continue;
+                        const int k = pos[l][j];
+                        const int cost = stamp[k] == sid ? -1 : bank_n[k & 31];
+                        if (cost < best_cost) { best_cost = cost; best = j; }
+                    }
+                    if (best >= 0) {
+                        used[l] |= 1u << best;
+                        order[l].push_back(best);
+                        const int k = pos[l][best];
+                        if (stamp[k] != sid) {
+                            stamp[k] = sid;
+                            bank_n[k & 31]++;
+                            if (first < 0) first = k;
+                        }
+                    }
+                }
+                const int pad_col = first < 0 ? 0 : first;
+                for (int l = 0; l < 32; l++) {
+                    const int r = sl * 32 + l;
                     E v{};
-                    if (e < nr) {
-                        int k = od[odp[r] + e];
+                    if (e < int(order[l].size())) {
+                        const int j = order[l][e], k = od[odp[r] + j];
                         v.x = T(dt * P.sx[k]); v.y = T(dt * P.sy[k]); v.z = T(dt_tau * P.cc[k]);
-                        int col = P.inv[P.col[k]];
-                        set_col(v, int(std::lower_bound(h0, h1, col) - h0));
+                        set_col(v, pos[l][j]);
                     } else {
-                        v.x = v.y = v.z = T(0);  // padding: zero coefficients on a valid slot
-                        set_col(v, 0);
+                        v.x = v.y = v.z = T(0);  // padding: zero coefficients on a position already read
+                        set_col(v, pad_col);
                     }
                     ent[base + size_t(32) * e + l] = v;
                 }

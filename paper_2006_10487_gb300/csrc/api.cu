@@ -433,20 +433,25 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
             if (P.col[k] != old) od.push_back(k);
         odp[r + 1] = int(od.size());
     }
-    std::vector<int> town(M.n_tiles);
+    // tile t's staged list: its own 128 device rows r0 .. r0 + 127 (the last
+    // tile's run reaches into the padding rows, never referenced), which the
+    // kernel copies in bulk, then the other nodes its rows touch, sorted,
+    // which it gathers; an entry's column is its node's position in the list
     std::vector<std::vector<int>> halo(M.n_tiles);
     parallel_for(M.n_tiles, [&](int t0, int t1) {
         for (int t = t0; t < t1; t++) {
-            // the tile's own rows are in the list too (their state is read from
-            // it); consecutive rows, so one contiguous run of the sorted list
+            const int r0 = t * kTileRows;
             std::vector<int> &h = halo[t];
-            for (int r = t * kTileRows; r < std::min(P.n, (t + 1) * kTileRows); r++) {
-                h.push_back(r);
-                for (int j = odp[r]; j < odp[r + 1]; j++) h.push_back(P.inv[P.col[od[j]]]);
-            }
+            for (int r = r0; r < std::min(P.n, r0 + kTileRows); r++)
+                for (int j = odp[r]; j < odp[r + 1]; j++) {
+                    const int c = P.inv[P.col[od[j]]];
+                    if (c < r0 || c >= r0 + kTileRows) h.push_back(c);
+                }
             std::sort(h.begin(), h.end());
             h.erase(std::unique(h.begin(), h.end()), h.end());
-            town[t] = int(std::lower_bound(h.begin(), h.end(), t * kTileRows) - h.begin());
+            std::vector<int> own(kTileRows);
+            for (int j = 0; j < kTileRows; j++) own[j] = r0 + j;
+            h.insert(h.begin(), own.begin(), own.end());
         }
     }, 16);
     for (int t = 0; t < M.n_tiles; t++) {
@@ -458,6 +463,13 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
         for (int t = t0; t < t1; t++) std::copy(halo[t].begin(), halo[t].end(), hnodes.begin() + hptr[t]);
     }, 16);
     halo.clear();
+    // position of device node c in tile t's staged list
+    auto halo_pos = [&](int t, int c) {
+        const int r0 = t * kTileRows;
+        if (c >= r0 && c < r0 + kTileRows) return c - r0;
+        const int *h0 = hnodes.data() + hptr[t] + kTileRows, *h1 = hnodes.data() + hptr[t + 1];
+        return kTileRows + int(std::lower_bound(h0, h1, c) - h0);
+    };
     std::vector<int> sptr(M.n_slices), slen(M.n_slices);
     std::vector<E> ent;
     auto set_col = [](E &v, int col) {
@@ -500,9 +512,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
                 order[l].clear();
                 used[l] = 0;
                 if (r >= P.n) continue;
-                const int *h0 = hnodes.data() + hptr[r / kTileRows], *h1 = hnodes.data() + hptr[r / kTileRows + 1];
-                for (int j = odp[r]; j < odp[r + 1]; j++)
-                    pos[l].push_back(int(std::lower_bound(h0, h1, P.inv[P.col[od[j]]]) - h0));
+                for (int j = odp[r]; j < odp[r + 1]; j++) pos[l].push_back(halo_pos(r / kTileRows, P.inv[P.col[od[j]]]));
             }
             bool small = true;  // the bank-aware order tracks up to 32 entries per row
             for (int l = 0; l < 32; l++) small = small && pos[l].size() <= 32;
@@ -569,10 +579,10 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     sptr.resize(size_t(4) * M.n_tiles + 1, int(ent.size()));
     for (int t = 0; t < M.n_tiles; t++) M.max_tile_ent = std::max(M.max_tile_ent, sptr[4 * t + 4] - sptr[4 * t]);
     M.halo_ptr = upload(c, hptr);
-    M.tile_own = upload(c, town);
     M.halo_nodes = upload(c, hnodes);
     // mbarrier (16 B), the tile's entries, the halo states
-    M.smem_bytes = 16 + size_t(M.max_tile_ent) * sizeof(E) + size_t(M.max_halo) * 9 * sizeof(T);
+    // (planes of a stride rounded up to 4 values: 16-byte aligned bulk copies)
+    M.smem_bytes = 16 + size_t(M.max_tile_ent) * sizeof(E) + size_t((M.max_halo + 3) & ~3) * 9 * sizeof(T);
     if (M.smem_bytes > 200 * 1024) throw CudaError{"mesh tiles touch too many nodes for shared memory"};
     configure_fv<T, T>(M.smem_bytes);
     configure_fv_prefetch<T, T>(M);

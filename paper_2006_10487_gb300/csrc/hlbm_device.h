@@ -45,11 +45,11 @@ struct DevMesh {
     int n_slices = 0, max_tile_ent = 0;
     void *ent = nullptr;
     int *slice_ptr = nullptr, *slice_len = nullptr;
-    // tiles of kTileRows consecutive rows; tile t touches the sorted nodes
-    // halo_nodes[halo_ptr[t] .. halo_ptr[t+1]) and entry columns index that list
+    // tiles of kTileRows consecutive rows; tile t's staged list
+    // halo_nodes[halo_ptr[t] .. halo_ptr[t+1]) is its own kTileRows rows, then
+    // the other nodes its rows touch (sorted); entry columns index that list
     int n_tiles = 0, max_halo = 0;
     int *halo_ptr = nullptr, *halo_nodes = nullptr;
-    int *tile_own = nullptr;  // position of tile t's first own row in its halo list (own rows are a run)
     int fv_variant = 1;       // FP32 sub-step kernel bounded for 1, 3: 7; 2, 4: 8 blocks per SM (3, 4: L2 prefetch)
     int pf_ahead[3] = {0, 0, 0};  // per variant: resident blocks (tile distance of the L2 prefetch)
     size_t smem_bytes = 0;

@@ -558,8 +558,8 @@ __device__ __forceinline__ F2 fmaf2(F2 a, F2 b, F2 c) { return {fma2(a.v, b.v, c
 // neighbours from shared memory.
 constexpr int kFvThreads = kTileRows;
 constexpr int kFvGroup = 2;
-constexpr int kFvHaloRegs = 3;
-constexpr int kFvPrefetchRegs = 2;  // halo nodes of the tile prefetched into L2, per thread
+constexpr int kFvHaloRegs = 1;  // staged nodes beyond the tile's own rows gathered per thread from registers
+constexpr int kFvPrefetchRegs = 1;  // nodes beyond a later tile's own rows prefetched into L2, per thread
 constexpr unsigned long long kWaitLimitNs = 500ull * 1000 * 1000;  // bounded waits give up after 0.5 s
 constexpr int kFlagTimeout = 2;  // health flag bit: a device-side wait gave up
 
@@ -897,16 +897,16 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
                                                    const int *__restrict__ slice_len,
                                                    const typename Ent<T>::type *__restrict__ ent, int max_tile_ent,
                                                    const int *__restrict__ halo_ptr,
-                                                   const int *__restrict__ halo_nodes,
-                                                   const int *__restrict__ tile_own, T dt_tau,
+                                                   const int *__restrict__ halo_nodes, T dt_tau,
                                                    int n_wall, int ring_start, int n_ring,
                                                    const T *__restrict__ Q0, const T *__restrict__ Q1, T theta_next,
                                                    T scale5, int star, int *flag, int pf_ahead)
 {
     using E = typename Ent<T>::type;
     extern __shared__ __align__(16) unsigned char fv_smem[];
-    // [0, 16): mbarrier; [16, ...): the tile's entries; then the halo states
-    const uint32_t bar = uint32_t(__cvta_generic_to_shared(fv_smem));
+    // [0, 16): two mbarriers (entries; the tile's own states); [16, ...): the
+    // tile's entries; then the staged states, nine planes of stride hs
+    const uint32_t bar_e = uint32_t(__cvta_generic_to_shared(fv_smem)), bar_s = bar_e + 8u;
     const E *se = reinterpret_cast<const E *>(fv_smem + 16);
     T *sh = reinterpret_cast<T *>(fv_smem + 16 + size_t(max_tile_ent) * sizeof(E));
     const int t = blockIdx.x;
@@ -914,40 +914,45 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
 #ifdef HLBM_DEBUG
     const int n_ent = slice_ptr[4 * t + 4] - e_begin;  // entries staged for this tile
 #endif
+    const int h0 = halo_ptr[t], hn = halo_ptr[t + 1] - h0, hs = (hn + 3) & ~3;
+    const int r0 = t * kFvThreads;
     if (threadIdx.x == 0) {
         const uint32_t bytes =
             uint32_t(HLBM_CHK(slice_ptr[4 * t + 4] - e_begin, max_tile_ent + 1, kSiteEntry)) * uint32_t(sizeof(E));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_e) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("{\n\t.reg .b64 st;\n\t"
-                     "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+                     "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar_e),
                      "r"(bytes)
                      : "memory");
         if (bytes > 0)
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                             bar + 16u),
-                         "l"(ent + e_begin), "r"(bytes), "r"(bar)
+                             bar_e + 16u),
+                         "l"(ent + e_begin), "r"(bytes), "r"(bar_e)
                          : "memory");
     }
     // Let the next sub-step's blocks start as soon as SM slots free up; they
     // only read constant operator data until their griddepcontrol.wait.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int h0 = halo_ptr[t], hn = halo_ptr[t + 1] - h0, own = tile_own[t];
-    const int r = t * blockDim.x + threadIdx.x;
+    const int r = r0 + threadIdx.x;
     const int rr = r < n ? r : n - 1;
     const int sl = rr >> 5;
     const int base = slice_ptr[sl] - e_begin + (rr & 31), len = slice_len[sl];
+    // the staged list: the tile's own 128 rows (device rows r0 .. r0 + 127, a
+    // run of every plane, copied in bulk), then the other nodes its rows
+    // touch (gathered)
     int hidx[kFvHaloRegs];
 #pragma unroll
     for (int j = 0; j < kFvHaloRegs; j++) {
-        const int h = threadIdx.x + j * kFvThreads;
+        const int h = kFvThreads + threadIdx.x + j * kFvThreads;
         hidx[j] = h < hn ? HLBM_CHK(halo_nodes[h0 + h], Np, kSiteMesh) : 0;
     }
     // The tile that will start about when this one ends (pf_ahead = the
     // resident blocks of this launch; blocks start in index order): its
-    // operator entries and, once the state is ready, its halo states are
-    // prefetched into L2, so that its gather finds them there.
+    // operator entries and, once the state is ready, its states are
+    // prefetched into L2, so that its copies find them there.
     const int tp = pf_ahead > 0 ? t + pf_ahead : int(gridDim.x);
     int pidx[kFvPrefetchRegs], hpn = 0;
     if (tp < int(gridDim.x)) {
@@ -955,7 +960,7 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
         hpn = halo_ptr[tp + 1] - hp0;
 #pragma unroll
         for (int j = 0; j < kFvPrefetchRegs; j++) {
-            const int h = threadIdx.x + j * kFvThreads;
+            const int h = kFvThreads + threadIdx.x + j * kFvThreads;
             pidx[j] = h < hpn ? HLBM_CHK(halo_nodes[hp0 + h], Np, kSiteMesh) : 0;
         }
         if (threadIdx.x == 0) {
@@ -967,33 +972,55 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
     }
     // wait until the previous sub-step (which wrote g) has completed
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (threadIdx.x == 0) {
+        constexpr uint32_t run = uint32_t(kFvThreads * sizeof(T));  // one plane's run of own rows
+        asm volatile("{\n\t.reg .b64 st;\n\t"
+                     "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar_s),
+                     "r"(9u * run)
+                     : "memory");
+        const uint32_t dst0 = uint32_t(__cvta_generic_to_shared(sh));
 #pragma unroll
-    for (int j = 0; j < kFvHaloRegs; j++) {
-        const int h = threadIdx.x + j * kFvThreads;
-        if (h < hn) {
+        for (int i = 0; i < 9; i++)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             dst0 + uint32_t(i * hs) * uint32_t(sizeof(T))),
+                         "l"(g + size_t(i) * Np + HLBM_CHK(r0, Np - kFvThreads + 1, kSiteMesh)), "r"(run), "r"(bar_s)
+                         : "memory");
+        if (tp < int(gridDim.x)) {
 #pragma unroll
-            for (int i = 0; i < 9; i++) sh[i * hn + h] = g[size_t(i) * Np + hidx[j]];
+            for (int i = 0; i < 9; i++)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g + size_t(i) * Np + size_t(tp) * kFvThreads),
+                             "r"(run)
+                             : "memory");
         }
     }
-    for (int h = threadIdx.x + kFvHaloRegs * kFvThreads; h < hn; h += kFvThreads) {
+#pragma unroll
+    for (int j = 0; j < kFvHaloRegs; j++) {
+        const int h = kFvThreads + threadIdx.x + j * kFvThreads;
+        if (h < hn) {
+#pragma unroll
+            for (int i = 0; i < 9; i++) sh[i * hs + h] = g[size_t(i) * Np + hidx[j]];
+        }
+    }
+    for (int h = kFvThreads * (1 + kFvHaloRegs) + threadIdx.x; h < hn; h += kFvThreads) {
         const int node = HLBM_CHK(halo_nodes[h0 + h], Np, kSiteMesh);
 #pragma unroll
-        for (int i = 0; i < 9; i++) sh[i * hn + h] = g[size_t(i) * Np + node];
+        for (int i = 0; i < 9; i++) sh[i * hs + h] = g[size_t(i) * Np + node];
     }
 #pragma unroll
     for (int j = 0; j < kFvPrefetchRegs; j++) {
-        if (threadIdx.x + j * kFvThreads < hpn) {
+        if (kFvThreads + threadIdx.x + j * kFvThreads < hpn) {
 #pragma unroll
             for (int i = 0; i < 9; i++)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(g + size_t(i) * Np + pidx[j]) : "memory");
         }
     }
     __syncthreads();
-    if (!mbar_wait(bar, 0)) {
-        // the entry copy did not arrive: report, give the copy one more bounded
-        // wait (it targets this block's shared memory) and leave
+    if (!mbar_wait(bar_e, 0) || !mbar_wait(bar_s, 0)) {
+        // a bulk copy did not arrive: report, give both copies one more
+        // bounded wait (they target this block's shared memory) and leave
         if (threadIdx.x == 0) atomicOr(flag, kFlagTimeout);
-        mbar_wait(bar, 0);
+        mbar_wait(bar_e, 0);
+        mbar_wait(bar_s, 0);
         return;
     }
     if (r >= n) return;
@@ -1004,9 +1031,9 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
     const int n_ent_chk = 0;
 #endif
     if constexpr (sizeof(T) == 4)
-        fv_row_f32(sh, hn, own + int(threadIdx.x), se, base, len, dt_tau, n_ent_chk, r1, ux, uy, nq);
+        fv_row_f32(sh, hs, int(threadIdx.x), se, base, len, dt_tau, n_ent_chk, r1, ux, uy, nq);
     else
-        fv_row_f64<T>(sh, hn, own + int(threadIdx.x), se, base, len, dt_tau, n_ent_chk, r1, ux, uy, nq);
+        fv_row_f64<T>(sh, hs, int(threadIdx.x), se, base, len, dt_tau, n_ent_chk, r1, ux, uy, nq);
     fv_finish_row<T>(gn, Np, r, n_wall, ring_start, n_ring, Q0, Q1, theta_next, scale5, star, r1, ux, uy, nq);
 }
 
@@ -1476,7 +1503,7 @@ template <typename T, typename S> void launch_fv(const DevCtx &C, int msub, cuda
         cudaLaunchKernelEx(&cfg, kern, (const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
                            (const int *)m.slice_ptr, (const int *)m.slice_len, (const typename Ent<T>::type *)m.ent,
                            m.max_tile_ent, (const int *)m.halo_ptr, (const int *)m.halo_nodes,
-                           (const int *)m.tile_own, dt_tau, m.n_wall, m.ring_start, m.n_ring, (const T *)m.Q0,
+                           dt_tau, m.n_wall, m.ring_start, m.n_ring, (const T *)m.Q0,
                            (const T *)m.Q1, theta_next, scale5, star, C.flag, pf);
     };
     if constexpr (sizeof(T) == 4) {

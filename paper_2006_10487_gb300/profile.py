@@ -44,8 +44,8 @@ def main():
            "n_sub": s.info("n_sub"), "fv_variant": s.info("fv_variant")}
     if args.kernel == "fv":
         # launches of the kernel before the timed graph: the FP32 autotuner's
-        # 2 x (3 + 20), the warm-up steps' sub-steps, the warm-up graph
-        tune = 46 if args.precision != "fp64" else 0
+        # 4 x (3 + 20), the warm-up steps' sub-steps, the warm-up graph
+        tune = 92 if args.precision != "fp64" else 0
         out["ncu_skip"] = tune + args.warmup * 2 ** (case.n_levels - 1) * int(out["n_sub"]) + args.reps
     s.close()
     print(json.dumps(out))

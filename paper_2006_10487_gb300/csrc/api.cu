@@ -409,7 +409,8 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     const LevelPlan &F = P.lv[P.L - 1];
     const DevLevel &FL = c->dev.lv[P.L - 1];
     M.n = P.n;
-    M.Np = (P.n + 31) / 32 * 32;
+    // rows padded to whole tiles: the sub-step kernel copies every tile's 128 rows in bulk
+    M.Np = (P.n + kTileRows - 1) / kTileRows * kTileRows;
     M.n_wall = P.n_wall;
     M.ring_start = P.ring_start;
     M.n_ring = P.n_ring;

@@ -551,11 +551,14 @@ __device__ __forceinline__ F2 fmaf2(F2 a, F2 b, F2 c) { return {fma2(a.v, b.v, c
 // are in Morton order).  Before the dependency wait (constant data only): one
 // thread starts a bulk asynchronous copy (TMA) of the tile's operator entries
 // (4 consecutive slices, one contiguous block) into shared memory, and every
-// thread loads up to kFvHaloRegs of the tile's halo node indices into
-// registers.  After the wait the states of every node the tile touches (its
-// sorted halo list, the tile's own rows included) are gathered into shared
-// memory, plane-major, in one round of loads; then each thread treats one row, reading its entries and its
-// neighbours from shared memory.
+// thread loads the index of the staged node it gathers.  After the wait the
+// states of every node the tile touches are staged in shared memory,
+// plane-major: the tile's own rows (the first kTileRows places of its staged
+// list) by nine bulk copies, one per plane, the other nodes (sorted, after
+// them) by the threads' loads; then each thread treats one row, reading its
+// entries and its neighbours from shared memory.  Within each 32-row slice the
+// set-up orders the rows' entries so that one slot's reads spread over the
+// shared-memory banks.
 constexpr int kFvThreads = kTileRows;
 constexpr int kFvGroup = 2;
 constexpr int kFvHaloRegs = 1;  // staged nodes beyond the tile's own rows gathered per thread from registers

@@ -434,6 +434,7 @@ def main():
         c04 = s4.time_kernel("collide0", 10)
         fvb4 = FV_BYTES[args.precision] * big.n_nodes
         lat4 = s4.info("lattice_updates")
+        s4_nsub = s4.info("n_sub")
         sb4 = lat4 * LAT_BYTES[args.precision] + fvb4 * s4.info("n_sub") * 2 ** (big.n_levels - 1)
         n0 = float(big.levels[0][0]) * float(big.levels[0][1])
         c0b = n0 * LAT_BYTES[args.precision]
@@ -453,6 +454,25 @@ def main():
                                "launch_ms": c04, "nodes": n0},
             "step": {"algorithmic_bytes": sb4, "achieved_gbs": sb4 / (ms4 * 1e-3) / 1e9,
                      "frac": sb4 / (ms4 * 1e-3) / 1e9 / peak}}
+        # the same case with the 16-bit lattice (FP16S), where the lattice is
+        # most of the bytes that the lower precision can save
+        if args.precision != "fp16s":
+            s4 = H.Solver(big, precision="fp16s", use_graphs=True)
+            s4.step(2)
+            s4.sync()
+            e0.record(stream)
+            s4.step(k4)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms16 = e0.elapsed_time(e1) / k4
+            c016 = s4.time_kernel("collide0", 10)
+            s4.close()
+            sb16 = lat4 * LAT_BYTES["fp16s"] + FV_BYTES["fp16s"] * big.n_nodes * s4_nsub * 2 ** (big.n_levels - 1)
+            line["hlbm_large"]["fp16s"] = {
+                "value": per4 / (ms16 * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms16, "steps": k4,
+                "step_frac": sb16 / (ms16 * 1e-3) / 1e9 / peak,
+                "collide_level0": {"launch_ms": c016, "bytes_per_launch": n0 * LAT_BYTES["fp16s"],
+                                   "frac": n0 * LAT_BYTES["fp16s"] / (c016 * 1e-3) / 1e9 / peak}}
         # ---- the accuracy half of the metric: FP32 and FP16S against the FP64
         # GPU path (pinned to the oracle at 1e-12) on the timed workload at
         # 8 degrees, 1000 coarse steps from the impulsive start
@@ -519,8 +539,9 @@ def main():
         # ---- Eq. 12-13 at 8 degrees (the paper's case for the mean C_p / C_f
         # figures) over a developed window: 8000 coarse steps of transient, then
         # 4000 averaged, with the odd-even filter of the mesh state (sigma =
-        # 0.002; without it the scheme goes unstable at about step 2500)
-        sig = 0.002
+        # 0.001, the smallest strength that kept this case stable for 20 000
+        # steps; without it the scheme goes unstable at about step 2500)
+        sig = 0.001
         c8 = make_case(WORKLOAD, aoa_deg=8.0, fv_filter=sig)
         s6 = H.Solver(c8, precision=args.precision, use_graphs=True, wall_stats=True, force_cap=16384)
         s6.step(8000)

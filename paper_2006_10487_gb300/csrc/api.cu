@@ -39,6 +39,12 @@ struct hlbm_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool side_ok[hlbm::kMaxLevels] = {};
+    // third branch: a finest step's finite-volume sub-steps run on mesh_side
+    // beside the coarser levels' lattice work that follows them, until the
+    // next read of the mesh state joins them back (mesh_pending)
+    cudaStream_t mesh_side = nullptr;
+    cudaEvent_t ev_mfork = nullptr, ev_mjoin = nullptr;
+    bool mesh_pending = false;
     int fv_variant_opt = 0;
     // mass monitoring (level 0, FP64): reference mass at create, last drift
     double *mass_buf = nullptr;  // [ny0 + 1]: row sums, total
@@ -217,12 +223,32 @@ void join(hlbm_ctx *c, cudaStream_t s)
     ck(cudaEventRecord(c->ev_join, c->side), "event record");
     ck(cudaStreamWaitEvent(s, c->ev_join, 0), "stream wait");
 }
+// The mesh branch: the finite-volume sub-steps of a finest step (they read
+// and write only the mesh state and read the Eq. 9 ring data) leave s on
+// c->mesh_side; s continues with the coarser levels' lattice work (which
+// touches neither), and every later reader or writer of the mesh state or of
+// the ring data (the next hole and ring interpolations, the forces, an
+// adjoint record) joins the branch first.
+void mesh_fork(hlbm_ctx *c, cudaStream_t s)
+{
+    ck(cudaEventRecord(c->ev_mfork, s), "event record");
+    ck(cudaStreamWaitEvent(c->mesh_side, c->ev_mfork, 0), "stream wait");
+    c->mesh_pending = true;
+}
+void mesh_join(hlbm_ctx *c, cudaStream_t s)
+{
+    if (!c->mesh_pending) return;
+    ck(cudaEventRecord(c->ev_mjoin, c->mesh_side), "event record");
+    ck(cudaStreamWaitEvent(s, c->ev_mjoin, 0), "stream wait");
+    c->mesh_pending = false;
+}
 
 template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double theta, cudaStream_t s)
 {
     DevCtx &D = c->dev;
     bool hybrid = (lvl == D.L - 1) && D.m.n > 0;
     bool child = lvl < D.L - 1;
+    if (hybrid) mesh_join(c, s);  // the previous finest step's sub-steps
     if (c->rec) {
         AdjRecorder &R = *c->rec;
         LevelRec r;
@@ -281,13 +307,18 @@ template <typename T, typename S> void level_step(hlbm_ctx *c, int lvl, double t
         if (c->rec) c->rec->recs.back().Q1 = c->rec->keep(D.m.Q1, 12 * size_t(std::max(1, D.m.n_ring)));
         if (branch) join(c, s);
         Range r("fv: sub-steps");
+        cudaStream_t sm = s;
+        if (c->mesh_side && !c->rec) {
+            mesh_fork(c, s);
+            sm = c->mesh_side;
+        }
         for (int m = 0; m < D.n_sub; m++) {  // Eq. 3, Eq. 5-7, wall rule
-            launch_fv<T, S>(D, m, s);
+            launch_fv<T, S>(D, m, sm);
             D.m.gcur ^= 1;
         }
         c->launches += 1 + D.n_sub;
         if (D.fv_filter > 0.0) {  // optional odd-even filter of the mesh state
-            launch_fv_filter<T, S>(D, s);
+            launch_fv_filter<T, S>(D, sm);
             D.m.gcur ^= 1;
             c->launches += 2;
         }
@@ -333,6 +364,7 @@ template <typename T, typename S> void coarse_step(hlbm_ctx *c, cudaStream_t s)
     long before = c->launches;
     Range step("coarse step");
     advance<T, S>(c, 0, 0.0, s);
+    mesh_join(c, s);
     if (c->dev.m.n > 0) {
         Range r("forces");
         launch_forces<T, S>(c->dev, s);
@@ -775,6 +807,9 @@ void release(hlbm_ctx *c)
     if (c->side) cudaStreamDestroy(c->side);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->mesh_side) cudaStreamDestroy(c->mesh_side);
+    if (c->ev_mfork) cudaEventDestroy(c->ev_mfork);
+    if (c->ev_mjoin) cudaEventDestroy(c->ev_mjoin);
 }
 
 }  // namespace
@@ -841,6 +876,9 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
         ck(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "stream create");
         ck(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event create");
         ck(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event create");
+        ck(cudaStreamCreateWithFlags(&c->mesh_side, cudaStreamNonBlocking), "stream create");
+        ck(cudaEventCreateWithFlags(&c->ev_mfork, cudaEventDisableTiming), "event create");
+        ck(cudaEventCreateWithFlags(&c->ev_mjoin, cudaEventDisableTiming), "event create");
         set_branches(c);
         {
             Range r("device upload and autotune");

@@ -60,6 +60,10 @@ struct hlbm_ctx {
     void *alloc_ctx = nullptr;
     std::vector<void *> blocks;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // two coarse steps from each parity in one graph: the second step's
+    // coarse-level lattice work runs beside the first step's last
+    // finite-volume sub-steps and forces
+    cudaGraphExec_t graph2[2] = {nullptr, nullptr};
     cudaGraph_t graph_tmpl[2] = {nullptr, nullptr};  // the captured graphs (child graphs of a batch)
     bool use_graphs = false;
     long steps = 0;
@@ -359,29 +363,34 @@ template <typename T, typename S> void advance(hlbm_ctx *c, int lvl, double thet
     }
 }
 
-template <typename T, typename S> void coarse_step(hlbm_ctx *c, cudaStream_t s)
+// One coarse step on s.  keep_branch: another coarse step follows in the same
+// graph, so the forces (which read the mesh state) stay on the mesh branch
+// and the next step's lattice work need not wait for them.
+template <typename T, typename S> void coarse_step(hlbm_ctx *c, cudaStream_t s, bool keep_branch = false)
 {
     long before = c->launches;
     Range step("coarse step");
     advance<T, S>(c, 0, 0.0, s);
-    mesh_join(c, s);
+    cudaStream_t sf = s;
+    if (keep_branch && c->mesh_pending) sf = c->mesh_side;
+    else mesh_join(c, s);
     if (c->dev.m.n > 0) {
         Range r("forces");
-        launch_forces<T, S>(c->dev, s);
+        launch_forces<T, S>(c->dev, sf);
         c->launches += 2;
         if (c->dev.m.wall_stats) {
-            launch_wall_stats<T, S>(c->dev, s);
+            launch_wall_stats<T, S>(c->dev, sf);
             c->launches += 1;
         }
     }
     c->launches_per_step = c->launches - before;
 }
 
-void enqueue_coarse_step(hlbm_ctx *c, cudaStream_t s)
+void enqueue_coarse_step(hlbm_ctx *c, cudaStream_t s, bool keep_branch = false)
 {
-    if (c->plan.precision == HLBM_FP32) coarse_step<float, float>(c, s);
-    else if (c->plan.precision == HLBM_FP16S) coarse_step<float, __half>(c, s);
-    else coarse_step<double, double>(c, s);
+    if (c->plan.precision == HLBM_FP32) coarse_step<float, float>(c, s, keep_branch);
+    else if (c->plan.precision == HLBM_FP16S) coarse_step<float, __half>(c, s, keep_branch);
+    else coarse_step<double, double>(c, s, keep_branch);
 }
 
 // Total mass of level 0 now (FP64; synchronises the context's stream).
@@ -763,6 +772,24 @@ void capture_graphs(hlbm_ctx *c)
         c->graph_tmpl[k] = g;
         ck(cudaGraphInstantiate(&c->graph[k], g, 0), "graph instantiate");
     }
+    for (int k = 0; k < 2; k++) {  // coarse steps k, k + 1 (mod 2)
+        cudaGraph_t g = nullptr;
+        set_phase(c, k);
+        ck(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        try {
+            enqueue_coarse_step(c, c->cap_stream, true);
+            set_phase(c, k + 1);
+            enqueue_coarse_step(c, c->cap_stream);
+        } catch (...) {
+            cudaStreamEndCapture(c->cap_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        ck(cudaStreamEndCapture(c->cap_stream, &g), "end capture");
+        const cudaError_t e = cudaGraphInstantiate(&c->graph2[k], g, 0);
+        cudaGraphDestroy(g);
+        ck(e, "graph instantiate");
+    }
     set_phase(c, c->steps);
 }
 
@@ -795,6 +822,7 @@ void release(hlbm_ctx *c)
 {
     for (int k = 0; k < 2; k++) {
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        if (c->graph2[k]) cudaGraphExecDestroy(c->graph2[k]);
         if (c->graph_tmpl[k]) cudaGraphDestroy(c->graph_tmpl[k]);
     }
     if (c->stream) cudaStreamSynchronize(c->stream);
@@ -918,7 +946,16 @@ int hlbm_step(hlbm_ctx *c, int n_coarse)
     try {
         for (int k = 0; k < n_coarse; k++) {
             if (c->use_graphs) {
-                ck(cudaGraphLaunch(c->graph[c->steps & 1], c->stream), "graph launch");
+                // two steps per launch where they remain and no health check falls between them
+                const bool pair = c->graph2[c->steps & 1] && k + 1 < n_coarse &&
+                                  !(c->check_every > 0 && (c->steps + 1) % c->check_every == 0);
+                if (pair) {
+                    ck(cudaGraphLaunch(c->graph2[c->steps & 1], c->stream), "graph launch");
+                    c->steps++;
+                    k++;
+                } else {
+                    ck(cudaGraphLaunch(c->graph[c->steps & 1], c->stream), "graph launch");
+                }
             } else {
                 set_phase(c, c->steps);
                 enqueue_coarse_step(c, c->stream);

@@ -313,7 +313,7 @@ def main():
     # ---- roofline of the dominant kernel (finite-volume sub-step), measured
     # live with CUDA events on the library's stream
     peak, peak_kind = _peaks()
-    fv_variant = [s.info("fv_variant")] + [s.info(f"fv_tune_us{v}") for v in (1, 2, 3, 4)]
+    fv_variant = [s.info("fv_variant")] + [s.info(f"fv_tune_us{v}") for v in range(1, 9)]
     fv_ms = s.time_kernel("fv", 200)
     n_sub = s.info("n_sub")
     fv_bytes = FV_BYTES[args.precision] * case.n_nodes
@@ -325,9 +325,12 @@ def main():
                 "traffic": _traffic("k_fv", args.precision), "bytes_per_unit": FV_BYTES[args.precision],
                 "units_per_launch": case.n_nodes, "bytes_per_launch": fv_bytes,
                 "kernel_bytes_per_launch": s.info("fv_bytes"), "launch_ms": fv_ms,
-                "autotuner": {"variant": fv_variant[0], "us_7_blocks_per_sm": fv_variant[1],
+                "autotuner": {"variant": fv_variant[0], "tile_rows": s.info("fv_tile_rows"),
+                              "us_7_blocks_per_sm": fv_variant[1],
                               "us_8_blocks_per_sm": fv_variant[2], "us_7_with_l2_prefetch": fv_variant[3],
-                              "us_8_with_l2_prefetch": fv_variant[4]},
+                              "us_8_with_l2_prefetch": fv_variant[4], "wide_256_rows_us_3_blocks_per_sm": fv_variant[5],
+                              "wide_us_4_blocks_per_sm": fv_variant[6], "wide_us_3_with_l2_prefetch": fv_variant[7],
+                              "wide_us_4_with_l2_prefetch": fv_variant[8]},
                 "l2_note": "the finite-volume working set (~37 MB) stays L2-resident between sub-steps; "
                            "hlbm_large carries the HBM-bound roofline of the same kernel",
                 "step": {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / args.steps * 1e-3) / 1e9,
@@ -448,7 +451,7 @@ def main():
                          "frac": fvb4 / (fv4 * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
                          "traffic": _traffic("k_fv_large", args.precision), "bytes_per_unit": FV_BYTES[args.precision],
                          "units_per_launch": big.n_nodes, "bytes_per_launch": fvb4, "launch_ms": fv4,
-                         "autotuner_variant": var4},
+                         "autotuner_variant": var4, "tile_rows": s4.info("fv_tile_rows")},
             "collide_level0": {"achieved": c0b / (c04 * 1e-3) / 1e9, "unit": "GB/s",
                                "frac": c0b / (c04 * 1e-3) / 1e9 / peak, "bytes_per_launch": c0b,
                                "launch_ms": c04, "nodes": n0},

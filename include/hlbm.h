@@ -91,11 +91,15 @@ typedef struct {
  * wall_stats: 1 adds to every coarse step the accumulation of the wall
  * coefficients read by hlbm_wall_stats (one small kernel over the wall
  * nodes); 0 leaves the step as it is.  fv_variant: variant of the FP32
- * finite-volume kernel: 0 times all four on this mesh at create and keeps the
- * fastest (the autotuner); 1 registers bounded for 7 resident blocks per SM,
- * 2 for 8; 3 and 4 the same with an L2 prefetch, by every block, of the
- * entries and halo states of the tile that starts about when it ends; all
- * give the same results (FP64 has one unbounded kernel; reports 1).
+ * finite-volume kernel: 0 times all eight on this mesh at create and keeps
+ * the fastest (the autotuner); 1-4 on tiles of 128 rows: 1 registers bounded
+ * for 7 resident blocks per SM, 2 for 8, 3 and 4 the same with an L2
+ * prefetch, by every block, of the entries and halo states of the tile that
+ * starts about when it ends; 5-8 the same four on tiles of 256 rows (3 and 4
+ * resident blocks per SM; HLBM_ECUDA if such a tile's staging does not fit in
+ * shared memory).  Variants of one tile size give the same results; the two
+ * tile sizes order each row's operator entries differently (FP32 rounding).
+ * FP64 has one unbounded kernel on 128-row tiles and reports 1.
  * fv_filter: strength sigma in [0, 1] of an odd-even filter of the mesh state
  * applied once per finest step after the Eq. 3 sub-steps (an addition to the
  * paper's method, 0 = off, the default of a zeroed struct): with the graph
@@ -172,9 +176,10 @@ int hlbm_populations(hlbm_ctx *ctx, int grid, double *out, size_t cap);
  * "launches_per_step" (kernels in one coarse step), "fv_bytes" (algorithmic
  * bytes of one finite-volume sub-step), "collide_bytes<l>" (algorithmic bytes
  * of one lattice step of level l), "fv_tiles" (blocks of one finite-volume
- * sub-step), "fv_smem" (their dynamic shared memory, bytes), "fv_variant"
- * (the variant in use, see options), "fv_tune_us1" .. "fv_tune_us4" (the
- * autotuner's launch times of the four variants, 0 if it did not run),
+ * sub-step), "fv_tile_rows" (rows per tile, 128 or 256), "fv_smem" (their
+ * dynamic shared memory, bytes), "fv_variant" (the variant in use, 1-8, see
+ * options), "fv_tune_us1" .. "fv_tune_us8" (the autotuner's launch times of
+ * the eight variants, 0 if it did not run or a tile size was not built),
  * "create_ms_setup", "create_ms_device", "create_ms_capture" (wall time of
  * hlbm_create's host set-up tables, device build with uploads, initial
  * state and autotuning, and graph capture, in ms; the device build splits

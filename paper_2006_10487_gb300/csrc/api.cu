@@ -49,7 +49,7 @@ struct hlbm_ctx {
     // mass monitoring (level 0, FP64): reference mass at create, last drift
     double *mass_buf = nullptr;  // [ny0 + 1]: row sums, total
     double mass0 = 0.0, mass_drift = 0.0, mass_nodes = 0.0;
-    double fv_tune_us[4] = {0.0, 0.0, 0.0, 0.0};
+    double fv_tune_us[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     double create_ms[3] = {0.0, 0.0, 0.0};  // host set-up tables, device build, graph capture
     double build_ms[2] = {0.0, 0.0};         // device build: tables and uploads; initial state and autotuner
     AdjTables adj;                            // finite-volume adjoint tables (built on first use)
@@ -443,76 +443,59 @@ template <typename T, typename S> void init_state(hlbm_ctx *c)
     ck(cudaGetLastError(), "init kernels");
 }
 
-template <typename T> void upload_mesh(hlbm_ctx *c)
+// One tiling of the finite-volume sub-step kernel (tiles of `rows` device
+// rows): each tile's staged list and the operator entries with their
+// positions in it, in a per-slice order spread over the shared-memory banks;
+// uploads them into tl (tl.rows stays 0 if a tile's staging does not fit in
+// shared memory).
+template <typename T>
+void build_tiles(hlbm_ctx *c, const std::vector<int> &odp, const std::vector<int> &od, const std::vector<int> &sptr,
+                 const std::vector<int> &slen, int rows, FvTiles &tl)
 {
-    Plan &P = c->plan;
-    DevMesh &M = c->dev.m;
-    const LevelPlan &F = P.lv[P.L - 1];
-    const DevLevel &FL = c->dev.lv[P.L - 1];
-    M.n = P.n;
-    // rows padded to whole tiles: the sub-step kernel copies every tile's 128 rows in bulk
-    M.Np = (P.n + kTileRows - 1) / kTileRows * kTileRows;
-    M.n_wall = P.n_wall;
-    M.ring_start = P.ring_start;
-    M.n_ring = P.n_ring;
-    for (int b = 0; b < 2; b++) M.g[b] = dalloc(c, size_t(9) * M.Np * sizeof(T));
-    if (c->dev.fv_filter > 0.0) M.lap = dalloc(c, size_t(9) * M.Np * sizeof(T));
-    // sliced-ELL operator rows in device order; the column of every entry is
-    // the position of the neighbour in its tile's halo list (the sorted nodes
-    // the tile's rows touch), which the kernel stages in shared memory
+    const Plan &P = c->plan;
+    const DevMesh &M = c->dev.m;
     using E = typename std::conditional<std::is_same<T, float>::value, float4, double4_32a>::type;
-    M.n_slices = M.Np / 32;
-    M.n_tiles = (P.n + kTileRows - 1) / kTileRows;
-    std::vector<int> hptr(M.n_tiles + 1, 0), hnodes;
-    // the self entry of a row is not stored: its streaming term vanishes in the
-    // difference form and its collision weight is C_PP = 11/18 on every node;
-    // off-diagonal entries of device row r: od[odp[r] .. odp[r + 1])
-    std::vector<int> odp(size_t(P.n) + 1, 0), od;
-    od.reserve(P.col.size());
-    for (int r = 0; r < P.n; r++) {
-        const int old = P.perm[r];
-        for (int k = P.rowptr[old]; k < P.rowptr[old + 1]; k++)
-            if (P.col[k] != old) od.push_back(k);
-        odp[r + 1] = int(od.size());
-    }
-    // tile t's staged list: its own 128 device rows r0 .. r0 + 127 (the last
+    tl = FvTiles();
+    const int n_tiles = (P.n + rows - 1) / rows;
+    int max_halo = 0;
+    std::vector<int> hptr(n_tiles + 1, 0), hnodes;
+    // tile t's staged list: its own device rows r0 .. r0 + rows - 1 (the last
     // tile's run reaches into the padding rows, never referenced), which the
     // kernel copies in bulk, then the other nodes its rows touch, sorted,
     // which it gathers; an entry's column is its node's position in the list
-    std::vector<std::vector<int>> halo(M.n_tiles);
-    parallel_for(M.n_tiles, [&](int t0, int t1) {
+    std::vector<std::vector<int>> halo(n_tiles);
+    parallel_for(n_tiles, [&](int t0, int t1) {
         for (int t = t0; t < t1; t++) {
-            const int r0 = t * kTileRows;
+            const int r0 = t * rows;
             std::vector<int> &h = halo[t];
-            for (int r = r0; r < std::min(P.n, r0 + kTileRows); r++)
+            for (int r = r0; r < std::min(P.n, r0 + rows); r++)
                 for (int j = odp[r]; j < odp[r + 1]; j++) {
                     const int c = P.inv[P.col[od[j]]];
-                    if (c < r0 || c >= r0 + kTileRows) h.push_back(c);
+                    if (c < r0 || c >= r0 + rows) h.push_back(c);
                 }
             std::sort(h.begin(), h.end());
             h.erase(std::unique(h.begin(), h.end()), h.end());
-            std::vector<int> own(kTileRows);
-            for (int j = 0; j < kTileRows; j++) own[j] = r0 + j;
+            std::vector<int> own(rows);
+            for (int j = 0; j < rows; j++) own[j] = r0 + j;
             h.insert(h.begin(), own.begin(), own.end());
         }
     }, 16);
-    for (int t = 0; t < M.n_tiles; t++) {
+    for (int t = 0; t < n_tiles; t++) {
         hptr[t + 1] = hptr[t] + int(halo[t].size());
-        M.max_halo = std::max(M.max_halo, int(halo[t].size()));
+        max_halo = std::max(max_halo, int(halo[t].size()));
     }
-    hnodes.resize(hptr[M.n_tiles]);
-    parallel_for(M.n_tiles, [&](int t0, int t1) {
+    hnodes.resize(hptr[n_tiles]);
+    parallel_for(n_tiles, [&](int t0, int t1) {
         for (int t = t0; t < t1; t++) std::copy(halo[t].begin(), halo[t].end(), hnodes.begin() + hptr[t]);
     }, 16);
     halo.clear();
     // position of device node c in tile t's staged list
     auto halo_pos = [&](int t, int c) {
-        const int r0 = t * kTileRows;
-        if (c >= r0 && c < r0 + kTileRows) return c - r0;
-        const int *h0 = hnodes.data() + hptr[t] + kTileRows, *h1 = hnodes.data() + hptr[t + 1];
-        return kTileRows + int(std::lower_bound(h0, h1, c) - h0);
+        const int r0 = t * rows;
+        if (c >= r0 && c < r0 + rows) return c - r0;
+        const int *h0 = hnodes.data() + hptr[t] + rows, *h1 = hnodes.data() + hptr[t + 1];
+        return rows + int(std::lower_bound(h0, h1, c) - h0);
     };
-    std::vector<int> sptr(M.n_slices), slen(M.n_slices);
     std::vector<E> ent;
     auto set_col = [](E &v, int col) {
         if (std::is_same<T, float>::value) { float fcol; std::memcpy(&fcol, &col, 4); std::memcpy(&v.w, &fcol, 4); }
@@ -520,19 +503,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     };
     // entries carry dt s_Pk and (dt / tau_u) C_Pk (the sub-step's constants folded in)
     const double dt = P.n_sub > 0 ? 1.0 / P.n_sub : 0.0, dt_tau = dt / P.tau_u;
-    // slice lengths and offsets, then the entries (slices in parallel)
-    size_t n_ent = 0;
-    for (int sl = 0; sl < M.n_slices; sl++) {
-        int len = 0;
-        for (int l = 0; l < 32; l++) {
-            int r = sl * 32 + l;
-            if (r < P.n) len = std::max(len, odp[r + 1] - odp[r]);
-        }
-        sptr[sl] = int(n_ent);
-        slen[sl] = len;
-        n_ent += size_t(32) * len;
-    }
-    ent.resize(n_ent);
+    ent.resize(size_t(sptr[M.n_slices]));
     // Entry order within a row is free (the sums are over all of them), so
     // each slice orders its 32 rows' entries slot by slot to spread the 32
     // shared-memory reads of one slot over the banks: a row takes, among its
@@ -542,7 +513,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     // padding entries (zero coefficients) read a position already read.
     parallel_for(M.n_slices, [&](int sl0, int sl1) {
         std::vector<int> pos[32], order[32];
-        std::vector<int> stamp(size_t(M.max_halo) + 1, -1);  // slot stamp of each staged position
+        std::vector<int> stamp(size_t(max_halo) + 1, -1);  // slot stamp of each staged position
         int stamp_id = 0;
         for (int sl = sl0; sl < sl1; sl++) {
             const int len = slen[sl];
@@ -554,7 +525,7 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
                 order[l].clear();
                 used[l] = 0;
                 if (r >= P.n) continue;
-                for (int j = odp[r]; j < odp[r + 1]; j++) pos[l].push_back(halo_pos(r / kTileRows, P.inv[P.col[od[j]]]));
+                for (int j = odp[r]; j < odp[r + 1]; j++) pos[l].push_back(halo_pos(r / rows, P.inv[P.col[od[j]]]));
             }
             bool small = true;  // the bank-aware order tracks up to 32 entries per row
             for (int l = 0; l < 32; l++) small = small && pos[l].size() <= 32;
@@ -617,18 +588,73 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
             }
         }
     }, 64);
-    // one past the end, for every tile's 4 slices (the last tile may have fewer)
-    sptr.resize(size_t(4) * M.n_tiles + 1, int(ent.size()));
-    for (int t = 0; t < M.n_tiles; t++) M.max_tile_ent = std::max(M.max_tile_ent, sptr[4 * t + 4] - sptr[4 * t]);
-    M.halo_ptr = upload(c, hptr);
-    M.halo_nodes = upload(c, hnodes);
-    // mbarrier (16 B), the tile's entries, the halo states
-    // (planes of a stride rounded up to 4 values: 16-byte aligned bulk copies)
-    M.smem_bytes = 16 + size_t(M.max_tile_ent) * sizeof(E) + size_t((M.max_halo + 3) & ~3) * 9 * sizeof(T);
-    if (M.smem_bytes > 200 * 1024) throw CudaError{"mesh tiles touch too many nodes for shared memory"};
-    configure_fv<T, T>(M.smem_bytes);
-    configure_fv_prefetch<T, T>(M);
-    M.ent = upload(c, ent);
+    int max_tile_ent = 0;
+    for (int t = 0; t < n_tiles; t++)
+        max_tile_ent = std::max(max_tile_ent, sptr[std::min(M.n_slices, (rows / 32) * (t + 1))] - sptr[(rows / 32) * t]);
+    // mbarriers (16 B), the tile's entries, the staged states (planes of a
+    // stride rounded up to 4 values: 16-byte aligned bulk copies)
+    const size_t smem = 16 + size_t(max_tile_ent) * sizeof(E) + size_t((max_halo + 3) & ~3) * 9 * sizeof(T);
+    if (smem > 200 * 1024) return;
+    tl.rows = rows;
+    tl.n_tiles = n_tiles;
+    tl.max_tile_ent = max_tile_ent;
+    tl.max_halo = max_halo;
+    tl.smem_bytes = smem;
+    configure_fv<T, T>(tl);
+    configure_fv_prefetch<T, T>(tl);
+    tl.halo_ptr = upload(c, hptr);
+    tl.halo_nodes = upload(c, hnodes);
+    tl.ent = upload(c, ent);
+}
+
+template <typename T> void upload_mesh(hlbm_ctx *c)
+{
+    Plan &P = c->plan;
+    DevMesh &M = c->dev.m;
+    const LevelPlan &F = P.lv[P.L - 1];
+    const DevLevel &FL = c->dev.lv[P.L - 1];
+    M.n = P.n;
+    // rows padded to whole tiles of either tiling: the sub-step kernel copies
+    // every tile's rows in bulk
+    M.Np = (P.n + kTileRowsWide - 1) / kTileRowsWide * kTileRowsWide;
+    M.n_wall = P.n_wall;
+    M.ring_start = P.ring_start;
+    M.n_ring = P.n_ring;
+    for (int b = 0; b < 2; b++) M.g[b] = dalloc(c, size_t(9) * M.Np * sizeof(T));
+    if (c->dev.fv_filter > 0.0) M.lap = dalloc(c, size_t(9) * M.Np * sizeof(T));
+    // the self entry of a row is not stored: its streaming term vanishes in the
+    // difference form and its collision weight is C_PP = 11/18 on every node;
+    // off-diagonal entries of device row r: od[odp[r] .. odp[r + 1])
+    std::vector<int> odp(size_t(P.n) + 1, 0), od;
+    od.reserve(P.col.size());
+    for (int r = 0; r < P.n; r++) {
+        const int old = P.perm[r];
+        for (int k = P.rowptr[old]; k < P.rowptr[old + 1]; k++)
+            if (P.col[k] != old) od.push_back(k);
+        odp[r + 1] = int(od.size());
+    }
+    // sliced-ELL operator rows in device order, 32-row slices: lengths and
+    // offsets (the same for every tiling), then each tiling's entries
+    M.n_slices = M.Np / 32;
+    std::vector<int> sptr(size_t(M.n_slices) + 1), slen(M.n_slices);
+    size_t n_ent = 0;
+    for (int sl = 0; sl < M.n_slices; sl++) {
+        int len = 0;
+        for (int l = 0; l < 32; l++) {
+            int r = sl * 32 + l;
+            if (r < P.n) len = std::max(len, odp[r + 1] - odp[r]);
+        }
+        sptr[sl] = int(n_ent);
+        slen[sl] = len;
+        n_ent += size_t(32) * len;
+    }
+    sptr[M.n_slices] = int(n_ent);
+    build_tiles<T>(c, odp, od, sptr, slen, kTileRows, M.tl);
+    if (!M.tl.rows) throw CudaError{"mesh tiles touch too many nodes for shared memory"};
+    // FP32: also the wide tiling, for the autotuner to time
+    if (std::is_same<T, float>::value && c->fv_variant_opt != 1 && c->fv_variant_opt != 2 &&
+        c->fv_variant_opt != 3 && c->fv_variant_opt != 4)
+        build_tiles<T>(c, odp, od, sptr, slen, kTileRowsWide, M.tl_alt);
     M.slice_ptr = upload(c, sptr);
     M.slice_len = upload(c, slen);
     M.Qb[0] = dalloc(c, size_t(12) * std::max(1, P.n_ring) * sizeof(T));
@@ -743,9 +769,24 @@ template <typename T, typename S> void build_device(hlbm_ctx *c)
     const auto t_up = std::chrono::steady_clock::now();
     init_state<T, S>(c);
     if (P.n > 0) {
-        if (c->plan.precision == HLBM_FP64) D.m.fv_variant = 1;
-        else if (c->fv_variant_opt > 0) D.m.fv_variant = c->fv_variant_opt;
-        else D.m.fv_variant = fv_autotune<T, S>(D, c->stream, c->fv_tune_us);
+        DevMesh &M = D.m;
+        if (c->plan.precision == HLBM_FP64) {
+            M.fv_variant = 1;
+        } else if (c->fv_variant_opt > 4) {  // a variant of the wide tiling, if it was built
+            if (!M.tl_alt.rows) throw CudaError{"fv_variant 5..8: the wide tiling does not fit in shared memory"};
+            std::swap(M.tl, M.tl_alt);
+            M.fv_variant = c->fv_variant_opt - 4;
+        } else if (c->fv_variant_opt > 0) {
+            M.fv_variant = c->fv_variant_opt;
+        } else {
+            fv_autotune<T, S>(D, c->stream, c->fv_tune_us);
+        }
+        ck(cudaStreamSynchronize(c->stream), "sync");
+        // the tiling not kept
+        dfree(c, M.tl_alt.ent);
+        dfree(c, M.tl_alt.halo_ptr);
+        dfree(c, M.tl_alt.halo_nodes);
+        M.tl_alt = FvTiles();
         ck(cudaGetLastError(), "finite-volume autotuner");
     }
     ck(cudaStreamSynchronize(c->stream), "sync");
@@ -890,7 +931,7 @@ int hlbm_create(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double R
     c->alloc_ctx = o.alloc_ctx;
     c->use_graphs = o.use_graphs != 0;
     c->dev.m.wall_stats = o.wall_stats != 0;
-    if (o.fv_variant < 0 || o.fv_variant > 4) { delete c; return fail(nullptr, HLBM_EINVAL, "fv_variant must be in 0..4"); }
+    if (o.fv_variant < 0 || o.fv_variant > 8) { delete c; return fail(nullptr, HLBM_EINVAL, "fv_variant must be in 0..8"); }
     c->fv_variant_opt = o.fv_variant;
     if (!(o.fv_filter >= 0.0 && o.fv_filter <= 1.0)) {
         delete c;
@@ -1088,7 +1129,7 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
         *value = u;
     } else if (k == "fv_updates") *value = double(P.n) * P.n_sub * double(1L << (P.L - 1));
     else if (k == "launches_per_step") *value = double(c->launches_per_step);
-    else if (k == "fv_tiles") *value = double(c->dev.m.n_tiles);
+    else if (k == "fv_tiles") *value = double(c->dev.m.tl.n_tiles);
     else if (k == "mass" || k == "mass_drift") {
         if (c->timing_dirty) return HLBM_ESTATE;
         try {
@@ -1103,7 +1144,9 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
         if (cudaDeviceSynchronize() != cudaSuccess) return HLBM_ECUDA;
         *value = debug_bounds(b) ? double(b[k == "bounds_sites"]) : -1.0;
     }
-    else if (k == "fv_variant") *value = double(c->dev.m.fv_variant);
+    else if (k == "fv_variant")
+        *value = double(c->dev.m.fv_variant + (c->dev.m.tl.rows == kTileRowsWide ? 4 : 0));
+    else if (k == "fv_tile_rows") *value = double(c->dev.m.tl.rows);
     else if (k == "fv_filter") *value = c->dev.fv_filter;
     else if (k == "create_ms_setup") *value = c->create_ms[0];
     else if (k == "create_ms_device") *value = c->create_ms[1];
@@ -1114,7 +1157,11 @@ int hlbm_info(const hlbm_ctx *c, const char *key, double *value)
     else if (k == "fv_tune_us2") *value = c->fv_tune_us[1];
     else if (k == "fv_tune_us3") *value = c->fv_tune_us[2];
     else if (k == "fv_tune_us4") *value = c->fv_tune_us[3];
-    else if (k == "fv_smem") *value = double(c->dev.m.smem_bytes);
+    else if (k == "fv_tune_us5") *value = c->fv_tune_us[4];
+    else if (k == "fv_tune_us6") *value = c->fv_tune_us[5];
+    else if (k == "fv_tune_us7") *value = c->fv_tune_us[6];
+    else if (k == "fv_tune_us8") *value = c->fv_tune_us[7];
+    else if (k == "fv_smem") *value = double(c->dev.m.tl.smem_bytes);
     else if (k == "fv_bytes") {
         // algorithmic bytes of one finite-volume sub-step: the 9 state values of
         // every node read and written, one (s_x, s_y, C, column) entry per

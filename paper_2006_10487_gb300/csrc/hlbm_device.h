@@ -32,27 +32,40 @@ struct DevLevel {
     int spar = 0;  // snapA = snap[spar], snapB = snap[spar ^ 1]
 };
 
+// One tiling of the finite-volume sub-step kernel: tiles of `rows`
+// consecutive device rows (= threads per block); tile t's staged list
+// halo_nodes[halo_ptr[t] .. halo_ptr[t+1]) is its own rows, then the other
+// nodes its rows touch (sorted); the operator entries (sliced ELL, see
+// DevMesh) carry positions in that list, in an order chosen per slice for
+// the shared-memory banks.
+struct FvTiles {
+    int rows = 0;  // 0: not built
+    int n_tiles = 0, max_tile_ent = 0, max_halo = 0;
+    void *ent = nullptr;
+    int *halo_ptr = nullptr, *halo_nodes = nullptr;
+    int pf_ahead[3] = {0, 0, 0};  // per register bound: resident blocks (tile distance of the L2 prefetch)
+    size_t smem_bytes = 0;
+};
+
 // The triangular mesh in device order (wall nodes, fluid nodes, ring nodes).
 struct DevMesh {
     int n = 0, Np = 0, n_wall = 0, ring_start = 0, n_ring = 0;
     void *g[2] = {nullptr, nullptr};  // [9][Np] (rho - 1, ux, uy, f^neq_3..8), double-buffered
     int gcur = 0;
     // Eq. 3 operators, sliced ELL with 32-row slices: entry e of row r sits at
-    // slice_ptr[r / 32] + 32 e + r % 32, as (dt s_x, dt s_y, dt / tau_u C,
-    // column); slice_ptr has n_slices + 1 elements, and the 4 slices of tile t
-    // are the contiguous block [slice_ptr[4 t], slice_ptr[4 t + 4]) of at most
+    // slice_ptr[r / 32] + 32 e + r % 32 of the tiling's entries, as
+    // (dt s_x, dt s_y, dt / tau_u C, column); slice_ptr has n_slices + 1
+    // elements, and the rows / 32 slices of tile t are the contiguous block
+    // [slice_ptr[(rows / 32) t], slice_ptr[(rows / 32) (t + 1)]) of at most
     // max_tile_ent entries
-    int n_slices = 0, max_tile_ent = 0;
-    void *ent = nullptr;
+    int n_slices = 0;
     int *slice_ptr = nullptr, *slice_len = nullptr;
-    // tiles of kTileRows consecutive rows; tile t's staged list
-    // halo_nodes[halo_ptr[t] .. halo_ptr[t+1]) is its own kTileRows rows, then
-    // the other nodes its rows touch (sorted); entry columns index that list
-    int n_tiles = 0, max_halo = 0;
-    int *halo_ptr = nullptr, *halo_nodes = nullptr;
-    int fv_variant = 1;       // FP32 sub-step kernel bounded for 1, 3: 7; 2, 4: 8 blocks per SM (3, 4: L2 prefetch)
-    int pf_ahead[3] = {0, 0, 0};  // per variant: resident blocks (tile distance of the L2 prefetch)
-    size_t smem_bytes = 0;
+    // the tiling in use (kTileRows or kTileRowsWide rows) and, until the
+    // autotuner has chosen, the other one
+    FvTiles tl, tl_alt;
+    // FP32 sub-step kernel bounded for 1, 3: 7 (wide tiles: 3); 2, 4: 8 (4)
+    // blocks per SM; 3, 4 with the L2 prefetch of a later tile
+    int fv_variant = 1;
     // [12][n_ring] Eq. 9 data at t and t + 1: two buffers whose roles swap
     // every finest step (the data at t + 1 of one step is the data at t of the
     // next: nothing writes the finest level's lattice in between)
@@ -96,15 +109,19 @@ struct DevCtx {
     int force_cap = 0;
 };
 
-constexpr int kTileRows = 128;  // rows per finite-volume tile (= threads per block)
+constexpr int kTileRows = 128;       // rows per finite-volume tile (= threads per block)
+constexpr int kTileRowsWide = 256;   // the wide tiling the FP32 autotuner also times
 
 // Launchers, T = arithmetic type, S = lattice storage type (T, or __half for
 // FP16S); raises the FV kernel's dynamic shared-memory limit (configure_fv).
-template <typename T, typename S> void configure_fv(size_t bytes);
-// resident blocks of each sub-step kernel variant on this mesh (m.pf_ahead)
-template <typename T, typename S> void configure_fv_prefetch(DevMesh &m);
-// times the FP32 sub-step kernel's variants on this mesh; returns the fastest
-template <typename T, typename S> int fv_autotune(DevCtx &, cudaStream_t, double us[4]);
+template <typename T, typename S> void configure_fv(const FvTiles &tl);
+// resident blocks of each sub-step kernel variant of a tiling (tl.pf_ahead)
+template <typename T, typename S> void configure_fv_prefetch(FvTiles &tl);
+// times the FP32 sub-step kernel's four variants on this mesh's tiling
+// (us[0..3]) and on the wide tiling if built (us[4..7]); leaves the fastest
+// in m.tl / m.fv_variant (the other tiling in m.tl_alt, for the caller to
+// free) and returns it as 1..4 (tiles of kTileRows) or 5..8 (wide tiles)
+template <typename T, typename S> int fv_autotune(DevCtx &, cudaStream_t, double us[8]);
 template <typename T, typename S> void launch_init_level(const DevCtx &, int c, unsigned long long seed, double perturb, cudaStream_t);
 template <typename T, typename S> void launch_collide(const DevCtx &, int c, cudaStream_t);
 template <typename T, typename S> void launch_outer_bc(const DevCtx &, cudaStream_t);

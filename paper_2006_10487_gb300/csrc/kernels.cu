@@ -550,7 +550,7 @@ __device__ __forceinline__ F2 fmaf2(F2 a, F2 b, F2 c) { return {fma2(a.v, b.v, c
 // Each block is one tile of kTileRows consecutive rows (a compact patch: rows
 // are in Morton order).  Before the dependency wait (constant data only): one
 // thread starts a bulk asynchronous copy (TMA) of the tile's operator entries
-// (4 consecutive slices, one contiguous block) into shared memory, and every
+// (its consecutive slices, one contiguous block) into shared memory, and every
 // thread loads the index of the staged node it gathers.  After the wait the
 // states of every node the tile touches are staged in shared memory,
 // plane-major: the tile's own rows (the first kTileRows places of its staged
@@ -559,7 +559,6 @@ __device__ __forceinline__ F2 fmaf2(F2 a, F2 b, F2 c) { return {fma2(a.v, b.v, c
 // entries and its neighbours from shared memory.  Within each 32-row slice the
 // set-up orders the rows' entries so that one slot's reads spread over the
 // shared-memory banks.
-constexpr int kFvThreads = kTileRows;
 constexpr int kFvGroup = 2;
 constexpr int kFvHaloRegs = 1;  // staged nodes beyond the tile's own rows gathered per thread from registers
 constexpr int kFvPrefetchRegs = 1;  // nodes beyond a later tile's own rows prefetched into L2, per thread
@@ -891,11 +890,13 @@ __device__ __forceinline__ void fv_finish_row(T *__restrict__ gn, int Np, int r,
     for (int i = 3; i < 9; i++) gn[size_t(i) * Np + r] = nq[i];
 }
 
-// MINB: blocks per SM the register allocation is bounded for (1: unbounded);
-// the FP32 kernel is built for 7 and 8, and each context keeps the faster one
-// for its mesh (fv_autotune); FP64 is built unbounded.
-template <typename T, int MINB>
-__global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
+// ROWS: rows per tile (= threads per block); MINB: blocks per SM the
+// register allocation is bounded for (1: unbounded).  The FP32 kernel is
+// built for 7 and 8 blocks of kTileRows rows and for 3 and 4 blocks of
+// kTileRowsWide rows, and each context keeps the fastest for its mesh
+// (fv_autotune); FP64 is built unbounded for kTileRows rows.
+template <typename T, int MINB, int ROWS>
+__global__ void __launch_bounds__(ROWS, MINB) k_fv(const T *__restrict__ g, T *__restrict__ gn, int Np, int n,
                                                    const int *__restrict__ slice_ptr,
                                                    const int *__restrict__ slice_len,
                                                    const typename Ent<T>::type *__restrict__ ent, int max_tile_ent,
@@ -913,15 +914,15 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
     const E *se = reinterpret_cast<const E *>(fv_smem + 16);
     T *sh = reinterpret_cast<T *>(fv_smem + 16 + size_t(max_tile_ent) * sizeof(E));
     const int t = blockIdx.x;
-    const int e_begin = slice_ptr[4 * t];
+    const int e_begin = slice_ptr[(ROWS / 32) * t];
 #ifdef HLBM_DEBUG
-    const int n_ent = slice_ptr[4 * t + 4] - e_begin;  // entries staged for this tile
+    const int n_ent = slice_ptr[(ROWS / 32) * (t + 1)] - e_begin;  // entries staged for this tile
 #endif
     const int h0 = halo_ptr[t], hn = halo_ptr[t + 1] - h0, hs = (hn + 3) & ~3;
-    const int r0 = t * kFvThreads;
+    const int r0 = t * ROWS;
     if (threadIdx.x == 0) {
         const uint32_t bytes =
-            uint32_t(HLBM_CHK(slice_ptr[4 * t + 4] - e_begin, max_tile_ent + 1, kSiteEntry)) * uint32_t(sizeof(E));
+            uint32_t(HLBM_CHK(slice_ptr[(ROWS / 32) * (t + 1)] - e_begin, max_tile_ent + 1, kSiteEntry)) * uint32_t(sizeof(E));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_e) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_s) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -949,7 +950,7 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
     int hidx[kFvHaloRegs];
 #pragma unroll
     for (int j = 0; j < kFvHaloRegs; j++) {
-        const int h = kFvThreads + threadIdx.x + j * kFvThreads;
+        const int h = ROWS + threadIdx.x + j * ROWS;
         hidx[j] = h < hn ? HLBM_CHK(halo_nodes[h0 + h], Np, kSiteMesh) : 0;
     }
     // The tile that will start about when this one ends (pf_ahead = the
@@ -963,12 +964,12 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
         hpn = halo_ptr[tp + 1] - hp0;
 #pragma unroll
         for (int j = 0; j < kFvPrefetchRegs; j++) {
-            const int h = kFvThreads + threadIdx.x + j * kFvThreads;
+            const int h = ROWS + threadIdx.x + j * ROWS;
             pidx[j] = h < hpn ? HLBM_CHK(halo_nodes[hp0 + h], Np, kSiteMesh) : 0;
         }
         if (threadIdx.x == 0) {
-            const int ep = slice_ptr[4 * tp];
-            const uint32_t pbytes = uint32_t(slice_ptr[4 * tp + 4] - ep) * uint32_t(sizeof(E));
+            const int ep = slice_ptr[(ROWS / 32) * tp];
+            const uint32_t pbytes = uint32_t(slice_ptr[(ROWS / 32) * (tp + 1)] - ep) * uint32_t(sizeof(E));
             if (pbytes > 0)
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ent + ep), "r"(pbytes) : "memory");
         }
@@ -976,7 +977,7 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
     // wait until the previous sub-step (which wrote g) has completed
     asm volatile("griddepcontrol.wait;" ::: "memory");
     if (threadIdx.x == 0) {
-        constexpr uint32_t run = uint32_t(kFvThreads * sizeof(T));  // one plane's run of own rows
+        constexpr uint32_t run = uint32_t(ROWS * sizeof(T));  // one plane's run of own rows
         asm volatile("{\n\t.reg .b64 st;\n\t"
                      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar_s),
                      "r"(9u * run)
@@ -986,32 +987,32 @@ __global__ void __launch_bounds__(kFvThreads, MINB) k_fv(const T *__restrict__ g
         for (int i = 0; i < 9; i++)
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                              dst0 + uint32_t(i * hs) * uint32_t(sizeof(T))),
-                         "l"(g + size_t(i) * Np + HLBM_CHK(r0, Np - kFvThreads + 1, kSiteMesh)), "r"(run), "r"(bar_s)
+                         "l"(g + size_t(i) * Np + HLBM_CHK(r0, Np - ROWS + 1, kSiteMesh)), "r"(run), "r"(bar_s)
                          : "memory");
         if (tp < int(gridDim.x)) {
 #pragma unroll
             for (int i = 0; i < 9; i++)
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g + size_t(i) * Np + size_t(tp) * kFvThreads),
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g + size_t(i) * Np + size_t(tp) * ROWS),
                              "r"(run)
                              : "memory");
         }
     }
 #pragma unroll
     for (int j = 0; j < kFvHaloRegs; j++) {
-        const int h = kFvThreads + threadIdx.x + j * kFvThreads;
+        const int h = ROWS + threadIdx.x + j * ROWS;
         if (h < hn) {
 #pragma unroll
             for (int i = 0; i < 9; i++) sh[i * hs + h] = g[size_t(i) * Np + hidx[j]];
         }
     }
-    for (int h = kFvThreads * (1 + kFvHaloRegs) + threadIdx.x; h < hn; h += kFvThreads) {
+    for (int h = ROWS * (1 + kFvHaloRegs) + threadIdx.x; h < hn; h += ROWS) {
         const int node = HLBM_CHK(halo_nodes[h0 + h], Np, kSiteMesh);
 #pragma unroll
         for (int i = 0; i < 9; i++) sh[i * hs + h] = g[size_t(i) * Np + node];
     }
 #pragma unroll
     for (int j = 0; j < kFvPrefetchRegs; j++) {
-        if (kFvThreads + threadIdx.x + j * kFvThreads < hpn) {
+        if (ROWS + threadIdx.x + j * ROWS < hpn) {
 #pragma unroll
             for (int i = 0; i < 9; i++)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(g + size_t(i) * Np + pidx[j]) : "memory");
@@ -1065,7 +1066,7 @@ __global__ void __launch_bounds__(128) k_fv_lap(const T *__restrict__ g, T *__re
                                                  const int *__restrict__ slice_ptr, const int *__restrict__ slice_len,
                                                  const typename Ent<T>::type *__restrict__ ent,
                                                  const int *__restrict__ halo_ptr, const int *__restrict__ halo_nodes,
-                                                 T c_scale, int n_wall, int ring_start)
+                                                 int rows, T c_scale, int n_wall, int ring_start)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -1083,7 +1084,7 @@ __global__ void __launch_bounds__(128) k_fv_lap(const T *__restrict__ g, T *__re
         acc[i] = T(0);
     }
     const int sl = r >> 5, base = slice_ptr[sl] + (r & 31), len = slice_len[sl];
-    const int h0 = halo_ptr[r / kTileRows];
+    const int h0 = halo_ptr[r / rows];
     for (int e = 0; e < len; e++) {
         T a, b, cs;
         int col;
@@ -1108,8 +1109,8 @@ __global__ void __launch_bounds__(128) k_fv_bilap(const T *__restrict__ g, const
                                                    const int *__restrict__ slice_ptr, const int *__restrict__ slice_len,
                                                    const typename Ent<T>::type *__restrict__ ent,
                                                    const int *__restrict__ halo_ptr,
-                                                   const int *__restrict__ halo_nodes, T c_scale, T sigma, int n_wall,
-                                                   int ring_start)
+                                                   const int *__restrict__ halo_nodes, int rows, T c_scale, T sigma,
+                                                   int n_wall, int ring_start)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -1125,7 +1126,7 @@ __global__ void __launch_bounds__(128) k_fv_bilap(const T *__restrict__ g, const
         acc[i] = T(0);
     }
     const int sl = r >> 5, base = slice_ptr[sl] + (r & 31), len = slice_len[sl];
-    const int h0 = halo_ptr[r / kTileRows];
+    const int h0 = halo_ptr[r / rows];
     for (int e = 0; e < len; e++) {
         T a, b, cs;
         int col;
@@ -1481,6 +1482,7 @@ template <typename T, typename S> void launch_hole_interp(const DevCtx &C, cudaS
 template <typename T, typename S> void launch_fv(const DevCtx &C, int msub, cudaStream_t s)
 {
     const DevMesh &m = C.m;
+    const FvTiles &tl = m.tl;
     const DevLevel &l = C.lv[C.L - 1];
     T dt_tau = T(C.dt_u / C.tau_u);
     T scale5 = T(1.0 - 1.0 / (2.0 * l.tau));
@@ -1489,31 +1491,37 @@ template <typename T, typename S> void launch_fv(const DevCtx &C, int msub, cuda
     // programmatic dependent launch: the sub-step may begin while the previous
     // kernel on the stream drains (it waits for it before reading the state)
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(m.n_tiles));
-    cfg.blockDim = dim3(kFvThreads);
-    cfg.dynamicSmemBytes = m.smem_bytes;
+    cfg.gridDim = dim3(unsigned(tl.n_tiles));
+    cfg.blockDim = dim3(unsigned(tl.rows));
+    cfg.dynamicSmemBytes = tl.smem_bytes;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // variants: 1, 2 bounded for 7, 8 resident blocks per SM; 3, 4 the same
-    // with the L2 prefetch of a later tile (FP64: one unbounded kernel)
+    // variants: 1, 2 bounded for the lower and the higher block count per SM;
+    // 3, 4 the same with the L2 prefetch of a later tile (FP64: one
+    // unbounded kernel)
     const int v = m.fv_variant, bound = (v == 2 || v == 4) ? 2 : 1;
-    const int pf = v >= 3 ? m.pf_ahead[bound] : 0;
+    const int pf = v >= 3 ? tl.pf_ahead[bound] : 0;
     auto go = [&](auto kern) {
         cudaLaunchKernelEx(&cfg, kern, (const T *)m.g[m.gcur], (T *)m.g[m.gcur ^ 1], m.Np, m.n,
-                           (const int *)m.slice_ptr, (const int *)m.slice_len, (const typename Ent<T>::type *)m.ent,
-                           m.max_tile_ent, (const int *)m.halo_ptr, (const int *)m.halo_nodes,
+                           (const int *)m.slice_ptr, (const int *)m.slice_len, (const typename Ent<T>::type *)tl.ent,
+                           tl.max_tile_ent, (const int *)tl.halo_ptr, (const int *)tl.halo_nodes,
                            dt_tau, m.n_wall, m.ring_start, m.n_ring, (const T *)m.Q0,
                            (const T *)m.Q1, theta_next, scale5, star, C.flag, pf);
     };
     if constexpr (sizeof(T) == 4) {
-        if (bound == 2) go(k_fv<T, 8>);
-        else go(k_fv<T, 7>);
+        if (tl.rows == kTileRowsWide) {
+            if (bound == 2) go(k_fv<T, 4, kTileRowsWide>);
+            else go(k_fv<T, 3, kTileRowsWide>);
+        } else {
+            if (bound == 2) go(k_fv<T, 8, kTileRows>);
+            else go(k_fv<T, 7, kTileRows>);
+        }
     } else {
-        go(k_fv<T, 1>);
+        go(k_fv<T, 1, kTileRows>);
     }
 }
 
@@ -1524,13 +1532,14 @@ template <typename T, typename S> void launch_fv_filter(const DevCtx &C, cudaStr
     const T c_scale = T(C.tau_u / C.dt_u);
     const unsigned nb = cdiv(m.n, 128);
     using E = typename Ent<T>::type;
+    const FvTiles &tl = m.tl;
     k_fv_lap<T><<<nb, 128, 0, s>>>((const T *)m.g[m.gcur], (T *)m.lap, m.Np, m.n, (const int *)m.slice_ptr,
-                                   (const int *)m.slice_len, (const E *)m.ent, (const int *)m.halo_ptr,
-                                   (const int *)m.halo_nodes, c_scale, m.n_wall, m.ring_start);
+                                   (const int *)m.slice_len, (const E *)tl.ent, (const int *)tl.halo_ptr,
+                                   (const int *)tl.halo_nodes, tl.rows, c_scale, m.n_wall, m.ring_start);
     k_fv_bilap<T><<<nb, 128, 0, s>>>((const T *)m.g[m.gcur], (const T *)m.lap, (T *)m.g[m.gcur ^ 1], m.Np, m.n,
-                                     (const int *)m.slice_ptr, (const int *)m.slice_len, (const E *)m.ent,
-                                     (const int *)m.halo_ptr, (const int *)m.halo_nodes, c_scale, T(C.fv_filter),
-                                     m.n_wall, m.ring_start);
+                                     (const int *)m.slice_ptr, (const int *)m.slice_len, (const E *)tl.ent,
+                                     (const int *)tl.halo_ptr, (const int *)tl.halo_nodes, tl.rows, c_scale,
+                                     T(C.fv_filter), m.n_wall, m.ring_start);
 }
 
 void launch_widen(const float *a, double *b, size_t n, cudaStream_t s)
@@ -1540,15 +1549,20 @@ void launch_widen(const float *a, double *b, size_t n, cudaStream_t s)
     k_widen<<<nb, 256, 0, s>>>(a, b, n);
 }
 
-// Autotuner of the sub-step kernel (FP32): times each variant on this mesh
-// (reps launches reading the current state buffer and writing the other one,
-// which the next sub-step overwrites, so the state is unchanged) and returns
-// the fastest (1, 2: registers bounded for 7, 8 blocks per SM; 3, 4: the same
-// with the L2 prefetch of a later tile's entries and halo states); *us
-// receives the mean launch times.  All variants execute the same arithmetic.
-template <typename T, typename S> int fv_autotune(DevCtx &C, cudaStream_t s, double us[4])
+// Autotuner of the sub-step kernel (FP32): on each tiling built (kTileRows
+// rows per tile and, if the set-up built it, kTileRowsWide) times each
+// variant on this mesh (reps launches reading the current state buffer and
+// writing the other one, which the next sub-step overwrites, so the state is
+// unchanged): 1, 2 registers bounded for the lower and the higher block count
+// per SM (7, 8 blocks of 128 rows; 3, 4 blocks of 256), 3, 4 the same with the
+// L2 prefetch of a later tile's entries and halo states.  us[0..3] and
+// us[4..7] receive the mean launch times of the two tilings.  Leaves the
+// fastest in m.tl and m.fv_variant (the other tiling in m.tl_alt) and returns
+// it as 1..8.  Variants of one tiling execute the same arithmetic; the two
+// tilings order each row's entries for their own shared-memory banks.
+template <typename T, typename S> int fv_autotune(DevCtx &C, cudaStream_t s, double us[8])
 {
-    us[0] = us[1] = us[2] = us[3] = 0.0;
+    for (int k = 0; k < 8; k++) us[k] = 0.0;
     if constexpr (sizeof(T) != 4) {
         return 1;
     } else {
@@ -1559,62 +1573,88 @@ template <typename T, typename S> int fv_autotune(DevCtx &C, cudaStream_t s, dou
             return 1;
         }
         const int reps = 20;
-        const int keep = m.fv_variant;
-        const int nv = 4;
-        for (int v = 1; v <= nv; v++) {
-            m.fv_variant = v;
-            for (int k = 0; k < 3; k++) launch_fv<T, S>(C, 0, s);
-            cudaEventRecord(e0, s);
-            for (int k = 0; k < reps; k++) launch_fv<T, S>(C, 0, s);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            us[v - 1] = 1e3 * double(ms) / reps;
+        int best = 0;  // 0..7
+        for (int w = 0; w < 2; w++) {
+            if (w == 1) {
+                if (m.tl_alt.rows == 0) break;
+                std::swap(m.tl, m.tl_alt);
+            }
+            for (int v = 1; v <= 4; v++) {
+                m.fv_variant = v;
+                for (int k = 0; k < 3; k++) launch_fv<T, S>(C, 0, s);
+                cudaEventRecord(e0, s);
+                for (int k = 0; k < reps; k++) launch_fv<T, S>(C, 0, s);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                us[4 * w + v - 1] = 1e3 * double(ms) / reps;
+                if (us[4 * w + v - 1] < us[best]) best = 4 * w + v - 1;
+            }
         }
-        m.fv_variant = keep;
+        // m.tl is the tiling timed last: keep the best one there
+        const bool wide_last = m.tl.rows == kTileRowsWide;
+        const bool want_wide = best >= 4;
+        if (wide_last != want_wide && m.tl_alt.rows != 0) std::swap(m.tl, m.tl_alt);
+        m.fv_variant = best % 4 + 1;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        int best = 1;
-        for (int v = 2; v <= nv; v++)
-            if (us[v - 1] < us[best - 1]) best = v;
-        return best;
+        return best + 1;
     }
 }
 
-template <typename T, typename S> void configure_fv(size_t bytes)
+// Raises the dynamic shared-memory limit of the tiling's kernels to the
+// device's opt-in maximum when the tiling needs more than the default (a
+// per-kernel setting shared by every context of the process, so it is never
+// lowered).
+template <typename T, typename S> void configure_fv(const FvTiles &tl)
 {
-    if (bytes > 48 * 1024) {
-        if constexpr (sizeof(T) == 4) {
-            cudaFuncSetAttribute(k_fv<T, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-            cudaFuncSetAttribute(k_fv<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (tl.smem_bytes <= 48 * 1024) return;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (tl.rows == kTileRowsWide) {
+            cudaFuncSetAttribute(k_fv<T, 3, kTileRowsWide>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            cudaFuncSetAttribute(k_fv<T, 4, kTileRowsWide>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         } else {
-            cudaFuncSetAttribute(k_fv<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+            cudaFuncSetAttribute(k_fv<T, 7, kTileRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            cudaFuncSetAttribute(k_fv<T, 8, kTileRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         }
+    } else {
+        cudaFuncSetAttribute(k_fv<T, 1, kTileRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     }
 }
 
-template <typename T, typename S> void configure_fv_prefetch(DevMesh &m)
+template <typename T, typename S> void configure_fv_prefetch(FvTiles &tl)
 {
     int dev = 0, sms = 0;
-    for (int v = 0; v < 3; v++) m.pf_ahead[v] = 0;
+    for (int v = 0; v < 3; v++) tl.pf_ahead[v] = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return;
     }
     auto resident = [&](auto kern) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFvThreads, m.smem_bytes) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tl.rows, tl.smem_bytes) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
         return per_sm * sms;
     };
     if constexpr (sizeof(T) == 4) {
-        m.pf_ahead[1] = resident(k_fv<T, 7>);
-        m.pf_ahead[2] = resident(k_fv<T, 8>);
+        if (tl.rows == kTileRowsWide) {
+            tl.pf_ahead[1] = resident(k_fv<T, 3, kTileRowsWide>);
+            tl.pf_ahead[2] = resident(k_fv<T, 4, kTileRowsWide>);
+        } else {
+            tl.pf_ahead[1] = resident(k_fv<T, 7, kTileRows>);
+            tl.pf_ahead[2] = resident(k_fv<T, 8, kTileRows>);
+        }
     } else {
-        m.pf_ahead[1] = resident(k_fv<T, 1>);
+        tl.pf_ahead[1] = resident(k_fv<T, 1, kTileRows>);
     }
 }
 
@@ -1676,8 +1716,8 @@ void launch_fields(const DevCtx &C, int grid, double *rho, double *ux, double *u
 }
 
 #define HLBM_INSTANTIATE(T, S)                                                                                   \
-    template void configure_fv<T, S>(size_t);                                                                    \
-    template void configure_fv_prefetch<T, S>(DevMesh &);                                                        \
+    template void configure_fv<T, S>(const FvTiles &);                                                           \
+    template void configure_fv_prefetch<T, S>(FvTiles &);                                                        \
     template void launch_init_level<T, S>(const DevCtx &, int, unsigned long long, double, cudaStream_t);        \
     template void launch_collide<T, S>(const DevCtx &, int, cudaStream_t);                                       \
     template void launch_outer_bc<T, S>(const DevCtx &, cudaStream_t);                                           \

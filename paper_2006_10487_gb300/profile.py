@@ -41,11 +41,11 @@ def main():
     nbytes = s.info(key)
     out = {"workload": args.workload, "kernel": args.kernel, "precision": args.precision,
            "launch_ms": ms, "bytes_per_launch": nbytes, "gbs": nbytes / (ms * 1e-3) / 1e9,
-           "n_sub": s.info("n_sub"), "fv_variant": s.info("fv_variant")}
+           "n_sub": s.info("n_sub"), "fv_variant": s.info("fv_variant"), "tile_rows": s.info("fv_tile_rows")}
     if args.kernel == "fv":
         # launches of the kernel before the timed graph: the FP32 autotuner's
-        # 4 x (3 + 20), the warm-up steps' sub-steps, the warm-up graph
-        tune = 92 if args.precision != "fp64" else 0
+        # 3 + 20 per variant timed, the warm-up steps' sub-steps, the warm-up graph
+        tune = 23 * sum(1 for v in range(1, 9) if s.info(f"fv_tune_us{v}") > 0)
         out["ncu_skip"] = tune + args.warmup * 2 ** (case.n_levels - 1) * int(out["n_sub"]) + args.reps
     s.close()
     print(json.dumps(out))

@@ -17,9 +17,11 @@ from workloads import make_case
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-# (workload, angle of attack, precision, coarse steps, wall statistics)
-RUNS = [("hlbm_mini2", 3.0, "fp64", 3, True), ("hlbm_single", 0.0, "fp32", 2, False),
-        ("hlbm_small", 8.0, "fp16s", 3, True)]
+# (workload, angle of attack, precision, coarse steps, wall statistics,
+# finite-volume variant: 0 autotuned, 2 and 8 on 128- and 256-row tiles)
+RUNS = [("hlbm_mini2", 3.0, "fp64", 3, True, 0), ("hlbm_single", 0.0, "fp32", 2, False, 2),
+        ("hlbm_small", 8.0, "fp16s", 3, True, 0), ("hlbm_single", 0.0, "fp32", 2, False, 8),
+        ("hlbm_mini2", 3.0, "fp32", 3, True, 6)]
 
 CHILD = r"""
 import json, sys
@@ -28,9 +30,9 @@ import paper_2006_10487_gb300 as H
 from workloads import make_case
 runs, out = json.loads(sys.argv[1]), sys.argv[2]
 arrays, report = {}, {}
-for j, (name, aoa, prec, steps, ws) in enumerate(runs):
+for j, (name, aoa, prec, steps, ws, var) in enumerate(runs):
     case = make_case(name, aoa_deg=aoa)
-    s = H.Solver(case, precision=prec, wall_stats=ws)
+    s = H.Solver(case, precision=prec, wall_stats=ws, fv_variant=var)
     s.step(steps)
     for g in list(range(case.n_levels)) + [-1]:
         arrays[f"{j}_{g}"] = np.stack(s.fields(g))
@@ -66,9 +68,9 @@ def test_parity_workloads_meet_no_bounds_violation(H, tmp_path):
     for j, (violations, sites) in report.items():
         assert violations == 0 and sites == 0, (RUNS[int(j)], violations, sites)
     dbg = np.load(out)
-    for j, (name, aoa, prec, steps, ws) in enumerate(RUNS):
+    for j, (name, aoa, prec, steps, ws, var) in enumerate(RUNS):
         case = make_case(name, aoa_deg=aoa)
-        s = H.Solver(case, precision=prec, wall_stats=ws)
+        s = H.Solver(case, precision=prec, wall_stats=ws, fv_variant=var)
         s.step(steps)
         assert s.info("bounds_violations") == -1  # the release library has no checks
         tol = 1e-12 if prec == "fp64" else 1e-5

@@ -57,13 +57,14 @@ def _create(H, case, allocator):
 def test_allocator_failure_is_reported_and_nothing_leaks(H):
     """A refusal at the first, a middle or the last device allocation of
     hlbm_create gives HLBM_ENOMEM and no context, and every block the
-    callback did hand out is given back."""
+    callback did hand out is given back (hlbm_create itself gives back the
+    tables of the finite-volume tiling its autotuner did not keep)."""
     case = make_case("hlbm_mini2")
     full = CountingAllocator(H)
     rc, ctx = _create(H, case, full)
     assert rc == H.HLBM_OK and ctx.value
     n = full.calls
-    assert n > 3 and len(full.live) == n
+    assert n > 3 and 0 < len(full.live) <= n
     H.lib().hlbm_destroy(ctx)
     assert not full.live
     for grant in (0, n // 2, n - 1):

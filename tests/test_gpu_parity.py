@@ -354,29 +354,65 @@ def test_wall_stats_reassemble_the_mean_forces(H):
 
 
 def test_fv_register_bounds_agree_bitwise_and_the_autotuner_reports(H):
-    """The four variants of the FP32 finite-volume kernel (registers bounded
-    for 7 and 8 resident blocks per SM, each with and without the L2 prefetch
-    of a later tile) run the same arithmetic: identical results, on a mesh of
-    a few tiles and on the 200 k-node mesh; the default (autotuned) context
-    reports its choice and the timings."""
+    """The variants of the FP32 finite-volume kernel: on each tiling (128- and
+    256-row tiles), registers bounded for the lower and the higher block count
+    per SM, each with and without the L2 prefetch of a later tile, run the
+    same arithmetic: identical results within a tiling, on a mesh of a few
+    tiles and on the 200 k-node mesh.  The two tilings order each row's
+    entries for their own shared-memory banks, so across tilings the fields
+    agree to FP32 rounding.  The default (autotuned) context reports its
+    choice and the timings of all eight."""
     for name, steps in (("hlbm_mini2", 9), ("hlbm_single", 1)):
         case = make_case(name, aoa_deg=3.0)
-        runs = [H.Solver(case, precision="fp32", fv_variant=v) for v in (1, 2, 3, 4)]
-        for v, s in zip((1, 2, 3, 4), runs):
-            assert s.info("fv_variant") == v
-            s.step(steps)
-        ref = runs[0]
-        ref_cd = ref.forces()[0]
-        for s in runs[1:]:
-            for g in grids(case):
-                for x, y in zip(ref.fields(g), s.fields(g)):
-                    assert np.array_equal(x, y, equal_nan=True), (name, g)
-            assert np.array_equal(ref_cd, s.forces()[0])
-        for s in runs:
-            s.close()
+        groups = []
+        for vs in ((1, 2, 3, 4), (5, 6, 7, 8)):
+            runs = [H.Solver(case, precision="fp32", fv_variant=v) for v in vs]
+            for v, s in zip(vs, runs):
+                assert s.info("fv_variant") == v
+                assert s.info("fv_tile_rows") == (128 if v <= 4 else 256)
+                s.step(steps)
+            ref = runs[0]
+            ref_cd = ref.forces()[0]
+            for s in runs[1:]:
+                for g in grids(case):
+                    for x, y in zip(ref.fields(g), s.fields(g)):
+                        assert np.array_equal(x, y, equal_nan=True), (name, g)
+                assert np.array_equal(ref_cd, s.forces()[0])
+            groups.append((ref, ref_cd))
+            for s in runs[1:]:
+                s.close()
+        (a, cda), (b, cdb) = groups
+        for g in grids(case):
+            (_, ax, ay), (_, bx, by) = a.fields(g), b.fields(g)
+            assert rel_velocity_diff(ax, ay, bx, by) <= 1e-5, (name, g)
+        assert np.abs(cda - cdb).max() <= 1e-5 * np.abs(cdb).max()
+        a.close()
+        b.close()
     t = H.Solver(make_case("hlbm_single"), precision="fp32")
-    assert t.info("fv_variant") in (1, 2, 3, 4)
-    assert all(t.info(f"fv_tune_us{v}") > 0 for v in (1, 2, 3, 4))
+    assert t.info("fv_variant") in range(1, 9)
+    assert t.info("fv_tile_rows") == (128 if t.info("fv_variant") <= 4 else 256)
+    assert all(t.info(f"fv_tune_us{v}") > 0 for v in range(1, 9))
+
+
+def test_wide_tiling_fp32_against_fp64(H):
+    """The 256-row tiling of the FP32 sub-step against the FP64 path on the
+    one-level airfoil case: velocity relative L2 within 1e-5 after 100
+    coarse steps, mean C_D and C_L within 1e-3."""
+    case = make_case("hlbm_small", aoa_deg=8.0)
+    a = H.Solver(case, precision="fp32", fv_variant=6)
+    b = H.Solver(case, precision="fp64")
+    assert a.info("fv_tile_rows") == 256 and b.info("fv_tile_rows") == 128
+    a.step(100)
+    b.step(100)
+    for g in grids(case):
+        _, ux, uy = a.fields(g)
+        _, vx, vy = b.fields(g)
+        m = np.isfinite(vx)
+        err = math.sqrt(((ux[m] - vx[m]) ** 2 + (uy[m] - vy[m]) ** 2).sum() / (vx[m] ** 2 + vy[m] ** 2).sum())
+        assert err <= 1e-5, f"grid {g}: velocity relative L2 {err:.2e}"
+    (cd, cl), (cd64, cl64) = a.forces(), b.forces()
+    assert abs(cd.mean() - cd64.mean()) <= 1e-3 * abs(cd64.mean())
+    assert abs(cl.mean() - cl64.mean()) <= 1e-3 * abs(cl64.mean())
 
 
 @pytest.mark.parametrize("name", ["hlbm_small", "hlbm_mini2"])

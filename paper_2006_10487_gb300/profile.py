@@ -1,7 +1,7 @@
 """Runs one kernel of the step on a named workload, for profilers.
 
 python -m paper_2006_10487_gb300.profile --workload hlbm_large_fv --kernel fv
-    [--precision fp32] [--warmup 2] [--reps 20]
+    [--precision fp32] [--warmup 2] [--reps 20] [--fv-variant N]
 
 Creates the solver (which runs its block-shape autotuner), advances `warmup`
 coarse steps, then launches `kernel` ("fv" for the Eq. 3 sub-step, "collideL"
@@ -29,11 +29,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16s"])
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--fv-variant", type=int, default=0, help="finite-volume kernel variant (0: autotuned)")
     args = ap.parse_args()
     import paper_2006_10487_gb300 as H
     from workloads import make_case
     case = make_case(args.workload)
-    s = H.Solver(case, precision=args.precision, use_graphs=True)
+    s = H.Solver(case, precision=args.precision, use_graphs=True, fv_variant=args.fv_variant)
     s.step(args.warmup)
     s.sync()
     ms = s.time_kernel(args.kernel, args.reps)

@@ -433,6 +433,7 @@ def main():
         torch.cuda.synchronize()
         ms4 = e0.elapsed_time(e1) / k4
         var4 = s4.info("fv_variant")
+        rows4 = s4.info("fv_tile_rows")
         fv4 = s4.time_kernel("fv", 230)
         c04 = s4.time_kernel("collide0", 10)
         fvb4 = FV_BYTES[args.precision] * big.n_nodes
@@ -451,7 +452,7 @@ def main():
                          "frac": fvb4 / (fv4 * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
                          "traffic": _traffic("k_fv_large", args.precision), "bytes_per_unit": FV_BYTES[args.precision],
                          "units_per_launch": big.n_nodes, "bytes_per_launch": fvb4, "launch_ms": fv4,
-                         "autotuner_variant": var4, "tile_rows": s4.info("fv_tile_rows")},
+                         "autotuner_variant": var4, "tile_rows": rows4},
             "collide_level0": {"achieved": c0b / (c04 * 1e-3) / 1e9, "unit": "GB/s",
                                "frac": c0b / (c04 * 1e-3) / 1e9 / peak, "bytes_per_launch": c0b,
                                "launch_ms": c04, "nodes": n0},

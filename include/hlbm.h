@@ -91,8 +91,10 @@ typedef struct {
  * wall_stats: 1 adds to every coarse step the accumulation of the wall
  * coefficients read by hlbm_wall_stats (one small kernel over the wall
  * nodes); 0 leaves the step as it is.  fv_variant: variant of the FP32
- * finite-volume kernel: 0 times all eight on this mesh at create and keeps
- * the fastest (the autotuner); 1-4 on tiles of 128 rows: 1 registers bounded
+ * finite-volume kernel: 0 times them on this mesh at create and keeps the
+ * fastest (the autotuner: the four on 128-row tiles and, where those tiles
+ * need more than two waves of 8 resident blocks per SM, the four on 256-row
+ * tiles); 1-4 on tiles of 128 rows: 1 registers bounded
  * for 7 resident blocks per SM, 2 for 8, 3 and 4 the same with an L2
  * prefetch, by every block, of the entries and halo states of the tile that
  * starts about when it ends; 5-8 the same four on tiles of 256 rows (3 and 4

@@ -651,9 +651,17 @@ template <typename T> void upload_mesh(hlbm_ctx *c)
     sptr[M.n_slices] = int(n_ent);
     build_tiles<T>(c, odp, od, sptr, slen, kTileRows, M.tl);
     if (!M.tl.rows) throw CudaError{"mesh tiles touch too many nodes for shared memory"};
-    // FP32: also the wide tiling, for the autotuner to time
-    if (std::is_same<T, float>::value && c->fv_variant_opt != 1 && c->fv_variant_opt != 2 &&
-        c->fv_variant_opt != 3 && c->fv_variant_opt != 4)
+    // FP32: also the wide tiling, when a variant of it is asked for or, for
+    // the autotuner, when the 128-row tiles need more than two waves of
+    // resident blocks (8 per SM): only there did the wide tiles win (the
+    // 1.5 M-node mesh, ~10 waves; not the 200 k mesh, 1.3 waves)
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 0;
+    }
+    const bool many_waves = sms > 0 && M.tl.n_tiles > 2 * 8 * sms;
+    if (std::is_same<T, float>::value && (c->fv_variant_opt > 4 || (c->fv_variant_opt == 0 && many_waves)))
         build_tiles<T>(c, odp, od, sptr, slen, kTileRowsWide, M.tl_alt);
     M.slice_ptr = upload(c, sptr);
     M.slice_len = upload(c, slen);

@@ -388,10 +388,18 @@ def test_fv_register_bounds_agree_bitwise_and_the_autotuner_reports(H):
         assert np.abs(cda - cdb).max() <= 1e-5 * np.abs(cdb).max()
         a.close()
         b.close()
+    # the autotuner times the 256-row tiles only where the 128-row tiles need
+    # more than two waves of resident blocks: not on the 200 k-node mesh, on
+    # the 1.5 M-node one
     t = H.Solver(make_case("hlbm_single"), precision="fp32")
-    assert t.info("fv_variant") in range(1, 9)
-    assert t.info("fv_tile_rows") == (128 if t.info("fv_variant") <= 4 else 256)
+    assert t.info("fv_variant") in range(1, 5) and t.info("fv_tile_rows") == 128
+    assert all(t.info(f"fv_tune_us{v}") > 0 for v in range(1, 5))
+    assert all(t.info(f"fv_tune_us{v}") == 0 for v in range(5, 9))
+    t.close()
+    t = H.Solver(make_case("hlbm_large_fv"), precision="fp32")
     assert all(t.info(f"fv_tune_us{v}") > 0 for v in range(1, 9))
+    assert t.info("fv_tile_rows") == (128 if t.info("fv_variant") <= 4 else 256)
+    t.close()
 
 
 def test_wide_tiling_fp32_against_fp64(H):

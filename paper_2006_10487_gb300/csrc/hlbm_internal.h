@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <new>
 #include <string>
 #include <thread>
@@ -74,6 +75,13 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
 // splitmix64-based initial density deviate in [-1, 1) (host side).
 double init_deviate(uint64_t seed, uint64_t grid, uint64_t node);
 
+// Runs task(j) for j in [0, n_tasks) on the process's host worker threads
+// (up to 15, started on first use and kept) and the calling thread, and
+// returns when all have run; false if a task threw (every task still runs).
+// Calls from different threads take turns; a call made from inside a task, or
+// in a process forked after the workers started, runs its tasks inline.
+bool run_tasks(int n_tasks, const std::function<void(int)> &task);
+
 // Runs f(begin, end) over [0, n) in contiguous chunks of at least `grain`
 // items on up to 16 host threads (inline when there is one chunk).  Chunks
 // write disjoint outputs, so results do not depend on the thread count.  A
@@ -86,25 +94,8 @@ template <typename F> void parallel_for(int n, F f, int grain = 2048)
         f(0, n);
         return;
     }
-    std::atomic<bool> failed{false};
-    auto run = [&](int j) {
-        try {
-            f(int(long(n) * j / nt), int(long(n) * (j + 1) / nt));
-        } catch (...) {
-            failed = true;
-        }
-    };
-    std::vector<std::thread> th;
-    for (int j = 1; j < nt; j++) {
-        try {
-            th.emplace_back(run, j);
-        } catch (...) {
-            run(j);  // no thread available: this chunk runs here
-        }
-    }
-    run(0);
-    for (auto &t : th) t.join();
-    if (failed) throw std::bad_alloc();
+    const bool ok = run_tasks(nt, [&](int j) { f(int(long(n) * j / nt), int(long(n) * (j + 1) / nt)); });
+    if (!ok) throw std::bad_alloc();
 }
 
 // Message returned by hlbm_last_error(NULL) on this thread.

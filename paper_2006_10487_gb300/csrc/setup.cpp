@@ -1,7 +1,13 @@
 // Host set-up of the HLBM step: geometry, Eq. 3 finite-volume operators,
 // Eq. 8 / Eq. 9 interpolation stencils, refinement maps and the sub-step
 // count.  All in FP64; the device tables are converted from this plan.
+#include <unistd.h>
+
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstring>
 
@@ -57,6 +63,105 @@ bool gauss_jordan(int n, double *A, double *b)
 }
 
 }  // namespace
+
+namespace {
+// The host worker threads of run_tasks: one job at a time; a job hands out
+// task indices through an atomic counter to the workers and the caller.
+struct Workers {
+    std::mutex run_mx;                 // one job at a time
+    std::mutex mx;
+    std::condition_variable wake, done;
+    std::vector<std::thread> th;
+    const std::function<void(int)> *task = nullptr;
+    int n_tasks = 0;
+    std::atomic<int> next{0};
+    int busy = 0;                      // workers still inside the current job
+    uint64_t job = 0;                  // job generation
+    std::atomic<bool> failed{false};
+    pid_t pid = 0;
+};
+thread_local bool t_in_task = false;
+
+void drain(Workers &w)
+{
+    for (int j; (j = w.next.fetch_add(1)) < w.n_tasks;) {
+        try {
+            (*w.task)(j);
+        } catch (...) {
+            w.failed = true;
+        }
+    }
+}
+
+Workers *workers()
+{
+    static std::mutex init_mx;
+    static Workers *w = nullptr;
+    std::lock_guard<std::mutex> lk(init_mx);
+    if (w && w->pid == getpid()) return w;
+    // first use, or a forked child (whose copy has no threads): a new set,
+    // the old one left as it is
+    Workers *nw = new Workers();
+    nw->pid = getpid();
+    const int hw = int(std::max(1u, std::thread::hardware_concurrency()));
+    for (int k = 1; k < std::min(hw, 16); k++) {
+        try {
+            nw->th.emplace_back([nw]() {
+                t_in_task = true;
+                uint64_t seen = 0;
+                for (;;) {
+                    {
+                        std::unique_lock<std::mutex> lk(nw->mx);
+                        nw->wake.wait(lk, [&] { return nw->job != seen; });
+                        seen = nw->job;
+                    }
+                    drain(*nw);
+                    std::lock_guard<std::mutex> lk(nw->mx);
+                    if (--nw->busy == 0) nw->done.notify_all();
+                }
+            });
+            nw->th.back().detach();
+        } catch (...) {
+            break;  // fewer workers
+        }
+    }
+    w = nw;
+    return w;
+}
+}  // namespace
+
+bool run_tasks(int n_tasks, const std::function<void(int)> &task)
+{
+    Workers *w = t_in_task ? nullptr : workers();
+    if (!w || w->th.empty()) {
+        bool ok = true;
+        for (int j = 0; j < n_tasks; j++) {
+            try {
+                task(j);
+            } catch (...) {
+                ok = false;
+            }
+        }
+        return ok;
+    }
+    std::lock_guard<std::mutex> run_lk(w->run_mx);
+    {
+        std::lock_guard<std::mutex> lk(w->mx);
+        w->task = &task;
+        w->n_tasks = n_tasks;
+        w->next = 0;
+        w->failed = false;
+        w->busy = int(w->th.size());
+        w->job++;
+    }
+    w->wake.notify_all();
+    t_in_task = true;
+    drain(*w);
+    t_in_task = false;
+    std::unique_lock<std::mutex> lk(w->mx);
+    w->done.wait(lk, [&] { return w->busy == 0; });
+    return !w->failed;
+}
 
 double init_deviate(uint64_t seed, uint64_t grid, uint64_t node)
 {
@@ -428,22 +533,32 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     std::vector<uint8_t> inhole(size_t(F.nx) * F.ny, 0);
     F.hx0.assign(F.ny, 0);
     F.hx1.assign(F.ny, 0);
-    for (int y = 0; y < F.ny; y++) {
-        int first = -1, last = -2;
-        for (int x = 0; x < F.nx; x++) {
-            double dx = double(x) - px, dy = double(y) - py;
-            double Xr = (ca * dx - sa * dy) + px - H[0];
-            double Yr = (sa * dx + ca * dy) + py - H[1];
-            double qx = Xr / H[2], qy = Yr / H[3];
-            if (qx * qx + qy * qy < 1.0) {
-                if (x == 0 || y == 0 || x == F.nx - 1 || y == F.ny - 1) { err = "hole reaches a level boundary"; return HLBM_EINVAL; }
-                if (first < 0) first = x;
-                else if (x != last + 1) { err = "hole row is not contiguous"; return HLBM_EINVAL; }
-                last = x;
-                inhole[size_t(y) * F.nx + x] = 1;
+    {
+        // rows in parallel; the first failing row (in row order) names the error
+        std::vector<uint8_t> row_err(F.ny, 0);  // 1: reaches a boundary, 2: not contiguous
+        parallel_for(F.ny, [&](int y0, int y1) {
+            for (int y = y0; y < y1; y++) {
+                int first = -1, last = -2;
+                for (int x = 0; x < F.nx && !row_err[y]; x++) {
+                    double dx = double(x) - px, dy = double(y) - py;
+                    double Xr = (ca * dx - sa * dy) + px - H[0];
+                    double Yr = (sa * dx + ca * dy) + py - H[1];
+                    double qx = Xr / H[2], qy = Yr / H[3];
+                    if (qx * qx + qy * qy < 1.0) {
+                        if (x == 0 || y == 0 || x == F.nx - 1 || y == F.ny - 1) { row_err[y] = 1; break; }
+                        if (first < 0) first = x;
+                        else if (x != last + 1) { row_err[y] = 2; break; }
+                        last = x;
+                        inhole[size_t(y) * F.nx + x] = 1;
+                    }
+                }
+                if (!row_err[y] && first >= 0) { F.hx0[y] = first; F.hx1[y] = last + 1; }
             }
+        }, 16);
+        for (int y = 0; y < F.ny; y++) {
+            if (row_err[y] == 1) { err = "hole reaches a level boundary"; return HLBM_EINVAL; }
+            if (row_err[y] == 2) { err = "hole row is not contiguous"; return HLBM_EINVAL; }
         }
-        if (first >= 0) { F.hx0[y] = first; F.hx1[y] = last + 1; }
     }
     // coarser levels: a covered node whose coincident finer node is not computed
     // is not computed either (per row again one interval)
@@ -463,13 +578,19 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
     }
     // structured interpolation nodes: hole nodes with a computed D2Q9 neighbour
     static const int ex[8] = {1, 0, -1, 0, 1, -1, -1, 1}, ey[8] = {0, 1, 0, -1, 1, 1, -1, -1};
-    for (int y = 1; y < F.ny - 1; y++)
-        for (int x = 1; x < F.nx - 1; x++) {
-            if (!inhole[size_t(y) * F.nx + x]) continue;
-            bool near = false;
-            for (int d = 0; d < 8; d++) near |= !inhole[size_t(y + ey[d]) * F.nx + x + ex[d]];
-            if (near) P.is_node.push_back(y * F.nx + x);
-        }
+    {
+        std::vector<std::vector<int>> per_row(F.ny);
+        parallel_for(F.ny - 2, [&](int j0, int j1) {
+            for (int y = j0 + 1; y < j1 + 1; y++)
+                for (int x = std::max(1, F.hx0[y]); x < std::min(F.nx - 1, F.hx1[y]); x++) {
+                    if (!inhole[size_t(y) * F.nx + x]) continue;
+                    bool near = false;
+                    for (int d = 0; d < 8; d++) near |= !inhole[size_t(y + ey[d]) * F.nx + x + ex[d]];
+                    if (near) per_row[y].push_back(y * F.nx + x);
+                }
+        }, 16);
+        for (int y = 1; y < F.ny - 1; y++) P.is_node.insert(P.is_node.end(), per_row[y].begin(), per_row[y].end());
+    }
 
     // ---- Eq. 8 stencils: containing triangle (lowest index when on an edge)
     // plus the far vertex across each of its three edges (Section 3, Fig. 1)
@@ -492,18 +613,33 @@ int build_plan(const hlbm_level *lv, int n_levels, const hlbm_mesh *m, double Re
             ni0 = std::min(ni0, i); ni1 = std::max(ni1, i); nj0 = std::min(nj0, j); nj1 = std::max(nj1, j);
         }
     }
-    for (int t = 0; t < P.ntri; t++) {
-        double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
-        for (int a = 0; a < 3; a++) {
-            V2 q = X(P.tri[3 * t + a]);
-            x0 = std::min(x0, q.x); x1 = std::max(x1, q.x); y0 = std::min(y0, q.y); y1 = std::max(y1, q.y);
-        }
-        int i0 = int((x0 - bx0) / cell), i1 = int((x1 - bx0) / cell);
-        int j0 = int((y0 - by0) / cell), j1 = int((y1 - by0) / cell);
-        i0 = std::max(i0, ni0); i1 = std::min(i1, ni1); j0 = std::max(j0, nj0); j1 = std::min(j1, nj1);
-        for (int j = j0; j <= j1; j++)
-            for (int i = i0; i <= i1; i++)
-                if (need[size_t(j) * gw + i]) bucket[size_t(j) * gw + i].push_back(t);
+    {
+        // triangle chunks in parallel, each listing (bucket, triangle) in
+        // triangle order; appended chunk by chunk, so every bucket lists its
+        // triangles in ascending order
+        std::mutex part_mx;
+        std::vector<std::pair<int, std::vector<std::pair<size_t, int>>>> parts;
+        parallel_for(P.ntri, [&](int t0, int t1) {
+            std::vector<std::pair<size_t, int>> mine;
+            for (int t = t0; t < t1; t++) {
+                double x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
+                for (int a = 0; a < 3; a++) {
+                    V2 q = X(P.tri[3 * t + a]);
+                    x0 = std::min(x0, q.x); x1 = std::max(x1, q.x); y0 = std::min(y0, q.y); y1 = std::max(y1, q.y);
+                }
+                int i0 = int((x0 - bx0) / cell), i1 = int((x1 - bx0) / cell);
+                int j0 = int((y0 - by0) / cell), j1 = int((y1 - by0) / cell);
+                i0 = std::max(i0, ni0); i1 = std::min(i1, ni1); j0 = std::max(j0, nj0); j1 = std::min(j1, nj1);
+                for (int j = j0; j <= j1; j++)
+                    for (int i = i0; i <= i1; i++)
+                        if (need[size_t(j) * gw + i]) mine.push_back({size_t(j) * gw + i, t});
+            }
+            std::lock_guard<std::mutex> lk(part_mx);
+            parts.push_back({t0, std::move(mine)});
+        });
+        std::sort(parts.begin(), parts.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
+        for (const auto &pt : parts)
+            for (const auto &bt : pt.second) bucket[bt.first].push_back(bt.second);
     }
     const size_t nis = P.is_node.size();
     P.is_don.resize(6 * nis);

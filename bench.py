@@ -375,8 +375,8 @@ def main():
             "dJ_daoa_per_deg": da5,
             "dJ_dthickness_modes": [float((gx5 * f).sum()) for f in thickness_modes(case)]}
         del gg5, gc5, gx5
-        # ---- adjoint of whole coarse steps, single-level configuration
-        # (config 1 lattice and mesh, FP64): 100 steps, J = mean C_D
+        # ---- adjoint of whole coarse steps, single-level layout (the 200 x 100
+        # lattice with the 5 200-node mesh, FP64): 100 steps, J = mean C_D
         small = make_case("hlbm_small", aoa_deg=4.0)
         s6 = H.Solver(small, precision="fp64", use_graphs=True)
         s6.step(2)
@@ -398,8 +398,8 @@ def main():
             "grad_norm_lattice": float((gl6 ** 2).sum() ** 0.5), "grad_norm_mesh": float((gm6 ** 2).sum() ** 0.5),
             "dJ_daoa_per_deg": da6, "dJ_dthickness_modes": [float((gx6 * f).sum()) for f in thickness_modes(small)]}
         del gl6, gm6, gx6
-        # the same on the refined three-level layout (config 2: 2048 x 1024 plus
-        # two nested boxes, 200 704-node mesh), 10 coarse steps
+        # the same on the refined three-level layout (2048 x 1024 plus two
+        # nested boxes, 200 704-node mesh), 10 coarse steps
         s7 = H.Solver(case, precision="fp64", use_graphs=True)
         s7.step(2)
         s7.sync()

@@ -111,8 +111,8 @@ def test_fp64_with_the_odd_even_filter_matches_oracle(H, orc, name, steps, aoa):
 
 
 @pytest.mark.slow
-def test_config1_full_run_fp64(H, orc):
-    """Config 1 over its whole nominal run (2000 steps of the 200 x 100 lattice
+def test_small_airfoil_full_run_fp64(H, orc):
+    """The one-level airfoil case over its whole nominal run (2000 steps of the 200 x 100 lattice
     with the 5 200-node mesh, Re 500, zero incidence): the FP64 force series
     within 1e-10 of the oracle's (OpenMP build, bitwise the serial one) at every
     step, and every field within 1e-10 at the end."""
@@ -161,7 +161,7 @@ def test_single_config_one_coarse_step_fp64(H, orc):
 
 
 @pytest.mark.slow
-def test_single_config_100_finest_steps_fp64(H, orc):
+def test_refined_airfoil_100_finest_steps_fp64(H, orc):
     """The benchmarked configuration (2048 x 1024 + two nested boxes, 200 704-node
     mesh) over 25 coarse steps = 100 steps of the finest lattice (3 100
     finite-volume sub-steps): every grid within 1e-12 of the oracle (OpenMP

@@ -3,7 +3,7 @@ step give, case by case, bitwise the results of stepping each case alone."""
 import numpy as np
 import pytest
 
-from workloads import make_case
+from workloads import ensemble_case, make_case
 
 pytestmark = pytest.mark.gpu
 
@@ -80,6 +80,34 @@ def test_batched_fp64_cases_match_the_oracle(H, orc):
             assert np.hypot(ax[m] - bx[m], ay[m] - by[m]).max() <= 1e-12 * np.hypot(bx[m], by[m]).max()
         (cd, cl), (ocd, ocl) = s.forces(), o.forces()
         assert len(cd) == 30
+        assert np.abs(cd - ocd).max() <= 1e-12 * np.abs(ocd).max()
+        assert np.abs(cl - ocl).max() <= 1e-12 * max(np.abs(ocl).max(), np.abs(ocd).max())
+    batch.close()
+
+
+def test_ensemble_cases_at_full_size_match_the_oracle(H, orc):
+    """Two members of the batched ensemble at their full sizes, the largest
+    (Re 5000 at 15 degrees: 2048 x 1024 lattice, 300 032-node mesh, 93
+    sub-steps per step) and the smallest (Re 500 at 0 degrees: 512 x 256, 20 480
+    nodes), FP64, advanced only by batched graph launches: every field within
+    1e-12 of its scale and the force series within 1e-12 of the oracle's
+    (OpenMP build) after two coarse steps."""
+    cases = [ensemble_case(5000.0, 15.0), ensemble_case(500.0, 0.0)]
+    solvers = [H.Solver(c, precision="fp64") for c in cases]
+    batch = H.Batch(solvers)
+    batch.step(2)
+    batch.sync()
+    for case, s in zip(cases, solvers):
+        o = orc.Oracle(case, openmp=True)
+        o.step(2)
+        for g in grids(case):
+            (ar, ax, ay), (br, bx, by) = s.fields(g), o.fields(g)
+            m = np.isfinite(br)
+            assert np.array_equal(np.isfinite(ar), m)
+            assert np.abs(ar[m] - br[m]).max() <= 1e-12 * np.abs(br[m]).max(), (case.name, g)
+            assert np.hypot(ax[m] - bx[m], ay[m] - by[m]).max() <= 1e-12 * np.hypot(bx[m], by[m]).max(), (case.name, g)
+        (cd, cl), (ocd, ocl) = s.forces(), o.forces()
+        assert len(cd) == 2
         assert np.abs(cd - ocd).max() <= 1e-12 * np.abs(ocd).max()
         assert np.abs(cl - ocl).max() <= 1e-12 * max(np.abs(ocl).max(), np.abs(ocd).max())
     batch.close()

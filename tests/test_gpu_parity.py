@@ -277,6 +277,26 @@ def test_fp16s_single_config_one_coarse_step(H, orc):
         assert err <= 2e-4, f"grid {g}: velocity relative L2 {err:.2e}"
 
 
+@pytest.mark.slow
+def test_large_re_one_coarse_step_fp64_matches_oracle(H, orc):
+    """The largest configuration at its full size (8192 x 4096 coarse level,
+    three nested boxes of 4097 x 2049, the 1.5 M-node mesh, Re 10^4; 8 finest
+    steps and 368 finite-volume sub-steps in one coarse step), FP64 against
+    the oracle (OpenMP build): every grid within FP64_TOL and the force
+    sample within 1e-12 of the oracle's."""
+    case = make_case("hlbm_large")
+    sol = H.Solver(case, precision="fp64")
+    sol.step(1)
+    sim = orc.Oracle(case, openmp=True)
+    sim.step(1)
+    compare_fields(sol, sim, case, FP64_TOL, "hlbm_large fp64")
+    (cd, cl), (ocd, ocl) = sol.forces(), sim.forces()
+    assert len(cd) == 1
+    assert abs(cd[0] - ocd[0]) <= 1e-12 * abs(ocd[0])
+    assert abs(cl[0] - ocl[0]) <= 1e-12 * max(abs(ocl[0]), abs(ocd[0]))
+    sol.close()
+
+
 def test_large_re_fp32_and_fp16s_against_fp64(H):
     """Large-Re configuration (8192x4096 coarse level, three nested boxes,
     1.5 M-node mesh, Re 10^4): FP32 and FP16S against the FP64 GPU path on the

@@ -504,6 +504,29 @@ def test_graphs_and_plain_launches_agree_bitwise(H, filt):
     assert np.array_equal(a.forces()[0], b.forces()[0])
 
 
+def test_step_graphs_with_health_checks_and_wall_stats_agree_bitwise(H):
+    """FP32 on the refined airfoil case with wall statistics: graphs of one
+    and two coarse steps (with the finite-volume branch and the forces kept on
+    it inside a pair), cut where a health check falls (every 3 steps) and at
+    odd call lengths, against plain launches of every step: the same fields,
+    forces and wall sums, bit for bit."""
+    case = make_case("hlbm_mini3", aoa_deg=6.0)
+    a = H.Solver(case, precision="fp32", use_graphs=True, check_every=3, wall_stats=True)
+    b = H.Solver(case, precision="fp32", use_graphs=False, wall_stats=True)
+    a.step(4)
+    a.step(7)
+    b.step(11)
+    for g in grids(case):
+        for x, y in zip(a.fields(g), b.fields(g)):
+            assert np.array_equal(x, y, equal_nan=True), g
+    (ca, la), (cb, lb) = a.forces(), b.forces()
+    assert len(ca) == 11 and np.array_equal(ca, cb) and np.array_equal(la, lb)
+    (wa, na), (wb, nb) = a.wall_stats(), b.wall_stats()
+    assert na == nb == 11 and np.array_equal(wa, wb)
+    a.close()
+    b.close()
+
+
 def test_runs_are_deterministic(H):
     case = make_case("hlbm_small")
     res = []

@@ -281,6 +281,70 @@ def test_fv_viscosity_on_periodic_triangles(orc):
     assert 3.5 < e8 / e16 < 4.5
 
 
+def _tg_modes(k, x, y):
+    """Velocity shape of the Taylor-Green vortex u = U (-cos kx sin ky, sin kx cos ky)."""
+    return -np.cos(k * x) * np.sin(k * y), np.sin(k * x) * np.cos(k * y)
+
+
+def _tg_amplitude(ux, uy, pu, pv):
+    return (ux * pu + uy * pv).sum() / (pu**2 + pv**2).sum()
+
+
+def _lattice_tg_nu(orc, n, tau, steps):
+    k, U = 2 * math.pi / n, 1e-3
+    X, Y = np.meshgrid(np.arange(n), np.arange(n))  # [y, x]
+    pu, pv = _tg_modes(k, X, Y)
+    f = np.zeros((n, n, 9))
+    for j in range(n):
+        for i in range(n):
+            f[j, i] = orc.feq(1.0, U * pu[j, i], U * pv[j, i])
+    amp = []
+    for _ in range(2):
+        f = orc.lattice_periodic(f, tau, steps)
+        r = f.sum(-1)
+        amp.append(_tg_amplitude((f * CX).sum(-1) / r, (f * CY).sum(-1) / r, pu, pv))
+    return math.log(amp[0] / amp[1]) / steps / (2 * k**2)
+
+
+def _fv_tg_nu(orc, n, tau_u, dt, t_end):
+    xy, tri, txy = _periodic_mesh(n)
+    ops = orc.fv_operators(xy, tri, txy)
+    k, U = 2 * math.pi / n, 1e-3
+    pu, pv = _tg_modes(k, xy[:, 0], xy[:, 1])
+    g = np.array([orc.feq(1.0, U * a, U * b) for a, b in zip(pu, pv)])
+    steps = int(round(t_end / dt))
+    amp = []
+    for _ in range(2):
+        for _ in range(steps):
+            g = orc.fv_substep(ops, dt, tau_u, g)
+        r = g.sum(1)
+        amp.append(_tg_amplitude((g * CX).sum(1) / r, (g * CY).sum(1) / r, pu, pv))
+    return math.log(amp[0] / amp[1]) / t_end / (2 * k**2)
+
+
+def test_taylor_green_decay_on_the_lattice(orc):
+    """Eq. 1: the Taylor-Green vortex of wavenumber k in both directions decays
+    at the closed-form rate 2 nu k^2 with nu = c_s^2 (tau - 1/2); the error
+    falls by 4x per halving of the lattice spacing (second order)."""
+    tau = 0.8
+    nu = (tau - 0.5) / 3
+    e16 = abs(_lattice_tg_nu(orc, 16, tau, 60) / nu - 1)
+    e32 = abs(_lattice_tg_nu(orc, 32, tau, 240) / nu - 1)
+    assert e32 < 2e-3
+    assert 3.5 < e16 / e32 < 4.5
+
+
+def test_taylor_green_decay_on_the_mesh(orc):
+    """Eq. 3: the same vortex on a periodic triangulated square decays at
+    2 nu k^2 with nu = c_s^2 tau_u, second order in the mesh spacing."""
+    tau_u = 0.1
+    nu = tau_u / 3
+    e8 = abs(_fv_tg_nu(orc, 8, tau_u, 0.002, 10.0) / nu - 1)
+    e16 = abs(_fv_tg_nu(orc, 16, tau_u, 0.002, 40.0) / nu - 1)
+    assert e16 < 0.08
+    assert 3.5 < e8 / e16 < 4.5
+
+
 def test_fv_uniform_state_is_steady(orc):
     """Eq. 3: a uniform equilibrium is a fixed point (sum_k s_k = 0, and f = f^eq)."""
     xy, tri = _random_patch()
